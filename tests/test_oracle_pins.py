@@ -1,0 +1,447 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed forms, invariants, library routines that a special case reduces to, and
+brute force.  CPU only."""
+import json
+import os
+from fractions import Fraction
+
+import mpmath
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+import oracle as O
+from oracle import graph as G
+from paper_2008_11476_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BORDERS = [O.BORDER_REPLICATE, O.BORDER_CONSTANT, O.BORDER_UNDEFINED]
+
+
+def interior(a, r):
+    return a[r:-r, r:-r] if r else a
+
+
+# --- Gaussian3x3 -------------------------------------------------------------------
+
+@pytest.mark.parametrize("c", [0, 1, 77, 255])
+@pytest.mark.parametrize("border", BORDERS)
+def test_gaussian_constant_is_fixed_point(orc, c, border):
+    img = np.full((9, 13), c, np.uint8)
+    out = O.gaussian3x3(img, border, cval=c)
+    if border == O.BORDER_UNDEFINED:
+        assert out.rect == (1, 1, 12, 8)
+        assert (interior(out.data, 1) == c).all()
+        assert (out.data[0] == 0).all() and (out.data[:, -1] == 0).all()
+    else:
+        assert out.rect == (0, 0, 13, 9)
+        assert (out.data == c).all()
+
+
+def test_gaussian_linear_ramp_interior(orc):
+    y, x = np.mgrid[0:20, 0:30]
+    img = (3 * x + 5 * y + 7).astype(np.uint8)  # max 3*29+5*19+7 = 189
+    out = O.gaussian3x3(img, O.BORDER_REPLICATE)
+    assert (interior(out.data, 1) == interior(img, 1)).all()
+
+
+@pytest.mark.parametrize("rounding,expect", [(O.ROUND_ZERO, (63, 31, 15)),
+                                              (O.ROUND_NEAREST, (64, 32, 16))])
+def test_gaussian_impulse(orc, rounding, expect):
+    img = np.zeros((7, 7), np.uint8)
+    img[3, 3] = 255
+    out = O.gaussian3x3(img, O.BORDER_REPLICATE, rounding=rounding).data
+    centre, edge, corner = expect
+    assert out[3, 3] == centre
+    assert out[2, 3] == out[4, 3] == out[3, 2] == out[3, 4] == edge
+    assert out[2, 2] == out[2, 4] == out[4, 2] == out[4, 4] == corner
+    assert out.sum() == centre + 4 * edge + 4 * corner
+
+
+def test_gaussian_one_pixel(orc):
+    img = np.array([[200]], np.uint8)
+    assert O.gaussian3x3(img, O.BORDER_REPLICATE).data[0, 0] == 200
+    # constant 10 around a single 200: (4*200 + 12*10) / 16 = 57.5 -> 57
+    assert O.gaussian3x3(img, O.BORDER_CONSTANT, cval=10).data[0, 0] == 57
+    assert O.gaussian3x3(img, O.BORDER_UNDEFINED).rect == (1, 1, 1, 1)
+
+
+@pytest.mark.parametrize("shape", [(1, 5), (5, 1), (2, 2), (17, 23), (32, 45)])
+def test_gaussian_matches_scipy_correlate(orc, shape):
+    img = synth.uniform_u8(shape[1], shape[0], seed=11)
+    w = np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]], np.int64)
+    ref_rep = ndi.correlate(img.astype(np.int64), w, mode="nearest") // 16
+    ref_con = ndi.correlate(img.astype(np.int64), w, mode="constant", cval=33) // 16
+    assert (O.gaussian3x3(img, O.BORDER_REPLICATE).data == ref_rep).all()
+    assert (O.gaussian3x3(img, O.BORDER_CONSTANT, cval=33).data == ref_con).all()
+
+
+def test_box3x3_matches_scipy(orc):
+    img = synth.uniform_u8(31, 17, seed=3)
+    ref = ndi.correlate(img.astype(np.int64), np.ones((3, 3), np.int64), mode="nearest")
+    assert (O.box3x3(img, O.BORDER_REPLICATE).data == ref // 9).all()
+    assert (O.box3x3(img, O.BORDER_REPLICATE, rounding=O.ROUND_NEAREST).data
+            == (ref + 4) // 9).all()
+
+
+# --- Sobel3x3 ------------------------------------------------------------------------
+
+def test_sobel_constant_is_zero(orc):
+    for border in BORDERS:
+        gx, gy = O.sobel3x3(np.full((6, 8), 99, np.uint8), border, cval=99)
+        assert (gx.data == 0).all() and (gy.data == 0).all()
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (0, 1), (2, 3), (4, 1)])
+def test_sobel_linear_ramp(orc, a, b):
+    y, x = np.mgrid[0:16, 0:20]
+    img = (a * x + b * y).astype(np.uint8)
+    gx, gy = O.sobel3x3(img, O.BORDER_REPLICATE)
+    assert (interior(gx.data, 1) == 8 * a).all()
+    assert (interior(gy.data, 1) == 8 * b).all()
+    # replicated edge columns / rows see half the difference
+    assert (gx.data[1:-1, 0] == 4 * a).all() and (gx.data[1:-1, -1] == 4 * a).all()
+    assert (gy.data[0, 1:-1] == 4 * b).all() and (gy.data[-1, 1:-1] == 4 * b).all()
+
+
+def test_sobel_matches_scipy_correlate(orc):
+    img = synth.uniform_u8(37, 29, seed=5)
+    kx = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]])
+    gx, gy = O.sobel3x3(img, O.BORDER_REPLICATE)
+    assert (gx.data == ndi.correlate(img.astype(np.int64), kx, mode="nearest")).all()
+    assert (gy.data == ndi.correlate(img.astype(np.int64), kx.T, mode="nearest")).all()
+    gx, gy = O.sobel3x3(img, O.BORDER_UNDEFINED)
+    ref = ndi.correlate(img.astype(np.int64), kx.T, mode="constant")
+    assert gx.rect == (1, 1, 36, 28)
+    assert (interior(gy.data, 1) == interior(ref, 1)).all()
+    assert (gy.data[0] == 0).all()
+
+
+# --- Magnitude / Phase -------------------------------------------------------------
+
+def _all_pairs(lim=1020):
+    v = np.arange(-lim, lim + 1, dtype=np.int16)
+    gx, gy = np.meshgrid(v, v)
+    return np.ascontiguousarray(gx), np.ascontiguousarray(gy)
+
+
+def test_magnitude_exhaustive_against_integer_sqrt(orc):
+    gx, gy = _all_pairs()
+    m = O.magnitude(gx, gy).data.astype(np.int64)
+    s4 = 4 * (gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2)
+    # floor(sqrt(s) + 1/2) == (isqrt(4 s) + 1) // 2, isqrt by integer correction
+    r = np.floor(np.sqrt(s4.astype(np.float64))).astype(np.int64)
+    r -= (r * r > s4)
+    r += ((r + 1) * (r + 1) <= s4)
+    assert (m == (r + 1) // 2).all()
+
+
+def test_phase_cardinal_and_diagonal_directions(orc):
+    cases = {(5, 0): 0, (0, 5): 64, (-5, 0): 128, (0, -5): 192, (7, 7): 32, (-7, 7): 96,
+             (-7, -7): 160, (7, -7): 224, (0, 0): 0}
+    gx = np.array([[k[0] for k in cases]], np.int16)
+    gy = np.array([[k[1] for k in cases]], np.int16)
+    assert list(O.phase(gx, gy).data[0]) == list(cases.values())
+
+
+def test_phase_symmetries(orc):
+    gx, gy = _all_pairs(300)
+    q = O.phase(gx, gy).data.astype(np.int64)
+    q_neg = O.phase(np.ascontiguousarray(-gx), np.ascontiguousarray(-gy)).data
+    q_swap = O.phase(gy, gx).data.astype(np.int64)
+    nz = (gx != 0) | (gy != 0)
+    assert (((q + 128) % 256)[nz] == q_neg[nz]).all()       # rotation by pi
+    assert (((64 - q) % 256)[nz] == q_swap[nz]).all()        # reflection in y = x
+
+
+def test_phase_against_mpmath_sample(orc):
+    mpmath.mp.dps = 40
+    rng = synth.randint(21, 0, 4000, -1020, 1020).reshape(2000, 2)
+    gx = np.ascontiguousarray(rng[:, 0].astype(np.int16)).reshape(1, -1)
+    gy = np.ascontiguousarray(rng[:, 1].astype(np.int16)).reshape(1, -1)
+    q = O.phase(gx, gy).data[0]
+    for i in range(gx.shape[1]):
+        a, b = int(gx[0, i]), int(gy[0, i])
+        if a == 0 and b == 0:
+            assert q[i] == 0
+            continue
+        phi = mpmath.atan2(b, a)
+        if phi < 0:
+            phi += 2 * mpmath.pi
+        exp = int(mpmath.floor(phi * 128 / mpmath.pi + mpmath.mpf(1) / 2)) % 256
+        assert q[i] == exp, (a, b)
+
+
+# --- Threshold ---------------------------------------------------------------------
+
+def test_threshold_step_at_value(orc):
+    v = np.arange(-32768, 32768, dtype=np.int32).astype(np.int16).reshape(256, 256)
+    out = O.threshold(v, 100).data.reshape(-1)
+    idx = np.arange(-32768, 32768)
+    assert out[idx == 100][0] == 0 and out[idx == 101][0] == 255
+    assert (np.diff(out.astype(np.int64)) >= 0).all()        # one step only
+    assert int((out == 255).sum()) == 32767 - 100
+    r = O.threshold_range(v, -5, 7, true_val=9, false_val=1).data.reshape(-1)
+    assert int((r == 9).sum()) == 13 and set(np.unique(r)) == {1, 9}
+
+
+def test_threshold_f32_uses_binary32_value(orc):
+    # 1e6 + 0.04 rounds to 1e6 + 0.0625 in binary32 (spacing 1/16 at 2^19..2^20)
+    x = np.array([[1e6, np.float32(1e6 + 0.04), np.nextafter(np.float32(1e6), 0)]],
+                 np.float32)
+    assert list(O.threshold(x, 1e6).data[0]) == [0, 255, 0]
+
+
+# --- ChannelExtract / arithmetic -----------------------------------------------------
+
+def test_channel_extract_inverts_interleave(orc):
+    w, h = 10, 3
+    Y = synth.uniform_u8(w, h, 1)
+    U = synth.uniform_u8(w // 2, h, 2)
+    V = synth.uniform_u8(w // 2, h, 3)
+    uyvy = np.empty((h, 2 * w), np.uint8)
+    uyvy[:, 0::4], uyvy[:, 1::4], uyvy[:, 2::4], uyvy[:, 3::4] = U, Y[:, 0::2], V, Y[:, 1::2]
+    assert (O.channel_extract_uyvy(uyvy, 0).data == Y).all()
+    assert (O.channel_extract_uyvy(uyvy, 1).data == U).all()
+    assert (O.channel_extract_uyvy(uyvy, 2).data == V).all()
+
+
+def test_arith_special_values(orc):
+    a = np.array([[200, 0, 255, 17]], np.uint8)
+    b = np.array([[100, 0, 255, 3]], np.uint8)
+    assert list(O.arith(a, b, np.uint8, O.ARITH_ADD, True).data[0]) == [255, 0, 255, 20]
+    assert list(O.arith(a, b, np.uint8, O.ARITH_ADD, False).data[0]) == [44, 0, 254, 20]
+    assert list(O.arith(a, b, np.int16, O.ARITH_ADD, True).data[0]) == [300, 0, 510, 20]
+    assert list(O.arith(b, a, np.uint8, O.ARITH_SUB, True).data[0]) == [0, 0, 0, 0]
+    assert list(O.arith(b, a, np.int16, O.ARITH_SUB, True).data[0]) == [-100, 0, 0, -14]
+    assert list(O.arith(b, a, np.uint8, O.ARITH_ABSDIFF, True).data[0]) == [100, 0, 0, 14]
+    s = np.array([[32000, -32000]], np.int16)
+    assert list(O.arith(s, s, np.int16, O.ARITH_ADD, True).data[0]) == [32767, -32768]
+    assert list(O.arith(s, s, np.int16, O.ARITH_ADD, False).data[0]) == [-1536, 1536]
+
+
+def test_arith_commutes_and_has_identity(orc):
+    a = synth.uniform_u8(40, 7, 8)
+    b = synth.uniform_u8(40, 7, 9)
+    z = np.zeros_like(a)
+    for sat in (True, False):
+        assert (O.arith(a, b, np.uint8, 0, sat).data == O.arith(b, a, np.uint8, 0, sat).data).all()
+        assert (O.arith(a, z, np.uint8, 0, sat).data == a).all()
+
+
+def test_convolve_laplacian_matches_scipy(orc):
+    img = synth.uniform_u8(25, 19, 4)
+    lap = np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], np.int32)
+    ref = ndi.correlate(img.astype(np.int64), lap, mode="nearest")
+    assert (O.convolve(img, lap, 0, O.BORDER_REPLICATE).data == ref).all()
+    # floor division by 2 for negative sums
+    assert (O.convolve(img, lap, 1, O.BORDER_REPLICATE).data == np.floor_divide(ref, 2)).all()
+
+
+# --- Harris pieces -----------------------------------------------------------------
+
+def test_window_sum_matches_scipy(orc):
+    a = synth.randint(3, 0, 21 * 15, -50000, 50000).astype(np.int32).reshape(15, 21)
+    ref = ndi.correlate(a.astype(np.int64), np.ones((5, 5), np.int64), mode="constant")
+    out = O.window_sum(a, 5, 5, O.BORDER_UNDEFINED)
+    assert out.rect == (2, 2, 19, 13)
+    assert (interior(out.data, 2) == interior(ref, 2)).all()
+    assert (out.data[:2] == 0).all() and (out.data[:, -2:] == 0).all()
+    rep = ndi.correlate(a.astype(np.int64), np.ones((3, 5), np.int64), mode="nearest")
+    assert (O.window_sum(a, 5, 3, O.BORDER_REPLICATE).data == rep).all()
+
+
+def _mp_round24(fr: Fraction) -> float:
+    """p/q rounded once to a 24-bit significand, ties to even (mpmath)."""
+    return float(mpmath.mpf(mpmath.libmp.from_rational(fr.numerator, fr.denominator, 24, "n")))
+
+
+def test_round_ratio_is_correctly_rounded(orc):
+    nums = [1, 2, 3, 7, 24, 25, 26, 16777217, 16777219, 25000001, 10**15 + 7,
+            -(10**14) - 3, 2**53 + 1, -5, 0]
+    nums += [int(v) for v in synth.randint(17, 0, 300, -(2**40), 2**40)]
+    for den in (1, 3, 7, 25, 1000):
+        for n in nums:
+            assert O.round_ratio(n, den) == _mp_round24(Fraction(n, den)), (n, den)
+    # ties go to the even significand
+    assert O.round_ratio(16777217, 1) == 16777216.0
+    assert O.round_ratio(16777219, 1) == 16777220.0
+
+
+def test_harris_response_closed_forms(orc):
+    s = np.array([[0, 5, 1000, 26010000]], np.int32)
+    z = np.zeros_like(s)
+    # Sxx = Syy = s, Sxy = 0, k = 1/25: R = s^2 - 4 s^2 / 25 = 21 s^2 / 25
+    r = O.harris_response(s, s, z, 1, 25).data[0]
+    for i, v in enumerate(s[0]):
+        assert r[i] == _mp_round24(Fraction(21 * int(v) ** 2, 25))
+    # a pure edge (Syy = Sxy = 0): R = -k Sxx^2 <= 0
+    r = O.harris_response(s, z, z, 1, 25).data[0]
+    assert (r <= 0).all() and r[2] == -40000.0
+    # Sxy^2 = Sxx Syy (rank one): det = 0
+    a = np.array([[4, 9]], np.int32)
+    b = np.array([[9, 4]], np.int32)
+    c = np.array([[6, -6]], np.int32)
+    r = O.harris_response(a, b, c, 1, 25).data[0]
+    assert list(r) == [_mp_round24(Fraction(-169, 25))] * 2
+
+
+def test_harris_graph_flat_edge_corner(orc):
+    img = np.full((40, 48), 90, np.uint8)
+    mask, resp = O.harris_graph(img, thr=1e6)
+    assert (resp == 0).all() and (mask == 0).all()
+    # vertical step edge: no positive response anywhere
+    img[:, 24:] = 200
+    mask, resp = O.harris_graph(img, thr=0.0)
+    assert (resp <= 0).all() and (mask == 0).all()
+    # bright square on dark: positive responses at its four corners only
+    img = np.zeros((40, 48), np.uint8)
+    img[10:30, 12:36] = 200
+    mask, resp = O.harris_graph(img, thr=1e6)
+    ys, xs = np.nonzero(mask)
+    assert len(ys) > 0
+    for y, x in zip(ys, xs):
+        assert min(abs(y - 10), abs(y - 29)) <= 3 and min(abs(x - 12), abs(x - 35)) <= 3
+    # undefined border: 3 pixels on each side stay zero
+    assert (resp[:3] == 0).all() and (resp[:, -3:] == 0).all()
+
+
+def test_edge_graph_ramp_and_constant(orc):
+    img = np.full((24, 32), 140, np.uint8)
+    ph, mk = O.edge_graph(img)
+    assert (ph == 0).all() and (mk == 0).all()
+    y, x = np.mgrid[0:24, 0:32]
+    ramp = (3 * x + 4 * y).astype(np.uint8)
+    ph, mk, mag = O.edge_graph(ramp, want_mag=True)
+    # Gaussian keeps the ramp inside 1 px; Sobel there sees gx = 24, gy = 32
+    assert (mag[2:-2, 2:-2] == 40).all()
+    assert (mk[2:-2, 2:-2] == 0).all()
+    # atan2(32, 24) = 0.9273 rad -> 0.9273 * 128 / pi = 37.78 -> 38
+    assert (ph[2:-2, 2:-2] == 38).all()
+
+
+# --- graph verification and Algorithm 1 ---------------------------------------------
+
+def _load_listing1():
+    spec = json.load(open(os.path.join(GOLDEN, "listing1_edge_graph.json")))
+    g = G.GraphDesc()
+    for im in spec["images"]:
+        if im["virtual"]:
+            g.virtual(im["name"])
+        else:
+            g.image(im["name"], im["w"], im["h"], im["fmt"])
+    for n in spec["nodes"]:
+        g.node(n["kind"], n["ins"], n["outs"], **n["params"])
+    return spec, g
+
+
+def test_listing1_dead_sobel_output(orc):
+    spec, g = _load_listing1()
+    ops = G.verify(g)
+    alive, alive_data = G.eliminate_dead(g, ops)
+    assert sorted(op.name for op in alive) == sorted(spec["expected_alive_ops"])
+    dead = sorted({op.name for op in ops} - {op.name for op in alive})
+    assert dead == spec["expected_dead_ops"]
+    for d in spec["expected_dead_data"]:
+        assert d not in alive_data
+
+
+def test_listing1_runs(orc):
+    spec, g = _load_listing1()
+    img0 = synth.uyvy(64, 48, 3)
+    out = G.run(g, {"img0": img0})["img1"].data
+    Y = O.channel_extract_uyvy(img0, 0)
+    _, gy = O.sobel3x3(O.gaussian3x3(Y, O.BORDER_REPLICATE))
+    ref = O.threshold(O.magnitude(gy, gy), 100).data
+    assert (out == ref).all()
+
+
+def _brute_alive(g, ops):
+    """An op is alive iff a directed path leads from it to a non-virtual image."""
+    readers = {}
+    for op in ops:
+        for i in op.ins:
+            readers.setdefault(i, []).append(op)
+    alive = set()
+    for op in ops:
+        stack, seen, hit = [op], set(), False
+        while stack and not hit:
+            o = stack.pop()
+            if o.name in seen:
+                continue
+            seen.add(o.name)
+            if not g.data[o.out].virtual:
+                hit = True
+            stack.extend(readers.get(o.out, ()))
+        if hit:
+            alive.add(op.name)
+    return alive
+
+
+def test_algorithm1_matches_brute_force_on_random_dags(orc):
+    kinds_1in = ["gaussian3x3", "box3x3"]
+    for seed in range(60):
+        u = synth.uniform01(seed, 30, 200)
+        k = 0
+        g = G.GraphDesc()
+        g.image("in0", 8, 8, "U8")
+        pool = ["in0"]
+        n_nodes = 2 + int(u[k] * 8); k += 1
+        for i in range(n_nodes):
+            src = pool[int(u[k] * len(pool))]; k += 1
+            virt = u[k] < 0.6; k += 1
+            name = f"d{i}"
+            if virt:
+                g.virtual(name)
+            else:
+                g.image(name, 8, 8, "U8")
+            g.node(kinds_1in[int(u[k] * 2)], [src], [name]); k += 1
+            pool.append(name)
+        ops = G.verify(g)
+        alive, _ = G.eliminate_dead(g, ops)
+        assert {op.name for op in alive} == _brute_alive(g, ops), seed
+
+
+def test_verify_rejects_cycle_and_bad_graphs(orc):
+    g = G.GraphDesc()
+    g.virtual("a", 8, 8, "U8")
+    g.virtual("b", 8, 8, "U8")
+    g.node("gaussian3x3", ["a"], ["b"])
+    g.node("gaussian3x3", ["b"], ["a"])
+    with pytest.raises(G.GraphError):
+        G.verify(g)
+    g = G.GraphDesc()
+    g.image("in", 8, 8, "S16")
+    g.image("out", 8, 8, "U8")
+    g.node("gaussian3x3", ["in"], ["out"])            # S16 into a U8-only input
+    with pytest.raises(G.GraphError):
+        G.verify(g)
+    g = G.GraphDesc()
+    g.image("in", 8, 8, "U8")
+    g.virtual("v")
+    g.image("out", 8, 8, "U8")
+    g.node("gaussian3x3", ["v"], ["out"])              # virtual never written
+    with pytest.raises(G.GraphError):
+        G.verify(g)
+    g = G.GraphDesc()
+    g.image("in", 8, 8, "U8")
+    g.image("out", 8, 8, "U8")
+    g.node("gaussian3x3", ["in"], ["out"])
+    g.node("box3x3", ["in"], ["out"])                  # two writers
+    with pytest.raises(G.GraphError):
+        G.verify(g)
+    assert not G.is_bipartite([(("D", "a"), ("D", "b"))])
+
+
+def test_nonvirtual_intermediate_keeps_upstream_alive(orc):
+    g = G.GraphDesc()
+    g.image("in", 8, 8, "U8")
+    g.image("mid", 8, 8, "U8")        # non-virtual, read downstream
+    g.virtual("dead")
+    g.node("gaussian3x3", ["in"], ["mid"])
+    g.node("box3x3", ["mid"], ["dead"])
+    g.image("iso", 8, 8, "U8")        # isolated image
+    ops = G.verify(g)
+    alive, data = G.eliminate_dead(g, ops)
+    assert [op.name for op in alive] == ["n0"]
+    assert "iso" not in data and "dead" not in data
