@@ -1,0 +1,762 @@
+// C ABI of the image-graph library: handle checks, object ownership and the
+// node constructors (Section 3.1, Listing 1; Section 5.1, Listing 4).
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "hvx_internal.h"
+
+using namespace hvx;
+
+namespace hvx {
+
+hvx_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return HVX_SUCCESS;
+    if (e == cudaErrorMemoryAllocation) return HVX_ERROR_NO_MEMORY;
+    return HVX_ERROR_DEVICE;
+}
+
+// ---------------------------------------------------------------------------
+DevicePool::~DevicePool() {
+    for (auto& kv : live_) cudaFree(kv.first);
+    for (auto& kv : cache_) cudaFree(kv.second);
+}
+
+hvx_status DevicePool::alloc(uint64_t bytes, void** out) {
+    std::lock_guard<std::mutex> lk(mu_);
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes == 0) bytes = 256;
+    // reuse a cached block of the same size
+    auto it = cache_.find(bytes);
+    if (it != cache_.end()) {
+        void* p = it->second;
+        cache_.erase(it);
+        live_[p] = bytes;
+        in_use_ += bytes;
+        *out = p;
+        return HVX_SUCCESS;
+    }
+    if (budget_ && in_use_ + bytes > budget_) return HVX_ERROR_OVER_BUDGET;
+    // return cached blocks to the driver until the new block fits the budget
+    while (budget_ && held_ + bytes > budget_ && !cache_.empty()) {
+        auto c = cache_.begin();
+        cudaFree(c->second);
+        held_ -= c->first;
+        cache_.erase(c);
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        // retry once after emptying the cache
+        for (auto& kv : cache_) {
+            cudaFree(kv.second);
+            held_ -= kv.first;
+        }
+        cache_.clear();
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return HVX_ERROR_NO_MEMORY;
+        }
+    }
+    live_[p] = bytes;
+    in_use_ += bytes;
+    held_ += bytes;
+    *out = p;
+    return HVX_SUCCESS;
+}
+
+void DevicePool::free(void* p) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = live_.find(p);
+    if (it == live_.end()) return;
+    in_use_ -= it->second;
+    cache_.emplace(it->second, p);
+    live_.erase(it);
+}
+
+void DevicePool::trim() {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto& kv : cache_) {
+        cudaFree(kv.second);
+        held_ -= kv.first;
+    }
+    cache_.clear();
+}
+
+}  // namespace hvx
+
+namespace {
+
+bool ok_ctx(hvx_context c) { return c && reinterpret_cast<Context*>(c)->magic == kMagicContext; }
+bool ok_graph(hvx_graph g) { return g && reinterpret_cast<Graph*>(g)->magic == kMagicGraph; }
+bool ok_image(hvx_image i) { return i && reinterpret_cast<Image*>(i)->magic == kMagicImage; }
+bool ok_node(hvx_node n) { return n && reinterpret_cast<Node*>(n)->magic == kMagicNode; }
+
+Context* C(hvx_context c) { return reinterpret_cast<Context*>(c); }
+Graph* G(hvx_graph g) { return reinterpret_cast<Graph*>(g); }
+Image* I(hvx_image i) { return reinterpret_cast<Image*>(i); }
+Node* N(hvx_node n) { return reinterpret_cast<Node*>(n); }
+
+bool valid_fmt(int f) { return f >= HVX_DF_U8 && f <= HVX_DF_UYVY; }
+
+void destroy_image(Image* im) {
+    if (im->dev && im->owns_mem) im->ctx->pool.free(im->dev);
+    im->magic = 0;
+    delete im;
+}
+
+void maybe_destroy(Image* im) {
+    if (im->user_refs <= 0 && im->node_refs <= 0 && !im->is_virtual) {
+        auto& v = im->ctx->images;
+        v.erase(std::remove(v.begin(), v.end(), im), v.end());
+        destroy_image(im);
+    }
+}
+
+void destroy_graph(Graph* g) {
+    if (g->scheduled && g->done) cudaEventSynchronize(g->done);
+    release_plan(g);
+    for (auto& n : g->nodes) {
+        for (Image* im : n->in)
+            if (im && !im->is_virtual) im->node_refs--;
+        for (Image* im : n->out)
+            if (im && !im->is_virtual) im->node_refs--;
+        n->magic = 0;
+    }
+    g->nodes.clear();
+    for (Image* v : g->virtuals) destroy_image(v);
+    g->virtuals.clear();
+    if (g->done) cudaEventDestroy(g->done);
+    g->magic = 0;
+    Context* ctx = g->ctx;
+    auto& gv = ctx->graphs;
+    gv.erase(std::remove(gv.begin(), gv.end(), g), gv.end());
+    delete g;
+    // images that were only kept alive by this graph's nodes
+    std::vector<Image*> imgs = ctx->images;
+    for (Image* im : imgs) maybe_destroy(im);
+}
+
+// A node is added only if every image argument is a live image of the
+// graph's context (virtual images must belong to the graph itself).
+bool image_usable(Graph* g, Image* im) {
+    if (!ok_image(reinterpret_cast<hvx_image>(im))) return false;
+    if (im->ctx != g->ctx) return false;
+    if (im->is_virtual && im->owner_graph != g) return false;
+    return true;
+}
+
+hvx_node add_node(hvx_graph hg, int kind, std::initializer_list<hvx_image> ins,
+                  std::initializer_list<hvx_image> outs, int required_outs, const NodeParams& p) {
+    if (!ok_graph(hg)) return nullptr;
+    Graph* g = G(hg);
+    std::unique_ptr<Node> n(new (std::nothrow) Node());
+    if (!n) {
+        g->last = HVX_ERROR_NO_MEMORY;
+        return nullptr;
+    }
+    for (hvx_image h : ins) {
+        if (!h || !image_usable(g, I(h))) {
+            g->last = HVX_ERROR_INVALID_REFERENCE;
+            return nullptr;
+        }
+        n->in.push_back(I(h));
+    }
+    int k = 0;
+    for (hvx_image h : outs) {
+        if (!h) {
+            if (k < required_outs) {
+                g->last = HVX_ERROR_INVALID_REFERENCE;
+                return nullptr;
+            }
+            n->out.push_back(nullptr);
+        } else {
+            if (!image_usable(g, I(h))) {
+                g->last = HVX_ERROR_INVALID_REFERENCE;
+                return nullptr;
+            }
+            n->out.push_back(I(h));
+        }
+        ++k;
+    }
+    n->graph = g;
+    n->kind = kind;
+    n->p = p;
+    for (Image* im : n->in)
+        if (!im->is_virtual) im->node_refs++;
+    for (Image* im : n->out)
+        if (im && !im->is_virtual) im->node_refs++;
+    Node* raw = n.get();
+    g->nodes.push_back(std::move(n));
+    release_plan(g);
+    g->last = HVX_SUCCESS;
+    return reinterpret_cast<hvx_node>(raw);
+}
+
+hvx_status set_last(Graph* g, hvx_status st) {
+    g->last = st;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hvxStatusString(hvx_status s) {
+    switch (s) {
+        case HVX_SUCCESS: return "HVX_SUCCESS";
+        case HVX_ERROR_INVALID_REFERENCE: return "HVX_ERROR_INVALID_REFERENCE";
+        case HVX_ERROR_INVALID_PARAMETERS: return "HVX_ERROR_INVALID_PARAMETERS";
+        case HVX_ERROR_INVALID_FORMAT: return "HVX_ERROR_INVALID_FORMAT";
+        case HVX_ERROR_INVALID_GRAPH: return "HVX_ERROR_INVALID_GRAPH";
+        case HVX_ERROR_NOT_VERIFIED: return "HVX_ERROR_NOT_VERIFIED";
+        case HVX_ERROR_NO_MEMORY: return "HVX_ERROR_NO_MEMORY";
+        case HVX_ERROR_OVER_BUDGET: return "HVX_ERROR_OVER_BUDGET";
+        case HVX_ERROR_TIMEOUT: return "HVX_ERROR_TIMEOUT";
+        case HVX_ERROR_DEVICE: return "HVX_ERROR_DEVICE";
+        case HVX_ERROR_NOT_SUPPORTED: return "HVX_ERROR_NOT_SUPPORTED";
+    }
+    return "HVX_UNKNOWN_STATUS";
+}
+
+hvx_status hvxCreateContext(hvx_context* out) { return hvxCreateContextEx(0, out); }
+
+hvx_status hvxCreateContextEx(int32_t flags, hvx_context* out) {
+    if (!out || (flags & ~HVX_CONTEXT_PLAN_ONLY)) return HVX_ERROR_INVALID_PARAMETERS;
+    Context* c = new (std::nothrow) Context();
+    if (!c) return HVX_ERROR_NO_MEMORY;
+    if (flags & HVX_CONTEXT_PLAN_ONLY) {
+        c->plan_only = true;
+        *out = reinterpret_cast<hvx_context>(c);
+        return HVX_SUCCESS;
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HVX_ERROR_DEVICE;
+    }
+    hvx_status st = ensure_context_device_state(c);
+    if (st != HVX_SUCCESS) {
+        delete c;
+        return st;
+    }
+    *out = reinterpret_cast<hvx_context>(c);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxReleaseContext(hvx_context* pc) {
+    if (!pc || !ok_ctx(*pc)) return HVX_ERROR_INVALID_REFERENCE;
+    Context* c = C(*pc);
+    if (!c->plan_only) cudaDeviceSynchronize();
+    std::vector<Server*> servers = c->servers;
+    for (Server* s : servers) server_destroy(s);
+    std::vector<Graph*> graphs = c->graphs;
+    for (Graph* g : graphs) destroy_graph(g);
+    std::vector<Image*> images = c->images;
+    for (Image* im : images) destroy_image(im);
+    c->images.clear();
+    destroy_batch_cache(c);
+    if (c->d_error) cudaFree(c->d_error);
+    c->magic = 0;
+    delete c;
+    *pc = nullptr;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxSetContextMemoryBudget(hvx_context ctx, uint64_t bytes) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    C(ctx)->pool.set_budget(bytes);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxGetContextMemoryUsage(hvx_context ctx, uint64_t* bytes) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!bytes) return HVX_ERROR_INVALID_PARAMETERS;
+    *bytes = C(ctx)->pool.in_use();
+    return HVX_SUCCESS;
+}
+
+// ---- images -----------------------------------------------------------------
+
+hvx_status hvxCreateImage(hvx_context ctx, uint32_t w, uint32_t h, int32_t fmt, hvx_image* out) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out || w == 0 || h == 0 || w > 32768u || h > 32768u)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    if (!valid_fmt(fmt)) return HVX_ERROR_INVALID_FORMAT;
+    if (fmt == HVX_DF_UYVY && (w & 1)) return HVX_ERROR_INVALID_PARAMETERS;
+    Context* c = C(ctx);
+    Image* im = new (std::nothrow) Image();
+    if (!im) return HVX_ERROR_NO_MEMORY;
+    im->ctx = c;
+    im->w = w;
+    im->h = h;
+    im->fmt = fmt;
+    im->pitch = ((uint64_t)w * bytes_per_pixel(fmt) + 127) / 128 * 128;
+    im->bytes = im->pitch * h;
+    if (!c->plan_only) {
+        hvx_status st = c->pool.alloc(im->bytes, &im->dev);
+        if (st != HVX_SUCCESS) {
+            delete im;
+            return st;
+        }
+        im->owns_mem = true;
+    }
+    im->valid = Rect{0, 0, (int)w, (int)h};
+    c->images.push_back(im);
+    *out = reinterpret_cast<hvx_image>(im);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxCreateImageFromHandle(hvx_context ctx, uint32_t w, uint32_t h, int32_t fmt,
+                                    void* dev_ptr, uint64_t pitch, hvx_image* out) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out || !dev_ptr || w == 0 || h == 0 || w > 32768u || h > 32768u)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    if (!valid_fmt(fmt)) return HVX_ERROR_INVALID_FORMAT;
+    if (fmt == HVX_DF_UYVY && (w & 1)) return HVX_ERROR_INVALID_PARAMETERS;
+    if (((uintptr_t)dev_ptr & 15) || (pitch & 15) || pitch < (uint64_t)w * bytes_per_pixel(fmt))
+        return HVX_ERROR_INVALID_PARAMETERS;
+    Image* im = new (std::nothrow) Image();
+    if (!im) return HVX_ERROR_NO_MEMORY;
+    im->ctx = C(ctx);
+    im->w = w;
+    im->h = h;
+    im->fmt = fmt;
+    im->dev = dev_ptr;
+    im->pitch = pitch;
+    im->bytes = pitch * h;
+    im->owns_mem = false;
+    im->valid = Rect{0, 0, (int)w, (int)h};
+    C(ctx)->images.push_back(im);
+    *out = reinterpret_cast<hvx_image>(im);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxSwapImageHandle(hvx_image img, void* dev_ptr, uint64_t pitch) {
+    if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
+    Image* im = I(img);
+    if (im->is_virtual || im->owns_mem) return HVX_ERROR_INVALID_REFERENCE;
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 15) || (pitch & 15) ||
+        pitch < (uint64_t)im->w * bytes_per_pixel(im->fmt))
+        return HVX_ERROR_INVALID_PARAMETERS;
+    im->dev = dev_ptr;
+    im->pitch = pitch;
+    im->bytes = pitch * im->h;
+    // launch parameters embed addresses and pitches: rebuild them for every
+    // verified graph that uses the image
+    for (Graph* g : im->ctx->graphs) {
+        if (!g->verified) continue;
+        bool uses = false;
+        for (auto& n : g->nodes) {
+            for (Image* x : n->in) uses |= x == im;
+            for (Image* x : n->out) uses |= x == im;
+        }
+        if (uses) {
+            if (g->scheduled) cudaEventSynchronize(g->done);
+            hvx_status st = prepare_launches(g);
+            if (st != HVX_SUCCESS) {
+                release_plan(g);
+                return st;
+            }
+        }
+    }
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxCreateVirtualImage(hvx_graph hg, uint32_t w, uint32_t h, int32_t fmt,
+                                 hvx_image* out) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out || (w == 0) != (h == 0)) return HVX_ERROR_INVALID_PARAMETERS;
+    if (fmt != HVX_DF_VIRT && !valid_fmt(fmt)) return HVX_ERROR_INVALID_FORMAT;
+    Graph* g = G(hg);
+    Image* im = new (std::nothrow) Image();
+    if (!im) return HVX_ERROR_NO_MEMORY;
+    im->ctx = g->ctx;
+    im->owner_graph = g;
+    im->is_virtual = true;
+    im->w = w;
+    im->h = h;
+    im->user_fixed_size = w != 0;
+    im->fmt = fmt;
+    im->user_fmt = fmt;
+    g->virtuals.push_back(im);
+    *out = reinterpret_cast<hvx_image>(im);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxReleaseImage(hvx_image* pimg) {
+    if (!pimg || !ok_image(*pimg)) return HVX_ERROR_INVALID_REFERENCE;
+    Image* im = I(*pimg);
+    *pimg = nullptr;
+    if (im->is_virtual) return HVX_SUCCESS;  // owned by its graph
+    im->user_refs--;
+    maybe_destroy(im);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxCopyImage(hvx_image img, void* host, uint64_t host_pitch, int32_t usage) {
+    if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
+    Image* im = I(img);
+    if (im->is_virtual) return HVX_ERROR_INVALID_REFERENCE;
+    if (im->ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    uint64_t row = (uint64_t)im->w * bytes_per_pixel(im->fmt);
+    if (!host || host_pitch < row) return HVX_ERROR_INVALID_PARAMETERS;
+    cudaError_t e;
+    if (usage == HVX_READ)
+        e = cudaMemcpy2D(host, host_pitch, im->dev, im->pitch, row, im->h, cudaMemcpyDeviceToHost);
+    else if (usage == HVX_WRITE)
+        e = cudaMemcpy2D(im->dev, im->pitch, host, host_pitch, row, im->h, cudaMemcpyHostToDevice);
+    else
+        return HVX_ERROR_INVALID_PARAMETERS;
+    return cuda_status(e);
+}
+
+hvx_status hvxGetImageDevicePtr(hvx_image img, void** dev, uint64_t* pitch) {
+    if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
+    Image* im = I(img);
+    if (im->is_virtual) return HVX_ERROR_INVALID_REFERENCE;
+    if (!dev || !pitch) return HVX_ERROR_INVALID_PARAMETERS;
+    *dev = im->dev;
+    *pitch = im->pitch;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxQueryImage(hvx_image img, uint32_t* w, uint32_t* h, int32_t* fmt) {
+    if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
+    Image* im = I(img);
+    if (w) *w = im->w;
+    if (h) *h = im->h;
+    if (fmt) *fmt = im->fmt;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxGetValidRegion(hvx_image img, hvx_rect* r) {
+    if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!r) return HVX_ERROR_INVALID_PARAMETERS;
+    Image* im = I(img);
+    r->start_x = im->valid.x0;
+    r->start_y = im->valid.y0;
+    r->end_x = im->valid.x1;
+    r->end_y = im->valid.y1;
+    return HVX_SUCCESS;
+}
+
+// ---- graphs -----------------------------------------------------------------------
+
+hvx_status hvxCreateGraph(hvx_context ctx, hvx_graph* out) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out) return HVX_ERROR_INVALID_PARAMETERS;
+    Graph* g = new (std::nothrow) Graph();
+    if (!g) return HVX_ERROR_NO_MEMORY;
+    g->ctx = C(ctx);
+    if (!g->ctx->plan_only &&
+        cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return HVX_ERROR_DEVICE;
+    }
+    C(ctx)->graphs.push_back(g);
+    *out = reinterpret_cast<hvx_graph>(g);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxReleaseGraph(hvx_graph* pg) {
+    if (!pg || !ok_graph(*pg)) return HVX_ERROR_INVALID_REFERENCE;
+    destroy_graph(G(*pg));
+    *pg = nullptr;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxVerifyGraph(hvx_graph hg) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = G(hg);
+    if (g->busy.load()) return set_last(g, HVX_ERROR_INVALID_GRAPH);
+    if (g->scheduled) {
+        cudaEventSynchronize(g->done);
+        g->scheduled = false;
+    }
+    return set_last(g, verify_graph(g));
+}
+
+hvx_status hvxScheduleGraph(hvx_graph hg, void* stream) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = G(hg);
+    if (!g->verified) return set_last(g, HVX_ERROR_NOT_VERIFIED);
+    if (g->ctx->plan_only) return set_last(g, HVX_ERROR_NOT_SUPPORTED);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    hvx_status st = launch_plan(g, s);
+    if (st != HVX_SUCCESS) return set_last(g, st);
+    if (cudaEventRecord(g->done, s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_last(g, HVX_ERROR_DEVICE);
+    }
+    g->scheduled = true;
+    g->last_stream = s;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxWaitGraph(hvx_graph hg) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = G(hg);
+    if (!g->scheduled) return HVX_SUCCESS;
+    cudaError_t e = cudaEventSynchronize(g->done);
+    g->scheduled = false;
+    if (e != cudaSuccess) return set_last(g, cuda_status(e));
+    return set_last(g, check_device_error(g->ctx));
+}
+
+hvx_status hvxProcessGraph(hvx_graph hg) {
+    hvx_status st = hvxScheduleGraph(hg, nullptr);
+    if (st != HVX_SUCCESS) return st;
+    return hvxWaitGraph(hg);
+}
+
+hvx_status hvxSetGraphFusion(hvx_graph hg, int32_t enable) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = G(hg);
+    g->fusion = enable != 0;
+    release_plan(g);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxGetGraphStatus(hvx_graph hg) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    return G(hg)->last;
+}
+
+hvx_status hvxQueryGraph(hvx_graph hg, int32_t attr, void* out, uint64_t size) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = G(hg);
+    if (!out) return HVX_ERROR_INVALID_PARAMETERS;
+    auto put32 = [&](int32_t v) {
+        if (size < 4) return HVX_ERROR_INVALID_PARAMETERS;
+        std::memcpy(out, &v, 4);
+        return HVX_SUCCESS;
+    };
+    auto put64 = [&](uint64_t v) {
+        if (size < 8) return HVX_ERROR_INVALID_PARAMETERS;
+        std::memcpy(out, &v, 8);
+        return HVX_SUCCESS;
+    };
+    switch (attr) {
+        case HVX_GRAPH_NUM_NODES: return put32((int32_t)g->nodes.size());
+        case HVX_GRAPH_FUSION: return put32(g->fusion ? 1 : 0);
+        default: break;
+    }
+    if (!g->verified) return HVX_ERROR_NOT_VERIFIED;
+    switch (attr) {
+        case HVX_GRAPH_NUM_OPS: return put32((int32_t)g->plan.ops.size());
+        case HVX_GRAPH_NUM_ALIVE_OPS: return put32((int32_t)g->plan.order.size());
+        case HVX_GRAPH_NUM_LAUNCHES: return put32((int32_t)g->plan.groups.size());
+        case HVX_GRAPH_INTERMEDIATE_BYTES: return put64(g->plan.intermediate_bytes);
+        case HVX_GRAPH_EXTERNAL_BYTES: return put64(g->plan.external_bytes);
+        case HVX_GRAPH_KERNEL_KINDS: {
+            const std::string& s = g->plan.kernel_kinds;
+            if (size < s.size() + 1) return HVX_ERROR_INVALID_PARAMETERS;
+            std::memcpy(out, s.c_str(), s.size() + 1);
+            return HVX_SUCCESS;
+        }
+    }
+    return HVX_ERROR_INVALID_PARAMETERS;
+}
+
+hvx_status hvxProcessGraphBatch(const hvx_graph* gs, int32_t n, void* stream) {
+    if (!gs || n <= 0) return HVX_ERROR_INVALID_PARAMETERS;
+    std::vector<Graph*> v;
+    for (int i = 0; i < n; ++i) {
+        if (!ok_graph(gs[i])) return HVX_ERROR_INVALID_REFERENCE;
+        if (!G(gs[i])->verified) return HVX_ERROR_NOT_VERIFIED;
+        if (G(gs[i])->ctx != G(gs[0])->ctx) return HVX_ERROR_INVALID_REFERENCE;
+        v.push_back(G(gs[i]));
+    }
+    if (v[0]->ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    return process_batch(v[0]->ctx, v.data(), n, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hvx_status hvxWaitBatch(hvx_context ctx, void* stream) {
+    if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
+    if (C(ctx)->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e);
+    return check_device_error(C(ctx));
+}
+
+// ---- nodes ----------------------------------------------------------------------------
+
+hvx_node hvxGaussian3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_GAUSS, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxBox3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_BOX, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxSobel3x3Node(hvx_graph g, hvx_image in, hvx_image gx, hvx_image gy) {
+    if (ok_graph(g) && !gx && !gy) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    return add_node(g, N_SOBEL, {in}, {gx, gy}, 0, NodeParams());
+}
+
+hvx_node hvxMagnitudeNode(hvx_graph g, hvx_image gx, hvx_image gy, hvx_image out) {
+    return add_node(g, N_MAG, {gx, gy}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxPhaseNode(hvx_graph g, hvx_image gx, hvx_image gy, hvx_image out) {
+    return add_node(g, N_PHASE, {gx, gy}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxThresholdNode(hvx_graph g, hvx_image in, int32_t type, double value, double upper,
+                          int32_t tv, int32_t fv, hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if ((type != HVX_THRESHOLD_BINARY && type != HVX_THRESHOLD_RANGE) || tv < 0 || tv > 255 ||
+        fv < 0 || fv > 255 || !std::isfinite(value) ||
+        (type == HVX_THRESHOLD_RANGE && (!std::isfinite(upper) || upper < value))) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.thr_type = type;
+    p.thr_value = value;
+    p.thr_upper = upper;
+    p.true_value = tv;
+    p.false_value = fv;
+    return add_node(g, N_THRESH, {in}, {out}, 1, p);
+}
+
+hvx_node hvxChannelExtractNode(hvx_graph g, hvx_image in, int32_t channel, hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if (channel < HVX_CHANNEL_Y || channel > HVX_CHANNEL_V) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.channel = channel;
+    return add_node(g, N_CHX, {in}, {out}, 1, p);
+}
+
+static hvx_node arith_node(hvx_graph g, int kind, hvx_image a, hvx_image b, int32_t policy,
+                           hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if (policy != HVX_POLICY_WRAP && policy != HVX_POLICY_SATURATE) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.policy = policy;
+    return add_node(g, kind, {a, b}, {out}, 1, p);
+}
+
+hvx_node hvxAddNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out) {
+    return arith_node(g, N_ADD, a, b, policy, out);
+}
+
+hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out) {
+    return arith_node(g, N_SUB, a, b, policy, out);
+}
+
+hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
+    return arith_node(g, N_ABSDIFF, a, b, HVX_POLICY_SATURATE, out);
+}
+
+hvx_node hvxConvolveNode(hvx_graph g, hvx_image in, const int32_t* coeffs, int32_t kw,
+                         int32_t kh, int32_t shift, hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if (!coeffs || kw < 1 || kh < 1 || kw > 7 || kh > 7 || !(kw & 1) || !(kh & 1) || shift < 0 ||
+        shift > 30) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.kw = kw;
+    p.kh = kh;
+    p.shift = shift;
+    p.coeffs.assign(coeffs, coeffs + kw * kh);
+    return add_node(g, N_CONV, {in}, {out}, 1, p);
+}
+
+hvx_node hvxPointNode(hvx_graph g, int32_t op, const hvx_image* ins, int32_t n_in,
+                      hvx_image out, const double* params, int32_t n_params) {
+    if (!ok_graph(g)) return nullptr;
+    NodeParams p;
+    p.custom_op = op;
+    if (op == HVX_POINT_MUL) {
+        if (n_in != 2 || !ins) {
+            G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+            return nullptr;
+        }
+        return add_node(g, N_POINT, {ins[0], ins[1]}, {out}, 1, p);
+    }
+    if (op == HVX_POINT_HARRIS_RESPONSE) {
+        if (n_in != 3 || !ins || n_params != 2 || !params || params[0] != std::floor(params[0]) ||
+            params[1] != std::floor(params[1]) || params[0] < 0 || params[0] > 1000 ||
+            params[1] < 1 || params[1] > 1000) {
+            G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+            return nullptr;
+        }
+        p.kn = (int64_t)params[0];
+        p.kd = (int64_t)params[1];
+        return add_node(g, N_POINT, {ins[0], ins[1], ins[2]}, {out}, 1, p);
+    }
+    G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+    return nullptr;
+}
+
+hvx_node hvxLocalNode(hvx_graph g, int32_t op, int32_t kw, int32_t kh, hvx_image in,
+                      hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if (op != HVX_LOCAL_SUM || kw < 1 || kh < 1 || kw > 9 || kh > 9 || !(kw & 1) || !(kh & 1)) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.custom_op = op;
+    p.kw = kw;
+    p.kh = kh;
+    return add_node(g, N_LOCAL, {in}, {out}, 1, p);
+}
+
+hvx_status hvxSetNodeBorder(hvx_node hn, int32_t mode, int32_t constant) {
+    if (!ok_node(hn)) return HVX_ERROR_INVALID_REFERENCE;
+    if (mode != HVX_BORDER_UNDEFINED && mode != HVX_BORDER_REPLICATE &&
+        mode != HVX_BORDER_CONSTANT)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    Node* n = N(hn);
+    n->border = mode;
+    n->cval = constant;
+    release_plan(n->graph);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxSetNodeRounding(hvx_node hn, int32_t rounding) {
+    if (!ok_node(hn)) return HVX_ERROR_INVALID_REFERENCE;
+    if (rounding != HVX_ROUND_TO_ZERO && rounding != HVX_ROUND_TO_NEAREST)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    Node* n = N(hn);
+    n->rounding = rounding;
+    release_plan(n->graph);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxQueryNode(hvx_node hn, int32_t attr, void* out, uint64_t size) {
+    if (!ok_node(hn)) return HVX_ERROR_INVALID_REFERENCE;
+    Node* n = N(hn);
+    if (!out || size < 4) return HVX_ERROR_INVALID_PARAMETERS;
+    if (!n->graph->verified) return HVX_ERROR_NOT_VERIFIED;
+    if (attr == HVX_NODE_LIVE_OUTPUTS) {
+        uint32_t m = n->live_mask;
+        std::memcpy(out, &m, 4);
+        return HVX_SUCCESS;
+    }
+    if (attr == HVX_NODE_GROUP) {
+        int32_t gi = n->live_mask ? n->group : -1;
+        std::memcpy(out, &gi, 4);
+        return HVX_SUCCESS;
+    }
+    return HVX_ERROR_INVALID_PARAMETERS;
+}
+
+}  // extern "C"

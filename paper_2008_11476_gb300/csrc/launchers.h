@@ -1,0 +1,31 @@
+// Host-side launch entry points of the CUDA kernels (one per kernel family).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "kernel_params.h"
+
+namespace hvx {
+
+// Persistent edge / Gaussian kernel over the tiles of many images.
+struct EdgeBatchDesc {
+    const CUtensorMap* maps;     // one per image, 64-byte aligned, in device memory
+    const EdgeParams* params;    // one per image, in device memory
+    const int* tile_start;       // n_img + 1 prefix sums of per-image tile counts
+    int n_img;
+    int total_tiles;
+    int gauss_only;
+    int* err;
+};
+
+cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, bool gauss_only,
+                        cudaStream_t s);
+cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
+int edge_batch_blocks_per_sm();
+
+cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);
+cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);
+cudaError_t launch_plain(const PlainParams& p, cudaStream_t s);
+
+}  // namespace hvx

@@ -1,0 +1,707 @@
+// Execution runtime: per-group kernel selection and launch parameters (TMA
+// descriptors included), plan launch, the device error word, and the batched
+// persistent launch replayed from captured CUDA graphs.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <unordered_map>
+
+#include "hvx_internal.h"
+#include "launchers.h"
+
+namespace hvx {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+std::atomic<uint64_t> g_plan_counter{0};
+
+hvx_status get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    });
+    return g_encode ? HVX_SUCCESS : HVX_ERROR_DEVICE;
+}
+
+// 2-D U8 tensor map of an image with a (box_w x box_h) box; out-of-image
+// elements of a box read as 0.
+hvx_status encode_u8_map(CUtensorMap* map, const Image* im, uint32_t box_w, uint32_t box_h) {
+    if (im->ctx->plan_only) {
+        std::memset(map, 0, sizeof(*map));
+        return HVX_SUCCESS;
+    }
+    hvx_status st = get_encoder();
+    if (st != HVX_SUCCESS) return st;
+    if (((uintptr_t)im->dev & 15) || (im->pitch & 15)) return HVX_ERROR_INVALID_PARAMETERS;
+    cuuint64_t dims[2] = {im->w, im->h};
+    cuuint64_t strides[1] = {im->pitch};
+    cuuint32_t box[2] = {box_w, box_h};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, im->dev, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HVX_SUCCESS : HVX_ERROR_DEVICE;
+}
+
+void set_rect(int32_t* d, const Rect& r) {
+    d[0] = r.x0;
+    d[1] = r.y0;
+    d[2] = r.x1;
+    d[3] = r.y1;
+}
+
+uint64_t image_bytes(const Image* im) { return (uint64_t)im->w * im->h * bytes_per_pixel(im->fmt); }
+
+// Point-operator parameters shared by GenStage and PlainParams.
+template <class T>
+void fill_point_params(T& st, const Op& op) {
+    const NodeParams& p = op.node->p;
+    st.i0 = st.i1 = st.i2 = st.i3 = 0;
+    st.f0 = st.f1 = 0.f;
+    st.k0 = st.k1 = 0;
+    switch (op.kind) {
+        case OP_THRESH:
+            st.i0 = p.thr_type;
+            st.i1 = p.true_value;
+            st.i2 = p.false_value;
+            st.i3 = op.in[0]->fmt == HVX_DF_F32;
+            st.k0 = (int64_t)p.thr_value;
+            st.k1 = (int64_t)p.thr_upper;
+            st.f0 = (float)p.thr_value;
+            st.f1 = (float)p.thr_upper;
+            break;
+        case OP_ADD:
+        case OP_SUB:
+        case OP_ABSDIFF:
+            st.i0 = p.policy == HVX_POLICY_SATURATE;
+            st.i1 = op.out->fmt;
+            break;
+        case OP_HARRIS:
+            st.k0 = p.kn;
+            st.k1 = p.kd;
+            break;
+        case OP_CHX: st.i0 = p.channel; break;
+        default: break;
+    }
+}
+
+// ---- edge group ---------------------------------------------------------------
+
+struct EdgeMatch {
+    int gauss = -1, sx = -1, sy = -1, mag = -1, thr = -1, ph = -1;
+};
+
+bool match_edge(const Plan& P, const Group& G, EdgeMatch& m) {
+    for (int i : G.ops) {
+        int* slot = nullptr;
+        switch (P.ops[i].kind) {
+            case OP_GAUSS: slot = &m.gauss; break;
+            case OP_SOBEL_X: slot = &m.sx; break;
+            case OP_SOBEL_Y: slot = &m.sy; break;
+            case OP_MAG: slot = &m.mag; break;
+            case OP_THRESH: slot = &m.thr; break;
+            case OP_PHASE: slot = &m.ph; break;
+            default: return false;
+        }
+        if (*slot >= 0) return false;
+        *slot = i;
+    }
+    if (m.gauss < 0 || m.sx < 0 || m.sy < 0) return false;
+    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx], &sy = P.ops[m.sy];
+    if (G.inputs.size() != 1 || G.inputs[0] != g.in[0] || g.in[0]->fmt != HVX_DF_U8) return false;
+    if (sx.in[0] != g.out || sy.in[0] != g.out || sx.node != sy.node) return false;
+    if (m.mag >= 0 && (P.ops[m.mag].in[0] != sx.out || P.ops[m.mag].in[1] != sy.out)) return false;
+    if (m.ph >= 0 && (P.ops[m.ph].in[0] != sx.out || P.ops[m.ph].in[1] != sy.out)) return false;
+    if (m.thr >= 0 && (m.mag < 0 || P.ops[m.thr].in[0] != P.ops[m.mag].out)) return false;
+    if (G.outputs.empty()) return false;
+    for (Image* o : G.outputs) {
+        bool ok = (m.thr >= 0 && o == P.ops[m.thr].out) || (m.ph >= 0 && o == P.ops[m.ph].out) ||
+                  (m.mag >= 0 && o == P.ops[m.mag].out);
+        if (!ok) return false;
+    }
+    return true;
+}
+
+void base_edge_params(EdgeParams& e, const Group& G, const Image* in, Context* ctx) {
+    std::memset(&e, 0, sizeof(e));
+    e.W = G.W;
+    e.H = G.H;
+    e.in = static_cast<const uint8_t*>(in->dev);
+    e.in_pitch = in->pitch;
+    e.err = ctx->d_error;
+    e.valid[0] = e.valid[1] = 0;
+    e.valid[2] = G.W;
+    e.valid[3] = G.H;
+}
+
+hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
+    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx];
+    EdgeParams& e = G.edge;
+    base_edge_params(e, G, g.in[0], ctx);
+    e.border_g = g.node->border;
+    e.cval_g = g.node->cval & 0xFF;
+    e.border_s = sx.node->border;
+    e.cval_s = sx.node->cval & 0xFF;
+    e.rounding = g.node->rounding;
+    set_rect(e.gvalid, g.out->valid);
+    set_rect(e.valid, rect_intersect(sx.out->valid, P.ops[m.sy].out->valid));
+    auto is_out = [&](const Image* im) {
+        return std::find(G.outputs.begin(), G.outputs.end(), im) != G.outputs.end();
+    };
+    if (m.ph >= 0) {
+        e.phase = static_cast<uint8_t*>(P.ops[m.ph].out->dev);
+        e.phase_pitch = P.ops[m.ph].out->pitch;
+    }
+    if (m.mag >= 0 && is_out(P.ops[m.mag].out)) {
+        e.mag = static_cast<int16_t*>(P.ops[m.mag].out->dev);
+        e.mag_pitch = P.ops[m.mag].out->pitch;
+    }
+    if (m.thr >= 0) {
+        const Op& t = P.ops[m.thr];
+        const NodeParams& tp = t.node->p;
+        e.mask = static_cast<uint8_t*>(t.out->dev);
+        e.mask_pitch = t.out->pitch;
+        e.tv = tp.true_value;
+        e.fv = tp.false_value;
+        e.thr_type = tp.thr_type;
+        e.thr_lo = (int32_t)std::max<int64_t>(-40000, std::min<int64_t>(40000, (int64_t)tp.thr_value));
+        e.thr_hi = (int32_t)std::max<int64_t>(-40000, std::min<int64_t>(40000, (int64_t)tp.thr_upper));
+        if (tp.thr_type == HVX_THRESHOLD_BINARY) {
+            // round(sqrt(s)) > T  <=>  s > T^2 + T  (T >= 0), always true for T < 0
+            int64_t T = (int64_t)tp.thr_value;
+            e.thr_general = 0;
+            if (T < 0)
+                e.s_thr = -1;
+            else if (T >= 32767)
+                e.s_thr = std::numeric_limits<int64_t>::max();
+            else
+                e.s_thr = T * T + T;
+        } else {
+            e.thr_general = 1;
+        }
+    }
+    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_TH + 4);
+}
+
+hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
+    const Op& g = P.ops[G.ops[0]];
+    EdgeParams& e = G.edge;
+    base_edge_params(e, G, g.in[0], ctx);
+    e.border_g = g.node->border;
+    e.cval_g = g.node->cval & 0xFF;
+    e.border_s = HVX_BORDER_UNDEFINED;
+    e.rounding = g.node->rounding;
+    e.gout = static_cast<uint8_t*>(g.out->dev);
+    e.gout_pitch = g.out->pitch;
+    set_rect(e.gvalid, g.out->valid);
+    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_TH + 4);
+}
+
+// ---- Harris group -------------------------------------------------------------
+
+struct HarrisMatch {
+    int sx = -1, sy = -1, pxx = -1, pyy = -1, pxy = -1, sxx = -1, syy = -1, sxy = -1, resp = -1,
+        thr = -1;
+};
+
+bool match_harris(const Plan& P, const Group& G, HarrisMatch& m) {
+    std::vector<int> muls, sums;
+    for (int i : G.ops) {
+        const Op& o = P.ops[i];
+        switch (o.kind) {
+            case OP_SOBEL_X:
+                if (m.sx >= 0) return false;
+                m.sx = i;
+                break;
+            case OP_SOBEL_Y:
+                if (m.sy >= 0) return false;
+                m.sy = i;
+                break;
+            case OP_MUL: muls.push_back(i); break;
+            case OP_LSUM: sums.push_back(i); break;
+            case OP_HARRIS:
+                if (m.resp >= 0) return false;
+                m.resp = i;
+                break;
+            case OP_THRESH:
+                if (m.thr >= 0) return false;
+                m.thr = i;
+                break;
+            default: return false;
+        }
+    }
+    if (m.sx < 0 || m.sy < 0 || muls.size() != 3 || sums.size() != 3 || m.resp < 0) return false;
+    const Op &sx = P.ops[m.sx], &sy = P.ops[m.sy];
+    if (sx.node != sy.node || G.inputs.size() != 1 || G.inputs[0] != sx.in[0]) return false;
+    Image *X = sx.out, *Y = sy.out;
+    for (int i : muls) {
+        const Op& o = P.ops[i];
+        if (o.in[0] == X && o.in[1] == X)
+            m.pxx = i;
+        else if (o.in[0] == Y && o.in[1] == Y)
+            m.pyy = i;
+        else if ((o.in[0] == X && o.in[1] == Y) || (o.in[0] == Y && o.in[1] == X))
+            m.pxy = i;
+        else
+            return false;
+    }
+    if (m.pxx < 0 || m.pyy < 0 || m.pxy < 0) return false;
+    const Op& s0 = P.ops[sums[0]];
+    for (int i : sums) {
+        const Op& o = P.ops[i];
+        if (o.rx != 2 || o.ry != 2 || o.node->border != s0.node->border ||
+            o.node->cval != s0.node->cval)
+            return false;
+        if (o.in[0] == P.ops[m.pxx].out)
+            m.sxx = i;
+        else if (o.in[0] == P.ops[m.pyy].out)
+            m.syy = i;
+        else if (o.in[0] == P.ops[m.pxy].out)
+            m.sxy = i;
+        else
+            return false;
+    }
+    if (m.sxx < 0 || m.syy < 0 || m.sxy < 0) return false;
+    const Op& r = P.ops[m.resp];
+    if (r.in[0] != P.ops[m.sxx].out || r.in[1] != P.ops[m.syy].out || r.in[2] != P.ops[m.sxy].out)
+        return false;
+    if (m.thr >= 0) {
+        const Op& t = P.ops[m.thr];
+        if (t.in[0] != r.out || t.node->p.thr_type != HVX_THRESHOLD_BINARY) return false;
+    }
+    for (Image* o : G.outputs)
+        if (!(o == r.out || (m.thr >= 0 && o == P.ops[m.thr].out))) return false;
+    return !G.outputs.empty();
+}
+
+// Largest q with round_to_binary32(q / kd) <= T, so that a binary32 response
+// exceeds T exactly when q > q_thr.  With m the midpoint between T and the
+// next binary32 value above it, round(v) <= T holds for v < m, and at v = m
+// when T's significand is even (ties to even).  kd * m is exact in double.
+int64_t harris_q_threshold(float T, int64_t kd) {
+    const double lim = 4611686018427387904.0;  // 2^62, beyond any |q| of 5x5 sums
+    if (std::isnan(T)) return std::numeric_limits<int64_t>::max();
+    float up = std::nextafter(T, std::numeric_limits<float>::infinity());
+    if (std::isinf(T) && T > 0) return std::numeric_limits<int64_t>::max();
+    double m = ((double)T + (double)up) * 0.5;
+    double B = (double)kd * m;
+    if (B >= lim) return (int64_t)lim;
+    if (B <= -lim) return -(int64_t)lim;
+    uint32_t bits;
+    std::memcpy(&bits, &T, 4);
+    bool tie_down = (bits & 1u) == 0;
+    double fl = std::floor(B);
+    if (fl == B) return tie_down ? (int64_t)B : (int64_t)B - 1;
+    return (int64_t)fl;
+}
+
+hvx_status build_harris(Plan& P, Group& G, const HarrisMatch& m, Context* ctx) {
+    const Op &sx = P.ops[m.sx], &s0 = P.ops[m.sxx], &r = P.ops[m.resp];
+    HarrisParams& h = G.harris;
+    std::memset(&h, 0, sizeof(h));
+    h.W = G.W;
+    h.H = G.H;
+    h.in = static_cast<const uint8_t*>(sx.in[0]->dev);
+    h.in_pitch = sx.in[0]->pitch;
+    h.border_s = sx.node->border;
+    h.cval_s = sx.node->cval & 0xFF;
+    h.border_b = s0.node->border;
+    h.cval_b = s0.node->cval;
+    h.wr = 2;
+    h.kn = r.node->p.kn;
+    h.kd = r.node->p.kd;
+    set_rect(h.pvalid, P.ops[m.pxy].out->valid);
+    set_rect(h.valid, r.out->valid);
+    h.err = ctx->d_error;
+    bool resp_out = std::find(G.outputs.begin(), G.outputs.end(), r.out) != G.outputs.end();
+    if (resp_out) {
+        h.resp = static_cast<float*>(r.out->dev);
+        h.resp_pitch = r.out->pitch;
+    }
+    if (m.thr >= 0) {
+        const Op& t = P.ops[m.thr];
+        h.mask = static_cast<uint8_t*>(t.out->dev);
+        h.mask_pitch = t.out->pitch;
+        h.tv = t.node->p.true_value;
+        h.fv = t.node->p.false_value;
+        h.q_thr = harris_q_threshold((float)t.node->p.thr_value, h.kd);
+    }
+    return encode_u8_map(&G.tmap, sx.in[0], HARRIS_LOAD_W, HARRIS_TH + 6);
+}
+
+// ---- plain point / generic ------------------------------------------------------
+
+void plain_img(PlainImg& d, const Image* im) {
+    d.ptr = im->dev;
+    d.pitch = im->pitch;
+    d.fmt = im->fmt;
+    d.pad = 0;
+}
+
+hvx_status build_point(Plan& P, Group& G) {
+    const Op& op = P.ops[G.ops[0]];
+    PlainParams& pp = G.plain;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.W = op.out->w;
+    pp.H = op.out->h;
+    pp.op = op.kind;
+    pp.n_in = op.n_in;
+    pp.n_out = 1;
+    for (int k = 0; k < op.n_in; ++k) plain_img(pp.in[k], op.in[k]);
+    plain_img(pp.out[0], op.out);
+    set_rect(pp.valid, op.out->valid);
+    fill_point_params(pp, op);
+    if (op.out->ctx->plan_only) return HVX_SUCCESS;
+    for (int k = 0; k < op.n_in; ++k)
+        if (!op.in[k]->dev) return HVX_ERROR_INVALID_GRAPH;
+    return op.out->dev ? HVX_SUCCESS : HVX_ERROR_INVALID_GRAPH;
+}
+
+hvx_status build_generic(Plan& P, Group& G) {
+    GenericDesc& d = G.gdesc;
+    std::memset(&d, 0, sizeof(d));
+    d.W = G.W;
+    d.H = G.H;
+    // halo of every image: sum of the window radii of in-group ops downstream
+    std::unordered_map<const Image*, int> halo, buf;
+    std::unordered_map<int, int> h_out;
+    for (auto it = G.ops.rbegin(); it != G.ops.rend(); ++it) {
+        const Op& op = P.ops[*it];
+        int h = 0;
+        for (int j : G.ops) {
+            const Op& c = P.ops[j];
+            for (int k = 0; k < c.n_in; ++k)
+                if (c.in[k] == op.out) h = std::max(h, h_out[j] + std::max(c.rx, c.ry));
+        }
+        h_out[*it] = h;
+        halo[op.out] = std::max(halo[op.out], h);
+    }
+    for (int j : G.ops) {
+        const Op& c = P.ops[j];
+        for (int k = 0; k < c.n_in; ++k)
+            if (std::find(G.inputs.begin(), G.inputs.end(), c.in[k]) != G.inputs.end())
+                halo[c.in[k]] = std::max(halo[c.in[k]], h_out[j] + std::max(c.rx, c.ry));
+    }
+    std::vector<const Image*> images(G.inputs.begin(), G.inputs.end());
+    for (int i : G.ops) images.push_back(P.ops[i].out);
+    if ((int)images.size() > GEN_MAX_BUF || (int)G.ops.size() > GEN_MAX_STAGE ||
+        (int)G.inputs.size() > GEN_MAX_EXT || (int)G.outputs.size() > GEN_MAX_EXT)
+        return HVX_ERROR_NOT_SUPPORTED;
+    int words = 0;
+    for (const Image* im : images) {
+        int b = d.n_buf++;
+        buf[im] = b;
+        GenBuf& gb = d.buf[b];
+        gb.halo = halo[im];
+        if (gb.halo > GEN_MAX_HALO) return HVX_ERROR_NOT_SUPPORTED;
+        gb.is_float = im->fmt == HVX_DF_F32;
+        gb.fill = FILL_NONE;
+        gb.cval = 0;
+        for (int j : G.ops) {
+            const Op& c = P.ops[j];
+            if (!op_is_local(c.kind)) continue;
+            for (int k = 0; k < c.n_in; ++k)
+                if (c.in[k] == im) {
+                    if (c.node->border == HVX_BORDER_REPLICATE) gb.fill = FILL_REPLICATE;
+                    if (c.node->border == HVX_BORDER_CONSTANT) {
+                        gb.fill = FILL_CONSTANT;
+                        gb.cval = im->fmt == HVX_DF_U8 ? (c.node->cval & 0xFF) : c.node->cval;
+                    }
+                }
+        }
+        set_rect(gb.valid, im->valid);
+        gb.smem_off = words;
+        words += (GEN_TW + 2 * gb.halo) * (GEN_TH + 2 * gb.halo);
+    }
+    d.smem_words = words;
+    if (words * 4 > 220 * 1024) return HVX_ERROR_NOT_SUPPORTED;
+    int coeffs = 0;
+    for (int i : G.ops) {
+        const Op& op = P.ops[i];
+        GenStage& st = d.st[d.n_stage++];
+        st.op = op.kind;
+        st.in[0] = st.in[1] = st.in[2] = -1;
+        for (int k = 0; k < op.n_in; ++k) st.in[k] = buf[op.in[k]];
+        st.out = buf[op.out];
+        st.rx = op.rx;
+        st.ry = op.ry;
+        st.rounding = op.node->rounding;
+        fill_point_params(st, op);
+        if (op.kind == OP_CONV) {
+            const std::vector<int32_t>& c = op.node->p.coeffs;
+            if (coeffs + (int)c.size() > GEN_MAX_COEFF) return HVX_ERROR_NOT_SUPPORTED;
+            st.coeff_off = coeffs;
+            st.shift = op.node->p.shift;
+            for (int32_t v : c) d.coeff[coeffs++] = v;
+        }
+    }
+    for (const Image* im : G.inputs) {
+        GenExt& e = d.in[d.n_in++];
+        e.ptr = im->dev;
+        e.pitch = im->pitch;
+        e.fmt = im->fmt;
+        e.buf = buf[im];
+        if (!im->dev && !im->ctx->plan_only) return HVX_ERROR_INVALID_GRAPH;
+    }
+    for (const Image* im : G.outputs) {
+        GenExt& e = d.out[d.n_out++];
+        e.ptr = im->dev;
+        e.pitch = im->pitch;
+        e.fmt = im->fmt;
+        e.buf = buf[im];
+        if (!im->dev && !im->ctx->plan_only) return HVX_ERROR_INVALID_GRAPH;
+    }
+    return HVX_SUCCESS;
+}
+
+}  // namespace
+
+hvx_status ensure_context_device_state(Context* ctx) {
+    if (!ctx->d_error) {
+        cudaError_t e = cudaMalloc(&ctx->d_error, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return HVX_ERROR_NO_MEMORY;
+        }
+        if (cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess) return HVX_ERROR_DEVICE;
+    }
+    if (!ctx->num_sms) {
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (ctx->num_sms <= 0) ctx->num_sms = 1;
+    }
+    return HVX_SUCCESS;
+}
+
+hvx_status check_device_error(Context* ctx) {
+    int v = 0;
+    if (cudaMemcpy(&v, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return HVX_ERROR_DEVICE;
+    }
+    if (v == 0) return HVX_SUCCESS;
+    cudaMemset(ctx->d_error, 0, sizeof(int));
+    return HVX_ERROR_TIMEOUT;
+}
+
+hvx_status prepare_launches(Graph* g) {
+    Plan& P = g->plan;
+    Context* ctx = g->ctx;
+    for (Group& G : P.groups) {
+        G.ext_bytes = G.mem_bytes = 0;
+        for (Image* im : G.inputs) {
+            G.mem_bytes += image_bytes(im);
+            if (!im->is_virtual) G.ext_bytes += image_bytes(im);
+        }
+        for (Image* im : G.outputs) {
+            G.mem_bytes += image_bytes(im);
+            if (!im->is_virtual) G.ext_bytes += image_bytes(im);
+        }
+        hvx_status st;
+        EdgeMatch em;
+        HarrisMatch hm;
+        const Op& first = P.ops[G.ops[0]];
+        if (G.ops.size() == 1 && first.kind == OP_GAUSS) {
+            G.kernel = GK_GAUSS;
+            st = build_gauss(P, G, ctx);
+        } else if (G.ops.size() == 1 && first.kind == OP_CHX &&
+                   first.node->p.channel != HVX_CHANNEL_Y) {
+            G.kernel = GK_CHX_UV;
+            st = build_point(P, G);
+        } else if (G.ops.size() == 1 && !op_is_local(first.kind)) {
+            G.kernel = GK_POINT;
+            st = build_point(P, G);
+        } else if (match_edge(P, G, em)) {
+            G.kernel = GK_EDGE;
+            st = build_edge(P, G, em, ctx);
+        } else if (match_harris(P, G, hm)) {
+            G.kernel = GK_HARRIS;
+            st = build_harris(P, G, hm, ctx);
+        } else {
+            G.kernel = GK_GENERIC;
+            st = build_generic(P, G);
+        }
+        if (st != HVX_SUCCESS) return st;
+    }
+    g->plan_id = ++g_plan_counter;
+    return HVX_SUCCESS;
+}
+
+hvx_status launch_plan(Graph* g, cudaStream_t s) {
+    for (Group& G : g->plan.groups) {
+        cudaError_t e = cudaSuccess;
+        switch (G.kernel) {
+            case GK_GAUSS: e = launch_edge(G.tmap, G.edge, true, s); break;
+            case GK_EDGE: e = launch_edge(G.tmap, G.edge, false, s); break;
+            case GK_HARRIS: e = launch_harris(G.tmap, G.harris, s); break;
+            case GK_POINT:
+            case GK_CHX_UV: e = launch_plain(G.plain, s); break;
+            default: e = launch_generic(G.gdesc, s); break;
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return HVX_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch
+
+struct BatchEntry {
+    std::vector<Graph*> graphs;
+    std::vector<uint64_t> plan_ids;
+    void* dmem = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+struct BatchCache {
+    std::vector<BatchEntry> entries;
+    cudaStream_t capture = nullptr;
+    uint64_t tick = 0;
+};
+
+void destroy_batch_cache(Context* ctx) {
+    BatchCache* bc = ctx->batch;
+    if (!bc) return;
+    for (BatchEntry& e : bc->entries) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.dmem) cudaFree(e.dmem);
+    }
+    if (bc->capture) cudaStreamDestroy(bc->capture);
+    delete bc;
+    ctx->batch = nullptr;
+}
+
+namespace {
+
+hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, bool gauss,
+                             BatchEntry& out) {
+    const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
+    const size_t params_off = maps_bytes;
+    const size_t tiles_off = params_off + (size_t)n * sizeof(EdgeParams);
+    const size_t total = tiles_off + (size_t)(n + 1) * sizeof(int);
+    std::vector<uint8_t> host(total);
+    std::vector<int> tile_start(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const Group& G = gs[i]->plan.groups[0];
+        std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap, sizeof(CUtensorMap));
+        std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &G.edge,
+                    sizeof(EdgeParams));
+        int tiles = (int)(((G.W + EDGE_TW - 1) / EDGE_TW) * ((G.H + EDGE_TH - 1) / EDGE_TH));
+        tile_start[i + 1] = tile_start[i] + tiles;
+    }
+    std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));
+    void* dmem = nullptr;
+    cudaError_t e = cudaMalloc(&dmem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HVX_ERROR_NO_MEMORY;
+    }
+    e = cudaMemcpy(dmem, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dmem);
+        return cuda_status(e);
+    }
+    EdgeBatchDesc d;
+    d.maps = static_cast<const CUtensorMap*>(dmem);
+    d.params = reinterpret_cast<const EdgeParams*>(static_cast<uint8_t*>(dmem) + params_off);
+    d.tile_start = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tiles_off);
+    d.n_img = n;
+    d.total_tiles = tile_start[n];
+    d.gauss_only = gauss ? 1 : 0;
+    d.err = ctx->d_error;
+    int per_sm = std::max(1, edge_batch_blocks_per_sm());
+    int grid = std::min(d.total_tiles, ctx->num_sms * per_sm);
+    if (!bc->capture) {
+        e = cudaStreamCreateWithFlags(&bc->capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaFree(dmem);
+            return cuda_status(e);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(bc->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch_edge_batch(d, grid, bc->capture);
+        e = cudaStreamEndCapture(bc->capture, &graph);
+        if (le != cudaSuccess) e = le;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dmem);
+        return cuda_status(e);
+    }
+    out.graphs.assign(gs, gs + n);
+    out.plan_ids.resize(n);
+    for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
+    out.dmem = dmem;
+    out.exec = exec;
+    return HVX_SUCCESS;
+}
+
+}  // namespace
+
+hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
+    // one persistent launch when every plan is a single edge group, or every
+    // plan a single Gaussian group
+    bool all_edge = true, all_gauss = true;
+    for (int i = 0; i < n; ++i) {
+        const Plan& P = gs[i]->plan;
+        bool one = P.groups.size() == 1;
+        all_edge &= one && P.groups[0].kernel == GK_EDGE;
+        all_gauss &= one && P.groups[0].kernel == GK_GAUSS;
+    }
+    if (!all_edge && !all_gauss) {
+        for (int i = 0; i < n; ++i) {
+            hvx_status st = launch_plan(gs[i], s);
+            if (st != HVX_SUCCESS) return st;
+        }
+        return HVX_SUCCESS;
+    }
+    if (!ctx->batch) ctx->batch = new BatchCache();
+    BatchCache* bc = ctx->batch;
+    BatchEntry* hit = nullptr;
+    for (BatchEntry& e : bc->entries) {
+        if ((int)e.graphs.size() != n) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i)
+            same = e.graphs[i] == gs[i] && e.plan_ids[i] == gs[i]->plan_id;
+        if (same) {
+            hit = &e;
+            break;
+        }
+    }
+    if (!hit) {
+        if (bc->entries.size() >= 16) {
+            auto oldest = std::min_element(
+                bc->entries.begin(), bc->entries.end(),
+                [](const BatchEntry& a, const BatchEntry& b) { return a.last_use < b.last_use; });
+            cudaStreamSynchronize(s);
+            if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
+            if (oldest->dmem) cudaFree(oldest->dmem);
+            bc->entries.erase(oldest);
+        }
+        BatchEntry fresh;
+        hvx_status st = build_batch_entry(ctx, bc, gs, n, all_gauss && !all_edge, fresh);
+        if (st != HVX_SUCCESS) return st;
+        bc->entries.push_back(fresh);
+        hit = &bc->entries.back();
+    }
+    hit->last_use = ++bc->tick;
+    return cuda_status(cudaGraphLaunch(hit->exec, s));
+}
+
+}  // namespace hvx

@@ -1,0 +1,324 @@
+// Serving loop: verified graphs are submitted as requests; a dispatcher
+// thread admits them in FIFO order while a slot and the device-memory budget
+// allow, launches each on the next of several streams so that admitted work
+// overlaps on the device, and retires requests as their completion events
+// fire.  Requests that arrive while others are running are admitted as soon
+// as slots and budget free up (continuous batching); latency is measured from
+// submission to completion.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "hvx_internal.h"
+
+namespace hvx {
+
+namespace {
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct Request {
+    uint64_t ticket = 0;
+    Graph* g = nullptr;
+    uint64_t bytes = 0;
+    double mpix = 0;
+    double t_submit = 0;
+    double latency_ms = 0;
+    hvx_status result = HVX_SUCCESS;
+    bool done = false;
+    cudaEvent_t ev = nullptr;
+};
+
+struct Server {
+    uint32_t magic = kMagicServer;
+    Context* ctx = nullptr;
+    uint64_t budget = 0;
+    int max_inflight = 1;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> event_pool;
+    int next_stream = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> inflight;
+    std::unordered_map<uint64_t, Request*> by_ticket;
+    uint64_t next_ticket = 1;
+    uint64_t reserved = 0;
+    bool stop = false;
+    std::thread dispatcher;
+
+    // statistics
+    uint64_t submitted = 0, completed = 0, failed = 0, max_in_flight = 0, peak_reserved = 0;
+    std::vector<double> latencies;
+    double mpix_completed = 0;
+
+    void run();
+};
+
+void Server::run() {
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+        // retire finished requests
+        for (size_t i = 0; i < inflight.size();) {
+            Request* r = inflight[i];
+            cudaError_t q = cudaEventQuery(r->ev);
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            r->latency_ms = now_ms() - r->t_submit;
+            r->result = q == cudaSuccess ? HVX_SUCCESS : cuda_status(q);
+            if (q != cudaSuccess) cudaGetLastError();
+            r->done = true;
+            reserved -= r->bytes;
+            r->g->busy.store(0);
+            event_pool.push_back(r->ev);
+            r->ev = nullptr;
+            if (r->result == HVX_SUCCESS) {
+                ++completed;
+                latencies.push_back(r->latency_ms);
+                mpix_completed += r->mpix;
+            } else {
+                ++failed;
+            }
+            inflight[i] = inflight.back();
+            inflight.pop_back();
+            cv_done.notify_all();
+        }
+        // admit in FIFO order while a slot and the budget allow
+        while (!queue.empty()) {
+            Request* r = queue.front();
+            if ((int)inflight.size() >= max_inflight) break;
+            if (budget && reserved + r->bytes > budget) break;
+            if (r->g->busy.load()) break;
+            queue.pop_front();
+            r->g->busy.store(1);
+            reserved += r->bytes;
+            peak_reserved = std::max(peak_reserved, reserved);
+            cudaStream_t s = streams[next_stream];
+            next_stream = (next_stream + 1) % (int)streams.size();
+            if (event_pool.empty()) {
+                cudaEvent_t e;
+                cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+                event_pool.push_back(e);
+            }
+            r->ev = event_pool.back();
+            event_pool.pop_back();
+            hvx_status st = launch_plan(r->g, s);
+            if (st == HVX_SUCCESS && cudaEventRecord(r->ev, s) != cudaSuccess) st = HVX_ERROR_DEVICE;
+            if (st != HVX_SUCCESS) {
+                cudaGetLastError();
+                r->result = st;
+                r->done = true;
+                r->latency_ms = now_ms() - r->t_submit;
+                reserved -= r->bytes;
+                r->g->busy.store(0);
+                event_pool.push_back(r->ev);
+                r->ev = nullptr;
+                ++failed;
+                cv_done.notify_all();
+                continue;
+            }
+            inflight.push_back(r);
+            max_in_flight = std::max<uint64_t>(max_in_flight, inflight.size());
+        }
+        if (stop && queue.empty() && inflight.empty()) break;
+        if (inflight.empty() && queue.empty()) {
+            cv_work.wait(lk);
+        } else {
+            // poll completions; new submissions wake the loop at once
+            cv_work.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+void server_destroy(Server* s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->dispatcher.joinable()) s->dispatcher.join();
+    for (auto& kv : s->by_ticket) {
+        if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+        delete kv.second;
+    }
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    auto& v = s->ctx->servers;
+    v.erase(std::remove(v.begin(), v.end(), s), v.end());
+    s->magic = 0;
+    delete s;
+}
+
+}  // namespace hvx
+
+using namespace hvx;
+
+namespace {
+bool ok_server(hvx_server s) { return s && reinterpret_cast<Server*>(s)->magic == kMagicServer; }
+Server* S(hvx_server s) { return reinterpret_cast<Server*>(s); }
+}  // namespace
+
+extern "C" {
+
+hvx_status hvxCreateServer(hvx_context ctx, uint64_t budget, int32_t max_inflight,
+                           int32_t n_streams, hvx_server* out) {
+    Context* c = reinterpret_cast<Context*>(ctx);
+    if (!c || c->magic != kMagicContext) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out || max_inflight < 1 || n_streams < 1 || n_streams > 64)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    Server* s = new (std::nothrow) Server();
+    if (!s) return HVX_ERROR_NO_MEMORY;
+    s->ctx = c;
+    s->budget = budget;
+    s->max_inflight = max_inflight;
+    for (int i = 0; i < n_streams; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return HVX_ERROR_DEVICE;
+        }
+        s->streams.push_back(st);
+    }
+    c->servers.push_back(s);
+    s->dispatcher = std::thread([s] { s->run(); });
+    *out = reinterpret_cast<hvx_server>(s);
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxServerSubmit(hvx_server hs, hvx_graph hg, uint64_t* ticket) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    Graph* g = reinterpret_cast<Graph*>(hg);
+    if (!g || g->magic != kMagicGraph) return HVX_ERROR_INVALID_REFERENCE;
+    if (!ticket) return HVX_ERROR_INVALID_PARAMETERS;
+    Server* s = S(hs);
+    if (g->ctx != s->ctx) return HVX_ERROR_INVALID_REFERENCE;
+    if (!g->verified) return HVX_ERROR_NOT_VERIFIED;
+    // device bytes the request holds while in flight: its images and the
+    // plan's materialised intermediates
+    uint64_t bytes = g->plan.intermediate_bytes;
+    double mpix = 0;
+    std::vector<const Image*> seen;
+    for (const Group& G : g->plan.groups) {
+        for (const Image* im : G.inputs)
+            if (!im->is_virtual && std::find(seen.begin(), seen.end(), im) == seen.end()) {
+                seen.push_back(im);
+                bytes += im->bytes;
+                mpix = std::max(mpix, (double)im->w * im->h / 1e6);
+            }
+        for (const Image* im : G.outputs)
+            if (!im->is_virtual && std::find(seen.begin(), seen.end(), im) == seen.end()) {
+                seen.push_back(im);
+                bytes += im->bytes;
+            }
+    }
+    if (s->budget && bytes > s->budget) return HVX_ERROR_OVER_BUDGET;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return HVX_ERROR_NO_MEMORY;
+    r->g = g;
+    r->bytes = bytes;
+    r->mpix = mpix;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete r;
+            return HVX_ERROR_INVALID_REFERENCE;
+        }
+        r->ticket = s->next_ticket++;
+        r->t_submit = now_ms();
+        s->queue.push_back(r);
+        s->by_ticket[r->ticket] = r;
+        ++s->submitted;
+    }
+    s->cv_work.notify_all();
+    *ticket = r->ticket;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxServerWait(hvx_server hs, uint64_t ticket, int32_t timeout_ms, hvx_status* result,
+                         double* latency_ms) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    Server* s = S(hs);
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->by_ticket.find(ticket);
+    if (it == s->by_ticket.end()) return HVX_ERROR_INVALID_PARAMETERS;
+    Request* r = it->second;
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, [&] { return r->done; });
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                    [&] { return r->done; })) {
+        return HVX_ERROR_TIMEOUT;
+    }
+    if (result) *result = r->result;
+    if (latency_ms) *latency_ms = r->latency_ms;
+    s->by_ticket.erase(it);
+    delete r;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxServerStats(hvx_server hs, hvx_server_stats* out) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!out) return HVX_ERROR_INVALID_PARAMETERS;
+    Server* s = S(hs);
+    std::lock_guard<std::mutex> lk(s->mu);
+    hvx_server_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.submitted = s->submitted;
+    st.completed = s->completed;
+    st.failed = s->failed;
+    st.queued = s->queue.size();
+    st.in_flight = s->inflight.size();
+    st.max_in_flight = s->max_in_flight;
+    st.bytes_reserved = s->reserved;
+    st.peak_bytes_reserved = s->peak_reserved;
+    st.mpix_completed = s->mpix_completed;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) {
+            size_t k = (size_t)std::ceil(p * v.size()) - 1;
+            return v[std::min(k, v.size() - 1)];
+        };
+        st.p50_ms = pct(0.50);
+        st.p99_ms = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        st.mean_ms = sum / v.size();
+        st.max_ms = v.back();
+    }
+    *out = st;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxServerResetStats(hvx_server hs) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    Server* s = S(hs);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->latencies.clear();
+    s->mpix_completed = 0;
+    s->max_in_flight = s->inflight.size();
+    s->peak_reserved = s->reserved;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxReleaseServer(hvx_server* hs) {
+    if (!hs || !ok_server(*hs)) return HVX_ERROR_INVALID_REFERENCE;
+    server_destroy(S(*hs));
+    *hs = nullptr;
+    return HVX_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,427 @@
+"""Python binding of the C ABI in include/hvx.h (ctypes, same names).
+
+Argument marshalling only: every call goes straight to libhvx.so, and every
+step of the image-graph path runs in the library's CUDA kernels.  A call that
+returns an error status raises ``HvxError``; out-parameters are returned.
+Handles are opaque ``ctypes.c_void_p`` values.
+
+The library is built in-tree on first use (``_build.build()``); if it cannot be
+built or loaded, importing any entry point raises — there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import _build
+
+# status codes
+HVX_SUCCESS = 0
+HVX_ERROR_INVALID_REFERENCE = -1
+HVX_ERROR_INVALID_PARAMETERS = -2
+HVX_ERROR_INVALID_FORMAT = -3
+HVX_ERROR_INVALID_GRAPH = -4
+HVX_ERROR_NOT_VERIFIED = -5
+HVX_ERROR_NO_MEMORY = -6
+HVX_ERROR_OVER_BUDGET = -7
+HVX_ERROR_TIMEOUT = -8
+HVX_ERROR_DEVICE = -9
+HVX_ERROR_NOT_SUPPORTED = -10
+
+HVX_DF_VIRT, HVX_DF_U8, HVX_DF_S16, HVX_DF_S32, HVX_DF_F32, HVX_DF_UYVY = 0, 1, 2, 3, 4, 5
+HVX_BORDER_UNDEFINED, HVX_BORDER_REPLICATE, HVX_BORDER_CONSTANT = 0, 1, 2
+HVX_ROUND_TO_ZERO, HVX_ROUND_TO_NEAREST = 0, 1
+HVX_THRESHOLD_BINARY, HVX_THRESHOLD_RANGE = 0, 1
+HVX_POLICY_WRAP, HVX_POLICY_SATURATE = 0, 1
+HVX_CHANNEL_Y, HVX_CHANNEL_U, HVX_CHANNEL_V = 0, 1, 2
+HVX_READ, HVX_WRITE = 1, 2
+HVX_POINT_MUL, HVX_POINT_HARRIS_RESPONSE = 1, 2
+HVX_LOCAL_SUM = 1
+HVX_GRAPH_NUM_NODES = 1
+HVX_GRAPH_NUM_OPS = 2
+HVX_GRAPH_NUM_ALIVE_OPS = 3
+HVX_GRAPH_NUM_LAUNCHES = 4
+HVX_GRAPH_INTERMEDIATE_BYTES = 5
+HVX_GRAPH_EXTERNAL_BYTES = 6
+HVX_GRAPH_FUSION = 7
+HVX_GRAPH_KERNEL_KINDS = 8
+HVX_NODE_LIVE_OUTPUTS = 1
+HVX_NODE_GROUP = 2
+
+BYTES_PER_PIXEL = {HVX_DF_U8: 1, HVX_DF_S16: 2, HVX_DF_S32: 4, HVX_DF_F32: 4, HVX_DF_UYVY: 2}
+
+
+class HvxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {hvxStatusString(status)} ({status})")
+
+
+class hvx_rect(ctypes.Structure):
+    _fields_ = [("start_x", ctypes.c_int32), ("start_y", ctypes.c_int32),
+                ("end_x", ctypes.c_int32), ("end_y", ctypes.c_int32)]
+
+
+class hvx_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "queued",
+                                               "in_flight", "max_in_flight", "bytes_reserved",
+                                               "peak_bytes_reserved")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                              "mpix_completed")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+U32 = ctypes.c_uint32
+U64 = ctypes.c_uint64
+PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "hvxStatusString": (ctypes.c_char_p, [I32]),
+    "hvxCreateContext": (I32, [PP]),
+    "hvxCreateContextEx": (I32, [I32, PP]),
+    "hvxReleaseContext": (I32, [PP]),
+    "hvxSetContextMemoryBudget": (I32, [P, U64]),
+    "hvxGetContextMemoryUsage": (I32, [P, ctypes.POINTER(U64)]),
+    "hvxCreateImage": (I32, [P, U32, U32, I32, PP]),
+    "hvxCreateImageFromHandle": (I32, [P, U32, U32, I32, P, U64, PP]),
+    "hvxSwapImageHandle": (I32, [P, P, U64]),
+    "hvxCreateVirtualImage": (I32, [P, U32, U32, I32, PP]),
+    "hvxReleaseImage": (I32, [PP]),
+    "hvxCopyImage": (I32, [P, P, U64, I32]),
+    "hvxGetImageDevicePtr": (I32, [P, PP, ctypes.POINTER(U64)]),
+    "hvxQueryImage": (I32, [P, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(I32)]),
+    "hvxGetValidRegion": (I32, [P, ctypes.POINTER(hvx_rect)]),
+    "hvxCreateGraph": (I32, [P, PP]),
+    "hvxReleaseGraph": (I32, [PP]),
+    "hvxVerifyGraph": (I32, [P]),
+    "hvxProcessGraph": (I32, [P]),
+    "hvxScheduleGraph": (I32, [P, P]),
+    "hvxWaitGraph": (I32, [P]),
+    "hvxSetGraphFusion": (I32, [P, I32]),
+    "hvxGetGraphStatus": (I32, [P]),
+    "hvxQueryGraph": (I32, [P, I32, P, U64]),
+    "hvxProcessGraphBatch": (I32, [PP, I32, P]),
+    "hvxWaitBatch": (I32, [P, P]),
+    "hvxGaussian3x3Node": (P, [P, P, P]),
+    "hvxBox3x3Node": (P, [P, P, P]),
+    "hvxSobel3x3Node": (P, [P, P, P, P]),
+    "hvxMagnitudeNode": (P, [P, P, P, P]),
+    "hvxPhaseNode": (P, [P, P, P, P]),
+    "hvxThresholdNode": (P, [P, P, I32, ctypes.c_double, ctypes.c_double, I32, I32, P]),
+    "hvxChannelExtractNode": (P, [P, P, I32, P]),
+    "hvxAddNode": (P, [P, P, P, I32, P]),
+    "hvxSubtractNode": (P, [P, P, P, I32, P]),
+    "hvxAbsDiffNode": (P, [P, P, P, P]),
+    "hvxConvolveNode": (P, [P, P, ctypes.POINTER(I32), I32, I32, I32, P]),
+    "hvxPointNode": (P, [P, I32, PP, I32, P, ctypes.POINTER(ctypes.c_double), I32]),
+    "hvxLocalNode": (P, [P, I32, I32, I32, P, P]),
+    "hvxSetNodeBorder": (I32, [P, I32, I32]),
+    "hvxSetNodeRounding": (I32, [P, I32]),
+    "hvxQueryNode": (I32, [P, I32, P, U64]),
+    "hvxCreateServer": (I32, [P, U64, I32, I32, PP]),
+    "hvxServerSubmit": (I32, [P, P, ctypes.POINTER(U64)]),
+    "hvxServerWait": (I32, [P, U64, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
+    "hvxServerStats": (I32, [P, ctypes.POINTER(hvx_server_stats)]),
+    "hvxServerResetStats": (I32, [P]),
+    "hvxReleaseServer": (I32, [PP]),
+}
+
+
+def lib():
+    """Load libhvx.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _ck(st: int, where: str):
+    if st != HVX_SUCCESS:
+        raise HvxError(st, where)
+
+
+def _node(h, g, where):
+    if not h:
+        raise HvxError(lib().hvxGetGraphStatus(g), where)
+    return h
+
+
+# --- status / context -----------------------------------------------------------
+
+def hvxStatusString(status: int) -> str:
+    return lib().hvxStatusString(status).decode()
+
+
+def hvxCreateContext():
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateContext(ctypes.byref(out)), "hvxCreateContext")
+    return out
+
+
+HVX_CONTEXT_PLAN_ONLY = 1
+
+
+def hvxCreateContextEx(flags: int):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateContextEx(flags, ctypes.byref(out)), "hvxCreateContextEx")
+    return out
+
+
+def hvxReleaseContext(ctx):
+    h = ctypes.c_void_p(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx)
+    _ck(lib().hvxReleaseContext(ctypes.byref(h)), "hvxReleaseContext")
+
+
+def hvxSetContextMemoryBudget(ctx, nbytes: int):
+    _ck(lib().hvxSetContextMemoryBudget(ctx, nbytes), "hvxSetContextMemoryBudget")
+
+
+def hvxGetContextMemoryUsage(ctx) -> int:
+    v = U64()
+    _ck(lib().hvxGetContextMemoryUsage(ctx, ctypes.byref(v)), "hvxGetContextMemoryUsage")
+    return v.value
+
+
+# --- images ------------------------------------------------------------------------
+
+def hvxCreateImage(ctx, w, h, fmt):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateImage(ctx, w, h, fmt, ctypes.byref(out)), "hvxCreateImage")
+    return out
+
+
+def hvxCreateImageFromHandle(ctx, w, h, fmt, dev_ptr: int, pitch: int):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateImageFromHandle(ctx, w, h, fmt, dev_ptr, pitch, ctypes.byref(out)),
+        "hvxCreateImageFromHandle")
+    return out
+
+
+def hvxSwapImageHandle(img, dev_ptr: int, pitch: int):
+    _ck(lib().hvxSwapImageHandle(img, dev_ptr, pitch), "hvxSwapImageHandle")
+
+
+def hvxCreateVirtualImage(graph, w=0, h=0, fmt=HVX_DF_VIRT):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateVirtualImage(graph, w, h, fmt, ctypes.byref(out)), "hvxCreateVirtualImage")
+    return out
+
+
+def hvxReleaseImage(img):
+    h = ctypes.c_void_p(img.value if isinstance(img, ctypes.c_void_p) else img)
+    _ck(lib().hvxReleaseImage(ctypes.byref(h)), "hvxReleaseImage")
+
+
+def hvxCopyImage(img, host_ptr: int, host_pitch: int, usage: int):
+    _ck(lib().hvxCopyImage(img, host_ptr, host_pitch, usage), "hvxCopyImage")
+
+
+def hvxGetImageDevicePtr(img):
+    p = ctypes.c_void_p()
+    pitch = U64()
+    _ck(lib().hvxGetImageDevicePtr(img, ctypes.byref(p), ctypes.byref(pitch)),
+        "hvxGetImageDevicePtr")
+    return p.value, pitch.value
+
+
+def hvxQueryImage(img):
+    w, h, f = U32(), U32(), I32()
+    _ck(lib().hvxQueryImage(img, ctypes.byref(w), ctypes.byref(h), ctypes.byref(f)),
+        "hvxQueryImage")
+    return w.value, h.value, f.value
+
+
+def hvxGetValidRegion(img):
+    r = hvx_rect()
+    _ck(lib().hvxGetValidRegion(img, ctypes.byref(r)), "hvxGetValidRegion")
+    return (r.start_x, r.start_y, r.end_x, r.end_y)
+
+
+# --- graphs ------------------------------------------------------------------------
+
+def hvxCreateGraph(ctx):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateGraph(ctx, ctypes.byref(out)), "hvxCreateGraph")
+    return out
+
+
+def hvxReleaseGraph(g):
+    h = ctypes.c_void_p(g.value if isinstance(g, ctypes.c_void_p) else g)
+    _ck(lib().hvxReleaseGraph(ctypes.byref(h)), "hvxReleaseGraph")
+
+
+def hvxVerifyGraph(g):
+    _ck(lib().hvxVerifyGraph(g), "hvxVerifyGraph")
+
+
+def hvxProcessGraph(g):
+    _ck(lib().hvxProcessGraph(g), "hvxProcessGraph")
+
+
+def hvxScheduleGraph(g, stream: int = 0):
+    _ck(lib().hvxScheduleGraph(g, stream), "hvxScheduleGraph")
+
+
+def hvxWaitGraph(g):
+    _ck(lib().hvxWaitGraph(g), "hvxWaitGraph")
+
+
+def hvxSetGraphFusion(g, enable: bool):
+    _ck(lib().hvxSetGraphFusion(g, 1 if enable else 0), "hvxSetGraphFusion")
+
+
+def hvxGetGraphStatus(g) -> int:
+    return lib().hvxGetGraphStatus(g)
+
+
+def hvxQueryGraph(g, attribute: int):
+    if attribute == HVX_GRAPH_KERNEL_KINDS:
+        buf = ctypes.create_string_buffer(1024)
+        _ck(lib().hvxQueryGraph(g, attribute, buf, 1024), "hvxQueryGraph")
+        return buf.value.decode()
+    if attribute in (HVX_GRAPH_INTERMEDIATE_BYTES, HVX_GRAPH_EXTERNAL_BYTES):
+        v = U64()
+        _ck(lib().hvxQueryGraph(g, attribute, ctypes.byref(v), 8), "hvxQueryGraph")
+        return v.value
+    v = I32()
+    _ck(lib().hvxQueryGraph(g, attribute, ctypes.byref(v), 4), "hvxQueryGraph")
+    return v.value
+
+
+def hvxProcessGraphBatch(graphs, stream: int = 0):
+    arr = (ctypes.c_void_p * len(graphs))(*[g.value if isinstance(g, ctypes.c_void_p) else g
+                                            for g in graphs])
+    _ck(lib().hvxProcessGraphBatch(arr, len(graphs), stream), "hvxProcessGraphBatch")
+
+
+def hvxWaitBatch(ctx, stream: int = 0):
+    _ck(lib().hvxWaitBatch(ctx, stream), "hvxWaitBatch")
+
+
+# --- nodes -------------------------------------------------------------------------
+
+def hvxGaussian3x3Node(g, i, o):
+    return _node(lib().hvxGaussian3x3Node(g, i, o), g, "hvxGaussian3x3Node")
+
+
+def hvxBox3x3Node(g, i, o):
+    return _node(lib().hvxBox3x3Node(g, i, o), g, "hvxBox3x3Node")
+
+
+def hvxSobel3x3Node(g, i, gx, gy):
+    return _node(lib().hvxSobel3x3Node(g, i, gx, gy), g, "hvxSobel3x3Node")
+
+
+def hvxMagnitudeNode(g, gx, gy, o):
+    return _node(lib().hvxMagnitudeNode(g, gx, gy, o), g, "hvxMagnitudeNode")
+
+
+def hvxPhaseNode(g, gx, gy, o):
+    return _node(lib().hvxPhaseNode(g, gx, gy, o), g, "hvxPhaseNode")
+
+
+def hvxThresholdNode(g, i, type_, value, upper, true_value, false_value, o):
+    return _node(lib().hvxThresholdNode(g, i, type_, float(value), float(upper), true_value,
+                                        false_value, o), g, "hvxThresholdNode")
+
+
+def hvxChannelExtractNode(g, i, channel, o):
+    return _node(lib().hvxChannelExtractNode(g, i, channel, o), g, "hvxChannelExtractNode")
+
+
+def hvxAddNode(g, a, b, policy, o):
+    return _node(lib().hvxAddNode(g, a, b, policy, o), g, "hvxAddNode")
+
+
+def hvxSubtractNode(g, a, b, policy, o):
+    return _node(lib().hvxSubtractNode(g, a, b, policy, o), g, "hvxSubtractNode")
+
+
+def hvxAbsDiffNode(g, a, b, o):
+    return _node(lib().hvxAbsDiffNode(g, a, b, o), g, "hvxAbsDiffNode")
+
+
+def hvxConvolveNode(g, i, coeffs, kw, kh, shift, o):
+    arr = (I32 * (kw * kh))(*[int(c) for c in coeffs])
+    return _node(lib().hvxConvolveNode(g, i, arr, kw, kh, shift, o), g, "hvxConvolveNode")
+
+
+def hvxPointNode(g, op, ins, out, params=()):
+    arr = (ctypes.c_void_p * len(ins))(*[x.value if isinstance(x, ctypes.c_void_p) else x
+                                         for x in ins])
+    prm = (ctypes.c_double * max(1, len(params)))(*params)
+    return _node(lib().hvxPointNode(g, op, arr, len(ins), out, prm, len(params)), g,
+                 "hvxPointNode")
+
+
+def hvxLocalNode(g, op, kw, kh, i, o):
+    return _node(lib().hvxLocalNode(g, op, kw, kh, i, o), g, "hvxLocalNode")
+
+
+def hvxSetNodeBorder(node, mode, constant=0):
+    _ck(lib().hvxSetNodeBorder(node, mode, constant), "hvxSetNodeBorder")
+
+
+def hvxSetNodeRounding(node, rounding):
+    _ck(lib().hvxSetNodeRounding(node, rounding), "hvxSetNodeRounding")
+
+
+def hvxQueryNode(node, attribute):
+    v = I32()
+    _ck(lib().hvxQueryNode(node, attribute, ctypes.byref(v), 4), "hvxQueryNode")
+    return v.value if attribute != HVX_NODE_LIVE_OUTPUTS else v.value & 0xFFFFFFFF
+
+
+# --- serving -----------------------------------------------------------------------
+
+def hvxCreateServer(ctx, mem_budget: int, max_in_flight: int, n_streams: int):
+    out = ctypes.c_void_p()
+    _ck(lib().hvxCreateServer(ctx, mem_budget, max_in_flight, n_streams, ctypes.byref(out)),
+        "hvxCreateServer")
+    return out
+
+
+def hvxServerSubmit(srv, g) -> int:
+    t = U64()
+    _ck(lib().hvxServerSubmit(srv, g, ctypes.byref(t)), "hvxServerSubmit")
+    return t.value
+
+
+def hvxServerWait(srv, ticket: int, timeout_ms: int = -1):
+    """Returns (request status, latency ms)."""
+    st = I32()
+    lat = ctypes.c_double()
+    _ck(lib().hvxServerWait(srv, ticket, timeout_ms, ctypes.byref(st), ctypes.byref(lat)),
+        "hvxServerWait")
+    return st.value, lat.value
+
+
+def hvxServerStats(srv) -> dict:
+    s = hvx_server_stats()
+    _ck(lib().hvxServerStats(srv, ctypes.byref(s)), "hvxServerStats")
+    return {n: getattr(s, n) for n, _ in hvx_server_stats._fields_}
+
+
+def hvxServerResetStats(srv):
+    _ck(lib().hvxServerResetStats(srv), "hvxServerResetStats")
+
+
+def hvxReleaseServer(srv):
+    h = ctypes.c_void_p(srv.value if isinstance(srv, ctypes.c_void_p) else srv)
+    _ck(lib().hvxReleaseServer(ctypes.byref(h)), "hvxReleaseServer")

@@ -1,0 +1,295 @@
+"""CPU tests of the C ABI: the library builds and exports every declared entry
+point, and the host-side graph logic (verification, Algorithm 1, valid
+regions, fusion planning) behaves as the oracle's graph layer says, using a
+plan-only context (no device)."""
+import os
+import re
+
+import pytest
+
+import oracle.graph as OG
+from paper_2008_11476_gb300 import graphs as PG
+from paper_2008_11476_gb300 import hvx as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hvx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hvx[A-Z]\w*)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    L = H.lib()
+    names = declared_functions()
+    assert len(names) >= 40
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in H._SIGS, f"binding lacks {n}"
+
+
+@pytest.fixture
+def pctx():
+    c = H.hvxCreateContextEx(H.HVX_CONTEXT_PLAN_ONLY)
+    yield c
+    H.hvxReleaseContext(c)
+
+
+def test_edge_graph_plans_one_fused_kernel(pctx):
+    inp = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
+    ph = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
+    mk = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
+    g = PG.edge_graph(pctx, inp, ph, mk)
+    assert PG.kernel_kinds(g) == ["fused_edge_tma"]
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES) == 1
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 0
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_EXTERNAL_BYTES) == 3 * 1920 * 1080
+    with pytest.raises(H.HvxError) as e:
+        H.hvxProcessGraph(g)
+    assert e.value.status == H.HVX_ERROR_NOT_SUPPORTED
+    # the same graph unfused: one launch per node, every virtual image in memory
+    g2 = PG.edge_graph(pctx, inp, ph, mk, fusion=False)
+    kinds = PG.kernel_kinds(g2)
+    assert kinds == ["gaussian3x3_tma", "staged_tile", "plain_point", "plain_point",
+                     "plain_point"]
+    # G (1 B) + gx, gy (2 B each) + magnitude (2 B), pitches padded to 128 B
+    assert H.hvxQueryGraph(g2, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 1080 * (1920 + 3 * 3840)
+
+
+def test_harris_graph_plans_one_fused_kernel(pctx):
+    inp = H.hvxCreateImage(pctx, 4096, 2160, H.HVX_DF_U8)
+    mk = H.hvxCreateImage(pctx, 4096, 2160, H.HVX_DF_U8)
+    g = PG.harris_graph(pctx, inp, mk)
+    assert PG.kernel_kinds(g) == ["fused_harris_tma"]
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_ALIVE_OPS) == 10
+    assert H.hvxGetValidRegion(mk) == (3, 3, 4093, 2157)
+    g2 = PG.harris_graph(pctx, inp, mk, fusion=False)
+    assert len(PG.kernel_kinds(g2)) == 9
+
+
+def _build_both(pctx, spec_nodes, images):
+    """The same graph through the C ABI and through the oracle's graph layer."""
+    g = H.hvxCreateGraph(pctx)
+    og = OG.GraphDesc()
+    handles = {}
+    for name, (virtual, w, h, fmt) in images.items():
+        if virtual:
+            handles[name] = H.hvxCreateVirtualImage(g)
+            og.virtual(name)
+        else:
+            handles[name] = H.hvxCreateImage(pctx, w, h, getattr(H, "HVX_DF_" + fmt))
+            og.image(name, w, h, fmt)
+    nodes = []
+    for kind, ins, outs in spec_nodes:
+        hi = [handles[i] for i in ins]
+        ho = [handles[o] if o else None for o in outs]
+        if kind == "gaussian3x3":
+            n = H.hvxGaussian3x3Node(g, hi[0], ho[0])
+        elif kind == "box3x3":
+            n = H.hvxBox3x3Node(g, hi[0], ho[0])
+        elif kind == "sobel3x3":
+            n = H.hvxSobel3x3Node(g, hi[0], ho[0], ho[1])
+        elif kind == "magnitude":
+            n = H.hvxMagnitudeNode(g, hi[0], hi[1], ho[0])
+        elif kind == "phase":
+            n = H.hvxPhaseNode(g, hi[0], hi[1], ho[0])
+        elif kind == "threshold":
+            n = H.hvxThresholdNode(g, hi[0], H.HVX_THRESHOLD_BINARY, 100, 0, 255, 0, ho[0])
+        elif kind == "channel_extract":
+            n = H.hvxChannelExtractNode(g, hi[0], 0, ho[0])
+        else:
+            raise ValueError(kind)
+        nodes.append(n)
+        og.node(kind, ins, outs, **({"value": 100} if kind == "threshold" else {}))
+    return g, og, nodes, handles
+
+
+def test_listing1_dead_sobel_output(pctx):
+    import json
+    spec = json.load(open(os.path.join(ROOT, "tests", "golden", "listing1_edge_graph.json")))
+    images = {im["name"]: (im["virtual"], im.get("w", 0), im.get("h", 0), im.get("fmt", ""))
+              for im in spec["images"]}
+    nodes = [(n["kind"], n["ins"], n["outs"]) for n in spec["nodes"]]
+    g, og, hn, _ = _build_both(pctx, nodes, images)
+    H.hvxVerifyGraph(g)
+    # Sobel's gx output (bit 0) is dead, gy (bit 1) alive
+    assert H.hvxQueryNode(hn[2], H.HVX_NODE_LIVE_OUTPUTS) == 0b10
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_OPS) == 6
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_ALIVE_OPS) == 5
+    alive, _ = OG.eliminate_dead(og, OG.verify(og))
+    assert len(alive) == 5
+    # all five live ops fuse into one staged-tile kernel
+    assert PG.kernel_kinds(g) == ["staged_tile"]
+
+
+def _alive_names_c(hn, spec_nodes):
+    names = set()
+    for i, (kind, ins, outs) in enumerate(spec_nodes):
+        m = H.hvxQueryNode(hn[i], H.HVX_NODE_LIVE_OUTPUTS)
+        if kind == "sobel3x3":
+            if m & 1:
+                names.add(f"n{i}.gx")
+            if m & 2:
+                names.add(f"n{i}.gy")
+        elif m & 1:
+            names.add(f"n{i}")
+    return names
+
+
+def test_dead_code_elimination_matches_oracle_on_random_graphs(pctx):
+    from paper_2008_11476_gb300 import synth
+    for seed in range(40):
+        u = synth.uniform01(seed, 40, 400)
+        k = 0
+        images = {"in0": (False, 16, 8, "U8")}
+        pool_u8 = ["in0"]
+        pool_s16 = []
+        nodes = []
+        for i in range(2 + int(u[k] * 7)):
+            k += 1
+            choice = int(u[k] * 5)
+            k += 1
+            virt = u[k] < 0.65
+            k += 1
+            if choice <= 1 or not pool_s16:
+                src = pool_u8[int(u[k] * len(pool_u8))]
+                k += 1
+                if choice == 0 or pool_s16 == [] and u[k] < 0.5:
+                    name = f"u{i}"
+                    images[name] = (virt, 16, 8, "U8")
+                    nodes.append(("gaussian3x3", [src], [name]))
+                    pool_u8.append(name)
+                else:
+                    gx, gy = f"gx{i}", f"gy{i}"
+                    images[gx] = (virt, 16, 8, "S16")
+                    images[gy] = (u[k] < 0.7, 16, 8, "S16")
+                    nodes.append(("sobel3x3", [src], [gx, gy]))
+                    pool_s16 += [gx, gy]
+                k += 1
+            else:
+                a = pool_s16[int(u[k] * len(pool_s16))]
+                k += 1
+                b = pool_s16[int(u[k] * len(pool_s16))]
+                k += 1
+                name = f"m{i}"
+                if choice == 2:
+                    images[name] = (virt, 16, 8, "S16")
+                    nodes.append(("magnitude", [a, b], [name]))
+                    pool_s16.append(name)
+                else:
+                    images[name] = (virt, 16, 8, "U8")
+                    nodes.append(("phase", [a, b], [name]))
+                    pool_u8.append(name)
+        g, og, hn, _ = _build_both(pctx, nodes, images)
+        H.hvxVerifyGraph(g)
+        alive, _ = OG.eliminate_dead(og, OG.verify(og))
+        assert _alive_names_c(hn, nodes) == {op.name for op in alive}, seed
+        H.hvxReleaseGraph(g)
+
+
+def test_verify_rejects_bad_graphs(pctx):
+    a = H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_U8)
+    b = H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_U8)
+    s16 = H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_S16)
+    # cycle through two virtual images
+    g = H.hvxCreateGraph(pctx)
+    v1 = H.hvxCreateVirtualImage(g)
+    v2 = H.hvxCreateVirtualImage(g)
+    H.hvxGaussian3x3Node(g, v1, v2)
+    H.hvxGaussian3x3Node(g, v2, v1)
+    H.hvxBox3x3Node(g, v2, b)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_GRAPH
+    # S16 into a U8-only input
+    g = H.hvxCreateGraph(pctx)
+    H.hvxGaussian3x3Node(g, s16, b)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_FORMAT
+    # virtual image read but never written
+    g = H.hvxCreateGraph(pctx)
+    v = H.hvxCreateVirtualImage(g)
+    H.hvxGaussian3x3Node(g, v, b)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_GRAPH
+    # two writers of one image
+    g = H.hvxCreateGraph(pctx)
+    H.hvxGaussian3x3Node(g, a, b)
+    H.hvxBox3x3Node(g, a, b)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_GRAPH
+    # size mismatch between inputs of a point node
+    small = H.hvxCreateImage(pctx, 4, 4, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxMagnitudeNode(g, s16, small, H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_S16))
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_PARAMETERS
+    # a virtual image of another graph
+    g1 = H.hvxCreateGraph(pctx)
+    foreign = H.hvxCreateVirtualImage(g1)
+    g2 = H.hvxCreateGraph(pctx)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxGaussian3x3Node(g2, a, foreign)
+    assert e.value.status == H.HVX_ERROR_INVALID_REFERENCE
+    # invalid node parameters are refused at creation
+    with pytest.raises(H.HvxError):
+        H.hvxLocalNode(g2, H.HVX_LOCAL_SUM, 4, 5, a, b)
+    with pytest.raises(H.HvxError):
+        H.hvxPointNode(g2, H.HVX_POINT_HARRIS_RESPONSE, [a, a, a], b, (1, 0))
+
+
+def test_edit_after_verify_requires_reverify(pctx):
+    a = H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_U8)
+    b = H.hvxCreateImage(pctx, 8, 8, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    n = H.hvxGaussian3x3Node(g, a, b)
+    H.hvxVerifyGraph(g)
+    H.hvxSetNodeBorder(n, H.HVX_BORDER_UNDEFINED, 0)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES)
+    assert e.value.status == H.HVX_ERROR_NOT_VERIFIED
+    H.hvxVerifyGraph(g)
+    assert H.hvxGetValidRegion(b) == (1, 1, 7, 7)
+
+
+def test_virtual_size_inference_and_declared_mismatch(pctx):
+    a = H.hvxCreateImage(pctx, 20, 10, H.HVX_DF_U8)
+    b = H.hvxCreateImage(pctx, 20, 10, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    v = H.hvxCreateVirtualImage(g)
+    H.hvxGaussian3x3Node(g, a, v)
+    H.hvxBox3x3Node(g, v, b)
+    H.hvxVerifyGraph(g)
+    assert H.hvxQueryImage(v) == (20, 10, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    v = H.hvxCreateVirtualImage(g, 0, 0, H.HVX_DF_S16)
+    H.hvxGaussian3x3Node(g, a, v)
+    H.hvxBox3x3Node(g, v, b)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxVerifyGraph(g)
+    assert e.value.status == H.HVX_ERROR_INVALID_FORMAT
+
+
+def test_fusion_grouping_of_mixed_chain(pctx):
+    """Channel extract (U plane: half width) closes its group; local -> local ->
+    point chains share one staged-tile kernel."""
+    yuv = H.hvxCreateImage(pctx, 64, 16, H.HVX_DF_UYVY)
+    out_u = H.hvxCreateImage(pctx, 32, 16, H.HVX_DF_U8)
+    out_y = H.hvxCreateImage(pctx, 64, 16, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    u = H.hvxCreateVirtualImage(g)
+    H.hvxChannelExtractNode(g, yuv, H.HVX_CHANNEL_U, u)
+    H.hvxBox3x3Node(g, u, out_u)
+    y = H.hvxCreateVirtualImage(g)
+    y2 = H.hvxCreateVirtualImage(g)
+    H.hvxChannelExtractNode(g, yuv, H.HVX_CHANNEL_Y, y)
+    H.hvxGaussian3x3Node(g, y, y2)
+    H.hvxBox3x3Node(g, y2, out_y)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["plain_channel_uv", "staged_tile", "staged_tile"]
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 16 * 128

@@ -1,0 +1,166 @@
+"""GPU tests of the batched persistent launch and of the serving loop: every
+result equals the oracle's and the result of the same graph run alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2008_11476_gb300 import graphs as PG
+from paper_2008_11476_gb300 import hvx as H
+from paper_2008_11476_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hvxCreateContext()
+    yield c
+    H.hvxReleaseContext(c)
+
+
+def _edge_set(ctx, sizes, seed):
+    items = []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed + i)
+        inp = PG.upload(ctx, img, H.HVX_DF_U8)
+        ph = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        g = PG.edge_graph(ctx, inp, ph, mk)
+        items.append((img, g, ph, mk))
+    return items
+
+
+def test_batch_uneven_sizes_matches_oracle(ctx):
+    sizes = synth.batch_sizes(24, seed=4, wlo=1, whi=700, hlo=1, hhi=400)
+    sizes += [(1, 1), (1920, 1080), (321, 2)]
+    items = _edge_set(ctx, sizes, 40)
+    graphs = [it[1] for it in items]
+    for _ in range(2):  # the second call replays the captured CUDA graph
+        H.hvxProcessGraphBatch(graphs)
+        H.hvxWaitBatch(ctx)
+        for img, g, ph, mk in items:
+            rp, rm = O.edge_graph(img)
+            np.testing.assert_array_equal(PG.download(mk), rm)
+            np.testing.assert_array_equal(PG.download(ph), rp)
+
+
+def test_batch_gaussian_only(ctx):
+    sizes = [(33, 7), (640, 480), (129, 300)]
+    outs = []
+    graphs = []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.uniform_u8(w, h, 60 + i)
+        o = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        graphs.append(PG.gaussian_graph(ctx, PG.upload(ctx, img, H.HVX_DF_U8), o))
+        outs.append((img, o))
+    H.hvxProcessGraphBatch(graphs)
+    H.hvxWaitBatch(ctx)
+    for img, o in outs:
+        np.testing.assert_array_equal(PG.download(o), O.gaussian3x3(img).data)
+
+
+def test_batch_mixed_kinds_falls_back_to_sequential(ctx):
+    img = synth.rects_noise(100, 60, 70)
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    mk = PG.empty(ctx, 100, 60, H.HVX_DF_U8)
+    g1 = PG.harris_graph(ctx, inp, mk)
+    g2o = PG.empty(ctx, 100, 60, H.HVX_DF_U8)
+    g2 = PG.gaussian_graph(ctx, inp, g2o)
+    H.hvxProcessGraphBatch([g1, g2])
+    H.hvxWaitBatch(ctx)
+    np.testing.assert_array_equal(PG.download(mk), O.harris_graph(img)[0])
+    np.testing.assert_array_equal(PG.download(g2o), O.gaussian3x3(img).data)
+
+
+def test_server_mix_equals_alone(ctx):
+    """Requests admitted together overlap on several streams; each output is
+    the same as when its graph runs alone."""
+    rng_sizes = [(640, 480), (1920, 1080), (333, 97)]
+    jobs = []
+    for i in range(9):
+        w, h = rng_sizes[i % 3]
+        img = synth.rects_noise(w, h, 80 + i)
+        inp = PG.upload(ctx, img, H.HVX_DF_U8)
+        kind = i % 3
+        if kind == 0:
+            o = PG.empty(ctx, w, h, H.HVX_DF_U8)
+            g = PG.gaussian_graph(ctx, inp, o)
+            outs = [o]
+        elif kind == 1:
+            ph, mk = PG.empty(ctx, w, h, H.HVX_DF_U8), PG.empty(ctx, w, h, H.HVX_DF_U8)
+            g = PG.edge_graph(ctx, inp, ph, mk)
+            outs = [ph, mk]
+        else:
+            mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+            g = PG.harris_graph(ctx, inp, mk)
+            outs = [mk]
+        jobs.append((g, outs))
+    alone = []
+    for g, outs in jobs:
+        H.hvxProcessGraph(g)
+        alone.append([PG.download(o) for o in outs])
+        for o in outs:  # clear, so the served run must write everything again
+            z = np.zeros_like(alone[-1][0])
+            H.hvxCopyImage(o, z.ctypes.data, z.strides[0], H.HVX_WRITE)
+    srv = H.hvxCreateServer(ctx, 1 << 30, 8, 4)
+    tickets = [H.hvxServerSubmit(srv, g) for g, _ in jobs]
+    for t in tickets:
+        st, lat = H.hvxServerWait(srv, t, 10000)
+        assert st == H.HVX_SUCCESS and lat > 0
+    for (g, outs), ref in zip(jobs, alone):
+        for o, r in zip(outs, ref):
+            np.testing.assert_array_equal(PG.download(o), r)
+    stats = H.hvxServerStats(srv)
+    assert stats["completed"] == 9 and stats["failed"] == 0
+    assert stats["max_in_flight"] >= 1 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    H.hvxReleaseServer(srv)
+
+
+def test_server_budget_admission(ctx):
+    """With a budget that holds one request, requests run one at a time and
+    all complete; a request larger than the budget is refused."""
+    w, h = 512, 256
+    jobs = []
+    for i in range(4):
+        img = synth.rects_noise(w, h, 90 + i)
+        inp = PG.upload(ctx, img, H.HVX_DF_U8)
+        ph, mk = PG.empty(ctx, w, h, H.HVX_DF_U8), PG.empty(ctx, w, h, H.HVX_DF_U8)
+        jobs.append((img, PG.edge_graph(ctx, inp, ph, mk), ph, mk))
+    one = 3 * w * h + 1024
+    srv = H.hvxCreateServer(ctx, one, 8, 4)
+    tickets = [H.hvxServerSubmit(srv, j[1]) for j in jobs]
+    for t in tickets:
+        assert H.hvxServerWait(srv, t, 10000)[0] == H.HVX_SUCCESS
+    st = H.hvxServerStats(srv)
+    assert st["max_in_flight"] == 1 and st["peak_bytes_reserved"] <= one
+    for img, g, ph, mk in jobs:
+        rp, rm = O.edge_graph(img)
+        np.testing.assert_array_equal(PG.download(mk), rm)
+    H.hvxReleaseServer(srv)
+    small = H.hvxCreateServer(ctx, 1000, 4, 1)
+    with pytest.raises(H.HvxError) as e:
+        H.hvxServerSubmit(small, jobs[0][1])
+    assert e.value.status == H.HVX_ERROR_OVER_BUDGET
+    H.hvxReleaseServer(small)
+
+
+def test_image_from_torch_tensor_and_swap(ctx):
+    torch = pytest.importorskip("torch")
+    w, h = 1000, 300
+    pitch = 1024
+    a = synth.rects_noise(w, h, 95)
+    b = synth.rects_noise(w, h, 96)
+    ta = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+    tb = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+    ta[:, :w] = torch.from_numpy(a).cuda()
+    tb[:, :w] = torch.from_numpy(b).cuda()
+    to = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    inp = H.hvxCreateImageFromHandle(ctx, w, h, H.HVX_DF_U8, ta.data_ptr(), pitch)
+    out = H.hvxCreateImageFromHandle(ctx, w, h, H.HVX_DF_U8, to.data_ptr(), pitch)
+    g = PG.gaussian_graph(ctx, inp, out)
+    H.hvxProcessGraph(g)
+    np.testing.assert_array_equal(to[:, :w].cpu().numpy(), O.gaussian3x3(a).data)
+    H.hvxSwapImageHandle(inp, tb.data_ptr(), pitch)  # next frame, graph stays verified
+    H.hvxProcessGraph(g)
+    np.testing.assert_array_equal(to[:, :w].cpu().numpy(), O.gaussian3x3(b).data)
