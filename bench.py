@@ -43,7 +43,7 @@ W, H_ = 1920, 1080
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=64)
@@ -60,28 +60,38 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)  # the sampler is running before the timed region opens
         except OSError:
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+        time.sleep(2.5 * self.interval_ms / 1000)  # the sample that covers the end
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
@@ -92,7 +102,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = self.t0 or 0.0
+        t1 = (self.t1 or 1e30) + 2.5 * self.interval_ms / 1000
+        sel = [ln for (t, ln) in self.lines if t0 <= t <= t1]
+        for ln in sel:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -251,8 +264,11 @@ def run_edge(args, world, rank, local, torch):
     for _ in range(args.warmup):
         step_fused()
     barrier(world, torch)
-    with ClockSampler(local) as clk:
-        t_fused = time_steps(torch, step_fused, args.steps, stream)
+    clk = ClockSampler(local).start()
+    clk.mark_start()
+    t_fused = time_steps(torch, step_fused, args.steps, stream)
+    clk.mark_end()
+    clk.stop()
     barrier(world, torch)
     t_fused = reduce_max(t_fused, world, torch)
 

@@ -115,29 +115,22 @@ __device__ __forceinline__ int magnitude_s16(int gx, int gy) {
 // ---------------------------------------------------------------------------
 // Phase: q = floor(atan2(gy, gx) * 128 / pi + 1/2) mod 256, angle in [0, 2 pi).
 //
-// The octant angle atan(t), t = min(|gx|,|gy|) / max(|gx|,|gy|) in [0, 1], is
-// evaluated in bins (128 / pi units) as t * P(t^2); P's coefficients come from
-// gen_phase_poly.py (max error 1.4e-5 bins in binary32).  Octant symmetries
-// give the full angle.  Pixels whose value lies within 1e-4 bins of a rounding
-// boundary (about 1.5e-4 of all integer pairs) are re-decided exactly: the
-// sign of gy cos(b) - gx sin(b) = r sin(theta - b) at the boundary angle b,
-// in double precision (|value| >= 2.9e-5 for every pair of 11-bit gradients,
-// far above double rounding error).
+// With mn = min(|gx|,|gy|), mx = max(|gx|,|gy|), the octant angle in bins
+// (128 / pi units) is a = atan(mn / mx) * 128 / pi in [0, 32], and the full
+// angle is B + s*a for a quadrant base B in {0, 64, 128, 256} and s = +-1.
+// a is never a half-integer for integer gradients (atan of a rational is a
+// rational multiple of pi only at 0 and 1), so round(B + s*a) = B + s*round(a)
+// and only the octant angle has to be rounded.  It is evaluated as t * P(t^2),
+// t = mn / mx, with P from gen_phase_poly.py (max error 1.4e-5 bins in
+// binary32).  When a + 1/2 lies within 1e-4 of an integer (about 1.5e-4 of all
+// integer pairs) the rounding is re-decided exactly: a >= j + 1/2 holds iff
+// mn cos(b_j) - mx sin(b_j) >= 0 with b_j = (j + 1/2) pi / 128, evaluated in
+// double (its magnitude is at least 2.9e-5 for 11-bit gradients, far above
+// double rounding error).
 
-static __device__ __noinline__ int phase_fixup(int gx, int gy, int q0, bool near_low) {
-    int k = near_low ? q0 - 1 : q0;  // boundary angle b = (k + 1/2) * pi / 128
-    double s, c;
-    sincospi(((double)k + 0.5) / 128.0, &s, &c);
-    double cross = (double)gy * c - (double)gx * s;
-    bool above = cross >= 0.0;  // theta >= b
-    if (near_low) return above ? q0 : q0 - 1;
-    return above ? q0 + 1 : q0;
-}
+#include "phase_table.h"
 
-__device__ __forceinline__ uint32_t phase_u8(int gx, int gy) {
-    int ax = abs(gx), ay = abs(gy);
-    int mx = max(ax, ay), mn = min(ax, ay);
-    if (mx == 0) return 0u;
+__device__ __forceinline__ int phase_octant_round(int mn, int mx) {
     float t = __fdividef((float)mn, (float)mx);
     float u = t * t;
     float p = 0.27753710746765137f;
@@ -147,18 +140,27 @@ __device__ __forceinline__ uint32_t phase_u8(int gx, int gy) {
     p = fmaf(p, u, 8.070429801940918f);
     p = fmaf(p, u, -13.574716567993164f);
     p = fmaf(p, u, 40.743507385253906f);
-    float a = p * t;                         // octant angle, bins in [0, 32]
-    float al = (ay > ax) ? 64.0f - a : a;    // first-quadrant angle in [0, 64]
-    float th;
-    if (gy >= 0)
-        th = (gx >= 0) ? al : 128.0f - al;
-    else
-        th = (gx >= 0) ? 256.0f - al : 128.0f + al;
-    float f = th + 0.5f;
-    float qf = floorf(f);
-    float d = f - qf;
-    int q = (int)qf;
-    if (d < 1e-4f || d > 1.0f - 1e-4f) q = phase_fixup(gx, gy, q, d < 0.5f);
+    float f = fmaf(p, t, 0.5f);
+    float fl = floorf(f);
+    float d = f - fl;
+    int ra = (int)fl;
+    if (fabsf(d - 0.5f) > 0.5f - 1e-4f) {
+        int j = d < 0.5f ? ra - 1 : ra;  // the boundary a + 1/2 is close to
+        if (j >= 0 && j < 32) {
+            double cr = (double)mn * kPhaseBoundCos[j] - (double)mx * kPhaseBoundSin[j];
+            ra = cr >= 0.0 ? j + 1 : j;
+        }
+    }
+    return ra;
+}
+
+__device__ __forceinline__ uint32_t phase_u8(int gx, int gy) {
+    int ax = abs(gx), ay = abs(gy);
+    int mx = max(ax, ay), mn = min(ax, ay);
+    if (mx == 0) return 0u;
+    int ra = phase_octant_round(mn, mx);
+    int q1 = ay > ax ? 64 - ra : ra;  // first-quadrant angle, 0 .. 64
+    int q = gy >= 0 ? (gx >= 0 ? q1 : 128 - q1) : (gx >= 0 ? 256 - q1 : 128 + q1);
     return (uint32_t)q & 255u;
 }
 

@@ -42,3 +42,24 @@ if __name__ == "__main__":
     cf = fit()
     print("coefficients (c0..c6):", ", ".join(f"{float(c)!r}f" for c in cf))
     print("max |error| in bins (binary32 Horner):", max_error_f32(cf))
+
+
+def boundary_table():
+    """cos / sin of the 32 rounding boundaries (j + 1/2) * pi / 128, j = 0..31,
+    of the octant angle (used by the exact re-decision near a boundary)."""
+    b = (np.arange(32) + 0.5) * np.pi / 128
+    return np.cos(b), np.sin(b)
+
+
+def write_table_header(path):
+    c, s = boundary_table()
+    fmt = lambda v: ",\n    ".join(", ".join(f"{x:.17g}" for x in v[i:i + 4]) for i in range(0, 32, 4))
+    with open(path, "w") as f:
+        f.write("// Generated by gen_phase_poly.py: cos / sin of the octant-angle rounding\n"
+                "// boundaries (j + 1/2) * pi / 128, j = 0..31.  Do not edit.\n#pragma once\n\n"
+                f"static __constant__ double kPhaseBoundCos[32] = {{\n    {fmt(c)}}};\n\n"
+                f"static __constant__ double kPhaseBoundSin[32] = {{\n    {fmt(s)}}};\n")
+
+
+if __name__ == "__main__" and len(__import__("sys").argv) > 1:
+    write_table_header(__import__("sys").argv[1])

@@ -84,7 +84,7 @@ struct GenericDesc {
 // Fused edge group: Gaussian3x3 -> Sobel3x3 -> {Magnitude -> Threshold, Phase}
 // (and the Gaussian3x3-only group, which writes G).
 constexpr int EDGE_TW = 128;  // output tile width (bytes of U8)
-constexpr int EDGE_TH = 32;   // output tile height
+constexpr int EDGE_TH = 30;   // output tile height (1080 = 36 x 30, 2160 = 72 x 30)
 constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_LOAD_W = EDGE_TW + 32;  // TMA box width: 16 B aligned both sides
 
@@ -106,8 +106,8 @@ struct EdgeParams {
     int32_t thr_general;       // 0: mask = gx^2 + gy^2 > s_thr; 1: threshold on magnitude
     int32_t thr_type, tv, fv;
     int32_t thr_lo, thr_hi;
+    int32_t s_thr;     // mask = gx^2 + gy^2 > s_thr (clamped to int32)
     int32_t pad;
-    int64_t s_thr;
     int32_t gvalid[4];  // valid rectangle of the Gaussian image
     int32_t valid[4];   // valid rectangle of the outputs
     int* err;

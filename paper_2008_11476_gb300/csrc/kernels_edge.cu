@@ -1,28 +1,31 @@
 // Fused edge-detection group and the Gaussian3x3 kernel (Table 2 local and
-// point operators; the edge graph of Listing 1 / Section 6 benchmarks):
+// point operators; the edge graph of Listing 1 / the Section 6 benchmarks):
 //
-//   in U8 --Gaussian3x3--> G (U8, on chip) --Sobel3x3--> gx, gy (S16, registers)
-//        --Magnitude--> m (S16) --Threshold--> mask (U8)
-//        --Phase--> phase (U8)
+//   in U8 --Gaussian3x3--> G (on chip) --Sobel3x3--> gx, gy (registers)
+//        --Magnitude--> m --Threshold--> mask (U8)      --Phase--> phase (U8)
 //
-// One CTA computes a 128 x 32 output tile:
-//   1. one TMA 2-D load brings the 160 x 36 input box (tile + 2-pixel halo,
+// One CTA (256 threads) computes a 128 x 30 output tile:
+//   1. one TMA 2-D load brings the 160 x 34 input box (tile + 2-pixel halo,
 //      widened to 16-byte-aligned columns) into shared memory; the hardware
 //      fills out-of-image bytes with 0, and edge tiles then apply the
-//      Gaussian's border mode to those bytes;
-//   2. G is computed over the tile + 1-pixel halo (130 x 34) into a shared
-//      line buffer; edge tiles then apply the Sobel's border mode to the G
+//      Gaussian's border mode to them;
+//   2. G over the tile + 1-pixel halo (130 x 32) is computed in SWAR form: each
+//      32-bit word holds two adjacent pixels as 16-bit lanes, so every add,
+//      shift and funnel shift works on two pixels; G stays in shared memory as
+//      16-bit pixels.  Edge tiles then apply the Sobel's border mode to the G
 //      cells outside the image (REPLICATE reads the replicated *Gaussian*
 //      output, as the node-by-node definition requires);
-//   3. each thread takes 16 consecutive pixels of one row, forms gx, gy with
-//      separable sums, and produces mask / phase / magnitude, written with
-//      16-byte stores.
+//   3. each item is 8 pixels of one row: gx and gy are formed in the same
+//      16-bit-lane form (biased so that no lane goes negative), unpacked to
+//      binary32 by exponent splicing, and the point operators run in binary32
+//      (every value involved is an integer below 2^24, so the float arithmetic
+//      is exact); the U8 results are written with 8-byte stores.
 // Magnitude followed by a binary threshold T is evaluated as
 // gx^2 + gy^2 > T^2 + T, which equals round(sqrt(gx^2 + gy^2)) > T exactly.
 //
 // The batch kernel runs the same tile code persistently over the tiles of
-// many images (one tensor map per image, kept in global memory), and issues
-// the TMA load of its next tile while it computes the current one.
+// many images (one tensor map per image, in global memory), and issues the
+// TMA load of its next tile as soon as the current input box has been read.
 #include "device_common.cuh"
 #include "launchers.h"
 
@@ -31,59 +34,48 @@ namespace {
 
 using namespace dev;
 
-constexpr int TW = EDGE_TW;
-constexpr int TH = EDGE_TH;
-constexpr int LW = EDGE_LOAD_W;
-constexpr int IN_ROWS = TH + 4;
-constexpr int G_ROWS = TH + 2;
+constexpr int TW = EDGE_TW;          // 128
+constexpr int TH = EDGE_TH;          // 30
+constexpr int LW = EDGE_LOAD_W;      // 160
+constexpr int IN_ROWS = TH + 4;      // 34
+constexpr int G_ROWS = TH + 2;       // 32
+constexpr int GW = TW + 16;          // G columns x0 - 8 .. x0 + 135
 constexpr uint32_t IN_BYTES = IN_ROWS * LW;
+
+// Kernel modes (template parameter).
+constexpr int M_GAUSS = 0;      // Gaussian3x3 alone: write G
+constexpr int M_MASK_PHASE = 1; // binary threshold mask + phase
+constexpr int M_MASK = 2;       // binary threshold mask only
+constexpr int M_PHASE = 3;      // phase only
+constexpr int M_GENERAL = 4;    // any outputs (magnitude export, range threshold)
 
 struct EdgeSmem {
     alignas(128) uint8_t in[IN_ROWS][LW];  // image (x0 - 16 + c, y0 - 2 + r)
-    alignas(16) uint8_t g[G_ROWS][LW];     // Gaussian (x0 - 16 + c, y0 - 1 + r)
+    alignas(16) uint16_t g[G_ROWS][GW];    // Gaussian (x0 - 8 + k, y0 - 1 + r)
     alignas(8) uint64_t bar;
     int img;                               // batch: image of the current tile
     int next_img;
 };
 
-__device__ __forceinline__ void load18(const uint8_t* row, int c, int v[18]) {
-    v[0] = row[c - 1];
-    uint4 q = *reinterpret_cast<const uint4*>(row + c);
-    uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[1 + j] = (w[j >> 2] >> (8 * (j & 3))) & 0xFF;
-    v[17] = row[c + 16];
+// 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
+__device__ __forceinline__ uint32_t lo_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }
+__device__ __forceinline__ uint32_t hi_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }
+
+// (lane1 of a, lane0 of b): the pair starting one pixel to the right of a.
+__device__ __forceinline__ uint32_t shift_pair(uint32_t a, uint32_t b) {
+    return __funnelshift_r(a, b, 16);
 }
 
-__device__ __forceinline__ uint32_t pack4(const uint32_t* b) {
-    return b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+// Lane values of a 16-bit-lane word as binary32, minus a bias, exactly.
+__device__ __forceinline__ float lane_lo_f(uint32_t w, float bias) {
+    return __int_as_float(__byte_perm(w, 0x4B00u, 0x5410)) - (8388608.0f + bias);
+}
+__device__ __forceinline__ float lane_hi_f(uint32_t w, float bias) {
+    return __int_as_float(__byte_perm(w, 0x4B00u, 0x5432)) - (8388608.0f + bias);
 }
 
-__device__ __forceinline__ void store16_u8(uint8_t* row, int x, int W, const uint32_t b[16]) {
-    if (x + 16 <= W) {
-        uint4 q;
-        q.x = pack4(b);
-        q.y = pack4(b + 4);
-        q.z = pack4(b + 8);
-        q.w = pack4(b + 12);
-        *reinterpret_cast<uint4*>(row + x) = q;
-    } else {
-        for (int j = 0; j < 16 && x + j < W; ++j) row[x + j] = (uint8_t)b[j];
-    }
-}
-
-__device__ __forceinline__ void store16_s16(int16_t* row, int x, int W, const int v[16]) {
-    if (x + 16 <= W) {
-        uint32_t w[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            w[j] = ((uint32_t)v[2 * j] & 0xFFFFu) | ((uint32_t)v[2 * j + 1] << 16);
-        uint4* d = reinterpret_cast<uint4*>(row + x);
-        d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    } else {
-        for (int j = 0; j < 16 && x + j < W; ++j) row[x + j] = (int16_t)v[j];
-    }
+__device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+    return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
 }
 
 __device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
@@ -94,7 +86,38 @@ __device__ __forceinline__ bool rect_is_full(const int32_t* r, const EdgeParams&
     return r[0] == 0 && r[1] == 0 && r[2] == (int)p.W && r[3] == (int)p.H;
 }
 
-// Apply the Gaussian's border mode to the input bytes outside the image.
+// Phase (see device_common.cuh: phase_u8) from exact binary32 gradients.
+__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
+    float ax = fabsf(gx), ay = fabsf(gy);
+    float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    float u = t * t;
+    float pp = 0.27753710746765137f;
+    pp = fmaf(pp, u, -1.3691582679748535f);
+    pp = fmaf(pp, u, 3.244159698486328f);
+    pp = fmaf(pp, u, -5.391748428344727f);
+    pp = fmaf(pp, u, 8.070429801940918f);
+    pp = fmaf(pp, u, -13.574716567993164f);
+    pp = fmaf(pp, u, 40.743507385253906f);
+    float f = fmaf(pp, t, 0.5f);
+    float fl = floorf(f);
+    float d = f - fl;
+    int ra = (int)fl;
+    if (fabsf(d - 0.5f) > 0.5f - 1e-4f) {
+        int j = d < 0.5f ? ra - 1 : ra;
+        if (j >= 0 && j < 32) {
+            double cr = (double)mn * kPhaseBoundCos[j] - (double)mx * kPhaseBoundSin[j];
+            ra = cr >= 0.0 ? j + 1 : j;
+        }
+    }
+    int q1 = ay > ax ? 64 - ra : ra;
+    bool sx = gx < 0.0f, sy = gy < 0.0f;
+    int q = (sx ? 128 : 0) + ((sx != sy) ? -q1 : q1);
+    return (uint32_t)q & 255u;
+}
+
+// ---- stage 1: input border -------------------------------------------------------
+
 __device__ void fix_input_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
@@ -106,138 +129,208 @@ __device__ void fix_input_border(EdgeSmem& sm, const EdgeParams& p, int x0, int 
         if (p.border_g == HVX_BORDER_CONSTANT) {
             v = (uint8_t)p.cval_g;
         } else {
-            int cy = clampi(y, 0, H - 1) - (y0 - 2);
-            int cx = clampi(x, 0, W - 1) - (x0 - 16);
-            v = sm.in[cy][cx];
+            v = sm.in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
         }
         sm.in[r][c] = v;
     }
 }
 
-// G over rows y0-1 .. y0+TH, columns x0-4 .. x0+TW+3 (4-pixel chunks).
-__device__ void compute_gaussian(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
-                                 bool interior) {
-    const int rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 8 : 0;
-    constexpr int CHUNKS = (TW + 8) / 4;  // 34 chunks of 4 columns, c = 12 .. 144
-    const bool full = interior || rect_is_full(p.gvalid, p);
-    for (int it = threadIdx.x; it < G_ROWS * CHUNKS; it += blockDim.x) {
-        int r = it / CHUNKS;
-        int c = 12 + 4 * (it - r * CHUNKS);
-        int v[6];
+// ---- stage 2: Gaussian in 16-bit lanes ---------------------------------------------
+// Item (r, q): G row r (y = y0 - 1 + r), pixels x = x0 + 8q .. x0 + 8q + 7;
+// group 0 also produces x0 - 1 and group 15 also x0 + 128.
+__device__ void gaussian_stage(EdgeSmem& sm, const EdgeParams& p) {
+    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
+    for (int it = threadIdx.x; it < G_ROWS * 16; it += blockDim.x) {
+        const int r = it >> 4, q = it & 15;
+        const int c = 16 + 8 * q;
+        uint32_t V[6];  // vertical sums of pixel pairs (x-2,x-1), (x,x+1) .. (x+8,x+9)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            int cc = c - 1 + j;
-            v[j] = sm.in[r][cc] + 2 * sm.in[r + 1][cc] + sm.in[r + 2][cc];
+        for (int dr = 0; dr < 3; ++dr) {
+            const uint8_t* row = sm.in[r + dr];
+            uint2 m = *reinterpret_cast<const uint2*>(row + c);
+            uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
+            uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
+            uint32_t P[6] = {hi_pair(wl), lo_pair(m.x), hi_pair(m.x),
+                             lo_pair(m.y), hi_pair(m.y), lo_pair(wr)};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) V[k] = dr == 0 ? P[k] : V[k] + (dr == 1 ? 2u : 1u) * P[k];
         }
-        uint32_t b[4];
+        uint32_t Gp[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = (uint32_t)((v[i] + 2 * v[i + 1] + v[i + 2] + rnd) >> 4);
-        if (!full) {
-            int y = y0 - 1 + r;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                int x = x0 - 16 + c + i;
-                if (x >= 0 && x < (int)p.W && y >= 0 && y < (int)p.H && !in_rect(p.gvalid, x, y))
-                    b[i] = 0;
-            }
+        for (int j = 1; j <= 4; ++j) {
+            uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
+            Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
         }
-        *reinterpret_cast<uint32_t*>(&sm.g[r][c]) = pack4(b);
+        *reinterpret_cast<uint4*>(&sm.g[r][8 + 8 * q]) = make_uint4(Gp[0], Gp[1], Gp[2], Gp[3]);
+        // The two halo columns, each written as a word together with the column
+        // beyond it set to 0: stage 3 reads those outer lanes (cols 6, 137)
+        // as part of its pair loads, and a zero lane cannot carry into its
+        // neighbour in the 16-bit-lane arithmetic.
+        if (q == 0) {  // x0 - 1 = V lane (x-2) + 2 (x-1) + (x)
+            uint32_t s = (V[0] & 0xFFFFu) + 2u * (V[0] >> 16) + (V[1] & 0xFFFFu) + (rnd & 0xFFFFu);
+            *reinterpret_cast<uint32_t*>(&sm.g[r][6]) = (s >> 4) << 16;
+        } else if (q == 15) {  // x0 + 128 = (x+7) + 2 (x+8) + (x+9), x = x0 + 120
+            uint32_t s = (V[4] >> 16) + 2u * (V[5] & 0xFFFFu) + (V[5] >> 16) + (rnd & 0xFFFFu);
+            *reinterpret_cast<uint32_t*>(&sm.g[r][136]) = s >> 4;
+        }
     }
 }
 
-// Apply the Sobel's border mode to the G cells outside the image.
+// G cells: zero inside the image but outside the Gaussian's valid region; the
+// Sobel's border mode outside the image.  Edge tiles only.
 __device__ void fix_g_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
-    if (p.border_s == HVX_BORDER_UNDEFINED) return;
-    constexpr int COLS = TW + 8;  // c = 12 .. 147
-    for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
-        int r = i / COLS, c = 12 + (i - r * COLS);
-        int x = x0 - 16 + c, y = y0 - 1 + r;
-        if (x >= 0 && x < W && y >= 0 && y < H) continue;
-        uint8_t v;
-        if (p.border_s == HVX_BORDER_CONSTANT) {
-            v = (uint8_t)p.cval_s;
-        } else {
-            int cy = clampi(y, 0, H - 1) - (y0 - 1);
-            int cx = clampi(x, 0, W - 1) - (x0 - 16);
-            v = sm.g[cy][cx];
+    constexpr int COLS = TW + 2;  // k = 7 .. 136
+    // pass 1: valid region of G
+    if (!rect_is_full(p.gvalid, p)) {
+        for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
+            int r = i / COLS, k = 7 + (i - r * COLS);
+            int x = x0 - 8 + k, y = y0 - 1 + r;
+            if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.gvalid, x, y)) sm.g[r][k] = 0;
         }
-        sm.g[r][c] = v;
+        __syncthreads();
+    }
+    if (p.border_s == HVX_BORDER_UNDEFINED) return;
+    for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
+        int r = i / COLS, k = 7 + (i - r * COLS);
+        int x = x0 - 8 + k, y = y0 - 1 + r;
+        if (x >= 0 && x < W && y >= 0 && y < H) continue;
+        uint16_t v;
+        if (p.border_s == HVX_BORDER_CONSTANT)
+            v = (uint16_t)(p.cval_s & 0xFF);
+        else
+            v = sm.g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
+        sm.g[r][k] = v;
     }
 }
 
-// Sobel + point operators for 16 pixels of one row, stores to global.
+// ---- stage 3: Sobel + point operators ------------------------------------------------
+
+__device__ __forceinline__ void load_g_row(const uint16_t* row, int k, uint32_t P[6]) {
+    uint4 m = *reinterpret_cast<const uint4*>(row + k);
+    P[0] = *reinterpret_cast<const uint32_t*>(row + k - 2);
+    P[1] = m.x;
+    P[2] = m.y;
+    P[3] = m.z;
+    P[4] = m.w;
+    P[5] = *reinterpret_cast<const uint32_t*>(row + k + 8);
+}
+
+__device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
+    if (x + 8 <= W) {
+        *reinterpret_cast<uint2*>(row + x) =
+            make_uint2(pack4(b[0], b[1], b[2], b[3]), pack4(b[4], b[5], b[6], b[7]));
+    } else {
+        for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (uint8_t)b[j];
+    }
+}
+
+template <int MODE>
 __device__ void sobel_point_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
                                   bool interior) {
-    const int row = threadIdx.x >> 3, seg = threadIdx.x & 7;
-    const int y = y0 + row, x = x0 + seg * 16;
-    if (y >= (int)p.H || x >= (int)p.W) return;
-    const int c = 16 + seg * 16;
-    int g0[18], g1[18], g2[18];
-    load18(sm.g[row], c, g0);
-    load18(sm.g[row + 1], c, g1);
-    load18(sm.g[row + 2], c, g2);
-    int vs[18], dy[18];
-#pragma unroll
-    for (int k = 0; k < 18; ++k) {
-        vs[k] = g0[k] + 2 * g1[k] + g2[k];
-        dy[k] = g2[k] - g0[k];
-    }
+    const float s_thr = (float)p.s_thr;
     const bool full = interior || rect_is_full(p.valid, p);
-    uint32_t mk[16], ph[16];
-    int mg[16];
+#pragma unroll 1
+    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
+        const int r = it >> 4, s8 = it & 15;
+        const int y = y0 + r, x = x0 + 8 * s8;
+        if (y >= (int)p.H || x >= (int)p.W) continue;
+        const int k = 8 + 8 * s8;
+        uint32_t A[6], B[6], C[6];
+        load_g_row(sm.g[r], k, A);
+        load_g_row(sm.g[r + 1], k, B);
+        load_g_row(sm.g[r + 2], k, C);
+        uint32_t vs[6], dy[6];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        int gx = vs[i + 2] - vs[i];
-        int gy = dy[i] + 2 * dy[i + 1] + dy[i + 2];
-        bool ok = full || in_rect(p.valid, x + i, y);
-        if (p.mask) {
-            uint32_t m;
-            if (!p.thr_general) {
-                long long s = (long long)gx * gx + (long long)gy * gy;
-                m = s > p.s_thr ? (uint32_t)p.tv : (uint32_t)p.fv;
-            } else {
-                int mv = magnitude_s16(gx, gy);
-                bool t = p.thr_type == HVX_THRESHOLD_BINARY ? mv > p.thr_lo
-                                                             : !(mv > p.thr_hi || mv < p.thr_lo);
-                m = t ? (uint32_t)p.tv : (uint32_t)p.fv;
-            }
-            mk[i] = ok ? m : 0u;
+        for (int j = 0; j < 6; ++j) {
+            vs[j] = A[j] + 2u * B[j] + C[j];          // <= 1020 per lane
+            dy[j] = C[j] + 0x00FF00FFu - A[j];        // gy part + 255 per lane
         }
-        if (p.phase) ph[i] = ok ? phase_u8(gx, gy) : 0u;
-        if (p.mag) mg[i] = ok ? magnitude_s16(gx, gy) : 0;
+        float gx[8], gy[8];
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            uint32_t gxp = shift_pair(vs[j], vs[j + 1]) + 0x04000400u - shift_pair(vs[j - 1], vs[j]);
+            uint32_t gyp = shift_pair(dy[j - 1], dy[j]) + 2u * dy[j] + shift_pair(dy[j], dy[j + 1]);
+            gx[2 * j - 2] = lane_lo_f(gxp, 1024.0f);
+            gx[2 * j - 1] = lane_hi_f(gxp, 1024.0f);
+            gy[2 * j - 2] = lane_lo_f(gyp, 1020.0f);
+            gy[2 * j - 1] = lane_hi_f(gyp, 1020.0f);
+        }
+        uint32_t mk[8], ph[8];
+        int mg[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            mk[i] = ph[i] = 0u;
+            mg[i] = 0;
+            if (MODE == M_MASK_PHASE || MODE == M_MASK) {
+                float s2 = fmaf(gx[i], gx[i], gy[i] * gy[i]);
+                mk[i] = s2 > s_thr ? (uint32_t)p.tv : (uint32_t)p.fv;
+            }
+            if (MODE == M_MASK_PHASE || MODE == M_PHASE) ph[i] = phase_from_float(gx[i], gy[i]);
+            if (MODE == M_GENERAL) {
+                int ix = (int)gx[i], iy = (int)gy[i];
+                mg[i] = magnitude_s16(ix, iy);
+                if (p.mask) {
+                    bool t;
+                    if (!p.thr_general)
+                        t = ix * ix + iy * iy > p.s_thr;
+                    else
+                        t = p.thr_type == HVX_THRESHOLD_BINARY
+                                ? mg[i] > p.thr_lo
+                                : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
+                    mk[i] = t ? (uint32_t)p.tv : (uint32_t)p.fv;
+                }
+                if (p.phase) ph[i] = phase_from_float(gx[i], gy[i]);
+            }
+        }
+        if (!full) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (!in_rect(p.valid, x + i, y)) {
+                    mk[i] = 0u;
+                    ph[i] = 0u;
+                    mg[i] = 0;
+                }
+        }
+        const bool want_mask =
+            MODE == M_MASK_PHASE || MODE == M_MASK || (MODE == M_GENERAL && p.mask);
+        const bool want_phase =
+            MODE == M_MASK_PHASE || MODE == M_PHASE || (MODE == M_GENERAL && p.phase);
+        if (want_mask) store8_u8(p.mask + (size_t)y * p.mask_pitch, x, p.W, mk);
+        if (want_phase) store8_u8(p.phase + (size_t)y * p.phase_pitch, x, p.W, ph);
+        if (MODE == M_GENERAL && p.mag) {
+            int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
+                                                      (size_t)y * p.mag_pitch);
+            if (x + 8 <= (int)p.W) {
+                *reinterpret_cast<uint4*>(row + x) =
+                    make_uint4((mg[0] & 0xFFFF) | ((uint32_t)mg[1] << 16),
+                               (mg[2] & 0xFFFF) | ((uint32_t)mg[3] << 16),
+                               (mg[4] & 0xFFFF) | ((uint32_t)mg[5] << 16),
+                               (mg[6] & 0xFFFF) | ((uint32_t)mg[7] << 16));
+            } else {
+                for (int j = 0; j < 8 && x + j < (int)p.W; ++j) row[x + j] = (int16_t)mg[j];
+            }
+        }
     }
-    if (p.mask) store16_u8(p.mask + (size_t)y * p.mask_pitch, x, p.W, mk);
-    if (p.phase) store16_u8(p.phase + (size_t)y * p.phase_pitch, x, p.W, ph);
-    if (p.mag)
-        store16_s16(reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
-                                               (size_t)y * p.mag_pitch),
-                    x, p.W, mg);
 }
 
-// Gaussian3x3 alone: 16 pixels of one row straight from the input box.
-__device__ void gaussian_only_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
-                                    bool interior) {
-    const int row = threadIdx.x >> 3, seg = threadIdx.x & 7;
-    const int y = y0 + row, x = x0 + seg * 16;
-    if (y >= (int)p.H || x >= (int)p.W) return;
-    const int c = 16 + seg * 16;
-    const int rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 8 : 0;
-    int a[18], b[18], d[18];
-    load18(sm.in[row + 1], c, a);
-    load18(sm.in[row + 2], c, b);
-    load18(sm.in[row + 3], c, d);
-    int v[18];
-#pragma unroll
-    for (int k = 0; k < 18; ++k) v[k] = a[k] + 2 * b[k] + d[k];
+// Gaussian3x3 alone: G rows y0 .. y0+TH-1 from shared memory to the output.
+__device__ void gaussian_out_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
+                                   bool interior) {
     const bool full = interior || rect_is_full(p.gvalid, p);
-    uint32_t o[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        uint32_t g = (uint32_t)((v[i] + 2 * v[i + 1] + v[i + 2] + rnd) >> 4);
-        o[i] = (full || in_rect(p.gvalid, x + i, y)) ? g : 0u;
+#pragma unroll 1
+    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
+        const int r = it >> 4, q = it & 15;
+        const int y = y0 + r, x = x0 + 8 * q;
+        if (y >= (int)p.H || x >= (int)p.W) continue;
+        uint4 m = *reinterpret_cast<const uint4*>(&sm.g[r + 1][8 + 8 * q]);
+        uint32_t b[8] = {m.x & 0xFFu, m.x >> 16, m.y & 0xFFu, m.y >> 16,
+                         m.z & 0xFFu, m.z >> 16, m.w & 0xFFu, m.w >> 16};
+        if (!full)
+            for (int i = 0; i < 8; ++i)
+                if (!in_rect(p.gvalid, x + i, y)) b[i] = 0;
+        store8_u8(p.gout + (size_t)y * p.gout_pitch, x, p.W, b);
     }
-    store16_u8(p.gout + (size_t)y * p.gout_pitch, x, p.W, o);
 }
 
 __device__ __forceinline__ void issue_load(EdgeSmem& sm, const CUtensorMap* map, int x0, int y0) {
@@ -245,26 +338,18 @@ __device__ __forceinline__ void issue_load(EdgeSmem& sm, const CUtensorMap* map,
     tma_load_2d(&sm.in[0][0], map, &sm.bar, x0 - 16, y0 - 2);
 }
 
-// One tile after its input box has landed in sm.in.
-__device__ void edge_tile_body(EdgeSmem& sm, const EdgeParams& p, int x0, int y0, bool gauss_only,
+// One tile after its input box has landed in sm.in.  If next_map is set,
+// thread 0 starts the next tile's load as soon as sm.in is no longer read.
+template <int MODE>
+__device__ void edge_tile_body(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
                                const CUtensorMap* next_map, int nx0, int ny0) {
     const bool interior = tile_is_interior(p, x0, y0);
     if (!interior) {
         fix_input_border(sm, p, x0, y0);
         __syncthreads();
     }
-    if (gauss_only) {
-        gaussian_only_stage(sm, p, x0, y0, interior);
-        __syncthreads();
-        if (next_map && threadIdx.x == 0) {
-            fence_proxy_async_smem();
-            issue_load(sm, next_map, nx0, ny0);
-        }
-        return;
-    }
-    compute_gaussian(sm, p, x0, y0, interior);
+    gaussian_stage(sm, p);
     __syncthreads();
-    // the input box is no longer read: start the next tile's load now
     if (next_map && threadIdx.x == 0) {
         fence_proxy_async_smem();
         issue_load(sm, next_map, nx0, ny0);
@@ -273,12 +358,16 @@ __device__ void edge_tile_body(EdgeSmem& sm, const EdgeParams& p, int x0, int y0
         fix_g_border(sm, p, x0, y0);
         __syncthreads();
     }
-    sobel_point_stage(sm, p, x0, y0, interior);
+    if (MODE == M_GAUSS)
+        gaussian_out_stage(sm, p, x0, y0, interior);
+    else
+        sobel_point_stage<MODE>(sm, p, x0, y0, interior);
     __syncthreads();
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(EDGE_THREADS, 3)
-    edge_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p, int gauss_only) {
+    edge_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
     __shared__ EdgeSmem sm;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     if (threadIdx.x == 0) {
@@ -288,7 +377,7 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3)
     __syncthreads();
     if (threadIdx.x == 0) issue_load(sm, &tmap, x0, y0);
     if (!mbar_wait_bounded(&sm.bar, 0, p.err)) return;
-    edge_tile_body(sm, p, x0, y0, gauss_only != 0, nullptr, 0, 0);
+    edge_tile_body<MODE>(sm, p, x0, y0, nullptr, 0, 0);
 }
 
 __device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
@@ -310,6 +399,7 @@ __device__ __forceinline__ void tile_origin(const EdgeParams& p, int t, int& x0,
     y0 = ty * TH;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(EDGE_THREADS, 3) edge_batch_kernel(const EdgeBatchDesc d) {
     __shared__ EdgeSmem sm;
     int t = blockIdx.x;
@@ -320,9 +410,8 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge_batch_kernel(const EdgeB
         int img = find_image(d.tile_start, d.n_img, t);
         sm.img = img;
         tensormap_acquire(&d.maps[img]);
-        EdgeParams p = d.params[img];
         int x0, y0;
-        tile_origin(p, t - d.tile_start[img], x0, y0);
+        tile_origin(d.params[img], t - d.tile_start[img], x0, y0);
         issue_load(sm, &d.maps[img], x0, y0);
     }
     __syncthreads();
@@ -332,8 +421,7 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge_batch_kernel(const EdgeB
         const EdgeParams& p = d.params[img];
         int x0, y0;
         tile_origin(p, t - __ldg(d.tile_start + img), x0, y0);
-        // next tile of this CTA: its image and origin (thread 0 issues the load)
-        int tn = t + gridDim.x;
+        const int tn = t + gridDim.x;
         const CUtensorMap* next_map = nullptr;
         int nx0 = 0, ny0 = 0;
         if (tn < d.total_tiles && threadIdx.x == 0) {
@@ -346,29 +434,59 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge_batch_kernel(const EdgeB
         bool ok = mbar_wait_bounded(&sm.bar, parity, d.err);
         if (__syncthreads_or(!ok)) return;
         parity ^= 1u;
-        edge_tile_body(sm, p, x0, y0, d.gauss_only != 0, next_map, nx0, ny0);
+        edge_tile_body<MODE>(sm, p, x0, y0, next_map, nx0, ny0);
         if (threadIdx.x == 0) sm.img = sm.next_img;
         __syncthreads();
     }
 }
 
-}  // namespace
-
-cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, bool gauss_only,
-                        cudaStream_t s) {
+template <int MODE>
+cudaError_t launch_mode(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
     dim3 grid((p.W + TW - 1) / TW, (p.H + TH - 1) / TH);
-    edge_kernel<<<grid, EDGE_THREADS, 0, s>>>(map, p, gauss_only ? 1 : 0);
+    edge_kernel<MODE><<<grid, EDGE_THREADS, 0, s>>>(map, p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s) {
-    edge_batch_kernel<<<grid, EDGE_THREADS, 0, s>>>(d);
+template <int MODE>
+cudaError_t launch_batch_mode(const EdgeBatchDesc& d, int grid, cudaStream_t s) {
+    edge_batch_kernel<MODE><<<grid, EDGE_THREADS, 0, s>>>(d);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+int edge_mode(const EdgeParams& p) {
+    if (p.gout) return M_GAUSS;
+    if (p.mag || p.thr_general) return M_GENERAL;
+    if (p.mask && p.phase) return M_MASK_PHASE;
+    if (p.mask) return M_MASK;
+    return M_PHASE;
+}
+
+cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
+    switch (edge_mode(p)) {
+        case M_GAUSS: return launch_mode<M_GAUSS>(map, p, s);
+        case M_MASK_PHASE: return launch_mode<M_MASK_PHASE>(map, p, s);
+        case M_MASK: return launch_mode<M_MASK>(map, p, s);
+        case M_PHASE: return launch_mode<M_PHASE>(map, p, s);
+        default: return launch_mode<M_GENERAL>(map, p, s);
+    }
+}
+
+cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s) {
+    switch (mode) {
+        case M_GAUSS: return launch_batch_mode<M_GAUSS>(d, grid, s);
+        case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, s);
+        case M_MASK: return launch_batch_mode<M_MASK>(d, grid, s);
+        case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, s);
+        default: return launch_batch_mode<M_GENERAL>(d, grid, s);
+    }
 }
 
 int edge_batch_blocks_per_sm() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel, EDGE_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel<M_MASK_PHASE>,
+                                                  EDGE_THREADS, 0);
     return n;
 }
 

@@ -15,13 +15,14 @@ struct EdgeBatchDesc {
     const int* tile_start;       // n_img + 1 prefix sums of per-image tile counts
     int n_img;
     int total_tiles;
-    int gauss_only;
     int* err;
 };
 
-cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, bool gauss_only,
-                        cudaStream_t s);
-cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
+// Output mode of an edge / Gaussian group (which kernel instantiation runs it);
+// every image of one batch launch must have the same mode.
+int edge_mode(const EdgeParams& p);
+cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
+cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s);
 int edge_batch_blocks_per_sm();
 
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);

@@ -184,9 +184,9 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
             if (T < 0)
                 e.s_thr = -1;
             else if (T >= 32767)
-                e.s_thr = std::numeric_limits<int64_t>::max();
+                e.s_thr = std::numeric_limits<int32_t>::max();
             else
-                e.s_thr = T * T + T;
+                e.s_thr = (int32_t)(T * T + T);
         } else {
             e.thr_general = 1;
         }
@@ -541,8 +541,8 @@ hvx_status launch_plan(Graph* g, cudaStream_t s) {
     for (Group& G : g->plan.groups) {
         cudaError_t e = cudaSuccess;
         switch (G.kernel) {
-            case GK_GAUSS: e = launch_edge(G.tmap, G.edge, true, s); break;
-            case GK_EDGE: e = launch_edge(G.tmap, G.edge, false, s); break;
+            case GK_GAUSS:
+            case GK_EDGE: e = launch_edge(G.tmap, G.edge, s); break;
             case GK_HARRIS: e = launch_harris(G.tmap, G.harris, s); break;
             case GK_POINT:
             case GK_CHX_UV: e = launch_plain(G.plain, s); break;
@@ -584,7 +584,7 @@ void destroy_batch_cache(Context* ctx) {
 
 namespace {
 
-hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, bool gauss,
+hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
                              BatchEntry& out) {
     const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
     const size_t params_off = maps_bytes;
@@ -618,7 +618,6 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     d.tile_start = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tiles_off);
     d.n_img = n;
     d.total_tiles = tile_start[n];
-    d.gauss_only = gauss ? 1 : 0;
     d.err = ctx->d_error;
     int per_sm = std::max(1, edge_batch_blocks_per_sm());
     int grid = std::min(d.total_tiles, ctx->num_sms * per_sm);
@@ -632,7 +631,7 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bc->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_edge_batch(d, grid, bc->capture);
+        cudaError_t le = launch_edge_batch(d, mode, grid, bc->capture);
         e = cudaStreamEndCapture(bc->capture, &graph);
         if (le != cudaSuccess) e = le;
     }
@@ -655,16 +654,21 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
 }  // namespace
 
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
-    // one persistent launch when every plan is a single edge group, or every
-    // plan a single Gaussian group
-    bool all_edge = true, all_gauss = true;
-    for (int i = 0; i < n; ++i) {
+    // one persistent launch when every plan is a single edge (or Gaussian)
+    // group and all of them use the same kernel mode
+    bool same = true;
+    int mode = -1;
+    for (int i = 0; i < n && same; ++i) {
         const Plan& P = gs[i]->plan;
-        bool one = P.groups.size() == 1;
-        all_edge &= one && P.groups[0].kernel == GK_EDGE;
-        all_gauss &= one && P.groups[0].kernel == GK_GAUSS;
+        same = P.groups.size() == 1 &&
+               (P.groups[0].kernel == GK_EDGE || P.groups[0].kernel == GK_GAUSS);
+        if (same) {
+            int m = edge_mode(P.groups[0].edge);
+            same = mode < 0 || m == mode;
+            mode = m;
+        }
     }
-    if (!all_edge && !all_gauss) {
+    if (!same) {
         for (int i = 0; i < n; ++i) {
             hvx_status st = launch_plan(gs[i], s);
             if (st != HVX_SUCCESS) return st;
@@ -695,7 +699,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             bc->entries.erase(oldest);
         }
         BatchEntry fresh;
-        hvx_status st = build_batch_entry(ctx, bc, gs, n, all_gauss && !all_edge, fresh);
+        hvx_status st = build_batch_entry(ctx, bc, gs, n, mode, fresh);
         if (st != HVX_SUCCESS) return st;
         bc->entries.push_back(fresh);
         hit = &bc->entries.back();

@@ -425,3 +425,4 @@ def hvxServerResetStats(srv):
 def hvxReleaseServer(srv):
     h = ctypes.c_void_p(srv.value if isinstance(srv, ctypes.c_void_p) else srv)
     _ck(lib().hvxReleaseServer(ctypes.byref(h)), "hvxReleaseServer")
+
