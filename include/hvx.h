@@ -375,6 +375,57 @@ hvx_status hvxServerResetStats(hvx_server s);
 /* Drain outstanding requests and destroy the server.  Sets *s to NULL. */
 hvx_status hvxReleaseServer(hvx_server* s);
 
+/* ------------------------------------------------------------------------ */
+/* Batched edge graph that allocates nothing.                                 */
+/*                                                                            */
+/* The paper has no counterpart to this call.  It exists for callers that     */
+/* must not allocate device memory: a process whose device memory is fully   */
+/* owned by another allocator (a framework's caching pool), a real-time loop  */
+/* that cannot afford cudaMalloc's implicit device synchronisation, or code   */
+/* running with a fixed memory footprint.  hvxProcessGraphBatch allocates     */
+/* (and caches) device memory for per-frame launch tables, and every context  */
+/* allocates a device error word; this call keeps all of that in one fixed    */
+/* array inside the library instead.                                         */
+
+/* Largest number of frames one hvxEdgeBatchNoAlloc call accepts.  The fixed
+ * scratch array sized for it (about 80 KB) is part of the library's device
+ * image: every GPU that loads the library holds it until the process exits. */
+#define HVX_NOALLOC_MAX_FRAMES 256
+
+/* One caller-owned frame: a U8 input and the U8 phase and / or mask outputs,
+ * all device pointers 16-byte aligned, pitches in bytes, multiples of 16 and
+ * at least width.  phase or mask may be NULL (not produced), the same way in
+ * every frame of one call.  1 <= width, height <= 32768. */
+typedef struct {
+    const void* in;
+    uint64_t in_pitch;
+    void* phase;
+    uint64_t phase_pitch;
+    void* mask;
+    uint64_t mask_pitch;
+    uint32_t width, height;
+} hvx_edge_frame;
+
+/* Run the edge graph Gaussian3x3 -> Sobel3x3 -> Magnitude -> binary Threshold
+ * (mask = 255 where round(magnitude) > threshold, else 0) and Phase on n
+ * frames with one persistent kernel launch on `stream` -- the result equals
+ * hvxProcessGraphBatch on edge graphs with the same border (applied to both
+ * local nodes, constant 0) and truncating Gaussian rounding.
+ *
+ * Allocates nothing: no cudaMalloc / cudaFree or other allocating routine.
+ * The launch tables and the device error word live in a fixed array of the
+ * library; its address is looked up (cudaGetSymbolAddress) on the first call
+ * made on each device, with that device current, so make that first call
+ * before any stream capture.  Every call rewrites the array (clearing the
+ * error word), so calls whose GPU work overlaps -- from different host
+ * threads or on different streams without ordering -- race on it; calls are
+ * serialised on the host side only.  The call waits for its work on `stream`
+ * and returns HVX_ERROR_TIMEOUT if a kernel's bounded wait ran out.
+ * Returns HVX_ERROR_OVER_BUDGET if n > HVX_NOALLOC_MAX_FRAMES and
+ * HVX_ERROR_INVALID_PARAMETERS for a NULL, misaligned or inconsistent frame. */
+hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t n, int32_t border,
+                               int32_t threshold, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

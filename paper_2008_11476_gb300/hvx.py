@@ -70,6 +70,16 @@ class hvx_server_stats(ctypes.Structure):
                                               "mpix_completed")]
 
 
+HVX_NOALLOC_MAX_FRAMES = 256
+
+
+class hvx_edge_frame(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("in_pitch", ctypes.c_uint64),
+                ("phase", ctypes.c_void_p), ("phase_pitch", ctypes.c_uint64),
+                ("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_uint64),
+                ("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -129,6 +139,7 @@ _SIGS = {
     "hvxServerStats": (I32, [P, ctypes.POINTER(hvx_server_stats)]),
     "hvxServerResetStats": (I32, [P]),
     "hvxReleaseServer": (I32, [PP]),
+    "hvxEdgeBatchNoAlloc": (I32, [ctypes.c_void_p, I32, I32, I32, P]),
 }
 
 
@@ -426,3 +437,11 @@ def hvxReleaseServer(srv):
     h = ctypes.c_void_p(srv.value if isinstance(srv, ctypes.c_void_p) else srv)
     _ck(lib().hvxReleaseServer(ctypes.byref(h)), "hvxReleaseServer")
 
+
+# --- batched edge graph without allocation --------------------------------------------
+
+def hvxEdgeBatchNoAlloc(frames, border: int, threshold: int, stream: int = 0):
+    """frames: sequence of hvx_edge_frame (device pointers and pitches)."""
+    arr = (hvx_edge_frame * len(frames))(*frames)
+    _ck(lib().hvxEdgeBatchNoAlloc(ctypes.cast(arr, ctypes.c_void_p), len(frames), border,
+                                  threshold, stream), "hvxEdgeBatchNoAlloc")
