@@ -154,6 +154,13 @@ hvx_status hvxCreateContextEx(int32_t flags, hvx_context* out);
  * first. */
 hvx_status hvxReleaseContext(hvx_context* ctx);
 
+/* Self-test of the device-side failure path: launches a kernel that waits on
+ * a barrier nothing ever completes.  Every wait in this library's kernels is
+ * bounded; this one must give up after a few milliseconds, record the
+ * failure in the context's error word and exit.  Returns HVX_ERROR_TIMEOUT
+ * when that happened (the expected result); the context remains usable. */
+hvx_status hvxSelfTestBoundedWait(hvx_context ctx);
+
 /* Cap the device bytes the context may allocate for images and plans
  * (0 = unlimited).  Allocations beyond it fail with HVX_ERROR_OVER_BUDGET. */
 hvx_status hvxSetContextMemoryBudget(hvx_context ctx, uint64_t bytes);

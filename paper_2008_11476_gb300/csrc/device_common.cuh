@@ -79,8 +79,8 @@ constexpr int ERR_TMA_TIMEOUT = 1;
 // second).  On time-out, record the error, wait once more with the same limit
 // so that a late copy does not land after the CTA has moved on, and return
 // false; the caller then leaves the tile.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
-    const long long limit = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  long long limit = 1ll << 31) {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > limit) {

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <mutex>
@@ -562,6 +563,7 @@ struct BatchEntry {
     void* dmem = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t last_use = 0;
+    int grid = 0;  // persistent CTAs chosen by the autotuner
 };
 
 struct BatchCache {
@@ -584,8 +586,52 @@ void destroy_batch_cache(Context* ctx) {
 
 namespace {
 
+// Persistent grid size for one batch signature: every candidate (1 .. the
+// occupancy limit of CTAs per SM) runs the batch twice on the internal
+// stream after the caller's stream has drained, timed with events; the
+// fastest is kept.  The batch's work is idempotent (every output pixel is
+// rewritten with the same value), so the trial runs are harmless.
+// HVX_AUTOTUNE=0 in the environment skips the trials and takes the
+// occupancy limit.
+int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode, cudaStream_t s) {
+    const int per_sm_max = std::max(1, edge_batch_blocks_per_sm());
+    int best = std::min(d.total_tiles, ctx->num_sms * per_sm_max);
+    const char* env = std::getenv("HVX_AUTOTUNE");
+    if ((env && env[0] == '0') || per_sm_max == 1) return best;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return best;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaEventDestroy(a);
+        return best;
+    }
+    float best_ms = 1e30f;
+    for (int per = 1; per <= per_sm_max; ++per) {
+        int grid = std::min(d.total_tiles, ctx->num_sms * per);
+        launch_edge_batch(d, mode, grid, bc->capture);  // warm-up
+        cudaEventRecord(a, bc->capture);
+        launch_edge_batch(d, mode, grid, bc->capture);
+        launch_edge_batch(d, mode, grid, bc->capture);
+        cudaEventRecord(b, bc->capture);
+        float ms = 0;
+        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = grid;
+        }
+        cudaGetLastError();
+        if (grid == d.total_tiles) break;  // more CTAs than tiles change nothing
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
 hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
-                             BatchEntry& out) {
+                             cudaStream_t user_stream, BatchEntry& out) {
     const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
     const size_t params_off = maps_bytes;
     const size_t tiles_off = params_off + (size_t)n * sizeof(EdgeParams);
@@ -619,8 +665,6 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     d.n_img = n;
     d.total_tiles = tile_start[n];
     d.err = ctx->d_error;
-    int per_sm = std::max(1, edge_batch_blocks_per_sm());
-    int grid = std::min(d.total_tiles, ctx->num_sms * per_sm);
     if (!bc->capture) {
         e = cudaStreamCreateWithFlags(&bc->capture, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
@@ -628,6 +672,7 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
             return cuda_status(e);
         }
     }
+    const int grid = autotune_grid(ctx, bc, d, mode, user_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bc->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -648,6 +693,7 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
     out.dmem = dmem;
     out.exec = exec;
+    out.grid = grid;
     return HVX_SUCCESS;
 }
 
@@ -699,7 +745,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             bc->entries.erase(oldest);
         }
         BatchEntry fresh;
-        hvx_status st = build_batch_entry(ctx, bc, gs, n, mode, fresh);
+        hvx_status st = build_batch_entry(ctx, bc, gs, n, mode, s, fresh);
         if (st != HVX_SUCCESS) return st;
         bc->entries.push_back(fresh);
         hit = &bc->entries.back();

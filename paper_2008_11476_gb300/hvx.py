@@ -96,6 +96,7 @@ _SIGS = {
     "hvxCreateContextEx": (I32, [I32, PP]),
     "hvxReleaseContext": (I32, [PP]),
     "hvxSetContextMemoryBudget": (I32, [P, U64]),
+    "hvxSelfTestBoundedWait": (I32, [P]),
     "hvxGetContextMemoryUsage": (I32, [P, ctypes.POINTER(U64)]),
     "hvxCreateImage": (I32, [P, U32, U32, I32, PP]),
     "hvxCreateImageFromHandle": (I32, [P, U32, U32, I32, P, U64, PP]),
@@ -197,6 +198,11 @@ def hvxCreateContextEx(flags: int):
 def hvxReleaseContext(ctx):
     h = ctypes.c_void_p(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx)
     _ck(lib().hvxReleaseContext(ctypes.byref(h)), "hvxReleaseContext")
+
+
+def hvxSelfTestBoundedWait(ctx) -> int:
+    """Status of the bounded-wait self-test (HVX_ERROR_TIMEOUT is the expected one)."""
+    return lib().hvxSelfTestBoundedWait(ctx)
 
 
 def hvxSetContextMemoryBudget(ctx, nbytes: int):

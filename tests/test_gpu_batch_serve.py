@@ -164,3 +164,37 @@ def test_image_from_torch_tensor_and_swap(ctx):
     H.hvxSwapImageHandle(inp, tb.data_ptr(), pitch)  # next frame, graph stays verified
     H.hvxProcessGraph(g)
     np.testing.assert_array_equal(to[:, :w].cpu().numpy(), O.gaussian3x3(b).data)
+
+
+def test_bench_configuration_64_frames_1080p(ctx):
+    """The launch configuration bench.py times: 64 frames of 1920x1080 in one
+    batched persistent launch; sampled frames (first, middle, last, each with
+    its own content) are compared whole with the oracle."""
+    F, w, h = 64, 1920, 1080
+    distinct = [synth.rects_noise(w, h, seed=2 + i) for i in range(8)]
+    graphs, outs = [], []
+    for i in range(F):
+        inp = PG.upload(ctx, distinct[i % 8], H.HVX_DF_U8)
+        ph, mk = PG.empty(ctx, w, h, H.HVX_DF_U8), PG.empty(ctx, w, h, H.HVX_DF_U8)
+        graphs.append(PG.edge_graph(ctx, inp, ph, mk))
+        outs.append((ph, mk))
+    for _ in range(2):
+        H.hvxProcessGraphBatch(graphs)
+    H.hvxWaitBatch(ctx)
+    for i in (0, 5, 31, 63):
+        rp, rm = O.edge_graph(distinct[i % 8])
+        np.testing.assert_array_equal(PG.download(outs[i][0]), rp)
+        np.testing.assert_array_equal(PG.download(outs[i][1]), rm)
+    for g in graphs:
+        H.hvxReleaseGraph(g)
+
+
+def test_device_bounded_wait_reports_timeout_and_context_survives(ctx):
+    assert H.hvxSelfTestBoundedWait(ctx) == H.HVX_ERROR_TIMEOUT
+    # the error word was cleared when it was read, and work still runs
+    img = synth.uniform_u8(100, 50, 3)
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    out = PG.empty(ctx, 100, 50, H.HVX_DF_U8)
+    g = PG.gaussian_graph(ctx, inp, out)
+    H.hvxProcessGraph(g)
+    np.testing.assert_array_equal(PG.download(out), O.gaussian3x3(img).data)
