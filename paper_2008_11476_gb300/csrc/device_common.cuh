@@ -261,5 +261,33 @@ __device__ __forceinline__ int32_t eval_point(const P& st, int32_t a, int32_t b,
     return 0;
 }
 
+// Calls f(r, c) for every cell (r, c) of an R x C box whose top-left cell is
+// image pixel (bx, by) and that lies outside the W x H image: the full rows
+// above and below the image, then the left / right strips of the rows in
+// between, spread over the CTA's threads.
+template <class F>
+__device__ __forceinline__ void for_each_outside(int R, int C, int bx, int by, int W, int H, F f) {
+    const int cl = clampi(-bx, 0, C), cr = max(cl, clampi(W - bx, 0, C));
+    const int rt = clampi(-by, 0, R), rb = max(rt, clampi(H - by, 0, R));
+    const int nfull = (rt + (R - rb)) * C;
+    const int side = cl + (C - cr);
+    const int n = nfull + (rb - rt) * side;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int r, c;
+        if (i < nfull) {
+            int rr = i / C;
+            c = i - rr * C;
+            r = rr < rt ? rr : rb + (rr - rt);
+        } else {
+            int j = i - nfull;
+            int rr = j / side;
+            int k = j - rr * side;
+            r = rt + rr;
+            c = k < cl ? k : cr + (k - cl);
+        }
+        f(r, c);
+    }
+}
+
 }  // namespace dev
 }  // namespace hvx

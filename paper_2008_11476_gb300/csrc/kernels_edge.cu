@@ -86,11 +86,18 @@ __device__ __forceinline__ bool rect_is_full(const int32_t* r, const EdgeParams&
     return r[0] == 0 && r[1] == 0 && r[2] == (int)p.W && r[3] == (int)p.H;
 }
 
+// Hardware reciprocal approximation (rcp.approx.ftz.f32, at most 1 ulp off).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Phase (see device_common.cuh: phase_u8) from exact binary32 gradients.
 __device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
     float ax = fabsf(gx), ay = fabsf(gy);
     float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    float t = mn * rcp_approx(fmaxf(mx, 1.0f));  // integers: mx = 0 only when mn = 0
     float u = t * t;
     float pp = 0.27753710746765137f;
     pp = fmaf(pp, u, -1.3691582679748535f);
@@ -121,18 +128,12 @@ __device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
 __device__ void fix_input_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
-    for (int i = threadIdx.x; i < IN_ROWS * LW; i += blockDim.x) {
-        int r = i / LW, c = i - r * LW;
+    const bool cst = p.border_g == HVX_BORDER_CONSTANT;
+    const uint8_t cv = (uint8_t)p.cval_g;
+    for_each_outside(IN_ROWS, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
         int x = x0 - 16 + c, y = y0 - 2 + r;
-        if (x >= 0 && x < W && y >= 0 && y < H) continue;
-        uint8_t v;
-        if (p.border_g == HVX_BORDER_CONSTANT) {
-            v = (uint8_t)p.cval_g;
-        } else {
-            v = sm.in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
-        }
-        sm.in[r][c] = v;
-    }
+        sm.in[r][c] = cst ? cv : sm.in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
+    });
 }
 
 // ---- stage 2: Gaussian in 16-bit lanes ---------------------------------------------
@@ -180,8 +181,7 @@ __device__ void gaussian_stage(EdgeSmem& sm, const EdgeParams& p) {
 // Sobel's border mode outside the image.  Edge tiles only.
 __device__ void fix_g_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
-    constexpr int COLS = TW + 2;  // k = 7 .. 136
-    // pass 1: valid region of G
+    constexpr int COLS = TW + 2;  // k = 7 .. 136, x = x0 - 1 .. x0 + 128
     if (!rect_is_full(p.gvalid, p)) {
         for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
             int r = i / COLS, k = 7 + (i - r * COLS);
@@ -191,17 +191,13 @@ __device__ void fix_g_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) 
         __syncthreads();
     }
     if (p.border_s == HVX_BORDER_UNDEFINED) return;
-    for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
-        int r = i / COLS, k = 7 + (i - r * COLS);
-        int x = x0 - 8 + k, y = y0 - 1 + r;
-        if (x >= 0 && x < W && y >= 0 && y < H) continue;
-        uint16_t v;
-        if (p.border_s == HVX_BORDER_CONSTANT)
-            v = (uint16_t)(p.cval_s & 0xFF);
-        else
-            v = sm.g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
-        sm.g[r][k] = v;
-    }
+    const bool cst = p.border_s == HVX_BORDER_CONSTANT;
+    const uint16_t cv = (uint16_t)(p.cval_s & 0xFF);
+    for_each_outside(G_ROWS, COLS, x0 - 1, y0 - 1, W, H, [&](int r, int c) {
+        int x = x0 - 1 + c, y = y0 - 1 + r;
+        sm.g[r][7 + c] =
+            cst ? cv : sm.g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
+    });
 }
 
 // ---- stage 3: Sobel + point operators ------------------------------------------------

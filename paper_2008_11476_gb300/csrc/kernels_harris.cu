@@ -6,14 +6,23 @@
 //        --point--> R = Sxx Syy - Sxy^2 - k (Sxx + Syy)^2 (F32)
 //        --Threshold--> mask (U8)
 //
-// One CTA computes a 64 x 32 output tile: a TMA box of the input with a
-// 3-pixel halo, the three products over the tile + 2-pixel halo into shared
-// memory (exact int32), their vertical 5-sums into shared memory, then per
-// thread 8 pixels of horizontal 5-sums, the response in exact 64-bit integer
-// form q = kd * R and the threshold.  R > T on the binary32 value is decided
-// as q > q_thr, where the host computed q_thr so that this equals the
-// comparison of the correctly rounded binary32 response with T.  When R is
-// exported it is rounded once from q / kd.
+// One CTA computes a 64 x 32 output tile from a TMA box of the input with a
+// 3-pixel halo:
+//   1. edge tiles apply the Sobel's border mode to the input bytes outside
+//      the image;
+//   2. items of 4 pixels of one row compute gx, gy with separable sums and
+//      store the three exact int32 products (16-byte stores) over the tile +
+//      2-pixel halo;
+//   3. edge tiles apply the window sums' border mode to the product cells
+//      outside the image;
+//   4. vertical 5-sums, 4 columns x 8 rows per item, sliding, 16-byte loads
+//      and stores;
+//   5. each thread takes 8 pixels of one row: horizontal 5-sums from three
+//      16-byte loads per product, the response in exact 64-bit integer form
+//      q = kd * R and the threshold.  R > T on the binary32 value is decided
+//      as q > q_thr, where the host computed q_thr so that this equals the
+//      comparison of the correctly rounded binary32 response with T.  When R
+//      is exported it is rounded once from q / kd.
 #include "device_common.cuh"
 #include "launchers.h"
 
@@ -22,18 +31,19 @@ namespace {
 
 using namespace dev;
 
-constexpr int TW = HARRIS_TW;
-constexpr int TH = HARRIS_TH;
-constexpr int LW = HARRIS_LOAD_W;     // 96
-constexpr int IN_ROWS = TH + 6;       // 38
-constexpr int PR = TH + 4;            // product rows (y0-2 .. y0+TH+1)
-constexpr int PC = TW + 4;            // product cols (x0-2 .. x0+TW+1)
+constexpr int TW = HARRIS_TW;     // 64
+constexpr int TH = HARRIS_TH;     // 32
+constexpr int LW = HARRIS_LOAD_W; // 96
+constexpr int IN_ROWS = TH + 6;   // 38
+constexpr int PR = TH + 4;        // product rows (y0-2 .. y0+TH+1)
+constexpr int PC = TW + 4;        // product cols (x0-2 .. x0+TW+1) = 68
+constexpr int PCS = TW + 8;       // product row stride (16-byte multiple)
 constexpr uint32_t IN_BYTES = IN_ROWS * LW;
 
 struct HarrisSmem {
     alignas(128) uint8_t in[IN_ROWS][LW];  // image (x0 - 16 + c, y0 - 3 + r)
-    alignas(16) int32_t p[3][PR][PC];      // products (x0 - 2 + c, y0 - 2 + r)
-    alignas(16) int32_t v[3][TH][PC];      // vertical 5-sums (x0 - 2 + c, y0 + r)
+    alignas(16) int32_t p[3][PR][PCS];     // products (x0 - 2 + c, y0 - 2 + r)
+    alignas(16) int32_t v[3][TH][PCS];     // vertical 5-sums (x0 - 2 + c, y0 + r)
     alignas(8) uint64_t bar;
 };
 
@@ -43,6 +53,13 @@ __device__ __forceinline__ bool interior_tile(const HarrisParams& p, int x0, int
 
 __device__ __forceinline__ bool full_rect(const int32_t* r, const HarrisParams& p) {
     return r[0] == 0 && r[1] == 0 && r[2] == (int)p.W && r[3] == (int)p.H;
+}
+
+__device__ __forceinline__ int4 add4(int4 a, int4 b) {
+    return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ int4 sub4(int4 a, int4 b) {
+    return make_int4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
 __global__ void __launch_bounds__(HARRIS_THREADS, 3)
@@ -65,47 +82,63 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
 
     // 1. the Sobel's border mode on input bytes outside the image
     if (!interior && p.border_s != HVX_BORDER_UNDEFINED) {
-        for (int i = threadIdx.x; i < IN_ROWS * LW; i += blockDim.x) {
-            int r = i / LW, c = i - r * LW;
+        const bool cst = p.border_s == HVX_BORDER_CONSTANT;
+        const uint8_t cv = (uint8_t)p.cval_s;
+        for_each_outside(IN_ROWS, LW, x0 - 16, y0 - 3, W, H, [&](int r, int c) {
             int x = x0 - 16 + c, y = y0 - 3 + r;
-            if (x >= 0 && x < W && y >= 0 && y < H) continue;
-            uint8_t val;
-            if (p.border_s == HVX_BORDER_CONSTANT)
-                val = (uint8_t)p.cval_s;
-            else
-                val = sm.in[clampi(y, 0, H - 1) - (y0 - 3)][clampi(x, 0, W - 1) - (x0 - 16)];
-            sm.in[r][c] = val;
-        }
+            sm.in[r][c] =
+                cst ? cv : sm.in[clampi(y, 0, H - 1) - (y0 - 3)][clampi(x, 0, W - 1) - (x0 - 16)];
+        });
         __syncthreads();
     }
 
-    // 2. gx, gy and their products over the tile + 2-pixel halo
+    // 2. gx, gy and their products over the tile + 2-pixel halo, 4 pixels per item
     const bool pfull = interior || full_rect(p.pvalid, p);
-    for (int i = threadIdx.x; i < PR * PC; i += blockDim.x) {
-        int r = i / PC, c = i - r * PC;
-        // input rows r .. r+2, columns c+13 .. c+15 hold the 3x3 window
-        const uint8_t* a = &sm.in[r][c + 13];
-        const uint8_t* b = &sm.in[r + 1][c + 13];
-        const uint8_t* d = &sm.in[r + 2][c + 13];
-        int gx = (a[2] - a[0]) + 2 * (b[2] - b[0]) + (d[2] - d[0]);
-        int gy = (d[0] + 2 * d[1] + d[2]) - (a[0] + 2 * a[1] + a[2]);
-        if (!pfull) {
-            int x = x0 - 2 + c, y = y0 - 2 + r;
-            if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.pvalid, x, y)) gx = gy = 0;
+    constexpr int CHUNKS = PC / 4;  // 17
+    for (int it = threadIdx.x; it < PR * CHUNKS; it += blockDim.x) {
+        const int r = it / CHUNKS, c = 4 * (it - r * CHUNKS);
+        // input rows r .. r+2; columns c+13 .. c+18 hold the windows of the 4 pixels
+        int vs[6], dy[6];
+        uint32_t w0[3][2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            w0[d][0] = *reinterpret_cast<const uint32_t*>(&sm.in[r + d][c + 12]);
+            w0[d][1] = *reinterpret_cast<const uint32_t*>(&sm.in[r + d][c + 16]);
         }
-        sm.p[0][r][c] = gx * gx;
-        sm.p[1][r][c] = gy * gy;
-        sm.p[2][r][c] = gx * gy;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            // byte c+13+k: word (k+1) >> 2, byte (k+1) & 3
+            const int wi = (k + 1) >> 2, sh = 8 * ((k + 1) & 3);
+            int a = (w0[0][wi] >> sh) & 0xFF, b = (w0[1][wi] >> sh) & 0xFF,
+                e = (w0[2][wi] >> sh) & 0xFF;
+            vs[k] = a + 2 * b + e;
+            dy[k] = e - a;
+        }
+        int px[4], py[4], pxy[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gx = vs[j + 2] - vs[j];
+            int gy = dy[j] + 2 * dy[j + 1] + dy[j + 2];
+            if (!pfull) {
+                int x = x0 - 2 + c + j, y = y0 - 2 + r;
+                if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.pvalid, x, y)) gx = gy = 0;
+            }
+            px[j] = gx * gx;
+            py[j] = gy * gy;
+            pxy[j] = gx * gy;
+        }
+        *reinterpret_cast<int4*>(&sm.p[0][r][c]) = make_int4(px[0], px[1], px[2], px[3]);
+        *reinterpret_cast<int4*>(&sm.p[1][r][c]) = make_int4(py[0], py[1], py[2], py[3]);
+        *reinterpret_cast<int4*>(&sm.p[2][r][c]) = make_int4(pxy[0], pxy[1], pxy[2], pxy[3]);
     }
     __syncthreads();
 
     // 3. the window sums' border mode on product cells outside the image
     if (!interior && p.border_b != HVX_BORDER_UNDEFINED) {
-        for (int i = threadIdx.x; i < PR * PC; i += blockDim.x) {
-            int r = i / PC, c = i - r * PC;
+        const bool cst = p.border_b == HVX_BORDER_CONSTANT;
+        for_each_outside(PR, PC, x0 - 2, y0 - 2, W, H, [&](int r, int c) {
             int x = x0 - 2 + c, y = y0 - 2 + r;
-            if (x >= 0 && x < W && y >= 0 && y < H) continue;
-            if (p.border_b == HVX_BORDER_CONSTANT) {
+            if (cst) {
                 sm.p[0][r][c] = sm.p[1][r][c] = sm.p[2][r][c] = p.cval_b;
             } else {
                 int cr = clampi(y, 0, H - 1) - (y0 - 2), cc = clampi(x, 0, W - 1) - (x0 - 2);
@@ -113,23 +146,28 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
                 sm.p[1][r][c] = sm.p[1][cr][cc];
                 sm.p[2][r][c] = sm.p[2][cr][cc];
             }
-        }
+        });
         __syncthreads();
     }
 
-    // 4. vertical 5-sums: one column of 8 rows per item
-    for (int i = threadIdx.x; i < 3 * PC * (TH / 8); i += blockDim.x) {
-        int k = i / (PC * (TH / 8));
-        int rem = i - k * PC * (TH / 8);
-        int c = rem % PC;
-        int r0 = (rem / PC) * 8;
-        int s = sm.p[k][r0][c] + sm.p[k][r0 + 1][c] + sm.p[k][r0 + 2][c] + sm.p[k][r0 + 3][c] +
-                sm.p[k][r0 + 4][c];
-        sm.v[k][r0][c] = s;
+    // 4. vertical 5-sums: 4 columns x 8 rows per item, sliding
+    for (int it = threadIdx.x; it < 3 * CHUNKS * (TH / 8); it += blockDim.x) {
+        const int k = it / (CHUNKS * (TH / 8));
+        const int rem = it - k * CHUNKS * (TH / 8);
+        const int c = 4 * (rem % CHUNKS);
+        const int r0 = 8 * (rem / CHUNKS);
+        const int32_t(*P)[PCS] = sm.p[k];
+        int4 s = add4(add4(*reinterpret_cast<const int4*>(&P[r0][c]),
+                           *reinterpret_cast<const int4*>(&P[r0 + 1][c])),
+                      add4(add4(*reinterpret_cast<const int4*>(&P[r0 + 2][c]),
+                                *reinterpret_cast<const int4*>(&P[r0 + 3][c])),
+                           *reinterpret_cast<const int4*>(&P[r0 + 4][c])));
+        *reinterpret_cast<int4*>(&sm.v[k][r0][c]) = s;
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
-            s += sm.p[k][r0 + j + 4][c] - sm.p[k][r0 + j - 1][c];
-            sm.v[k][r0 + j][c] = s;
+            s = sub4(add4(s, *reinterpret_cast<const int4*>(&P[r0 + j + 4][c])),
+                     *reinterpret_cast<const int4*>(&P[r0 + j - 1][c]));
+            *reinterpret_cast<int4*>(&sm.v[k][r0 + j][c]) = s;
         }
     }
     __syncthreads();
@@ -142,12 +180,14 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
     int S[3][8];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int32_t* vr = &sm.v[k][row][seg * 8];
-        int s = vr[0] + vr[1] + vr[2] + vr[3] + vr[4];
+        const int4* vr = reinterpret_cast<const int4*>(&sm.v[k][row][seg * 8]);
+        int4 a = vr[0], b = vr[1], c = vr[2];
+        int v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        int s = v[0] + v[1] + v[2] + v[3] + v[4];
         S[k][0] = s;
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
-            s += vr[j + 4] - vr[j - 1];
+            s += v[j + 4] - v[j - 1];
             S[k][j] = s;
         }
     }

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
@@ -623,6 +624,9 @@ int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode
             best = grid;
         }
         cudaGetLastError();
+        if (std::getenv("HVX_AUTOTUNE_VERBOSE"))
+            std::fprintf(stderr, "hvx autotune: %d tiles, grid %d (%d CTAs/SM): %.4f ms\n",
+                         d.total_tiles, grid, per, ms / 2);
         if (grid == d.total_tiles) break;  // more CTAs than tiles change nothing
     }
     cudaEventDestroy(a);
