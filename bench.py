@@ -18,6 +18,7 @@ the host (cpu_baseline); SM clocks sampled during the timed region.
 --impl reference times the CPU oracle on the same metric (the reference arm).
 --workload gauss | harris | batch | serve measure the other workloads:
   gauss   Gaussian3x3 on one 640x480 U8 image per step (launch latency bound)
+  gauss-batch  Gaussian3x3 on --frames 1920x1080 frames per step, one launch
   harris  Harris graph on 4096x2160 U8, BORDER_UNDEFINED, 16 frames per step
   batch   256 images of uneven sizes (w 320..3840, h 240..2160) through the
           edge graph in one autotuned persistent launch, vs 256 unfused runs
@@ -55,7 +56,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=64)
     ap.add_argument("--workload", default="edge",
-                    choices=["edge", "gauss", "harris", "batch", "serve"])
+                    choices=["edge", "gauss", "gauss-batch", "harris", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -297,22 +298,47 @@ def run_edge(args, world, rank, local, torch):
     barrier(world, torch)
     t_plain = reduce_max(time_steps(torch, step_plain, plain_steps, stream), world, torch)
 
-    # end to end: pinned host frames in, outputs back, around the same C ABI call
+    # end to end: every step copies its frames in from pinned host memory, runs
+    # the fused batch through the C ABI and reads both outputs back.  The step
+    # is cut into chunks of frames that flow through three streams (copy in ->
+    # hvxProcessGraphBatch -> copy out), so host<->device copies in both
+    # directions overlap the kernels of neighbouring chunks.
     h_in = torch.empty((F, H_, pitch), dtype=torch.uint8).pin_memory()
     h_in.copy_(t_in.cpu())
     h_ph = torch.empty_like(h_in).pin_memory()
     h_mk = torch.empty_like(h_in).pin_memory()
+    chunk = max(1, F // 8)
+    chunks = [(i, min(F, i + chunk)) for i in range(0, F, chunk)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    sub = [fused[a:b] for a, b in chunks]
 
     def step_e2e():
-        t_in.copy_(h_in, non_blocking=True)
-        H.hvxProcessGraphBatch(fused, sh)
-        h_ph.copy_(t_ph, non_blocking=True)
-        h_mk.copy_(t_mk, non_blocking=True)
+        done_out = []
+        s_in.wait_stream(stream)  # the previous step has released the device frames
+        for (a, b), gs in zip(chunks, sub):
+            with torch.cuda.stream(s_in):
+                t_in[a:b].copy_(h_in[a:b], non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            H.hvxProcessGraphBatch(gs, sh)
+            ev_k = torch.cuda.Event()
+            ev_k.record(stream)
+            s_out.wait_event(ev_k)
+            with torch.cuda.stream(s_out):
+                h_ph[a:b].copy_(t_ph[a:b], non_blocking=True)
+                h_mk[a:b].copy_(t_mk[a:b], non_blocking=True)
+                ev_o = torch.cuda.Event()
+                ev_o.record(s_out)
+            done_out.append(ev_o)
+        for ev in done_out:  # the step ends when its last result is on the host
+            stream.wait_event(ev)
 
     e2e_steps = max(2, min(args.steps, 40) // 4)
     step_e2e()
     barrier(world, torch)
     t_e2e = reduce_max(time_steps(torch, step_e2e, e2e_steps, stream), world, torch)
+    assert (h_mk[F - 1].numpy() == t_mk[F - 1].cpu().numpy()).all()
     H.hvxWaitBatch(ctx, sh)  # surfaces any device-side error
 
     serving = None
@@ -485,6 +511,52 @@ def run_gauss(args, world, rank, local, torch):
                           "gpu_launches": args.steps, "clocks": clocks}), flush=True)
 
 
+def run_gauss_batch(args, world, rank, local, torch):
+    """Gaussian3x3 alone on --frames 1920x1080 frames per step, one batched
+    launch: the HBM roofline of the Gaussian kernel (2 B/px)."""
+    from paper_2008_11476_gb300 import graphs as PG
+    from paper_2008_11476_gb300 import hvx as H
+    from paper_2008_11476_gb300 import synth
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = H.hvxCreateContext()
+    F = args.frames
+    distinct = [synth.uniform_u8(W, H_, seed=1 + i) for i in range(min(F, 8))]
+    t_in, ins = wrap_frames(ctx, torch, H, [distinct[i % len(distinct)] for i in range(F)], W, H_, W)
+    t_o, outs = empty_frames(ctx, torch, H, F, W, H_, W)
+    graphs = [PG.gaussian_graph(ctx, a, o) for a, o in zip(ins, outs)]
+    assert PG.kernel_kinds(graphs[0]) == ["gaussian3x3_tma"]
+
+    def step():
+        H.hvxProcessGraphBatch(graphs, sh)
+
+    step()
+    for _ in range(args.warmup):
+        step()
+    barrier(world, torch)
+    t, clocks = timed_with_clocks(torch, step, args.steps, stream, local)
+    t = reduce_max(t, world, torch)
+    H.hvxWaitBatch(ctx, sh)
+    H.hvxReleaseContext(ctx)
+    if rank == 0:
+        peaks, src = measured_peaks()
+        ext = 2 * W * H_ * F
+        ach = ext / (t / args.steps) / 1e9
+        print(json.dumps({
+            "metric": "Gaussian3x3 Mpix/s (batched 1920x1080 frames)",
+            "value": round(W * H_ * F / 1e6 * args.steps / t * world, 1), "unit": "Mpix/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic (uniform bytes)",
+            "config": {"workload": f"Gaussian3x3 1920x1080 U8 BORDER_REPLICATE, {F} frames per "
+                                   "step in one persistent launch", "l2": "larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs"),
+                         "unit": "GB/s", "frac": round(ach / peaks.get("hbm_gbs", 6800), 4),
+                         "peak_source": src, "kernel": "edge_batch_kernel<0>",
+                         "algorithmic_bytes_per_launch": ext},
+            "gpu_launches": args.steps, "clocks": clocks}), flush=True)
+
+
 def run_harris(args, world, rank, local, torch):
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
@@ -644,8 +716,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    fn = {"edge": run_edge, "gauss": run_gauss, "harris": run_harris, "batch": run_batch,
-          "serve": run_serve}[args.workload]
+    fn = {"edge": run_edge, "gauss": run_gauss, "gauss-batch": run_gauss_batch,
+          "harris": run_harris, "batch": run_batch, "serve": run_serve}[args.workload]
     fn(args, world, rank, local, torch)
     if world > 1:
         import torch.distributed as dist

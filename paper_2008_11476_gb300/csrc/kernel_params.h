@@ -87,6 +87,7 @@ constexpr int EDGE_TW = 128;  // output tile width (bytes of U8)
 constexpr int EDGE_TH = 30;   // output tile height (1080 = 36 x 30, 2160 = 72 x 30)
 constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_LOAD_W = EDGE_TW + 32;  // TMA box width: 16 B aligned both sides
+constexpr int EDGE_STAGES = 3;             // input boxes in flight per persistent CTA
 
 struct EdgeParams {
     uint32_t W, H;

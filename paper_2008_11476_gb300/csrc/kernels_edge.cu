@@ -49,12 +49,21 @@ constexpr int M_MASK = 2;       // binary threshold mask only
 constexpr int M_PHASE = 3;      // phase only
 constexpr int M_GENERAL = 4;    // any outputs (magnitude export, range threshold)
 
+constexpr int STAGES = EDGE_STAGES;     // input boxes in flight per CTA (batch kernel)
+
+using InTile = uint8_t[IN_ROWS][LW];    // image (x0 - 16 + c, y0 - 2 + r)
+using GTile = uint16_t[G_ROWS][GW];     // Gaussian (x0 - 8 + k, y0 - 1 + r)
+
+struct alignas(128) InStage {
+    InTile b;
+};
+
+template <int NS>
 struct EdgeSmem {
-    alignas(128) uint8_t in[IN_ROWS][LW];  // image (x0 - 16 + c, y0 - 2 + r)
-    alignas(16) uint16_t g[G_ROWS][GW];    // Gaussian (x0 - 8 + k, y0 - 1 + r)
-    alignas(8) uint64_t bar;
-    int img;                               // batch: image of the current tile
-    int next_img;
+    InStage in[NS];                     // ring of TMA destinations
+    alignas(16) GTile g;
+    alignas(8) uint64_t bar[NS];
+    int img[NS];                        // batch: image of the tile in each stage
 };
 
 // 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
@@ -125,21 +134,21 @@ __device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
 
 // ---- stage 1: input border -------------------------------------------------------
 
-__device__ void fix_input_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
+__device__ void fix_input_border(InTile& in, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
     const bool cst = p.border_g == HVX_BORDER_CONSTANT;
     const uint8_t cv = (uint8_t)p.cval_g;
     for_each_outside(IN_ROWS, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
         int x = x0 - 16 + c, y = y0 - 2 + r;
-        sm.in[r][c] = cst ? cv : sm.in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
+        in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
     });
 }
 
 // ---- stage 2: Gaussian in 16-bit lanes ---------------------------------------------
 // Item (r, q): G row r (y = y0 - 1 + r), pixels x = x0 + 8q .. x0 + 8q + 7;
 // group 0 also produces x0 - 1 and group 15 also x0 + 128.
-__device__ void gaussian_stage(EdgeSmem& sm, const EdgeParams& p) {
+__device__ void gaussian_stage(const InTile& in, GTile& g, const EdgeParams& p) {
     const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
     for (int it = threadIdx.x; it < G_ROWS * 16; it += blockDim.x) {
         const int r = it >> 4, q = it & 15;
@@ -147,7 +156,7 @@ __device__ void gaussian_stage(EdgeSmem& sm, const EdgeParams& p) {
         uint32_t V[6];  // vertical sums of pixel pairs (x-2,x-1), (x,x+1) .. (x+8,x+9)
 #pragma unroll
         for (int dr = 0; dr < 3; ++dr) {
-            const uint8_t* row = sm.in[r + dr];
+            const uint8_t* row = in[r + dr];
             uint2 m = *reinterpret_cast<const uint2*>(row + c);
             uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
             uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
@@ -162,31 +171,31 @@ __device__ void gaussian_stage(EdgeSmem& sm, const EdgeParams& p) {
             uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
             Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
         }
-        *reinterpret_cast<uint4*>(&sm.g[r][8 + 8 * q]) = make_uint4(Gp[0], Gp[1], Gp[2], Gp[3]);
+        *reinterpret_cast<uint4*>(&g[r][8 + 8 * q]) = make_uint4(Gp[0], Gp[1], Gp[2], Gp[3]);
         // The two halo columns, each written as a word together with the column
         // beyond it set to 0: stage 3 reads those outer lanes (cols 6, 137)
         // as part of its pair loads, and a zero lane cannot carry into its
         // neighbour in the 16-bit-lane arithmetic.
         if (q == 0) {  // x0 - 1 = V lane (x-2) + 2 (x-1) + (x)
             uint32_t s = (V[0] & 0xFFFFu) + 2u * (V[0] >> 16) + (V[1] & 0xFFFFu) + (rnd & 0xFFFFu);
-            *reinterpret_cast<uint32_t*>(&sm.g[r][6]) = (s >> 4) << 16;
+            *reinterpret_cast<uint32_t*>(&g[r][6]) = (s >> 4) << 16;
         } else if (q == 15) {  // x0 + 128 = (x+7) + 2 (x+8) + (x+9), x = x0 + 120
             uint32_t s = (V[4] >> 16) + 2u * (V[5] & 0xFFFFu) + (V[5] >> 16) + (rnd & 0xFFFFu);
-            *reinterpret_cast<uint32_t*>(&sm.g[r][136]) = s >> 4;
+            *reinterpret_cast<uint32_t*>(&g[r][136]) = s >> 4;
         }
     }
 }
 
 // G cells: zero inside the image but outside the Gaussian's valid region; the
 // Sobel's border mode outside the image.  Edge tiles only.
-__device__ void fix_g_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) {
+__device__ void fix_g_border(GTile& g, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
     constexpr int COLS = TW + 2;  // k = 7 .. 136, x = x0 - 1 .. x0 + 128
     if (!rect_is_full(p.gvalid, p)) {
         for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
             int r = i / COLS, k = 7 + (i - r * COLS);
             int x = x0 - 8 + k, y = y0 - 1 + r;
-            if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.gvalid, x, y)) sm.g[r][k] = 0;
+            if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.gvalid, x, y)) g[r][k] = 0;
         }
         __syncthreads();
     }
@@ -195,8 +204,8 @@ __device__ void fix_g_border(EdgeSmem& sm, const EdgeParams& p, int x0, int y0) 
     const uint16_t cv = (uint16_t)(p.cval_s & 0xFF);
     for_each_outside(G_ROWS, COLS, x0 - 1, y0 - 1, W, H, [&](int r, int c) {
         int x = x0 - 1 + c, y = y0 - 1 + r;
-        sm.g[r][7 + c] =
-            cst ? cv : sm.g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
+        g[r][7 + c] =
+            cst ? cv : g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
     });
 }
 
@@ -222,7 +231,7 @@ __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint
 }
 
 template <int MODE>
-__device__ void sobel_point_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
+__device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, int y0,
                                   bool interior) {
     const float s_thr = (float)p.s_thr;
     const bool full = interior || rect_is_full(p.valid, p);
@@ -233,9 +242,9 @@ __device__ void sobel_point_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int
         if (y >= (int)p.H || x >= (int)p.W) continue;
         const int k = 8 + 8 * s8;
         uint32_t A[6], B[6], C[6];
-        load_g_row(sm.g[r], k, A);
-        load_g_row(sm.g[r + 1], k, B);
-        load_g_row(sm.g[r + 2], k, C);
+        load_g_row(g[r], k, A);
+        load_g_row(g[r + 1], k, B);
+        load_g_row(g[r + 2], k, C);
         uint32_t vs[6], dy[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
@@ -311,7 +320,7 @@ __device__ void sobel_point_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int
 }
 
 // Gaussian3x3 alone: G rows y0 .. y0+TH-1 from shared memory to the output.
-__device__ void gaussian_out_stage(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
+__device__ void gaussian_out_stage(const GTile& g, const EdgeParams& p, int x0, int y0,
                                    bool interior) {
     const bool full = interior || rect_is_full(p.gvalid, p);
 #pragma unroll 1
@@ -319,7 +328,7 @@ __device__ void gaussian_out_stage(EdgeSmem& sm, const EdgeParams& p, int x0, in
         const int r = it >> 4, q = it & 15;
         const int y = y0 + r, x = x0 + 8 * q;
         if (y >= (int)p.H || x >= (int)p.W) continue;
-        uint4 m = *reinterpret_cast<const uint4*>(&sm.g[r + 1][8 + 8 * q]);
+        uint4 m = *reinterpret_cast<const uint4*>(&g[r + 1][8 + 8 * q]);
         uint32_t b[8] = {m.x & 0xFFu, m.x >> 16, m.y & 0xFFu, m.y >> 16,
                          m.z & 0xFFu, m.z >> 16, m.w & 0xFFu, m.w >> 16};
         if (!full)
@@ -329,51 +338,50 @@ __device__ void gaussian_out_stage(EdgeSmem& sm, const EdgeParams& p, int x0, in
     }
 }
 
-__device__ __forceinline__ void issue_load(EdgeSmem& sm, const CUtensorMap* map, int x0, int y0) {
-    mbar_arrive_expect_tx(&sm.bar, IN_BYTES);
-    tma_load_2d(&sm.in[0][0], map, &sm.bar, x0 - 16, y0 - 2);
-}
-
-// One tile after its input box has landed in sm.in.  If next_map is set,
-// thread 0 starts the next tile's load as soon as sm.in is no longer read.
-template <int MODE>
-__device__ void edge_tile_body(EdgeSmem& sm, const EdgeParams& p, int x0, int y0,
-                               const CUtensorMap* next_map, int nx0, int ny0) {
+// One tile after its input box has landed in `in`.  `prefetch` runs on
+// thread 0 as soon as `in` is no longer read (after the Gaussian stage), so
+// that the box can be refilled while the rest of the tile is computed.
+template <int MODE, class Prefetch>
+__device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0, int y0,
+                               Prefetch prefetch) {
     const bool interior = tile_is_interior(p, x0, y0);
     if (!interior) {
-        fix_input_border(sm, p, x0, y0);
+        fix_input_border(in, p, x0, y0);
         __syncthreads();
     }
-    gaussian_stage(sm, p);
+    gaussian_stage(in, g, p);
     __syncthreads();
-    if (next_map && threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        issue_load(sm, next_map, nx0, ny0);
-    }
+    if (threadIdx.x == 0) prefetch();
     if (!interior) {
-        fix_g_border(sm, p, x0, y0);
+        fix_g_border(g, p, x0, y0);
         __syncthreads();
     }
     if (MODE == M_GAUSS)
-        gaussian_out_stage(sm, p, x0, y0, interior);
+        gaussian_out_stage(g, p, x0, y0, interior);
     else
-        sobel_point_stage<MODE>(sm, p, x0, y0, interior);
+        sobel_point_stage<MODE>(g, p, x0, y0, interior);
     __syncthreads();
 }
 
+__device__ __forceinline__ void issue_box(InTile& in, uint64_t* bar, const CUtensorMap* map, int x0,
+                                          int y0) {
+    mbar_arrive_expect_tx(bar, IN_BYTES);
+    tma_load_2d(&in[0][0], map, bar, x0 - 16, y0 - 2);
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(EDGE_THREADS, 3)
+__global__ void __launch_bounds__(EDGE_THREADS, 4)
     edge_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
-    __shared__ EdgeSmem sm;
+    __shared__ EdgeSmem<1> sm;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar, 1);
+        mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) issue_load(sm, &tmap, x0, y0);
-    if (!mbar_wait_bounded(&sm.bar, 0, p.err)) return;
-    edge_tile_body<MODE>(sm, p, x0, y0, nullptr, 0, 0);
+    if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
+    if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
+    edge_tile_body<MODE>(sm.in[0].b, sm.g, p, x0, y0, [] {});
 }
 
 __device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
@@ -395,44 +403,51 @@ __device__ __forceinline__ void tile_origin(const EdgeParams& p, int t, int& x0,
     y0 = ty * TH;
 }
 
+// Thread 0: start the TMA load of batch tile t into ring stage s.
+__device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, int s,
+                                           int t) {
+    const int img = find_image(d.tile_start, d.n_img, t);
+    sm.img[s] = img;
+    tensormap_acquire(&d.maps[img]);
+    int x0, y0;
+    tile_origin(d.params[img], t - __ldg(d.tile_start + img), x0, y0);
+    issue_box(sm.in[s].b, &sm.bar[s], &d.maps[img], x0, y0);
+}
+
+// Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
+// CTA lives in ring stage k mod STAGES, so STAGES input boxes are in flight
+// while one is computed.
 template <int MODE>
-__global__ void __launch_bounds__(EDGE_THREADS, 3) edge_batch_kernel(const EdgeBatchDesc d) {
-    __shared__ EdgeSmem sm;
-    int t = blockIdx.x;
-    if (t >= d.total_tiles) return;
+__global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeBatchDesc d) {
+    __shared__ EdgeSmem<STAGES> sm;
+    const int first = blockIdx.x;
+    if (first >= d.total_tiles) return;
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar, 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
         fence_barrier_init();
-        int img = find_image(d.tile_start, d.n_img, t);
-        sm.img = img;
-        tensormap_acquire(&d.maps[img]);
-        int x0, y0;
-        tile_origin(d.params[img], t - d.tile_start[img], x0, y0);
-        issue_load(sm, &d.maps[img], x0, y0);
+        for (int s = 0; s < STAGES; ++s) {
+            const int t = first + s * (int)gridDim.x;
+            if (t < d.total_tiles) issue_tile(sm, d, s, t);
+        }
     }
     __syncthreads();
-    uint32_t parity = 0;
-    for (; t < d.total_tiles; t += gridDim.x) {
-        const int img = sm.img;
+    int k = 0;
+    for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
+        const int s = k % STAGES;
+        const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
+        const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
+        if (__syncthreads_or(!ok)) return;
+        const int img = sm.img[s];
         const EdgeParams& p = d.params[img];
         int x0, y0;
         tile_origin(p, t - __ldg(d.tile_start + img), x0, y0);
-        const int tn = t + gridDim.x;
-        const CUtensorMap* next_map = nullptr;
-        int nx0 = 0, ny0 = 0;
-        if (tn < d.total_tiles && threadIdx.x == 0) {
-            int ni = find_image(d.tile_start, d.n_img, tn);
-            sm.next_img = ni;
-            tensormap_acquire(&d.maps[ni]);
-            tile_origin(d.params[ni], tn - d.tile_start[ni], nx0, ny0);
-            next_map = &d.maps[ni];
-        }
-        bool ok = mbar_wait_bounded(&sm.bar, parity, d.err);
-        if (__syncthreads_or(!ok)) return;
-        parity ^= 1u;
-        edge_tile_body<MODE>(sm, p, x0, y0, next_map, nx0, ny0);
-        if (threadIdx.x == 0) sm.img = sm.next_img;
-        __syncthreads();
+        const int tn = t + STAGES * (int)gridDim.x;  // the next tile of this stage
+        edge_tile_body<MODE>(sm.in[s].b, sm.g, p, x0, y0, [&] {
+            if (tn < d.total_tiles) {
+                fence_proxy_async_smem();
+                issue_tile(sm, d, s, tn);
+            }
+        });
     }
 }
 
