@@ -132,6 +132,15 @@ __device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
     return (uint32_t)q & 255u;
 }
 
+__device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
+    if (x + 8 <= W) {
+        *reinterpret_cast<uint2*>(row + x) =
+            make_uint2(pack4(b[0], b[1], b[2], b[3]), pack4(b[4], b[5], b[6], b[7]));
+    } else {
+        for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (uint8_t)b[j];
+    }
+}
+
 // ---- stage 1: input border -------------------------------------------------------
 
 __device__ void fix_input_border(InTile& in, const EdgeParams& p, int x0, int y0) {
@@ -172,16 +181,74 @@ __device__ void gaussian_stage(const InTile& in, GTile& g, const EdgeParams& p) 
             Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
         }
         *reinterpret_cast<uint4*>(&g[r][8 + 8 * q]) = make_uint4(Gp[0], Gp[1], Gp[2], Gp[3]);
-        // The two halo columns, each written as a word together with the column
-        // beyond it set to 0: stage 3 reads those outer lanes (cols 6, 137)
-        // as part of its pair loads, and a zero lane cannot carry into its
-        // neighbour in the 16-bit-lane arithmetic.
-        if (q == 0) {  // x0 - 1 = V lane (x-2) + 2 (x-1) + (x)
-            uint32_t s = (V[0] & 0xFFFFu) + 2u * (V[0] >> 16) + (V[1] & 0xFFFFu) + (rnd & 0xFFFFu);
-            *reinterpret_cast<uint32_t*>(&g[r][6]) = (s >> 4) << 16;
-        } else if (q == 15) {  // x0 + 128 = (x+7) + 2 (x+8) + (x+9), x = x0 + 120
-            uint32_t s = (V[4] >> 16) + 2u * (V[5] & 0xFFFFu) + (V[5] >> 16) + (rnd & 0xFFFFu);
+    }
+    // The two halo columns x0 - 1 and x0 + 128, one scalar item per row and
+    // side on the first 64 threads (kept out of the loop above, where they
+    // would make every warp diverge).  Each is written as a word together
+    // with the column beyond it set to 0: stage 3 reads those outer lanes
+    // (cols 6, 137) as part of its pair loads, and a zero lane cannot carry
+    // into its neighbour in the 16-bit-lane arithmetic.
+    if (threadIdx.x < 2 * G_ROWS) {
+        const int r = threadIdx.x >> 1, side = threadIdx.x & 1;
+        const int c = side ? 16 + TW : 15;  // input column of the halo pixel
+        uint32_t s = rnd & 0xFFFFu;
+#pragma unroll
+        for (int dr = 0; dr < 3; ++dr) {
+            const uint32_t w = dr == 1 ? 2u : 1u;
+            s += w * (in[r + dr][c - 1] + 2u * in[r + dr][c] + in[r + dr][c + 1]);
+        }
+        if (side)
             *reinterpret_cast<uint32_t*>(&g[r][136]) = s >> 4;
+        else
+            *reinterpret_cast<uint32_t*>(&g[r][6]) = (s >> 4) << 16;
+    }
+}
+
+// Gaussian3x3 alone: 8 output pixels per item straight from the input box in
+// 16-bit lanes, packed to bytes and stored; no shared-memory round trip.
+__device__ void gaussian_direct_stage(const InTile& in, const EdgeParams& p, int x0, int y0,
+                                      bool interior) {
+    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
+    const bool full = interior || rect_is_full(p.gvalid, p);
+#pragma unroll 1
+    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
+        const int r = it >> 4, q = it & 15;
+        const int y = y0 + r, x = x0 + 8 * q;
+        if (y >= (int)p.H || x >= (int)p.W) continue;
+        const int c = 16 + 8 * q;
+        uint32_t V[6];
+#pragma unroll
+        for (int dr = 0; dr < 3; ++dr) {
+            const uint8_t* row = in[r + 1 + dr];
+            uint2 m = *reinterpret_cast<const uint2*>(row + c);
+            uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
+            uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
+            uint32_t P[6] = {hi_pair(wl), lo_pair(m.x), hi_pair(m.x),
+                             lo_pair(m.y), hi_pair(m.y), lo_pair(wr)};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) V[k] = dr == 0 ? P[k] : V[k] + (dr == 1 ? 2u : 1u) * P[k];
+        }
+        uint32_t Gp[4];
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
+            Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
+        }
+        uint8_t* dst = p.gout + (size_t)y * p.gout_pitch;
+        if (full && x + 8 <= (int)p.W) {
+            *reinterpret_cast<uint2*>(dst + x) =
+                make_uint2(__byte_perm(Gp[0], Gp[1], 0x6420), __byte_perm(Gp[2], Gp[3], 0x6420));
+        } else {
+            uint32_t b[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                b[2 * j] = Gp[j] & 0xFFu;
+                b[2 * j + 1] = Gp[j] >> 16;
+            }
+            if (!full)
+                for (int i = 0; i < 8; ++i)
+                    if (!in_rect(p.gvalid, x + i, y)) b[i] = 0;
+            store8_u8(dst, x, p.W, b);
         }
     }
 }
@@ -219,15 +286,6 @@ __device__ __forceinline__ void load_g_row(const uint16_t* row, int k, uint32_t 
     P[3] = m.z;
     P[4] = m.w;
     P[5] = *reinterpret_cast<const uint32_t*>(row + k + 8);
-}
-
-__device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
-    if (x + 8 <= W) {
-        *reinterpret_cast<uint2*>(row + x) =
-            make_uint2(pack4(b[0], b[1], b[2], b[3]), pack4(b[4], b[5], b[6], b[7]));
-    } else {
-        for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (uint8_t)b[j];
-    }
 }
 
 template <int MODE>
@@ -319,25 +377,6 @@ __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, i
     }
 }
 
-// Gaussian3x3 alone: G rows y0 .. y0+TH-1 from shared memory to the output.
-__device__ void gaussian_out_stage(const GTile& g, const EdgeParams& p, int x0, int y0,
-                                   bool interior) {
-    const bool full = interior || rect_is_full(p.gvalid, p);
-#pragma unroll 1
-    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
-        const int r = it >> 4, q = it & 15;
-        const int y = y0 + r, x = x0 + 8 * q;
-        if (y >= (int)p.H || x >= (int)p.W) continue;
-        uint4 m = *reinterpret_cast<const uint4*>(&g[r + 1][8 + 8 * q]);
-        uint32_t b[8] = {m.x & 0xFFu, m.x >> 16, m.y & 0xFFu, m.y >> 16,
-                         m.z & 0xFFu, m.z >> 16, m.w & 0xFFu, m.w >> 16};
-        if (!full)
-            for (int i = 0; i < 8; ++i)
-                if (!in_rect(p.gvalid, x + i, y)) b[i] = 0;
-        store8_u8(p.gout + (size_t)y * p.gout_pitch, x, p.W, b);
-    }
-}
-
 // One tile after its input box has landed in `in`.  `prefetch` runs on
 // thread 0 as soon as `in` is no longer read (after the Gaussian stage), so
 // that the box can be refilled while the rest of the tile is computed.
@@ -349,6 +388,12 @@ __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0
         fix_input_border(in, p, x0, y0);
         __syncthreads();
     }
+    if (MODE == M_GAUSS) {
+        gaussian_direct_stage(in, p, x0, y0, interior);
+        __syncthreads();  // the input box is no longer read
+        if (threadIdx.x == 0) prefetch();
+        return;
+    }
     gaussian_stage(in, g, p);
     __syncthreads();
     if (threadIdx.x == 0) prefetch();
@@ -356,10 +401,7 @@ __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0
         fix_g_border(g, p, x0, y0);
         __syncthreads();
     }
-    if (MODE == M_GAUSS)
-        gaussian_out_stage(g, p, x0, y0, interior);
-    else
-        sobel_point_stage<MODE>(g, p, x0, y0, interior);
+    sobel_point_stage<MODE>(g, p, x0, y0, interior);
     __syncthreads();
 }
 
