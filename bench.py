@@ -133,6 +133,33 @@ class ClockSampler:
                 "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+EDGE_SOURCES = ["kernels_edge.cu", "device_common.cuh", "kernel_params.h", "phase_table.h",
+                "launchers.h"]
+
+
+def kernel_source_hash(files=EDGE_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2008_11476_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, frames: int):
+    """DRAM bytes per launch from the committed ncu record, or None when the
+    kernel's sources changed since the counters were taken or the launch
+    size differs."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256") != kernel_source_hash() or rec.get("frames") != frames:
+        return None
+    return int(rec["dram_read_bytes"] + rec["dram_write_bytes"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -377,7 +404,8 @@ def run_edge(args, world, rank, local, torch):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
-                     "traffic": None, "peak_source": src, "kernel": "edge_batch_kernel",
+                     "traffic": recorded_traffic("edge_batch_kernel<MASK_PHASE>", F),
+                     "peak_source": src, "kernel": "edge_batch_kernel",
                      "algorithmic_bytes_per_launch": ext_bytes},
         "e2e": {"value": round(e2e_v, 1), "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(F * H_ * pitch),
