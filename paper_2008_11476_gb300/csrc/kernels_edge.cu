@@ -63,7 +63,11 @@ struct EdgeSmem {
     InStage in[NS];                     // ring of TMA destinations
     alignas(16) GTile g;
     alignas(8) uint64_t bar[NS];
-    int img[NS];                        // batch: image of the tile in each stage
+    // batch: parameters and origin of the tiles in flight, in a ring one longer
+    // than the input ring (tile k uses slot k mod (NS + 1), so the slot that
+    // tile k + NS fills belongs to tile k - 1, which is finished)
+    EdgeParams prm[NS + 1];
+    int tx0[NS + 1], ty0[NS + 1];
 };
 
 // 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
@@ -377,9 +381,9 @@ __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, i
     }
 }
 
-// One tile after its input box has landed in `in`.  `prefetch` runs on
-// thread 0 as soon as `in` is no longer read (after the Gaussian stage), so
-// that the box can be refilled while the rest of the tile is computed.
+// One tile after its input box has landed in `in`.  `prefetch` runs on warp
+// 0 as soon as `in` is no longer read (after the Gaussian stage), so that the
+// box can be refilled while the rest of the tile is computed.
 template <int MODE, class Prefetch>
 __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0, int y0,
                                Prefetch prefetch) {
@@ -391,12 +395,12 @@ __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0
     if (MODE == M_GAUSS) {
         gaussian_direct_stage(in, p, x0, y0, interior);
         __syncthreads();  // the input box is no longer read
-        if (threadIdx.x == 0) prefetch();
+        if (threadIdx.x < 32) prefetch();
         return;
     }
     gaussian_stage(in, g, p);
     __syncthreads();
-    if (threadIdx.x == 0) prefetch();
+    if (threadIdx.x < 32) prefetch();
     if (!interior) {
         fix_g_border(g, p, x0, y0);
         __syncthreads();
@@ -445,50 +449,62 @@ __device__ __forceinline__ void tile_origin(const EdgeParams& p, int t, int& x0,
     y0 = ty * TH;
 }
 
-// Thread 0: start the TMA load of batch tile t into ring stage s.
+// Warp 0: stage the parameters and origin of batch tile t in parameter slot
+// ps and start the TMA load of its input box into ring stage s.
 __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, int s,
-                                           int t) {
-    const int img = find_image(d.tile_start, d.n_img, t);
-    sm.img[s] = img;
-    tensormap_acquire(&d.maps[img]);
-    int x0, y0;
-    tile_origin(d.params[img], t - __ldg(d.tile_start + img), x0, y0);
-    issue_box(sm.in[s].b, &sm.bar[s], &d.maps[img], x0, y0);
+                                           int ps, int t) {
+    const int lane = threadIdx.x & 31;
+    int img = 0;
+    if (lane == 0) img = find_image(d.tile_start, d.n_img, t);
+    img = __shfl_sync(0xffffffffu, img, 0);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.params[img]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.prm[ps]);
+    for (int i = lane; i < (int)(sizeof(EdgeParams) / 4); i += 32) dst[i] = __ldg(src + i);
+    __syncwarp();
+    if (lane == 0) {
+        int x0, y0;
+        tile_origin(sm.prm[ps], t - __ldg(d.tile_start + img), x0, y0);
+        sm.tx0[ps] = x0;
+        sm.ty0[ps] = y0;
+        tensormap_acquire(&d.maps[img]);
+        fence_proxy_async_smem();
+        issue_box(sm.in[s].b, &sm.bar[s], &d.maps[img], x0, y0);
+    }
 }
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
 // CTA lives in ring stage k mod STAGES, so STAGES input boxes are in flight
-// while one is computed.
+// while one is computed.  Each tile's parameters come from shared memory.
 template <int MODE>
 __global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeBatchDesc d) {
     __shared__ EdgeSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
-        fence_barrier_init();
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
+            fence_barrier_init();
+        }
+        __syncwarp();
         for (int s = 0; s < STAGES; ++s) {
             const int t = first + s * (int)gridDim.x;
-            if (t < d.total_tiles) issue_tile(sm, d, s, t);
+            if (t < d.total_tiles) issue_tile(sm, d, s, s, t);
         }
     }
     __syncthreads();
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
         const int s = k % STAGES;
+        const int ps = k % (STAGES + 1);
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
         const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
         if (__syncthreads_or(!ok)) return;
-        const int img = sm.img[s];
-        const EdgeParams& p = d.params[img];
-        int x0, y0;
-        tile_origin(p, t - __ldg(d.tile_start + img), x0, y0);
+        const EdgeParams& p = sm.prm[ps];
+        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const int tn = t + STAGES * (int)gridDim.x;  // the next tile of this stage
+        const int pn = (k + STAGES) % (STAGES + 1);
         edge_tile_body<MODE>(sm.in[s].b, sm.g, p, x0, y0, [&] {
-            if (tn < d.total_tiles) {
-                fence_proxy_async_smem();
-                issue_tile(sm, d, s, tn);
-            }
+            if (tn < d.total_tiles) issue_tile(sm, d, s, pn, tn);
         });
     }
 }
