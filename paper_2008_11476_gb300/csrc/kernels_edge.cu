@@ -68,6 +68,7 @@ struct EdgeSmem {
     // tile k + NS fills belongs to tile k - 1, which is finished)
     EdgeParams prm[NS + 1];
     int tx0[NS + 1], ty0[NS + 1];
+    float tanb[36];                     // Phase boundary tangents (kPhaseTan)
 };
 
 // 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
@@ -106,34 +107,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Phase (see device_common.cuh: phase_u8) from exact binary32 gradients.
-__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy) {
-    float ax = fabsf(gx), ay = fabsf(gy);
-    float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    float t = mn * rcp_approx(fmaxf(mx, 1.0f));  // integers: mx = 0 only when mn = 0
-    float u = t * t;
-    float pp = 0.27753710746765137f;
-    pp = fmaf(pp, u, -1.3691582679748535f);
-    pp = fmaf(pp, u, 3.244159698486328f);
-    pp = fmaf(pp, u, -5.391748428344727f);
-    pp = fmaf(pp, u, 8.070429801940918f);
-    pp = fmaf(pp, u, -13.574716567993164f);
-    pp = fmaf(pp, u, 40.743507385253906f);
-    float f = fmaf(pp, t, 0.5f);
-    float fl = floorf(f);
-    float d = f - fl;
-    int ra = (int)fl;
-    if (fabsf(d - 0.5f) > 0.5f - 1e-4f) {
-        int j = d < 0.5f ? ra - 1 : ra;
-        if (j >= 0 && j < 32) {
-            double cr = (double)mn * kPhaseBoundCos[j] - (double)mx * kPhaseBoundSin[j];
-            ra = cr >= 0.0 ? j + 1 : j;
-        }
-    }
-    int q1 = ay > ax ? 64 - ra : ra;
-    bool sx = gx < 0.0f, sy = gy < 0.0f;
-    int q = (sx ? 128 : 0) + ((sx != sy) ? -q1 : q1);
-    return (uint32_t)q & 255u;
+// Phase from exact integer gradients held in binary32 (gen_phase_poly.py
+// derives and checks every step over all integer gradient pairs): with
+// mn, mx = min, max of |gx|, |gy| and t = mn / mx, the rounded octant angle
+// is n or n - 1 for n = floor(1 + t (A + B t)), and it is n exactly when
+// mn - mx tan((n - 1/2) pi / 128) > 0.  tanb holds those tangents (n = 0..33)
+// in shared memory.  The octant angle then maps to the full turn by the
+// signs of gx, gy and the swap of |gx|, |gy|; the low byte is the phase.
+__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const float* tanb) {
+    const float ax = fabsf(gx), ay = fabsf(gy);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mn * rcp_approx(fmaxf(mx, 1.0f));  // integers: mx = 0 only when mn = 0
+    const int n = __float2int_rd(fmaf(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 1.0f));  // 1..33
+    const int ra = fmaf(-mx, tanb[n], mn) > 0.0f ? n : n - 1;
+    const int q1 = ay > ax ? 64 - ra : ra;
+    const bool sx = gx < 0.0f, sy = gy < 0.0f;
+    return (uint32_t)((sx ? 128 : 0) + ((sx != sy) ? -q1 : q1));
 }
 
 __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
@@ -214,11 +203,14 @@ __device__ void gaussian_direct_stage(const InTile& in, const EdgeParams& p, int
                                       bool interior) {
     const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
     const bool full = interior || rect_is_full(p.gvalid, p);
+    const int W = p.W, H = p.H;
+    uint8_t* const gout = p.gout;
+    const size_t gpitch = p.gout_pitch;
 #pragma unroll 1
     for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
         const int r = it >> 4, q = it & 15;
         const int y = y0 + r, x = x0 + 8 * q;
-        if (y >= (int)p.H || x >= (int)p.W) continue;
+        if (y >= H || x >= W) continue;
         const int c = 16 + 8 * q;
         uint32_t V[6];
 #pragma unroll
@@ -238,8 +230,8 @@ __device__ void gaussian_direct_stage(const InTile& in, const EdgeParams& p, int
             uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
             Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
         }
-        uint8_t* dst = p.gout + (size_t)y * p.gout_pitch;
-        if (full && x + 8 <= (int)p.W) {
+        uint8_t* dst = gout + (size_t)y * gpitch;
+        if (full && x + 8 <= W) {
             *reinterpret_cast<uint2*>(dst + x) =
                 make_uint2(__byte_perm(Gp[0], Gp[1], 0x6420), __byte_perm(Gp[2], Gp[3], 0x6420));
         } else {
@@ -252,7 +244,7 @@ __device__ void gaussian_direct_stage(const InTile& in, const EdgeParams& p, int
             if (!full)
                 for (int i = 0; i < 8; ++i)
                     if (!in_rect(p.gvalid, x + i, y)) b[i] = 0;
-            store8_u8(dst, x, p.W, b);
+            store8_u8(dst, x, W, b);
         }
     }
 }
@@ -292,16 +284,40 @@ __device__ __forceinline__ void load_g_row(const uint16_t* row, int k, uint32_t 
     P[5] = *reinterpret_cast<const uint32_t*>(row + k + 8);
 }
 
+// All-ones when a > b, else 0 (one instruction).
+__device__ __forceinline__ uint32_t set_gt(float a, float b) {
+    uint32_t r;
+    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void store8_words(uint8_t* row, int x, int W, uint32_t lo, uint32_t hi) {
+    if (x + 8 <= W) {
+        *reinterpret_cast<uint2*>(row + x) = make_uint2(lo, hi);
+    } else {
+        for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (uint8_t)((j < 4 ? lo : hi) >> (8 * (j & 3)));
+    }
+}
+
 template <int MODE>
 __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, int y0,
-                                  bool interior) {
+                                  bool interior, const float* tanb) {
     const float s_thr = (float)p.s_thr;
     const bool full = interior || rect_is_full(p.valid, p);
+    const int W = p.W, H = p.H;
+    // mask bytes from all-ones / zero compare results: (c & (tv ^ fv)) ^ fv
+    const uint32_t tvx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
+    const uint32_t fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
+    constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK;
+    constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
+    uint8_t* const mask = p.mask;
+    uint8_t* const phase = p.phase;
+    const size_t mask_pitch = p.mask_pitch, phase_pitch = p.phase_pitch;
 #pragma unroll 1
     for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
         const int r = it >> 4, s8 = it & 15;
         const int y = y0 + r, x = x0 + 8 * s8;
-        if (y >= (int)p.H || x >= (int)p.W) continue;
+        if (y >= H || x >= W) continue;
         const int k = 8 + 8 * s8;
         uint32_t A[6], B[6], C[6];
         load_g_row(g[r], k, A);
@@ -329,15 +345,12 @@ __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, i
         for (int i = 0; i < 8; ++i) {
             mk[i] = ph[i] = 0u;
             mg[i] = 0;
-            if (MODE == M_MASK_PHASE || MODE == M_MASK) {
-                float s2 = fmaf(gx[i], gx[i], gy[i] * gy[i]);
-                mk[i] = s2 > s_thr ? (uint32_t)p.tv : (uint32_t)p.fv;
-            }
-            if (MODE == M_MASK_PHASE || MODE == M_PHASE) ph[i] = phase_from_float(gx[i], gy[i]);
+            if (kMask) mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), s_thr);
+            if (kPhase) ph[i] = phase_from_float(gx[i], gy[i], tanb);
             if (MODE == M_GENERAL) {
                 int ix = (int)gx[i], iy = (int)gy[i];
                 mg[i] = magnitude_s16(ix, iy);
-                if (p.mask) {
+                if (mask) {
                     bool t;
                     if (!p.thr_general)
                         t = ix * ix + iy * iy > p.s_thr;
@@ -345,37 +358,45 @@ __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, i
                         t = p.thr_type == HVX_THRESHOLD_BINARY
                                 ? mg[i] > p.thr_lo
                                 : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
-                    mk[i] = t ? (uint32_t)p.tv : (uint32_t)p.fv;
+                    mk[i] = t ? 0xFFFFFFFFu : 0u;
                 }
-                if (p.phase) ph[i] = phase_from_float(gx[i], gy[i]);
+                if (phase) ph[i] = phase_from_float(gx[i], gy[i], tanb);
             }
         }
-        if (!full) {
+        const bool want_mask = kMask || (MODE == M_GENERAL && mask);
+        const bool want_phase = kPhase || (MODE == M_GENERAL && phase);
+        if (full) {
+            if (want_mask)
+                store8_words(mask + (size_t)y * mask_pitch, x, W,
+                             (pack4(mk[0], mk[1], mk[2], mk[3]) & tvx) ^ fvx,
+                             (pack4(mk[4], mk[5], mk[6], mk[7]) & tvx) ^ fvx);
+            if (want_phase)
+                store8_words(phase + (size_t)y * phase_pitch, x, W,
+                             pack4(ph[0], ph[1], ph[2], ph[3]), pack4(ph[4], ph[5], ph[6], ph[7]));
+        } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                mk[i] = (mk[i] & tvx) ^ fvx;
                 if (!in_rect(p.valid, x + i, y)) {
                     mk[i] = 0u;
                     ph[i] = 0u;
                     mg[i] = 0;
                 }
+            }
+            if (want_mask) store8_u8(mask + (size_t)y * mask_pitch, x, W, mk);
+            if (want_phase) store8_u8(phase + (size_t)y * phase_pitch, x, W, ph);
         }
-        const bool want_mask =
-            MODE == M_MASK_PHASE || MODE == M_MASK || (MODE == M_GENERAL && p.mask);
-        const bool want_phase =
-            MODE == M_MASK_PHASE || MODE == M_PHASE || (MODE == M_GENERAL && p.phase);
-        if (want_mask) store8_u8(p.mask + (size_t)y * p.mask_pitch, x, p.W, mk);
-        if (want_phase) store8_u8(p.phase + (size_t)y * p.phase_pitch, x, p.W, ph);
         if (MODE == M_GENERAL && p.mag) {
             int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
                                                       (size_t)y * p.mag_pitch);
-            if (x + 8 <= (int)p.W) {
+            if (x + 8 <= W) {
                 *reinterpret_cast<uint4*>(row + x) =
                     make_uint4((mg[0] & 0xFFFF) | ((uint32_t)mg[1] << 16),
                                (mg[2] & 0xFFFF) | ((uint32_t)mg[3] << 16),
                                (mg[4] & 0xFFFF) | ((uint32_t)mg[5] << 16),
                                (mg[6] & 0xFFFF) | ((uint32_t)mg[7] << 16));
             } else {
-                for (int j = 0; j < 8 && x + j < (int)p.W; ++j) row[x + j] = (int16_t)mg[j];
+                for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (int16_t)mg[j];
             }
         }
     }
@@ -386,7 +407,7 @@ __device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, i
 // box can be refilled while the rest of the tile is computed.
 template <int MODE, class Prefetch>
 __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0, int y0,
-                               Prefetch prefetch) {
+                               const float* tanb, Prefetch prefetch) {
     const bool interior = tile_is_interior(p, x0, y0);
     if (!interior) {
         fix_input_border(in, p, x0, y0);
@@ -405,7 +426,7 @@ __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0
         fix_g_border(g, p, x0, y0);
         __syncthreads();
     }
-    sobel_point_stage<MODE>(g, p, x0, y0, interior);
+    sobel_point_stage<MODE>(g, p, x0, y0, interior, tanb);
     __syncthreads();
 }
 
@@ -424,10 +445,11 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4)
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
+    if (threadIdx.x < 34) sm.tanb[threadIdx.x] = kPhaseTan[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
     if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
-    edge_tile_body<MODE>(sm.in[0].b, sm.g, p, x0, y0, [] {});
+    edge_tile_body<MODE>(sm.in[0].b, sm.g, p, x0, y0, sm.tanb, [] {});
 }
 
 __device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
@@ -490,6 +512,8 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeB
             const int t = first + s * (int)gridDim.x;
             if (t < d.total_tiles) issue_tile(sm, d, s, s, t);
         }
+    } else if (threadIdx.x < 32 + 34) {
+        sm.tanb[threadIdx.x - 32] = kPhaseTan[threadIdx.x - 32];
     }
     __syncthreads();
     int k = 0;
@@ -503,7 +527,7 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeB
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const int tn = t + STAGES * (int)gridDim.x;  // the next tile of this stage
         const int pn = (k + STAGES) % (STAGES + 1);
-        edge_tile_body<MODE>(sm.in[s].b, sm.g, p, x0, y0, [&] {
+        edge_tile_body<MODE>(sm.in[s].b, sm.g, p, x0, y0, sm.tanb, [&] {
             if (tn < d.total_tiles) issue_tile(sm, d, s, pn, tn);
         });
     }
