@@ -580,7 +580,7 @@ def run_gauss_batch(args, world, rank, local, torch):
                                    "step in one persistent launch", "l2": "larger than L2"},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs"),
                          "unit": "GB/s", "frac": round(ach / peaks.get("hbm_gbs", 6800), 4),
-                         "peak_source": src, "kernel": "edge_batch_kernel<0>",
+                         "peak_source": src, "kernel": "gauss_batch_kernel",
                          "algorithmic_bytes_per_launch": ext},
             "gpu_launches": args.steps, "clocks": clocks}), flush=True)
 

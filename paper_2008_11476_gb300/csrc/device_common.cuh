@@ -216,6 +216,10 @@ __device__ __forceinline__ float ratio_to_float(long long q, long long d) {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+__device__ __forceinline__ bool rect_full(const int32_t* r, int W, int H) {
+    return r[0] == 0 && r[1] == 0 && r[2] == W && r[3] == H;
+}
+
 __device__ __forceinline__ bool in_rect(const int32_t* r, int x, int y) {
     return x >= r[0] && x < r[2] && y >= r[1] && y < r[3];
 }
@@ -287,6 +291,33 @@ __device__ __forceinline__ void for_each_outside(int R, int C, int bx, int by, i
         }
         f(r, c);
     }
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit-lane (SWAR) helpers of the U8 stencil kernels: two pixels per
+// 32-bit word, so that one add or shift works on both.
+
+// 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
+__device__ __forceinline__ uint32_t lo_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }
+__device__ __forceinline__ uint32_t hi_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }
+
+// (lane1 of a, lane0 of b): the pair starting one pixel to the right of a.
+__device__ __forceinline__ uint32_t shift_pair(uint32_t a, uint32_t b) {
+    return __funnelshift_r(a, b, 16);
+}
+
+// Batch tile t -> image: the last i with tile_start[i] <= t (binary search
+// over the n + 1 prefix sums of per-image tile counts).
+__device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace dev

@@ -89,6 +89,16 @@ constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_LOAD_W = EDGE_TW + 32;  // TMA box width: 16 B aligned both sides
 constexpr int EDGE_STAGES = 3;             // input boxes in flight per persistent CTA
 
+// Gaussian3x3 group alone (its own kernel, same parameter block): tall tiles,
+// each thread slides a 3-row window down one 8-pixel column strip.
+constexpr int GAUSS_TW = 128;
+constexpr int GAUSS_TH = 120;              // 1080 = 9 x 120, 2160 = 18 x 120, 480 = 4 x 120
+constexpr int GAUSS_THREADS = 128;         // 16 column strips x 8 row groups
+constexpr int GAUSS_ROWS = GAUSS_TH / 8;   // output rows per thread (15)
+constexpr int GAUSS_LOAD_W = GAUSS_TW + 32;
+constexpr int GAUSS_LOAD_H = GAUSS_TH + 2;
+constexpr int GAUSS_STAGES = 2;            // input boxes per persistent CTA
+
 struct EdgeParams {
     uint32_t W, H;
     const uint8_t* in;

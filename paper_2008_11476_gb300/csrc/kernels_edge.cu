@@ -1,5 +1,5 @@
-// Fused edge-detection group and the Gaussian3x3 kernel (Table 2 local and
-// point operators; the edge graph of Listing 1 / the Section 6 benchmarks):
+// Fused edge-detection group (Table 2 local and point operators; the edge
+// graph of Listing 1 / the Section 6 benchmarks):
 //
 //   in U8 --Gaussian3x3--> G (on chip) --Sobel3x3--> gx, gy (registers)
 //        --Magnitude--> m --Threshold--> mask (U8)      --Phase--> phase (U8)
@@ -43,7 +43,7 @@ constexpr int GW = TW + 16;          // G columns x0 - 8 .. x0 + 135
 constexpr uint32_t IN_BYTES = IN_ROWS * LW;
 
 // Kernel modes (template parameter).
-constexpr int M_GAUSS = 0;      // Gaussian3x3 alone: write G
+constexpr int M_GAUSS = EDGE_MODE_GAUSS;  // Gaussian3x3 alone (kernels_gauss.cu)
 constexpr int M_MASK_PHASE = 1; // binary threshold mask + phase
 constexpr int M_MASK = 2;       // binary threshold mask only
 constexpr int M_PHASE = 3;      // phase only
@@ -70,15 +70,6 @@ struct EdgeSmem {
     int tx0[NS + 1], ty0[NS + 1];
     float tanb[36];                     // Phase boundary tangents (kPhaseTan)
 };
-
-// 16-bit lane pairs of bytes: (b0, b1) and (b2, b3) of a word.
-__device__ __forceinline__ uint32_t lo_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }
-__device__ __forceinline__ uint32_t hi_pair(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }
-
-// (lane1 of a, lane0 of b): the pair starting one pixel to the right of a.
-__device__ __forceinline__ uint32_t shift_pair(uint32_t a, uint32_t b) {
-    return __funnelshift_r(a, b, 16);
-}
 
 // Lane values of a 16-bit-lane word as binary32, minus a bias, exactly.
 __device__ __forceinline__ float lane_lo_f(uint32_t w, float bias) {
@@ -194,58 +185,6 @@ __device__ void gaussian_stage(const InTile& in, GTile& g, const EdgeParams& p) 
             *reinterpret_cast<uint32_t*>(&g[r][136]) = s >> 4;
         else
             *reinterpret_cast<uint32_t*>(&g[r][6]) = (s >> 4) << 16;
-    }
-}
-
-// Gaussian3x3 alone: 8 output pixels per item straight from the input box in
-// 16-bit lanes, packed to bytes and stored; no shared-memory round trip.
-__device__ void gaussian_direct_stage(const InTile& in, const EdgeParams& p, int x0, int y0,
-                                      bool interior) {
-    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
-    const bool full = interior || rect_is_full(p.gvalid, p);
-    const int W = p.W, H = p.H;
-    uint8_t* const gout = p.gout;
-    const size_t gpitch = p.gout_pitch;
-#pragma unroll 1
-    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
-        const int r = it >> 4, q = it & 15;
-        const int y = y0 + r, x = x0 + 8 * q;
-        if (y >= H || x >= W) continue;
-        const int c = 16 + 8 * q;
-        uint32_t V[6];
-#pragma unroll
-        for (int dr = 0; dr < 3; ++dr) {
-            const uint8_t* row = in[r + 1 + dr];
-            uint2 m = *reinterpret_cast<const uint2*>(row + c);
-            uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
-            uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
-            uint32_t P[6] = {hi_pair(wl), lo_pair(m.x), hi_pair(m.x),
-                             lo_pair(m.y), hi_pair(m.y), lo_pair(wr)};
-#pragma unroll
-            for (int k = 0; k < 6; ++k) V[k] = dr == 0 ? P[k] : V[k] + (dr == 1 ? 2u : 1u) * P[k];
-        }
-        uint32_t Gp[4];
-#pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
-            Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
-        }
-        uint8_t* dst = gout + (size_t)y * gpitch;
-        if (full && x + 8 <= W) {
-            *reinterpret_cast<uint2*>(dst + x) =
-                make_uint2(__byte_perm(Gp[0], Gp[1], 0x6420), __byte_perm(Gp[2], Gp[3], 0x6420));
-        } else {
-            uint32_t b[8];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                b[2 * j] = Gp[j] & 0xFFu;
-                b[2 * j + 1] = Gp[j] >> 16;
-            }
-            if (!full)
-                for (int i = 0; i < 8; ++i)
-                    if (!in_rect(p.gvalid, x + i, y)) b[i] = 0;
-            store8_u8(dst, x, W, b);
-        }
     }
 }
 
@@ -413,12 +352,6 @@ __device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0
         fix_input_border(in, p, x0, y0);
         __syncthreads();
     }
-    if (MODE == M_GAUSS) {
-        gaussian_direct_stage(in, p, x0, y0, interior);
-        __syncthreads();  // the input box is no longer read
-        if (threadIdx.x < 32) prefetch();
-        return;
-    }
     gaussian_stage(in, g, p);
     __syncthreads();
     if (threadIdx.x < 32) prefetch();
@@ -450,18 +383,6 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4)
     if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
     if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
     edge_tile_body<MODE>(sm.in[0].b, sm.g, p, x0, y0, sm.tanb, [] {});
-}
-
-__device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(tile_start + mid) <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ void tile_origin(const EdgeParams& p, int t, int& x0, int& y0) {
@@ -556,9 +477,14 @@ int edge_mode(const EdgeParams& p) {
     return M_PHASE;
 }
 
+void edge_tile_dims(int mode, int* tw, int* th) {
+    *tw = mode == M_GAUSS ? GAUSS_TW : EDGE_TW;
+    *th = mode == M_GAUSS ? GAUSS_TH : EDGE_TH;
+}
+
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
     switch (edge_mode(p)) {
-        case M_GAUSS: return launch_mode<M_GAUSS>(map, p, s);
+        case M_GAUSS: return launch_gauss(map, p, s);
         case M_MASK_PHASE: return launch_mode<M_MASK_PHASE>(map, p, s);
         case M_MASK: return launch_mode<M_MASK>(map, p, s);
         case M_PHASE: return launch_mode<M_PHASE>(map, p, s);
@@ -568,7 +494,7 @@ cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_
 
 cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s) {
     switch (mode) {
-        case M_GAUSS: return launch_batch_mode<M_GAUSS>(d, grid, s);
+        case M_GAUSS: return launch_gauss_batch(d, grid, s);
         case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, s);
         case M_MASK: return launch_batch_mode<M_MASK>(d, grid, s);
         case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, s);
@@ -576,7 +502,8 @@ cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaSt
     }
 }
 
-int edge_batch_blocks_per_sm() {
+int edge_batch_blocks_per_sm(int mode) {
+    if (mode == M_GAUSS) return gauss_batch_blocks_per_sm();
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel<M_MASK_PHASE>,
                                                   EDGE_THREADS, 0);

@@ -1,0 +1,263 @@
+// Gaussian3x3 node alone (Table 2 local operator): the plain Gaussian graph
+// and the Gaussian requests of a serving mix.
+//
+// One CTA (128 threads) computes a 128 x 120 output tile from one TMA box of
+// 160 x 122 input bytes (the tile plus one halo row above and below; the
+// columns widened to 16-byte boundaries, x0 - 16 .. x0 + 143).  Thread (q, g)
+// owns the 8-pixel column strip x0 + 8q .. x0 + 8q + 7 and the 15 rows
+// y0 + 15g .. y0 + 15g + 14, and walks down them with a 3-row window: each
+// input row is read from shared memory once (three loads), split once into
+// 16-bit lanes of pixel pairs, and serves three output rows.  The vertical and
+// horizontal 1-2-1 sums, the rounding term and the shift by 4 all work on two
+// pixels per 32-bit add; the 8 output bytes are gathered by two byte permutes
+// and written with one 8-byte store (a half-warp writes 128 contiguous bytes).
+//
+// Edge tiles first apply the node's border mode to the box cells outside the
+// image (the TMA load fills them with 0); pixels outside the output's valid
+// region (BORDER_UNDEFINED) are written as 0.
+//
+// The batch kernel runs persistently over the tiles of many images (one
+// tensor map and parameter block per image), with two boxes in flight per
+// CTA: the next tile's box is loading while the current one is computed.
+#include "device_common.cuh"
+#include "launchers.h"
+
+namespace hvx {
+namespace {
+
+using namespace dev;
+
+constexpr int TW = GAUSS_TW;          // 128
+constexpr int TH = GAUSS_TH;          // 120
+constexpr int LW = GAUSS_LOAD_W;      // 160
+constexpr int LH = GAUSS_LOAD_H;      // 122
+constexpr int ROWS = GAUSS_ROWS;      // 15 output rows per thread
+constexpr int STAGES = GAUSS_STAGES;  // 2
+constexpr uint32_t BOX_BYTES = LW * LH;
+static_assert(GAUSS_THREADS == 16 * (TH / ROWS), "16 strips x row groups");
+
+using Box = uint8_t[LH][LW];  // image (x0 - 16 + c, y0 - 1 + r)
+
+struct alignas(128) BoxStage {
+    Box b;
+};
+
+template <int NS>
+struct GaussSmem {
+    BoxStage in[NS];
+    alignas(8) uint64_t bar[NS];
+    // batch: parameters and origin of the tiles in flight (slot k mod (NS + 1))
+    EdgeParams prm[NS + 1];
+    int tx0[NS + 1], ty0[NS + 1];
+};
+
+__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
+    return x0 >= 1 && y0 >= 1 && x0 + TW + 1 <= (int)p.W && y0 + TH + 1 <= (int)p.H;
+}
+
+// Box cells outside the image under REPLICATE / CONSTANT (edge tiles only).
+__device__ void fix_box_border(Box& in, const EdgeParams& p, int x0, int y0) {
+    const int W = p.W, H = p.H;
+    if (p.border_g == HVX_BORDER_UNDEFINED) return;
+    const bool cst = p.border_g == HVX_BORDER_CONSTANT;
+    const uint8_t cv = (uint8_t)p.cval_g;
+    for_each_outside(LH, LW, x0 - 16, y0 - 1, W, H, [&](int r, int c) {
+        const int x = x0 - 16 + c, y = y0 - 1 + r;
+        in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 16)];
+    });
+}
+
+// Pixel pairs (x - 2, x - 1), (x, x + 1) .. (x + 8, x + 9) of one box row as
+// 16-bit lanes, for the strip starting at box column c (= x - x0 + 16).
+__device__ __forceinline__ void load_pairs(const uint8_t* row, int c, uint32_t P[6]) {
+    const uint2 m = *reinterpret_cast<const uint2*>(row + c);
+    const uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
+    const uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
+    P[0] = hi_pair(wl);
+    P[1] = lo_pair(m.x);
+    P[2] = hi_pair(m.x);
+    P[3] = lo_pair(m.y);
+    P[4] = hi_pair(m.y);
+    P[5] = lo_pair(wr);
+}
+
+// Gaussian outputs x .. x + 7 of one row from the pair words of the input rows
+// above (a), at (b) and below (c); bytes packed into two words.  Each lane
+// sum is at most 16 * 255 + 8 < 2^12, so lanes never carry into each other;
+// after the shift by 4 the results sit in bytes 0 and 2 of each word.
+__device__ __forceinline__ uint2 gauss8(const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                                        uint32_t rnd) {
+    uint32_t V[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) V[k] = a[k] + 2u * b[k] + c[k];
+    uint32_t o[4];
+#pragma unroll
+    for (int j = 1; j <= 4; ++j)
+        o[j - 1] = (shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd) >> 4;
+    return make_uint2(__byte_perm(o[0], o[1], 0x6420), __byte_perm(o[2], o[3], 0x6420));
+}
+
+// Store of a strip row that is cut by the right image edge or crosses the
+// output's valid region.
+__device__ __noinline__ void store_edge(uint8_t* dst, int x, int y, const EdgeParams& p, uint2 o) {
+    const bool full = rect_full(p.gvalid, p.W, p.H);
+    for (int j = 0; j < 8 && x + j < (int)p.W; ++j) {
+        uint8_t v = (uint8_t)((j < 4 ? o.x : o.y) >> (8 * (j & 3)));
+        if (!full && !in_rect(p.gvalid, x + j, y)) v = 0;
+        dst[x + j] = v;
+    }
+}
+
+// One tile after its box has landed (and, on edge tiles, been border-fixed).
+__device__ __forceinline__ void gauss_tile(const Box& in, const EdgeParams& p, int x0, int y0,
+                                           bool interior) {
+    const int q = threadIdx.x & 15, g = threadIdx.x >> 4;
+    const int W = p.W, H = p.H;
+    const int x = x0 + 8 * q, yb = y0 + ROWS * g;
+    if (x >= W || yb >= H) return;
+    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
+    const size_t pitch = p.gout_pitch;
+    uint8_t* dst = p.gout + (size_t)yb * pitch;
+    const uint8_t* row = &in[ROWS * g][0];  // input row yb - 1
+    const int c = 16 + 8 * q;
+    uint32_t P[3][6];
+    load_pairs(row, c, P[0]);
+    load_pairs(row + LW, c, P[1]);
+    const bool fast = (interior || rect_full(p.gvalid, W, H)) && x + 8 <= W && yb + ROWS <= H;
+    if (fast) {
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            load_pairs(row + (i + 2) * LW, c, P[(i + 2) % 3]);
+            *reinterpret_cast<uint2*>(dst + x) = gauss8(P[i % 3], P[(i + 1) % 3], P[(i + 2) % 3], rnd);
+            dst += pitch;
+        }
+    } else {
+        const int n = min(ROWS, H - yb);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            uint32_t* a = P[0];
+            uint32_t* b = P[1];
+            uint32_t c2[6];
+            load_pairs(row + (i + 2) * LW, c, c2);
+            store_edge(dst, x, yb + i, p, gauss8(a, b, c2, rnd));
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                a[k] = b[k];
+                b[k] = c2[k];
+            }
+            dst += pitch;
+        }
+    }
+}
+
+__device__ __forceinline__ void issue_box(Box& in, uint64_t* bar, const CUtensorMap* map, int x0,
+                                          int y0) {
+    mbar_arrive_expect_tx(bar, BOX_BYTES);
+    tma_load_2d(&in[0][0], map, bar, x0 - 16, y0 - 1);
+}
+
+__global__ void __launch_bounds__(GAUSS_THREADS)
+    gauss_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
+    __shared__ GaussSmem<1> sm;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
+    if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
+    const bool interior = tile_is_interior(p, x0, y0);
+    if (!interior) {
+        fix_box_border(sm.in[0].b, p, x0, y0);
+        __syncthreads();
+    }
+    gauss_tile(sm.in[0].b, p, x0, y0, interior);
+}
+
+// Warp 0: stage the parameters and origin of batch tile t in slot ps and
+// start the TMA load of its box into stage s.
+__device__ __forceinline__ void issue_tile(GaussSmem<STAGES>& sm, const EdgeBatchDesc& d, int s,
+                                           int ps, int t) {
+    const int lane = threadIdx.x & 31;
+    int img = 0;
+    if (lane == 0) img = find_image(d.tile_start, d.n_img, t);
+    img = __shfl_sync(0xffffffffu, img, 0);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.params[img]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.prm[ps]);
+    for (int i = lane; i < (int)(sizeof(EdgeParams) / 4); i += 32) dst[i] = __ldg(src + i);
+    __syncwarp();
+    if (lane == 0) {
+        const int tiles_x = (sm.prm[ps].W + TW - 1) / TW;
+        const int local = t - __ldg(d.tile_start + img);
+        const int ty = local / tiles_x;
+        const int x0 = (local - ty * tiles_x) * TW, y0 = ty * TH;
+        sm.tx0[ps] = x0;
+        sm.ty0[ps] = y0;
+        tensormap_acquire(&d.maps[img]);
+        fence_proxy_async_smem();
+        issue_box(sm.in[s].b, &sm.bar[s], &d.maps[img], x0, y0);
+    }
+}
+
+// Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
+// CTA lives in box stage k mod STAGES.
+__global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBatchDesc d) {
+    __shared__ GaussSmem<STAGES> sm;
+    const int first = blockIdx.x;
+    if (first >= d.total_tiles) return;
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
+            fence_barrier_init();
+        }
+        __syncwarp();
+        for (int s = 0; s < STAGES; ++s) {
+            const int t = first + s * (int)gridDim.x;
+            if (t < d.total_tiles) issue_tile(sm, d, s, s, t);
+        }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
+        const int s = k % STAGES;
+        const int ps = k % (STAGES + 1);
+        const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
+        const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
+        if (__syncthreads_or(!ok)) return;
+        const EdgeParams& p = sm.prm[ps];
+        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
+        const bool interior = tile_is_interior(p, x0, y0);
+        if (!interior) {
+            fix_box_border(sm.in[s].b, p, x0, y0);
+            __syncthreads();
+        }
+        gauss_tile(sm.in[s].b, p, x0, y0, interior);
+        __syncthreads();  // box s is no longer read
+        if (threadIdx.x < 32) {
+            const int tn = t + STAGES * (int)gridDim.x;
+            if (tn < d.total_tiles) issue_tile(sm, d, s, (k + STAGES) % (STAGES + 1), tn);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
+    dim3 grid((p.W + TW - 1) / TW, (p.H + TH - 1) / TH);
+    gauss_kernel<<<grid, GAUSS_THREADS, 0, s>>>(map, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s) {
+    gauss_batch_kernel<<<grid, GAUSS_THREADS, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+int gauss_batch_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gauss_batch_kernel, GAUSS_THREADS, 0);
+    return n;
+}
+
+}  // namespace hvx

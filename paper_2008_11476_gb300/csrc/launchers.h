@@ -19,11 +19,18 @@ struct EdgeBatchDesc {
 };
 
 // Output mode of an edge / Gaussian group (which kernel instantiation runs it);
-// every image of one batch launch must have the same mode.
+// every image of one batch launch must have the same mode.  EDGE_MODE_GAUSS
+// (the Gaussian3x3 group alone) runs the Gaussian kernel, with its own tile.
+constexpr int EDGE_MODE_GAUSS = 0;
 int edge_mode(const EdgeParams& p);
+void edge_tile_dims(int mode, int* tw, int* th);
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
 cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s);
-int edge_batch_blocks_per_sm();
+int edge_batch_blocks_per_sm(int mode);
+
+cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
+cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
+int gauss_batch_blocks_per_sm();
 
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);
 cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);

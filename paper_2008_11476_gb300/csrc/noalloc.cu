@@ -181,7 +181,7 @@ extern "C" hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t 
     d.err = d_err;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = edge_batch_blocks_per_sm();
+    int per_sm = edge_batch_blocks_per_sm(edge_mode(params[0]));
     int grid = std::min(d.total_tiles, std::max(1, sms) * std::max(1, per_sm));
     if (launch_edge_batch(d, edge_mode(params[0]), grid, s) != cudaSuccess) {
         cudaGetLastError();

@@ -207,7 +207,7 @@ hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
     e.gout = static_cast<uint8_t*>(g.out->dev);
     e.gout_pitch = g.out->pitch;
     set_rect(e.gvalid, g.out->valid);
-    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_TH + 4);
+    return encode_u8_map(&G.tmap, g.in[0], GAUSS_LOAD_W, GAUSS_LOAD_H);
 }
 
 // ---- Harris group -------------------------------------------------------------
@@ -595,7 +595,7 @@ namespace {
 // HVX_AUTOTUNE=0 in the environment skips the trials and takes the
 // occupancy limit.
 int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode, cudaStream_t s) {
-    const int per_sm_max = std::max(1, edge_batch_blocks_per_sm());
+    const int per_sm_max = std::max(1, edge_batch_blocks_per_sm(mode));
     int best = std::min(d.total_tiles, ctx->num_sms * per_sm_max);
     const char* env = std::getenv("HVX_AUTOTUNE");
     if ((env && env[0] == '0') || per_sm_max == 1) return best;
@@ -642,12 +642,14 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     const size_t total = tiles_off + (size_t)(n + 1) * sizeof(int);
     std::vector<uint8_t> host(total);
     std::vector<int> tile_start(n + 1, 0);
+    int tw = 0, th = 0;
+    edge_tile_dims(mode, &tw, &th);
     for (int i = 0; i < n; ++i) {
         const Group& G = gs[i]->plan.groups[0];
         std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap, sizeof(CUtensorMap));
         std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &G.edge,
                     sizeof(EdgeParams));
-        int tiles = (int)(((G.W + EDGE_TW - 1) / EDGE_TW) * ((G.H + EDGE_TH - 1) / EDGE_TH));
+        int tiles = (int)(((G.W + tw - 1) / tw) * ((G.H + th - 1) / th));
         tile_start[i + 1] = tile_start[i] + tiles;
     }
     std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));

@@ -34,7 +34,8 @@ def circ_diff(a, b):
 
 # --- Gaussian3x3 (the plain one-node graph) --------------------------------------
 
-@pytest.mark.parametrize("w,h", SIZES)
+# the Gaussian kernel's tiles are 128 x 120: add sizes with several ragged tile rows
+@pytest.mark.parametrize("w,h", SIZES + [(300, 250), (385, 361)])
 @pytest.mark.parametrize("border", BORDERS)
 def test_gaussian(ctx, w, h, border):
     img = synth.uniform_u8(w, h, seed=1 + w + h)
