@@ -11,16 +11,19 @@ turn, and round a exactly.
    b_j = (j + 1/2) pi / 128, j = 0..31 (kPhaseBoundCos / kPhaseBoundSin).
 
 2. The fused edge kernel takes one cheap guess y = t (A + B t) (max error
-   0.14 bins, so n = floor(y + 1) is the true rounded value or one above it)
-   and always decides between n - 1 and n with one exact test against the
-   boundary beta_n = (n - 1/2) pi / 128 (n = 0..33):
+   0.14 bins, so n = floor(y + 1) is the true rounded value or one above it;
+   a round-down fma adds 1.5 * 2^23 + 1, so that n is read off the low
+   mantissa bits) and always decides between n - 1 and n with one exact test
+   against the boundary beta_n = (n - 1/2) pi / 128 (n = 1..33):
        a >= n - 1/2  <=>  mn - mx tan(beta_n) > 0,
-   evaluated as fma(-mx, T_n, mn) > 0 with T_n = tan(beta_n) rounded to
-   binary32 (kPhaseTan).  Over all integer gradients (|gx|, |gy| <= 1020)
+   evaluated as fma(-mx, T_n, mn) with T_n = tan(beta_n) rounded to binary32
+   (kPhaseTan).  Over all integer gradients (|gx|, |gy| <= 1020)
    |mn - mx tan(beta_n)| is at least 3.15e-5 while mx |tan(beta_n) - T_n| is
    at most 2.93e-5, so the exact value of the fma has the true sign, and its
-   one rounding keeps that sign; verify_tan_test() checks every pair.  The
-   strict '>' makes gx = gy = 0 give 0.
+   one rounding keeps that sign (it is never 0 for mx >= 1).  mx is raised
+   to 1 for gx = gy = 0, which makes the test negative there (phase 0).  The
+   kernel's table, indexed by octant and n, maps the octant angle to the
+   phase byte.  verify_tan_test() and verify_phase_all() check every pair.
 
 Run: python gen_phase_poly.py [path of phase_table.h to write]
 """
@@ -99,16 +102,30 @@ def _all_pairs():
     return mn[keep].astype(np.float64), mx[keep].astype(np.float64)
 
 
+def _guess_n(t, A, B):
+    """n = floor(t * fma(t, B, A) + 1) as the kernel's round-down fma forms it
+    (the product is exact in double, and so is adding 1)."""
+    inner = np.float32(np.float64(t) * np.float64(B) + np.float64(A))
+    return np.floor(np.float64(t) * np.float64(inner) + 1.0).astype(np.int64)
+
+
+def _perturbed(t0, du):
+    t = t0
+    for _ in range(abs(du)):
+        t = np.nextafter(t, np.float32(np.inf if du > 0 else -np.inf))
+    return np.where(t0 == 0, t0, t).astype(np.float32)
+
+
 def verify_tan_test(A=None, B=None, T=None, rcp_ulps=4):
     """Emulate the edge kernel's octant rounding on every integer pair
     0 <= mn <= mx <= 1020 and compare with round(atan(mn / mx) * 128 / pi).
 
     The guess is checked with t moved by +-rcp_ulps binary32 ulps (the
     hardware reciprocal is approximate); the exact test is emulated
-    bit-exactly: mn - mx T_n is formed exactly in double (a 10-bit integer
-    times a binary32 value) and rounded once to binary32, as the fma does.
-    Returns the number of mismatching pairs (0 expected) and the smallest
-    |mn - mx tan(beta_n)| over the pairs.
+    bit-exactly: mn - max(mx, 1) T_n is formed exactly in double (a 10-bit
+    integer times a binary32 value) and rounded once to binary32, as the fma
+    does.  Returns the number of mismatching pairs (0 expected) and the
+    smallest |mn - mx tan(beta_n)| over the pairs with mx > 0.
     """
     if A is None:
         A, B = fit_guess()
@@ -116,28 +133,65 @@ def verify_tan_test(A=None, B=None, T=None, rcp_ulps=4):
         T, _ = tan_table()
     mn, mx = _all_pairs()
     truth = np.floor(np.arctan2(mn, mx) * 128 / np.pi + 0.5).astype(np.int64)
+    mx1 = np.maximum(mx, 1.0)
     bad = 0
     tmin = np.inf
-    t0 = np.where(mx > 0, mn / np.maximum(mx, 1), 0.0).astype(np.float32)
+    t0 = (mn / mx1).astype(np.float32)
     for du in (-rcp_ulps, 0, rcp_ulps):
-        t = t0
-        if du:
-            t = np.nextafter(t0, np.float32(np.inf if du > 0 else -np.inf))
-            for _ in range(abs(du) - 1):
-                t = np.nextafter(t, np.float32(np.inf if du > 0 else -np.inf))
-            t = np.where(t0 == 0, t0, t).astype(np.float32)
-        inner = np.float32(np.float64(t) * np.float64(B) + np.float64(A))
-        y1 = np.float32(np.float64(t) * np.float64(inner) + 1.0)
-        n = np.floor(y1).astype(np.int64)
-        if n.min() < 0 or n.max() > 33:
+        n = _guess_n(_perturbed(t0, du), A, B)
+        if n.min() < 1 or n.max() > 33:
             return -1, 0.0
-        h = np.float32(mn - mx * np.float64(T[n]))  # the fma, rounded once
-        ra = n - 1 + (h > 0)
+        h = np.float32(mn - mx1 * np.float64(T[n]))  # the fma, rounded once
+        if np.any(h == 0):
+            return -1, 0.0
+        ra = n - (h < 0)
         bad += int(np.count_nonzero(ra != truth))
         if du == 0:
             gap = np.abs(mn - mx * np.tan((n - 0.5) * np.pi / 128))
             tmin = float(gap[mx > 0].min())
     return bad, tmin
+
+
+def phase_table(T=None):
+    """The kernel's (octant, n) table: octant o = 4 [gx < 0] + 2 [gy < 0] +
+    [|gy| > |gx|]; entry o * 34 + n holds T_n and the phase bytes for the
+    octant angle n (q_ge) and n - 1 (q_lt)."""
+    if T is None:
+        T, _ = tan_table()
+    q_ge = np.zeros(8 * 34, np.int64)
+    q_lt = np.zeros(8 * 34, np.int64)
+    for o in range(8):
+        sx, sy, sw = (o >> 2) & 1, (o >> 1) & 1, o & 1
+        for n in range(34):
+            for k, dst in ((0, q_ge), (1, q_lt)):
+                ra = n - k
+                q1 = 64 - ra if sw else ra
+                dst[o * 34 + n] = ((128 if sx else 0) + (-q1 if sx != sy else q1)) & 255
+    return np.tile(T, 8), q_ge, q_lt
+
+
+def verify_phase_all(A=None, B=None, T=None, table=None):
+    """Every (gx, gy) in [-1020, 1020]^2 through the emulated kernel Phase
+    (guess, table, exact test) against round(atan2(gy, gx) * 128 / pi) mod
+    256.  Returns the number of mismatches (0 expected)."""
+    if A is None:
+        A, B = fit_guess()
+    tan8, q_ge, q_lt = phase_table(T) if table is None else table
+    g = np.arange(-GMAX, GMAX + 1, dtype=np.float64)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    gx, gy = gx.ravel(), gy.ravel()
+    ax, ay = np.abs(gx), np.abs(gy)
+    mx = np.maximum(np.maximum(ax, ay), 1.0)
+    mn = np.minimum(ax, ay)
+    n = _guess_n((mn / mx).astype(np.float32), A, B)
+    o = 136 * (gx < 0) + 68 * (gy < 0) + 34 * (ay > ax)
+    idx = o + n
+    h = np.float32(mn - mx * np.float64(tan8[idx]))
+    q = np.where(h < 0, q_lt[idx], q_ge[idx])
+    ang = np.arctan2(gy, gx)
+    ang = np.where(ang < 0, ang + 2 * np.pi, ang)
+    truth = np.floor(ang * 128 / np.pi + 0.5).astype(np.int64) % 256
+    return int(np.count_nonzero(q != truth))
 
 
 def write_table_header(path):
@@ -173,5 +227,6 @@ if __name__ == "__main__":
     T, err = tan_table()
     print("largest 1020 |tan - T_n|:", 1020 * np.abs(err).max())
     print("exact test over all integer pairs (mismatches, min gap):", verify_tan_test(A, B, T))
+    print("full phase over all (gx, gy) (mismatches):", verify_phase_all(A, B, T))
     if len(sys.argv) > 1:
         write_table_header(sys.argv[1])

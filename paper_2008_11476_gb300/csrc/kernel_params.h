@@ -81,13 +81,16 @@ struct GenericDesc {
 };
 
 // ---------------------------------------------------------------------------
-// Fused edge group: Gaussian3x3 -> Sobel3x3 -> {Magnitude -> Threshold, Phase}
-// (and the Gaussian3x3-only group, which writes G).
-constexpr int EDGE_TW = 128;  // output tile width (bytes of U8)
-constexpr int EDGE_TH = 30;   // output tile height (1080 = 36 x 30, 2160 = 72 x 30)
-constexpr int EDGE_THREADS = 256;
+// Fused edge group: Gaussian3x3 -> Sobel3x3 -> {Magnitude -> Threshold, Phase}.
+// Tall tiles; each thread slides a 3-row window of input rows and of Gaussian
+// rows down one 8-pixel column strip.
+constexpr int EDGE_TW = 128;               // output tile width (bytes of U8)
+constexpr int EDGE_TH = 120;               // 1080 = 9 x 120, 2160 = 18 x 120, 480 = 4 x 120
+constexpr int EDGE_THREADS = 128;          // 16 column strips x 8 row groups
+constexpr int EDGE_ROWS = EDGE_TH / 8;     // output rows per thread (15)
 constexpr int EDGE_LOAD_W = EDGE_TW + 32;  // TMA box width: 16 B aligned both sides
-constexpr int EDGE_STAGES = 3;             // input boxes in flight per persistent CTA
+constexpr int EDGE_LOAD_H = EDGE_TH + 4;   // two halo rows above and below
+constexpr int EDGE_STAGES = 2;             // input boxes per persistent CTA
 
 // Gaussian3x3 group alone (its own kernel, same parameter block): tall tiles,
 // each thread slides a 3-row window down one 8-pixel column strip.

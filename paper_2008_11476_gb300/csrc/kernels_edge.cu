@@ -1,31 +1,40 @@
 // Fused edge-detection group (Table 2 local and point operators; the edge
 // graph of Listing 1 / the Section 6 benchmarks):
 //
-//   in U8 --Gaussian3x3--> G (on chip) --Sobel3x3--> gx, gy (registers)
+//   in U8 --Gaussian3x3--> G --Sobel3x3--> gx, gy
 //        --Magnitude--> m --Threshold--> mask (U8)      --Phase--> phase (U8)
 //
-// One CTA (256 threads) computes a 128 x 30 output tile:
-//   1. one TMA 2-D load brings the 160 x 34 input box (tile + 2-pixel halo,
-//      widened to 16-byte-aligned columns) into shared memory; the hardware
-//      fills out-of-image bytes with 0, and edge tiles then apply the
-//      Gaussian's border mode to them;
-//   2. G over the tile + 1-pixel halo (130 x 32) is computed in SWAR form: each
-//      32-bit word holds two adjacent pixels as 16-bit lanes, so every add,
-//      shift and funnel shift works on two pixels; G stays in shared memory as
-//      16-bit pixels.  Edge tiles then apply the Sobel's border mode to the G
-//      cells outside the image (REPLICATE reads the replicated *Gaussian*
-//      output, as the node-by-node definition requires);
-//   3. each item is 8 pixels of one row: gx and gy are formed in the same
-//      16-bit-lane form (biased so that no lane goes negative), unpacked to
-//      binary32 by exponent splicing, and the point operators run in binary32
-//      (every value involved is an integer below 2^24, so the float arithmetic
-//      is exact); the U8 results are written with 8-byte stores.
-// Magnitude followed by a binary threshold T is evaluated as
-// gx^2 + gy^2 > T^2 + T, which equals round(sqrt(gx^2 + gy^2)) > T exactly.
+// G, gx, gy and m never leave the SM.  One CTA (128 threads) computes a
+// 128 x 120 output tile from one TMA box of 160 x 124 input bytes (the tile
+// plus a 2-pixel halo, columns widened to 16-byte boundaries).  Thread (q, g)
+// owns the 8-pixel column strip x = x0 + 8q .. x + 7 and the 15 output rows
+// y0 + 15g .. y0 + 15g + 14, and walks down them with two sliding 3-row
+// windows held in registers:
+//   * input rows, each read from shared memory once (three loads) and split
+//     once into 16-bit lanes of pixel pairs;
+//   * Gaussian rows: each G row (the 10 values x - 1 .. x + 8 the Sobel needs,
+//     in five words of pairs (x - 1 + 2j, x + 2j)) is computed once from three
+//     input rows and enters three Sobel rows.
+// Gaussian and Sobel sums run in 16-bit lanes (two pixels per 32-bit add,
+// biased so that no lane goes negative); gx and gy are unpacked to binary32
+// by exponent splicing and the point operators run in binary32, where every
+// value is an exact integer.  Magnitude followed by a binary threshold T is
+// evaluated as gx^2 + gy^2 > T^2 + T, which equals round(sqrt(gx^2 + gy^2)) > T.
+// The mask and phase bytes of a strip row leave in one 8-byte store each (a
+// half-warp writes 128 contiguous bytes).
+//
+// Borders.  The TMA load fills the box cells outside the image with 0; edge
+// tiles then apply the Gaussian's border mode to them.  G rows and columns
+// outside the image take the Sobel's border mode (REPLICATE reads the
+// replicated *Gaussian output*, as the node-by-node definition requires), and
+// G inside the image but outside the Gaussian's valid region is 0; those G
+// rows are rebuilt lane by lane on a slow path that only the threads whose
+// window touches the image edge take.  Outputs outside their valid region
+// are written as 0.
 //
 // The batch kernel runs the same tile code persistently over the tiles of
-// many images (one tensor map per image, in global memory), and issues the
-// TMA load of its next tile as soon as the current input box has been read.
+// many images (one tensor map and parameter block per image) with two boxes
+// in flight per CTA.
 #include "device_common.cuh"
 #include "launchers.h"
 
@@ -35,40 +44,46 @@ namespace {
 using namespace dev;
 
 constexpr int TW = EDGE_TW;          // 128
-constexpr int TH = EDGE_TH;          // 30
+constexpr int TH = EDGE_TH;          // 120
 constexpr int LW = EDGE_LOAD_W;      // 160
-constexpr int IN_ROWS = TH + 4;      // 34
-constexpr int G_ROWS = TH + 2;       // 32
-constexpr int GW = TW + 16;          // G columns x0 - 8 .. x0 + 135
-constexpr uint32_t IN_BYTES = IN_ROWS * LW;
+constexpr int LH = EDGE_LOAD_H;      // 124
+constexpr int ROWS = EDGE_ROWS;      // 15
+constexpr int STAGES = EDGE_STAGES;  // 2
+constexpr uint32_t BOX_BYTES = LW * LH;
+static_assert(EDGE_THREADS == 16 * (TH / ROWS), "16 strips x row groups");
 
 // Kernel modes (template parameter).
 constexpr int M_GAUSS = EDGE_MODE_GAUSS;  // Gaussian3x3 alone (kernels_gauss.cu)
-constexpr int M_MASK_PHASE = 1; // binary threshold mask + phase
-constexpr int M_MASK = 2;       // binary threshold mask only
-constexpr int M_PHASE = 3;      // phase only
-constexpr int M_GENERAL = 4;    // any outputs (magnitude export, range threshold)
+constexpr int M_MASK_PHASE = 1;  // binary threshold mask + phase
+constexpr int M_MASK = 2;        // binary threshold mask only
+constexpr int M_PHASE = 3;       // phase only
+constexpr int M_GENERAL = 4;     // any outputs (magnitude export, range threshold)
 
-constexpr int STAGES = EDGE_STAGES;     // input boxes in flight per CTA (batch kernel)
+using Box = uint8_t[LH][LW];  // image (x0 - 16 + c, y0 - 2 + r)
 
-using InTile = uint8_t[IN_ROWS][LW];    // image (x0 - 16 + c, y0 - 2 + r)
-using GTile = uint16_t[G_ROWS][GW];     // Gaussian (x0 - 8 + k, y0 - 1 + r)
+struct alignas(128) BoxStage {
+    Box b;
+};
 
-struct alignas(128) InStage {
-    InTile b;
+// Phase table entry for octant o = 4 [gx < 0] + 2 [gy < 0] + [|gy| > |gx|]
+// and guess n (entry o * 34 + n): tan((n - 1/2) pi / 128), and the phase byte
+// for the octant angle n (byte 0) and n - 1 (byte 1).
+struct PhaseEntry {
+    float tan;
+    uint32_t q;
 };
 
 template <int NS>
 struct EdgeSmem {
-    InStage in[NS];                     // ring of TMA destinations
-    alignas(16) GTile g;
+    BoxStage in[NS];                    // ring of TMA destinations
     alignas(8) uint64_t bar[NS];
     // batch: parameters and origin of the tiles in flight, in a ring one longer
-    // than the input ring (tile k uses slot k mod (NS + 1), so the slot that
+    // than the box ring (tile k uses slot k mod (NS + 1), so the slot that
     // tile k + NS fills belongs to tile k - 1, which is finished)
     EdgeParams prm[NS + 1];
     int tx0[NS + 1], ty0[NS + 1];
-    float tanb[36];                     // Phase boundary tangents (kPhaseTan)
+    PhaseEntry plut[8 * 34];            // Phase table (build_phase_lut)
+    uint32_t gslow[EDGE_THREADS][5];    // per-thread result of the slow G path
 };
 
 // Lane values of a 16-bit-lane word as binary32, minus a bias, exactly.
@@ -83,14 +98,6 @@ __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2,
     return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
 }
 
-__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
-    return x0 >= 2 && y0 >= 2 && x0 + TW + 2 <= (int)p.W && y0 + TH + 2 <= (int)p.H;
-}
-
-__device__ __forceinline__ bool rect_is_full(const int32_t* r, const EdgeParams& p) {
-    return r[0] == 0 && r[1] == 0 && r[2] == (int)p.W && r[3] == (int)p.H;
-}
-
 // Hardware reciprocal approximation (rcp.approx.ftz.f32, at most 1 ulp off).
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -98,22 +105,57 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// All-ones when a > b, else 0 (one instruction).
+__device__ __forceinline__ uint32_t set_gt(float a, float b) {
+    uint32_t r;
+    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Fill the Phase table (once per CTA).
+__device__ void build_phase_lut(PhaseEntry* lut) {
+    for (int i = threadIdx.x; i < 8 * 34; i += blockDim.x) {
+        const int o = i / 34, n = i - o * 34;
+        const bool sx = (o >> 2) & 1, sy = (o >> 1) & 1, sw = o & 1;
+        uint32_t q[2];
+        for (int k = 0; k < 2; ++k) {
+            const int ra = n - k;                 // octant angle in bins, 0 .. 32
+            const int q1 = sw ? 64 - ra : ra;     // first-quadrant angle
+            q[k] = (uint32_t)((sx ? 128 : 0) + ((sx != sy) ? -q1 : q1)) & 0xFFu;
+        }
+        lut[i].tan = kPhaseTan[n];
+        lut[i].q = q[0] | (q[1] << 8);
+    }
+}
+
+__device__ __forceinline__ float fma_rm(float a, float b, float c) {
+    float r;
+    asm("fma.rm.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Phase from exact integer gradients held in binary32 (gen_phase_poly.py
 // derives and checks every step over all integer gradient pairs): with
 // mn, mx = min, max of |gx|, |gy| and t = mn / mx, the rounded octant angle
 // is n or n - 1 for n = floor(1 + t (A + B t)), and it is n exactly when
-// mn - mx tan((n - 1/2) pi / 128) > 0.  tanb holds those tangents (n = 0..33)
-// in shared memory.  The octant angle then maps to the full turn by the
-// signs of gx, gy and the swap of |gx|, |gy|; the low byte is the phase.
-__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const float* tanb) {
+// mn - mx tan((n - 1/2) pi / 128) > 0.  n comes out of a round-down fma as
+// the low mantissa bits of a number in [1.5 * 2^23, 2^24); the table entry of
+// (octant, n) holds tan((n - 1/2) pi / 128) and the final phase byte for both
+// outcomes, and the sign of the test picks the byte.  The entry index is
+// formed with multiply-adds of sign bits.  gx = gy = 0 gives t = 0, n = 1 and
+// a negative test (mx is raised to 1 there), so phase 0.
+__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const PhaseEntry* lut) {
     const float ax = fabsf(gx), ay = fabsf(gy);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = mn * rcp_approx(fmaxf(mx, 1.0f));  // integers: mx = 0 only when mn = 0
-    const int n = __float2int_rd(fmaf(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 1.0f));  // 1..33
-    const int ra = fmaf(-mx, tanb[n], mn) > 0.0f ? n : n - 1;
-    const int q1 = ay > ax ? 64 - ra : ra;
-    const bool sx = gx < 0.0f, sy = gy < 0.0f;
-    return (uint32_t)((sx ? 128 : 0) + ((sx != sy) ? -q1 : q1));
+    const float mx = fmaxf(fmaxf(ax, ay), 1.0f), mn = fminf(ax, ay);
+    const float t = mn * rcp_approx(mx);
+    const float y = fma_rm(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 12582913.0f);  // 1.5*2^23 + 1
+    int idx = __float_as_int(y) - 0x4B400000;                // n = 1 .. 33
+    idx = (int)(__float_as_uint(gx) >> 31) * 136 + idx;     // + 4 * 34 [gx < 0]
+    idx = (int)(__float_as_uint(gy) >> 31) * 68 + idx;      // + 2 * 34 [gy < 0]
+    idx = (int)set_gt(ay, ax) * -34 + idx;                  // + 34 [|gy| > |gx|]
+    const PhaseEntry e = lut[idx];
+    const float h = fmaf(-mx, e.tan, mn);  // < 0: the octant angle rounds to n - 1
+    return __byte_perm(e.q, 0u, __float_as_uint(h) >> 31);
 }
 
 __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
@@ -125,252 +167,352 @@ __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint
     }
 }
 
-// ---- stage 1: input border -------------------------------------------------------
+__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
+    return x0 >= 2 && y0 >= 2 && x0 + TW + 2 <= (int)p.W && y0 + TH + 2 <= (int)p.H;
+}
 
-__device__ void fix_input_border(InTile& in, const EdgeParams& p, int x0, int y0) {
+// ---- input box border ------------------------------------------------------------
+
+__device__ void fix_input_border(Box& in, const EdgeParams& p, int x0, int y0) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
     const bool cst = p.border_g == HVX_BORDER_CONSTANT;
     const uint8_t cv = (uint8_t)p.cval_g;
-    for_each_outside(IN_ROWS, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
-        int x = x0 - 16 + c, y = y0 - 2 + r;
+    for_each_outside(LH, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
+        const int x = x0 - 16 + c, y = y0 - 2 + r;
         in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
     });
 }
 
-// ---- stage 2: Gaussian in 16-bit lanes ---------------------------------------------
-// Item (r, q): G row r (y = y0 - 1 + r), pixels x = x0 + 8q .. x0 + 8q + 7;
-// group 0 also produces x0 - 1 and group 15 also x0 + 128.
-__device__ void gaussian_stage(const InTile& in, GTile& g, const EdgeParams& p) {
-    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
-    for (int it = threadIdx.x; it < G_ROWS * 16; it += blockDim.x) {
-        const int r = it >> 4, q = it & 15;
-        const int c = 16 + 8 * q;
-        uint32_t V[6];  // vertical sums of pixel pairs (x-2,x-1), (x,x+1) .. (x+8,x+9)
-#pragma unroll
-        for (int dr = 0; dr < 3; ++dr) {
-            const uint8_t* row = in[r + dr];
-            uint2 m = *reinterpret_cast<const uint2*>(row + c);
-            uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
-            uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
-            uint32_t P[6] = {hi_pair(wl), lo_pair(m.x), hi_pair(m.x),
-                             lo_pair(m.y), hi_pair(m.y), lo_pair(wr)};
-#pragma unroll
-            for (int k = 0; k < 6; ++k) V[k] = dr == 0 ? P[k] : V[k] + (dr == 1 ? 2u : 1u) * P[k];
-        }
-        uint32_t Gp[4];
-#pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            uint32_t s = shift_pair(V[j - 1], V[j]) + shift_pair(V[j], V[j + 1]) + 2u * V[j] + rnd;
-            Gp[j - 1] = (s >> 4) & 0x00FF00FFu;
-        }
-        *reinterpret_cast<uint4*>(&g[r][8 + 8 * q]) = make_uint4(Gp[0], Gp[1], Gp[2], Gp[3]);
-    }
-    // The two halo columns x0 - 1 and x0 + 128, one scalar item per row and
-    // side on the first 64 threads (kept out of the loop above, where they
-    // would make every warp diverge).  Each is written as a word together
-    // with the column beyond it set to 0: stage 3 reads those outer lanes
-    // (cols 6, 137) as part of its pair loads, and a zero lane cannot carry
-    // into its neighbour in the 16-bit-lane arithmetic.
-    if (threadIdx.x < 2 * G_ROWS) {
-        const int r = threadIdx.x >> 1, side = threadIdx.x & 1;
-        const int c = side ? 16 + TW : 15;  // input column of the halo pixel
-        uint32_t s = rnd & 0xFFFFu;
-#pragma unroll
-        for (int dr = 0; dr < 3; ++dr) {
-            const uint32_t w = dr == 1 ? 2u : 1u;
-            s += w * (in[r + dr][c - 1] + 2u * in[r + dr][c] + in[r + dr][c + 1]);
-        }
-        if (side)
-            *reinterpret_cast<uint32_t*>(&g[r][136]) = s >> 4;
-        else
-            *reinterpret_cast<uint32_t*>(&g[r][6]) = (s >> 4) << 16;
-    }
+// ---- Gaussian rows ---------------------------------------------------------------
+
+// Pixel pairs (x - 2, x - 1), (x, x + 1) .. (x + 8, x + 9) of one box row as
+// 16-bit lanes, for the strip starting at box column c (= x - x0 + 16).
+__device__ __forceinline__ void load_pairs(const uint8_t* row, int c, uint32_t P[6]) {
+    const uint2 m = *reinterpret_cast<const uint2*>(row + c);
+    const uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
+    const uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
+    P[0] = hi_pair(wl);
+    P[1] = lo_pair(m.x);
+    P[2] = hi_pair(m.x);
+    P[3] = lo_pair(m.y);
+    P[4] = hi_pair(m.y);
+    P[5] = lo_pair(wr);
 }
 
-// G cells: zero inside the image but outside the Gaussian's valid region; the
-// Sobel's border mode outside the image.  Edge tiles only.
-__device__ void fix_g_border(GTile& g, const EdgeParams& p, int x0, int y0) {
+// G at x - 1 .. x + 8 of one row from the pair words of the input rows above
+// (a), at (b) and below (c): word j holds (x - 1 + 2j, x + 2j) in 16-bit lanes.
+// Lane sums stay below 16 * 255 + 8 < 2^12, so lanes never carry.
+__device__ __forceinline__ void g_row(const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                                      uint32_t rnd, uint32_t* G) {
+    uint32_t V[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) V[k] = a[k] + 2u * b[k] + c[k];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        G[j] = ((V[j] + V[j + 1] + rnd + 2u * shift_pair(V[j], V[j + 1])) >> 4) & 0x00FF00FFu;
+}
+
+// G row yq (x - 1 .. x + 8) as the Sobel reads it, for a strip whose window
+// leaves the Gaussian's valid region: outside the image the Sobel's border
+// mode (REPLICATE: the Gaussian output at the clamped position; CONSTANT: the
+// constant; UNDEFINED: 0, read by no valid output), inside the image but
+// outside the valid region 0, else the Gaussian of the border-fixed box.
+// The result goes to the thread's slot G in shared memory (the caller copies
+// it into registers), so the call needs no local-memory array.
+__device__ __noinline__ void g_row_edge(const Box& in, const EdgeParams& p, int x, int x0, int y0,
+                                        int yq, uint32_t rnd, uint32_t* G) {
     const int W = p.W, H = p.H;
-    constexpr int COLS = TW + 2;  // k = 7 .. 136, x = x0 - 1 .. x0 + 128
-    if (!rect_is_full(p.gvalid, p)) {
-        for (int i = threadIdx.x; i < G_ROWS * COLS; i += blockDim.x) {
-            int r = i / COLS, k = 7 + (i - r * COLS);
-            int x = x0 - 8 + k, y = y0 - 1 + r;
-            if (x >= 0 && x < W && y >= 0 && y < H && !in_rect(p.gvalid, x, y)) g[r][k] = 0;
+    const uint32_t cv = (uint32_t)(p.cval_s & 0xFF);
+    int yy = yq;
+    if (yy < 0 || yy >= H) {
+        if (p.border_s != HVX_BORDER_REPLICATE) {
+            const uint32_t v = p.border_s == HVX_BORDER_CONSTANT ? cv * 0x00010001u : 0u;
+            for (int j = 0; j < 5; ++j) G[j] = v;
+            return;
         }
-        __syncthreads();
+        yy = clampi(yy, 0, H - 1);
     }
-    if (p.border_s == HVX_BORDER_UNDEFINED) return;
-    const bool cst = p.border_s == HVX_BORDER_CONSTANT;
-    const uint16_t cv = (uint16_t)(p.cval_s & 0xFF);
-    for_each_outside(G_ROWS, COLS, x0 - 1, y0 - 1, W, H, [&](int r, int c) {
-        int x = x0 - 1 + c, y = y0 - 1 + r;
-        g[r][7 + c] =
-            cst ? cv : g[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 8)];
-    });
+    const bool row_ok = yy >= p.gvalid[1] && yy < p.gvalid[3];
+    const uint8_t* r0 = in[yy - y0 + 1];  // image rows yy - 1, yy, yy + 1
+    const uint8_t* r1 = in[yy - y0 + 2];
+    const uint8_t* r2 = in[yy - y0 + 3];
+    uint32_t g[10];
+    for (int l = 0; l < 10; ++l) {
+        int xs = x - 1 + l;
+        if (xs < 0 || xs >= W) {
+            if (p.border_s != HVX_BORDER_REPLICATE) {
+                g[l] = p.border_s == HVX_BORDER_CONSTANT ? cv : 0u;
+                continue;
+            }
+            xs = clampi(xs, 0, W - 1);
+        }
+        if (!row_ok || xs < p.gvalid[0] || xs >= p.gvalid[2]) {
+            g[l] = 0;
+            continue;
+        }
+        const int c = xs - x0 + 16;
+        const uint32_t s = (r0[c - 1] + 2u * r0[c] + r0[c + 1]) +
+                           2u * (r1[c - 1] + 2u * r1[c] + r1[c + 1]) +
+                           (r2[c - 1] + 2u * r2[c] + r2[c + 1]) + (rnd & 0xFFFFu);
+        g[l] = s >> 4;
+    }
+    for (int j = 0; j < 5; ++j) G[j] = g[2 * j] | (g[2 * j + 1] << 16);
 }
 
-// ---- stage 3: Sobel + point operators ------------------------------------------------
+// How a strip forms its G rows (fixed for a tile).  When the Sobel's border is
+// UNDEFINED no valid output reads G outside the Gaussian's valid region, so
+// every row is formed the fast way.  Otherwise rows outside the valid rows
+// take the scalar path, and so do rows of strips whose columns leave the valid
+// columns -- except when the valid region is the whole image: then only lanes
+// outside the image differ, and they are patched in registers.
+struct GPolicy {
+    int gv1, gv3;      // valid rows of G
+    bool sobel_undef;
+    int colmode;       // 0: no column fix, 1: patch lanes outside the image, 2: scalar path
+    bool rep;          // Sobel border REPLICATE (else CONSTANT)
+    bool left;         // x == 0: lane 0 (x - 1) is outside the image
+    int L;             // lanes 0 .. L - 1 are inside the image
+    uint32_t cv;       // Sobel border constant
+};
 
-__device__ __forceinline__ void load_g_row(const uint16_t* row, int k, uint32_t P[6]) {
-    uint4 m = *reinterpret_cast<const uint4*>(row + k);
-    P[0] = *reinterpret_cast<const uint32_t*>(row + k - 2);
-    P[1] = m.x;
-    P[2] = m.y;
-    P[3] = m.z;
-    P[4] = m.w;
-    P[5] = *reinterpret_cast<const uint32_t*>(row + k + 8);
+__device__ __forceinline__ void patch_cols(const GPolicy& gp, uint32_t* G) {
+    if (gp.left) G[0] = (G[0] & 0xFFFF0000u) | (gp.rep ? (G[0] >> 16) : gp.cv);
+    if (gp.L < 10) {
+        uint32_t v = gp.cv;
+        if (gp.rep) {  // the last lane inside the image
+            const int k = gp.L - 1;
+            uint32_t w = G[0];
+#pragma unroll
+            for (int j = 1; j < 5; ++j) w = (k >> 1) == j ? G[j] : w;
+            v = (k & 1) ? (w >> 16) : (w & 0xFFFFu);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            if (2 * j >= gp.L)
+                G[j] = v * 0x00010001u;
+            else if (2 * j + 1 >= gp.L)
+                G[j] = (G[j] & 0xFFFFu) | (v << 16);
+        }
+    }
 }
 
-// All-ones when a > b, else 0 (one instruction).
-__device__ __forceinline__ uint32_t set_gt(float a, float b) {
-    uint32_t r;
-    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
-    return r;
+// G row yg from the input pair rows a, b, c (the rows yg - 1, yg, yg + 1).
+__device__ __forceinline__ void g_row_any(const GPolicy& gp, const Box& in, const EdgeParams& p,
+                                          int x, int x0, int y0, int yg, uint32_t rnd,
+                                          uint32_t* gslow, const uint32_t* a, const uint32_t* b,
+                                          const uint32_t* c, uint32_t* G) {
+    const bool row_slow = !gp.sobel_undef && (yg < gp.gv1 || yg >= gp.gv3);
+    if (!row_slow && gp.colmode < 2) {
+        g_row(a, b, c, rnd, G);
+        if (gp.colmode == 1) patch_cols(gp, G);
+    } else {
+        g_row_edge(in, p, x, x0, y0, yg, rnd, gslow);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) G[j] = gslow[j];
+    }
 }
+
+// ---- Sobel + point operators of one output row --------------------------------------
+
+// gx, gy at x .. x + 7 from the G rows above (a), at (b) and below (c).
+// Lanes: vs <= 1020, dy = c - a + 255 in [0, 510]; gx + 1024 and gy + 1020
+// are in [4, 2044].
+__device__ __forceinline__ void sobel8(const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                                       float* gx, float* gy) {
+    uint32_t vs[5], dy[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        vs[j] = a[j] + 2u * b[j] + c[j];
+        dy[j] = c[j] + 0x00FF00FFu - a[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t gxp = vs[j + 1] + 0x04000400u - vs[j];
+        const uint32_t gyp = dy[j] + dy[j + 1] + 2u * shift_pair(dy[j], dy[j + 1]);
+        gx[2 * j] = lane_lo_f(gxp, 1024.0f);
+        gx[2 * j + 1] = lane_hi_f(gxp, 1024.0f);
+        gy[2 * j] = lane_lo_f(gyp, 1020.0f);
+        gy[2 * j + 1] = lane_hi_f(gyp, 1020.0f);
+    }
+}
+
+// Per-thread view of a tile's parameters, held in registers.
+struct RowCtx {
+    const PhaseEntry* plut;
+    uint32_t* gslow;    // this thread's slow-path slot in shared memory
+    uint8_t* mask;
+    uint8_t* phase;
+    size_t mask_pitch, phase_pitch;
+    float s_thr;
+    uint32_t tvx, fvx;  // mask bytes: (c & tvx) ^ fvx from all-ones / zero compares
+    int W, x;
+    bool full;          // every output of the strip is inside its valid region
+};
 
 __device__ __forceinline__ void store8_words(uint8_t* row, int x, int W, uint32_t lo, uint32_t hi) {
     if (x + 8 <= W) {
         *reinterpret_cast<uint2*>(row + x) = make_uint2(lo, hi);
     } else {
-        for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (uint8_t)((j < 4 ? lo : hi) >> (8 * (j & 3)));
+        for (int j = 0; j < 8 && x + j < W; ++j)
+            row[x + j] = (uint8_t)((j < 4 ? lo : hi) >> (8 * (j & 3)));
     }
 }
 
 template <int MODE>
-__device__ void sobel_point_stage(const GTile& g, const EdgeParams& p, int x0, int y0,
-                                  bool interior, const float* tanb) {
-    const float s_thr = (float)p.s_thr;
-    const bool full = interior || rect_is_full(p.valid, p);
-    const int W = p.W, H = p.H;
-    // mask bytes from all-ones / zero compare results: (c & (tv ^ fv)) ^ fv
-    const uint32_t tvx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
-    const uint32_t fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
+__device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p, const float* gx,
+                                          const float* gy, int y) {
     constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK;
     constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
-    uint8_t* const mask = p.mask;
-    uint8_t* const phase = p.phase;
-    const size_t mask_pitch = p.mask_pitch, phase_pitch = p.phase_pitch;
-#pragma unroll 1
-    for (int it = threadIdx.x; it < TH * 16; it += blockDim.x) {
-        const int r = it >> 4, s8 = it & 15;
-        const int y = y0 + r, x = x0 + 8 * s8;
-        if (y >= H || x >= W) continue;
-        const int k = 8 + 8 * s8;
-        uint32_t A[6], B[6], C[6];
-        load_g_row(g[r], k, A);
-        load_g_row(g[r + 1], k, B);
-        load_g_row(g[r + 2], k, C);
-        uint32_t vs[6], dy[6];
+    uint32_t mk[8], ph[8];
+    int mg[8];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            vs[j] = A[j] + 2u * B[j] + C[j];          // <= 1020 per lane
-            dy[j] = C[j] + 0x00FF00FFu - A[j];        // gy part + 255 per lane
+    for (int i = 0; i < 8; ++i) {
+        mk[i] = ph[i] = 0u;
+        mg[i] = 0;
+        if (kMask) mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), cx.s_thr);
+        if (kPhase) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
+        if (MODE == M_GENERAL) {
+            const int ix = (int)gx[i], iy = (int)gy[i];
+            mg[i] = magnitude_s16(ix, iy);
+            if (cx.mask) {
+                bool t;
+                if (!p.thr_general)
+                    t = ix * ix + iy * iy > p.s_thr;
+                else
+                    t = p.thr_type == HVX_THRESHOLD_BINARY ? mg[i] > p.thr_lo
+                                                           : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
+                mk[i] = t ? 0xFFFFFFFFu : 0u;
+            }
+            if (cx.phase) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
         }
-        float gx[8], gy[8];
-#pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            uint32_t gxp = shift_pair(vs[j], vs[j + 1]) + 0x04000400u - shift_pair(vs[j - 1], vs[j]);
-            uint32_t gyp = shift_pair(dy[j - 1], dy[j]) + 2u * dy[j] + shift_pair(dy[j], dy[j + 1]);
-            gx[2 * j - 2] = lane_lo_f(gxp, 1024.0f);
-            gx[2 * j - 1] = lane_hi_f(gxp, 1024.0f);
-            gy[2 * j - 2] = lane_lo_f(gyp, 1020.0f);
-            gy[2 * j - 1] = lane_hi_f(gyp, 1020.0f);
-        }
-        uint32_t mk[8], ph[8];
-        int mg[8];
+    }
+    const bool want_mask = kMask || (MODE == M_GENERAL && cx.mask);
+    const bool want_phase = kPhase || (MODE == M_GENERAL && cx.phase);
+    const int x = cx.x;
+    if (cx.full) {
+        if (want_mask)
+            store8_words(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W,
+                         (pack4(mk[0], mk[1], mk[2], mk[3]) & cx.tvx) ^ cx.fvx,
+                         (pack4(mk[4], mk[5], mk[6], mk[7]) & cx.tvx) ^ cx.fvx);
+        if (want_phase)
+            store8_words(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W,
+                         pack4(ph[0], ph[1], ph[2], ph[3]), pack4(ph[4], ph[5], ph[6], ph[7]));
+    } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            mk[i] = ph[i] = 0u;
-            mg[i] = 0;
-            if (kMask) mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), s_thr);
-            if (kPhase) ph[i] = phase_from_float(gx[i], gy[i], tanb);
-            if (MODE == M_GENERAL) {
-                int ix = (int)gx[i], iy = (int)gy[i];
-                mg[i] = magnitude_s16(ix, iy);
-                if (mask) {
-                    bool t;
-                    if (!p.thr_general)
-                        t = ix * ix + iy * iy > p.s_thr;
-                    else
-                        t = p.thr_type == HVX_THRESHOLD_BINARY
-                                ? mg[i] > p.thr_lo
-                                : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
-                    mk[i] = t ? 0xFFFFFFFFu : 0u;
-                }
-                if (phase) ph[i] = phase_from_float(gx[i], gy[i], tanb);
+            mk[i] = (mk[i] & cx.tvx) ^ cx.fvx;
+            if (!in_rect(p.valid, x + i, y)) {
+                mk[i] = 0u;
+                ph[i] = 0u;
+                mg[i] = 0;
             }
         }
-        const bool want_mask = kMask || (MODE == M_GENERAL && mask);
-        const bool want_phase = kPhase || (MODE == M_GENERAL && phase);
-        if (full) {
-            if (want_mask)
-                store8_words(mask + (size_t)y * mask_pitch, x, W,
-                             (pack4(mk[0], mk[1], mk[2], mk[3]) & tvx) ^ fvx,
-                             (pack4(mk[4], mk[5], mk[6], mk[7]) & tvx) ^ fvx);
-            if (want_phase)
-                store8_words(phase + (size_t)y * phase_pitch, x, W,
-                             pack4(ph[0], ph[1], ph[2], ph[3]), pack4(ph[4], ph[5], ph[6], ph[7]));
+        if (want_mask) store8_u8(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W, mk);
+        if (want_phase) store8_u8(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W, ph);
+    }
+    if (MODE == M_GENERAL && p.mag) {
+        int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
+                                                  (size_t)y * p.mag_pitch);
+        if (x + 8 <= cx.W) {
+            *reinterpret_cast<uint4*>(row + x) =
+                make_uint4((mg[0] & 0xFFFF) | ((uint32_t)mg[1] << 16),
+                           (mg[2] & 0xFFFF) | ((uint32_t)mg[3] << 16),
+                           (mg[4] & 0xFFFF) | ((uint32_t)mg[5] << 16),
+                           (mg[6] & 0xFFFF) | ((uint32_t)mg[7] << 16));
         } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                mk[i] = (mk[i] & tvx) ^ fvx;
-                if (!in_rect(p.valid, x + i, y)) {
-                    mk[i] = 0u;
-                    ph[i] = 0u;
-                    mg[i] = 0;
-                }
-            }
-            if (want_mask) store8_u8(mask + (size_t)y * mask_pitch, x, W, mk);
-            if (want_phase) store8_u8(phase + (size_t)y * phase_pitch, x, W, ph);
-        }
-        if (MODE == M_GENERAL && p.mag) {
-            int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
-                                                      (size_t)y * p.mag_pitch);
-            if (x + 8 <= W) {
-                *reinterpret_cast<uint4*>(row + x) =
-                    make_uint4((mg[0] & 0xFFFF) | ((uint32_t)mg[1] << 16),
-                               (mg[2] & 0xFFFF) | ((uint32_t)mg[3] << 16),
-                               (mg[4] & 0xFFFF) | ((uint32_t)mg[5] << 16),
-                               (mg[6] & 0xFFFF) | ((uint32_t)mg[7] << 16));
-            } else {
-                for (int j = 0; j < 8 && x + j < W; ++j) row[x + j] = (int16_t)mg[j];
-            }
+            for (int j = 0; j < 8 && x + j < cx.W; ++j) row[x + j] = (int16_t)mg[j];
         }
     }
 }
 
-// One tile after its input box has landed in `in`.  `prefetch` runs on warp
-// 0 as soon as `in` is no longer read (after the Gaussian stage), so that the
-// box can be refilled while the rest of the tile is computed.
-template <int MODE, class Prefetch>
-__device__ void edge_tile_body(InTile& in, GTile& g, const EdgeParams& p, int x0, int y0,
-                               const float* tanb, Prefetch prefetch) {
-    const bool interior = tile_is_interior(p, x0, y0);
-    if (!interior) {
-        fix_input_border(in, p, x0, y0);
-        __syncthreads();
-    }
-    gaussian_stage(in, g, p);
-    __syncthreads();
-    if (threadIdx.x < 32) prefetch();
-    if (!interior) {
-        fix_g_border(g, p, x0, y0);
-        __syncthreads();
-    }
-    sobel_point_stage<MODE>(g, p, x0, y0, interior, tanb);
-    __syncthreads();
+// ---- one tile ------------------------------------------------------------------------
+
+// One output row y of the strip: load input row y + 2 into Pn, form G row y + 1
+// into Gc from (Pa, Pb, Pn), then Sobel over (Ga, Gb, Gc) and the point ops.
+template <int MODE>
+__device__ __forceinline__ void edge_row(const RowCtx& cx, const GPolicy& gp, const EdgeParams& p,
+                                         const Box& in, const uint8_t* in_row, int c, int x0,
+                                         int y0, uint32_t rnd, const uint32_t* Pa,
+                                         const uint32_t* Pb, uint32_t* Pn, const uint32_t* Ga,
+                                         const uint32_t* Gb, uint32_t* Gc, int y) {
+    load_pairs(in_row, c, Pn);
+    g_row_any(gp, in, p, cx.x, x0, y0, y + 1, rnd, cx.gslow, Pa, Pb, Pn, Gc);
+    float gx[8], gy[8];
+    sobel8(Ga, Gb, Gc, gx, gy);
+    point_row<MODE>(cx, p, gx, gy, y);
 }
 
-__device__ __forceinline__ void issue_box(InTile& in, uint64_t* bar, const CUtensorMap* map, int x0,
+// One tile after its box has landed (and, on edge tiles, been border-fixed).
+template <int MODE>
+__device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, int x0, int y0,
+                                          bool interior, const PhaseEntry* plut,
+                                          uint32_t (*gslow)[5]) {
+    const int q = threadIdx.x & 15, gi = threadIdx.x >> 4;
+    const int W = p.W, H = p.H;
+    const int x = x0 + 8 * q, yb = y0 + ROWS * gi;
+    if (x >= W || yb >= H) return;
+    RowCtx cx;
+    cx.plut = plut;
+    cx.gslow = gslow[threadIdx.x];
+    cx.mask = p.mask;
+    cx.phase = p.phase;
+    cx.mask_pitch = p.mask_pitch;
+    cx.phase_pitch = p.phase_pitch;
+    cx.s_thr = (float)p.s_thr;
+    cx.tvx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
+    cx.fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
+    cx.W = W;
+    cx.x = x;
+    cx.full = interior || rect_full(p.valid, W, H);
+    const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
+    GPolicy gp;
+    gp.gv1 = p.gvalid[1];
+    gp.gv3 = p.gvalid[3];
+    gp.sobel_undef = p.border_s == HVX_BORDER_UNDEFINED;
+    const bool cols_ok = x - 1 >= p.gvalid[0] && x + 8 < p.gvalid[2];
+    gp.colmode = (gp.sobel_undef || cols_ok) ? 0 : rect_full(p.gvalid, W, H) ? 1 : 2;
+    gp.rep = p.border_s == HVX_BORDER_REPLICATE;
+    gp.left = x == 0;
+    gp.L = min(10, W - x + 1);
+    gp.cv = (uint32_t)(p.cval_s & 0xFF);
+    const int c = 16 + 8 * q;
+    const uint8_t* row = &in[ROWS * gi][0];  // input row yb - 2
+    // prologue: G rows yb - 1 and yb
+    uint32_t P0[6], P1[6], P2[6], G0[5], G1[5], G2[5];
+    load_pairs(row, c, P1);           // yb - 2
+    load_pairs(row + LW, c, P2);      // yb - 1
+    load_pairs(row + 2 * LW, c, P0);  // yb
+    g_row_any(gp, in, p, x, x0, y0, yb - 1, rnd, cx.gslow, P1, P2, P0, G0);
+    load_pairs(row + 3 * LW, c, P1);  // yb + 1
+    g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
+    // rows: P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y); the
+    // windows rotate with period 3, so three rows per trip keep them in place
+    const int n = min(ROWS, H - yb);
+    const uint8_t* r = row + 4 * LW;  // input row yb + 2
+#pragma unroll 1
+    for (int i = 0; i < n; i += 3) {
+        edge_row<MODE>(cx, gp, p, in, r, c, x0, y0, rnd, P0, P1, P2, G0, G1, G2, yb + i);
+        if (i + 1 >= n) break;
+        edge_row<MODE>(cx, gp, p, in, r + LW, c, x0, y0, rnd, P1, P2, P0, G1, G2, G0,
+                       yb + i + 1);
+        if (i + 2 >= n) break;
+        edge_row<MODE>(cx, gp, p, in, r + 2 * LW, c, x0, y0, rnd, P2, P0, P1, G2, G0, G1,
+                       yb + i + 2);
+        r += 3 * LW;
+    }
+}
+
+// ---- kernels -------------------------------------------------------------------------
+
+__device__ __forceinline__ void issue_box(Box& in, uint64_t* bar, const CUtensorMap* map, int x0,
                                           int y0) {
-    mbar_arrive_expect_tx(bar, IN_BYTES);
+    mbar_arrive_expect_tx(bar, BOX_BYTES);
     tma_load_2d(&in[0][0], map, bar, x0 - 16, y0 - 2);
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(EDGE_THREADS, 4)
+__global__ void __launch_bounds__(EDGE_THREADS)
     edge_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
     __shared__ EdgeSmem<1> sm;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
@@ -378,22 +520,21 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4)
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
-    if (threadIdx.x < 34) sm.tanb[threadIdx.x] = kPhaseTan[threadIdx.x];
+    build_phase_lut(sm.plut);
     __syncthreads();
     if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
-    if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
-    edge_tile_body<MODE>(sm.in[0].b, sm.g, p, x0, y0, sm.tanb, [] {});
+    // every thread leaves together when the (bounded) wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(&sm.bar[0], 0, p.err))) return;
+    const bool interior = tile_is_interior(p, x0, y0);
+    if (!interior) {
+        fix_input_border(sm.in[0].b, p, x0, y0);
+        __syncthreads();
+    }
+    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior, sm.plut, sm.gslow);
 }
 
-__device__ __forceinline__ void tile_origin(const EdgeParams& p, int t, int& x0, int& y0) {
-    int tiles_x = (p.W + TW - 1) / TW;
-    int ty = t / tiles_x;
-    x0 = (t - ty * tiles_x) * TW;
-    y0 = ty * TH;
-}
-
-// Warp 0: stage the parameters and origin of batch tile t in parameter slot
-// ps and start the TMA load of its input box into ring stage s.
+// Warp 0: stage the parameters and origin of batch tile t in slot ps and
+// start the TMA load of its box into stage s.
 __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, int s,
                                            int ps, int t) {
     const int lane = threadIdx.x & 31;
@@ -405,8 +546,10 @@ __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatch
     for (int i = lane; i < (int)(sizeof(EdgeParams) / 4); i += 32) dst[i] = __ldg(src + i);
     __syncwarp();
     if (lane == 0) {
-        int x0, y0;
-        tile_origin(sm.prm[ps], t - __ldg(d.tile_start + img), x0, y0);
+        const int tiles_x = (sm.prm[ps].W + TW - 1) / TW;
+        const int local = t - __ldg(d.tile_start + img);
+        const int ty = local / tiles_x;
+        const int x0 = (local - ty * tiles_x) * TW, y0 = ty * TH;
         sm.tx0[ps] = x0;
         sm.ty0[ps] = y0;
         tensormap_acquire(&d.maps[img]);
@@ -416,10 +559,12 @@ __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatch
 }
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
-// CTA lives in ring stage k mod STAGES, so STAGES input boxes are in flight
-// while one is computed.  Each tile's parameters come from shared memory.
+// CTA lives in box stage k mod STAGES, so the next box loads while one is
+// computed.  Each tile's parameters come from shared memory.  A wait that
+// runs out (bounded, about a second) records the error and ends the CTA,
+// after thread 0 has waited (bounded) for the copies still in flight.
 template <int MODE>
-__global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeBatchDesc d) {
+__global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatchDesc d) {
     __shared__ EdgeSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
@@ -433,9 +578,8 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeB
             const int t = first + s * (int)gridDim.x;
             if (t < d.total_tiles) issue_tile(sm, d, s, s, t);
         }
-    } else if (threadIdx.x < 32 + 34) {
-        sm.tanb[threadIdx.x - 32] = kPhaseTan[threadIdx.x - 32];
     }
+    build_phase_lut(sm.plut);
     __syncthreads();
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
@@ -443,14 +587,27 @@ __global__ void __launch_bounds__(EDGE_THREADS, 4) edge_batch_kernel(const EdgeB
         const int ps = k % (STAGES + 1);
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
         const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
-        if (__syncthreads_or(!ok)) return;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0)  // tiles k + 1 .. k + STAGES - 1 may still be loading
+                for (int j = 1; j < STAGES; ++j)
+                    if (t + j * (int)gridDim.x < d.total_tiles)
+                        mbar_wait_bounded(&sm.bar[(k + j) % STAGES],
+                                          (uint32_t)((k + j) / STAGES) & 1u, nullptr);
+            return;
+        }
         const EdgeParams& p = sm.prm[ps];
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
-        const int tn = t + STAGES * (int)gridDim.x;  // the next tile of this stage
-        const int pn = (k + STAGES) % (STAGES + 1);
-        edge_tile_body<MODE>(sm.in[s].b, sm.g, p, x0, y0, sm.tanb, [&] {
-            if (tn < d.total_tiles) issue_tile(sm, d, s, pn, tn);
-        });
+        const bool interior = tile_is_interior(p, x0, y0);
+        if (!interior) {
+            fix_input_border(sm.in[s].b, p, x0, y0);
+            __syncthreads();
+        }
+        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior, sm.plut, sm.gslow);
+        __syncthreads();  // box s is no longer read
+        if (threadIdx.x < 32) {
+            const int tn = t + STAGES * (int)gridDim.x;
+            if (tn < d.total_tiles) issue_tile(sm, d, s, (k + STAGES) % (STAGES + 1), tn);
+        }
     }
 }
 

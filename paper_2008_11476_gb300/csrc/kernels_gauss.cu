@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(GAUSS_THREADS)
     }
     __syncthreads();
     if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
-    if (!mbar_wait_bounded(&sm.bar[0], 0, p.err)) return;
+    // every thread leaves together when the (bounded) wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(&sm.bar[0], 0, p.err))) return;
     const bool interior = tile_is_interior(p, x0, y0);
     if (!interior) {
         fix_box_border(sm.in[0].b, p, x0, y0);
@@ -201,7 +202,9 @@ __device__ __forceinline__ void issue_tile(GaussSmem<STAGES>& sm, const EdgeBatc
 }
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
-// CTA lives in box stage k mod STAGES.
+// CTA lives in box stage k mod STAGES.  A wait that runs out (bounded, about a
+// second) records the error and ends the CTA, after thread 0 has waited
+// (bounded) for the copies still in flight.
 __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBatchDesc d) {
     __shared__ GaussSmem<STAGES> sm;
     const int first = blockIdx.x;
@@ -224,7 +227,14 @@ __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBa
         const int ps = k % (STAGES + 1);
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
         const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
-        if (__syncthreads_or(!ok)) return;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0)  // tiles k + 1 .. k + STAGES - 1 may still be loading
+                for (int j = 1; j < STAGES; ++j)
+                    if (t + j * (int)gridDim.x < d.total_tiles)
+                        mbar_wait_bounded(&sm.bar[(k + j) % STAGES],
+                                          (uint32_t)((k + j) / STAGES) & 1u, nullptr);
+            return;
+        }
         const EdgeParams& p = sm.prm[ps];
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const bool interior = tile_is_interior(p, x0, y0);

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
         mbar_arrive_expect_tx(&sm.bar, IN_BYTES);
         tma_load_2d(&sm.in[0][0], &tmap, &sm.bar, x0 - 16, y0 - 3);
     }
-    if (!mbar_wait_bounded(&sm.bar, 0, p.err)) return;
+    // every thread leaves together when the (bounded) wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(&sm.bar, 0, p.err))) return;
     const bool interior = interior_tile(p, x0, y0);
 
     // 1. the Sobel's border mode on input bytes outside the image

@@ -155,7 +155,7 @@ extern "C" hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t 
         e.err = d_err;
         cuuint64_t dims[2] = {f.width, f.height};
         cuuint64_t strides[1] = {f.in_pitch};
-        cuuint32_t box[2] = {EDGE_LOAD_W, EDGE_TH + 4};
+        cuuint32_t box[2] = {EDGE_LOAD_W, EDGE_LOAD_H};
         cuuint32_t estr[2] = {1, 1};
         if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(f.in), dims,
                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

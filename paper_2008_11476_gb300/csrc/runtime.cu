@@ -193,7 +193,7 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
             e.thr_general = 1;
         }
     }
-    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_TH + 4);
+    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_LOAD_H);
 }
 
 hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {

@@ -78,7 +78,7 @@ def run_edge(ctx, img, border, cval=0, fusion=True, want_mag=False, rounding=0, 
     return res, kinds
 
 
-@pytest.mark.parametrize("w,h", SIZES + [(1920, 1080)])
+@pytest.mark.parametrize("w,h", SIZES + [(385, 361), (1920, 1080)])
 @pytest.mark.parametrize("border", BORDERS)
 def test_edge_graph_fused_and_plain(ctx, w, h, border):
     img = synth.rects_noise(w, h, seed=2)
@@ -94,6 +94,27 @@ def test_edge_graph_fused_and_plain(ctx, w, h, border):
     np.testing.assert_array_equal(ph2, ph)
     np.testing.assert_array_equal(mk2, mk)
     np.testing.assert_array_equal(mg2, mg)
+
+
+# the fused kernel's specialisations (mask + phase, mask only, phase only) on
+# sizes with several ragged 128 x 120 tiles in both directions
+@pytest.mark.parametrize("w,h", [(131, 37), (385, 361), (1000, 250)])
+@pytest.mark.parametrize("border", BORDERS)
+def test_edge_output_modes(ctx, w, h, border):
+    img = synth.rects_noise(w, h, seed=5 + w)
+    ref_ph, ref_mk = O.edge_graph(img, B_ORC[border], 9, O.ROUND_ZERO, 100)
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    for want_ph, want_mk in ((True, True), (False, True), (True, False)):
+        ph = PG.empty(ctx, w, h, H.HVX_DF_U8) if want_ph else None
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8) if want_mk else None
+        g = PG.edge_graph(ctx, inp, ph, mk, border=border, cval=9)
+        assert PG.kernel_kinds(g) == ["fused_edge_tma"]
+        H.hvxProcessGraph(g)
+        if want_ph:
+            np.testing.assert_array_equal(PG.download(ph), ref_ph)
+        if want_mk:
+            np.testing.assert_array_equal(PG.download(mk), ref_mk)
+        H.hvxReleaseGraph(g)
 
 
 @pytest.mark.parametrize("thr", [-5, 0, 1, 100, 1443, 40000])

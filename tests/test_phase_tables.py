@@ -29,6 +29,21 @@ def test_tan_test_exact_over_all_integer_pairs():
     assert gap > 3e-5  # smallest |mn - mx tan(beta_n)| over all pairs
 
 
+def test_phase_all_gradient_pairs():
+    # the kernel's whole Phase path (guess, octant table, exact test) on every
+    # (gx, gy) in [-1020, 1020]^2 against round(atan2(gy, gx) * 128 / pi) mod 256
+    assert _gen().verify_phase_all() == 0
+
+
+def test_planted_octant_table_error_is_caught():
+    g = _gen()
+    tan8, q_ge, q_lt = g.phase_table()
+    bad = q_ge.copy()
+    bad[5 * 34 + 7] = (bad[5 * 34 + 7] + 1) % 256  # one octant entry off by one bin
+    assert g.verify_phase_all(table=(tan8, bad, q_lt)) > 0
+    assert g.verify_phase_all(table=(tan8, q_lt, q_ge)) > 0  # outcomes swapped
+
+
 def test_planted_table_error_is_caught():
     g = _gen()
     T, _ = g.tan_table()
