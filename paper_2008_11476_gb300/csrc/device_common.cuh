@@ -60,6 +60,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Bulk copy (no tensor map) of `bytes` from global to shared memory,
+// signalled on `bar`; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -307,12 +317,24 @@ __device__ __forceinline__ uint32_t shift_pair(uint32_t a, uint32_t b) {
 }
 
 // Batch tile t -> image: the last i with tile_start[i] <= t (binary search
-// over the n + 1 prefix sums of per-image tile counts).
+// over the n + 1 prefix sums of per-image tile counts), in global memory or
+// in a shared-memory copy.
 __device__ __forceinline__ int find_image(const int* tile_start, int n, int t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (__ldg(tile_start + mid) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int find_image_smem(const int* tile_start, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= t)
             lo = mid;
         else
             hi = mid - 1;

@@ -102,7 +102,13 @@ constexpr int GAUSS_LOAD_W = GAUSS_TW + 32;
 constexpr int GAUSS_LOAD_H = GAUSS_TH + 2;
 constexpr int GAUSS_STAGES = 2;            // input boxes per persistent CTA
 
-struct EdgeParams {
+// Persistent batch kernels keep the per-image tile tables of batches of at
+// most this many images in shared memory (larger batches search them in
+// global memory).
+constexpr int BATCH_SMEM_IMAGES = 256;
+
+// 16-byte aligned and sized: the batch kernels fetch it with one bulk copy.
+struct alignas(16) EdgeParams {
     uint32_t W, H;
     const uint8_t* in;
     uint64_t in_pitch;

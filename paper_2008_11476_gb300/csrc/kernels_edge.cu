@@ -84,6 +84,8 @@ struct EdgeSmem {
     int tx0[NS + 1], ty0[NS + 1];
     PhaseEntry plut[8 * 34];            // Phase table (build_phase_lut)
     uint32_t gslow[EDGE_THREADS][5];    // per-thread result of the slow G path
+    // batch of at most BATCH_SMEM_IMAGES images: its tile tables
+    int ts[BATCH_SMEM_IMAGES + 1], tx[BATCH_SMEM_IMAGES];
 };
 
 // Lane values of a 16-bit-lane word as binary32, minus a bias, exactly.
@@ -533,29 +535,31 @@ __global__ void __launch_bounds__(EDGE_THREADS)
     edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior, sm.plut, sm.gslow);
 }
 
-// Warp 0: stage the parameters and origin of batch tile t in slot ps and
-// start the TMA load of its box into stage s.
-__device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, int s,
-                                           int ps, int t) {
-    const int lane = threadIdx.x & 31;
-    int img = 0;
-    if (lane == 0) img = find_image(d.tile_start, d.n_img, t);
-    img = __shfl_sync(0xffffffffu, img, 0);
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.params[img]);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.prm[ps]);
-    for (int i = lane; i < (int)(sizeof(EdgeParams) / 4); i += 32) dst[i] = __ldg(src + i);
-    __syncwarp();
-    if (lane == 0) {
-        const int tiles_x = (sm.prm[ps].W + TW - 1) / TW;
-        const int local = t - __ldg(d.tile_start + img);
-        const int ty = local / tiles_x;
-        const int x0 = (local - ty * tiles_x) * TW, y0 = ty * TH;
-        sm.tx0[ps] = x0;
-        sm.ty0[ps] = y0;
-        tensormap_acquire(&d.maps[img]);
-        fence_proxy_async_smem();
-        issue_box(sm.in[s].b, &sm.bar[s], &d.maps[img], x0, y0);
+// Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
+// its image's parameter block into slot ps and the TMA load of its box into
+// stage s, both completing on the stage's barrier (so the issuing thread never
+// waits on global memory).  `tab`: the tile tables are in shared memory.
+__device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, bool tab,
+                                           int s, int ps, int t) {
+    int img, t0, tiles_x;
+    if (tab) {
+        img = find_image_smem(sm.ts, d.n_img, t);
+        t0 = sm.ts[img];
+        tiles_x = sm.tx[img];
+    } else {
+        img = find_image(d.tile_start, d.n_img, t);
+        t0 = __ldg(d.tile_start + img);
+        tiles_x = __ldg(d.tiles_x + img);
     }
+    const int local = t - t0, ty = local / tiles_x;
+    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * TH;
+    sm.tx0[ps] = x0;
+    sm.ty0[ps] = y0;
+    tensormap_acquire(&d.maps[img]);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&sm.bar[s], BOX_BYTES + (uint32_t)sizeof(EdgeParams));
+    bulk_copy_g2s(&sm.prm[ps], &d.params[img], (uint32_t)sizeof(EdgeParams), &sm.bar[s]);
+    tma_load_2d(&sm.in[s].b[0][0], &d.maps[img], &sm.bar[s], x0 - 16, y0 - 2);
 }
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
@@ -568,19 +572,23 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
     __shared__ EdgeSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
-    if (threadIdx.x < 32) {
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
-            fence_barrier_init();
-        }
-        __syncwarp();
-        for (int s = 0; s < STAGES; ++s) {
-            const int t = first + s * (int)gridDim.x;
-            if (t < d.total_tiles) issue_tile(sm, d, s, s, t);
-        }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
+        fence_barrier_init();
     }
+    const bool tab = d.n_img <= BATCH_SMEM_IMAGES;
+    if (tab)
+        for (int i = threadIdx.x; i <= d.n_img; i += blockDim.x) {
+            sm.ts[i] = __ldg(d.tile_start + i);
+            if (i < d.n_img) sm.tx[i] = __ldg(d.tiles_x + i);
+        }
     build_phase_lut(sm.plut);
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int s = 0; s < STAGES; ++s) {
+            const int t = first + s * (int)gridDim.x;
+            if (t < d.total_tiles) issue_tile(sm, d, tab, s, s, t);
+        }
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
         const int s = k % STAGES;
@@ -603,10 +611,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
             __syncthreads();
         }
         edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior, sm.plut, sm.gslow);
-        __syncthreads();  // box s is no longer read
-        if (threadIdx.x < 32) {
+        __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
+        if (threadIdx.x == 0) {
             const int tn = t + STAGES * (int)gridDim.x;
-            if (tn < d.total_tiles) issue_tile(sm, d, s, (k + STAGES) % (STAGES + 1), tn);
+            if (tn < d.total_tiles) issue_tile(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
         }
     }
 }

@@ -28,11 +28,13 @@ namespace {
 constexpr int kMaxFrames = HVX_NOALLOC_MAX_FRAMES;
 
 // Scratch layout (bytes): [0, 256) device error word; then the tile prefix
-// table (kMaxFrames + 1 ints); then kMaxFrames EdgeParams; then kMaxFrames
-// tensor maps (64-byte aligned).
+// table (kMaxFrames + 1 ints); then the tile columns per frame (kMaxFrames
+// ints); then kMaxFrames EdgeParams; then kMaxFrames tensor maps (64-byte
+// aligned).
 constexpr size_t kErrOff = 0;
 constexpr size_t kTilesOff = 256;
-constexpr size_t kParamsOff = (kTilesOff + (kMaxFrames + 1) * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kTilesXOff = (kTilesOff + (kMaxFrames + 1) * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kParamsOff = (kTilesXOff + kMaxFrames * sizeof(int) + 255) / 256 * 256;
 constexpr size_t kMapsOff =
     (kParamsOff + kMaxFrames * sizeof(EdgeParams) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kMapsOff + kMaxFrames * sizeof(CUtensorMap);
@@ -117,6 +119,7 @@ extern "C" hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t 
     // host image of the scratch: error word 0, tile table, params, maps
     std::memset(g_host_stage, 0, kParamsOff);
     int* tiles = reinterpret_cast<int*>(g_host_stage + kTilesOff);
+    int* tiles_x = reinterpret_cast<int*>(g_host_stage + kTilesXOff);
     EdgeParams* params = reinterpret_cast<EdgeParams*>(g_host_stage + kParamsOff);
     CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(g_host_stage + kMapsOff);
     int* d_err = reinterpret_cast<int*>(dscr + kErrOff);
@@ -162,8 +165,8 @@ extern "C" hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t 
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return HVX_ERROR_INVALID_PARAMETERS;
-        int t = (int)(((f.width + EDGE_TW - 1) / EDGE_TW) * ((f.height + EDGE_TH - 1) / EDGE_TH));
-        tiles[i + 1] = tiles[i] + t;
+        tiles_x[i] = (int)((f.width + EDGE_TW - 1) / EDGE_TW);
+        tiles[i + 1] = tiles[i] + tiles_x[i] * (int)((f.height + EDGE_TH - 1) / EDGE_TH);
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // one copy: error word cleared, tables and maps (only the used part)
@@ -176,6 +179,7 @@ extern "C" hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t 
     d.maps = reinterpret_cast<const CUtensorMap*>(dscr + kMapsOff);
     d.params = reinterpret_cast<const EdgeParams*>(dscr + kParamsOff);
     d.tile_start = reinterpret_cast<const int*>(dscr + kTilesOff);
+    d.tiles_x = reinterpret_cast<const int*>(dscr + kTilesXOff);
     d.n_img = n;
     d.total_tiles = tiles[n];
     d.err = d_err;

@@ -639,9 +639,10 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
     const size_t params_off = maps_bytes;
     const size_t tiles_off = params_off + (size_t)n * sizeof(EdgeParams);
-    const size_t total = tiles_off + (size_t)(n + 1) * sizeof(int);
+    const size_t tx_off = tiles_off + (size_t)(n + 1) * sizeof(int);
+    const size_t total = tx_off + (size_t)n * sizeof(int);
     std::vector<uint8_t> host(total);
-    std::vector<int> tile_start(n + 1, 0);
+    std::vector<int> tile_start(n + 1, 0), tiles_x(n, 0);
     int tw = 0, th = 0;
     edge_tile_dims(mode, &tw, &th);
     for (int i = 0; i < n; ++i) {
@@ -649,10 +650,12 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
         std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap, sizeof(CUtensorMap));
         std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &G.edge,
                     sizeof(EdgeParams));
-        int tiles = (int)(((G.W + tw - 1) / tw) * ((G.H + th - 1) / th));
+        tiles_x[i] = (int)((G.W + tw - 1) / tw);
+        int tiles = tiles_x[i] * (int)((G.H + th - 1) / th);
         tile_start[i + 1] = tile_start[i] + tiles;
     }
     std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));
+    std::memcpy(host.data() + tx_off, tiles_x.data(), n * sizeof(int));
     void* dmem = nullptr;
     cudaError_t e = cudaMalloc(&dmem, total);
     if (e != cudaSuccess) {
@@ -668,6 +671,7 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     d.maps = static_cast<const CUtensorMap*>(dmem);
     d.params = reinterpret_cast<const EdgeParams*>(static_cast<uint8_t*>(dmem) + params_off);
     d.tile_start = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tiles_off);
+    d.tiles_x = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tx_off);
     d.n_img = n;
     d.total_tiles = tile_start[n];
     d.err = ctx->d_error;
