@@ -153,7 +153,7 @@ struct HarrisParams {
     int32_t border_b, cval_b;  // how the window sums read the products
     int32_t wr;                // window radius (2 for 5x5)
     int32_t tv, fv;
-    int32_t pad;
+    int32_t rows;              // BORDER_UNDEFINED kernel: output rows per thread
     int64_t kn, kd;
     int64_t q_thr;     // mask = kd * R > q_thr, exact integer form of R_f32 > T
     int32_t pvalid[4]; // valid rectangle of gx, gy and the products

@@ -225,9 +225,283 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
     }
 }
 
+// ---- BORDER_UNDEFINED fast path ------------------------------------------------------
+// When both the Sobel and the window sums leave their border UNDEFINED, no
+// valid output reads a gradient or product outside the image or outside its
+// valid region, so no border fix-up is needed anywhere.  One CTA (128
+// threads) computes a 112 x 8R output tile from one TMA box of 144 x (8R + 6)
+// input bytes.  Thread (q, g) owns the 8 columns xs = x0 - 8 + 8q .. xs + 7
+// (q = 0 .. 15) and R rows; strips 1 .. 14 produce the outputs, strips 0 and
+// 15 only provide the vertical sums of the halo columns to their neighbours.
+// R (8 .. 24) is chosen per image size at plan time so that the busiest SM
+// walks the fewest rows (harris_fast_rows); 4 CTAs share an SM.
+// Each thread walks down its rows:
+//   * each step forms one new gradient row (gx, gy at its 8 columns) in
+//     biased 16-bit lanes from a sliding 3-row window of input pixel pairs,
+//     keeps it in a 5-row ring in shared memory (the thread's own slots), and
+//     forms the three exact int32 products;
+//   * 24 running vertical 5-sums (8 columns x 3 products) gain the new row
+//     and, after the outputs of the row, lose the row that leaves the window
+//     (its products recomputed from the ring);
+//   * the vertical sums of columns xs - 2, xs - 1 and xs + 8, xs + 9 come from
+//     the neighbouring lanes by shuffles; horizontal 5-sums slide along the
+//     strip, then the exact 64-bit response q = kd * R and the threshold
+//     q > q_thr, as in the general kernel.
+// Every thread runs all R rows (rows below the image read box rows the TMA
+// filled with 0 and are not stored), so the shuffles always see full warps.
+constexpr int FTW = 112, FTHREADS = 128;
+constexpr int FROWS_MIN = 8, FROWS_MAX = 24;  // boxes up to 144 x 198 bytes
+constexpr int FLW = FTW + 32;                 // box columns x0 - 16 .. x0 + 127
+constexpr int FLH_MAX = 8 * FROWS_MAX + 6;    // box rows y0 - 3 .. y0 + 8R + 2
+constexpr int RING = 5;        // gradient rows of the vertical window
+constexpr int RSTRIDE = 11;    // 16-byte units per thread: 5 rows x 2 + 1 (odd: no conflicts)
+static_assert(FTHREADS == 16 * 8, "16 strips x 8 row groups");
+static_assert(FTW % 16 == 0, "TMA boxes start on 16-byte columns");
+
+struct FastSmem {
+    alignas(128) uint8_t in[FLH_MAX][FLW];  // image (x0 - 16 + c, y0 - 3 + r)
+    alignas(16) uint4 ring[FTHREADS][RSTRIDE];
+    alignas(8) uint64_t bar;
+};
+
+// Pixel pairs (xs - 2, xs - 1), (xs, xs + 1) .. (xs + 8, xs + 9) of one box
+// row, for the strip starting at box column c (= xs - x0 + 16).
+__device__ __forceinline__ void load_pairs6(const uint8_t* row, int c, uint32_t P[6]) {
+    const uint32_t wl = *reinterpret_cast<const uint32_t*>(row + c - 4);
+    const uint2 m = *reinterpret_cast<const uint2*>(row + c);
+    const uint32_t wr = *reinterpret_cast<const uint32_t*>(row + c + 8);
+    P[0] = hi_pair(wl);
+    P[1] = lo_pair(m.x);
+    P[2] = hi_pair(m.x);
+    P[3] = lo_pair(m.y);
+    P[4] = hi_pair(m.y);
+    P[5] = lo_pair(wr);
+}
+
+// Gradient row from the input pair rows above (a), at (b) and below (c): word
+// j holds columns (xs + 2j, xs + 2j + 1); gx + 1024 in G[j], gy + 1024 in
+// G[4 + j].  Lanes: vertical sums <= 1020, differences + 255 in [0, 510], so
+// every lane stays in [4, 2044] and never borrows from its neighbour.
+__device__ __forceinline__ void grad_row(const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                                         uint32_t* G) {
+    uint32_t V[6], D[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        V[k] = a[k] + 2u * b[k] + c[k];
+        D[k] = c[k] + 0x00FF00FFu - a[k];
+    }
+    uint32_t sv[5], sd[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        sv[k] = shift_pair(V[k], V[k + 1]);  // columns (xs - 1 + 2k, xs + 2k)
+        sd[k] = shift_pair(D[k], D[k + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        G[j] = sv[j + 1] + 0x04000400u - sv[j];
+        G[4 + j] = sd[j] + sd[j + 1] + 2u * D[j + 1] + 0x00040004u;
+    }
+}
+
+// S[k][c] += SIGN * (product k of the gradient row G at column c).
+template <int SIGN>
+__device__ __forceinline__ void accumulate(const uint32_t* G, int (*S)[8]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int gx = (int)((G[j] >> (16 * h)) & 0xFFFFu) - 1024;
+            const int gy = (int)((G[4 + j] >> (16 * h)) & 0xFFFFu) - 1024;
+            const int c = 2 * j + h;
+            S[0][c] += SIGN * (gx * gx);
+            S[1][c] += SIGN * (gy * gy);
+            S[2][c] += SIGN * (gx * gy);
+        }
+    }
+}
+
+// q = kd (a b - c^2) - kn (a + b)^2 for 0 <= a, b < 2^25 and 1 <= kn, kd <=
+// 1000 (32-bit factors, 64-bit products).
+__device__ __forceinline__ long long harris_q32(int a, int b, int c, int kn, int kd) {
+    const long long det = (long long)a * b - (long long)c * c;
+    const unsigned tr = (unsigned)(a + b);
+    return det * kd - (long long)((unsigned long long)tr * tr) * kn;
+}
+
+__global__ void __launch_bounds__(FTHREADS, 4)
+    harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
+    const int R = p.rows;
+    const int x0 = blockIdx.x * FTW, y0 = blockIdx.y * 8 * R;
+    const int W = p.W, H = p.H;
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&sm.bar, (uint32_t)(FLW * (8 * R + 6)));
+        tma_load_2d(&sm.in[0][0], &tmap, &sm.bar, x0 - 16, y0 - 3);
+    }
+    // every thread leaves together when the (bounded) wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(&sm.bar, 0, p.err))) return;
+
+    const int q = threadIdx.x & 15, g = threadIdx.x >> 4;
+    const int xs = x0 - 8 + 8 * q, yb = y0 + R * g;
+    const bool producer = q >= 1 && q <= 14 && xs < W;
+    const int c = 8 + 8 * q;
+    const uint8_t* row = &sm.in[R * g][0];  // input row yb - 3
+    uint4* ring = sm.ring[threadIdx.x];
+    const bool full = xs >= p.valid[0] && xs + 8 <= p.valid[2] && yb >= p.valid[1] &&
+                      yb + R <= p.valid[3];
+    const int kn = (int)p.kn, kd = (int)p.kd;
+    int S[3][8];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) S[k][j] = 0;
+    // prologue: gradient rows yb - 2 .. yb + 1 (input rows yb - 3 .. yb + 2)
+    uint32_t A[6], B[6], C[6], G[8];
+    load_pairs6(row, c, A);
+    load_pairs6(row + FLW, c, B);
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        load_pairs6(row + (r + 2) * FLW, c, C);
+        grad_row(A, B, C, G);
+        ring[2 * r + 0] = make_uint4(G[0], G[1], G[2], G[3]);
+        ring[2 * r + 1] = make_uint4(G[4], G[5], G[6], G[7]);
+        accumulate<1>(G, S);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            A[k] = B[k];
+            B[k] = C[k];
+        }
+    }
+    uint8_t* mrow = p.mask ? p.mask + (size_t)yb * p.mask_pitch : nullptr;
+    float* rrow = p.resp ? reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(p.resp) +
+                                                    (size_t)yb * p.resp_pitch)
+                         : nullptr;
+#pragma unroll 1
+    for (int i = 0; i < R; ++i) {
+        const int y = yb + i;
+        // new gradient row y + 2 (input rows y + 1 .. y + 3) into ring slot (i + 4) mod 5
+        load_pairs6(row + (i + 6) * FLW, c, C);
+        grad_row(A, B, C, G);
+        const int sn = (i + 4) % RING, so = i % RING;
+        ring[2 * sn + 0] = make_uint4(G[0], G[1], G[2], G[3]);
+        ring[2 * sn + 1] = make_uint4(G[4], G[5], G[6], G[7]);
+        accumulate<1>(G, S);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            A[k] = B[k];
+            B[k] = C[k];
+        }
+        // vertical sums of the halo columns from the neighbouring strips
+        int L[3][2], R[3][2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            L[k][0] = __shfl_up_sync(0xffffffffu, S[k][6], 1);
+            L[k][1] = __shfl_up_sync(0xffffffffu, S[k][7], 1);
+            R[k][0] = __shfl_down_sync(0xffffffffu, S[k][0], 1);
+            R[k][1] = __shfl_down_sync(0xffffffffu, S[k][1], 1);
+        }
+        if (producer && y < H) {
+            uint32_t mk[8];
+            float rv[8];
+            int h[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) h[k] = L[k][0] + L[k][1] + S[k][0] + S[k][1] + S[k][2];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j > 0) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int add = j + 2 < 8 ? S[k][j + 2] : R[k][j - 6];
+                        const int sub = j - 3 >= 0 ? S[k][j - 3] : L[k][j - 1];
+                        h[k] += add - sub;
+                    }
+                }
+                const long long qv = harris_q32(h[0], h[1], h[2], kn, kd);
+                const bool ok = full || in_rect(p.valid, xs + j, y);
+                mk[j] = ok ? (qv > p.q_thr ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
+                if (rrow) rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
+            }
+            if (mrow) {
+                if (xs + 8 <= W) {
+                    *reinterpret_cast<uint2*>(mrow + xs) =
+                        make_uint2(mk[0] | (mk[1] << 8) | (mk[2] << 16) | (mk[3] << 24),
+                                   mk[4] | (mk[5] << 8) | (mk[6] << 16) | (mk[7] << 24));
+                } else {
+                    for (int j = 0; j < 8 && xs + j < W; ++j) mrow[xs + j] = (uint8_t)mk[j];
+                }
+            }
+            if (rrow) {
+                if (xs + 8 <= W) {
+                    float4* d4 = reinterpret_cast<float4*>(rrow + xs);
+                    d4[0] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+                    d4[1] = make_float4(rv[4], rv[5], rv[6], rv[7]);
+                } else {
+                    for (int j = 0; j < 8 && xs + j < W; ++j) rrow[xs + j] = rv[j];
+                }
+            }
+        }
+        if (mrow) mrow += p.mask_pitch;
+        if (rrow) rrow = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(rrow) + p.resp_pitch);
+        // gradient row y - 2 leaves the window
+        const uint4 o0 = ring[2 * so + 0], o1 = ring[2 * so + 1];
+        const uint32_t O[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+        accumulate<-1>(O, S);
+    }
+}
+
 }  // namespace
 
+bool harris_fast_path(const HarrisParams& p) {
+    return p.border_s == HVX_BORDER_UNDEFINED && p.border_b == HVX_BORDER_UNDEFINED && p.wr == 2 &&
+           p.rows >= FROWS_MIN && p.rows <= FROWS_MAX;
+}
+
+// Rows per thread of the BORDER_UNDEFINED kernel for a W x H image on
+// `num_sms` SMs: the R that minimises (waves of 4 CTAs per SM) x (rows each
+// CTA walks, R plus the 4-row prologue).  Measured on 4096 x 2160: R = 17 (592
+// CTAs, one full wave) 41 us; R = 20 (518) and 23 (444 CTAs, SMs left with
+// fewer than 4) 49 us; R = 15 (666 CTAs, two waves) 54 us.
+int harris_fast_rows(int W, int H, int num_sms) {
+    const long tiles_x = (W + FTW - 1) / FTW;
+    const long slots = 4L * (num_sms > 0 ? num_sms : 1);
+    int best = FROWS_MAX;
+    long best_cost = -1;
+    for (int r = FROWS_MIN; r <= FROWS_MAX; ++r) {
+        const long tiles = tiles_x * ((H + 8 * r - 1) / (8 * r));
+        const long cost = (tiles + slots - 1) / slots * (r + 4);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = r;
+        }
+    }
+    return best;
+}
+
+void harris_box(const HarrisParams& p, int* w, int* h) {
+    *w = harris_fast_path(p) ? FLW : HARRIS_LOAD_W;
+    *h = harris_fast_path(p) ? 8 * p.rows + 6 : HARRIS_TH + 6;
+}
+
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s) {
+    if (harris_fast_path(p)) {
+        static bool fast_attr = false;
+        const int smem = (int)sizeof(FastSmem);
+        if (!fast_attr) {
+            cudaError_t e = cudaFuncSetAttribute(harris_fast_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            fast_attr = true;
+        }
+        dim3 grid((p.W + FTW - 1) / FTW, (p.H + 8 * p.rows - 1) / (8 * p.rows));
+        harris_fast_kernel<<<grid, FTHREADS, smem, s>>>(map, p);
+        return cudaGetLastError();
+    }
     static bool attr_set = false;
     const int smem = (int)sizeof(HarrisSmem);
     if (!attr_set) {

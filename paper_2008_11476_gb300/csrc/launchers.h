@@ -33,6 +33,11 @@ cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream
 cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
 int gauss_batch_blocks_per_sm();
 
+// Harris: the UNDEFINED-border fast kernel or the general one; the tensor map
+// of the group's input must use the box harris_box() gives.
+bool harris_fast_path(const HarrisParams& p);
+int harris_fast_rows(int W, int H, int num_sms);
+void harris_box(const HarrisParams& p, int* w, int* h);
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);
 cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);
 cudaError_t launch_plain(const PlainParams& p, cudaStream_t s);

@@ -321,6 +321,7 @@ hvx_status build_harris(Plan& P, Group& G, const HarrisMatch& m, Context* ctx) {
     h.border_b = s0.node->border;
     h.cval_b = s0.node->cval;
     h.wr = 2;
+    h.rows = harris_fast_rows((int)G.W, (int)G.H, ctx->num_sms > 0 ? ctx->num_sms : 152);
     h.kn = r.node->p.kn;
     h.kd = r.node->p.kd;
     set_rect(h.pvalid, P.ops[m.pxy].out->valid);
@@ -339,7 +340,9 @@ hvx_status build_harris(Plan& P, Group& G, const HarrisMatch& m, Context* ctx) {
         h.fv = t.node->p.false_value;
         h.q_thr = harris_q_threshold((float)t.node->p.thr_value, h.kd);
     }
-    return encode_u8_map(&G.tmap, sx.in[0], HARRIS_LOAD_W, HARRIS_TH + 6);
+    int bw = 0, bh = 0;
+    harris_box(h, &bw, &bh);
+    return encode_u8_map(&G.tmap, sx.in[0], bw, bh);
 }
 
 // ---- plain point / generic ------------------------------------------------------

@@ -314,7 +314,7 @@ def check_resp(got, ref):
     np.testing.assert_array_equal(got, ref)  # single rounding of the exact value
 
 
-@pytest.mark.parametrize("w,h", [(1, 1), (7, 7), (64, 32), (97, 45), (300, 200)])
+@pytest.mark.parametrize("w,h", [(1, 1), (7, 7), (64, 32), (97, 45), (300, 200), (385, 361)])
 @pytest.mark.parametrize("border", BORDERS)
 def test_harris_fused_and_plain(ctx, w, h, border):
     img = synth.rects_noise(w, h, seed=3)
@@ -336,6 +336,23 @@ def test_harris_full_size_4096x2160(ctx):
     assert kinds == ["fused_harris_tma"]
     np.testing.assert_array_equal(mk, ref_mk)
     check_resp(r, ref_r)
+
+
+@pytest.mark.parametrize("w,h", [(1000, 700), (129, 241)])
+def test_harris_mask_only_undefined(ctx, w, h):
+    # the BORDER_UNDEFINED kernel without the response export (the benchmark's
+    # form), on ragged 128 x 120 tiles, and with a non-default k = 3/50
+    img = synth.rects_noise(w, h, seed=11)
+    for kn, kd, thr in ((1, 25, 1e6), (3, 50, 2.5e7)):
+        ref_mk, _ = O.harris_graph(img, O.BORDER_UNDEFINED, kn, kd, thr)
+        inp = PG.upload(ctx, img, H.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        g = PG.harris_graph(ctx, inp, mk, None, kn=kn, kd=kd, thr=thr)
+        assert PG.kernel_kinds(g) == ["fused_harris_tma"]
+        H.hvxProcessGraph(g)
+        np.testing.assert_array_equal(PG.download(mk), ref_mk)
+        assert ref_mk.any() and not ref_mk.all()
+        H.hvxReleaseGraph(g)
 
 
 def test_harris_clean_corners(ctx):
