@@ -328,6 +328,30 @@ __device__ __forceinline__ long long harris_q32(int a, int b, int c, int kn, int
     return det * kd - (long long)((unsigned long long)tr * tr) * kn;
 }
 
+// q > q_thr, decided in binary32 when the computed q is farther from the
+// threshold than its error bound, else exactly in 64-bit integers.  With
+// u = 2^-24 and M = kd (a b + c^2) + kn (a + b)^2, the binary32 evaluation
+// below (rounded conversions, products, one rounding per fused multiply-add)
+// is within 8u M of q, the threshold's conversion within u |q_thr|, and the
+// bound 2^-19 M' + 2^-21 |q_thr'| (primes: as computed) exceeds their sum with
+// a 4-fold margin (tests/test_harris_decision.py replays the procedure).
+// Inputs: 0 <= a, b < 2^25, |c| < 2^25.  qtf = q_thr in binary32, qtb =
+// 2^-21 |qtf|.
+__device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, float kdf, float qtf,
+                                             float qtb, int kn, int kd, long long q_thr) {
+    const float A = __int2float_rn(a), B = __int2float_rn(b), C = __int2float_rn(c);
+    const float P = __fmul_rn(A, B);
+    const float D = fmaf(-C, C, P);
+    const float S = __fadd_rn(A, B);
+    const float V = __fmul_rn(knf, __fmul_rn(S, S));
+    const float Q = fmaf(kdf, D, -V);
+    const float M = fmaf(kdf, fmaf(C, C, P), V);
+    const float bound = fmaf(0x1p-19f, M, qtb);
+    const float d = __fsub_rn(Q, qtf);
+    if (fabsf(d) > bound) return d > 0.0f;
+    return harris_q32(a, b, c, kn, kd) > q_thr;
+}
+
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -356,6 +380,8 @@ __global__ void __launch_bounds__(FTHREADS, 4)
     const bool full = xs >= p.valid[0] && xs + 8 <= p.valid[2] && yb >= p.valid[1] &&
                       yb + R <= p.valid[3];
     const int kn = (int)p.kn, kd = (int)p.kd;
+    const float knf = (float)kn, kdf = (float)kd;
+    const float qtf = (float)p.q_thr, qtb = fabsf(qtf) * 0x1p-21f;
     int S[3][8];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -422,10 +448,16 @@ __global__ void __launch_bounds__(FTHREADS, 4)
                         h[k] += add - sub;
                     }
                 }
-                const long long qv = harris_q32(h[0], h[1], h[2], kn, kd);
                 const bool ok = full || in_rect(p.valid, xs + j, y);
-                mk[j] = ok ? (qv > p.q_thr ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
-                if (rrow) rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
+                bool hit;
+                if (rrow) {  // the response is exported: exact q for both
+                    const long long qv = harris_q32(h[0], h[1], h[2], kn, kd);
+                    hit = qv > p.q_thr;
+                    rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
+                } else {
+                    hit = harris_above(h[0], h[1], h[2], knf, kdf, qtf, qtb, kn, kd, p.q_thr);
+                }
+                mk[j] = ok ? (hit ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
             }
             if (mrow) {
                 if (xs + 8 <= W) {
