@@ -226,14 +226,21 @@ def edge_config(args, world):
 # ---------------------------------------------------------------------------
 # CPU oracle legs (the only places bench.py runs oracle/)
 
-def cpu_oracle_edge(n_frames: int):
-    """The CPU oracle (single-threaded C) over n_frames 1080p edge-graph frames."""
+def cpu_oracle_edge(n_frames: int, threads: int = 1):
+    """The CPU oracle (C, one frame per call) over n_frames 1080p edge-graph
+    frames, on `threads` host threads (the C calls run without the GIL)."""
     import oracle as O
     from paper_2008_11476_gb300 import synth
     frames = [synth.rects_noise(W, H_, seed=2 + i) for i in range(min(n_frames, 4))]
+    O.edge_graph(frames[0][:64, :64].copy())  # load the library outside the timing
     t0 = time.perf_counter()
-    for i in range(n_frames):
-        O.edge_graph(frames[i % len(frames)])
+    if threads <= 1:
+        for i in range(n_frames):
+            O.edge_graph(frames[i % len(frames)])
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda i: O.edge_graph(frames[i % len(frames)]), range(n_frames)))
     dt = time.perf_counter() - t0
     return n_frames * W * H_ / 1e6 / dt, dt
 
@@ -400,13 +407,19 @@ def run_edge(args, world, rank, local, torch):
     ext_bytes = 3 * W * H_ * F  # input + phase + mask, per launch (per GPU)
     kernel_s = t_fused / args.steps
     achieved = ext_bytes / kernel_s / 1e9
-    cpu = None
+    cpu = cpu_all = None
     if not args.no_cpu_baseline:
         n = 48
         v_cpu, dt = cpu_oracle_edge(n)
         cpu = {"value": round(v_cpu, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} frames of 1920x1080 through the C oracle, single thread "
                          f"({dt:.1f} s)"}
+        nt = max(1, os.cpu_count() or 1)
+        n_all = 6 * nt
+        v_all, dt_all = cpu_oracle_edge(n_all, nt)
+        cpu_all = {"value": round(v_all, 3), "unit": "Mpix/s", "cores": nt, "kind": "oracle",
+                   "sample": f"{n_all} frames of 1920x1080 through the C oracle, one frame per "
+                             f"call on {nt} threads ({dt_all:.1f} s)"}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mpix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -430,6 +443,7 @@ def run_edge(args, world, rank, local, torch):
         "serving": serving,
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -740,13 +754,31 @@ def run_serve(args, world, rank, local, torch):
     ctx = H.hvxCreateContext()
     secs = args.serve_seconds if args.serve_seconds is not None else 5.0
     res = serve_compare(ctx, H, PG, synth, secs, instances=4)
+    # offered-rate sweep of the fused server up to saturation (the host loop
+    # that submits requests is the limit at the top), and a 256 MB budget run
+    # where admission waits for memory
+    pool = build_serve_pool(ctx, H, PG, synth, True, 4)
+    sweep = []
+    for rate in (2000.0, 5000.0, 10000.0, 20000.0, 40000.0):
+        srv = H.hvxCreateServer(ctx, 40 << 30, 16, 8)
+        r = serve_run(H, synth, pool, srv, 1.0, rate, seed=6)
+        r["achieved_req_per_s"] = round(r["requests"] / r["seconds"], 1)
+        sweep.append(r)
+        H.hvxReleaseServer(srv)
+    srv = H.hvxCreateServer(ctx, 256 << 20, 16, 8)
+    small = serve_run(H, synth, pool, srv, 1.0, 2000.0, seed=7)
+    H.hvxReleaseServer(srv)
+    for lst in pool.values():
+        for g in lst:
+            H.hvxReleaseGraph(g)
     H.hvxReleaseContext(ctx)
     if rank == 0:
         f, p = res["fused_continuous"], res["unfused_one_at_a_time"]
         print(json.dumps({"metric": "serving p50/p99 ms and Mpix/s", "value": f["p99_ms"],
                           "unit": "ms (p99)", "higher_is_better": False, "n_gpus": world,
                           "dtype": "u8", "data": "synthetic", "serving": res,
-                          "p99_speedup_vs_unfused": round(p["p99_ms"] / max(f["p99_ms"], 1e-9), 2)}),
+                          "p99_speedup_vs_unfused": round(p["p99_ms"] / max(f["p99_ms"], 1e-9), 2),
+                          "rate_sweep_fused": sweep, "budget_256MB_fused": small}),
               flush=True)
 
 
