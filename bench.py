@@ -667,7 +667,7 @@ def run_harris(args, world, rank, local, torch):
             "roofline": {"bound": "hbm", "achieved": round(ext / per_launch_s / 1e9, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": round(ext / per_launch_s / 1e9 / peaks.get("hbm_gbs", 6800), 4),
-                         "peak_source": src, "kernel": "harris_kernel",
+                         "peak_source": src, "kernel": "harris_fast_kernel",
                          "algorithmic_bytes_per_launch": ext},
             "gpu_launches": steps * F, "clocks": clocks}), flush=True)
 

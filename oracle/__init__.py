@@ -86,7 +86,10 @@ def _declare(L):
     L.orc_harris_graph.argtypes = [P, P, P, I, I, I, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.c_double, P]
     L.orc_edge_graph.argtypes = [P, P, P, P, I, I, I, I, I, I, P]
-    for name in ("orc_gaussian3x3", "orc_box3x3", "orc_sobel3x3", "orc_window_sum_s32",
+    L.orc_morph3x3.argtypes = [P, P, I, I, I, I, I, R, R]
+    L.orc_bitwise.argtypes = [P, P, P, I, I, I, R, R, R]
+    for name in ("orc_gaussian3x3", "orc_box3x3", "orc_morph3x3", "orc_bitwise",
+                 "orc_sobel3x3", "orc_window_sum_s32",
                  "orc_convolve_u8_s16", "orc_magnitude", "orc_phase", "orc_threshold",
                  "orc_channel_extract_uyvy", "orc_arith", "orc_mul_s16_s32",
                  "orc_harris_response", "orc_harris_graph", "orc_edge_graph"):
@@ -151,6 +154,32 @@ def box3x3(src, border=BORDER_REPLICATE, cval=0, rounding=ROUND_ZERO) -> Img:
     vo = (ctypes.c_int * 4)()
     _check(lib().orc_box3x3(_p(s.data), _p(out), s.w, s.h, border, cval, rounding,
                             _rect(s.rect), vo))
+    return Img(out, tuple(vo))
+
+
+MORPH_DILATE, MORPH_ERODE, MORPH_MEDIAN = 0, 1, 2
+BIT_AND, BIT_OR, BIT_XOR, BIT_NOT = 0, 1, 2, 3
+
+
+def morph3x3(src, op, border=BORDER_REPLICATE, cval=0) -> Img:
+    """Dilate3x3 / Erode3x3 / Median3x3 (max / min / median of the 3x3 window)."""
+    s = _as_img(src)
+    assert s.data.dtype == np.uint8
+    out = np.empty_like(s.data)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_morph3x3(_p(s.data), _p(out), s.w, s.h, border, cval, op, _rect(s.rect), vo))
+    return Img(out, tuple(vo))
+
+
+def bitwise(a, b, op) -> Img:
+    """And / Or / Xor of two U8 images, or Not of one (b None)."""
+    A = _as_img(a)
+    B = _as_img(b) if b is not None else None
+    assert A.data.dtype == np.uint8
+    out = np.empty_like(A.data)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_bitwise(_p(A.data), _p(B.data) if B is not None else None, _p(out), A.w, A.h,
+                             op, _rect(A.rect), _rect(B.rect if B is not None else A.rect), vo))
     return Img(out, tuple(vo))
 
 

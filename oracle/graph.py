@@ -103,9 +103,10 @@ def edges(g: GraphDesc, ops: list[Op]):
 # --- verification (Section 3.1, Section 5.2) -------------------------------------
 
 _POINT_OUT = {"magnitude": "S16", "phase": "U8", "threshold": "U8", "mul": "S32",
-              "harris_response": "F32"}
+              "harris_response": "F32", "and": "U8", "or": "U8", "xor": "U8", "not": "U8"}
 _LOCAL_OUT = {"gaussian3x3": "U8", "box3x3": "U8", "sobel_x": "S16", "sobel_y": "S16",
-              "window_sum": "S32", "convolve": "S16"}
+              "window_sum": "S32", "convolve": "S16", "dilate3x3": "U8", "erode3x3": "U8",
+              "median3x3": "U8"}
 _IN_FMTS = {
     "gaussian3x3": [("U8",)], "box3x3": [("U8",)], "sobel_x": [("U8",)],
     "sobel_y": [("U8",)], "window_sum": [("S32",)], "convolve": [("U8",)],
@@ -115,6 +116,9 @@ _IN_FMTS = {
     "channel_extract": [("UYVY",)],
     "add": [("U8", "S16"), ("U8", "S16")], "subtract": [("U8", "S16"), ("U8", "S16")],
     "absdiff": [("U8", "S16"), ("U8", "S16")],
+    "dilate3x3": [("U8",)], "erode3x3": [("U8",)], "median3x3": [("U8",)],
+    "and": [("U8",), ("U8",)], "or": [("U8",), ("U8",)], "xor": [("U8",), ("U8",)],
+    "not": [("U8",)],
 }
 
 
@@ -284,6 +288,8 @@ _BORDER = {"undefined": O.BORDER_UNDEFINED, "replicate": O.BORDER_REPLICATE,
            "constant": O.BORDER_CONSTANT}
 _ROUND = {"zero": O.ROUND_ZERO, "nearest": O.ROUND_NEAREST}
 _ARITH = {"add": O.ARITH_ADD, "subtract": O.ARITH_SUB, "absdiff": O.ARITH_ABSDIFF}
+_MORPH = {"dilate3x3": O.MORPH_DILATE, "erode3x3": O.MORPH_ERODE, "median3x3": O.MORPH_MEDIAN}
+_BITS = {"and": O.BIT_AND, "or": O.BIT_OR, "xor": O.BIT_XOR, "not": O.BIT_NOT}
 _NPFMT = {"U8": np.uint8, "S16": np.int16, "S32": np.int32, "F32": np.float32}
 
 
@@ -332,6 +338,10 @@ def run(g: GraphDesc, inputs: dict, dce: bool = True) -> dict:
             r = O.harris_response(x[0], x[1], x[2], p.get("kn", 1), p.get("kd", 25))
         elif k == "channel_extract":
             r = O.channel_extract_uyvy(x[0].data, p.get("channel", 0))
+        elif k in _MORPH:
+            r = O.morph3x3(x[0], _MORPH[k], b, c)
+        elif k in _BITS:
+            r = O.bitwise(x[0], x[1] if k != "not" else None, _BITS[k])
         elif k in _ARITH:
             r = O.arith(x[0], x[1], _NPFMT[g.data[op.out].fmt], _ARITH[k],
                         p.get("policy", "saturate") == "saturate")

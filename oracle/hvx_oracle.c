@@ -139,6 +139,46 @@ int orc_box3x3(const uint8_t* in, uint8_t* out, int w, int h, int border, int cv
     return ORC_OK;
 }
 
+/* Dilate3x3, Erode3x3, Median3x3 (Table 2 local operators on U8): the
+ * maximum (op 0), minimum (op 1) or median (op 2) of the nine samples of the
+ * 3x3 window, read under the node's border mode.  The median sorts the nine
+ * values (insertion sort) and takes the fifth. */
+int orc_morph3x3(const uint8_t* in, uint8_t* out, int w, int h, int border, int cval, int op,
+                 const int vin[4], int vout[4]) {
+    int r[4];
+    if (w <= 0 || h <= 0 || op < 0 || op > 2) return ORC_ERR;
+    rect_local(r, vin, 1, 1, border);
+    memset(out, 0, (size_t)w * h);
+    for (int y = r[1]; y < r[3]; ++y)
+        for (int x = r[0]; x < r[2]; ++x) {
+            int v[9], n = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                    v[n++] = (int)read_u8(in, w, h, x + dx, y + dy, border, cval);
+            int res;
+            if (op == 0) {
+                res = v[0];
+                for (int i = 1; i < 9; ++i) res = v[i] > res ? v[i] : res;
+            } else if (op == 1) {
+                res = v[0];
+                for (int i = 1; i < 9; ++i) res = v[i] < res ? v[i] : res;
+            } else {
+                for (int i = 1; i < 9; ++i) {
+                    int t = v[i], j = i - 1;
+                    while (j >= 0 && v[j] > t) {
+                        v[j + 1] = v[j];
+                        --j;
+                    }
+                    v[j + 1] = t;
+                }
+                res = v[4];
+            }
+            out[(size_t)y * w + x] = (uint8_t)res;
+        }
+    rect_copy(vout, r);
+    return ORC_OK;
+}
+
 /* Sobel3x3 (Table 2; Listing 1, and the dead-output example of Section 5.2.2).
  * gx with [-1 0 1; -2 0 2; -1 0 1], gy with [-1 -2 -1; 0 0 0; 1 2 1], no
  * scaling: |g| <= 1020 fits S16.  Either output may be NULL. */
@@ -353,6 +393,26 @@ int orc_arith(const void* a, int fa, const void* b, int fb, void* out, int fo, i
             int64_t bv = (int64_t)load_as_double(b, fb, i);
             int64_t v = op == 0 ? av + bv : (op == 1 ? av - bv : (av > bv ? av - bv : bv - av));
             store_int(out, fo, i, sat_or_wrap(v, fo, saturate));
+        }
+    rect_copy(vout, r);
+    return ORC_OK;
+}
+
+/* Bitwise point operators on U8 (Table 2: And, Or, Xor, Not): op 0 = a & b,
+ * 1 = a | b, 2 = a ^ b, 3 = ~a (b unused, may be NULL). */
+int orc_bitwise(const uint8_t* a, const uint8_t* b, uint8_t* out, int w, int h, int op,
+                const int va[4], const int vb[4], int vout[4]) {
+    int r[4];
+    if (op < 0 || op > 3 || (op < 3 && !b)) return ORC_ERR;
+    if (op == 3) rect_copy(r, va);
+    else rect_intersect(r, va, vb);
+    memset(out, 0, (size_t)w * h);
+    for (int y = r[1]; y < r[3]; ++y)
+        for (int x = r[0]; x < r[2]; ++x) {
+            size_t i = (size_t)y * w + x;
+            int v = op == 0 ? (a[i] & b[i]) : op == 1 ? (a[i] | b[i]) : op == 2 ? (a[i] ^ b[i])
+                                                                         : (~a[i] & 0xFF);
+            out[i] = (uint8_t)v;
         }
     rect_copy(vout, r);
     return ORC_OK;

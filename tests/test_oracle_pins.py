@@ -445,3 +445,72 @@ def test_nonvirtual_intermediate_keeps_upstream_alive(orc):
     alive, data = G.eliminate_dead(g, ops)
     assert [op.name for op in alive] == ["n0"]
     assert "iso" not in data and "dead" not in data
+
+
+# --- Dilate3x3 / Erode3x3 / Median3x3, And / Or / Xor / Not (Table 2) ----------------
+
+MORPH_REF = {O.MORPH_DILATE: ndi.grey_dilation, O.MORPH_ERODE: ndi.grey_erosion,
+             O.MORPH_MEDIAN: ndi.median_filter}
+
+
+@pytest.mark.parametrize("op", [O.MORPH_DILATE, O.MORPH_ERODE, O.MORPH_MEDIAN])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 5), (17, 23)])
+def test_morph_matches_scipy(orc, op, shape):
+    img = synth.uniform_u8(shape[1], shape[0], seed=11 + op)
+    f = MORPH_REF[op]
+    r = O.morph3x3(img, op, O.BORDER_REPLICATE)
+    assert (r.data == f(img, size=3, mode="nearest")).all()
+    r = O.morph3x3(img, op, O.BORDER_CONSTANT, cval=77)
+    assert (r.data == f(img, size=3, mode="constant", cval=77)).all()
+    r = O.morph3x3(img, op, O.BORDER_UNDEFINED)
+    h, w = shape
+    assert r.rect == (1, 1, max(1, w - 1), max(1, h - 1))
+    inner = f(img, size=3, mode="nearest")[1:h - 1, 1:w - 1]
+    assert (r.data[1:h - 1, 1:w - 1] == inner).all()
+    mask = np.ones_like(img, bool)
+    mask[1:h - 1, 1:w - 1] = False
+    assert (r.data[mask] == 0).all()
+
+
+def test_morph_impulses(orc):
+    z = np.zeros((7, 9), np.uint8)
+    z[3, 4] = 255
+    d = O.morph3x3(z, O.MORPH_DILATE, O.BORDER_REPLICATE).data
+    assert (d[2:5, 3:6] == 255).all() and d.sum() == 9 * 255
+    assert (O.morph3x3(z, O.MORPH_MEDIAN, O.BORDER_REPLICATE).data == 0).all()
+    hole = np.full((7, 9), 200, np.uint8)
+    hole[3, 4] = 0
+    e = O.morph3x3(hole, O.MORPH_ERODE, O.BORDER_REPLICATE).data
+    assert (e[2:5, 3:6] == 0).all() and (e == 0).sum() == 9
+    # median of the window values 0..8 (a permutation) is 4
+    perm = np.array([[5, 1, 7], [0, 8, 3], [6, 2, 4]], np.uint8)
+    assert O.morph3x3(perm, O.MORPH_MEDIAN, O.BORDER_UNDEFINED).data[1, 1] == 4
+
+
+def test_bitwise_matches_numpy(orc):
+    a = synth.uniform_u8(19, 13, seed=21)
+    b = synth.uniform_u8(19, 13, seed=22)
+    assert (O.bitwise(a, b, O.BIT_AND).data == (a & b)).all()
+    assert (O.bitwise(a, b, O.BIT_OR).data == (a | b)).all()
+    assert (O.bitwise(a, b, O.BIT_XOR).data == (a ^ b)).all()
+    assert (O.bitwise(a, None, O.BIT_NOT).data == (~a)).all()
+    # valid regions intersect
+    ra = O.Img(a, (1, 2, 18, 12))
+    rb = O.Img(b, (3, 0, 19, 10))
+    r = O.bitwise(ra, rb, O.BIT_AND)
+    assert r.rect == (3, 2, 18, 10)
+    assert (r.data[:2] == 0).all() and (r.data[:, :3] == 0).all()
+
+
+def test_graph_runner_morphology_closing(orc):
+    # closing (dilate then erode) as an oracle graph equals the two calls
+    img = synth.uniform_u8(24, 16, seed=5)
+    g = G.GraphDesc()
+    g.image("in", 24, 16, "U8")
+    g.virtual("d")
+    g.image("out", 24, 16, "U8")
+    g.node("dilate3x3", ["in"], ["d"], border="replicate")
+    g.node("erode3x3", ["d"], ["out"], border="replicate")
+    res = G.run(g, {"in": img})["out"]
+    ref = O.morph3x3(O.morph3x3(img, O.MORPH_DILATE), O.MORPH_ERODE)
+    assert (res.data == ref.data).all()
