@@ -274,6 +274,13 @@ hvx_node hvxGaussian3x3Node(hvx_graph g, hvx_image in, hvx_image out);
 /* Box3x3 (local): U8 -> U8, 3x3 sum / 9. */
 hvx_node hvxBox3x3Node(hvx_graph g, hvx_image in, hvx_image out);
 
+/* Dilate3x3 / Erode3x3 / Median3x3 (local, Table 2): U8 -> U8, the maximum /
+ * minimum / median of the nine samples of the 3x3 window (border mode as set
+ * on the node). */
+hvx_node hvxDilate3x3Node(hvx_graph g, hvx_image in, hvx_image out);
+hvx_node hvxErode3x3Node(hvx_graph g, hvx_image in, hvx_image out);
+hvx_node hvxMedian3x3Node(hvx_graph g, hvx_image in, hvx_image out);
+
 /* Sobel3x3 (local): U8 -> S16 gx (kernel [-1 0 1; -2 0 2; -1 0 1]) and S16 gy
  * (its transpose).  Either output may be NULL; an output no one reads is
  * removed by dead-computation elimination (Section 5.2.2). */
@@ -305,6 +312,12 @@ hvx_node hvxChannelExtractNode(hvx_graph g, hvx_image in, int32_t channel, hvx_i
 hvx_node hvxAddNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
+
+/* And / Or / Xor (point, Table 2): U8, U8 -> U8 bitwise; Not: U8 -> U8. */
+hvx_node hvxAndNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
+hvx_node hvxOrNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
+hvx_node hvxXorNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
+hvx_node hvxNotNode(hvx_graph g, hvx_image in, hvx_image out);
 
 /* Convolve (local): U8 -> S16, integer kw x kh coefficients (row-major,
  * applied without flipping, odd sizes up to 7x7), the sum floor-divided by

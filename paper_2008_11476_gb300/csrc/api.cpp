@@ -593,6 +593,34 @@ hvx_node hvxBox3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
     return add_node(g, N_BOX, {in}, {out}, 1, NodeParams());
 }
 
+hvx_node hvxDilate3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_DILATE, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxErode3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_ERODE, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxMedian3x3Node(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_MEDIAN, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxAndNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
+    return add_node(g, N_AND, {a, b}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxOrNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
+    return add_node(g, N_OR, {a, b}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxXorNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
+    return add_node(g, N_XOR, {a, b}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxNotNode(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_NOT, {in}, {out}, 1, NodeParams());
+}
+
 hvx_node hvxSobel3x3Node(hvx_graph g, hvx_image in, hvx_image gx, hvx_image gy) {
     if (ok_graph(g) && !gx && !gy) {
         G(g)->last = HVX_ERROR_INVALID_PARAMETERS;

@@ -269,6 +269,10 @@ __device__ __forceinline__ int32_t eval_point(const P& st, int32_t a, int32_t b,
             return st.i0 ? sat_s16(r) : (int32_t)(int16_t)(uint16_t)(r & 0xFFFF);
         }
         case OP_MUL: return a * b;
+        case OP_AND: return a & b;
+        case OP_OR: return a | b;
+        case OP_XOR: return a ^ b;
+        case OP_NOT: return ~a & 0xFF;
         case OP_HARRIS:
             return __float_as_int(ratio_to_float(harris_q(a, b, c, st.k0, st.k1), st.k1));
     }

@@ -58,13 +58,21 @@ const char* op_name(int kind) {
         case OP_HARRIS: return "harris_response";
         case OP_LSUM: return "window_sum";
         case OP_CONV: return "convolve";
+        case OP_DILATE: return "dilate3x3";
+        case OP_ERODE: return "erode3x3";
+        case OP_MEDIAN: return "median3x3";
+        case OP_AND: return "and";
+        case OP_OR: return "or";
+        case OP_XOR: return "xor";
+        case OP_NOT: return "not";
     }
     return "?";
 }
 
 bool op_is_local(int kind) {
     return kind == OP_GAUSS || kind == OP_BOX || kind == OP_SOBEL_X || kind == OP_SOBEL_Y ||
-           kind == OP_LSUM || kind == OP_CONV;
+           kind == OP_LSUM || kind == OP_CONV || kind == OP_DILATE || kind == OP_ERODE ||
+           kind == OP_MEDIAN;
 }
 
 const char* group_kernel_name(int gk) {
@@ -111,6 +119,13 @@ void lower(Graph* g, Plan& P) {
         switch (n->kind) {
             case N_GAUSS: add(OP_GAUSS, 0, 1); break;
             case N_BOX: add(OP_BOX, 0, 1); break;
+            case N_DILATE: add(OP_DILATE, 0, 1); break;
+            case N_ERODE: add(OP_ERODE, 0, 1); break;
+            case N_MEDIAN: add(OP_MEDIAN, 0, 1); break;
+            case N_AND: add(OP_AND, 0, 0); break;
+            case N_OR: add(OP_OR, 0, 0); break;
+            case N_XOR: add(OP_XOR, 0, 0); break;
+            case N_NOT: add(OP_NOT, 0, 0); break;
             case N_SOBEL:
                 if (!n->out[0] && !n->out[1]) fail(HVX_ERROR_INVALID_PARAMETERS);
                 if (n->out[0]) add(OP_SOBEL_X, 0, 1);
@@ -157,7 +172,14 @@ void infer(Op& op) {
     uint32_t ow = in[0]->w, oh = in[0]->h;
     switch (op.kind) {
         case OP_GAUSS:
-        case OP_BOX: need(0, {HVX_DF_U8}); of = HVX_DF_U8; break;
+        case OP_BOX:
+        case OP_DILATE:
+        case OP_ERODE:
+        case OP_MEDIAN:
+        case OP_NOT: need(0, {HVX_DF_U8}); of = HVX_DF_U8; break;
+        case OP_AND:
+        case OP_OR:
+        case OP_XOR: need(0, {HVX_DF_U8}); need(1, {HVX_DF_U8}); of = HVX_DF_U8; break;
         case OP_SOBEL_X:
         case OP_SOBEL_Y: need(0, {HVX_DF_U8}); of = HVX_DF_S16; break;
         case OP_CONV: need(0, {HVX_DF_U8}); of = HVX_DF_S16; break;

@@ -100,6 +100,13 @@ enum NodeKind : int {
     N_CONV,
     N_POINT,
     N_LOCAL,
+    N_DILATE,
+    N_ERODE,
+    N_MEDIAN,
+    N_AND,
+    N_OR,
+    N_XOR,
+    N_NOT,
 };
 
 struct NodeParams {

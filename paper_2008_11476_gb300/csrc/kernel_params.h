@@ -25,6 +25,13 @@ enum OpKind : int {
     OP_HARRIS,
     OP_LSUM,
     OP_CONV,
+    OP_DILATE,
+    OP_ERODE,
+    OP_MEDIAN,
+    OP_AND,
+    OP_OR,
+    OP_XOR,
+    OP_NOT,
 };
 
 // ---------------------------------------------------------------------------

@@ -96,6 +96,31 @@ __device__ int32_t eval_op(const Ctx& c, const GenStage& st, int x, int y) {
             long long q = s >> st.shift;  // arithmetic shift: floor division
             return (int32_t)(q > 32767 ? 32767 : (q < -32768 ? -32768 : q));
         }
+        case OP_DILATE:
+        case OP_ERODE: {
+            int m = c.at(st.in[0], x - 1, y - 1);
+            for (int k = 1; k < 9; ++k) {
+                const int v = c.at(st.in[0], x + k % 3 - 1, y + k / 3 - 1);
+                m = st.op == OP_DILATE ? max(m, v) : min(m, v);
+            }
+            return m;
+        }
+        case OP_MEDIAN: {
+            int v[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = c.at(st.in[0], x + k % 3 - 1, y + k / 3 - 1);
+            // median of nine by the exchange network of Paeth (Graphics Gems)
+            auto cx = [&](int i, int j) {
+                const int lo = min(v[i], v[j]), hi = max(v[i], v[j]);
+                v[i] = lo;
+                v[j] = hi;
+            };
+            cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 1); cx(3, 4); cx(6, 7);
+            cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 3); cx(5, 8); cx(4, 7);
+            cx(3, 6); cx(1, 4); cx(2, 5); cx(4, 7); cx(4, 2); cx(6, 4);
+            cx(4, 2);
+            return v[4];
+        }
         case OP_LSUM: {
             long long s = 0;
             for (int dy = -st.ry; dy <= st.ry; ++dy)

@@ -120,6 +120,13 @@ _SIGS = {
     "hvxWaitBatch": (I32, [P, P]),
     "hvxGaussian3x3Node": (P, [P, P, P]),
     "hvxBox3x3Node": (P, [P, P, P]),
+    "hvxDilate3x3Node": (P, [P, P, P]),
+    "hvxErode3x3Node": (P, [P, P, P]),
+    "hvxMedian3x3Node": (P, [P, P, P]),
+    "hvxAndNode": (P, [P, P, P, P]),
+    "hvxOrNode": (P, [P, P, P, P]),
+    "hvxXorNode": (P, [P, P, P, P]),
+    "hvxNotNode": (P, [P, P, P]),
     "hvxSobel3x3Node": (P, [P, P, P, P]),
     "hvxMagnitudeNode": (P, [P, P, P, P]),
     "hvxPhaseNode": (P, [P, P, P, P]),
@@ -339,6 +346,34 @@ def hvxGaussian3x3Node(g, i, o):
 
 def hvxBox3x3Node(g, i, o):
     return _node(lib().hvxBox3x3Node(g, i, o), g, "hvxBox3x3Node")
+
+
+def hvxDilate3x3Node(g, i, o):
+    return _node(lib().hvxDilate3x3Node(g, i, o), g, "hvxDilate3x3Node")
+
+
+def hvxErode3x3Node(g, i, o):
+    return _node(lib().hvxErode3x3Node(g, i, o), g, "hvxErode3x3Node")
+
+
+def hvxMedian3x3Node(g, i, o):
+    return _node(lib().hvxMedian3x3Node(g, i, o), g, "hvxMedian3x3Node")
+
+
+def hvxAndNode(g, a, b, o):
+    return _node(lib().hvxAndNode(g, a, b, o), g, "hvxAndNode")
+
+
+def hvxOrNode(g, a, b, o):
+    return _node(lib().hvxOrNode(g, a, b, o), g, "hvxOrNode")
+
+
+def hvxXorNode(g, a, b, o):
+    return _node(lib().hvxXorNode(g, a, b, o), g, "hvxXorNode")
+
+
+def hvxNotNode(g, i, o):
+    return _node(lib().hvxNotNode(g, i, o), g, "hvxNotNode")
 
 
 def hvxSobel3x3Node(g, i, gx, gy):

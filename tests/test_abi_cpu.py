@@ -293,3 +293,40 @@ def test_fusion_grouping_of_mixed_chain(pctx):
     H.hvxVerifyGraph(g)
     assert PG.kernel_kinds(g) == ["plain_channel_uv", "staged_tile", "staged_tile"]
     assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 16 * 128
+
+
+def test_morphology_graph_plans_one_staged_group(pctx):
+    # closing -> |closing - in| -> threshold, AND the input's median: six
+    # Table 2 nodes, one staged-tile launch fused, six unfused
+    w, h = 640, 480
+    for fusion, n_launch in ((True, 1), (False, 6)):
+        src = H.hvxCreateImage(pctx, w, h, H.HVX_DF_U8)
+        out = H.hvxCreateImage(pctx, w, h, H.HVX_DF_U8)
+        g = H.hvxCreateGraph(pctx)
+        d, c, diff, mask, med = (H.hvxCreateVirtualImage(g) for _ in range(5))
+        for n in (H.hvxDilate3x3Node(g, src, d), H.hvxErode3x3Node(g, d, c),
+                  H.hvxMedian3x3Node(g, src, med)):
+            H.hvxSetNodeBorder(n, H.HVX_BORDER_UNDEFINED, 0)
+        H.hvxAbsDiffNode(g, c, src, diff)
+        H.hvxThresholdNode(g, diff, H.HVX_THRESHOLD_BINARY, 20, 0, 255, 0, mask)
+        H.hvxAndNode(g, med, mask, out)
+        H.hvxSetGraphFusion(g, fusion)
+        H.hvxVerifyGraph(g)
+        assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES) == n_launch
+        assert H.hvxGetValidRegion(out) == (2, 2, w - 2, h - 2)
+        if fusion:
+            assert PG.kernel_kinds(g) == ["staged_tile"]
+            assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 0
+
+
+def test_bitwise_and_morph_reject_wrong_formats(pctx):
+    a16 = H.hvxCreateImage(pctx, 32, 8, H.HVX_DF_S16)
+    u8 = H.hvxCreateImage(pctx, 32, 8, H.HVX_DF_U8)
+    out = H.hvxCreateImage(pctx, 32, 8, H.HVX_DF_U8)
+    for build in (lambda g: H.hvxAndNode(g, a16, u8, out), lambda g: H.hvxDilate3x3Node(g, a16, out),
+                  lambda g: H.hvxNotNode(g, a16, out)):
+        g = H.hvxCreateGraph(pctx)
+        build(g)
+        with pytest.raises(H.HvxError) as e:
+            H.hvxVerifyGraph(g)
+        assert e.value.status == H.HVX_ERROR_INVALID_FORMAT
