@@ -44,113 +44,163 @@ __device__ __forceinline__ void store_pixel(const GenExt& e, int x, int y, int32
     }
 }
 
-struct Ctx {
-    const GenericDesc& d;
-    int32_t* s;
-    int x0, y0;
-    __device__ __forceinline__ int32_t at(int bi, int x, int y) const {
-        const GenBuf& b = d.buf[bi];
-        int i = x - (x0 - b.halo), j = y - (y0 - b.halo);
-        return s[b.smem_off + j * buf_w(b) + i];
-    }
+// A buffer seen from the cells of another (output) buffer: element (c, r) of
+// the output buffer sits at p[r * w + c] of the input buffer (the output's
+// halo never exceeds its inputs' halos).
+struct View {
+    const int32_t* p;
+    int w;
 };
 
-__device__ int32_t eval_op(const Ctx& c, const GenStage& st, int x, int y) {
+__device__ __forceinline__ View view_of(const GenericDesc& d, const int32_t* s, int bi, int out_halo) {
+    const GenBuf& b = d.buf[bi];
+    const int w = buf_w(b), dh = b.halo - out_halo;
+    return View{s + b.smem_off + dh * w + dh, w};
+}
+
+// Calls f(c, r) for every cell of a bw x bh buffer: warps take rows, lanes
+// consecutive columns (conflict-free shared-memory rows, no divisions).
+template <class F>
+__device__ __forceinline__ void for_cells(int bw, int bh, F f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < bh; r += nw)
+        for (int c = lane; c < bw; c += 32) f(c, r);
+}
+
+// Writes one stage's buffer: every cell inside the image gets v(c, r, q0, ..)
+// when it lies in the op's valid region, else 0; returns whether some cell lies
+// outside the image (the caller fills those).  The op is uniform, so each
+// instantiation is one tight loop.
+template <class V>
+__device__ __forceinline__ bool stage_cells(const GenBuf& ob, int32_t* out, int ox, int oy, int W,
+                                            int H, V v) {
+    const int bw = buf_w(ob), bh = buf_h(ob);
+    bool edge = false;
+    for_cells(bw, bh, [&](int c, int r) {
+        const int x = ox + c, y = oy + r;
+        if (x < 0 || x >= W || y < 0 || y >= H) {
+            edge = true;
+            return;
+        }
+        out[r * bw + c] = in_rect(ob.valid, x, y) ? v(c, r) : 0;
+    });
+    return edge;
+}
+
+__device__ bool run_stage(const GenericDesc& d, int32_t* s, const GenStage& st, int x0, int y0) {
+    const GenBuf& ob = d.buf[st.out];
+    int32_t* out = s + ob.smem_off;
+    const int ox = x0 - ob.halo, oy = y0 - ob.halo;
+    const int W = d.W, H = d.H;
+    const View a = view_of(d, s, st.in[0], ob.halo);
     switch (st.op) {
-        case OP_GAUSS: {
-            int s = 0;
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx)
-                    s += (2 - dx * dx) * (2 - dy * dy) * c.at(st.in[0], x + dx, y + dy);
-            return st.rounding == HVX_ROUND_TO_NEAREST ? (s + 8) >> 4 : s >> 4;
-        }
+        case OP_GAUSS:
         case OP_BOX: {
-            int s = 0;
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) s += c.at(st.in[0], x + dx, y + dy);
-            return st.rounding == HVX_ROUND_TO_NEAREST ? (s + 4) / 9 : s / 9;
+            const bool gauss = st.op == OP_GAUSS, near = st.rounding == HVX_ROUND_TO_NEAREST;
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                const int32_t* q = a.p + r * a.w + c;
+                const int32_t* u = q - a.w;
+                const int32_t* l = q + a.w;
+                if (gauss) {
+                    const int t = (u[-1] + 2 * u[0] + u[1]) + 2 * (q[-1] + 2 * q[0] + q[1]) +
+                                  (l[-1] + 2 * l[0] + l[1]);
+                    return near ? (t + 8) >> 4 : t >> 4;
+                }
+                const int t = u[-1] + u[0] + u[1] + q[-1] + q[0] + q[1] + l[-1] + l[0] + l[1];
+                return near ? (t + 4) / 9 : t / 9;
+            });
         }
-        case OP_SOBEL_X: {
-            int s = 0;
-            for (int dy = -1; dy <= 1; ++dy) {
-                int w = 2 - dy * dy;
-                s += w * (c.at(st.in[0], x + 1, y + dy) - c.at(st.in[0], x - 1, y + dy));
-            }
-            return s;
-        }
-        case OP_SOBEL_Y: {
-            int s = 0;
-            for (int dx = -1; dx <= 1; ++dx) {
-                int w = 2 - dx * dx;
-                s += w * (c.at(st.in[0], x + dx, y + 1) - c.at(st.in[0], x + dx, y - 1));
-            }
-            return s;
-        }
-        case OP_CONV: {
-            long long s = 0;
-            const int kw = 2 * st.rx + 1;
-            for (int dy = -st.ry; dy <= st.ry; ++dy)
-                for (int dx = -st.rx; dx <= st.rx; ++dx)
-                    s += (long long)c.d.coeff[st.coeff_off + (dy + st.ry) * kw + (dx + st.rx)] *
-                         c.at(st.in[0], x + dx, y + dy);
-            long long q = s >> st.shift;  // arithmetic shift: floor division
-            return (int32_t)(q > 32767 ? 32767 : (q < -32768 ? -32768 : q));
-        }
+        case OP_SOBEL_X:
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                const int32_t* q = a.p + r * a.w + c;
+                return (q[1 - a.w] - q[-1 - a.w]) + 2 * (q[1] - q[-1]) + (q[1 + a.w] - q[-1 + a.w]);
+            });
+        case OP_SOBEL_Y:
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                const int32_t* q = a.p + r * a.w + c;
+                return (q[a.w - 1] - q[-a.w - 1]) + 2 * (q[a.w] - q[-a.w]) + (q[a.w + 1] - q[-a.w + 1]);
+            });
         case OP_DILATE:
         case OP_ERODE: {
-            int m = c.at(st.in[0], x - 1, y - 1);
-            for (int k = 1; k < 9; ++k) {
-                const int v = c.at(st.in[0], x + k % 3 - 1, y + k / 3 - 1);
-                m = st.op == OP_DILATE ? max(m, v) : min(m, v);
-            }
-            return m;
-        }
-        case OP_MEDIAN: {
-            int v[9];
+            const bool dil = st.op == OP_DILATE;
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                const int32_t* q = a.p + (r - 1) * a.w + c;
+                int m = q[-1];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = c.at(st.in[0], x + k % 3 - 1, y + k / 3 - 1);
-            // median of nine by the exchange network of Paeth (Graphics Gems)
-            auto cx = [&](int i, int j) {
-                const int lo = min(v[i], v[j]), hi = max(v[i], v[j]);
-                v[i] = lo;
-                v[j] = hi;
-            };
-            cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 1); cx(3, 4); cx(6, 7);
-            cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 3); cx(5, 8); cx(4, 7);
-            cx(3, 6); cx(1, 4); cx(2, 5); cx(4, 7); cx(4, 2); cx(6, 4);
-            cx(4, 2);
-            return v[4];
+                for (int k = 1; k < 9; ++k) {
+                    const int v = q[(k / 3) * a.w + k % 3 - 1];
+                    m = dil ? max(m, v) : min(m, v);
+                }
+                return m;
+            });
         }
-        case OP_LSUM: {
-            long long s = 0;
-            for (int dy = -st.ry; dy <= st.ry; ++dy)
-                for (int dx = -st.rx; dx <= st.rx; ++dx) s += c.at(st.in[0], x + dx, y + dy);
-            return (int32_t)s;
-        }
+        case OP_MEDIAN:
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                const int32_t* q = a.p + (r - 1) * a.w + c;
+                int v[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = q[(k / 3) * a.w + k % 3 - 1];
+                // median of nine by the exchange network of Paeth (Graphics Gems)
+                auto cx = [&](int i, int j) {
+                    const int lo = min(v[i], v[j]), hi = max(v[i], v[j]);
+                    v[i] = lo;
+                    v[j] = hi;
+                };
+                cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 1); cx(3, 4); cx(6, 7);
+                cx(1, 2); cx(4, 5); cx(7, 8); cx(0, 3); cx(5, 8); cx(4, 7);
+                cx(3, 6); cx(1, 4); cx(2, 5); cx(4, 7); cx(4, 2); cx(6, 4);
+                cx(4, 2);
+                return v[4];
+            });
+        case OP_CONV:
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                long long t = 0;
+                const int kw = 2 * st.rx + 1;
+                const int32_t* q = a.p + (r - st.ry) * a.w + (c - st.rx);
+                for (int dy = 0; dy <= 2 * st.ry; ++dy)
+                    for (int dx = 0; dx < kw; ++dx)
+                        t += (long long)d.coeff[st.coeff_off + dy * kw + dx] * q[dy * a.w + dx];
+                const long long v = t >> st.shift;  // arithmetic shift: floor division
+                return (int32_t)(v > 32767 ? 32767 : (v < -32768 ? -32768 : v));
+            });
+        case OP_LSUM:
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                long long t = 0;
+                const int32_t* q = a.p + (r - st.ry) * a.w + (c - st.rx);
+                for (int dy = 0; dy <= 2 * st.ry; ++dy)
+                    for (int dx = 0; dx <= 2 * st.rx; ++dx) t += q[dy * a.w + dx];
+                return (int32_t)t;
+            });
         default: {
-            int32_t a = c.at(st.in[0], x, y);
-            int32_t b = st.in[1] >= 0 ? c.at(st.in[1], x, y) : 0;
-            int32_t cc = st.in[2] >= 0 ? c.at(st.in[2], x, y) : 0;
-            return eval_point(st, a, b, cc);
+            const View b = st.in[1] >= 0 ? view_of(d, s, st.in[1], ob.halo) : a;
+            const View e = st.in[2] >= 0 ? view_of(d, s, st.in[2], ob.halo) : a;
+            return stage_cells(ob, out, ox, oy, W, H, [&](int c, int r) {
+                return eval_point(st, a.p[r * a.w + c], b.p[r * b.w + c], e.p[r * e.w + c]);
+            });
         }
     }
-    return 0;
+}
+
+// Value of buffer bi at image pixel (x, y) (inside the buffer).
+__device__ __forceinline__ int32_t buf_at(const GenericDesc& d, const int32_t* s, int bi, int x0,
+                                          int y0, int x, int y) {
+    const GenBuf& b = d.buf[bi];
+    return s[b.smem_off + (y - (y0 - b.halo)) * buf_w(b) + (x - (x0 - b.halo))];
 }
 
 __global__ void __launch_bounds__(GEN_THREADS) generic_kernel(const GenericDesc d) {
     extern __shared__ int32_t s[];
     const int x0 = blockIdx.x * GEN_TW, y0 = blockIdx.y * GEN_TH;
     const int W = d.W, H = d.H;
-    Ctx c{d, s, x0, y0};
 
     // external inputs, border applied
     for (int e = 0; e < d.n_in; ++e) {
         const GenExt& ex = d.in[e];
         const GenBuf& b = d.buf[ex.buf];
-        const int bw = buf_w(b), n = bw * buf_h(b);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            int j = i / bw;
-            int x = x0 - b.halo + (i - j * bw), y = y0 - b.halo + j;
+        const int bw = buf_w(b);
+        int32_t* dst = s + b.smem_off;
+        for_cells(bw, buf_h(b), [&](int c, int r) {
+            const int x = x0 - b.halo + c, y = y0 - b.halo + r;
             int32_t v;
             if (x >= 0 && x < W && y >= 0 && y < H)
                 v = load_pixel(ex, x, y);
@@ -160,50 +210,41 @@ __global__ void __launch_bounds__(GEN_THREADS) generic_kernel(const GenericDesc 
                 v = load_pixel(ex, clampi(x, 0, W - 1), clampi(y, 0, H - 1));
             else
                 v = 0;
-            s[b.smem_off + i] = v;
-        }
+            dst[r * bw + c] = v;
+        });
     }
     __syncthreads();
 
     for (int k = 0; k < d.n_stage; ++k) {
         const GenStage& st = d.st[k];
-        const GenBuf& b = d.buf[st.out];
-        const int bw = buf_w(b), n = bw * buf_h(b);
-        bool edge = false;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            int j = i / bw;
-            int x = x0 - b.halo + (i - j * bw), y = y0 - b.halo + j;
-            if (x >= 0 && x < W && y >= 0 && y < H) {
-                s[b.smem_off + i] = in_rect(b.valid, x, y) ? eval_op(c, st, x, y) : 0;
-            } else {
-                edge = true;
-            }
-        }
+        const bool edge = run_stage(d, s, st, x0, y0);
         if (__syncthreads_or(edge)) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                int j = i / bw;
-                int x = x0 - b.halo + (i - j * bw), y = y0 - b.halo + j;
-                if (x >= 0 && x < W && y >= 0 && y < H) continue;
+            // cells outside the image, the way the op's local consumers read them
+            const GenBuf& b = d.buf[st.out];
+            const int bw = buf_w(b);
+            int32_t* out = s + b.smem_off;
+            for_cells(bw, buf_h(b), [&](int c, int r) {
+                const int x = x0 - b.halo + c, y = y0 - b.halo + r;
+                if (x >= 0 && x < W && y >= 0 && y < H) return;
                 int32_t v;
                 if (b.fill == FILL_CONSTANT)
                     v = b.cval;
                 else if (b.fill == FILL_REPLICATE)
-                    v = c.at(st.out, clampi(x, 0, W - 1), clampi(y, 0, H - 1));
+                    v = buf_at(d, s, st.out, x0, y0, clampi(x, 0, W - 1), clampi(y, 0, H - 1));
                 else
                     v = 0;
-                s[b.smem_off + i] = v;
-            }
+                out[r * bw + c] = v;
+            });
             __syncthreads();
         }
     }
 
     for (int e = 0; e < d.n_out; ++e) {
         const GenExt& ex = d.out[e];
-        for (int i = threadIdx.x; i < GEN_TW * GEN_TH; i += blockDim.x) {
-            int j = i / GEN_TW;
-            int x = x0 + (i - j * GEN_TW), y = y0 + j;
-            if (x < W && y < H) store_pixel(ex, x, y, c.at(ex.buf, x, y));
-        }
+        for_cells(GEN_TW, GEN_TH, [&](int c, int r) {
+            const int x = x0 + c, y = y0 + r;
+            if (x < W && y < H) store_pixel(ex, x, y, buf_at(d, s, ex.buf, x0, y0, x, y));
+        });
     }
 }
 
