@@ -328,14 +328,23 @@ __device__ __forceinline__ void sobel8(const uint32_t* a, const uint32_t* b, con
         vs[j] = a[j] + 2u * b[j] + c[j];
         dy[j] = c[j] + 0x00FF00FFu - a[j];
     }
+    // both lanes of a word unpacked by one packed binary32 subtraction
+    const float2 bx = make_float2(-(8388608.0f + 1024.0f), -(8388608.0f + 1024.0f));
+    const float2 by = make_float2(-(8388608.0f + 1020.0f), -(8388608.0f + 1020.0f));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t gxp = vs[j + 1] + 0x04000400u - vs[j];
         const uint32_t gyp = dy[j] + dy[j + 1] + 2u * shift_pair(dy[j], dy[j + 1]);
-        gx[2 * j] = lane_lo_f(gxp, 1024.0f);
-        gx[2 * j + 1] = lane_hi_f(gxp, 1024.0f);
-        gy[2 * j] = lane_lo_f(gyp, 1020.0f);
-        gy[2 * j + 1] = lane_hi_f(gyp, 1020.0f);
+        const float2 fx = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gxp, 0x4B00u, 0x5410)),
+                                                 __int_as_float(__byte_perm(gxp, 0x4B00u, 0x5432))),
+                                     bx);
+        const float2 fy = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gyp, 0x4B00u, 0x5410)),
+                                                 __int_as_float(__byte_perm(gyp, 0x4B00u, 0x5432))),
+                                     by);
+        gx[2 * j] = fx.x;
+        gx[2 * j + 1] = fx.y;
+        gy[2 * j] = fy.x;
+        gy[2 * j + 1] = fy.y;
     }
 }
 
@@ -368,12 +377,29 @@ __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p,
     constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
     uint32_t mk[8], ph[8];
     int mg[8];
+    if (kMask) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            if (kPhase) {
+                mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), cx.s_thr);
+                mk[i + 1] = set_gt(fmaf(gx[i + 1], gx[i + 1], gy[i + 1] * gy[i + 1]), cx.s_thr);
+            } else {  // mask alone: gx^2 + gy^2 of two pixels per packed operation
+                const float2 X = make_float2(gx[i], gx[i + 1]), Y = make_float2(gy[i], gy[i + 1]);
+                const float2 s2 = __ffma2_rn(X, X, __fmul2_rn(Y, Y));
+                mk[i] = set_gt(s2.x, cx.s_thr);
+                mk[i + 1] = set_gt(s2.y, cx.s_thr);
+            }
+        }
+    }
+    if (kPhase) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        mk[i] = ph[i] = 0u;
+        if (!kMask) mk[i] = 0u;
+        if (!kPhase) ph[i] = 0u;
         mg[i] = 0;
-        if (kMask) mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), cx.s_thr);
-        if (kPhase) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
         if (MODE == M_GENERAL) {
             const int ix = (int)gx[i], iy = (int)gy[i];
             mg[i] = magnitude_s16(ix, iy);
