@@ -87,8 +87,11 @@ def _declare(L):
                                    ctypes.c_double, P]
     L.orc_edge_graph.argtypes = [P, P, P, P, I, I, I, I, I, I, P]
     L.orc_morph3x3.argtypes = [P, P, I, I, I, I, I, R, R]
+    L.orc_convolve_u8_u8.argtypes = [P, P, I, I, I, I, P, I, I, I, R, R]
+    L.orc_tomasi_response.argtypes = [P, P, P, P, I, I, R, R, R, R]
     L.orc_bitwise.argtypes = [P, P, P, I, I, I, R, R, R]
     for name in ("orc_gaussian3x3", "orc_box3x3", "orc_morph3x3", "orc_bitwise",
+                 "orc_convolve_u8_u8", "orc_tomasi_response",
                  "orc_sobel3x3", "orc_window_sum_s32",
                  "orc_convolve_u8_s16", "orc_magnitude", "orc_phase", "orc_threshold",
                  "orc_channel_extract_uyvy", "orc_arith", "orc_mul_s16_s32",
@@ -204,15 +207,25 @@ def window_sum(src, kw=5, kh=5, border=BORDER_UNDEFINED, cval=0) -> Img:
     return Img(out, tuple(vo))
 
 
-def convolve(src, coeffs, shift=0, border=BORDER_REPLICATE, cval=0) -> Img:
+def convolve(src, coeffs, shift=0, border=BORDER_REPLICATE, cval=0, out_dtype=np.int16) -> Img:
     s = _as_img(src)
     assert s.data.dtype == np.uint8
     c = np.ascontiguousarray(np.asarray(coeffs, np.int32))
     kh, kw = c.shape
-    out = np.empty(s.data.shape, np.int16)
+    out = np.empty(s.data.shape, out_dtype)
     vo = (ctypes.c_int * 4)()
-    _check(lib().orc_convolve_u8_s16(_p(s.data), _p(out), s.w, s.h, kw, kh, _p(c), shift,
-                                     border, cval, _rect(s.rect), vo))
+    fn = lib().orc_convolve_u8_u8 if np.dtype(out_dtype) == np.uint8 else lib().orc_convolve_u8_s16
+    _check(fn(_p(s.data), _p(out), s.w, s.h, kw, kh, _p(c), shift, border, cval, _rect(s.rect), vo))
+    return Img(out, tuple(vo))
+
+
+def tomasi_response(sxx, syy, sxy) -> Img:
+    """Shi-Tomasi response: smaller eigenvalue of [Sxx Sxy; Sxy Syy], F32."""
+    A, B, C = _as_img(sxx), _as_img(syy), _as_img(sxy)
+    out = np.empty(A.data.shape, np.float32)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_tomasi_response(_p(A.data), _p(B.data), _p(C.data), _p(out), A.w, A.h,
+                                     _rect(A.rect), _rect(B.rect), _rect(C.rect), vo))
     return Img(out, tuple(vo))
 
 

@@ -103,16 +103,17 @@ def edges(g: GraphDesc, ops: list[Op]):
 # --- verification (Section 3.1, Section 5.2) -------------------------------------
 
 _POINT_OUT = {"magnitude": "S16", "phase": "U8", "threshold": "U8", "mul": "S32",
-              "harris_response": "F32", "and": "U8", "or": "U8", "xor": "U8", "not": "U8"}
+              "harris_response": "F32", "tomasi_response": "F32", "and": "U8", "or": "U8",
+              "xor": "U8", "not": "U8"}
 _LOCAL_OUT = {"gaussian3x3": "U8", "box3x3": "U8", "sobel_x": "S16", "sobel_y": "S16",
-              "window_sum": "S32", "convolve": "S16", "dilate3x3": "U8", "erode3x3": "U8",
-              "median3x3": "U8"}
+              "window_sum": "S32", "dilate3x3": "U8", "erode3x3": "U8", "median3x3": "U8"}
 _IN_FMTS = {
     "gaussian3x3": [("U8",)], "box3x3": [("U8",)], "sobel_x": [("U8",)],
     "sobel_y": [("U8",)], "window_sum": [("S32",)], "convolve": [("U8",)],
     "magnitude": [("S16",), ("S16",)], "phase": [("S16",), ("S16",)],
     "threshold": [("U8", "S16", "S32", "F32")], "mul": [("S16",), ("S16",)],
     "harris_response": [("S32",), ("S32",), ("S32",)],
+    "tomasi_response": [("S32",), ("S32",), ("S32",)],
     "channel_extract": [("UYVY",)],
     "add": [("U8", "S16"), ("U8", "S16")], "subtract": [("U8", "S16"), ("U8", "S16")],
     "absdiff": [("U8", "S16"), ("U8", "S16")],
@@ -217,6 +218,10 @@ def _infer(g: GraphDesc, op: Op):
             of = _POINT_OUT[op.kind]
         elif op.kind in _LOCAL_OUT:
             of = _LOCAL_OUT[op.kind]
+        elif op.kind == "convolve":  # U8 or S16 output: the output image decides
+            of = g.data[op.out].fmt or "S16"
+            if of not in ("U8", "S16"):
+                raise GraphError(f"{op.name}: convolve output must be U8 or S16")
         else:  # add / subtract / absdiff: the output image's own format decides
             of = g.data[op.out].fmt or ("S16" if "S16" in [d.fmt for d in ins] else "U8")
     out = g.data[op.out]
@@ -320,7 +325,8 @@ def run(g: GraphDesc, inputs: dict, dce: bool = True) -> dict:
         elif k == "window_sum":
             r = O.window_sum(x[0], p.get("kw", 5), p.get("kh", 5), b, c)
         elif k == "convolve":
-            r = O.convolve(x[0], p["coeffs"], p.get("shift", 0), b, c)
+            r = O.convolve(x[0], p["coeffs"], p.get("shift", 0), b, c,
+                           _NPFMT[g.data[op.out].fmt])
         elif k == "magnitude":
             r = O.magnitude(x[0], x[1])
         elif k == "phase":
@@ -334,6 +340,8 @@ def run(g: GraphDesc, inputs: dict, dce: bool = True) -> dict:
                                       p.get("false_value", 0))
         elif k == "mul":
             r = O.mul_s32(x[0], x[1])
+        elif k == "tomasi_response":
+            r = O.tomasi_response(x[0], x[1], x[2])
         elif k == "harris_response":
             r = O.harris_response(x[0], x[1], x[2], p.get("kn", 1), p.get("kd", 25))
         elif k == "channel_extract":

@@ -264,6 +264,35 @@ int orc_convolve_u8_s16(const uint8_t* in, int16_t* out, int w, int h, int kw, i
     return ORC_OK;
 }
 
+/* Convolve with a U8 output (the OpenVX Convolve output may be U8): the same
+ * floor-divided sum, saturated to 0 .. 255. */
+int orc_convolve_u8_u8(const uint8_t* in, uint8_t* out, int w, int h, int kw, int kh,
+                       const int32_t* coeffs, int shift, int border, int cval,
+                       const int vin[4], int vout[4]) {
+    int r[4];
+    int rx = kw / 2, ry = kh / 2;
+    if (w <= 0 || h <= 0 || kw <= 0 || kh <= 0 || !(kw & 1) || !(kh & 1) || shift < 0 ||
+        shift > 30)
+        return ORC_ERR;
+    rect_local(r, vin, rx, ry, border);
+    memset(out, 0, (size_t)w * h);
+    for (int y = r[1]; y < r[3]; ++y)
+        for (int x = r[0]; x < r[2]; ++x) {
+            int64_t s = 0;
+            for (int dy = -ry; dy <= ry; ++dy)
+                for (int dx = -rx; dx <= rx; ++dx)
+                    s += (int64_t)coeffs[(dy + ry) * kw + (dx + rx)] *
+                         read_u8(in, w, h, x + dx, y + dy, border, cval);
+            int64_t d = (int64_t)1 << shift;
+            int64_t q = s >= 0 ? s / d : -((-s + d - 1) / d);
+            if (q > 255) q = 255;
+            if (q < 0) q = 0;
+            out[(size_t)y * w + x] = (uint8_t)q;
+        }
+    rect_copy(vout, r);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Point operators (Table 2 "point"; Section 4)                               */
 
@@ -491,6 +520,30 @@ float orc_round_ratio(int64_t num, int64_t den) {
  * the functions above (Sobel3x3 -> gx^2, gy^2, gx*gy -> 5x5 window sums ->
  * response -> binary threshold), for the cpu_baseline timing and smoke check.
  * scratch must hold 2*w*h int16 + 6*w*h int32 + w*h float. */
+/* Shi-Tomasi response (the Tomasi application of Section 6: the smaller
+ * eigenvalue of the structure tensor [Sxx Sxy; Sxy Syy]):
+ *   lambda_min = (Sxx + Syy - sqrt((Sxx - Syy)^2 + 4 Sxy^2)) / 2,
+ * evaluated in long double from the exact integer discriminant and rounded
+ * once to binary32. */
+int orc_tomasi_response(const int32_t* sxx, const int32_t* syy, const int32_t* sxy, float* out,
+                        int w, int h, const int va[4], const int vb[4], const int vc[4],
+                        int vout[4]) {
+    int r[4], t[4];
+    rect_intersect(t, va, vb);
+    rect_intersect(r, t, vc);
+    memset(out, 0, sizeof(float) * (size_t)w * h);
+    for (int y = r[1]; y < r[3]; ++y)
+        for (int x = r[0]; x < r[2]; ++x) {
+            size_t i = (size_t)y * w + x;
+            int64_t a = sxx[i], b = syy[i], c = sxy[i];
+            int64_t disc = (a - b) * (a - b) + 4 * c * c;
+            long double lam = ((long double)(a + b) - sqrtl((long double)disc)) / 2.0L;
+            out[i] = (float)lam;
+        }
+    rect_copy(vout, r);
+    return ORC_OK;
+}
+
 int orc_harris_graph(const uint8_t* in, uint8_t* mask, float* resp, int w, int h, int border,
                      int64_t kn, int64_t kd, double thr, void* scratch) {
     size_t n = (size_t)w * h;

@@ -514,3 +514,35 @@ def test_graph_runner_morphology_closing(orc):
     res = G.run(g, {"in": img})["out"]
     ref = O.morph3x3(O.morph3x3(img, O.MORPH_DILATE), O.MORPH_ERODE)
     assert (res.data == ref.data).all()
+
+
+# --- Convolve with U8 output, Shi-Tomasi response (the Section 6 applications) ------
+
+def test_convolve_u8_output_is_saturated_s16(orc):
+    img = synth.uniform_u8(23, 19, seed=17)
+    sharpen = np.array([[0, -1, 0], [-1, 8, -1], [0, -1, 0]], np.int32)
+    for border in BORDERS:
+        s16 = O.convolve(img, sharpen, 2, border, 40)
+        u8 = O.convolve(img, sharpen, 2, border, 40, np.uint8)
+        assert u8.rect == s16.rect
+        assert (u8.data == np.clip(s16.data, 0, 255)).all()
+    assert (O.convolve(img, sharpen, 2, out_dtype=np.uint8).data == 255).any()
+
+
+def test_tomasi_closed_forms_and_eigvalsh(orc):
+    a = np.array([[100, 7, 5000, 0, 26010000]], np.int32)
+    b = np.array([[30, 7, 5000, 9, 26010000]], np.int32)
+    c = np.array([[0, 3, 5000, 0, -26010000]], np.int32)
+    r = O.tomasi_response(a, b, c).data[0]
+    # diagonal: min(a, b); a = b: a - |c|; rank one (c^2 = a b): 0
+    assert r[0] == 30 and r[1] == 4 and r[2] == 0 and r[3] == 0 and r[4] == 0
+    rng = np.random.default_rng(5)
+    A = rng.integers(0, 2 ** 24, 500)
+    B = rng.integers(0, 2 ** 24, 500)
+    C = (rng.uniform(-1, 1, 500) * np.sqrt(A * B.astype(np.float64))).astype(np.int64)
+    got = O.tomasi_response(A.astype(np.int32)[None], B.astype(np.int32)[None],
+                            C.astype(np.int32)[None]).data[0].astype(np.float64)
+    ref = np.array([np.linalg.eigvalsh(np.array([[x, z], [z, y]], np.float64))[0]
+                    for x, y, z in zip(A, B, C)])
+    scale = np.maximum(np.abs(A) + np.abs(B), 1)
+    assert np.all(np.abs(got - ref) <= 1e-6 * scale)
