@@ -26,6 +26,8 @@ the host (cpu_baseline); SM clocks sampled during the timed region.
           640x480 .. 7680x4320, 40 GB budget, fused vs one-at-a-time unfused
   morph   Dilate3x3 / Erode3x3 / Median3x3 / AbsDiff / Threshold / And graph
           on 1920x1080 frames (staged-tile executor), fused vs unfused
+  apps    the nine applications of the paper's evaluation (Gauss .. Tomasi)
+          on 1920x1080 frames, fused vs unfused
 
 Multi-GPU (torchrun, one rank per GPU): replicas only -- every rank runs the
 same per-GPU batch on its own frames; value = all frames / max rank time.
@@ -59,7 +61,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=64)
     ap.add_argument("--workload", default="edge",
                     choices=["edge", "gauss", "gauss-batch", "harris", "batch", "serve",
-                             "morph"])
+                             "morph", "apps"])
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -750,6 +752,71 @@ def run_morph(args, world, rank, local, torch):
             "gpu_launches": steps * F, "clocks": clocks}), flush=True)
 
 
+def run_apps(args, world, rank, local, torch):
+    """The applications of the paper's evaluation (Section 6) on 1920x1080
+    frames, one launch (or one launch per node, unfused) per frame: Mpix/s
+    fused and unfused, the fused kernel, and the HBM fraction on external
+    bytes."""
+    from paper_2008_11476_gb300 import apps as A
+    from paper_2008_11476_gb300 import graphs as PG
+    from paper_2008_11476_gb300 import hvx as H
+    from paper_2008_11476_gb300 import synth
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = H.hvxCreateContext()
+    F = 16
+    distinct = [synth.rects_noise(W, H_, seed=50 + i) for i in range(4)]
+    t_in, ins = wrap_frames(ctx, torch, H, [distinct[i % 4] for i in range(F)], W, H_, W)
+    peaks, src = measured_peaks()
+    bpp = {H.HVX_DF_U8: 1, H.HVX_DF_S16: 2}
+    res = {}
+    steps = max(3, args.steps // 20)
+    for name, build in A.APPS:
+        fused, plain = [], []
+        for a in ins:
+            g, outs = build(ctx, a, W, H_, True)
+            fused.append(g)
+            g2, _ = build(ctx, a, W, H_, False)
+            plain.append(g2)
+        ext = W * H_ * (1 + sum(bpp[f] for _, _, f in outs))
+
+        def run(gs):
+            for gr in gs:
+                H.hvxScheduleGraph(gr, sh)
+
+        for _ in range(args.warmup):
+            run(fused)
+        run(plain)
+        barrier(world, torch)
+        tf = reduce_max(time_steps(torch, lambda: run(fused), steps, stream), world, torch)
+        tp = reduce_max(time_steps(torch, lambda: run(plain), steps, stream), world, torch)
+        fv = W * H_ * F * steps / tf / 1e6 * world
+        pv = W * H_ * F * steps / tp / 1e6 * world
+        res[name] = {"fused_mpix_s": round(fv, 1), "unfused_mpix_s": round(pv, 1),
+                     "speedup": round(fv / pv, 2), "kernel": PG.kernel_kinds(fused[0])[0],
+                     "unfused_launches_per_frame": H.hvxQueryGraph(plain[0],
+                                                                   H.HVX_GRAPH_NUM_LAUNCHES),
+                     "external_bytes_per_px": ext // (W * H_),
+                     "hbm_frac": round(ext * F * steps / tf / 1e9 / peaks.get("hbm_gbs", 6800),
+                                       4)}
+        H.hvxWaitGraph(fused[-1])
+        for gr in fused + plain:
+            H.hvxReleaseGraph(gr)
+    H.hvxReleaseContext(ctx)
+    if rank == 0:
+        gm = float(np.exp(np.mean([np.log(v["fused_mpix_s"]) for v in res.values()])))
+        print(json.dumps({
+            "metric": "paper application suite Mpix/s (1920x1080, geometric mean, fused)",
+            "value": round(gm, 1), "unit": "Mpix/s", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u8/s16",
+            "data": "synthetic (seeded rectangles + sigma 10 noise)",
+            "config": {"workload": "Gauss, Laplacian, FChain, SobelX, EdgFig2, Sobel, Unsharp, "
+                                   "Harris, Tomasi (Section 6) on 16 1920x1080 U8 frames per "
+                                   "step, one launch per frame",
+                       "l2": "16 distinct frames per step, larger than L2"},
+            "apps": res, "peak_source": src, "gpu_launches": steps * F * len(res)}), flush=True)
+
+
 def run_batch(args, world, rank, local, torch):
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
@@ -873,7 +940,7 @@ def main():
         dist.init_process_group("nccl")
     fn = {"edge": run_edge, "gauss": run_gauss, "gauss-batch": run_gauss_batch,
           "harris": run_harris, "batch": run_batch, "serve": run_serve,
-          "morph": run_morph}[args.workload]
+          "morph": run_morph, "apps": run_apps}[args.workload]
     fn(args, world, rank, local, torch)
     if world > 1:
         import torch.distributed as dist

@@ -94,6 +94,7 @@ typedef int32_t hvx_status;
 /* Custom point operators (hvxPointNode). */
 #define HVX_POINT_MUL 1             /* S16 a, S16 b -> S32 a*b (exact)        */
 #define HVX_POINT_HARRIS_RESPONSE 2 /* S32 Sxx, Syy, Sxy -> F32 R; params kn, kd */
+#define HVX_POINT_TOMASI_RESPONSE 3 /* S32 Sxx, Syy, Sxy -> F32 smaller eigenvalue */
 
 /* Custom local operators (hvxLocalNode). */
 #define HVX_LOCAL_SUM 1 /* S32 -> S32: unweighted kw x kh window sum (exact) */
@@ -319,7 +320,7 @@ hvx_node hvxOrNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 hvx_node hvxXorNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 hvx_node hvxNotNode(hvx_graph g, hvx_image in, hvx_image out);
 
-/* Convolve (local): U8 -> S16, integer kw x kh coefficients (row-major,
+/* Convolve (local): U8 -> S16 (or U8, see hvxPointNode's notes), integer kw x kh coefficients (row-major,
  * applied without flipping, odd sizes up to 7x7), the sum floor-divided by
  * 2^shift and saturated to S16. */
 hvx_node hvxConvolveNode(hvx_graph g, hvx_image in, const int32_t* coeffs, int32_t kw,
@@ -329,7 +330,15 @@ hvx_node hvxConvolveNode(hvx_graph g, hvx_image in, const int32_t* coeffs, int32
  * point abstraction).  op HVX_POINT_MUL takes 2 S16 inputs; op
  * HVX_POINT_HARRIS_RESPONSE takes S32 Sxx, Syy, Sxy and params = {kn, kd}
  * (integers, k = kn / kd, 0 <= kn <= 1000, 1 <= kd <= 1000) and returns the
- * binary32 value nearest to Sxx*Syy - Sxy^2 - k (Sxx + Syy)^2. */
+ * binary32 value nearest to Sxx*Syy - Sxy^2 - k (Sxx + Syy)^2.  op
+ * HVX_POINT_TOMASI_RESPONSE (the Tomasi application of Section 6) takes S32
+ * Sxx, Syy, Sxy, no params, and returns the smaller eigenvalue of
+ * [Sxx Sxy; Sxy Syy] in binary32, 2 det / (tr + sqrt(tr^2 - 4 det)) from the
+ * exact 64-bit det and discriminant (a few binary32 rounding steps: within
+ * 1e-6 relative of the exact value).
+ *
+ * Convolve's output may also be a U8 image (the sum saturated to 0 .. 255);
+ * a virtual output is S16 unless created with format U8. */
 hvx_node hvxPointNode(hvx_graph g, int32_t op, const hvx_image* ins, int32_t n_in,
                       hvx_image out, const double* params, int32_t n_params);
 

@@ -729,6 +729,13 @@ hvx_node hvxPointNode(hvx_graph g, int32_t op, const hvx_image* ins, int32_t n_i
         p.kd = (int64_t)params[1];
         return add_node(g, N_POINT, {ins[0], ins[1], ins[2]}, {out}, 1, p);
     }
+    if (op == HVX_POINT_TOMASI_RESPONSE) {
+        if (n_in != 3 || !ins) {
+            G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+            return nullptr;
+        }
+        return add_node(g, N_POINT, {ins[0], ins[1], ins[2]}, {out}, 1, p);
+    }
     G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
     return nullptr;
 }

@@ -275,6 +275,16 @@ __device__ __forceinline__ int32_t eval_point(const P& st, int32_t a, int32_t b,
         case OP_NOT: return ~a & 0xFF;
         case OP_HARRIS:
             return __float_as_int(ratio_to_float(harris_q(a, b, c, st.k0, st.k1), st.k1));
+        case OP_TOMASI: {
+            // smaller eigenvalue of [a c; c b] = (tr - s) / 2 = 2 det / (tr + s),
+            // s = sqrt((a - b)^2 + 4 c^2), without the cancellation of tr - s
+            const long long det = (long long)a * b - (long long)c * c;
+            const long long d = (long long)a - b;
+            const long long disc = d * d + 4ll * c * c;  // < 2^53 for |a|, |b|, |c| < 2^25
+            const float s = sqrtf((float)disc), tr = (float)((long long)a + b);
+            const float den = tr + s;
+            return __float_as_int(den == 0.0f ? tr : 2.0f * (float)det / den);
+        }
     }
     return 0;
 }

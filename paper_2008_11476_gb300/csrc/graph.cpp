@@ -65,6 +65,7 @@ const char* op_name(int kind) {
         case OP_OR: return "or";
         case OP_XOR: return "xor";
         case OP_NOT: return "not";
+        case OP_TOMASI: return "tomasi_response";
     }
     return "?";
 }
@@ -145,7 +146,10 @@ void lower(Graph* g, Plan& P) {
                 break;
             }
             case N_POINT:
-                add(n->p.custom_op == HVX_POINT_MUL ? OP_MUL : OP_HARRIS, 0, 0);
+                add(n->p.custom_op == HVX_POINT_MUL      ? OP_MUL
+                    : n->p.custom_op == HVX_POINT_TOMASI_RESPONSE ? OP_TOMASI
+                                                             : OP_HARRIS,
+                    0, 0);
                 break;
             case N_LOCAL: {
                 add(OP_LSUM, 0, 0);
@@ -182,7 +186,12 @@ void infer(Op& op) {
         case OP_XOR: need(0, {HVX_DF_U8}); need(1, {HVX_DF_U8}); of = HVX_DF_U8; break;
         case OP_SOBEL_X:
         case OP_SOBEL_Y: need(0, {HVX_DF_U8}); of = HVX_DF_S16; break;
-        case OP_CONV: need(0, {HVX_DF_U8}); of = HVX_DF_S16; break;
+        case OP_CONV: {
+            need(0, {HVX_DF_U8});
+            const int declared = op.out->is_virtual ? op.out->user_fmt : op.out->fmt;
+            of = declared == HVX_DF_U8 ? HVX_DF_U8 : HVX_DF_S16;
+            break;
+        }
         case OP_LSUM: need(0, {HVX_DF_S32}); of = HVX_DF_S32; break;
         case OP_MAG: need(0, {HVX_DF_S16}); need(1, {HVX_DF_S16}); of = HVX_DF_S16; break;
         case OP_PHASE: need(0, {HVX_DF_S16}); need(1, {HVX_DF_S16}); of = HVX_DF_U8; break;
@@ -220,6 +229,7 @@ void infer(Op& op) {
         }
         case OP_MUL: need(0, {HVX_DF_S16}); need(1, {HVX_DF_S16}); of = HVX_DF_S32; break;
         case OP_HARRIS:
+        case OP_TOMASI:
             need(0, {HVX_DF_S32});
             need(1, {HVX_DF_S32});
             need(2, {HVX_DF_S32});

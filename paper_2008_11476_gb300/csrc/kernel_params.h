@@ -32,6 +32,7 @@ enum OpKind : int {
     OP_OR,
     OP_XOR,
     OP_NOT,
+    OP_TOMASI,
 };
 
 // ---------------------------------------------------------------------------

@@ -161,6 +161,7 @@ __device__ bool run_stage(const GenericDesc& d, int32_t* s, const GenStage& st, 
                     for (int dx = 0; dx < kw; ++dx)
                         t += (long long)d.coeff[st.coeff_off + dy * kw + dx] * q[dy * a.w + dx];
                 const long long v = t >> st.shift;  // arithmetic shift: floor division
+                if (st.i0 == HVX_DF_U8) return (int32_t)(v > 255 ? 255 : (v < 0 ? 0 : v));
                 return (int32_t)(v > 32767 ? 32767 : (v < -32768 ? -32768 : v));
             });
         case OP_LSUM:

@@ -448,6 +448,7 @@ hvx_status build_generic(Plan& P, Group& G) {
             if (coeffs + (int)c.size() > GEN_MAX_COEFF) return HVX_ERROR_NOT_SUPPORTED;
             st.coeff_off = coeffs;
             st.shift = op.node->p.shift;
+            st.i0 = op.out->fmt;  // U8 or S16: the saturation range
             for (int32_t v : c) d.coeff[coeffs++] = v;
         }
     }

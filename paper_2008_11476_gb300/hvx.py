@@ -35,7 +35,7 @@ HVX_THRESHOLD_BINARY, HVX_THRESHOLD_RANGE = 0, 1
 HVX_POLICY_WRAP, HVX_POLICY_SATURATE = 0, 1
 HVX_CHANNEL_Y, HVX_CHANNEL_U, HVX_CHANNEL_V = 0, 1, 2
 HVX_READ, HVX_WRITE = 1, 2
-HVX_POINT_MUL, HVX_POINT_HARRIS_RESPONSE = 1, 2
+HVX_POINT_MUL, HVX_POINT_HARRIS_RESPONSE, HVX_POINT_TOMASI_RESPONSE = 1, 2, 3
 HVX_LOCAL_SUM = 1
 HVX_GRAPH_NUM_NODES = 1
 HVX_GRAPH_NUM_OPS = 2

@@ -1,0 +1,139 @@
+"""GPU parity of the paper's Section 6 applications (paper_2008_11476_gb300/
+apps.py) against the CPU oracle run node by node on the same graph (written
+here again in the oracle's vocabulary), fused and unfused, on a frame-sized and
+a ragged image.  Integer outputs must match exactly; the Tomasi mask may differ
+only where the oracle's binary32 response lies within 1e-5 relative of the
+threshold (the GPU evaluates the eigenvalue in binary32)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import graph as OG
+from paper_2008_11476_gb300 import apps as A
+from paper_2008_11476_gb300 import graphs as PG
+from paper_2008_11476_gb300 import hvx as H
+from paper_2008_11476_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+B5 = [[1, 4, 6, 4, 1], [4, 16, 24, 16, 4], [6, 24, 36, 24, 6], [4, 16, 24, 16, 4],
+      [1, 4, 6, 4, 1]]
+B3 = [[1, 2, 1], [2, 4, 2], [1, 2, 1]]
+LAP = [[0, 1, 0], [1, -4, 1], [0, 1, 0]]
+SHARP = [[0, -1, 0], [-1, 8, -1], [0, -1, 0]]
+REP = dict(border="replicate")
+UND = dict(border="undefined")
+
+
+def oracle_graph(name, w, h):
+    """The application as an oracle graph; returns (graph, output names)."""
+    g = OG.GraphDesc()
+    g.image("in", w, h, "U8")
+    n = g.node
+    if name == "Gauss":
+        g.image("out", w, h, "U8")
+        n("convolve", ["in"], ["out"], coeffs=B5, shift=8, **REP)
+        return g, ["out"]
+    if name == "Laplacian":
+        g.image("out", w, h, "S16")
+        n("convolve", ["in"], ["out"], coeffs=LAP, shift=0, **REP)
+        return g, ["out"]
+    if name == "FChain":
+        g.virtual("a", fmt="U8")
+        g.virtual("b", fmt="U8")
+        g.image("out", w, h, "U8")
+        n("convolve", ["in"], ["a"], coeffs=B3, shift=4, **REP)
+        n("convolve", ["a"], ["b"], coeffs=B5, shift=8, **REP)
+        n("convolve", ["b"], ["out"], coeffs=SHARP, shift=2, **REP)
+        return g, ["out"]
+    if name == "SobelX":
+        g.image("gx", w, h, "S16")
+        n("sobel3x3", ["in"], ["gx", None], **REP)
+        return g, ["gx"]
+    if name == "EdgFig2":
+        for v in ("G", "gx", "gy", "m"):
+            g.virtual(v)
+        g.image("phase", w, h, "U8")
+        g.image("mask", w, h, "U8")
+        n("gaussian3x3", ["in"], ["G"], **REP)
+        n("sobel3x3", ["G"], ["gx", "gy"], **REP)
+        n("magnitude", ["gx", "gy"], ["m"])
+        n("threshold", ["m"], ["mask"], value=100)
+        n("phase", ["gx", "gy"], ["phase"])
+        return g, ["phase", "mask"]
+    if name == "Sobel":
+        for v in ("gx", "gy", "m"):
+            g.virtual(v)
+        g.image("out", w, h, "U8")
+        n("sobel3x3", ["in"], ["gx", "gy"], **REP)
+        n("magnitude", ["gx", "gy"], ["m"])
+        n("threshold", ["m"], ["out"], value=100)
+        return g, ["out"]
+    if name == "Unsharp":
+        g.virtual("blur")
+        g.virtual("d", fmt="S16")
+        g.virtual("d2", fmt="S16")
+        g.image("out", w, h, "S16")
+        n("gaussian3x3", ["in"], ["blur"], **REP)
+        n("subtract", ["in", "blur"], ["d"])
+        n("add", ["d", "d"], ["d2"])
+        n("add", ["in", "d2"], ["out"])
+        return g, ["out"]
+    # Harris / Tomasi
+    for v in ("gx", "gy", "pxx", "pyy", "pxy", "sxx", "syy", "sxy", "r"):
+        g.virtual(v)
+    g.image("mask", w, h, "U8")
+    n("sobel3x3", ["in"], ["gx", "gy"], **UND)
+    for p, a, b in (("pxx", "gx", "gx"), ("pyy", "gy", "gy"), ("pxy", "gx", "gy")):
+        n("mul", [a, b], [p])
+        n("window_sum", [p], ["s" + p[1:]], kw=5, kh=5, **UND)
+    if name == "Harris":
+        n("harris_response", ["sxx", "syy", "sxy"], ["r"], kn=1, kd=25)
+        n("threshold", ["r"], ["mask"], value=1e6)
+    else:
+        n("tomasi_response", ["sxx", "syy", "sxy"], ["r"])
+        n("threshold", ["r"], ["mask"], value=A.TOMASI_THRESHOLD)
+    return g, ["mask"]
+
+
+def tomasi_response_oracle(img):
+    gx, gy = O.sobel3x3(img, O.BORDER_UNDEFINED)
+    s = [O.window_sum(O.mul_s32(a, b), 5, 5, O.BORDER_UNDEFINED)
+         for a, b in ((gx, gx), (gy, gy), (gx, gy))]
+    return O.tomasi_response(*s)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hvxCreateContext()
+    yield c
+    H.hvxReleaseContext(c)
+
+
+@pytest.mark.parametrize("name", [a for a, _ in A.APPS])
+@pytest.mark.parametrize("w,h", [(640, 480), (385, 361)])
+def test_app_matches_oracle(ctx, name, w, h):
+    img = synth.rects_noise(w, h, seed=13)
+    og, outs = oracle_graph(name, w, h)
+    ref = OG.run(og, {"in": img})
+    build = dict(A.APPS)[name]
+    for fusion in (True, False):
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        g, res = build(ctx, src, w, h, fusion)
+        kinds = PG.kernel_kinds(g)
+        if fusion:
+            assert len(kinds) == 1, kinds
+        H.hvxProcessGraph(g)
+        for (oname, im, fmt), rname in zip(res, outs):
+            got = PG.download(im)
+            want = ref[rname].data
+            if name == "Tomasi":
+                lam = tomasi_response_oracle(img).data
+                near = np.abs(lam - A.TOMASI_THRESHOLD) <= 1e-5 * A.TOMASI_THRESHOLD
+                assert near.sum() < 20
+                np.testing.assert_array_equal(got[~near], want[~near])
+                assert want.any() and not want.all()
+            else:
+                np.testing.assert_array_equal(got, want)
+            assert H.hvxGetValidRegion(im) == ref[rname].rect
+        H.hvxReleaseGraph(g)
