@@ -111,6 +111,18 @@ typedef int32_t hvx_status;
 #define HVX_GRAPH_FUSION 7          /* int32: 1 if fusion is enabled            */
 #define HVX_GRAPH_KERNEL_KINDS 8    /* char[size]: comma-separated kernel names
                                        of the verified plan, in launch order   */
+#define HVX_GRAPH_GENERATED_KERNELS 9 /* int32: launches that run a kernel generated
+                                         for the graph (hvxSetGraphCodegen)     */
+
+/* Code generation modes (hvxSetGraphCodegen). */
+#define HVX_CODEGEN_OFF 0     /* staged-tile groups run the library's interpreter kernel */
+#define HVX_CODEGEN_AUTO 1    /* default: generate and compile a kernel per staged-tile
+                                 group when a device is present; if NVRTC is missing or
+                                 a group's shape is not handled, that group runs the
+                                 interpreter kernel (same results)                      */
+#define HVX_CODEGEN_REQUIRE 2 /* generate every staged-tile group's kernel, also in a
+                                 plan-only context (compile only); verification fails
+                                 with HVX_ERROR_NOT_SUPPORTED where that is impossible   */
 
 /* hvxQueryNode attributes */
 #define HVX_NODE_LIVE_OUTPUTS 1 /* uint32 bitmask: output i computed if bit i set */
@@ -250,6 +262,23 @@ hvx_status hvxWaitGraph(hvx_graph g);
  * device memory: the plain one-launch-per-node form.  Marks the graph
  * unverified. */
 hvx_status hvxSetGraphFusion(hvx_graph g, int32_t enable);
+
+/* Code generation for the graph's staged-tile groups (Section 5: the fused
+ * partitions of the graph become source code specialised to them).  At
+ * verification each such group's kernel is emitted as CUDA C++ with every
+ * operator, constant, border fill and coefficient compiled in, compiled with
+ * NVRTC for sm_103a and loaded; kernels are cached by source text for the life
+ * of the process, so graphs of the same shape compile once.  Generated
+ * kernels give the same results as the interpreter, cell for cell.  mode is
+ * HVX_CODEGEN_*; marks the graph unverified. */
+hvx_status hvxSetGraphCodegen(hvx_graph g, int32_t mode);
+
+/* Source text of the kernel generated for launch `group` of a verified graph
+ * (0-based, in launch order).  Writes at most size bytes including the
+ * terminating NUL to buf (buf may be NULL with size 0) and returns the full
+ * length; -1 if that launch runs no generated kernel or the graph is invalid
+ * or unverified. */
+int64_t hvxGetGraphKernelSource(hvx_graph g, int32_t group, char* buf, uint64_t size);
 
 /* Last error recorded on the graph (for NULL returns of node constructors). */
 hvx_status hvxGetGraphStatus(hvx_graph g);

@@ -3,6 +3,10 @@
 Every translation unit under csrc/ is compiled in parallel into _build/, then
 linked into paper_2008_11476_gb300/libhvx.so (CUDA runtime linked statically).
 A build is skipped when the library is newer than every source file.
+
+The headers that kernels generated at run time include (csrc/codegen.cpp
+compiles them with NVRTC) are embedded into the library as string constants:
+_build/jit_headers.inc is written from them before compiling.
 """
 from __future__ import annotations
 
@@ -19,7 +23,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhvx.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
+          "-I", BUILD]
+
+# (C++ identifier, header under csrc/) embedded for the run-time compiler
+JIT_HEADERS = [("kJitPointMath", "point_math.cuh"), ("kJitPhaseTable", "phase_table.h"),
+               ("kJitParams", "jit_params.h")]
 
 
 def nvcc() -> str:
@@ -42,10 +51,26 @@ def _stale() -> bool:
     return any(os.path.getmtime(f) > t for f in deps)
 
 
+def write_jit_headers() -> None:
+    parts = ["// Written by _build.py: headers of the kernels generated at run time.\n"]
+    for name, fn in JIT_HEADERS:
+        with open(os.path.join(CSRC, fn)) as f:
+            text = f.read()
+        if ")HVXJIT\"" in text:
+            raise RuntimeError(f"{fn} contains the raw-string delimiter")
+        parts.append(f'static const char {name}[] = R"HVXJIT({text})HVXJIT";\n')
+    out = os.path.join(BUILD, "jit_headers.inc")
+    tmp = out + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        f.write("".join(parts))
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_headers()
     cc = nvcc()
     procs = []
     objs = []

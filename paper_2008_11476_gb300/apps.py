@@ -6,7 +6,8 @@ library's nodes, for the suite benchmark (bench.py --workload apps) and tests.
     FChain     three chained convolutions (3x3 binomial, 5x5 binomial, 3x3 sharpen)
     SobelX     Sobel3x3, horizontal derivative only
     EdgFig2    the edge detector of Listing 1 / Fig. 2 (Gaussian, Sobel,
-               Magnitude -> Threshold, Phase)
+               Magnitude of the vertical derivative -> Threshold; the
+               horizontal derivative is the redundant kernel DCE removes)
     Sobel      Sobel3x3 -> Magnitude -> Threshold (three nodes)
     Unsharp    one Gaussian3x3 and three point nodes: in + 2 (in - blur), S16
     Harris     Sobel, three products, three 5x5 window sums, response, threshold
@@ -77,11 +78,17 @@ def sobel_x(ctx, src, w, h, fusion=True):
 
 
 def edg_fig2(ctx, src, w, h, fusion=True):
-    from . import graphs as PG
-    ph = _img(ctx, w, h, H.HVX_DF_U8)
-    mk = _img(ctx, w, h, H.HVX_DF_U8)
-    g = PG.edge_graph(ctx, src, ph, mk, fusion=fusion)
-    return g, [("phase", ph, H.HVX_DF_U8), ("mask", mk, H.HVX_DF_U8)]
+    # the graph of Listing 1 / Fig. 2 on a U8 input: only the vertical
+    # derivative reaches the output, so the horizontal one is dead
+    # (Algorithm 1 removes it) and Magnitude takes gy twice, as printed
+    out = _img(ctx, w, h, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(ctx)
+    blur, gx, gy, m = (H.hvxCreateVirtualImage(g) for _ in range(4))
+    _rep(H.hvxGaussian3x3Node(g, src, blur))
+    _rep(H.hvxSobel3x3Node(g, blur, gx, gy))
+    H.hvxMagnitudeNode(g, gy, gy, m)
+    H.hvxThresholdNode(g, m, H.HVX_THRESHOLD_BINARY, 100, 0, 255, 0, out)
+    return _done(g, fusion), [("out", out, H.HVX_DF_U8)]
 
 
 def sobel(ctx, src, w, h, fusion=True):

@@ -521,6 +521,31 @@ hvx_status hvxSetGraphFusion(hvx_graph hg, int32_t enable) {
     return HVX_SUCCESS;
 }
 
+hvx_status hvxSetGraphCodegen(hvx_graph hg, int32_t mode) {
+    if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
+    if (mode != HVX_CODEGEN_OFF && mode != HVX_CODEGEN_AUTO && mode != HVX_CODEGEN_REQUIRE)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    Graph* g = G(hg);
+    g->codegen = mode;
+    release_plan(g);
+    return HVX_SUCCESS;
+}
+
+int64_t hvxGetGraphKernelSource(hvx_graph hg, int32_t group, char* buf, uint64_t size) {
+    if (!ok_graph(hg)) return -1;
+    Graph* g = G(hg);
+    if (!g->verified || group < 0 || group >= (int32_t)g->plan.groups.size()) return -1;
+    const Group& gr = g->plan.groups[group];
+    if (!gr.jit_on) return -1;
+    const std::string& s = jit_source(gr.jit);
+    if (buf && size > 0) {
+        const uint64_t n = std::min<uint64_t>(size - 1, s.size());
+        std::memcpy(buf, s.data(), n);
+        buf[n] = '\0';
+    }
+    return (int64_t)s.size();
+}
+
 hvx_status hvxGetGraphStatus(hvx_graph hg) {
     if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
     return G(hg)->last;
@@ -552,6 +577,11 @@ hvx_status hvxQueryGraph(hvx_graph hg, int32_t attr, void* out, uint64_t size) {
         case HVX_GRAPH_NUM_LAUNCHES: return put32((int32_t)g->plan.groups.size());
         case HVX_GRAPH_INTERMEDIATE_BYTES: return put64(g->plan.intermediate_bytes);
         case HVX_GRAPH_EXTERNAL_BYTES: return put64(g->plan.external_bytes);
+        case HVX_GRAPH_GENERATED_KERNELS: {
+            int32_t n = 0;
+            for (const Group& gr : g->plan.groups) n += gr.jit_on ? 1 : 0;
+            return put32(n);
+        }
         case HVX_GRAPH_KERNEL_KINDS: {
             const std::string& s = g->plan.kernel_kinds;
             if (size < s.size() + 1) return HVX_ERROR_INVALID_PARAMETERS;

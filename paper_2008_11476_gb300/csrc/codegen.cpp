@@ -1,0 +1,1018 @@
+// Code generation for fused groups (Section 5: the paper's framework turns
+// every fused OpenVX graph partition into source code specialised to it and
+// compiles that; here the source is CUDA C++ for sm_103a, compiled at verify
+// time with NVRTC and loaded with the driver API).
+//
+// The generated kernel computes one output tile per CTA, like the staged-tile
+// interpreter (kernels_generic.cu), with the same results cell for cell:
+//   * every operator, constant, format, border fill and coefficient is
+//     compiled in (constant propagation); zero convolution taps disappear and
+//     sums are accumulated in 32 bits where the input range allows;
+//   * only images that a local operator reads are staged in shared memory;
+//     point operators, and local operators read only by point operators, are
+//     evaluated inline where their value is used, each once per cell;
+//   * images staged at the same depth of local operators with the same halo
+//     are produced by one pass over the cells (e.g. the three Harris / Tomasi
+//     products, from one inline Sobel);
+//   * tiles whose cells all lie inside every image's valid region (all but a
+//     ring of tiles along the image border) run without a single bounds,
+//     validity or fill test; the others run the checked instance of the same
+//     template.
+// Kernels are cached by source text, so graphs of the same shape share one.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hvx_internal.h"
+#include "jit_params.h"
+#include "kernel_params.h"
+
+namespace hvx {
+
+static_assert(HVX_JIT_MAX_BUF == GEN_MAX_BUF, "generated kernels index the group's buffers");
+static_assert(HVX_JIT_MAX_EXT == GEN_MAX_EXT, "generated kernels index the group's images");
+
+namespace {
+
+// Headers compiled into the library (written by _build.py from csrc/): the
+// exact point arithmetic and the launch parameter block.
+#include "jit_headers.inc"
+
+// ---------------------------------------------------------------------------
+// NVRTC, opened at run time (the toolkit's libnvrtc), and the driver calls
+// that load and launch a compiled module.
+
+typedef int (*FnCreate)(void**, const char*, const char*, int, const char* const*,
+                        const char* const*);
+typedef int (*FnCompile)(void*, int, const char* const*);
+typedef int (*FnSize)(void*, size_t*);
+typedef int (*FnGet)(void*, char*);
+typedef int (*FnDestroy)(void**);
+typedef CUresult (*FnModuleLoadData)(CUmodule*, const void*);
+typedef CUresult (*FnModuleGetFunction)(CUfunction*, CUmodule, const char*);
+typedef CUresult (*FnFuncSetAttribute)(CUfunction, CUfunction_attribute, int);
+typedef CUresult (*FnLaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
+                                   unsigned, unsigned, CUstream, void**, void**);
+
+struct Nvrtc {
+    bool ok = false;
+    std::string why;
+    FnCreate create = nullptr;
+    FnCompile compile = nullptr;
+    FnSize cubin_size = nullptr, log_size = nullptr;
+    FnGet cubin = nullptr, log = nullptr;
+    FnDestroy destroy = nullptr;
+};
+
+Nvrtc& nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        std::vector<std::string> dirs;
+        if (const char* h = getenv("CUDA_HOME")) dirs.push_back(std::string(h) + "/lib64/");
+        dirs.push_back("/usr/local/cuda/lib64/");
+        dirs.push_back("");
+        void* lib = nullptr;
+        for (const std::string& d : dirs) {
+            // the builtins library first, so that NVRTC finds it whatever the
+            // loader's search path
+            dlopen((d + "libnvrtc-builtins.so.13.0").c_str(), RTLD_NOW | RTLD_GLOBAL);
+            lib = dlopen((d + "libnvrtc.so.13").c_str(), RTLD_NOW | RTLD_GLOBAL);
+            if (lib) break;
+        }
+        if (!lib) {
+            n.why = "libnvrtc.so.13 not found";
+            return;
+        }
+        n.create = (FnCreate)dlsym(lib, "nvrtcCreateProgram");
+        n.compile = (FnCompile)dlsym(lib, "nvrtcCompileProgram");
+        n.cubin_size = (FnSize)dlsym(lib, "nvrtcGetCUBINSize");
+        n.cubin = (FnGet)dlsym(lib, "nvrtcGetCUBIN");
+        n.log_size = (FnSize)dlsym(lib, "nvrtcGetProgramLogSize");
+        n.log = (FnGet)dlsym(lib, "nvrtcGetProgramLog");
+        n.destroy = (FnDestroy)dlsym(lib, "nvrtcDestroyProgram");
+        n.ok = n.create && n.compile && n.cubin_size && n.cubin && n.log_size && n.log &&
+               n.destroy;
+        if (!n.ok) n.why = "libnvrtc lacks an entry point";
+    });
+    return n;
+}
+
+struct Driver {
+    bool ok = false;
+    FnModuleLoadData load = nullptr;
+    FnModuleGetFunction get = nullptr;
+    FnFuncSetAttribute attr = nullptr;
+    FnLaunchKernel launch = nullptr;
+};
+
+Driver& driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto entry = [](const char* name) -> void* {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion(name, &fn, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            return fn;
+        };
+        d.load = (FnModuleLoadData)entry("cuModuleLoadData");
+        d.get = (FnModuleGetFunction)entry("cuModuleGetFunction");
+        d.attr = (FnFuncSetAttribute)entry("cuFuncSetAttribute");
+        d.launch = (FnLaunchKernel)entry("cuLaunchKernel");
+        d.ok = d.load && d.get && d.attr && d.launch;
+    });
+    return d;
+}
+
+}  // namespace
+
+// One compiled (and, with a device, loaded) generated kernel.
+struct JitKernel {
+    std::string source;
+    std::string log;
+    std::vector<char> cubin;
+    bool compiled = false;
+    int device = -1;           // loaded on this device (-1: not loaded)
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    int smem_bytes = 0;
+    int tw = 0, th = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Source emission
+
+constexpr int kThreads = 256;  // 8 warps: warps take rows, lanes columns
+
+struct Emitter {
+    const GenericDesc& d;
+    int tw = 0, th = 0;
+    std::vector<int> producer;  // buffer -> stage index, or -1 (external input)
+    std::vector<int> ext_in;    // buffer -> external input index, or -1
+    std::vector<bool> staged;   // buffer lives in shared memory
+    std::vector<int> level;     // depth of local operators
+    // Separable window sums and convolutions (a rank-one integer kernel
+    // r s^T of at least 15 taps): row sums with s are staged in shared
+    // memory, the column sum with r is taken where the value is used.
+    std::vector<std::vector<int>> sep_s, sep_r;  // per stage; empty: not separable
+
+    // Shared-memory slots: staged images (slot = buffer) and row-sum buffers
+    // (slot = n_buf + stage); live from the pass that writes them to the
+    // last pass that reads them, so slots of disjoint lifetimes share words.
+    struct Slot {
+        int w = 0, h = 0;
+        int def = -1, last = -1;
+        int off = -1;
+    };
+    std::vector<Slot> slot;
+
+    enum PassKind { LOAD, ROW, CELLS, OUT };
+    struct Pass {
+        PassKind kind = CELLS;
+        int h = 0;                  // halo of the cells (CELLS / OUT)
+        std::vector<int> targets;   // buffers (LOAD / CELLS) or stages (ROW)
+        std::vector<bool> need_op;  // CELLS / OUT: stages evaluated at each cell
+        std::vector<bool> need_ld;  // external images read directly
+        std::vector<bool> read_cell;  // staged buffers read at the cell itself
+    };
+    std::vector<Pass> passes;
+    int smem_words = 0;
+    std::ostringstream o;
+
+    explicit Emitter(const GenericDesc& desc) : d(desc) {}
+
+    static bool is_local(int op) {
+        return op == OP_GAUSS || op == OP_BOX || op == OP_SOBEL_X || op == OP_SOBEL_Y ||
+               op == OP_CONV || op == OP_LSUM || op == OP_DILATE || op == OP_ERODE ||
+               op == OP_MEDIAN;
+    }
+
+    int bw(int b) const { return tw + 2 * d.buf[b].halo; }
+    int bh(int b) const { return th + 2 * d.buf[b].halo; }
+    int row_slot(int k) const { return d.n_buf + k; }
+    bool separable(int k) const { return !sep_s[k].empty(); }
+
+    // c (kh x kw, row-major) = r s^T with integer r, s; s primitive.
+    static bool factor(const int32_t* c, int kw, int kh, std::vector<int>& s, std::vector<int>& r) {
+        int i0 = -1;
+        for (int i = 0; i < kh && i0 < 0; ++i)
+            for (int j = 0; j < kw; ++j)
+                if (c[i * kw + j] != 0) {
+                    i0 = i;
+                    break;
+                }
+        if (i0 < 0) return false;
+        int g = 0;
+        for (int j = 0; j < kw; ++j) {
+            int a = std::abs(c[i0 * kw + j]);
+            while (a) {
+                const int t = g % a;
+                g = a;
+                a = t;
+            }
+        }
+        s.assign(kw, 0);
+        r.assign(kh, 0);
+        int j0 = -1;
+        for (int j = 0; j < kw; ++j) {
+            s[j] = c[i0 * kw + j] / g;
+            if (s[j] != 0 && j0 < 0) j0 = j;
+        }
+        for (int i = 0; i < kh; ++i) {
+            if (c[i * kw + j0] % s[j0] != 0) return false;
+            r[i] = c[i * kw + j0] / s[j0];
+            for (int j = 0; j < kw; ++j)
+                if ((long long)c[i * kw + j] != (long long)r[i] * s[j]) return false;
+        }
+        return true;
+    }
+
+    void analyse() {
+        const int nb = d.n_buf;
+        producer.assign(nb, -1);
+        ext_in.assign(nb, -1);
+        staged.assign(nb, false);
+        level.assign(nb, 0);
+        sep_s.assign(d.n_stage, {});
+        sep_r.assign(d.n_stage, {});
+        for (int e = 0; e < d.n_in; ++e) ext_in[d.in[e].buf] = e;
+        for (int k = 0; k < d.n_stage; ++k) {
+            const GenStage& st = d.st[k];
+            producer[st.out] = k;
+            if (is_local(st.op)) staged[st.in[0]] = true;
+            const int kw = 2 * st.rx + 1, kh = 2 * st.ry + 1;
+            if (kw < 3 || kh < 3 || kw * kh < 15) continue;
+            if (st.op == OP_LSUM) {
+                sep_s[k].assign(kw, 1);
+                sep_r[k].assign(kh, 1);
+            } else if (st.op == OP_CONV) {
+                std::vector<int> fs, fr;
+                long long bound = 0;
+                for (int i = 0; i < kw * kh; ++i)
+                    bound += std::llabs((long long)d.coeff[st.coeff_off + i]);
+                bound *= max_abs(d.buf[st.in[0]].fmt);
+                // row sums are stored as int32: only when the whole sum fits
+                if (bound < (1ll << 31) && factor(d.coeff + st.coeff_off, kw, kh, fs, fr)) {
+                    sep_s[k] = fs;
+                    sep_r[k] = fr;
+                }
+            }
+        }
+        for (int k = 0; k < d.n_stage; ++k) {  // stages are in topological order
+            const GenStage& st = d.st[k];
+            int l = 0;
+            for (int i = 0; i < 3; ++i)
+                if (st.in[i] >= 0) l = std::max(l, level[st.in[i]]);
+            level[st.out] = l + (is_local(st.op) ? 1 : 0);
+        }
+    }
+
+    // Marks what a pass must evaluate to produce buffer b at a cell: ops
+    // evaluated inline and external images read directly.  False if a local
+    // operator's input is not staged yet.
+    bool visit(int b, const std::vector<bool>& avail, Pass& p) {
+        if (avail[b]) {
+            p.read_cell[b] = true;
+            return true;
+        }
+        if (ext_in[b] >= 0) {
+            if (staged[b]) return false;
+            p.need_ld[b] = true;
+            return true;
+        }
+        const int k = producer[b];
+        if (k < 0) return false;
+        if (p.need_op[k]) return true;
+        p.need_op[k] = true;
+        const GenStage& st = d.st[k];
+        if (is_local(st.op)) return avail[st.in[0]];
+        for (int i = 0; i < 3; ++i)
+            if (st.in[i] >= 0 && !visit(st.in[i], avail, p)) return false;
+        return true;
+    }
+
+    bool add_cells_pass(const std::vector<int>& targets, int h, std::vector<bool>& avail,
+                        std::vector<bool>& rows_done) {
+        Pass p;
+        p.kind = targets.empty() ? OUT : CELLS;
+        p.h = h;
+        p.targets = targets;
+        p.need_op.assign(d.n_stage, false);
+        p.need_ld.assign(d.n_buf, false);
+        p.read_cell.assign(d.n_buf, false);
+        std::vector<int> want = targets;
+        if (targets.empty())
+            for (int e = 0; e < d.n_out; ++e) want.push_back(d.out[e].buf);
+        for (int b : want)
+            if (!visit(b, avail, p)) return false;
+        Pass rp;
+        rp.kind = ROW;
+        for (int k = 0; k < d.n_stage; ++k)
+            if (p.need_op[k] && separable(k) && !rows_done[k]) {
+                rp.targets.push_back(k);
+                rows_done[k] = true;
+            }
+        if (!rp.targets.empty()) passes.push_back(rp);
+        passes.push_back(p);
+        for (int b : targets) avail[b] = true;
+        return true;
+    }
+
+    // Pass list: staged external inputs, then staged op outputs by depth of
+    // local operators and halo (larger first; equal ones share a pass), each
+    // preceded by the row sums it needs, then the external outputs.
+    bool plan() {
+        passes.clear();
+        std::vector<bool> avail(d.n_buf, false), rows_done(d.n_stage, false);
+        Pass ld;
+        ld.kind = LOAD;
+        for (int b = 0; b < d.n_buf; ++b)
+            if (staged[b] && ext_in[b] >= 0) {
+                ld.targets.push_back(b);
+                avail[b] = true;
+            }
+        if (!ld.targets.empty()) passes.push_back(ld);
+        std::vector<int> order;
+        for (int b = 0; b < d.n_buf; ++b)
+            if (staged[b] && ext_in[b] < 0) order.push_back(b);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (level[a] != level[b]) return level[a] < level[b];
+            return d.buf[a].halo > d.buf[b].halo;
+        });
+        for (size_t i = 0; i < order.size();) {
+            std::vector<int> tg{order[i]};
+            size_t j = i + 1;
+            while (j < order.size() && level[order[j]] == level[order[i]] &&
+                   d.buf[order[j]].halo == d.buf[order[i]].halo)
+                tg.push_back(order[j++]);
+            if (!add_cells_pass(tg, d.buf[order[i]].halo, avail, rows_done)) return false;
+            i = j;
+        }
+        return add_cells_pass({}, 0, avail, rows_done);
+    }
+
+    // Slot sizes for the current tile, lifetimes, and first-fit offsets among
+    // slots whose lifetimes overlap; returns the words needed.
+    int allocate() {
+        slot.assign(d.n_buf + d.n_stage, Slot{});
+        for (int b = 0; b < d.n_buf; ++b)
+            if (staged[b]) {
+                slot[b].w = bw(b);
+                slot[b].h = bh(b);
+            }
+        for (int k = 0; k < d.n_stage; ++k)
+            if (separable(k)) {
+                const int hl = d.buf[d.st[k].out].halo;
+                slot[row_slot(k)].w = tw + 2 * hl;
+                slot[row_slot(k)].h = th + 2 * hl + 2 * d.st[k].ry;
+            }
+        auto use = [&](int s, int i) { slot[s].last = std::max(slot[s].last, i); };
+        for (int i = 0; i < (int)passes.size(); ++i) {
+            const Pass& p = passes[i];
+            if (p.kind == LOAD) {
+                for (int b : p.targets) slot[b].def = i;
+            } else if (p.kind == ROW) {
+                for (int k : p.targets) {
+                    slot[row_slot(k)].def = i;
+                    use(d.st[k].in[0], i);
+                }
+            } else {
+                for (int b : p.targets) slot[b].def = i;
+                for (int b = 0; b < d.n_buf; ++b)
+                    if (p.read_cell[b]) use(b, i);
+                for (int k = 0; k < d.n_stage; ++k)
+                    if (p.need_op[k] && is_local(d.st[k].op))
+                        use(separable(k) ? row_slot(k) : d.st[k].in[0], i);
+            }
+        }
+        std::vector<int> ids;
+        for (int s = 0; s < (int)slot.size(); ++s)
+            if (slot[s].w > 0) {
+                if (slot[s].last < slot[s].def) slot[s].last = slot[s].def;
+                ids.push_back(s);
+            }
+        std::stable_sort(ids.begin(), ids.end(),
+                         [&](int a, int b) { return slot[a].def < slot[b].def; });
+        int words = 0;
+        std::vector<int> placed;
+        for (int s : ids) {
+            const int n = (slot[s].w * slot[s].h + 3) & ~3;  // 16-byte aligned slots
+            std::vector<std::pair<int, int>> busy;
+            for (int t : placed)
+                if (slot[t].def <= slot[s].last && slot[s].def <= slot[t].last)
+                    busy.push_back({slot[t].off, slot[t].off + ((slot[t].w * slot[t].h + 3) & ~3)});
+            std::sort(busy.begin(), busy.end());
+            int off = 0;
+            for (const auto& iv : busy) {
+                if (off + n <= iv.first) break;
+                off = std::max(off, iv.second);
+            }
+            slot[s].off = off;
+            placed.push_back(s);
+            words = std::max(words, off + n);
+        }
+        return words;
+    }
+
+    // Tile shape: the largest whose shared memory fits twice per SM.
+    bool choose_tile() {
+        static const int shapes[][2] = {{128, 32}, {128, 16}, {64, 16}, {32, 16}};
+        for (const auto& sh : shapes) {
+            tw = sh[0];
+            th = sh[1];
+            smem_words = allocate();
+            if (smem_words * 4 <= 110 * 1024) return true;
+        }
+        return false;
+    }
+
+    static std::string lit64(long long v) {
+        if (v == (-9223372036854775807ll - 1)) return "(-9223372036854775807LL - 1)";
+        return "(" + std::to_string(v) + "LL)";
+    }
+
+    static std::string flit(float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return "__int_as_float(" + std::to_string((int32_t)u) + ")";
+    }
+
+    // Largest |value| an image of this format holds.
+    static long long max_abs(int fmt) {
+        switch (fmt) {
+            case HVX_DF_U8: return 255;
+            case HVX_DF_S16: return 32768;
+            case HVX_DF_UYVY: return 65535;
+            default: return 2147483648ll;
+        }
+    }
+
+    // Expression of the value of buffer b at the current cell.
+    std::string val(int b) const { return "v" + std::to_string(b); }
+
+    // Read of staged buffer b at offset (dx, dy) from the current cell.
+    std::string tap(int b, int dx, int dy) const {
+        const int off = dy * bw(b) + dx;
+        std::string s = "B" + std::to_string(b) + "[q" + std::to_string(b);
+        if (off > 0) s += " + " + std::to_string(off);
+        if (off < 0) s += " - " + std::to_string(-off);
+        return s + "]";
+    }
+
+    std::string point_expr(const GenStage& st) const {
+        const std::string a = st.in[0] >= 0 ? val(st.in[0]) : "0";
+        const std::string b = st.in[1] >= 0 ? val(st.in[1]) : "0";
+        const std::string c = st.in[2] >= 0 ? val(st.in[2]) : "0";
+        switch (st.op) {
+            case OP_MAG: return "magnitude_s16(" + a + ", " + b + ")";
+            case OP_PHASE: return "(int)phase_u8(" + a + ", " + b + ")";
+            case OP_THRESH: {
+                std::string t;
+                if (st.i3) {
+                    const std::string f = "__int_as_float(" + a + ")";
+                    t = st.i0 == HVX_THRESHOLD_BINARY
+                            ? "(" + f + " > " + flit(st.f0) + ")"
+                            : "!(" + f + " > " + flit(st.f1) + " || " + f + " < " + flit(st.f0) +
+                                  ")";
+                } else {
+                    const std::string v = "(long long)" + a;
+                    t = st.i0 == HVX_THRESHOLD_BINARY
+                            ? "(" + v + " > " + lit64(st.k0) + ")"
+                            : "!(" + v + " > " + lit64(st.k1) + " || " + v + " < " +
+                                  lit64(st.k0) + ")";
+                }
+                return "(" + t + " ? " + std::to_string(st.i1) + " : " + std::to_string(st.i2) +
+                       ")";
+            }
+            case OP_CHX: return "((" + a + " >> 8) & 0xFF)";
+            case OP_ADD:
+            case OP_SUB:
+            case OP_ABSDIFF: {
+                std::string r = st.op == OP_ADD   ? "(" + a + " + " + b + ")"
+                                : st.op == OP_SUB ? "(" + a + " - " + b + ")"
+                                                  : "abs(" + a + " - " + b + ")";
+                if (st.i1 == HVX_DF_U8) return st.i0 ? "sat_u8(" + r + ")" : "(" + r + " & 0xFF)";
+                return st.i0 ? "sat_s16(" + r + ")"
+                             : "(int)(short)(unsigned short)(" + r + " & 0xFFFF)";
+            }
+            case OP_MUL: return "(int)((unsigned)" + a + " * (unsigned)" + b + ")";
+            case OP_AND: return "(" + a + " & " + b + ")";
+            case OP_OR: return "(" + a + " | " + b + ")";
+            case OP_XOR: return "(" + a + " ^ " + b + ")";
+            case OP_NOT: return "(~" + a + " & 0xFF)";
+            case OP_HARRIS:
+                return "__float_as_int(ratio_to_float(harris_q(" + a + ", " + b + ", " + c + ", " +
+                       lit64(st.k0) + ", " + lit64(st.k1) + "), " + lit64(st.k1) + "))";
+            case OP_TOMASI:
+                return "__float_as_int(tomasi_response_f32(" + a + ", " + b + ", " + c + "))";
+        }
+        return "0";
+    }
+
+    // Statements assigning the local operator of stage k at the current cell
+    // to variable `dst` (its input is staged).
+    void emit_local(const GenStage& st, const std::string& dst, const std::string& ind) {
+        const int b = st.in[0];
+        auto T = [&](int dx, int dy) { return tap(b, dx, dy); };
+        switch (st.op) {
+            case OP_GAUSS:
+            case OP_BOX: {
+                const bool g = st.op == OP_GAUSS, near = st.rounding == HVX_ROUND_TO_NEAREST;
+                o << ind << "{\n" << ind << "  const int t = ";
+                if (g)
+                    o << "(" << T(-1, -1) << " + 2 * " << T(0, -1) << " + " << T(1, -1) << ") + 2 * ("
+                      << T(-1, 0) << " + 2 * " << T(0, 0) << " + " << T(1, 0) << ") + (" << T(-1, 1)
+                      << " + 2 * " << T(0, 1) << " + " << T(1, 1) << ");\n";
+                else {
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            o << T(dx, dy) << ((dx == 1 && dy == 1) ? ";\n" : " + ");
+                }
+                if (g)
+                    o << ind << "  " << dst << " = " << (near ? "(t + 8) >> 4" : "t >> 4") << ";\n";
+                else
+                    o << ind << "  " << dst << " = " << (near ? "(t + 4) / 9" : "t / 9") << ";\n";
+                o << ind << "}\n";
+                return;
+            }
+            case OP_SOBEL_X:
+                o << ind << dst << " = (" << T(1, -1) << " - " << T(-1, -1) << ") + 2 * (" << T(1, 0)
+                  << " - " << T(-1, 0) << ") + (" << T(1, 1) << " - " << T(-1, 1) << ");\n";
+                return;
+            case OP_SOBEL_Y:
+                o << ind << dst << " = (" << T(-1, 1) << " - " << T(-1, -1) << ") + 2 * (" << T(0, 1)
+                  << " - " << T(0, -1) << ") + (" << T(1, 1) << " - " << T(1, -1) << ");\n";
+                return;
+            case OP_DILATE:
+            case OP_ERODE: {
+                const char* f = st.op == OP_DILATE ? "max" : "min";
+                o << ind << "{\n" << ind << "  int m = " << T(-1, -1) << ";\n";
+                for (int k = 1; k < 9; ++k)
+                    o << ind << "  m = " << f << "(m, " << T(k % 3 - 1, k / 3 - 1) << ");\n";
+                o << ind << "  " << dst << " = m;\n" << ind << "}\n";
+                return;
+            }
+            case OP_MEDIAN: {
+                // median of nine by the exchange network of Paeth (Graphics Gems)
+                o << ind << "{\n";
+                for (int k = 0; k < 9; ++k)
+                    o << ind << "  int m" << k << " = " << T(k % 3 - 1, k / 3 - 1) << ";\n";
+                static const int net[19][2] = {{1, 2}, {4, 5}, {7, 8}, {0, 1}, {3, 4}, {6, 7},
+                                               {1, 2}, {4, 5}, {7, 8}, {0, 3}, {5, 8}, {4, 7},
+                                               {3, 6}, {1, 4}, {2, 5}, {4, 7}, {4, 2}, {6, 4},
+                                               {4, 2}};
+                for (const auto& e : net)
+                    o << ind << "  { const int lo = min(m" << e[0] << ", m" << e[1]
+                      << "), hi = max(m" << e[0] << ", m" << e[1] << "); m" << e[0] << " = lo; m"
+                      << e[1] << " = hi; }\n";
+                o << ind << "  " << dst << " = m4;\n" << ind << "}\n";
+                return;
+            }
+            case OP_CONV: {
+                const int kw = 2 * st.rx + 1, kh = 2 * st.ry + 1;
+                long long bound = 0;
+                for (int i = 0; i < kw * kh; ++i)
+                    bound += std::llabs((long long)d.coeff[st.coeff_off + i]);
+                bound *= max_abs(d.buf[b].fmt);
+                const bool narrow = bound < (1ll << 31);
+                const char* acc = narrow ? "int" : "long long";
+                o << ind << "{\n" << ind << "  " << acc << " t = 0;\n";
+                for (int dy = 0; dy < kh; ++dy)
+                    for (int dx = 0; dx < kw; ++dx) {
+                        const int c = d.coeff[st.coeff_off + dy * kw + dx];
+                        if (c == 0) continue;
+                        o << ind << "  t += ";
+                        if (c != 1) o << "(" << acc << ")" << c << " * ";
+                        o << "(" << acc << ")" << T(dx - st.rx, dy - st.ry) << ";\n";
+                    }
+                o << ind << "  t >>= " << st.shift << ";\n";
+                if (st.i0 == HVX_DF_U8)
+                    o << ind << "  " << dst << " = (int)(t > 255 ? 255 : (t < 0 ? 0 : t));\n";
+                else
+                    o << ind << "  " << dst
+                      << " = (int)(t > 32767 ? 32767 : (t < -32768 ? -32768 : t));\n";
+                o << ind << "}\n";
+                return;
+            }
+            case OP_LSUM: {
+                // int32 wrap-around sum: the low 32 bits of the exact sum
+                o << ind << "{\n" << ind << "  unsigned t = 0;\n";
+                for (int dy = -st.ry; dy <= st.ry; ++dy)
+                    for (int dx = -st.rx; dx <= st.rx; ++dx)
+                        o << ind << "  t += (unsigned)" << T(dx, dy) << ";\n";
+                o << ind << "  " << dst << " = (int)t;\n" << ind << "}\n";
+                return;
+            }
+        }
+    }
+
+    // The cell loop of a pass: warps take rows, lanes consecutive columns
+    // (conflict-free shared-memory rows); cell (c, r) is image pixel
+    // (x0 + c - xo, y0 + r - yo).
+    void open_cells(int rows, int cols, int xo, int yo, bool unroll_rows, bool xy = true) {
+        o << (unroll_rows ? "  #pragma unroll\n" : "  #pragma unroll 1\n")
+          << "  for (int r = warp; r < " << rows << "; r += " << kThreads / 32 << ") {\n"
+          << "    #pragma unroll\n"
+          << "    for (int c = lane; c < " << cols << "; c += 32) {\n";
+        if (xy) o << "      const int x = x0 + c - " << xo << ", y = y0 + r - " << yo << ";\n";
+    }
+    void close_cells() { o << "    }\n  }\n"; }
+
+    // Fill value of a cell of staged buffer b outside the image:
+    // `clamped_read` reads the buffer (or the external image) at the nearest
+    // image pixel.
+    std::string fill_expr(int b, const std::string& clamped_read) const {
+        const GenBuf& g = d.buf[b];
+        if (g.fill == FILL_CONSTANT) return std::to_string(g.cval);
+        if (g.fill == FILL_REPLICATE) return clamped_read;
+        return "0";
+    }
+
+    std::string slot_name(int s) const {
+        return s < d.n_buf ? "B" + std::to_string(s) : "R" + std::to_string(s - d.n_buf);
+    }
+
+    // All loads of a staged external input are independent: both loops are
+    // unrolled so that they are all in flight at once.
+    void emit_load(int b) {
+        const int e = ext_in[b], h = d.buf[b].halo;
+        const std::string ld = "hvx_ld<" + std::to_string(d.in[e].fmt) + ">(p.in[" +
+                               std::to_string(e) + "], p.in_pitch[" + std::to_string(e) + "], ";
+        o << "  // external input " << e << " -> B" << b << " (halo " << h << ")\n";
+        open_cells(bh(b), bw(b), h, h, true);
+        o << "      int v;\n"
+          << "      if (!CHECK || (x >= 0 && x < p.W && y >= 0 && y < p.H)) v = " << ld
+          << "x, y);\n"
+          << "      else v = "
+          << fill_expr(b, ld + "min(max(x, 0), p.W - 1), min(max(y, 0), p.H - 1))") << ";\n"
+          << "      B" << b << "[r * " << bw(b) << " + c] = v;\n";
+        close_cells();
+    }
+
+    // Row sums of separable stage k over its output region grown by its row
+    // radius; its staged input covers that region (input halo >= output
+    // halo + radius) and holds border fills where it leaves the image.
+    void emit_row(int k) {
+        const GenStage& st = d.st[k];
+        const int b = st.in[0], hb = d.buf[b].halo, hl = d.buf[st.out].halo;
+        const Slot& R = slot[row_slot(k)];
+        o << "  // row sums of op " << k << " -> R" << k << " (" << R.w << " x " << R.h << ")\n";
+        open_cells(R.h, R.w, 0, 0, false, false);
+        o << "      const int q = (r + " << hb - hl - st.ry << ") * " << bw(b) << " + c + "
+          << hb - hl << ";\n";
+        const bool lsum = st.op == OP_LSUM;
+        o << "      " << (lsum ? "unsigned" : "int") << " t = 0;\n";
+        for (int j = 0; j < (int)sep_s[k].size(); ++j) {
+            const int c = sep_s[k][j];
+            if (c == 0) continue;
+            const int off = j - st.rx;
+            const std::string rd = "B" + std::to_string(b) + "[q" +
+                                   (off > 0 ? " + " + std::to_string(off)
+                                            : off < 0 ? " - " + std::to_string(-off) : "") +
+                                   "]";
+            if (lsum)
+                o << "      t += (unsigned)" << rd << ";\n";
+            else
+                o << "      t += " << (c == 1 ? "" : std::to_string(c) + " * ") << rd << ";\n";
+        }
+        o << "      R" << k << "[r * " << R.w << " + c] = (int)t;\n";
+        close_cells();
+    }
+
+    // Column sum of separable stage k at the current cell of a pass of halo h.
+    void emit_sep(int k, const std::string& dst, const std::string& ind) {
+        const GenStage& st = d.st[k];
+        const Slot& R = slot[row_slot(k)];
+        const bool lsum = st.op == OP_LSUM;
+        o << ind << "{\n" << ind << "  " << (lsum ? "unsigned" : "int") << " t = 0;\n";
+        for (int i = 0; i < (int)sep_r[k].size(); ++i) {
+            const int c = sep_r[k][i];
+            if (c == 0) continue;
+            const int off = (i - st.ry) * R.w;
+            const std::string rd = "R" + std::to_string(k) + "[qR" + std::to_string(k) +
+                                   (off > 0 ? " + " + std::to_string(off)
+                                            : off < 0 ? " - " + std::to_string(-off) : "") +
+                                   "]";
+            if (lsum)
+                o << ind << "  t += (unsigned)" << rd << ";\n";
+            else
+                o << ind << "  t += " << (c == 1 ? "" : std::to_string(c) + " * ") << rd << ";\n";
+        }
+        if (lsum) {
+            o << ind << "  " << dst << " = (int)t;\n";
+        } else {
+            o << ind << "  t >>= " << st.shift << ";\n";
+            if (st.i0 == HVX_DF_U8)
+                o << ind << "  " << dst << " = t > 255 ? 255 : (t < 0 ? 0 : t);\n";
+            else
+                o << ind << "  " << dst << " = t > 32767 ? 32767 : (t < -32768 ? -32768 : t);\n";
+        }
+        o << ind << "}\n";
+    }
+
+    // One pass over the cells of halo p.h producing the pass's staged
+    // buffers or, for the last pass, the external outputs.
+    void emit_cells(const Pass& p) {
+        const int h = p.h;
+        const bool outputs = p.kind == OUT;
+        std::vector<bool> tapped(d.n_buf, false);
+        for (int k = 0; k < d.n_stage; ++k)
+            if (p.need_op[k] && is_local(d.st[k].op) && !separable(k))
+                tapped[d.st[k].in[0]] = true;
+        o << "  // pass: ";
+        if (outputs)
+            o << "external outputs";
+        else
+            for (int b : p.targets) o << "B" << b << " ";
+        o << "(halo " << h << ")\n";
+        open_cells(th + 2 * h, tw + 2 * h, h, h, false);
+        o << "      if (CHECK && (x < 0 || x >= p.W || y < 0 || y >= p.H)) continue;\n";
+        for (int b = 0; b < d.n_buf; ++b)
+            if (tapped[b] || p.read_cell[b]) {
+                const int dh = d.buf[b].halo - h;
+                o << "      const int q" << b << " = (r + " << dh << ") * " << bw(b) << " + c + "
+                  << dh << ";\n";
+                if (p.read_cell[b])
+                    o << "      const int v" << b << " = B" << b << "[q" << b << "];\n";
+            }
+        for (int k = 0; k < d.n_stage; ++k)
+            if (p.need_op[k] && separable(k)) {
+                const int dh = d.buf[d.st[k].out].halo - h;
+                o << "      const int qR" << k << " = (r + " << dh + d.st[k].ry << ") * "
+                  << slot[row_slot(k)].w << " + c + " << dh << ";\n";
+            }
+        for (int b = 0; b < d.n_buf; ++b)
+            if (p.need_ld[b]) {
+                const int e = ext_in[b];
+                o << "      const int v" << b << " = hvx_ld<" << d.in[e].fmt << ">(p.in[" << e
+                  << "], p.in_pitch[" << e << "], x, y);\n";
+            }
+        for (int k = 0; k < d.n_stage; ++k) {
+            if (!p.need_op[k]) continue;
+            const GenStage& st = d.st[k];
+            const std::string v = val(st.out);
+            o << "      int " << v << ";\n";
+            if (separable(k))
+                emit_sep(k, v, "      ");
+            else if (is_local(st.op))
+                emit_local(st, v, "      ");
+            else
+                o << "      " << v << " = " << point_expr(st) << ";\n";
+            o << "      if (CHECK && !hvx_in(p.valid[" << st.out << "], x, y)) " << v << " = 0;\n";
+        }
+        if (outputs) {
+            for (int e = 0; e < d.n_out; ++e)
+                o << "      hvx_st<" << d.out[e].fmt << ">(p.out[" << e << "], p.out_pitch[" << e
+                  << "], x, y, " << val(d.out[e].buf) << ");\n";
+            close_cells();
+            return;
+        }
+        for (int b : p.targets) o << "      B" << b << "[r * " << bw(b) << " + c] = " << val(b) << ";\n";
+        close_cells();
+        // cells outside the image, the way the local consumers read them
+        o << "  if (CHECK) {\n    __syncthreads();\n";
+        for (int b : p.targets) {
+            o << "    {\n";
+            open_cells(bh(b), bw(b), h, h, false);
+            o << "      if (x >= 0 && x < p.W && y >= 0 && y < p.H) continue;\n"
+              << "      B" << b << "[r * " << bw(b) << " + c] = "
+              << fill_expr(b, "B" + std::to_string(b) + "[(min(max(y, 0), p.H - 1) - y0 + " +
+                                  std::to_string(h) + ") * " + std::to_string(bw(b)) +
+                                  " + min(max(x, 0), p.W - 1) - x0 + " + std::to_string(h) + "]")
+              << ";\n";
+            close_cells();
+            o << "    }\n";
+        }
+        o << "  }\n  __syncthreads();\n";
+    }
+
+    bool emit() {
+        analyse();
+        if (!plan() || !choose_tile()) return false;
+        o << "// generated kernel: " << d.n_stage << " ops, " << d.n_buf << " images, tile " << tw
+          << " x " << th << ", " << passes.size() << " passes, " << smem_words * 4
+          << " bytes of shared memory\n"
+          << "#include \"point_math.cuh\"\n#include \"jit_params.h\"\n\n"
+          << "__device__ __forceinline__ bool hvx_in(const int* r, int x, int y) {\n"
+          << "  return x >= r[0] && x < r[2] && y >= r[1] && y < r[3];\n}\n"
+          << "template <int F>\n"
+          << "__device__ __forceinline__ int hvx_ld(const void* base, unsigned long long pitch, "
+             "int x, int y) {\n"
+          << "  const unsigned char* row = (const unsigned char*)base + (unsigned long long)y * "
+             "pitch;\n"
+          << "  if (F == " << HVX_DF_U8 << ") return __ldg(row + x);\n"
+          << "  if (F == " << HVX_DF_S16 << ") return __ldg((const short*)row + x);\n"
+          << "  if (F == " << HVX_DF_UYVY << ") return __ldg((const unsigned short*)row + x);\n"
+          << "  return __ldg((const int*)row + x);\n}\n"
+          << "template <int F>\n"
+          << "__device__ __forceinline__ void hvx_st(void* base, unsigned long long pitch, int x, "
+             "int y, int v) {\n"
+          << "  unsigned char* row = (unsigned char*)base + (unsigned long long)y * pitch;\n"
+          << "  if (F == " << HVX_DF_U8 << ") row[x] = (unsigned char)v;\n"
+          << "  else if (F == " << HVX_DF_S16 << ") ((short*)row)[x] = (short)v;\n"
+          << "  else ((int*)row)[x] = v;\n}\n\n"
+          << "template <bool CHECK>\n"
+          << "__device__ __forceinline__ void hvx_tile(const HvxJitParams& p, int* smem, int x0, "
+             "int y0) {\n"
+          << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
+        for (int s = 0; s < (int)slot.size(); ++s)
+            if (slot[s].w > 0)
+                o << "  int* const " << slot_name(s) << " = smem + " << slot[s].off << ";  // "
+                  << slot[s].w << " x " << slot[s].h << ", passes " << slot[s].def << ".."
+                  << slot[s].last << "\n";
+        for (const Pass& p : passes) {
+            switch (p.kind) {
+                case LOAD:
+                    for (int b : p.targets) emit_load(b);
+                    o << "  __syncthreads();\n";
+                    break;
+                case ROW:
+                    for (int k : p.targets) emit_row(k);
+                    o << "  __syncthreads();\n";
+                    break;
+                case CELLS:
+                case OUT: emit_cells(p); break;
+            }
+        }
+        o << "}\n\n"
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+          << ") hvx_generated(const HvxJitParams p) {\n"
+          << "  extern __shared__ __align__(16) int smem[];\n"
+          << "  const int tx = blockIdx.x, ty = blockIdx.y;\n"
+          << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
+          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "  else\n"
+          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "}\n";
+        return true;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Compilation and the kernel cache
+
+std::mutex g_mu;
+
+std::unordered_map<std::string, std::unique_ptr<JitKernel>>& cache() {
+    static auto* c = new std::unordered_map<std::string, std::unique_ptr<JitKernel>>();
+    return *c;
+}
+
+bool compile(JitKernel& k) {
+    Nvrtc& n = nvrtc();
+    if (!n.ok) {
+        k.log = n.why;
+        return false;
+    }
+    const char* names[] = {"point_math.cuh", "phase_table.h", "jit_params.h"};
+    const char* texts[] = {kJitPointMath, kJitPhaseTable, kJitParams};
+    void* prog = nullptr;
+    if (n.create(&prog, k.source.c_str(), "hvx_generated.cu", 3, texts, names) != 0) {
+        k.log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    // no fast-math flags: the exact arithmetic relies on IEEE division and sqrt
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--device-int128",
+                          "-default-device"};
+    const int r = n.compile(prog, 4, opts);
+    size_t ls = 0;
+    if (n.log_size(prog, &ls) == 0 && ls > 1) {
+        k.log.assign(ls, '\0');
+        n.log(prog, &k.log[0]);
+        k.log.resize(ls - 1);
+    }
+    if (r == 0) {
+        size_t cs = 0;
+        if (n.cubin_size(prog, &cs) == 0 && cs > 0) {
+            k.cubin.assign(cs, 0);
+            k.compiled = n.cubin(prog, k.cubin.data()) == 0;
+        }
+    }
+    n.destroy(&prog);
+    return k.compiled;
+}
+
+bool load(JitKernel& k, int device, std::string* why) {
+    Driver& dr = driver();
+    if (!dr.ok) {
+        *why = "driver entry points unavailable";
+        return false;
+    }
+    if (dr.load(&k.mod, k.cubin.data()) != CUDA_SUCCESS ||
+        dr.get(&k.fn, k.mod, "hvx_generated") != CUDA_SUCCESS) {
+        *why = "cuModuleLoadData / cuModuleGetFunction failed";
+        return false;
+    }
+    if (k.smem_bytes > 48 * 1024 &&
+        dr.attr(k.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k.smem_bytes) !=
+            CUDA_SUCCESS) {
+        *why = "cuFuncSetAttribute failed";
+        return false;
+    }
+    k.device = device;
+    return true;
+}
+
+int ceil_div(int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); }
+int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+}  // namespace
+
+bool jit_available() { return nvrtc().ok; }
+
+bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* out,
+                 std::string* why) {
+    Emitter em(d);
+    if (!em.emit()) {
+        *why = "group shape not handled by the code generator";
+        return false;
+    }
+    const std::string src = em.o.str();
+    JitKernel* k = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        std::unique_ptr<JitKernel>& slot =
+            cache()[(load_module ? std::to_string(device) : std::string("-")) + "\n" + src];
+        if (!slot) {
+            slot.reset(new JitKernel);
+            slot->source = src;
+            slot->tw = em.tw;
+            slot->th = em.th;
+            slot->smem_bytes = em.smem_words * 4;
+            compile(*slot);
+        }
+        if (!slot->compiled) {
+            *why = "NVRTC: " + slot->log;
+            return false;
+        }
+        if (load_module && slot->device != device && !load(*slot, device, why)) return false;
+        k = slot.get();
+    }
+    JitLaunch& j = *out;
+    j.k = k;
+    std::memset(&j.p, 0, sizeof(j.p));
+    HvxJitParams& p = j.p;
+    p.W = d.W;
+    p.H = d.H;
+    for (int b = 0; b < d.n_buf; ++b)
+        for (int i = 0; i < 4; ++i) p.valid[b][i] = d.buf[b].valid[i];
+    for (int e = 0; e < d.n_in; ++e) {
+        p.in[e] = d.in[e].ptr;
+        p.in_pitch[e] = d.in[e].pitch;
+    }
+    for (int e = 0; e < d.n_out; ++e) {
+        p.out[e] = d.out[e].ptr;
+        p.out_pitch[e] = d.out[e].pitch;
+    }
+    // interior tiles: every image's cells of the tile grown by its halo lie in
+    // its valid region (external inputs: in the image; they are read as stored)
+    const int tw = k->tw, th = k->th;
+    j.gx = (unsigned)((d.W + tw - 1) / tw);
+    j.gy = (unsigned)((d.H + th - 1) / th);
+    int ix0 = 0, iy0 = 0, ix1 = (int)j.gx - 1, iy1 = (int)j.gy - 1;
+    std::vector<bool> is_in(d.n_buf, false);
+    for (int e = 0; e < d.n_in; ++e) is_in[d.in[e].buf] = true;
+    for (int b = 0; b < d.n_buf; ++b) {
+        const int h = d.buf[b].halo;
+        int r[4] = {0, 0, (int)d.W, (int)d.H};
+        if (!is_in[b])
+            for (int i = 0; i < 4; ++i) r[i] = d.buf[b].valid[i];
+        ix0 = std::max(ix0, ceil_div(r[0] + h, tw));
+        iy0 = std::max(iy0, ceil_div(r[1] + h, th));
+        ix1 = std::min(ix1, floor_div(r[2] - h - tw, tw));
+        iy1 = std::min(iy1, floor_div(r[3] - h - th, th));
+    }
+    p.ix0 = ix0;
+    p.ix1 = ix1;
+    p.iy0 = iy0;
+    p.iy1 = iy1;
+    return true;
+}
+
+cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s) {
+    void* args[] = {const_cast<HvxJitParams*>(&j.p)};
+    const CUresult r = driver().launch(j.k->fn, j.gx, j.gy, 1, kThreads, 1, 1,
+                                       (unsigned)j.k->smem_bytes, (CUstream)s, args, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+const std::string& jit_source(const JitLaunch& j) { return j.k->source; }
+
+}  // namespace hvx

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/hvx.h"
+#include "jit_params.h"
 #include "kernel_params.h"
 
 namespace hvx {
@@ -151,6 +152,14 @@ struct Op {
     int group = -1;
 };
 
+// A kernel generated for a staged-tile group (codegen.cpp) and its launch.
+struct JitKernel;
+struct JitLaunch {
+    JitKernel* k = nullptr;  // cached for the life of the process
+    HvxJitParams p;
+    unsigned gx = 0, gy = 0;
+};
+
 // A fused group: ops run by one kernel launch.
 enum GroupKernel : int {
     GK_GENERIC = 0,  // staged tile interpreter (any point/local ops)
@@ -175,6 +184,8 @@ struct Group {
     EdgeParams edge;             // for GK_EDGE / GK_GAUSS
     HarrisParams harris;         // for GK_HARRIS
     PlainParams plain;           // for GK_POINT / GK_CHX_UV
+    JitLaunch jit;               // GK_GENERIC with a generated kernel
+    bool jit_on = false;
     uint64_t ext_bytes = 0;      // bytes of non-virtual images read + written
     uint64_t mem_bytes = 0;      // bytes of every image read + written
     bool closed = false;         // planning: no further op may join
@@ -198,6 +209,7 @@ struct Graph {
     std::vector<Image*> virtuals;
     bool verified = false;
     bool fusion = true;
+    int codegen = HVX_CODEGEN_AUTO;
     hvx_status last = HVX_SUCCESS;
     Plan plan;
     cudaEvent_t done = nullptr;
@@ -233,6 +245,14 @@ hvx_status check_device_error(Context* ctx);
 hvx_status ensure_context_device_state(Context* ctx);
 void destroy_batch_cache(Context* ctx);
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s);
+
+// code generation for staged-tile groups (codegen.cpp): generate, compile
+// (cached by source) and, with load_module, load the group's kernel
+bool jit_available();
+bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* out,
+                 std::string* why);
+cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s);
+const std::string& jit_source(const JitLaunch& j);
 
 // server (server.cpp)
 void server_destroy(Server* s);

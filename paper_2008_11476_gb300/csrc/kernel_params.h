@@ -55,6 +55,7 @@ struct GenBuf {
     int32_t is_float;  // cells hold binary32 (else int32)
     int32_t smem_off;  // offset in 4-byte words
     int32_t valid[4];  // valid rectangle of the image held (x0, y0, x1, y1)
+    int32_t fmt;       // HVX_DF_* of the image held
 };
 
 struct GenStage {

@@ -411,6 +411,7 @@ hvx_status build_generic(Plan& P, Group& G) {
         gb.halo = halo[im];
         if (gb.halo > GEN_MAX_HALO) return HVX_ERROR_NOT_SUPPORTED;
         gb.is_float = im->fmt == HVX_DF_F32;
+        gb.fmt = im->fmt;
         gb.fill = FILL_NONE;
         gb.cval = 0;
         for (int j : G.ops) {
@@ -536,6 +537,17 @@ hvx_status prepare_launches(Graph* g) {
         } else {
             G.kernel = GK_GENERIC;
             st = build_generic(P, G);
+            G.jit_on = false;
+            // plan-only contexts compile generated kernels only when asked to
+            const bool gen = g->codegen == HVX_CODEGEN_REQUIRE ||
+                             (g->codegen == HVX_CODEGEN_AUTO && !ctx->plan_only);
+            if (st == HVX_SUCCESS && gen) {
+                std::string why;
+                G.jit_on = jit_prepare(G.gdesc, !ctx->plan_only, ctx->device, &G.jit, &why);
+                if (!G.jit_on && getenv("HVX_CODEGEN_VERBOSE"))
+                    fprintf(stderr, "hvx: no generated kernel for a group: %s\n", why.c_str());
+                if (!G.jit_on && g->codegen == HVX_CODEGEN_REQUIRE) return HVX_ERROR_NOT_SUPPORTED;
+            }
         }
         if (st != HVX_SUCCESS) return st;
     }
@@ -552,7 +564,7 @@ hvx_status launch_plan(Graph* g, cudaStream_t s) {
             case GK_HARRIS: e = launch_harris(G.tmap, G.harris, s); break;
             case GK_POINT:
             case GK_CHX_UV: e = launch_plain(G.plain, s); break;
-            default: e = launch_generic(G.gdesc, s); break;
+            default: e = G.jit_on ? jit_launch(G.jit, s) : launch_generic(G.gdesc, s); break;
         }
         if (e != cudaSuccess) return cuda_status(e);
     }

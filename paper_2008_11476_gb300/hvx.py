@@ -45,6 +45,8 @@ HVX_GRAPH_INTERMEDIATE_BYTES = 5
 HVX_GRAPH_EXTERNAL_BYTES = 6
 HVX_GRAPH_FUSION = 7
 HVX_GRAPH_KERNEL_KINDS = 8
+HVX_GRAPH_GENERATED_KERNELS = 9
+HVX_CODEGEN_OFF, HVX_CODEGEN_AUTO, HVX_CODEGEN_REQUIRE = 0, 1, 2
 HVX_NODE_LIVE_OUTPUTS = 1
 HVX_NODE_GROUP = 2
 
@@ -114,6 +116,8 @@ _SIGS = {
     "hvxScheduleGraph": (I32, [P, P]),
     "hvxWaitGraph": (I32, [P]),
     "hvxSetGraphFusion": (I32, [P, I32]),
+    "hvxSetGraphCodegen": (I32, [P, I32]),
+    "hvxGetGraphKernelSource": (ctypes.c_int64, [P, I32, ctypes.c_char_p, U64]),
     "hvxGetGraphStatus": (I32, [P]),
     "hvxQueryGraph": (I32, [P, I32, P, U64]),
     "hvxProcessGraphBatch": (I32, [PP, I32, P]),
@@ -308,6 +312,20 @@ def hvxWaitGraph(g):
 
 def hvxSetGraphFusion(g, enable: bool):
     _ck(lib().hvxSetGraphFusion(g, 1 if enable else 0), "hvxSetGraphFusion")
+
+
+def hvxSetGraphCodegen(g, mode: int):
+    _ck(lib().hvxSetGraphCodegen(g, mode), "hvxSetGraphCodegen")
+
+
+def hvxGetGraphKernelSource(g, group: int):
+    """Source of the kernel generated for launch `group`, or None."""
+    n = lib().hvxGetGraphKernelSource(g, group, None, 0)
+    if n < 0:
+        return None
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().hvxGetGraphKernelSource(g, group, buf, n + 1)
+    return buf.value.decode()
 
 
 def hvxGetGraphStatus(g) -> int:

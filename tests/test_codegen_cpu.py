@@ -1,0 +1,97 @@
+"""Code generation without a GPU: in a plan-only context with
+HVX_CODEGEN_REQUIRE, verification emits each staged-tile group's kernel and
+compiles it with NVRTC for sm_103a (nothing is loaded or run).  Checks that the
+applications of the paper's evaluation all compile, that the generator folds
+the constants it is given, and the mode switches."""
+import numpy as np
+import pytest
+
+from paper_2008_11476_gb300 import apps as A
+from paper_2008_11476_gb300 import graphs as PG
+from paper_2008_11476_gb300 import hvx as H
+
+
+@pytest.fixture
+def pctx():
+    c = H.hvxCreateContextEx(H.HVX_CONTEXT_PLAN_ONLY)
+    yield c
+    H.hvxReleaseContext(c)
+
+
+def _gen(ctx, build, w=1920, h=1080, fusion=True, mode=H.HVX_CODEGEN_REQUIRE):
+    src = H.hvxCreateImage(ctx, w, h, H.HVX_DF_U8)
+    g, _ = build(ctx, src, w, h, fusion)
+    H.hvxSetGraphCodegen(g, mode)
+    H.hvxVerifyGraph(g)
+    return g
+
+
+@pytest.mark.parametrize("name", [a for a, _ in A.APPS])
+def test_applications_compile(pctx, name):
+    g = _gen(pctx, dict(A.APPS)[name])
+    kinds = PG.kernel_kinds(g)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == kinds.count("staged_tile")
+    for i, k in enumerate(kinds):
+        s = H.hvxGetGraphKernelSource(g, i)
+        assert (s is not None) == (k == "staged_tile")
+        if s:
+            assert "hvx_generated" in s and "hvx_tile<false>" in s
+
+
+def test_constants_are_folded(pctx):
+    # Laplacian: the four zero taps of the 3x3 kernel are dropped and the sum
+    # of U8 inputs with coefficients up to 4 is accumulated in 32 bits
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.laplacian), 0)
+    assert s.count("t += ") == 5
+    assert "long long t" not in s
+    # the threshold of the Sobel application is a literal
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel), 0)
+    assert "(100LL)" in s
+
+
+def test_products_share_one_pass(pctx):
+    # Tomasi: the three products are staged by one pass that evaluates the
+    # Sobel derivatives once; the sums, response and threshold are evaluated
+    # inline in the output pass
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.tomasi), 0)
+    assert s.count("// pass:") == 2
+    assert "tomasi_response_f32" in s
+
+
+def test_same_shape_same_source(pctx):
+    a = H.hvxGetGraphKernelSource(_gen(pctx, A.fchain, 640, 480), 0)
+    b = H.hvxGetGraphKernelSource(_gen(pctx, A.fchain, 1920, 1080), 0)
+    assert a == b  # the image size is a launch parameter, not compiled in
+
+
+def test_modes(pctx):
+    g = _gen(pctx, A.unsharp, mode=H.HVX_CODEGEN_OFF)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 0
+    assert H.hvxGetGraphKernelSource(g, 0) is None
+    # a plan-only context does not compile unless required
+    g = _gen(pctx, A.unsharp, mode=H.HVX_CODEGEN_AUTO)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 0
+    with pytest.raises(H.HvxError):
+        H.hvxSetGraphCodegen(g, 7)
+
+
+def test_unfused_nodes_compile(pctx):
+    # one generated kernel per staged-tile node when fusion is off
+    g = _gen(pctx, A.tomasi, fusion=False)
+    kinds = PG.kernel_kinds(g)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == kinds.count("staged_tile") > 0
+
+
+def test_every_border_mode_compiles(pctx):
+    for border in (H.HVX_BORDER_UNDEFINED, H.HVX_BORDER_REPLICATE, H.HVX_BORDER_CONSTANT):
+        src = H.hvxCreateImage(pctx, 333, 77, H.HVX_DF_U8)
+        out = H.hvxCreateImage(pctx, 333, 77, H.HVX_DF_S16)
+        g = H.hvxCreateGraph(pctx)
+        a = H.hvxCreateVirtualImage(g)
+        H.hvxSetNodeBorder(H.hvxMedian3x3Node(g, src, a), border, 7)
+        n = H.hvxConvolveNode(g, a, np.arange(-12, 13), 5, 5, 1, out)
+        H.hvxSetNodeBorder(n, border, 9)
+        H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_REQUIRE)
+        H.hvxVerifyGraph(g)
+        s = H.hvxGetGraphKernelSource(g, 0)
+        assert ("= 9;" in s) == (border == H.HVX_BORDER_CONSTANT)  # the fill constant

@@ -1,7 +1,8 @@
 """GPU parity of the paper's Section 6 applications (paper_2008_11476_gb300/
 apps.py) against the CPU oracle run node by node on the same graph (written
-here again in the oracle's vocabulary), fused and unfused, on a frame-sized and
-a ragged image.  Integer outputs must match exactly; the Tomasi mask may differ
+here again in the oracle's vocabulary), fused and unfused, with the
+staged-tile groups run by the interpreter kernel and by kernels generated for
+the graph, on a frame-sized and a ragged image.  Integer outputs must match exactly; the Tomasi mask may differ
 only where the oracle's binary32 response lies within 1e-5 relative of the
 threshold (the GPU evaluates the eigenvalue in binary32)."""
 import numpy as np
@@ -53,14 +54,12 @@ def oracle_graph(name, w, h):
     if name == "EdgFig2":
         for v in ("G", "gx", "gy", "m"):
             g.virtual(v)
-        g.image("phase", w, h, "U8")
-        g.image("mask", w, h, "U8")
+        g.image("out", w, h, "U8")
         n("gaussian3x3", ["in"], ["G"], **REP)
         n("sobel3x3", ["G"], ["gx", "gy"], **REP)
-        n("magnitude", ["gx", "gy"], ["m"])
-        n("threshold", ["m"], ["mask"], value=100)
-        n("phase", ["gx", "gy"], ["phase"])
-        return g, ["phase", "mask"]
+        n("magnitude", ["gy", "gy"], ["m"])
+        n("threshold", ["m"], ["out"], value=100)
+        return g, ["out"]
     if name == "Sobel":
         for v in ("gx", "gy", "m"):
             g.virtual(v)
@@ -110,9 +109,10 @@ def ctx():
     H.hvxReleaseContext(c)
 
 
+@pytest.mark.parametrize("codegen", [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE])
 @pytest.mark.parametrize("name", [a for a, _ in A.APPS])
 @pytest.mark.parametrize("w,h", [(640, 480), (385, 361)])
-def test_app_matches_oracle(ctx, name, w, h):
+def test_app_matches_oracle(ctx, name, w, h, codegen):
     img = synth.rects_noise(w, h, seed=13)
     og, outs = oracle_graph(name, w, h)
     ref = OG.run(og, {"in": img})
@@ -120,9 +120,13 @@ def test_app_matches_oracle(ctx, name, w, h):
     for fusion in (True, False):
         src = PG.upload(ctx, img, H.HVX_DF_U8)
         g, res = build(ctx, src, w, h, fusion)
+        H.hvxSetGraphCodegen(g, codegen)
+        H.hvxVerifyGraph(g)
         kinds = PG.kernel_kinds(g)
         if fusion:
             assert len(kinds) == 1, kinds
+        gen = H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS)
+        assert gen == (kinds.count("staged_tile") if codegen else 0)
         H.hvxProcessGraph(g)
         for (oname, im, fmt), rname in zip(res, outs):
             got = PG.download(im)

@@ -1,0 +1,239 @@
+"""Kernels generated per graph (hvxSetGraphCodegen) against the CPU oracle and
+against the staged-tile interpreter kernel: seeded random graphs of point and
+local nodes (every border mode, U8 and S16 images, outputs that later nodes
+also read), fused and unfused, on sizes with no interior tile, with ragged
+tiles and with many interior tiles.  Bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import graph as OG
+from paper_2008_11476_gb300 import graphs as PG
+from paper_2008_11476_gb300 import hvx as H
+from paper_2008_11476_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FMT = {"U8": H.HVX_DF_U8, "S16": H.HVX_DF_S16}
+BORDER = {"replicate": H.HVX_BORDER_REPLICATE, "constant": H.HVX_BORDER_CONSTANT,
+          "undefined": H.HVX_BORDER_UNDEFINED}
+
+
+def random_graph(seed):
+    """A random node list: (kind, inputs, outputs, params, output formats)."""
+    rng = np.random.default_rng(seed)
+    fmt = {"in": "U8"}
+    sobel_out = set()
+    nodes = []
+    n = int(rng.integers(2, 8))
+    for i in range(n):
+        u8 = [k for k, f in fmt.items() if f == "U8"]
+        s16 = [k for k, f in fmt.items() if f == "S16"]
+        kinds = ["gaussian3x3", "box3x3", "dilate3x3", "erode3x3", "median3x3", "convolve",
+                 "sobel3x3", "not", "threshold", "and", "add"]
+        if s16:
+            kinds += ["magnitude", "threshold16", "add16"]
+        if len(sobel_out) >= 2:
+            kinds += ["phase"]
+        k = kinds[int(rng.integers(len(kinds)))]
+        pick = lambda pool: pool[int(rng.integers(len(pool)))]  # noqa: E731
+        o = f"t{i}"
+        p = {}
+        if k in ("gaussian3x3", "box3x3", "dilate3x3", "erode3x3", "median3x3", "convolve",
+                 "sobel3x3"):
+            p["border"] = ["replicate", "constant", "undefined"][int(rng.integers(3))]
+            p["cval"] = int(rng.integers(0, 256))
+        if k in ("gaussian3x3", "box3x3"):
+            p["rounding"] = ["zero", "nearest"][int(rng.integers(2))]
+            nodes.append((k, [pick(u8)], [o], p, ["U8"]))
+            fmt[o] = "U8"
+        elif k in ("dilate3x3", "erode3x3", "median3x3"):
+            nodes.append((k, [pick(u8)], [o], p, ["U8"]))
+            fmt[o] = "U8"
+        elif k == "convolve":
+            ks = [3, 5][int(rng.integers(2))]
+            p["coeffs"] = rng.integers(-6, 9, size=(ks, ks)).tolist()
+            p["shift"] = int(rng.integers(0, 5))
+            f = ["U8", "S16"][int(rng.integers(2))]
+            nodes.append((k, [pick(u8)], [o], p, [f]))
+            fmt[o] = f
+        elif k == "sobel3x3":
+            outs = [o + "x", o + "y"]
+            if rng.random() < 0.3:
+                outs[int(rng.integers(2))] = None
+            nodes.append((k, [pick(u8)], outs, p, ["S16", "S16"]))
+            for v in outs:
+                if v:
+                    fmt[v] = "S16"
+                    sobel_out.add(v)
+        elif k == "not":
+            nodes.append((k, [pick(u8)], [o], p, ["U8"]))
+            fmt[o] = "U8"
+        elif k in ("threshold", "threshold16"):
+            src = pick(u8) if k == "threshold" else pick(s16)
+            lo = int(rng.integers(0, 200)) if k == "threshold" else int(rng.integers(-300, 300))
+            if rng.random() < 0.5:
+                p.update(type="binary", value=lo)
+            else:
+                p.update(type="range", lower=lo, upper=lo + int(rng.integers(0, 120)))
+            p.update(true_value=int(rng.integers(0, 256)), false_value=int(rng.integers(0, 256)))
+            nodes.append(("threshold", [src], [o], p, ["U8"]))
+            fmt[o] = "U8"
+        elif k == "and":
+            kk = ["and", "or", "xor"][int(rng.integers(3))]
+            nodes.append((kk, [pick(u8), pick(u8)], [o], p, ["U8"]))
+            fmt[o] = "U8"
+        elif k in ("add", "add16"):
+            kk = ["add", "subtract", "absdiff"][int(rng.integers(3))]
+            a = pick(u8) if k == "add" else pick(s16)
+            b = pick(u8) if rng.random() < 0.5 or not s16 else pick(s16)
+            f = "S16" if "S16" in (fmt[a], fmt[b]) or rng.random() < 0.5 else "U8"
+            if kk != "absdiff":
+                p["policy"] = ["saturate", "wrap"][int(rng.integers(2))]
+            nodes.append((kk, [a, b], [o], p, [f]))
+            fmt[o] = f
+        elif k == "magnitude":
+            nodes.append((k, [pick(s16), pick(s16)], [o], p, ["S16"]))
+            fmt[o] = "S16"
+        elif k == "phase":
+            so = sorted(sobel_out)
+            nodes.append((k, [pick(so), pick(so)], [o], p, ["U8"]))
+            fmt[o] = "U8"
+    read = {i for _, ins, _, _, _ in nodes for i in ins}
+    made = [v for _, _, outs, _, _ in nodes for v in outs if v]
+    external = {v for v in made if v not in read or rng.random() < 0.3}
+    return nodes, fmt, external
+
+
+def build_oracle(nodes, fmt, external, w, h):
+    g = OG.GraphDesc()
+    g.image("in", w, h, "U8")
+    for v, f in fmt.items():
+        if v == "in":
+            continue
+        if v in external:
+            g.image(v, w, h, f)
+        else:
+            g.virtual(v, fmt=f)
+    for k, ins, outs, p, _ in nodes:
+        g.node(k, ins, outs, **p)
+    return g
+
+
+def build_hvx(ctx, src, nodes, fmt, external, w, h):
+    g = H.hvxCreateGraph(ctx)
+    im = {"in": src}
+    for v, f in fmt.items():
+        if v == "in":
+            continue
+        im[v] = (PG.empty(ctx, w, h, FMT[f]) if v in external
+                 else H.hvxCreateVirtualImage(g, 0, 0, FMT[f]))
+    pol = {"saturate": H.HVX_POLICY_SATURATE, "wrap": H.HVX_POLICY_WRAP}
+    for k, ins, outs, p, _ in nodes:
+        a = [im[i] for i in ins]
+        o = im[outs[0]] if outs[0] else None
+        if k == "gaussian3x3":
+            n = H.hvxGaussian3x3Node(g, a[0], o)
+        elif k == "box3x3":
+            n = H.hvxBox3x3Node(g, a[0], o)
+        elif k == "dilate3x3":
+            n = H.hvxDilate3x3Node(g, a[0], o)
+        elif k == "erode3x3":
+            n = H.hvxErode3x3Node(g, a[0], o)
+        elif k == "median3x3":
+            n = H.hvxMedian3x3Node(g, a[0], o)
+        elif k == "convolve":
+            c = np.asarray(p["coeffs"])
+            n = H.hvxConvolveNode(g, a[0], c.ravel(), c.shape[1], c.shape[0], p["shift"], o)
+        elif k == "sobel3x3":
+            n = H.hvxSobel3x3Node(g, a[0], o, im[outs[1]] if outs[1] else None)
+        elif k == "not":
+            n = H.hvxNotNode(g, a[0], o)
+        elif k in ("and", "or", "xor"):
+            n = {"and": H.hvxAndNode, "or": H.hvxOrNode, "xor": H.hvxXorNode}[k](g, a[0], a[1], o)
+        elif k == "threshold":
+            if p["type"] == "binary":
+                n = H.hvxThresholdNode(g, a[0], H.HVX_THRESHOLD_BINARY, p["value"], 0,
+                                       p["true_value"], p["false_value"], o)
+            else:
+                n = H.hvxThresholdNode(g, a[0], H.HVX_THRESHOLD_RANGE, p["lower"], p["upper"],
+                                       p["true_value"], p["false_value"], o)
+        elif k == "add":
+            n = H.hvxAddNode(g, a[0], a[1], pol[p["policy"]], o)
+        elif k == "subtract":
+            n = H.hvxSubtractNode(g, a[0], a[1], pol[p["policy"]], o)
+        elif k == "absdiff":
+            n = H.hvxAbsDiffNode(g, a[0], a[1], o)
+        elif k == "magnitude":
+            n = H.hvxMagnitudeNode(g, a[0], a[1], o)
+        elif k == "phase":
+            n = H.hvxPhaseNode(g, a[0], a[1], o)
+        if "border" in p:
+            H.hvxSetNodeBorder(n, BORDER[p["border"]], p["cval"])
+        if p.get("rounding") == "nearest":
+            H.hvxSetNodeRounding(n, H.HVX_ROUND_TO_NEAREST)
+    return g, im
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hvxCreateContext()
+    yield c
+    H.hvxReleaseContext(c)
+
+
+@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("w,h", [(7, 5), (300, 250)])
+def test_random_graph_generated_matches_oracle(ctx, seed, w, h):
+    nodes, fmt, external = random_graph(seed)
+    img = synth.rects_noise(w, h, seed=seed + 100)
+    ref = OG.run(build_oracle(nodes, fmt, external, w, h), {"in": img})
+    src = PG.upload(ctx, img, H.HVX_DF_U8)
+    for fusion in (True, False):
+        for codegen in (H.HVX_CODEGEN_REQUIRE, H.HVX_CODEGEN_OFF):
+            g, im = build_hvx(ctx, src, nodes, fmt, external, w, h)
+            H.hvxSetGraphFusion(g, fusion)
+            H.hvxSetGraphCodegen(g, codegen)
+            H.hvxVerifyGraph(g)
+            kinds = PG.kernel_kinds(g)
+            gen = H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS)
+            assert gen == (kinds.count("staged_tile") if codegen else 0), kinds
+            H.hvxProcessGraph(g)
+            for v in external:
+                if v not in ref:  # written by a node that dead-code elimination removed
+                    continue
+                np.testing.assert_array_equal(PG.download(im[v]), ref[v].data,
+                                              err_msg=f"{v} fusion={fusion} codegen={codegen}")
+                assert H.hvxGetValidRegion(im[v]) == ref[v].rect
+            H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("w,h", [(1920, 1080), (1000, 999)])
+def test_generated_interior_tiles_large(ctx, w, h):
+    # frame-sized images: most tiles take the unchecked path
+    for seed in (3, 11, 29):
+        nodes, fmt, external = random_graph(seed)
+        img = synth.rects_noise(w, h, seed=seed)
+        ref = OG.run(build_oracle(nodes, fmt, external, w, h), {"in": img})
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        g, im = build_hvx(ctx, src, nodes, fmt, external, w, h)
+        H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_REQUIRE)
+        H.hvxVerifyGraph(g)
+        H.hvxProcessGraph(g)
+        for v in external:
+            if v in ref:
+                np.testing.assert_array_equal(PG.download(im[v]), ref[v].data)
+        H.hvxReleaseGraph(g)
+
+
+def test_generated_source_query(ctx):
+    src = PG.upload(ctx, synth.rects_noise(64, 48, seed=1), H.HVX_DF_U8)
+    out = PG.empty(ctx, 64, 48, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(ctx)
+    H.hvxMedian3x3Node(g, src, out)
+    H.hvxVerifyGraph(g)
+    s = H.hvxGetGraphKernelSource(g, 0)
+    assert s is not None and "hvx_generated" in s
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_OFF)
+    H.hvxVerifyGraph(g)
+    assert H.hvxGetGraphKernelSource(g, 0) is None
+    H.hvxReleaseGraph(g)

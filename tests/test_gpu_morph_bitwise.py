@@ -1,7 +1,8 @@
 """GPU parity of the Table 2 nodes added beyond the edge and Harris graphs:
 Dilate3x3, Erode3x3, Median3x3 (local) and And, Or, Xor, Not (point), alone
 (one launch per node) and fused into one staged-tile group, against the CPU
-oracle, bit-exact, under every border mode and on sizes with ragged tiles."""
+oracle, bit-exact, under every border mode and on sizes with ragged tiles,
+with the interpreter kernel and with kernels generated for the graph."""
 import numpy as np
 import pytest
 
@@ -29,9 +30,13 @@ def ctx():
     H.hvxReleaseContext(c)
 
 
+CODEGEN = [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE]
+
+
+@pytest.mark.parametrize("codegen", CODEGEN)
 @pytest.mark.parametrize("w,h", [(1, 1), (3, 2), (65, 17), (131, 37), (300, 250)])
 @pytest.mark.parametrize("border", BORDERS)
-def test_morph_nodes_alone(ctx, w, h, border):
+def test_morph_nodes_alone(ctx, w, h, border, codegen):
     # the three nodes read the same input: fused they form one staged-tile
     # group with three outputs, unfused three launches
     img = synth.rects_noise(w, h, seed=8 + w)
@@ -45,6 +50,7 @@ def test_morph_nodes_alone(ctx, w, h, border):
             H.hvxSetNodeBorder(n, border, 31)
             outs.append((o, op))
         H.hvxSetGraphFusion(g, fusion)
+        H.hvxSetGraphCodegen(g, codegen)
         H.hvxVerifyGraph(g)
         assert PG.kernel_kinds(g) == kinds
         H.hvxProcessGraph(g)
@@ -97,9 +103,10 @@ def _closing_tophat_oracle(img, border, cval):
     return OG.run(og, {"in": img})["out"]
 
 
+@pytest.mark.parametrize("codegen", CODEGEN)
 @pytest.mark.parametrize("w,h", [(97, 45), (300, 250)])
 @pytest.mark.parametrize("border", BORDERS)
-def test_morph_graph_fused_matches_oracle(ctx, w, h, border):
+def test_morph_graph_fused_matches_oracle(ctx, w, h, border, codegen):
     img = synth.rects_noise(w, h, seed=44)
     ref = _closing_tophat_oracle(img, border, 9)
     for fusion in (True, False):
@@ -114,6 +121,7 @@ def test_morph_graph_fused_matches_oracle(ctx, w, h, border):
         H.hvxThresholdNode(g, diff, H.HVX_THRESHOLD_BINARY, 20, 0, 255, 0, mask)
         H.hvxAndNode(g, med, mask, out)
         H.hvxSetGraphFusion(g, fusion)
+        H.hvxSetGraphCodegen(g, codegen)
         H.hvxVerifyGraph(g)
         kinds = PG.kernel_kinds(g)
         if fusion:
