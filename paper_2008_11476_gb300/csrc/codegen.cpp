@@ -150,6 +150,7 @@ struct JitKernel {
     int device = -1;           // loaded on this device (-1: not loaded)
     CUmodule mod = nullptr;
     CUfunction fn = nullptr;
+    CUfunction fn_batch = nullptr;  // several images per launch
     int smem_bytes = 0;
     int tw = 0, th = 0;
 };
@@ -860,6 +861,27 @@ struct Emitter {
           << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "  else\n"
           << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "}\n\n"
+          << "// n images in one launch: block t is tile t - tile_start[i] of the last\n"
+          << "// image i with tile_start[i] <= t\n"
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+          << ") hvx_generated_batch(const HvxJitParams* __restrict__ ps, const int* __restrict__ "
+             "tile_start, int n) {\n"
+          << "  extern __shared__ __align__(16) int smem[];\n"
+          << "  const int t = blockIdx.x;\n"
+          << "  int lo = 0, hi = n - 1;\n"
+          << "  while (lo < hi) {\n"
+          << "    const int mid = (lo + hi + 1) >> 1;\n"
+          << "    if (__ldg(tile_start + mid) <= t) lo = mid; else hi = mid - 1;\n"
+          << "  }\n"
+          << "  const HvxJitParams& p = ps[lo];\n"
+          << "  const int local = t - __ldg(tile_start + lo), gx = (p.W + " << tw - 1 << ") / "
+          << tw << ";\n"
+          << "  const int ty = local / gx, tx = local - ty * gx;\n"
+          << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
+          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "  else\n"
+          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "}\n";
         return true;
     }
@@ -916,13 +938,16 @@ bool load(JitKernel& k, int device, std::string* why) {
         return false;
     }
     if (dr.load(&k.mod, k.cubin.data()) != CUDA_SUCCESS ||
-        dr.get(&k.fn, k.mod, "hvx_generated") != CUDA_SUCCESS) {
+        dr.get(&k.fn, k.mod, "hvx_generated") != CUDA_SUCCESS ||
+        dr.get(&k.fn_batch, k.mod, "hvx_generated_batch") != CUDA_SUCCESS) {
         *why = "cuModuleLoadData / cuModuleGetFunction failed";
         return false;
     }
     if (k.smem_bytes > 48 * 1024 &&
-        dr.attr(k.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k.smem_bytes) !=
-            CUDA_SUCCESS) {
+        (dr.attr(k.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k.smem_bytes) !=
+             CUDA_SUCCESS ||
+         dr.attr(k.fn_batch, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k.smem_bytes) !=
+             CUDA_SUCCESS)) {
         *why = "cuFuncSetAttribute failed";
         return false;
     }
@@ -1011,6 +1036,19 @@ cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s) {
     const CUresult r = driver().launch(j.k->fn, j.gx, j.gy, 1, kThreads, 1, 1,
                                        (unsigned)j.k->smem_bytes, (CUstream)s, args, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_launch_batch(const JitKernel* k, const HvxJitParams* params, const int* tile_start,
+                             int n, int total_tiles, cudaStream_t s) {
+    void* args[] = {&params, &tile_start, &n};
+    const CUresult r = driver().launch(k->fn_batch, (unsigned)total_tiles, 1, 1, kThreads, 1, 1,
+                                       (unsigned)k->smem_bytes, (CUstream)s, args, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+void jit_tile(const JitKernel* k, int* tw, int* th) {
+    *tw = k->tw;
+    *th = k->th;
 }
 
 const std::string& jit_source(const JitLaunch& j) { return j.k->source; }

@@ -252,6 +252,11 @@ bool jit_available();
 bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* out,
                  std::string* why);
 cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s);
+// n images' groups that run the same generated kernel, in one launch: params
+// and tile_start (n + 1 prefix sums of tiles per image) in device memory
+cudaError_t jit_launch_batch(const JitKernel* k, const HvxJitParams* params, const int* tile_start,
+                             int n, int total_tiles, cudaStream_t s);
+void jit_tile(const JitKernel* k, int* tw, int* th);
 const std::string& jit_source(const JitLaunch& j);
 
 // server (server.cpp)

@@ -581,6 +581,9 @@ struct BatchEntry {
     cudaGraphExec_t exec = nullptr;
     uint64_t last_use = 0;
     int grid = 0;  // persistent CTAs chosen by the autotuner
+    // generated-kernel batches: one direct launch over every image's tiles
+    JitKernel* jk = nullptr;
+    int n = 0, total_tiles = 0;
 };
 
 struct BatchCache {
@@ -725,10 +728,59 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
 
 }  // namespace
 
+// Batch of graphs whose plans are one group running the same generated
+// kernel: the images' launch parameters and tile prefix sums in one device
+// block.
+hvx_status build_jit_batch_entry(Graph* const* gs, int n, JitKernel* jk, BatchEntry& out) {
+    int tw = 0, th = 0;
+    jit_tile(jk, &tw, &th);
+    const size_t tiles_off = (size_t)n * sizeof(HvxJitParams);
+    const size_t total = tiles_off + (size_t)(n + 1) * sizeof(int);
+    std::vector<uint8_t> host(total);
+    std::vector<int> tile_start(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const Group& G = gs[i]->plan.groups[0];
+        std::memcpy(host.data() + (size_t)i * sizeof(HvxJitParams), &G.jit.p, sizeof(HvxJitParams));
+        const long long t = (long long)tile_start[i] + (long long)G.jit.gx * G.jit.gy;
+        if (t > (1ll << 30)) return HVX_ERROR_NOT_SUPPORTED;
+        tile_start[i + 1] = (int)t;
+    }
+    std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));
+    void* dmem = nullptr;
+    cudaError_t e = cudaMalloc(&dmem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HVX_ERROR_NO_MEMORY;
+    }
+    e = cudaMemcpy(dmem, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dmem);
+        return cuda_status(e);
+    }
+    out.graphs.assign(gs, gs + n);
+    out.plan_ids.resize(n);
+    for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
+    out.dmem = dmem;
+    out.jk = jk;
+    out.n = n;
+    out.total_tiles = tile_start[n];
+    return HVX_SUCCESS;
+}
+
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
+    // one launch when every plan is a single group running the same
+    // generated kernel
+    JitKernel* jk = nullptr;
+    bool jit_same = true;
+    for (int i = 0; i < n && jit_same; ++i) {
+        const Plan& P = gs[i]->plan;
+        jit_same = P.groups.size() == 1 && P.groups[0].kernel == GK_GENERIC &&
+                   P.groups[0].jit_on && (!jk || P.groups[0].jit.k == jk);
+        if (jit_same) jk = P.groups[0].jit.k;
+    }
     // one persistent launch when every plan is a single edge (or Gaussian)
     // group and all of them use the same kernel mode
-    bool same = true;
+    bool same = !jit_same;
     int mode = -1;
     for (int i = 0; i < n && same; ++i) {
         const Plan& P = gs[i]->plan;
@@ -740,7 +792,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             mode = m;
         }
     }
-    if (!same) {
+    if (!same && !jit_same) {
         for (int i = 0; i < n; ++i) {
             hvx_status st = launch_plan(gs[i], s);
             if (st != HVX_SUCCESS) return st;
@@ -771,12 +823,20 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             bc->entries.erase(oldest);
         }
         BatchEntry fresh;
-        hvx_status st = build_batch_entry(ctx, bc, gs, n, mode, s, fresh);
+        hvx_status st = jit_same ? build_jit_batch_entry(gs, n, jk, fresh)
+                                 : build_batch_entry(ctx, bc, gs, n, mode, s, fresh);
         if (st != HVX_SUCCESS) return st;
         bc->entries.push_back(fresh);
         hit = &bc->entries.back();
     }
     hit->last_use = ++bc->tick;
+    if (hit->jk) {
+        const uint8_t* base = static_cast<const uint8_t*>(hit->dmem);
+        return cuda_status(jit_launch_batch(
+            hit->jk, reinterpret_cast<const HvxJitParams*>(base),
+            reinterpret_cast<const int*>(base + (size_t)hit->n * sizeof(HvxJitParams)), hit->n,
+            hit->total_tiles, s));
+    }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
 }
 

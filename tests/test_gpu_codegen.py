@@ -237,3 +237,50 @@ def test_generated_source_query(ctx):
     H.hvxVerifyGraph(g)
     assert H.hvxGetGraphKernelSource(g, 0) is None
     H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("name", ["FChain", "Tomasi", "Unsharp", "EdgFig2"])
+def test_batched_generated_kernel(ctx, name):
+    # graphs of the same shape on images of different sizes share one
+    # generated kernel: hvxProcessGraphBatch runs them in one launch
+    from paper_2008_11476_gb300 import apps as A
+    build = dict(A.APPS)[name]
+    sizes = [(300, 250), (1, 1), (640, 480), (97, 45), (129, 33)]
+    graphs, outs, refs = [], [], []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=70 + i)
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        g, res = build(ctx, src, w, h, True)
+        assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 1
+        graphs.append(g)
+        outs.append(res)
+        g2, res2 = build(ctx, PG.upload(ctx, img, H.HVX_DF_U8), w, h, True)
+        H.hvxSetGraphCodegen(g2, H.HVX_CODEGEN_OFF)
+        H.hvxVerifyGraph(g2)
+        H.hvxProcessGraph(g2)
+        refs.append([PG.download(im) for _, im, _ in res2])
+    for _ in range(2):  # the second call reuses the cached batch
+        H.hvxProcessGraphBatch(graphs)
+        H.hvxWaitBatch(ctx)
+        for res, ref in zip(outs, refs):
+            for (_, im, _), want in zip(res, ref):
+                np.testing.assert_array_equal(PG.download(im), want)
+
+
+def test_batch_of_different_generated_kernels(ctx):
+    # different shapes: the batch call falls back to one launch per graph
+    from paper_2008_11476_gb300 import apps as A
+    graphs, outs, refs = [], [], []
+    for i, (name, build) in enumerate(A.APPS):
+        img = synth.rects_noise(200, 120, seed=90 + i)
+        g, res = build(ctx, PG.upload(ctx, img, H.HVX_DF_U8), 200, 120, True)
+        g2, res2 = build(ctx, PG.upload(ctx, img, H.HVX_DF_U8), 200, 120, True)
+        H.hvxProcessGraph(g2)
+        graphs.append(g)
+        outs.append(res)
+        refs.append([PG.download(im) for _, im, _ in res2])
+    H.hvxProcessGraphBatch(graphs)
+    H.hvxWaitBatch(ctx)
+    for res, ref in zip(outs, refs):
+        for (_, im, _), want in zip(res, ref):
+            np.testing.assert_array_equal(PG.download(im), want)
