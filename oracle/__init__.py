@@ -32,6 +32,8 @@ _lib = None
 BORDER_UNDEFINED = 0
 BORDER_REPLICATE = 1
 BORDER_CONSTANT = 2
+BORDER_MIRROR = 3   # Hipacc MIRROR: ... c b a | a b c ... (reflect with the edge repeated)
+BORDER_REPEAT = 4   # Hipacc REPEAT: periodic continuation
 
 ROUND_ZERO = 0
 ROUND_NEAREST = 1

@@ -290,7 +290,7 @@ def _depth_first_visit(v_start, D_in, G_trans):
 # --- execution -----------------------------------------------------------------
 
 _BORDER = {"undefined": O.BORDER_UNDEFINED, "replicate": O.BORDER_REPLICATE,
-           "constant": O.BORDER_CONSTANT}
+           "constant": O.BORDER_CONSTANT, "mirror": O.BORDER_MIRROR, "repeat": O.BORDER_REPEAT}
 _ROUND = {"zero": O.ROUND_ZERO, "nearest": O.ROUND_NEAREST}
 _ARITH = {"add": O.ARITH_ADD, "subtract": O.ARITH_SUB, "absdiff": O.ARITH_ABSDIFF}
 _MORPH = {"dilate3x3": O.MORPH_DILATE, "erode3x3": O.MORPH_ERODE, "median3x3": O.MORPH_MEDIAN}

@@ -23,7 +23,13 @@
  *   - BORDER_REPLICATE reads the nearest pixel of the image (coordinates
  *     clamped to [0,W-1]x[0,H-1]); BORDER_CONSTANT reads a constant.  Both
  *     apply at the image edge (the paper's Hipacc listing selects clamping
- *     as its boundary condition, Section 3.2).
+ *     as its boundary condition, Section 3.2).  BORDER_MIRROR and
+ *     BORDER_REPEAT are the other boundary conditions the Hipacc DSL of
+ *     Section 3.2 names (MIRROR, REPEAT); the paper does not define them.
+ *     Reading: MIRROR reflects a coordinate about the image edge with the
+ *     edge pixel repeated (... c b a | a b c ...), again and again until it
+ *     lies inside; REPEAT continues the image periodically.  Like
+ *     REPLICATE, neither shrinks the valid rectangle.
  *
  * The OpenVX per-node arithmetic (saturation, rounding) is not printed in the
  * paper; the readings taken here are listed at each function.
@@ -36,6 +42,8 @@
 #define ORC_BORDER_UNDEFINED 0
 #define ORC_BORDER_REPLICATE 1
 #define ORC_BORDER_CONSTANT 2
+#define ORC_BORDER_MIRROR 3
+#define ORC_BORDER_REPEAT 4
 
 #define ORC_ROUND_ZERO 0
 #define ORC_ROUND_NEAREST 1
@@ -77,17 +85,34 @@ static void rect_local(int dst[4], const int src[4], int rx, int ry, int border)
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* The coordinate inside [0, n) that coordinate v reads under MIRROR (reflect
+ * about the edge it crossed, repeating the edge sample, until inside) or
+ * REPEAT (shift by the extent n until inside). */
+static int wrap_coord(int v, int n, int border) {
+    while (v < 0 || v >= n) {
+        if (border == ORC_BORDER_REPEAT)
+            v = v < 0 ? v + n : v - n;
+        else
+            v = v < 0 ? -v - 1 : 2 * n - 1 - v;
+    }
+    return v;
+}
+
 /* Read one input sample of a local operator at (x, y), which may lie outside
  * the image.  Under UNDEFINED the caller never asks for such a sample. */
 static int64_t read_u8(const uint8_t* p, int w, int h, int x, int y, int border, int cval) {
     if (x >= 0 && x < w && y >= 0 && y < h) return p[(size_t)y * w + x];
     if (border == ORC_BORDER_CONSTANT) return (uint8_t)cval;
+    if (border == ORC_BORDER_MIRROR || border == ORC_BORDER_REPEAT)
+        return p[(size_t)wrap_coord(y, h, border) * w + wrap_coord(x, w, border)];
     return p[(size_t)clampi(y, 0, h - 1) * w + clampi(x, 0, w - 1)];
 }
 
 static int64_t read_s32(const int32_t* p, int w, int h, int x, int y, int border, int cval) {
     if (x >= 0 && x < w && y >= 0 && y < h) return p[(size_t)y * w + x];
     if (border == ORC_BORDER_CONSTANT) return cval;
+    if (border == ORC_BORDER_MIRROR || border == ORC_BORDER_REPEAT)
+        return p[(size_t)wrap_coord(y, h, border) * w + wrap_coord(x, w, border)];
     return p[(size_t)clampi(y, 0, h - 1) * w + clampi(x, 0, w - 1)];
 }
 

@@ -546,3 +546,60 @@ def test_tomasi_closed_forms_and_eigvalsh(orc):
                     for x, y, z in zip(A, B, C)])
     scale = np.maximum(np.abs(A) + np.abs(B), 1)
     assert np.all(np.abs(got - ref) <= 1e-6 * scale)
+
+
+# --- MIRROR / REPEAT boundary conditions (Hipacc's MIRROR, REPEAT) ----------
+# scipy.ndimage's "reflect" extends ... c b a | a b c ... and "wrap" is
+# periodic: the two readings of the oracle.  Small images exercise repeated
+# reflection (windows wider than the image).
+
+def _bm(mode):
+    import oracle as O
+    return O.BORDER_MIRROR if mode == "reflect" else O.BORDER_REPEAT
+
+
+@pytest.mark.parametrize("mode", ["reflect", "wrap"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (3, 2), (9, 13), (40, 31)])
+def test_mirror_repeat_gaussian_box_sobel_match_scipy(orc, mode, shape):
+    img = synth.uniform_u8(shape[1], shape[0], seed=shape[0] * 7 + shape[1])
+    b = _bm(mode)
+    a = img.astype(np.int64)
+    w = np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]], np.int64)
+    assert (orc.gaussian3x3(img, b).data == ndi.correlate(a, w, mode=mode) // 16).all()
+    assert (orc.box3x3(img, b).data == ndi.correlate(a, np.ones((3, 3), np.int64), mode=mode) // 9).all()
+    kx = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]], np.int64)
+    gx, gy = orc.sobel3x3(img, b)
+    assert (gx.data == ndi.correlate(a, kx, mode=mode)).all()
+    assert (gy.data == ndi.correlate(a, kx.T, mode=mode)).all()
+    for r in (orc.gaussian3x3(img, b), gx):
+        assert r.rect == (0, 0, shape[1], shape[0])  # no shrinking
+
+
+@pytest.mark.parametrize("mode", ["reflect", "wrap"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 2), (4, 3), (23, 17)])
+def test_mirror_repeat_convolve_window_sum_morph_match_scipy(orc, mode, shape):
+    img = synth.uniform_u8(shape[1], shape[0], seed=91 + shape[0])
+    b = _bm(mode)
+    a = img.astype(np.int64)
+    c = np.arange(-12, 13, dtype=np.int64).reshape(5, 5)
+    want = np.clip(ndi.correlate(a, c, mode=mode) >> 2, -32768, 32767)
+    assert (orc.convolve(img, c, 2, b).data == want).all()
+    s32 = synth.uniform_u8(shape[1], shape[0], seed=5).astype(np.int32) * 1000 - 100000
+    ws = orc.window_sum(orc.Img(s32), 5, 3, b)
+    assert (ws.data == ndi.correlate(s32.astype(np.int64), np.ones((3, 5), np.int64),
+                                     mode=mode)).all()
+    for op, f in ((orc.MORPH_DILATE, ndi.grey_dilation), (orc.MORPH_ERODE, ndi.grey_erosion),
+                  (orc.MORPH_MEDIAN, ndi.median_filter)):
+        assert (orc.morph3x3(img, op, b).data == f(img, size=3, mode=mode)).all()
+
+
+def test_mirror_repeat_brute_force_coordinates(orc):
+    # the reading written out on a 1-D ramp: index i of a 3-pixel row
+    img = np.array([[10, 20, 30]], np.uint8)
+    c = np.zeros((1, 5), np.int64)
+    c[0, 0] = 1  # reads x - 2
+    got_m = orc.convolve(img, c, 0, orc.BORDER_MIRROR).data[0].tolist()
+    got_r = orc.convolve(img, c, 0, orc.BORDER_REPEAT).data[0].tolist()
+    # x - 2 for x = 0, 1, 2 is -2, -1, 0: mirror -> 1, 0, 0; repeat -> 1, 2, 0
+    assert got_m == [20, 10, 10]
+    assert got_r == [20, 30, 10]
