@@ -68,10 +68,18 @@ typedef int32_t hvx_status;
  * (Hipacc's CLAMP boundary condition, Section 3.2); CONSTANT reads a constant
  * outside the image; UNDEFINED computes only pixels whose whole window lies in
  * the input's valid region, so the valid region shrinks by the window radius
- * and pixels outside it are written as 0. */
+ * and pixels outside it are written as 0.  MIRROR and REPEAT are Hipacc's
+ * other boundary conditions (Section 3.2 names them; the paper does not define
+ * them): MIRROR reflects coordinates about the image edge with the edge pixel
+ * repeated (... c b a | a b c ...), as often as needed; REPEAT continues the
+ * image periodically.  Both read arbitrary pixels of their input, so a local
+ * node under them reads its input from memory: the planner does not fuse it
+ * with the node that produces that input. */
 #define HVX_BORDER_UNDEFINED 0
 #define HVX_BORDER_REPLICATE 1
 #define HVX_BORDER_CONSTANT 2
+#define HVX_BORDER_MIRROR 3
+#define HVX_BORDER_REPEAT 4
 
 /* Rounding of the divisions in Gaussian3x3 (by 16) and Box3x3 (by 9). */
 #define HVX_ROUND_TO_ZERO 0

@@ -92,12 +92,14 @@ def _declare(L):
     L.orc_convolve_u8_u8.argtypes = [P, P, I, I, I, I, P, I, I, I, R, R]
     L.orc_tomasi_response.argtypes = [P, P, P, P, I, I, R, R, R, R]
     L.orc_bitwise.argtypes = [P, P, P, I, I, I, R, R, R]
+    L.orc_multiply.argtypes = [P, I, P, I, P, I, I, I, ctypes.c_float, I, I, R, R, R]
     for name in ("orc_gaussian3x3", "orc_box3x3", "orc_morph3x3", "orc_bitwise",
                  "orc_convolve_u8_u8", "orc_tomasi_response",
                  "orc_sobel3x3", "orc_window_sum_s32",
                  "orc_convolve_u8_s16", "orc_magnitude", "orc_phase", "orc_threshold",
                  "orc_channel_extract_uyvy", "orc_arith", "orc_mul_s16_s32",
-                 "orc_harris_response", "orc_harris_graph", "orc_edge_graph"):
+                 "orc_harris_response", "orc_harris_graph", "orc_edge_graph",
+                 "orc_multiply"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -290,6 +292,19 @@ def arith(a, b, out_dtype, op=ARITH_ADD, saturate=True) -> Img:
     _check(lib().orc_arith(_p(A.data), _FMT_OF[A.data.dtype], _p(B.data),
                            _FMT_OF[B.data.dtype], _p(out), _FMT_OF[np.dtype(out_dtype)],
                            A.w, A.h, op, int(saturate), _rect(A.rect), _rect(B.rect), vo))
+    return Img(out, tuple(vo))
+
+
+def multiply(a, b, scale, out_dtype, saturate=True, nearest_even=False) -> Img:
+    """Multiply node: a * b * scale (scale rounded to binary32), one rounding
+    (toward zero, or to nearest with ties to even), then wrap / saturate."""
+    A, B = _as_img(a), _as_img(b)
+    out = np.empty(A.data.shape, out_dtype)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_multiply(_p(A.data), _FMT_OF[A.data.dtype], _p(B.data),
+                              _FMT_OF[B.data.dtype], _p(out), _FMT_OF[np.dtype(out_dtype)],
+                              A.w, A.h, ctypes.c_float(scale), int(saturate), int(nearest_even),
+                              _rect(A.rect), _rect(B.rect), vo))
     return Img(out, tuple(vo))
 
 

@@ -117,6 +117,7 @@ _IN_FMTS = {
     "channel_extract": [("UYVY",)],
     "add": [("U8", "S16"), ("U8", "S16")], "subtract": [("U8", "S16"), ("U8", "S16")],
     "absdiff": [("U8", "S16"), ("U8", "S16")],
+    "multiply": [("U8", "S16"), ("U8", "S16")],
     "dilate3x3": [("U8",)], "erode3x3": [("U8",)], "median3x3": [("U8",)],
     "and": [("U8",), ("U8",)], "or": [("U8",), ("U8",)], "xor": [("U8",), ("U8",)],
     "not": [("U8",)],
@@ -350,6 +351,10 @@ def run(g: GraphDesc, inputs: dict, dce: bool = True) -> dict:
             r = O.morph3x3(x[0], _MORPH[k], b, c)
         elif k in _BITS:
             r = O.bitwise(x[0], x[1] if k != "not" else None, _BITS[k])
+        elif k == "multiply":
+            r = O.multiply(x[0], x[1], p.get("scale", 1.0), _NPFMT[g.data[op.out].fmt],
+                           p.get("policy", "saturate") == "saturate",
+                           p.get("rounding", "zero") == "nearest_even")
         elif k in _ARITH:
             r = O.arith(x[0], x[1], _NPFMT[g.data[op.out].fmt], _ARITH[k],
                         p.get("policy", "saturate") == "saturate")

@@ -786,9 +786,7 @@ hvx_node hvxLocalNode(hvx_graph g, int32_t op, int32_t kw, int32_t kh, hvx_image
 
 hvx_status hvxSetNodeBorder(hvx_node hn, int32_t mode, int32_t constant) {
     if (!ok_node(hn)) return HVX_ERROR_INVALID_REFERENCE;
-    if (mode != HVX_BORDER_UNDEFINED && mode != HVX_BORDER_REPLICATE &&
-        mode != HVX_BORDER_CONSTANT)
-        return HVX_ERROR_INVALID_PARAMETERS;
+    if (mode < HVX_BORDER_UNDEFINED || mode > HVX_BORDER_REPEAT) return HVX_ERROR_INVALID_PARAMETERS;
     Node* n = N(hn);
     n->border = mode;
     n->cval = constant;

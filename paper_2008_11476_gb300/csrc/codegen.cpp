@@ -646,6 +646,15 @@ struct Emitter {
         return "0";
     }
 
+    // Coordinates an external input's out-of-image cell reads.
+    std::string fill_coords(int b) const {
+        switch (d.buf[b].fill) {
+            case FILL_MIRROR: return "hvx_mirror(x, p.W), hvx_mirror(y, p.H))";
+            case FILL_REPEAT: return "hvx_repeat(x, p.W), hvx_repeat(y, p.H))";
+            default: return "min(max(x, 0), p.W - 1), min(max(y, 0), p.H - 1))";
+        }
+    }
+
     std::string slot_name(int s) const {
         return s < d.n_buf ? "B" + std::to_string(s) : "R" + std::to_string(s - d.n_buf);
     }
@@ -662,7 +671,10 @@ struct Emitter {
           << "      if (!CHECK || (x >= 0 && x < p.W && y >= 0 && y < p.H)) v = " << ld
           << "x, y);\n"
           << "      else v = "
-          << fill_expr(b, ld + "min(max(x, 0), p.W - 1), min(max(y, 0), p.H - 1))") << ";\n"
+          << (d.buf[b].fill == FILL_MIRROR || d.buf[b].fill == FILL_REPEAT
+                  ? ld + fill_coords(b)
+                  : fill_expr(b, ld + fill_coords(b)))
+          << ";\n"
           << "      B" << b << "[r * " << bw(b) << " + c] = v;\n";
         close_cells();
     }
@@ -806,6 +818,10 @@ struct Emitter {
 
     bool emit() {
         analyse();
+        // MIRROR / REPEAT fills are only possible for external inputs
+        for (int b = 0; b < d.n_buf; ++b)
+            if ((d.buf[b].fill == FILL_MIRROR || d.buf[b].fill == FILL_REPEAT) && ext_in[b] < 0)
+                return false;
         if (!plan() || !choose_tile()) return false;
         o << "// generated kernel: " << d.n_stage << " ops, " << d.n_buf << " images, tile " << tw
           << " x " << th << ", " << passes.size() << " passes, " << smem_words * 4
@@ -813,6 +829,11 @@ struct Emitter {
           << "#include \"point_math.cuh\"\n#include \"jit_params.h\"\n\n"
           << "__device__ __forceinline__ bool hvx_in(const int* r, int x, int y) {\n"
           << "  return x >= r[0] && x < r[2] && y >= r[1] && y < r[3];\n}\n"
+          << "__device__ __forceinline__ int hvx_mirror(int v, int n) {\n"
+          << "  const int p = 2 * n;\n  int m = v % p;\n  if (m < 0) m += p;\n"
+          << "  return m < n ? m : p - 1 - m;\n}\n"
+          << "__device__ __forceinline__ int hvx_repeat(int v, int n) {\n"
+          << "  const int m = v % n;\n  return m < 0 ? m + n : m;\n}\n"
           << "template <int F>\n"
           << "__device__ __forceinline__ int hvx_ld(const void* base, unsigned long long pitch, "
              "int x, int y) {\n"

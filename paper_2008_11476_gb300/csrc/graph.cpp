@@ -399,8 +399,11 @@ struct Planner {
                 if (it != node_group.end()) target = it->second;
             } else {
                 bool size_change = op.kind == OP_CHX && op.node->p.channel != HVX_CHANNEL_Y;
+                // a MIRROR / REPEAT local op reads its inputs from memory, like
+                // external inputs, whoever produces them
+                const bool wraps = op_is_local(op.kind) && border_wraps(op.node->border);
                 std::set<int> prod_groups;
-                for (int k = 0; k < op.n_in; ++k) {
+                for (int k = 0; k < op.n_in && !wraps; ++k) {
                     auto w = writer.find(op.in[k]);
                     if (w != writer.end()) prod_groups.insert(op_group[w->second]);
                 }
@@ -425,6 +428,12 @@ struct Planner {
                     int gi = *prod_groups.begin();
                     Group& G = P.groups[gi];
                     bool same_size = G.W == op.out->w && G.H == op.out->h;
+                    // MIRROR / REPEAT read pixels anywhere in the input: never
+                    // from a tile of the producer fused into the same kernel
+                    if (op_is_local(op.kind) && border_wraps(op.node->border))
+                        for (int j : G.ops)
+                            for (int k = 0; k < op.n_in; ++k)
+                                if (P.ops[j].out == op.in[k]) same_size = false;
                     std::vector<int> trial = G.ops;
                     trial.push_back(i);
                     if (!G.closed && same_size && border_compatible(G.ops, op) &&
@@ -576,8 +585,7 @@ hvx_status verify_graph(Graph* g) {
             const NodeParams& p = op.node->p;
             if (op_is_local(op.kind)) {
                 int b = op.node->border;
-                if (b != HVX_BORDER_UNDEFINED && b != HVX_BORDER_REPLICATE &&
-                    b != HVX_BORDER_CONSTANT)
+                if (b < HVX_BORDER_UNDEFINED || b > HVX_BORDER_REPEAT)
                     fail(HVX_ERROR_INVALID_PARAMETERS);
             }
             if (op.kind == OP_HARRIS && (p.kd < 1 || p.kd > 1000 || p.kn < 0 || p.kn > 1000))

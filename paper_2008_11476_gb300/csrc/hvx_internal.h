@@ -152,6 +152,12 @@ struct Op {
     int group = -1;
 };
 
+// MIRROR / REPEAT read arbitrary pixels of a local operator's input: such an
+// input is read from memory, never from a fused producer's tile.
+inline bool border_wraps(int border) {
+    return border == HVX_BORDER_MIRROR || border == HVX_BORDER_REPEAT;
+}
+
 // A kernel generated for a staged-tile group (codegen.cpp) and its launch.
 struct JitKernel;
 struct JitLaunch {

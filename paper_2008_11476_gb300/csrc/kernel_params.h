@@ -46,7 +46,13 @@ constexpr int GEN_TW = 64;   // output tile width of the generic executor
 constexpr int GEN_TH = 16;   // output tile height
 constexpr int GEN_THREADS = 256;
 
-enum GenFill : int32_t { FILL_NONE = 0, FILL_REPLICATE = 1, FILL_CONSTANT = 2 };
+enum GenFill : int32_t {
+    FILL_NONE = 0,
+    FILL_REPLICATE = 1,
+    FILL_CONSTANT = 2,
+    FILL_MIRROR = 3,  // external inputs only
+    FILL_REPEAT = 4,  // external inputs only
+};
 
 struct GenBuf {
     int32_t halo;      // the buffer holds the output tile grown by `halo` pixels

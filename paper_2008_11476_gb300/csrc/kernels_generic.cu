@@ -8,7 +8,9 @@
 // are loaded with their border mode applied; each op then computes its buffer
 // cells that lie in the image (0 outside the image's valid region), and cells
 // outside the image are filled the way the op's local consumers read them
-// (REPLICATE from the nearest image cell, CONSTANT with the constant).  Group
+// (REPLICATE from the nearest image cell, CONSTANT with the constant; MIRROR
+// and REPEAT only occur on external inputs, read at the reflected or
+// periodic pixel).  Group
 // outputs are written from the buffers' central 64 x 16 region.  Cells hold
 // int32 (U8 / S16 / S32 / UYVY pairs) or binary32 (F32).
 #include "device_common.cuh"
@@ -42,6 +44,20 @@ __device__ __forceinline__ void store_pixel(const GenExt& e, int x, int y, int32
         case HVX_DF_S32:
         case HVX_DF_F32: reinterpret_cast<int32_t*>(row)[x] = v; break;
     }
+}
+
+// Image coordinate read by coordinate v (extent n) under MIRROR: reflection
+// about the edge with the edge pixel repeated has period 2n; under REPEAT the
+// period is n.
+__device__ __forceinline__ int mirror_coord(int v, int n) {
+    const int p = 2 * n;
+    int m = v % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+__device__ __forceinline__ int repeat_coord(int v, int n) {
+    const int m = v % n;
+    return m < 0 ? m + n : m;
 }
 
 // A buffer seen from the cells of another (output) buffer: element (c, r) of
@@ -209,6 +225,10 @@ __global__ void __launch_bounds__(GEN_THREADS) generic_kernel(const GenericDesc 
                 v = b.cval;
             else if (b.fill == FILL_REPLICATE)
                 v = load_pixel(ex, clampi(x, 0, W - 1), clampi(y, 0, H - 1));
+            else if (b.fill == FILL_MIRROR)
+                v = load_pixel(ex, mirror_coord(x, W), mirror_coord(y, H));
+            else if (b.fill == FILL_REPEAT)
+                v = load_pixel(ex, repeat_coord(x, W), repeat_coord(y, H));
             else
                 v = 0;
             dst[r * bw + c] = v;

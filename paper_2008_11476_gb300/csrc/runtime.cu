@@ -121,6 +121,7 @@ bool match_edge(const Plan& P, const Group& G, EdgeMatch& m) {
     }
     if (m.gauss < 0 || m.sx < 0 || m.sy < 0) return false;
     const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx], &sy = P.ops[m.sy];
+    if (border_wraps(g.node->border) || border_wraps(sx.node->border)) return false;
     if (G.inputs.size() != 1 || G.inputs[0] != g.in[0] || g.in[0]->fmt != HVX_DF_U8) return false;
     if (sx.in[0] != g.out || sy.in[0] != g.out || sx.node != sy.node) return false;
     if (m.mag >= 0 && (P.ops[m.mag].in[0] != sx.out || P.ops[m.mag].in[1] != sy.out)) return false;
@@ -246,6 +247,7 @@ bool match_harris(const Plan& P, const Group& G, HarrisMatch& m) {
     if (m.sx < 0 || m.sy < 0 || muls.size() != 3 || sums.size() != 3 || m.resp < 0) return false;
     const Op &sx = P.ops[m.sx], &sy = P.ops[m.sy];
     if (sx.node != sy.node || G.inputs.size() != 1 || G.inputs[0] != sx.in[0]) return false;
+    if (border_wraps(sx.node->border)) return false;
     Image *X = sx.out, *Y = sy.out;
     for (int i : muls) {
         const Op& o = P.ops[i];
@@ -263,6 +265,7 @@ bool match_harris(const Plan& P, const Group& G, HarrisMatch& m) {
     for (int i : sums) {
         const Op& o = P.ops[i];
         if (o.rx != 2 || o.ry != 2 || o.node->border != s0.node->border ||
+            border_wraps(o.node->border) ||
             o.node->cval != s0.node->cval)
             return false;
         if (o.in[0] == P.ops[m.pxx].out)
@@ -420,12 +423,20 @@ hvx_status build_generic(Plan& P, Group& G) {
             for (int k = 0; k < c.n_in; ++k)
                 if (c.in[k] == im) {
                     if (c.node->border == HVX_BORDER_REPLICATE) gb.fill = FILL_REPLICATE;
+                    if (c.node->border == HVX_BORDER_MIRROR) gb.fill = FILL_MIRROR;
+                    if (c.node->border == HVX_BORDER_REPEAT) gb.fill = FILL_REPEAT;
                     if (c.node->border == HVX_BORDER_CONSTANT) {
                         gb.fill = FILL_CONSTANT;
                         gb.cval = im->fmt == HVX_DF_U8 ? (c.node->cval & 0xFF) : c.node->cval;
                     }
                 }
         }
+        // MIRROR / REPEAT fills read anywhere in the image: only external
+        // inputs, loaded from memory, can take them (the planner keeps such
+        // consumers out of their producer's group)
+        if ((gb.fill == FILL_MIRROR || gb.fill == FILL_REPEAT) &&
+            std::find(G.inputs.begin(), G.inputs.end(), im) == G.inputs.end())
+            return HVX_ERROR_NOT_SUPPORTED;
         set_rect(gb.valid, im->valid);
         gb.smem_off = words;
         words += (GEN_TW + 2 * gb.halo) * (GEN_TH + 2 * gb.halo);
@@ -518,7 +529,7 @@ hvx_status prepare_launches(Graph* g) {
         EdgeMatch em;
         HarrisMatch hm;
         const Op& first = P.ops[G.ops[0]];
-        if (G.ops.size() == 1 && first.kind == OP_GAUSS) {
+        if (G.ops.size() == 1 && first.kind == OP_GAUSS && !border_wraps(first.node->border)) {
             G.kernel = GK_GAUSS;
             st = build_gauss(P, G, ctx);
         } else if (G.ops.size() == 1 && first.kind == OP_CHX &&

@@ -30,6 +30,7 @@ HVX_ERROR_NOT_SUPPORTED = -10
 
 HVX_DF_VIRT, HVX_DF_U8, HVX_DF_S16, HVX_DF_S32, HVX_DF_F32, HVX_DF_UYVY = 0, 1, 2, 3, 4, 5
 HVX_BORDER_UNDEFINED, HVX_BORDER_REPLICATE, HVX_BORDER_CONSTANT = 0, 1, 2
+HVX_BORDER_MIRROR, HVX_BORDER_REPEAT = 3, 4
 HVX_ROUND_TO_ZERO, HVX_ROUND_TO_NEAREST = 0, 1
 HVX_THRESHOLD_BINARY, HVX_THRESHOLD_RANGE = 0, 1
 HVX_POLICY_WRAP, HVX_POLICY_SATURATE = 0, 1

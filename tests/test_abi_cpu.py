@@ -349,3 +349,27 @@ def test_section6_applications_plan(pctx):
             # the horizontal Sobel derivative is the redundant kernel of Fig. 2
             assert (H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_ALIVE_OPS)
                     == H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_OPS) - 1)
+
+
+def test_mirror_repeat_plan(pctx):
+    # MIRROR / REPEAT local nodes take the staged-tile path and never read a
+    # fused producer's tile; their outputs keep the full valid region
+    src = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+    for border in (H.HVX_BORDER_MIRROR, H.HVX_BORDER_REPEAT):
+        out = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+        g = H.hvxCreateGraph(pctx)
+        H.hvxSetNodeBorder(H.hvxGaussian3x3Node(g, src, out), border, 0)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["staged_tile"]
+        assert H.hvxGetValidRegion(out) == (0, 0, 640, 480)
+        ph = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+        mk = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+        g = PG.edge_graph(pctx, src, ph, mk, border=border)
+        kinds = PG.kernel_kinds(g)
+        assert "fused_edge_tma" not in kinds and len(kinds) == 2  # Sobel reads G from memory
+        g = PG.edge_graph(pctx, src, ph, mk, sobel_border=border)
+        assert "fused_edge_tma" not in PG.kernel_kinds(g)
+        assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 640 * 480
+    g = H.hvxCreateGraph(pctx)
+    with pytest.raises(H.HvxError):
+        H.hvxSetNodeBorder(H.hvxGaussian3x3Node(g, src, H.hvxCreateVirtualImage(g)), 5, 0)

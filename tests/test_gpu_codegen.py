@@ -1,7 +1,7 @@
 """Kernels generated per graph (hvxSetGraphCodegen) against the CPU oracle and
 against the staged-tile interpreter kernel: seeded random graphs of point and
-local nodes (every border mode, U8 and S16 images, outputs that later nodes
-also read), fused and unfused, on sizes with no interior tile, with ragged
+local nodes (every border mode including MIRROR and REPEAT, U8 and S16
+images, outputs that later nodes also read), fused and unfused, on sizes with no interior tile, with ragged
 tiles and with many interior tiles.  Bit-exact."""
 import numpy as np
 import pytest
@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 FMT = {"U8": H.HVX_DF_U8, "S16": H.HVX_DF_S16}
 BORDER = {"replicate": H.HVX_BORDER_REPLICATE, "constant": H.HVX_BORDER_CONSTANT,
-          "undefined": H.HVX_BORDER_UNDEFINED}
+          "undefined": H.HVX_BORDER_UNDEFINED, "mirror": H.HVX_BORDER_MIRROR,
+          "repeat": H.HVX_BORDER_REPEAT}
 
 
 def random_graph(seed):
@@ -40,7 +41,8 @@ def random_graph(seed):
         p = {}
         if k in ("gaussian3x3", "box3x3", "dilate3x3", "erode3x3", "median3x3", "convolve",
                  "sobel3x3"):
-            p["border"] = ["replicate", "constant", "undefined"][int(rng.integers(3))]
+            p["border"] = ["replicate", "constant", "undefined", "mirror",
+                           "repeat"][int(rng.integers(5))]
             p["cval"] = int(rng.integers(0, 256))
         if k in ("gaussian3x3", "box3x3"):
             p["rounding"] = ["zero", "nearest"][int(rng.integers(2))]
@@ -284,3 +286,62 @@ def test_batch_of_different_generated_kernels(ctx):
     for res, ref in zip(outs, refs):
         for (_, im, _), want in zip(res, ref):
             np.testing.assert_array_equal(PG.download(im), want)
+
+
+WRAPS = [H.HVX_BORDER_MIRROR, H.HVX_BORDER_REPEAT]
+
+
+@pytest.mark.parametrize("codegen", [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE])
+@pytest.mark.parametrize("border", WRAPS)
+@pytest.mark.parametrize("w,h", [(1, 1), (2, 3), (5, 4), (131, 37), (300, 250)])
+def test_mirror_repeat_every_local_node(ctx, border, w, h, codegen):
+    import oracle as O
+    ob = O.BORDER_MIRROR if border == H.HVX_BORDER_MIRROR else O.BORDER_REPEAT
+    img = synth.rects_noise(w, h, seed=w * 3 + h)
+    src = PG.upload(ctx, img, H.HVX_DF_U8)
+    c5 = np.arange(-12, 13).reshape(5, 5)
+    cases = [
+        (lambda g, o: H.hvxGaussian3x3Node(g, src, o), H.HVX_DF_U8, O.gaussian3x3(img, ob)),
+        (lambda g, o: H.hvxBox3x3Node(g, src, o), H.HVX_DF_U8, O.box3x3(img, ob)),
+        (lambda g, o: H.hvxDilate3x3Node(g, src, o), H.HVX_DF_U8,
+         O.morph3x3(img, O.MORPH_DILATE, ob)),
+        (lambda g, o: H.hvxMedian3x3Node(g, src, o), H.HVX_DF_U8,
+         O.morph3x3(img, O.MORPH_MEDIAN, ob)),
+        (lambda g, o: H.hvxConvolveNode(g, src, c5.ravel(), 5, 5, 2, o), H.HVX_DF_S16,
+         O.convolve(img, c5, 2, ob)),
+        (lambda g, o: H.hvxSobel3x3Node(g, src, o, None), H.HVX_DF_S16, O.sobel3x3(img, ob)[0]),
+    ]
+    for make, fmt, ref in cases:
+        out = PG.empty(ctx, w, h, fmt)
+        g = H.hvxCreateGraph(ctx)
+        H.hvxSetNodeBorder(make(g, out), border, 0)
+        H.hvxSetGraphCodegen(g, codegen)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["staged_tile"]
+        H.hvxProcessGraph(g)
+        np.testing.assert_array_equal(PG.download(out), ref.data)
+        assert H.hvxGetValidRegion(out) == (0, 0, w, h)
+        H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("border", WRAPS)
+def test_mirror_repeat_consumer_reads_materialised_producer(ctx, border):
+    # Gaussian (REPLICATE) -> Sobel (MIRROR / REPEAT) -> Magnitude: the Sobel
+    # does not fuse with the Gaussian; the Gaussian image goes through memory
+    import oracle as O
+    ob = O.BORDER_MIRROR if border == H.HVX_BORDER_MIRROR else O.BORDER_REPEAT
+    w, h = 203, 77
+    img = synth.rects_noise(w, h, seed=5)
+    src = PG.upload(ctx, img, H.HVX_DF_U8)
+    out = PG.empty(ctx, w, h, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(ctx)
+    G, gx, gy = (H.hvxCreateVirtualImage(g) for _ in range(3))
+    H.hvxGaussian3x3Node(g, src, G)
+    H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, G, gx, gy), border, 0)
+    H.hvxMagnitudeNode(g, gx, gy, out)
+    H.hvxVerifyGraph(g)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES) == 2
+    H.hvxProcessGraph(g)
+    gxr, gyr = O.sobel3x3(O.gaussian3x3(img, O.BORDER_REPLICATE), ob)
+    np.testing.assert_array_equal(PG.download(out), O.magnitude(gxr, gyr).data)
+    H.hvxReleaseGraph(g)

@@ -603,3 +603,52 @@ def test_mirror_repeat_brute_force_coordinates(orc):
     # x - 2 for x = 0, 1, 2 is -2, -1, 0: mirror -> 1, 0, 0; repeat -> 1, 2, 0
     assert got_m == [20, 10, 10]
     assert got_r == [20, 30, 10]
+
+
+# --- Multiply (Table 2 point operator) --------------------------------------
+
+def _mul_exact(a, b, scale, out_dtype, saturate, nearest_even):
+    """a * b * scale as an exact fraction, rounded once, then wrapped or
+    saturated: element by element in Python integers."""
+    s = Fraction(float(np.float32(scale)))
+    lo, hi, bits = (0, 255, 8) if out_dtype == np.uint8 else (-32768, 32767, 16)
+    out = np.empty(a.shape, out_dtype)
+    for i in np.ndindex(a.shape):
+        v = Fraction(int(a[i])) * int(b[i]) * s
+        r = round(v) if nearest_even else int(v)  # round(): ties to even; int(): toward zero
+        if saturate:
+            r = min(max(r, lo), hi)
+        else:
+            r &= (1 << bits) - 1
+            if out_dtype == np.int16 and r >= 1 << 15:
+                r -= 1 << 16
+        out[i] = r
+    return out
+
+
+@pytest.mark.parametrize("scale", [1.0, 1 / 255, 0.5, 0.75, 3.0, 2.0 ** -10, 1 / 3, 0.0, 65536.0])
+@pytest.mark.parametrize("fmts", [(np.uint8, np.uint8, np.uint8), (np.uint8, np.int16, np.int16),
+                                  (np.int16, np.int16, np.int16)])
+def test_multiply_exact_rounding(orc, scale, fmts):
+    ta, tb, to = fmts
+    rng = np.random.default_rng(7)
+    a = (rng.integers(0, 256, (9, 11)) if ta == np.uint8
+         else rng.integers(-32768, 32768, (9, 11))).astype(ta)
+    b = (rng.integers(0, 256, (9, 11)) if tb == np.uint8
+         else rng.integers(-32768, 32768, (9, 11))).astype(tb)
+    for sat in (True, False):
+        for ne in (False, True):
+            got = orc.multiply(a, b, scale, to, sat, ne).data
+            np.testing.assert_array_equal(got, _mul_exact(a, b, scale, to, sat, ne))
+
+
+def test_multiply_ties_and_signs(orc):
+    a = np.array([[3, 5, -3, -5, 7]], np.int16)
+    one = np.ones_like(a)
+    half_even = orc.multiply(a, one, 0.5, np.int16, True, True).data[0].tolist()
+    half_zero = orc.multiply(a, one, 0.5, np.int16, True, False).data[0].tolist()
+    assert half_even == [2, 2, -2, -2, 4]   # 1.5, 2.5, -1.5, -2.5, 3.5 to even
+    assert half_zero == [1, 2, -1, -2, 3]
+    big = np.array([[255]], np.uint8)
+    assert orc.multiply(big, big, 1.0, np.uint8, True).data[0, 0] == 255
+    assert orc.multiply(big, big, 1.0, np.uint8, False).data[0, 0] == (255 * 255) & 0xFF
