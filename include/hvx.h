@@ -84,6 +84,7 @@ typedef int32_t hvx_status;
 /* Rounding of the divisions in Gaussian3x3 (by 16) and Box3x3 (by 9). */
 #define HVX_ROUND_TO_ZERO 0
 #define HVX_ROUND_TO_NEAREST 1 /* round half up */
+#define HVX_ROUND_TO_NEAREST_EVEN 2 /* Multiply: ties to even */
 
 #define HVX_THRESHOLD_BINARY 0 /* out = in > value ? true : false            */
 #define HVX_THRESHOLD_RANGE 1  /* out = (in > upper || in < lower) ? f : t   */
@@ -350,6 +351,15 @@ hvx_node hvxChannelExtractNode(hvx_graph g, hvx_image in, int32_t channel, hvx_i
 hvx_node hvxAddNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
+
+/* Multiply (point, Table 2): U8 or S16 inputs -> U8 or S16 output (formats as
+ * for Add).  out = a * b * scale, taken exactly for the binary32 scale given
+ * (0 <= scale <= 65536), rounded once per rounding (HVX_ROUND_TO_ZERO or
+ * HVX_ROUND_TO_NEAREST_EVEN), then wrapped or saturated per policy.  NULL
+ * (graph status HVX_ERROR_INVALID_PARAMETERS) for a scale, policy or rounding
+ * outside these values. */
+hvx_node hvxMultiplyNode(hvx_graph g, hvx_image a, hvx_image b, float scale, int32_t policy,
+                         int32_t rounding, hvx_image out);
 
 /* And / Or / Xor (point, Table 2): U8, U8 -> U8 bitwise; Not: U8 -> U8. */
 hvx_node hvxAndNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);

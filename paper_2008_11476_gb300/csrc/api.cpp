@@ -716,6 +716,22 @@ hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, 
     return arith_node(g, N_SUB, a, b, policy, out);
 }
 
+hvx_node hvxMultiplyNode(hvx_graph g, hvx_image a, hvx_image b, float scale, int32_t policy,
+                         int32_t rounding, hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    if (!(scale >= 0.0f && scale <= 65536.0f) ||
+        (policy != HVX_POLICY_WRAP && policy != HVX_POLICY_SATURATE) ||
+        (rounding != HVX_ROUND_TO_ZERO && rounding != HVX_ROUND_TO_NEAREST_EVEN)) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.policy = policy;
+    p.scale = scale;
+    p.mul_rounding = rounding;
+    return add_node(g, N_MULTIPLY, {a, b}, {out}, 1, p);
+}
+
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
     return arith_node(g, N_ABSDIFF, a, b, HVX_POLICY_SATURATE, out);
 }

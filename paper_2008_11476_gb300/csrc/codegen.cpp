@@ -523,6 +523,14 @@ struct Emitter {
                        lit64(st.k0) + ", " + lit64(st.k1) + "), " + lit64(st.k1) + "))";
             case OP_TOMASI:
                 return "__float_as_int(tomasi_response_f32(" + a + ", " + b + ", " + c + "))";
+            case OP_MULTIPLY: {
+                const std::string v = "multiply_scaled(" + a + ", " + b + ", " + lit64(st.k0) +
+                                      ", " + std::to_string(st.i3) + ", " +
+                                      (st.i2 ? "true" : "false") + ")";
+                if (st.i1 == HVX_DF_U8)
+                    return st.i0 ? "sat64_u8(" + v + ")" : "(int)(" + v + " & 0xFF)";
+                return st.i0 ? "sat64_s16(" + v + ")" : "wrap64_s16(" + v + ")";
+            }
         }
         return "0";
     }

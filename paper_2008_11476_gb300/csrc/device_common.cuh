@@ -162,6 +162,11 @@ __device__ __forceinline__ int32_t eval_point(const P& st, int32_t a, int32_t b,
         case OP_HARRIS:
             return __float_as_int(ratio_to_float(harris_q(a, b, c, st.k0, st.k1), st.k1));
         case OP_TOMASI: return __float_as_int(tomasi_response_f32(a, b, c));
+        case OP_MULTIPLY: {
+            const long long v = multiply_scaled(a, b, st.k0, st.i3, st.i2 != 0);
+            if (st.i1 == HVX_DF_U8) return st.i0 ? sat64_u8(v) : (int32_t)(v & 0xFF);
+            return st.i0 ? sat64_s16(v) : wrap64_s16(v);
+        }
     }
     return 0;
 }

@@ -66,6 +66,7 @@ const char* op_name(int kind) {
         case OP_XOR: return "xor";
         case OP_NOT: return "not";
         case OP_TOMASI: return "tomasi_response";
+        case OP_MULTIPLY: return "multiply";
     }
     return "?";
 }
@@ -127,6 +128,7 @@ void lower(Graph* g, Plan& P) {
             case N_OR: add(OP_OR, 0, 0); break;
             case N_XOR: add(OP_XOR, 0, 0); break;
             case N_NOT: add(OP_NOT, 0, 0); break;
+            case N_MULTIPLY: add(OP_MULTIPLY, 0, 0); break;
             case N_SOBEL:
                 if (!n->out[0] && !n->out[1]) fail(HVX_ERROR_INVALID_PARAMETERS);
                 if (n->out[0]) add(OP_SOBEL_X, 0, 1);
@@ -215,7 +217,8 @@ void infer(Op& op) {
             break;
         case OP_ADD:
         case OP_SUB:
-        case OP_ABSDIFF: {
+        case OP_ABSDIFF:
+        case OP_MULTIPLY: {
             need(0, {HVX_DF_U8, HVX_DF_S16});
             need(1, {HVX_DF_U8, HVX_DF_S16});
             bool any16 = in[0]->fmt == HVX_DF_S16 || in[1]->fmt == HVX_DF_S16;

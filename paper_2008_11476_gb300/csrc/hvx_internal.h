@@ -108,6 +108,7 @@ enum NodeKind : int {
     N_OR,
     N_XOR,
     N_NOT,
+    N_MULTIPLY,
 };
 
 struct NodeParams {
@@ -121,6 +122,8 @@ struct NodeParams {
     int kw = 3, kh = 3;
     int shift = 0;
     std::vector<int32_t> coeffs;
+    float scale = 1.0f;        // Multiply
+    int mul_rounding = HVX_ROUND_TO_ZERO;
 };
 
 struct Node {

@@ -33,6 +33,7 @@ enum OpKind : int {
     OP_XOR,
     OP_NOT,
     OP_TOMASI,
+    OP_MULTIPLY,
 };
 
 // ---------------------------------------------------------------------------

@@ -130,6 +130,32 @@ __device__ __forceinline__ int sat_u8(int v) { return min(max(v, 0), 255); }
 __device__ __forceinline__ int sat_s16(int v) { return min(max(v, -32768), 32767); }
 
 // ---------------------------------------------------------------------------
+// Multiply: a * b * scale for scale = m * 2^e (m the 24-bit significand of a
+// binary32 scale <= 2^16), exact in 64-bit integers (|a b m| < 2^54), rounded
+// once toward zero or to nearest with ties to even.
+__device__ __forceinline__ long long multiply_scaled(int a, int b, long long m, int e,
+                                                     bool nearest_even) {
+    const long long p = (long long)a * b * m;
+    if (e >= 0) return p << e;  // |p| 2^e <= 2^30 * 2^16
+    const int k = -e;
+    if (k > 62) return 0;       // |p| 2^-k < 2^54 / 2^63 < 1/2
+    const unsigned long long u = p < 0 ? 0ull - (unsigned long long)p : (unsigned long long)p;
+    unsigned long long q = u >> k;
+    if (nearest_even) {
+        const unsigned long long rem = u & ((1ull << k) - 1), half = 1ull << (k - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    return p < 0 ? -(long long)q : (long long)q;
+}
+
+// Saturation / wrap-around of a 64-bit result to U8 or S16.
+__device__ __forceinline__ int sat64_u8(long long v) { return (int)(v < 0 ? 0 : (v > 255 ? 255 : v)); }
+__device__ __forceinline__ int sat64_s16(long long v) {
+    return (int)(v < -32768 ? -32768 : (v > 32767 ? 32767 : v));
+}
+__device__ __forceinline__ int wrap64_s16(long long v) { return (int)(short)(unsigned short)(v & 0xFFFF); }
+
+// ---------------------------------------------------------------------------
 // Shi-Tomasi response: the smaller eigenvalue of the structure matrix
 // [a c; c b] of exact integer window sums, (tr - s) / 2 = 2 det / (tr + s)
 // with s = sqrt((a - b)^2 + 4 c^2), written without the cancellation of

@@ -93,6 +93,17 @@ void fill_point_params(T& st, const Op& op) {
             st.k0 = p.kn;
             st.k1 = p.kd;
             break;
+        case OP_MULTIPLY: {
+            // scale = k0 * 2^i3 exactly (k0 the 24-bit significand)
+            int ex = 0;
+            const float fr = std::frexp(p.scale, &ex);
+            st.k0 = (int64_t)std::ldexp((double)fr, 24);
+            st.i3 = p.scale == 0.0f ? 0 : ex - 24;
+            st.i0 = p.policy == HVX_POLICY_SATURATE;
+            st.i1 = op.out->fmt;
+            st.i2 = p.mul_rounding == HVX_ROUND_TO_NEAREST_EVEN;
+            break;
+        }
         case OP_CHX: st.i0 = p.channel; break;
         default: break;
     }

@@ -32,6 +32,7 @@ HVX_DF_VIRT, HVX_DF_U8, HVX_DF_S16, HVX_DF_S32, HVX_DF_F32, HVX_DF_UYVY = 0, 1, 
 HVX_BORDER_UNDEFINED, HVX_BORDER_REPLICATE, HVX_BORDER_CONSTANT = 0, 1, 2
 HVX_BORDER_MIRROR, HVX_BORDER_REPEAT = 3, 4
 HVX_ROUND_TO_ZERO, HVX_ROUND_TO_NEAREST = 0, 1
+HVX_ROUND_TO_NEAREST_EVEN = 2
 HVX_THRESHOLD_BINARY, HVX_THRESHOLD_RANGE = 0, 1
 HVX_POLICY_WRAP, HVX_POLICY_SATURATE = 0, 1
 HVX_CHANNEL_Y, HVX_CHANNEL_U, HVX_CHANNEL_V = 0, 1, 2
@@ -140,6 +141,7 @@ _SIGS = {
     "hvxAddNode": (P, [P, P, P, I32, P]),
     "hvxSubtractNode": (P, [P, P, P, I32, P]),
     "hvxAbsDiffNode": (P, [P, P, P, P]),
+    "hvxMultiplyNode": (P, [P, P, P, ctypes.c_float, I32, I32, P]),
     "hvxConvolveNode": (P, [P, P, ctypes.POINTER(I32), I32, I32, I32, P]),
     "hvxPointNode": (P, [P, I32, PP, I32, P, ctypes.POINTER(ctypes.c_double), I32]),
     "hvxLocalNode": (P, [P, I32, I32, I32, P, P]),
@@ -422,6 +424,11 @@ def hvxAddNode(g, a, b, policy, o):
 
 def hvxSubtractNode(g, a, b, policy, o):
     return _node(lib().hvxSubtractNode(g, a, b, policy, o), g, "hvxSubtractNode")
+
+
+def hvxMultiplyNode(g, a, b, scale, policy, rounding, o):
+    return _node(lib().hvxMultiplyNode(g, a, b, float(scale), policy, rounding, o), g,
+                 "hvxMultiplyNode")
 
 
 def hvxAbsDiffNode(g, a, b, o):

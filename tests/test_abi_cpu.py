@@ -373,3 +373,24 @@ def test_mirror_repeat_plan(pctx):
     g = H.hvxCreateGraph(pctx)
     with pytest.raises(H.HvxError):
         H.hvxSetNodeBorder(H.hvxGaussian3x3Node(g, src, H.hvxCreateVirtualImage(g)), 5, 0)
+
+
+def test_multiply_node_parameters(pctx):
+    a = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8)
+    b = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    for scale, rnd in ((-1.0, H.HVX_ROUND_TO_ZERO), (1e6, H.HVX_ROUND_TO_ZERO),
+                       (float("nan"), H.HVX_ROUND_TO_ZERO), (1.0, H.HVX_ROUND_TO_NEAREST)):
+        with pytest.raises(H.HvxError):
+            H.hvxMultiplyNode(g, a, b, scale, H.HVX_POLICY_SATURATE, rnd,
+                              H.hvxCreateVirtualImage(g))
+    out8 = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxMultiplyNode(g, a, b, 0.5, H.HVX_POLICY_SATURATE, H.HVX_ROUND_TO_NEAREST_EVEN, out8)
+    with pytest.raises(H.HvxError):  # an S16 input cannot give a U8 product
+        H.hvxVerifyGraph(g)
+    out16 = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxMultiplyNode(g, a, b, 0.5, H.HVX_POLICY_WRAP, H.HVX_ROUND_TO_ZERO, out16)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["plain_point"]

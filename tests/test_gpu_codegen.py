@@ -85,12 +85,15 @@ def random_graph(seed):
             nodes.append((kk, [pick(u8), pick(u8)], [o], p, ["U8"]))
             fmt[o] = "U8"
         elif k in ("add", "add16"):
-            kk = ["add", "subtract", "absdiff"][int(rng.integers(3))]
+            kk = ["add", "subtract", "absdiff", "multiply"][int(rng.integers(4))]
             a = pick(u8) if k == "add" else pick(s16)
             b = pick(u8) if rng.random() < 0.5 or not s16 else pick(s16)
             f = "S16" if "S16" in (fmt[a], fmt[b]) or rng.random() < 0.5 else "U8"
             if kk != "absdiff":
                 p["policy"] = ["saturate", "wrap"][int(rng.integers(2))]
+            if kk == "multiply":
+                p["scale"] = [1.0, 1 / 255, 0.5, 3.0, 2.0 ** -7][int(rng.integers(5))]
+                p["rounding"] = ["zero", "nearest_even"][int(rng.integers(2))]
             nodes.append((kk, [a, b], [o], p, [f]))
             fmt[o] = f
         elif k == "magnitude":
@@ -165,13 +168,17 @@ def build_hvx(ctx, src, nodes, fmt, external, w, h):
             n = H.hvxSubtractNode(g, a[0], a[1], pol[p["policy"]], o)
         elif k == "absdiff":
             n = H.hvxAbsDiffNode(g, a[0], a[1], o)
+        elif k == "multiply":
+            n = H.hvxMultiplyNode(g, a[0], a[1], p["scale"], pol[p["policy"]],
+                                  H.HVX_ROUND_TO_NEAREST_EVEN if p["rounding"] == "nearest_even"
+                                  else H.HVX_ROUND_TO_ZERO, o)
         elif k == "magnitude":
             n = H.hvxMagnitudeNode(g, a[0], a[1], o)
         elif k == "phase":
             n = H.hvxPhaseNode(g, a[0], a[1], o)
         if "border" in p:
             H.hvxSetNodeBorder(n, BORDER[p["border"]], p["cval"])
-        if p.get("rounding") == "nearest":
+        if p.get("rounding") == "nearest" and k != "multiply":
             H.hvxSetNodeRounding(n, H.HVX_ROUND_TO_NEAREST)
     return g, im
 
@@ -345,3 +352,39 @@ def test_mirror_repeat_consumer_reads_materialised_producer(ctx, border):
     gxr, gyr = O.sobel3x3(O.gaussian3x3(img, O.BORDER_REPLICATE), ob)
     np.testing.assert_array_equal(PG.download(out), O.magnitude(gxr, gyr).data)
     H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("fmts", [("U8", "U8", "U8"), ("U8", "S16", "S16"), ("S16", "S16", "S16"),
+                                  ("U8", "U8", "S16")])
+@pytest.mark.parametrize("scale", [1.0, 1 / 255, 0.5, 3.0, 2.0 ** -20, 65536.0])
+def test_multiply_node(ctx, fmts, scale):
+    import oracle as O
+    npf = {"U8": np.uint8, "S16": np.int16}
+    w, h = 97, 31
+    rng = np.random.default_rng(int(scale * 1000) % 97)
+    arrs = []
+    for f in fmts[:2]:
+        arrs.append((rng.integers(0, 256, (h, w)) if f == "U8"
+                     else rng.integers(-32768, 32768, (h, w))).astype(npf[f]))
+    srcs = [PG.upload(ctx, a, FMT[f]) for a, f in zip(arrs, fmts[:2])]
+    for pol, sat in ((H.HVX_POLICY_SATURATE, True), (H.HVX_POLICY_WRAP, False)):
+        for rnd, ne in ((H.HVX_ROUND_TO_ZERO, False), (H.HVX_ROUND_TO_NEAREST_EVEN, True)):
+            ref = O.multiply(arrs[0], arrs[1], scale, npf[fmts[2]], sat, ne)
+            for fused in (False, True):
+                out = PG.empty(ctx, w, h, FMT[fmts[2]])
+                g = H.hvxCreateGraph(ctx)
+                if fused:  # inside a generated kernel, behind a Dilate of the first input
+                    d = H.hvxCreateVirtualImage(g)
+                    if fmts[0] != "U8":
+                        continue
+                    H.hvxSetNodeBorder(H.hvxDilate3x3Node(g, srcs[0], d), H.HVX_BORDER_REPLICATE, 0)
+                    H.hvxMultiplyNode(g, d, srcs[1], scale, pol, rnd, out)
+                    want = O.multiply(O.morph3x3(arrs[0], O.MORPH_DILATE), arrs[1], scale,
+                                      npf[fmts[2]], sat, ne).data
+                else:
+                    H.hvxMultiplyNode(g, srcs[0], srcs[1], scale, pol, rnd, out)
+                    want = ref.data
+                H.hvxVerifyGraph(g)
+                H.hvxProcessGraph(g)
+                np.testing.assert_array_equal(PG.download(out), want)
+                H.hvxReleaseGraph(g)
