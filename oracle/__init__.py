@@ -93,13 +93,19 @@ def _declare(L):
     L.orc_tomasi_response.argtypes = [P, P, P, P, I, I, R, R, R, R]
     L.orc_bitwise.argtypes = [P, P, P, I, I, I, R, R, R]
     L.orc_multiply.argtypes = [P, I, P, I, P, I, I, I, ctypes.c_float, I, I, R, R, R]
+    L.orc_mean_stddev.argtypes = [P, I, I, I, R, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_float)]
+    L.orc_minmaxloc.argtypes = [P, I, I, I, R, ctypes.POINTER(ctypes.c_int64)]
+    L.orc_histogram.argtypes = [P, I, I, R, I, I, I, P]
+    L.orc_equalize_hist.argtypes = [P, P, I, I, R, R]
     for name in ("orc_gaussian3x3", "orc_box3x3", "orc_morph3x3", "orc_bitwise",
                  "orc_convolve_u8_u8", "orc_tomasi_response",
                  "orc_sobel3x3", "orc_window_sum_s32",
                  "orc_convolve_u8_s16", "orc_magnitude", "orc_phase", "orc_threshold",
                  "orc_channel_extract_uyvy", "orc_arith", "orc_mul_s16_s32",
                  "orc_harris_response", "orc_harris_graph", "orc_edge_graph",
-                 "orc_multiply"):
+                 "orc_multiply", "orc_mean_stddev", "orc_minmaxloc", "orc_histogram",
+                 "orc_equalize_hist"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -305,6 +311,45 @@ def multiply(a, b, scale, out_dtype, saturate=True, nearest_even=False) -> Img:
                               _FMT_OF[B.data.dtype], _p(out), _FMT_OF[np.dtype(out_dtype)],
                               A.w, A.h, ctypes.c_float(scale), int(saturate), int(nearest_even),
                               _rect(A.rect), _rect(B.rect), vo))
+    return Img(out, tuple(vo))
+
+
+def mean_stddev(src):
+    """Global reduction: (mean, stddev, (S1, S2, N)) over the valid rectangle;
+    mean and stddev binary32 (Python floats holding binary32 values)."""
+    A = _as_img(src)
+    sums = (ctypes.c_int64 * 3)()
+    out = (ctypes.c_float * 2)()
+    _check(lib().orc_mean_stddev(_p(A.data), _FMT_OF[A.data.dtype], A.w, A.h, _rect(A.rect),
+                                 sums, out))
+    return out[0], out[1], (sums[0], sums[1], sums[2])
+
+
+def minmaxloc(src):
+    """Global reduction: dict(min, max, min_count, max_count, min_loc, max_loc),
+    locations (x, y) of the first occurrence in raster order."""
+    A = _as_img(src)
+    r = (ctypes.c_int64 * 8)()
+    _check(lib().orc_minmaxloc(_p(A.data), _FMT_OF[A.data.dtype], A.w, A.h, _rect(A.rect), r))
+    return {"min": r[0], "max": r[1], "min_count": r[2], "max_count": r[3],
+            "min_loc": (r[4], r[5]), "max_loc": (r[6], r[7])}
+
+
+def histogram(src, num_bins=256, offset=0, range_=256) -> np.ndarray:
+    A = _as_img(src)
+    assert A.data.dtype == np.uint8
+    bins = np.zeros(num_bins, np.uint32)
+    _check(lib().orc_histogram(_p(A.data), A.w, A.h, _rect(A.rect), num_bins, offset, range_,
+                               _p(bins)))
+    return bins
+
+
+def equalize_hist(src) -> Img:
+    A = _as_img(src)
+    assert A.data.dtype == np.uint8
+    out = np.empty(A.data.shape, np.uint8)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_equalize_hist(_p(A.data), _p(out), A.w, A.h, _rect(A.rect), vo))
     return Img(out, tuple(vo))
 
 

@@ -632,3 +632,132 @@ int orc_edge_graph(const uint8_t* in, uint8_t* phase, uint8_t* mask, int16_t* ma
     orc_phase(gx, gy, phase, w, h, vs, vs, vp);
     return orc_threshold(mag, ORC_S16, mask, w, h, 0, (double)thr, 0.0, 255, 0, vm, vt);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Global operators (Table 2 "reduce" and "histogram"; Section 4: the output
+ * depends on the whole input image).  Each traverses the input's valid
+ * rectangle in raster order.                                                 */
+
+/* MeanStdDev (reduction): the exact sums S1 = sum v, S2 = sum v^2 and the
+ * count N (sums[0..2]); mean = S1 / N and stddev = sqrt(N S2 - S1^2) / N.
+ * Reading (OpenVX gives no formula for the rounding): the population
+ * standard deviation; mean and stddev are the binary32 roundings of the
+ * double results of these expressions, with N S2 - S1^2 exact (128-bit) and
+ * converted to double once.  N = 0 gives mean = stddev = 0. */
+int orc_mean_stddev(const void* in, int fmt, int w, int h, const int vin[4], int64_t sums[3],
+                    float out[2]) {
+    int64_t s1 = 0, s2 = 0, n = 0;
+    (void)w;
+    (void)h;
+    if (fmt != ORC_U8 && fmt != ORC_S16) return ORC_ERR;
+    for (int y = vin[1]; y < vin[3]; ++y)
+        for (int x = vin[0]; x < vin[2]; ++x) {
+            int64_t v = (int64_t)load_as_double(in, fmt, (size_t)y * w + x);
+            s1 += v;
+            s2 += v * v;
+            n += 1;
+        }
+    sums[0] = s1;
+    sums[1] = s2;
+    sums[2] = n;
+    if (n == 0) {
+        out[0] = out[1] = 0.0f;
+        return ORC_OK;
+    }
+    __int128 var_n2 = (__int128)n * s2 - (__int128)s1 * s1;
+    out[0] = (float)((double)s1 / (double)n);
+    out[1] = (float)(sqrt((double)var_n2) / (double)n);
+    return ORC_OK;
+}
+
+/* MinMaxLoc (reduction): the minimum and maximum, how many pixels take each,
+ * and the first pixel (raster order) where each occurs.  res = {min, max,
+ * min_count, max_count, min_x, min_y, max_x, max_y}; an empty rectangle gives
+ * counts 0 and locations -1. */
+int orc_minmaxloc(const void* in, int fmt, int w, int h, const int vin[4], int64_t res[8]) {
+    (void)h;
+    if (fmt != ORC_U8 && fmt != ORC_S16) return ORC_ERR;
+    int64_t mn = 0, mx = 0, cmn = 0, cmx = 0;
+    int64_t mnx = -1, mny = -1, mxx = -1, mxy = -1;
+    for (int y = vin[1]; y < vin[3]; ++y)
+        for (int x = vin[0]; x < vin[2]; ++x) {
+            int64_t v = (int64_t)load_as_double(in, fmt, (size_t)y * w + x);
+            if (cmn == 0 || v < mn) {
+                mn = v;
+                cmn = 0;
+                mnx = x;
+                mny = y;
+            }
+            if (v == mn) cmn += 1;
+            if (cmx == 0 || v > mx) {
+                mx = v;
+                cmx = 0;
+                mxx = x;
+                mxy = y;
+            }
+            if (v == mx) cmx += 1;
+        }
+    res[0] = mn;
+    res[1] = mx;
+    res[2] = cmn;
+    res[3] = cmx;
+    res[4] = mnx;
+    res[5] = mny;
+    res[6] = mxx;
+    res[7] = mxy;
+    return ORC_OK;
+}
+
+/* Histogram (Table 2 "histogram"): num_bins bins over [offset, offset +
+ * range) of a U8 image; value v falls in bin (v - offset) * num_bins / range
+ * (integer division, the OpenVX distribution); values outside are not
+ * counted.  1 <= num_bins <= 256, offset >= 0, range >= 1, offset + range <=
+ * 256. */
+int orc_histogram(const uint8_t* in, int w, int h, const int vin[4], int num_bins, int offset,
+                  int range, uint32_t* bins) {
+    (void)h;
+    if (num_bins < 1 || num_bins > 256 || offset < 0 || range < 1 || offset + range > 256)
+        return ORC_ERR;
+    memset(bins, 0, (size_t)num_bins * sizeof(uint32_t));
+    for (int y = vin[1]; y < vin[3]; ++y)
+        for (int x = vin[0]; x < vin[2]; ++x) {
+            int v = in[(size_t)y * w + x];
+            if (v >= offset && v < offset + range) bins[(v - offset) * num_bins / range] += 1;
+        }
+    return ORC_OK;
+}
+
+/* EqualizeHist (Table 2: histogram + point): with the 256-bin histogram of
+ * the input's valid rectangle, its cumulative sum c, cmin = c at the smallest
+ * value present and N the pixel count, each pixel v becomes
+ * round((c[v] - cmin) * 255 / (N - cmin)) with halves rounded up.  Reading:
+ * OpenVX leaves the formula open; this is the usual normalised cumulative
+ * histogram.  A constant image (N == cmin) is left unchanged.  0 outside the
+ * valid rectangle, like every point operator. */
+int orc_equalize_hist(const uint8_t* in, uint8_t* out, int w, int h, const int vin[4],
+                      int vout[4]) {
+    uint32_t hist[256];
+    int64_t c[256], n = 0, cmin = -1;
+    int full[4];
+    orc_histogram(in, w, h, vin, 256, 0, 256, hist);
+    for (int v = 0; v < 256; ++v) {
+        n += hist[v];
+        c[v] = n;
+        if (cmin < 0 && hist[v] > 0) cmin = c[v];
+    }
+    memset(out, 0, (size_t)w * h);
+    for (int y = vin[1]; y < vin[3]; ++y)
+        for (int x = vin[0]; x < vin[2]; ++x) {
+            size_t i = (size_t)y * w + x;
+            if (n == cmin) {
+                out[i] = in[i];
+            } else {
+                int64_t num = (c[in[i]] - cmin) * 255;
+                int64_t den = n - cmin;
+                out[i] = (uint8_t)((2 * num + den) / (2 * den));
+            }
+        }
+    rect_copy(full, vin);
+    rect_copy(vout, full);
+    return ORC_OK;
+}

@@ -652,3 +652,78 @@ def test_multiply_ties_and_signs(orc):
     big = np.array([[255]], np.uint8)
     assert orc.multiply(big, big, 1.0, np.uint8, True).data[0, 0] == 255
     assert orc.multiply(big, big, 1.0, np.uint8, False).data[0, 0] == (255 * 255) & 0xFF
+
+
+# --- Global operators (Table 2 reduce / histogram) ---------------------------
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_mean_stddev_against_numpy(orc, dtype):
+    rng = np.random.default_rng(3)
+    a = (rng.integers(0, 256, (37, 53)) if dtype == np.uint8
+         else rng.integers(-32768, 32768, (37, 53))).astype(dtype)
+    mean, std, (s1, s2, n) = orc.mean_stddev(a)
+    wide = a.astype(np.int64)
+    assert (s1, s2, n) == (int(wide.sum()), int((wide * wide).sum()), a.size)
+    assert mean == np.float32(np.mean(wide, dtype=np.float64))
+    assert abs(std - np.std(wide.astype(np.float64))) <= 2e-7 * max(1.0, std)
+    # a valid rectangle restricts the traversal
+    m2, s2_, (t1, _, t3) = orc.mean_stddev(orc.Img(a, (5, 7, 40, 30)))
+    assert (t1, t3) == (int(wide[7:30, 5:40].sum()), 35 * 23)
+
+
+def test_mean_stddev_closed_forms(orc):
+    c = np.full((9, 9), 77, np.uint8)
+    assert orc.mean_stddev(c)[:2] == (77.0, 0.0)
+    two = np.array([[10, 30] * 8] * 4, np.uint8)   # half 10, half 30
+    assert orc.mean_stddev(two)[:2] == (20.0, 10.0)
+    assert orc.mean_stddev(orc.Img(c, (3, 3, 3, 3)))[:2] == (0.0, 0.0)  # empty
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_minmaxloc_against_numpy(orc, dtype):
+    rng = np.random.default_rng(11)
+    a = (rng.integers(0, 256, (41, 29)) if dtype == np.uint8
+         else rng.integers(-500, 500, (41, 29))).astype(dtype)
+    r = orc.minmaxloc(a)
+    assert r["min"] == a.min() and r["max"] == a.max()
+    assert r["min_count"] == (a == a.min()).sum() and r["max_count"] == (a == a.max()).sum()
+    iy, ix = np.unravel_index(np.argmin(a), a.shape)    # argmin: first occurrence
+    assert r["min_loc"] == (ix, iy)
+    iy, ix = np.unravel_index(np.argmax(a), a.shape)
+    assert r["max_loc"] == (ix, iy)
+    sub = orc.minmaxloc(orc.Img(a, (4, 6, 20, 33)))
+    s = a[6:33, 4:20]
+    iy, ix = np.unravel_index(np.argmax(s), s.shape)
+    assert sub["max"] == s.max() and sub["max_loc"] == (ix + 4, iy + 6)
+
+
+@pytest.mark.parametrize("nb,off,rng_", [(256, 0, 256), (16, 0, 256), (3, 0, 256), (10, 50, 100),
+                                         (7, 200, 56), (1, 0, 1)])
+def test_histogram_against_numpy(orc, nb, off, rng_):
+    a = synth.uniform_u8(61, 47, seed=nb + off)
+    got = orc.histogram(a, nb, off, rng_)
+    want, _ = np.histogram(a, bins=nb, range=(off, off + rng_))
+    # numpy's last bin is closed on the right: drop the value offset + range
+    if off + rng_ <= 255:
+        want[-1] -= int((a == off + rng_).sum())
+    np.testing.assert_array_equal(got, want)
+    assert got.sum() == ((a >= off) & (a < off + rng_)).sum()
+
+
+def test_equalize_hist_closed_forms_and_brute_force(orc):
+    c = np.full((6, 7), 123, np.uint8)
+    assert (orc.equalize_hist(c).data == c).all()            # constant: unchanged
+    two = np.array([[40, 90] * 5] * 3, np.uint8)
+    e = orc.equalize_hist(two).data
+    assert set(np.unique(e)) == {0, 255}                      # two levels spread to the extremes
+    ramp = np.repeat(np.arange(256, dtype=np.uint8)[None, :], 3, axis=0)
+    assert (orc.equalize_hist(ramp).data == ramp).all()       # flat histogram: identity
+    a = synth.uniform_u8(13, 9, seed=2) // 16 * 16 + 3
+    out = orc.equalize_hist(a).data
+    n = a.size
+    cmin = (a <= a.min()).sum()
+    for v in np.unique(a):                                     # rank form of the definition
+        cv = int((a <= v).sum())
+        want = ((cv - cmin) * 255 * 2 + (n - cmin)) // (2 * (n - cmin))
+        assert (out[a == v] == want).all()
+    assert (np.diff(out.ravel()[np.argsort(a.ravel(), kind="stable")].astype(int)) >= 0).all()
