@@ -361,6 +361,55 @@ hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 hvx_node hvxMultiplyNode(hvx_graph g, hvx_image a, hvx_image b, float scale, int32_t policy,
                          int32_t rounding, hvx_image out);
 
+/* Global operators (Table 2 "reduce" and "histogram"; Section 4: the output
+ * depends on the whole image).  Each node owns a result that
+ * hvxGetNodeResult copies out after the graph ran; the traversal covers the
+ * input's valid region.  Fused after the group that produces their input,
+ * they reduce that group's values as they are computed (no image is written
+ * for them); otherwise they read their input from memory. */
+
+/* MeanStdDev (U8 or S16): exact sums; mean = sum / count and stddev =
+ * sqrt(count * sum_squares - sum^2) / count (population), each rounded to
+ * binary32 from the double result of that expression. */
+typedef struct hvx_mean_stddev_s {
+    float mean, stddev;
+    int64_t sum;
+    uint64_t sum_squares, count;
+} hvx_mean_stddev;
+hvx_node hvxMeanStdDevNode(hvx_graph g, hvx_image in);
+
+/* MinMaxLoc (U8 or S16): the minimum and maximum, how many pixels take each,
+ * and the first pixel of each in raster order; an empty valid region gives
+ * counts 0 and locations -1. */
+typedef struct hvx_minmaxloc_s {
+    int32_t min, max;
+    uint64_t min_count, max_count;
+    int32_t min_x, min_y, max_x, max_y;
+} hvx_minmaxloc;
+hvx_node hvxMinMaxLocNode(hvx_graph g, hvx_image in);
+
+/* Histogram (U8): num_bins (1..256) bins over [offset, offset + range)
+ * (offset + range <= 256); value v counts in bin (v - offset) * num_bins /
+ * range (integer division); values outside are not counted.  The result is
+ * uint32_t[num_bins].  NULL (HVX_ERROR_INVALID_PARAMETERS) for other values. */
+hvx_node hvxHistogramNode(hvx_graph g, hvx_image in, int32_t num_bins, int32_t offset,
+                          int32_t range);
+
+/* EqualizeHist (U8 -> U8; histogram + point): with c the cumulative 256-bin
+ * histogram of the input's valid region, cmin its value at the smallest
+ * pixel value present and N the pixel count, v becomes
+ * round((c[v] - cmin) * 255 / (N - cmin)), halves up; a constant image is
+ * copied.  Runs as its own two launches (the histogram must be complete
+ * before any pixel is mapped). */
+hvx_node hvxEqualizeHistNode(hvx_graph g, hvx_image in, hvx_image out);
+
+/* Copy a global operator's result (hvx_mean_stddev, hvx_minmaxloc, or
+ * uint32_t[num_bins]) to host memory out (size bytes).  Call after the
+ * graph's processing has completed (hvxProcessGraph, or hvxWaitGraph /
+ * hvxWaitBatch after scheduling).  HVX_ERROR_NOT_SUPPORTED in a plan-only
+ * context; HVX_ERROR_INVALID_PARAMETERS for other nodes or a short buffer. */
+hvx_status hvxGetNodeResult(hvx_node node, void* out, uint64_t size);
+
 /* And / Or / Xor (point, Table 2): U8, U8 -> U8 bitwise; Not: U8 -> U8. */
 hvx_node hvxAndNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 hvx_node hvxOrNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);

@@ -28,7 +28,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "
 
 # (C++ identifier, header under csrc/) embedded for the run-time compiler
 JIT_HEADERS = [("kJitPointMath", "point_math.cuh"), ("kJitPhaseTable", "phase_table.h"),
-               ("kJitParams", "jit_params.h")]
+               ("kJitParams", "jit_params.h"), ("kJitReduceMath", "reduce_math.cuh")]
 
 
 def nvcc() -> str:

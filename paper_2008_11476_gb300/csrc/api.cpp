@@ -119,6 +119,8 @@ void destroy_graph(Graph* g) {
     if (g->scheduled && g->done) cudaEventSynchronize(g->done);
     release_plan(g);
     for (auto& n : g->nodes) {
+        if (n->d_aux) cudaFree(n->d_aux);
+        n->d_aux = nullptr;
         for (Image* im : n->in)
             if (im && !im->is_virtual) im->node_refs--;
         for (Image* im : n->out)
@@ -836,6 +838,109 @@ hvx_status hvxQueryNode(hvx_node hn, int32_t attr, void* out, uint64_t size) {
         return HVX_SUCCESS;
     }
     return HVX_ERROR_INVALID_PARAMETERS;
+}
+
+// ---- global operators (Table 2 "reduce" / "histogram") ---------------------------
+
+static hvx_node global_node(hvx_graph hg, int kind, hvx_image in, const NodeParams& p) {
+    if (!ok_graph(hg)) return nullptr;
+    Graph* g = G(hg);
+    // the node's result: a non-virtual data vertex owned by the graph
+    Image* r = new (std::nothrow) Image();
+    if (!r) {
+        g->last = HVX_ERROR_NO_MEMORY;
+        return nullptr;
+    }
+    r->ctx = g->ctx;
+    r->owner_graph = g;
+    r->is_result = true;
+    r->fmt = r->user_fmt = HVX_DF_RESULT;
+    g->virtuals.push_back(r);
+    return add_node(hg, kind, {in}, {reinterpret_cast<hvx_image>(r)}, 1, p);
+}
+
+hvx_node hvxMeanStdDevNode(hvx_graph g, hvx_image in) {
+    return global_node(g, N_MEANSTD, in, NodeParams());
+}
+
+hvx_node hvxMinMaxLocNode(hvx_graph g, hvx_image in) {
+    return global_node(g, N_MINMAX, in, NodeParams());
+}
+
+hvx_node hvxHistogramNode(hvx_graph g, hvx_image in, int32_t num_bins, int32_t offset,
+                          int32_t range) {
+    if (!ok_graph(g)) return nullptr;
+    if (num_bins < 1 || num_bins > 256 || offset < 0 || range < 1 || offset + range > 256) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.hist_bins = num_bins;
+    p.hist_offset = offset;
+    p.hist_range = range;
+    return global_node(g, N_HIST, in, p);
+}
+
+hvx_node hvxEqualizeHistNode(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_EQHIST, {in}, {out}, 1, NodeParams());
+}
+
+hvx_status hvxGetNodeResult(hvx_node hn, void* out, uint64_t size) {
+    if (!ok_node(hn)) return HVX_ERROR_INVALID_REFERENCE;
+    Node* n = N(hn);
+    if (!out) return HVX_ERROR_INVALID_PARAMETERS;
+    if (n->kind != N_MEANSTD && n->kind != N_MINMAX && n->kind != N_HIST)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    if (!n->graph->verified) return HVX_ERROR_NOT_VERIFIED;
+    if (n->graph->ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    Image* r = n->out[0];
+    if (!r || !r->dev) return HVX_ERROR_NOT_VERIFIED;
+    if (n->kind == N_HIST) {
+        const uint64_t bytes = 4ull * (uint64_t)n->p.hist_bins;
+        if (size < bytes) return HVX_ERROR_INVALID_PARAMETERS;
+        return cuda_status(cudaMemcpy(out, r->dev, bytes, cudaMemcpyDeviceToHost));
+    }
+    uint64_t w[4] = {0, 0, 0, 0};
+    const uint64_t bytes = n->kind == N_MEANSTD ? 24 : 32;
+    cudaError_t e = cudaMemcpy(w, r->dev, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (n->kind == N_MEANSTD) {
+        if (size < sizeof(hvx_mean_stddev)) return HVX_ERROR_INVALID_PARAMETERS;
+        hvx_mean_stddev m;
+        std::memset(&m, 0, sizeof(m));
+        m.sum = (int64_t)w[0];
+        m.sum_squares = w[1];
+        m.count = w[2];
+        if (m.count) {
+            // mean = S1 / N, stddev = sqrt(N S2 - S1^2) / N, N S2 - S1^2 exact
+            const __int128 var_n2 = (__int128)m.count * (__int128)m.sum_squares -
+                                    (__int128)m.sum * (__int128)m.sum;
+            m.mean = (float)((double)m.sum / (double)m.count);
+            m.stddev = (float)(std::sqrt((double)var_n2) / (double)m.count);
+        }
+        std::memcpy(out, &m, sizeof(m));
+        return HVX_SUCCESS;
+    }
+    if (size < sizeof(hvx_minmaxloc)) return HVX_ERROR_INVALID_PARAMETERS;
+    hvx_minmaxloc m;
+    std::memset(&m, 0, sizeof(m));
+    m.min_x = m.min_y = m.max_x = m.max_y = -1;
+    const uint64_t W = n->in[0]->w;
+    const uint64_t cmask = (1ull << 40) - 1;
+    if (w[0] != ~0ull) {
+        m.min = (int32_t)(w[0] >> 32) - 32768;
+        m.min_x = (int32_t)((w[0] & 0xFFFFFFFFull) % W);
+        m.min_y = (int32_t)((w[0] & 0xFFFFFFFFull) / W);
+        m.min_count = w[2] & cmask;
+    }
+    if (w[1] != ~0ull) {
+        m.max = 32767 - (int32_t)(w[1] >> 32);
+        m.max_x = (int32_t)((w[1] & 0xFFFFFFFFull) % W);
+        m.max_y = (int32_t)((w[1] & 0xFFFFFFFFull) / W);
+        m.max_count = w[3] & cmask;
+    }
+    std::memcpy(out, &m, sizeof(m));
+    return HVX_SUCCESS;
 }
 
 }  // extern "C"

@@ -173,6 +173,9 @@ struct Emitter {
     // r s^T of at least 15 taps): row sums with s are staged in shared
     // memory, the column sum with r is taken where the value is used.
     std::vector<std::vector<int>> sep_s, sep_r;  // per stage; empty: not separable
+    // global operators (MeanStdDev, MinMaxLoc, Histogram): reductions of their
+    // input over the output pass's cells; res[j] of the launch parameters
+    std::vector<int> globals;
 
     // Shared-memory slots: staged images (slot = buffer) and row-sum buffers
     // (slot = n_buf + stage); live from the pass that writes them to the
@@ -254,8 +257,13 @@ struct Emitter {
         sep_s.assign(d.n_stage, {});
         sep_r.assign(d.n_stage, {});
         for (int e = 0; e < d.n_in; ++e) ext_in[d.in[e].buf] = e;
+        globals.clear();
         for (int k = 0; k < d.n_stage; ++k) {
             const GenStage& st = d.st[k];
+            if (op_is_global(st.op)) {
+                globals.push_back(k);
+                continue;
+            }
             producer[st.out] = k;
             if (is_local(st.op)) staged[st.in[0]] = true;
             const int kw = 2 * st.rx + 1, kh = 2 * st.ry + 1;
@@ -278,6 +286,7 @@ struct Emitter {
         }
         for (int k = 0; k < d.n_stage; ++k) {  // stages are in topological order
             const GenStage& st = d.st[k];
+            if (st.out < 0) continue;
             int l = 0;
             for (int i = 0; i < 3; ++i)
                 if (st.in[i] >= 0) l = std::max(l, level[st.in[i]]);
@@ -319,8 +328,10 @@ struct Emitter {
         p.need_ld.assign(d.n_buf, false);
         p.read_cell.assign(d.n_buf, false);
         std::vector<int> want = targets;
-        if (targets.empty())
+        if (targets.empty()) {
             for (int e = 0; e < d.n_out; ++e) want.push_back(d.out[e].buf);
+            for (int k : globals) want.push_back(d.st[k].in[0]);
+        }
         for (int b : want)
             if (!visit(b, avail, p)) return false;
         Pass rp;
@@ -763,6 +774,14 @@ struct Emitter {
         else
             for (int b : p.targets) o << "B" << b << " ";
         o << "(halo " << h << ")\n";
+        if (outputs)
+            for (int k : globals) {
+                if (d.st[k].op == OP_MEANSTD)
+                    o << "  long long g" << k << "_s1 = 0;\n  unsigned long long g" << k
+                      << "_s2 = 0;\n  unsigned g" << k << "_n = 0;\n";
+                else if (d.st[k].op == OP_MINMAX)
+                    o << "  HvxMinMaxAcc g" << k << "_mm;\n  hvx_mm_init(g" << k << "_mm);\n";
+            }
         open_cells(th + 2 * h, tw + 2 * h, h, h, false);
         o << "      if (CHECK && (x < 0 || x >= p.W || y < 0 || y >= p.H)) continue;\n";
         for (int b = 0; b < d.n_buf; ++b)
@@ -802,7 +821,37 @@ struct Emitter {
             for (int e = 0; e < d.n_out; ++e)
                 o << "      hvx_st<" << d.out[e].fmt << ">(p.out[" << e << "], p.out_pitch[" << e
                   << "], x, y, " << val(d.out[e].buf) << ");\n";
+            for (int k : globals) {
+                const GenStage& st = d.st[k];
+                const std::string v = val(st.in[0]), g = "g" + std::to_string(k);
+                o << "      if (!CHECK || hvx_in(p.valid[" << st.in[0] << "], x, y)) {\n";
+                if (st.op == OP_MEANSTD)
+                    o << "        " << g << "_s1 += " << v << ";\n        " << g
+                      << "_s2 += (unsigned long long)((long long)" << v << " * " << v
+                      << ");\n        ++" << g << "_n;\n";
+                else if (st.op == OP_MINMAX)
+                    o << "        hvx_mm_add(" << g << "_mm, " << v
+                      << ", (unsigned)y * (unsigned)p.W + (unsigned)x);\n";
+                else
+                    o << "        if (" << v << " >= " << st.i1 << " && " << v << " < "
+                      << st.i1 + st.i2 << ") atomicAdd(&" << g << "_bins[(" << v << " - " << st.i1
+                      << ") * " << st.i0 << " / " << st.i2 << "], 1u);\n";
+                o << "      }\n";
+            }
             close_cells();
+            for (size_t j = 0; j < globals.size(); ++j) {
+                const int k = globals[j];
+                const std::string g = "g" + std::to_string(k), res = "p.res[" + std::to_string(j) + "]";
+                if (d.st[k].op == OP_MEANSTD)
+                    o << "  hvx_ms_commit(" << res << ", " << g << "_s1, " << g << "_s2, " << g
+                      << "_n);\n";
+                else if (d.st[k].op == OP_MINMAX)
+                    o << "  hvx_mm_commit_warp(" << res << ", " << g << "_mm);\n";
+                else
+                    o << "  __syncthreads();\n  for (int i = threadIdx.x; i < " << d.st[k].i0
+                      << "; i += " << kThreads << ")\n    if (" << g << "_bins[i]) atomicAdd((unsigned*)"
+                      << res << " + i, " << g << "_bins[i]);\n";
+            }
             return;
         }
         for (int b : p.targets) o << "      B" << b << "[r * " << bw(b) << " + c] = " << val(b) << ";\n";
@@ -834,7 +883,8 @@ struct Emitter {
         o << "// generated kernel: " << d.n_stage << " ops, " << d.n_buf << " images, tile " << tw
           << " x " << th << ", " << passes.size() << " passes, " << smem_words * 4
           << " bytes of shared memory\n"
-          << "#include \"point_math.cuh\"\n#include \"jit_params.h\"\n\n"
+          << "#include \"point_math.cuh\"\n#include \"reduce_math.cuh\"\n"
+          << "#include \"jit_params.h\"\n\n"
           << "__device__ __forceinline__ bool hvx_in(const int* r, int x, int y) {\n"
           << "  return x >= r[0] && x < r[2] && y >= r[1] && y < r[3];\n}\n"
           << "__device__ __forceinline__ int hvx_mirror(int v, int n) {\n"
@@ -862,6 +912,15 @@ struct Emitter {
           << "__device__ __forceinline__ void hvx_tile(const HvxJitParams& p, int* smem, int x0, "
              "int y0) {\n"
           << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
+        bool hist = false;
+        for (int k : globals)
+            if (d.st[k].op == OP_HIST) {
+                o << "  __shared__ unsigned g" << k << "_bins[" << d.st[k].i0 << "];\n"
+                  << "  for (int i = threadIdx.x; i < " << d.st[k].i0 << "; i += " << kThreads
+                  << ") g" << k << "_bins[i] = 0;\n";
+                hist = true;
+            }
+        if (hist) o << "  __syncthreads();\n";
         for (int s = 0; s < (int)slot.size(); ++s)
             if (slot[s].w > 0)
                 o << "  int* const " << slot_name(s) << " = smem + " << slot[s].off << ";  // "
@@ -932,10 +991,10 @@ bool compile(JitKernel& k) {
         k.log = n.why;
         return false;
     }
-    const char* names[] = {"point_math.cuh", "phase_table.h", "jit_params.h"};
-    const char* texts[] = {kJitPointMath, kJitPhaseTable, kJitParams};
+    const char* names[] = {"point_math.cuh", "phase_table.h", "jit_params.h", "reduce_math.cuh"};
+    const char* texts[] = {kJitPointMath, kJitPhaseTable, kJitParams, kJitReduceMath};
     void* prog = nullptr;
-    if (n.create(&prog, k.source.c_str(), "hvx_generated.cu", 3, texts, names) != 0) {
+    if (n.create(&prog, k.source.c_str(), "hvx_generated.cu", 4, texts, names) != 0) {
         k.log = "nvrtcCreateProgram failed";
         return false;
     }
@@ -1035,6 +1094,12 @@ bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* 
         p.out[e] = d.out[e].ptr;
         p.out_pitch[e] = d.out[e].pitch;
     }
+    int nres = 0;
+    for (int k = 0; k < d.n_stage; ++k)
+        if (op_is_global(d.st[k].op)) {
+            if (nres >= HVX_JIT_MAX_RES) return false;
+            p.res[nres++] = d.st[k].res;
+        }
     // interior tiles: every image's cells of the tile grown by its halo lie in
     // its valid region (external inputs: in the image; they are read as stored)
     const int tw = k->tw, th = k->th;

@@ -108,6 +108,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Exact point arithmetic (Magnitude, Phase, Harris and Shi-Tomasi responses):
 // a self-contained header that generated kernels include too.
 #include "point_math.cuh"
+#include "reduce_math.cuh"
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -67,6 +67,10 @@ const char* op_name(int kind) {
         case OP_NOT: return "not";
         case OP_TOMASI: return "tomasi_response";
         case OP_MULTIPLY: return "multiply";
+        case OP_MEANSTD: return "mean_stddev";
+        case OP_MINMAX: return "minmaxloc";
+        case OP_HIST: return "histogram";
+        case OP_EQHIST: return "equalize_hist";
     }
     return "?";
 }
@@ -85,6 +89,7 @@ const char* group_kernel_name(int gk) {
         case GK_HARRIS: return "fused_harris_tma";
         case GK_POINT: return "plain_point";
         case GK_CHX_UV: return "plain_channel_uv";
+        case GK_EQHIST: return "equalize_hist";
     }
     return "?";
 }
@@ -129,6 +134,10 @@ void lower(Graph* g, Plan& P) {
             case N_XOR: add(OP_XOR, 0, 0); break;
             case N_NOT: add(OP_NOT, 0, 0); break;
             case N_MULTIPLY: add(OP_MULTIPLY, 0, 0); break;
+            case N_MEANSTD: add(OP_MEANSTD, 0, 0); break;
+            case N_MINMAX: add(OP_MINMAX, 0, 0); break;
+            case N_HIST: add(OP_HIST, 0, 0); break;
+            case N_EQHIST: add(OP_EQHIST, 0, 0); break;
             case N_SOBEL:
                 if (!n->out[0] && !n->out[1]) fail(HVX_ERROR_INVALID_PARAMETERS);
                 if (n->out[0]) add(OP_SOBEL_X, 0, 1);
@@ -238,6 +247,10 @@ void infer(Op& op) {
             need(2, {HVX_DF_S32});
             of = HVX_DF_F32;
             break;
+        case OP_MEANSTD:
+        case OP_MINMAX: need(0, {HVX_DF_U8, HVX_DF_S16}); of = HVX_DF_RESULT; break;
+        case OP_HIST: need(0, {HVX_DF_U8}); of = HVX_DF_RESULT; break;
+        case OP_EQHIST: need(0, {HVX_DF_U8}); of = HVX_DF_U8; break;
         default: fail(HVX_ERROR_INVALID_PARAMETERS);
     }
     if (op.kind != OP_CHX)
@@ -245,7 +258,7 @@ void infer(Op& op) {
             if (in[i]->w != ow || in[i]->h != oh) fail(HVX_ERROR_INVALID_PARAMETERS);
     if (ow == 0 || oh == 0) fail(HVX_ERROR_INVALID_PARAMETERS);
     Image* o = op.out;
-    if (o->is_virtual) {
+    if (o->is_virtual || o->is_result) {
         if (o->user_fixed_size && (o->w != ow || o->h != oh)) fail(HVX_ERROR_INVALID_PARAMETERS);
         if (o->user_fmt != HVX_DF_VIRT && o->user_fmt != of) fail(HVX_ERROR_INVALID_FORMAT);
         o->w = ow;
@@ -326,6 +339,7 @@ struct Planner {
         std::unordered_map<int, int> h_out;  // op -> halo of its output
         for (auto it = ops.rbegin(); it != ops.rend(); ++it) {
             const Op& op = P.ops[*it];
+            if (op.out->is_result) continue;  // no pixels
             int h = 0;
             for (int j : ops) {
                 const Op& c = P.ops[j];
@@ -359,7 +373,11 @@ struct Planner {
         // alive ops outside the group
         std::set<int> members(ops.begin(), ops.end());
         int n_out = 0;
+        int n_global = 0;
+        for (int i : ops) n_global += op_is_global(P.ops[i].kind) ? 1 : 0;
+        if (n_global > HVX_JIT_MAX_RES) return false;
         for (Image* im : produced) {
+            if (im->is_result) continue;
             bool out = !im->is_virtual;
             for (int j : P.order)
                 if (!members.count(j))
@@ -401,7 +419,10 @@ struct Planner {
                 auto it = node_group.find(op.node);
                 if (it != node_group.end()) target = it->second;
             } else {
-                bool size_change = op.kind == OP_CHX && op.node->p.channel != HVX_CHANNEL_Y;
+                // ops that run alone: U/V extraction changes the size, and
+                // EqualizeHist needs its whole histogram before any output
+                bool size_change = (op.kind == OP_CHX && op.node->p.channel != HVX_CHANNEL_Y) ||
+                                   op.kind == OP_EQHIST;
                 // a MIRROR / REPEAT local op reads its inputs from memory, like
                 // external inputs, whoever produces them
                 const bool wraps = op_is_local(op.kind) && border_wraps(op.node->border);
@@ -410,7 +431,9 @@ struct Planner {
                     auto w = writer.find(op.in[k]);
                     if (w != writer.end()) prod_groups.insert(op_group[w->second]);
                 }
-                if (prod_groups.empty()) {
+                // a global operator on an external image runs on its own
+                // rather than joining a group that merely reads that image
+                if (prod_groups.empty() && !op_is_global(op.kind)) {
                     // only external inputs: join the group of a sibling op of the
                     // same node (the two Sobel derivatives), else the latest group
                     // that already reads one of these inputs, so the input is read
@@ -450,7 +473,8 @@ struct Planner {
                 P.groups[target].W = op.out->w;
                 P.groups[target].H = op.out->h;
                 P.groups[target].closed =
-                    op.kind == OP_CHX && op.node->p.channel != HVX_CHANNEL_Y;
+                    (op.kind == OP_CHX && op.node->p.channel != HVX_CHANNEL_Y) ||
+                    op.kind == OP_EQHIST;
                 node_group[op.node] = target;
             }
             P.groups[target].ops.push_back(i);
@@ -473,6 +497,7 @@ struct Planner {
             }
             for (int i : G.ops) {
                 Image* o = P.ops[i].out;
+                if (o->is_result) continue;
                 bool needed = !o->is_virtual;
                 for (int j : P.order)
                     if (op_group[j] != (int)gi)

@@ -82,7 +82,14 @@ struct Image {
     int node_refs = 0;
     // Set by verification: a virtual image whose values live only on chip.
     bool materialized = false;
+    // The result of a global operator (MeanStdDev, MinMaxLoc, Histogram): a
+    // non-virtual data vertex of the graph owned by it, with no pixels; dev
+    // holds the device result block.
+    bool is_result = false;
 };
+
+// Internal format of result images.
+constexpr int HVX_DF_RESULT = 100;
 
 const char* op_name(int kind);
 bool op_is_local(int kind);
@@ -109,6 +116,10 @@ enum NodeKind : int {
     N_XOR,
     N_NOT,
     N_MULTIPLY,
+    N_MEANSTD,
+    N_MINMAX,
+    N_HIST,
+    N_EQHIST,
 };
 
 struct NodeParams {
@@ -124,6 +135,7 @@ struct NodeParams {
     std::vector<int32_t> coeffs;
     float scale = 1.0f;        // Multiply
     int mul_rounding = HVX_ROUND_TO_ZERO;
+    int hist_bins = 256, hist_offset = 0, hist_range = 256;  // Histogram
 };
 
 struct Node {
@@ -136,6 +148,7 @@ struct Node {
     int border = HVX_BORDER_REPLICATE;
     int cval = 0;
     int rounding = HVX_ROUND_TO_ZERO;
+    void* d_aux = nullptr;  // EqualizeHist: its 256-bin device histogram
     // set by verification
     uint32_t live_mask = 0;
     int group = -1;
@@ -177,6 +190,14 @@ enum GroupKernel : int {
     GK_HARRIS,       // Sobel -> products -> window sums -> response -> threshold
     GK_POINT,        // plain point op
     GK_CHX_UV,       // ChannelExtract U/V (half width)
+    GK_EQHIST,       // EqualizeHist: histogram, then the mapping
+};
+
+// A device block set before a group's launch (global operators' results).
+struct ResultReset {
+    void* p;
+    int byte;
+    uint64_t n;
 };
 const char* group_kernel_name(int gk);
 
@@ -195,6 +216,8 @@ struct Group {
     PlainParams plain;           // for GK_POINT / GK_CHX_UV
     JitLaunch jit;               // GK_GENERIC with a generated kernel
     bool jit_on = false;
+    EqHistParams eqh;            // GK_EQHIST
+    std::vector<ResultReset> resets;
     uint64_t ext_bytes = 0;      // bytes of non-virtual images read + written
     uint64_t mem_bytes = 0;      // bytes of every image read + written
     bool closed = false;         // planning: no further op may join

@@ -7,6 +7,7 @@
 
 #define HVX_JIT_MAX_BUF 12
 #define HVX_JIT_MAX_EXT 6
+#define HVX_JIT_MAX_RES 4
 
 struct HvxJitParams {
     int W, H;                       // size of every image of the group
@@ -18,4 +19,5 @@ struct HvxJitParams {
     unsigned long long in_pitch[HVX_JIT_MAX_EXT];
     void* out[HVX_JIT_MAX_EXT];     // external outputs
     unsigned long long out_pitch[HVX_JIT_MAX_EXT];
+    void* res[HVX_JIT_MAX_RES];     // result blocks of the group's global operators
 };

@@ -34,7 +34,30 @@ enum OpKind : int {
     OP_NOT,
     OP_TOMASI,
     OP_MULTIPLY,
+    // global operators (Table 2 "reduce" / "histogram"): no image output
+    OP_MEANSTD,
+    OP_MINMAX,
+    OP_HIST,
+    // EqualizeHist (histogram + point): its own two launches
+    OP_EQHIST,
 };
+
+#ifdef __CUDACC__
+#define HVX_HD __host__ __device__
+#else
+#define HVX_HD
+#endif
+
+HVX_HD inline bool op_is_global(int kind) {
+    return kind == OP_MEANSTD || kind == OP_MINMAX || kind == OP_HIST;
+}
+
+// Bytes of a global operator's device result block, and the byte every
+// byte of it is set to before a launch.
+HVX_HD inline unsigned long long global_result_bytes(int kind, int bins) {
+    return kind == OP_MEANSTD ? 24ull : kind == OP_MINMAX ? 32ull : 4ull * (unsigned long long)bins;
+}
+HVX_HD inline int global_result_fill(int kind) { return kind == OP_MINMAX ? 0xFF : 0; }
 
 // ---------------------------------------------------------------------------
 // Generic staged tile executor (any fused group of point / local ops).
@@ -75,6 +98,7 @@ struct GenStage {
     int32_t coeff_off, shift;
     float f0, f1;      // F32 thresholds
     int64_t k0, k1;    // integer thresholds, or kn / kd of the Harris response
+    void* res;         // global operators: device result block (out is -1)
 };
 
 struct GenExt {
@@ -82,6 +106,18 @@ struct GenExt {
     uint64_t pitch;
     int32_t fmt;       // HVX_DF_*
     int32_t buf;
+};
+
+// EqualizeHist: histogram of the input's valid rectangle, then the mapping
+// through the normalised cumulative histogram.
+struct EqHistParams {
+    uint32_t W, H;
+    const uint8_t* in;
+    uint64_t in_pitch;
+    uint8_t* out;
+    uint64_t out_pitch;
+    uint32_t* hist;    // 256 bins, zeroed before the first launch
+    int32_t valid[4];  // the input's valid rectangle (= the output's)
 };
 
 struct GenericDesc {

@@ -103,7 +103,50 @@ __device__ __forceinline__ bool stage_cells(const GenBuf& ob, int32_t* out, int 
     return edge;
 }
 
+// A global operator over the tile's cells of its input that lie in the
+// image and in the input's valid rectangle: per-thread partial results,
+// combined per warp and added to the result block.
+__device__ void run_global(const GenericDesc& d, int32_t* s, const GenStage& st, int x0, int y0) {
+    const View a = view_of(d, s, st.in[0], 0);
+    const int32_t* vr = d.buf[st.in[0]].valid;
+    const int W = d.W;
+    long long s1 = 0;
+    unsigned long long s2 = 0;
+    unsigned n = 0;
+    HvxMinMaxAcc mm;
+    hvx_mm_init(mm);
+    uint32_t* bins = reinterpret_cast<uint32_t*>(s + st.i3);
+    for_cells(GEN_TW, GEN_TH, [&](int c, int r) {
+        const int x = x0 + c, y = y0 + r;
+        if (x >= W || y >= d.H || !in_rect(vr, x, y)) return;
+        const int v = a.p[r * a.w + c];
+        if (st.op == OP_MEANSTD) {
+            s1 += v;
+            s2 += (unsigned long long)((long long)v * v);
+            ++n;
+        } else if (st.op == OP_MINMAX) {
+            hvx_mm_add(mm, v, (unsigned)y * (unsigned)W + (unsigned)x);
+        } else if (v >= st.i1 && v < st.i1 + st.i2) {
+            atomicAdd(&bins[(v - st.i1) * st.i0 / st.i2], 1u);
+        }
+    });
+    if (st.op == OP_MEANSTD) {
+        hvx_ms_commit(st.res, s1, s2, n);
+    } else if (st.op == OP_MINMAX) {
+        hvx_mm_commit_warp(st.res, mm);
+    } else {
+        __syncthreads();
+        uint32_t* g = static_cast<uint32_t*>(st.res);
+        for (int i = threadIdx.x; i < st.i0; i += blockDim.x)
+            if (bins[i]) atomicAdd(&g[i], bins[i]);
+    }
+}
+
 __device__ bool run_stage(const GenericDesc& d, int32_t* s, const GenStage& st, int x0, int y0) {
+    if (op_is_global(st.op)) {
+        run_global(d, s, st, x0, y0);
+        return false;
+    }
     const GenBuf& ob = d.buf[st.out];
     int32_t* out = s + ob.smem_off;
     const int ox = x0 - ob.halo, oy = y0 - ob.halo;
@@ -209,6 +252,11 @@ __global__ void __launch_bounds__(GEN_THREADS) generic_kernel(const GenericDesc 
     extern __shared__ int32_t s[];
     const int x0 = blockIdx.x * GEN_TW, y0 = blockIdx.y * GEN_TH;
     const int W = d.W, H = d.H;
+
+    // the tile's histograms of global operators start empty
+    for (int k = 0; k < d.n_stage; ++k)
+        if (d.st[k].op == OP_HIST)
+            for (int i = threadIdx.x; i < d.st[k].i0; i += blockDim.x) s[d.st[k].i3 + i] = 0;
 
     // external inputs, border applied
     for (int e = 0; e < d.n_in; ++e) {

@@ -41,5 +41,6 @@ void harris_box(const HarrisParams& p, int* w, int* h);
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);
 cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);
 cudaError_t launch_plain(const PlainParams& p, cudaStream_t s);
+cudaError_t launch_eqhist(const EqHistParams& p, cudaStream_t s);
 
 }  // namespace hvx

@@ -387,6 +387,22 @@ hvx_status build_point(Plan& P, Group& G) {
     return op.out->dev ? HVX_SUCCESS : HVX_ERROR_INVALID_GRAPH;
 }
 
+hvx_status build_eqhist(Plan& P, Group& G) {
+    const Op& op = P.ops[G.ops[0]];
+    EqHistParams& q = G.eqh;
+    std::memset(&q, 0, sizeof(q));
+    q.W = op.out->w;
+    q.H = op.out->h;
+    q.in = static_cast<const uint8_t*>(op.in[0]->dev);
+    q.in_pitch = op.in[0]->pitch;
+    q.out = static_cast<uint8_t*>(op.out->dev);
+    q.out_pitch = op.out->pitch;
+    q.hist = static_cast<uint32_t*>(op.node->d_aux);
+    set_rect(q.valid, op.in[0]->valid);
+    if (op.out->ctx->plan_only) return HVX_SUCCESS;
+    return q.in && q.out && q.hist ? HVX_SUCCESS : HVX_ERROR_INVALID_GRAPH;
+}
+
 hvx_status build_generic(Plan& P, Group& G) {
     GenericDesc& d = G.gdesc;
     std::memset(&d, 0, sizeof(d));
@@ -413,7 +429,8 @@ hvx_status build_generic(Plan& P, Group& G) {
                 halo[c.in[k]] = std::max(halo[c.in[k]], h_out[j] + std::max(c.rx, c.ry));
     }
     std::vector<const Image*> images(G.inputs.begin(), G.inputs.end());
-    for (int i : G.ops) images.push_back(P.ops[i].out);
+    for (int i : G.ops)
+        if (!P.ops[i].out->is_result) images.push_back(P.ops[i].out);
     if ((int)images.size() > GEN_MAX_BUF || (int)G.ops.size() > GEN_MAX_STAGE ||
         (int)G.inputs.size() > GEN_MAX_EXT || (int)G.outputs.size() > GEN_MAX_EXT)
         return HVX_ERROR_NOT_SUPPORTED;
@@ -461,7 +478,8 @@ hvx_status build_generic(Plan& P, Group& G) {
         st.op = op.kind;
         st.in[0] = st.in[1] = st.in[2] = -1;
         for (int k = 0; k < op.n_in; ++k) st.in[k] = buf[op.in[k]];
-        st.out = buf[op.out];
+        st.out = op.out->is_result ? -1 : buf[op.out];
+        st.res = op.out->is_result ? op.out->dev : nullptr;
         st.rx = op.rx;
         st.ry = op.ry;
         st.rounding = op.node->rounding;
@@ -473,6 +491,16 @@ hvx_status build_generic(Plan& P, Group& G) {
             st.shift = op.node->p.shift;
             st.i0 = op.out->fmt;  // U8 or S16: the saturation range
             for (int32_t v : c) d.coeff[coeffs++] = v;
+        }
+        if (op.kind == OP_HIST) {
+            // bins, offset, range; shared-memory words of the tile's histogram
+            st.i0 = op.node->p.hist_bins;
+            st.i1 = op.node->p.hist_offset;
+            st.i2 = op.node->p.hist_range;
+            st.i3 = words;
+            words += (st.i0 + 3) & ~3;
+            d.smem_words = words;
+            if (words * 4 > 220 * 1024) return HVX_ERROR_NOT_SUPPORTED;
         }
     }
     for (const Image* im : G.inputs) {
@@ -523,9 +551,42 @@ hvx_status check_device_error(Context* ctx) {
     return HVX_ERROR_TIMEOUT;
 }
 
+// Device result blocks of global operators (kept with the result image for
+// the life of the graph) and EqualizeHist's histogram.
+hvx_status alloc_results(Plan& P, Context* ctx) {
+    for (int i : P.order) {
+        Op& op = P.ops[i];
+        if (op_is_global(op.kind)) {
+            const uint64_t n = global_result_bytes(op.kind, op.node->p.hist_bins);
+            if (op.out->dev && op.out->bytes != n) {
+                ctx->pool.free(op.out->dev);
+                op.out->dev = nullptr;
+            }
+            if (!op.out->dev) {
+                hvx_status st = ctx->pool.alloc(n, &op.out->dev);
+                if (st != HVX_SUCCESS) return st;
+                op.out->owns_mem = true;
+                op.out->bytes = n;
+                cudaMemset(op.out->dev, global_result_fill(op.kind), n);
+            }
+        }
+        if (op.kind == OP_EQHIST && !op.node->d_aux) {
+            if (cudaMalloc(&op.node->d_aux, 256 * sizeof(uint32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                return HVX_ERROR_NO_MEMORY;
+            }
+        }
+    }
+    return HVX_SUCCESS;
+}
+
 hvx_status prepare_launches(Graph* g) {
     Plan& P = g->plan;
     Context* ctx = g->ctx;
+    if (!ctx->plan_only) {
+        hvx_status st = alloc_results(P, ctx);
+        if (st != HVX_SUCCESS) return st;
+    }
     for (Group& G : P.groups) {
         G.ext_bytes = G.mem_bytes = 0;
         for (Image* im : G.inputs) {
@@ -540,14 +601,25 @@ hvx_status prepare_launches(Graph* g) {
         EdgeMatch em;
         HarrisMatch hm;
         const Op& first = P.ops[G.ops[0]];
-        if (G.ops.size() == 1 && first.kind == OP_GAUSS && !border_wraps(first.node->border)) {
+        G.resets.clear();
+        for (int i : G.ops) {
+            const Op& op = P.ops[i];
+            if (op_is_global(op.kind) && op.out->dev)
+                G.resets.push_back({op.out->dev, global_result_fill(op.kind), op.out->bytes});
+            if (op.kind == OP_EQHIST && op.node->d_aux)
+                G.resets.push_back({op.node->d_aux, 0, 256 * sizeof(uint32_t)});
+        }
+        if (G.ops.size() == 1 && first.kind == OP_EQHIST) {
+            G.kernel = GK_EQHIST;
+            st = build_eqhist(P, G);
+        } else if (G.ops.size() == 1 && first.kind == OP_GAUSS && !border_wraps(first.node->border)) {
             G.kernel = GK_GAUSS;
             st = build_gauss(P, G, ctx);
         } else if (G.ops.size() == 1 && first.kind == OP_CHX &&
                    first.node->p.channel != HVX_CHANNEL_Y) {
             G.kernel = GK_CHX_UV;
             st = build_point(P, G);
-        } else if (G.ops.size() == 1 && !op_is_local(first.kind)) {
+        } else if (G.ops.size() == 1 && !op_is_local(first.kind) && !op_is_global(first.kind)) {
             G.kernel = GK_POINT;
             st = build_point(P, G);
         } else if (match_edge(P, G, em)) {
@@ -580,7 +652,12 @@ hvx_status prepare_launches(Graph* g) {
 hvx_status launch_plan(Graph* g, cudaStream_t s) {
     for (Group& G : g->plan.groups) {
         cudaError_t e = cudaSuccess;
+        for (const ResultReset& r : G.resets) {
+            e = cudaMemsetAsync(r.p, r.byte, r.n, s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
         switch (G.kernel) {
+            case GK_EQHIST: e = launch_eqhist(G.eqh, s); break;
             case GK_GAUSS:
             case GK_EDGE: e = launch_edge(G.tmap, G.edge, s); break;
             case GK_HARRIS: e = launch_harris(G.tmap, G.harris, s); break;
@@ -853,6 +930,11 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
     }
     hit->last_use = ++bc->tick;
     if (hit->jk) {
+        for (int i = 0; i < n; ++i)
+            for (const ResultReset& rr : gs[i]->plan.groups[0].resets) {
+                cudaError_t e = cudaMemsetAsync(rr.p, rr.byte, rr.n, s);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
         const uint8_t* base = static_cast<const uint8_t*>(hit->dmem);
         return cuda_status(jit_launch_batch(
             hit->jk, reinterpret_cast<const HvxJitParams*>(base),

@@ -142,6 +142,11 @@ _SIGS = {
     "hvxSubtractNode": (P, [P, P, P, I32, P]),
     "hvxAbsDiffNode": (P, [P, P, P, P]),
     "hvxMultiplyNode": (P, [P, P, P, ctypes.c_float, I32, I32, P]),
+    "hvxMeanStdDevNode": (P, [P, P]),
+    "hvxMinMaxLocNode": (P, [P, P]),
+    "hvxHistogramNode": (P, [P, P, I32, I32, I32]),
+    "hvxEqualizeHistNode": (P, [P, P, P]),
+    "hvxGetNodeResult": (I32, [P, P, U64]),
     "hvxConvolveNode": (P, [P, P, ctypes.POINTER(I32), I32, I32, I32, P]),
     "hvxPointNode": (P, [P, I32, PP, I32, P, ctypes.POINTER(ctypes.c_double), I32]),
     "hvxLocalNode": (P, [P, I32, I32, I32, P, P]),
@@ -512,3 +517,46 @@ def hvxEdgeBatchNoAlloc(frames, border: int, threshold: int, stream: int = 0):
     arr = (hvx_edge_frame * len(frames))(*frames)
     _ck(lib().hvxEdgeBatchNoAlloc(ctypes.cast(arr, ctypes.c_void_p), len(frames), border,
                                   threshold, stream), "hvxEdgeBatchNoAlloc")
+
+
+# --- global operators ---------------------------------------------------------
+
+class HvxMeanStdDev(ctypes.Structure):
+    """hvx_mean_stddev of include/hvx.h."""
+    _fields_ = [("mean", ctypes.c_float), ("stddev", ctypes.c_float), ("sum", ctypes.c_int64),
+                ("sum_squares", ctypes.c_uint64), ("count", ctypes.c_uint64)]
+
+
+class HvxMinMaxLoc(ctypes.Structure):
+    """hvx_minmaxloc of include/hvx.h."""
+    _fields_ = [("min", ctypes.c_int32), ("max", ctypes.c_int32),
+                ("min_count", ctypes.c_uint64), ("max_count", ctypes.c_uint64),
+                ("min_x", ctypes.c_int32), ("min_y", ctypes.c_int32),
+                ("max_x", ctypes.c_int32), ("max_y", ctypes.c_int32)]
+
+
+def hvxMeanStdDevNode(g, i):
+    return _node(lib().hvxMeanStdDevNode(g, i), g, "hvxMeanStdDevNode")
+
+
+def hvxMinMaxLocNode(g, i):
+    return _node(lib().hvxMinMaxLocNode(g, i), g, "hvxMinMaxLocNode")
+
+
+def hvxHistogramNode(g, i, num_bins, offset, range_):
+    return _node(lib().hvxHistogramNode(g, i, num_bins, offset, range_), g, "hvxHistogramNode")
+
+
+def hvxEqualizeHistNode(g, i, o):
+    return _node(lib().hvxEqualizeHistNode(g, i, o), g, "hvxEqualizeHistNode")
+
+
+def hvxGetNodeResult(node, out):
+    """Copy a global operator's result into `out`: an HvxMeanStdDev, an
+    HvxMinMaxLoc, or a uint32 numpy array of the histogram's bins."""
+    if isinstance(out, ctypes.Structure):
+        _ck(lib().hvxGetNodeResult(node, ctypes.byref(out), ctypes.sizeof(out)),
+            "hvxGetNodeResult")
+    else:
+        _ck(lib().hvxGetNodeResult(node, out.ctypes.data, out.nbytes), "hvxGetNodeResult")
+    return out

@@ -394,3 +394,45 @@ def test_multiply_node_parameters(pctx):
     H.hvxMultiplyNode(g, a, b, 0.5, H.HVX_POLICY_WRAP, H.HVX_ROUND_TO_ZERO, out16)
     H.hvxVerifyGraph(g)
     assert PG.kernel_kinds(g) == ["plain_point"]
+
+
+def test_global_operator_plans(pctx):
+    src = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+    # alone on an external image: its own staged-tile launch
+    g = H.hvxCreateGraph(pctx)
+    H.hvxMeanStdDevNode(g, src)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["staged_tile"]
+    # fused as epilogues: one launch, no image written for them
+    g = H.hvxCreateGraph(pctx)
+    G, x, y, m = (H.hvxCreateVirtualImage(g) for _ in range(4))
+    H.hvxGaussian3x3Node(g, src, G)
+    H.hvxSobel3x3Node(g, G, x, y)
+    H.hvxMagnitudeNode(g, x, y, m)
+    mm = H.hvxMinMaxLocNode(g, m)
+    H.hvxHistogramNode(g, G, 8, 0, 256)
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_REQUIRE)
+    H.hvxVerifyGraph(g)
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES) == 1
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_INTERMEDIATE_BYTES) == 0
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 1
+    with pytest.raises(H.HvxError):  # no device: no results
+        H.hvxGetNodeResult(mm, H.HvxMinMaxLoc())
+    # EqualizeHist runs on its own after its input is in memory
+    out = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(pctx)
+    G = H.hvxCreateVirtualImage(g)
+    H.hvxGaussian3x3Node(g, src, G)
+    H.hvxEqualizeHistNode(g, G, out)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["gaussian3x3_tma", "equalize_hist"]
+    # parameter ranges
+    g = H.hvxCreateGraph(pctx)
+    for args in ((0, 0, 256), (257, 0, 256), (16, 200, 100), (16, -1, 10), (16, 0, 0)):
+        with pytest.raises(H.HvxError):
+            H.hvxHistogramNode(g, src, *args)
+    s16 = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxHistogramNode(g, s16, 16, 0, 256)
+    with pytest.raises(H.HvxError):  # histograms take U8 only
+        H.hvxVerifyGraph(g)
