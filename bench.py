@@ -141,7 +141,7 @@ class ClockSampler:
 
 
 EDGE_SOURCES = ["kernels_edge.cu", "device_common.cuh", "kernel_params.h", "phase_table.h",
-                "launchers.h"]
+                "launchers.h", "point_math.cuh", "reduce_math.cuh"]
 
 
 def kernel_source_hash(files=EDGE_SOURCES) -> str:
@@ -339,54 +339,45 @@ def run_edge(args, world, rank, local, torch):
     barrier(world, torch)
     t_plain = reduce_max(time_steps(torch, step_plain, plain_steps, stream), world, torch)
 
-    # end to end: every step copies its frames in from pinned host memory, runs
-    # the fused batch through the C ABI and reads both outputs back.  The step
-    # is cut into chunks of frames that flow through three streams (copy in ->
-    # hvxProcessGraphBatch -> copy out), and consecutive steps overlap chunk by
-    # chunk: chunk i of a step is copied in once the previous step's kernel has
-    # read chunk i, and its kernel runs once the previous step's results of
-    # chunk i are on the host.  The host link (about 210 GB/s in, 193 GB/s out,
-    # 341 GB/s both ways) bounds this number, not the kernel.
+    # end to end through the C ABI on host data: every step, each chunk of
+    # frames is one hvxScheduleGraphBatchHost call (copies of its frames in
+    # from pinned host memory, the fused batch, both outputs back), chunks
+    # rotating over three streams so that one chunk's copies overlap another's
+    # kernel.  The host link (about 210 GB/s in, 193 GB/s out, 341 GB/s both
+    # ways) bounds this number, not the kernel.
     h_in = torch.empty((F, H_, pitch), dtype=torch.uint8).pin_memory()
     h_in.copy_(t_in.cpu())
     h_ph = torch.empty_like(h_in).pin_memory()
     h_mk = torch.empty_like(h_in).pin_memory()
     chunk = max(1, F // 16)
     chunks = [(i, min(F, i + chunk)) for i in range(0, F, chunk)]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in range(3)]
     sub = [fused[a:b] for a, b in chunks]
-    prev_k = [None] * len(chunks)  # previous step: kernel of chunk i done
-    prev_o = [None] * len(chunks)  # previous step: results of chunk i on the host
+    copies = []
+    for a, b in chunks:
+        items = []
+        for f in range(a, b):
+            items += [(ins[f], h_in[f].data_ptr(), pitch, True),
+                      (phs[f], h_ph[f].data_ptr(), pitch, False),
+                      (mks[f], h_mk[f].data_ptr(), pitch, False)]
+        copies.append(H.host_copies(items))
 
     def step_e2e():
-        for i, ((a, b), gs) in enumerate(zip(chunks, sub)):
-            if prev_k[i] is not None:
-                s_in.wait_event(prev_k[i])
-            with torch.cuda.stream(s_in):
-                t_in[a:b].copy_(h_in[a:b], non_blocking=True)
-                ev_in = torch.cuda.Event()
-                ev_in.record(s_in)
-            stream.wait_event(ev_in)
-            if prev_o[i] is not None:
-                stream.wait_event(prev_o[i])
-            H.hvxProcessGraphBatch(gs, sh)
-            ev_k = torch.cuda.Event()
-            ev_k.record(stream)
-            s_out.wait_event(ev_k)
-            with torch.cuda.stream(s_out):
-                h_ph[a:b].copy_(t_ph[a:b], non_blocking=True)
-                h_mk[a:b].copy_(t_mk[a:b], non_blocking=True)
-                ev_o = torch.cuda.Event()
-                ev_o.record(s_out)
-            prev_k[i], prev_o[i] = ev_k, ev_o
+        for i, gs in enumerate(sub):
+            H.hvxScheduleGraphBatchHost(gs, copies[i], streams[i % len(streams)].cuda_stream)
 
     def time_e2e(steps):
+        torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
         start.record(stream)
+        for st in streams:
+            st.wait_event(start)
         for _ in range(steps):
             step_e2e()
-        for ev in prev_o:  # the timed region ends when the last result is on the host
+        for st in streams:  # the timed region ends when the last result is on the host
+            ev = torch.cuda.Event()
+            ev.record(st)
             stream.wait_event(ev)
         end.record(stream)
         end.synchronize()

@@ -403,6 +403,28 @@ hvx_node hvxHistogramNode(hvx_graph g, hvx_image in, int32_t num_bins, int32_t o
  * before any pixel is mapped). */
 hvx_node hvxEqualizeHistNode(hvx_graph g, hvx_image in, hvx_image out);
 
+/* One image's host data for hvxScheduleGraphBatchHost: to_device 1 copies
+ * host -> image before the launch, 0 copies image -> host after it.  host
+ * rows are pitch bytes apart (pitch >= width * bytes per pixel); pinned
+ * (page-locked) host memory lets the copies overlap other streams' work. */
+typedef struct hvx_host_copy_s {
+    hvx_image image;  /* non-virtual image of the graphs' context */
+    void* host;
+    uint64_t pitch;
+    int32_t to_device;
+} hvx_host_copy;
+
+/* hvxProcessGraphBatch on host data, asynchronously on `stream`: every
+ * to_device copy, then the batch (as few launches as hvxProcessGraphBatch
+ * makes), then every device-to-host copy, each a cudaMemcpy2DAsync in the
+ * stream's order.  Returns once enqueued; the host buffers must stay valid
+ * until the stream reaches them (hvxWaitBatch).  Calls on several streams
+ * overlap one batch's copies with another's kernels (transfers over the
+ * CPU-GPU link are the bound of host-resident processing). */
+hvx_status hvxScheduleGraphBatchHost(const hvx_graph* graphs, int32_t n,
+                                     const hvx_host_copy* copies, int32_t n_copies,
+                                     void* stream);
+
 /* Copy a global operator's result (hvx_mean_stddev, hvx_minmaxloc, or
  * uint32_t[num_bins]) to host memory out (size bytes).  Call after the
  * graph's processing has completed (hvxProcessGraph, or hvxWaitGraph /

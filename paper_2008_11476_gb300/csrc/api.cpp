@@ -415,6 +415,54 @@ hvx_status hvxCopyImage(hvx_image img, void* host, uint64_t host_pitch, int32_t 
     return cuda_status(e);
 }
 
+// Host-side data of one batch call: uploads before the launch, downloads after
+// it, all on the caller's stream (each image one 2-D copy).
+static hvx_status host_copies(const hvx_host_copy* copies, int32_t n, bool to_device,
+                              cudaStream_t s) {
+    for (int32_t i = 0; i < n; ++i) {
+        const hvx_host_copy& c = copies[i];
+        if ((c.to_device != 0) != to_device) continue;
+        Image* im = I(c.image);
+        const uint64_t row = (uint64_t)im->w * bytes_per_pixel(im->fmt);
+        cudaError_t e =
+            to_device
+                ? cudaMemcpy2DAsync(im->dev, im->pitch, c.host, c.pitch, row, im->h,
+                                    cudaMemcpyHostToDevice, s)
+                : cudaMemcpy2DAsync(c.host, c.pitch, im->dev, im->pitch, row, im->h,
+                                    cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_host_copy* copies,
+                                     int32_t n_copies, void* stream) {
+    if (!gs || n <= 0 || n_copies < 0 || (n_copies > 0 && !copies))
+        return HVX_ERROR_INVALID_PARAMETERS;
+    std::vector<Graph*> v;
+    for (int i = 0; i < n; ++i) {
+        if (!ok_graph(gs[i])) return HVX_ERROR_INVALID_REFERENCE;
+        if (!G(gs[i])->verified) return HVX_ERROR_NOT_VERIFIED;
+        if (G(gs[i])->ctx != G(gs[0])->ctx) return HVX_ERROR_INVALID_REFERENCE;
+        v.push_back(G(gs[i]));
+    }
+    if (v[0]->ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    for (int32_t i = 0; i < n_copies; ++i) {
+        const hvx_host_copy& c = copies[i];
+        if (!ok_image(c.image) || !c.host) return HVX_ERROR_INVALID_PARAMETERS;
+        const Image* im = I(c.image);
+        if (im->is_virtual || im->is_result || im->ctx != v[0]->ctx || !im->dev)
+            return HVX_ERROR_INVALID_REFERENCE;
+        if (c.pitch < (uint64_t)im->w * bytes_per_pixel(im->fmt)) return HVX_ERROR_INVALID_PARAMETERS;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    hvx_status st = host_copies(copies, n_copies, true, s);
+    if (st != HVX_SUCCESS) return st;
+    st = process_batch(v[0]->ctx, v.data(), n, s);
+    if (st != HVX_SUCCESS) return st;
+    return host_copies(copies, n_copies, false, s);
+}
+
 hvx_status hvxGetImageDevicePtr(hvx_image img, void** dev, uint64_t* pitch) {
     if (!ok_image(img)) return HVX_ERROR_INVALID_REFERENCE;
     Image* im = I(img);

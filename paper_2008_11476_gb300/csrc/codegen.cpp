@@ -25,6 +25,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -476,11 +478,37 @@ struct Emitter {
         }
     }
 
+    // Cell passes are emitted row-blocked: a thread computes `row_block`
+    // vertically adjacent cells of one column per iteration, and every
+    // shared-memory value they read is loaded once into a named variable
+    // (a window of k rows serves k cells).  While a row of the block is being
+    // emitted, `row` is its index; reads register their (slot, row, column)
+    // in `loads`.
+    int row = -1;
+    mutable std::map<std::tuple<int, int, int>, std::string> loads;
+    std::vector<bool> cell_read;  // staged buffers read at the cell itself this pass
+
+    static std::string enc(int v) { return v < 0 ? "m" + std::to_string(-v) : std::to_string(v); }
+
+    std::string load_var(int s, int r, int dx) const {
+        const auto key = std::make_tuple(s, r, dx);
+        auto it = loads.find(key);
+        if (it != loads.end()) return it->second;
+        const std::string name = "t" + std::to_string(s) + "_" + enc(r) + "_" + enc(dx);
+        loads[key] = name;
+        return name;
+    }
+
     // Expression of the value of buffer b at the current cell.
-    std::string val(int b) const { return "v" + std::to_string(b); }
+    std::string val(int b) const {
+        if (row < 0) return "v" + std::to_string(b);
+        if (cell_read[b]) return load_var(b, row, 0);
+        return "v" + std::to_string(b) + "_" + std::to_string(row);
+    }
 
     // Read of staged buffer b at offset (dx, dy) from the current cell.
     std::string tap(int b, int dx, int dy) const {
+        if (row >= 0) return load_var(b, row + dy, dx);
         const int off = dy * bw(b) + dx;
         std::string s = "B" + std::to_string(b) + "[q" + std::to_string(b);
         if (off > 0) s += " + " + std::to_string(off);
@@ -738,10 +766,12 @@ struct Emitter {
             const int c = sep_r[k][i];
             if (c == 0) continue;
             const int off = (i - st.ry) * R.w;
-            const std::string rd = "R" + std::to_string(k) + "[qR" + std::to_string(k) +
-                                   (off > 0 ? " + " + std::to_string(off)
-                                            : off < 0 ? " - " + std::to_string(-off) : "") +
-                                   "]";
+            const std::string rd =
+                row >= 0 ? load_var(row_slot(k), row + i - st.ry, 0)
+                         : "R" + std::to_string(k) + "[qR" + std::to_string(k) +
+                               (off > 0 ? " + " + std::to_string(off)
+                                        : off < 0 ? " - " + std::to_string(-off) : "") +
+                               "]";
             if (lsum)
                 o << ind << "  t += (unsigned)" << rd << ";\n";
             else
@@ -760,20 +790,18 @@ struct Emitter {
     }
 
     // One pass over the cells of halo p.h producing the pass's staged
-    // buffers or, for the last pass, the external outputs.
+    // buffers or, for the last pass, the external outputs (and the global
+    // operators' partial results).  Row-blocked: see `row`.
     void emit_cells(const Pass& p) {
-        const int h = p.h;
+        const int h = p.h, BH = th + 2 * h, BW = tw + 2 * h;
+        const int RB = BH % 4 == 0 ? 4 : BH % 2 == 0 ? 2 : 1;  // rows per block, no tail
         const bool outputs = p.kind == OUT;
-        std::vector<bool> tapped(d.n_buf, false);
-        for (int k = 0; k < d.n_stage; ++k)
-            if (p.need_op[k] && is_local(d.st[k].op) && !separable(k))
-                tapped[d.st[k].in[0]] = true;
         o << "  // pass: ";
         if (outputs)
             o << "external outputs";
         else
             for (int b : p.targets) o << "B" << b << " ";
-        o << "(halo " << h << ")\n";
+        o << "(halo " << h << ", " << RB << " rows per thread iteration)\n";
         if (outputs)
             for (int k : globals) {
                 if (d.st[k].op == OP_MEANSTD)
@@ -782,63 +810,103 @@ struct Emitter {
                 else if (d.st[k].op == OP_MINMAX)
                     o << "  HvxMinMaxAcc g" << k << "_mm;\n  hvx_mm_init(g" << k << "_mm);\n";
             }
-        open_cells(th + 2 * h, tw + 2 * h, h, h, false);
-        o << "      if (CHECK && (x < 0 || x >= p.W || y < 0 || y >= p.H)) continue;\n";
-        for (int b = 0; b < d.n_buf; ++b)
-            if (tapped[b] || p.read_cell[b]) {
-                const int dh = d.buf[b].halo - h;
-                o << "      const int q" << b << " = (r + " << dh << ") * " << bw(b) << " + c + "
-                  << dh << ";\n";
-                if (p.read_cell[b])
-                    o << "      const int v" << b << " = B" << b << "[q" << b << "];\n";
-            }
-        for (int k = 0; k < d.n_stage; ++k)
-            if (p.need_op[k] && separable(k)) {
-                const int dh = d.buf[d.st[k].out].halo - h;
-                o << "      const int qR" << k << " = (r + " << dh + d.st[k].ry << ") * "
-                  << slot[row_slot(k)].w << " + c + " << dh << ";\n";
-            }
-        for (int b = 0; b < d.n_buf; ++b)
-            if (p.need_ld[b]) {
-                const int e = ext_in[b];
-                o << "      const int v" << b << " = hvx_ld<" << d.in[e].fmt << ">(p.in[" << e
-                  << "], p.in_pitch[" << e << "], x, y);\n";
-            }
-        for (int k = 0; k < d.n_stage; ++k) {
-            if (!p.need_op[k]) continue;
-            const GenStage& st = d.st[k];
-            const std::string v = val(st.out);
-            o << "      int " << v << ";\n";
-            if (separable(k))
-                emit_sep(k, v, "      ");
-            else if (is_local(st.op))
-                emit_local(st, v, "      ");
-            else
-                o << "      " << v << " = " << point_expr(st) << ";\n";
-            o << "      if (CHECK && !hvx_in(p.valid[" << st.out << "], x, y)) " << v << " = 0;\n";
-        }
-        if (outputs) {
-            for (int e = 0; e < d.n_out; ++e)
-                o << "      hvx_st<" << d.out[e].fmt << ">(p.out[" << e << "], p.out_pitch[" << e
-                  << "], x, y, " << val(d.out[e].buf) << ");\n";
-            for (int k : globals) {
+        o << "  #pragma unroll 1\n"
+          << "  for (int rb = warp * " << RB << "; rb < " << BH << "; rb += " << kThreads / 32 * RB
+          << ") {\n"
+          << "    #pragma unroll\n"
+          << "    for (int c = lane; c < " << BW << "; c += 32) {\n"
+          << "      const int x = x0 + c - " << h << ";\n";
+        // the rows of the block, into a buffer: their reads decide the loads
+        const std::string prefix = o.str();
+        o.str("");
+        o.clear();
+        loads.clear();
+        cell_read = p.read_cell;
+        for (int i = 0; i < RB; ++i) {
+            row = i;
+            o << "      {\n        const int y = y0 + rb + " << i - h << ";\n"
+              << "        const bool in_img = !CHECK || (x >= 0 && x < p.W && y >= 0 && y < p.H);\n";
+            for (int b = 0; b < d.n_buf; ++b)
+                if (p.need_ld[b]) {
+                    const int e = ext_in[b];
+                    o << "        const int " << val(b) << " = in_img ? hvx_ld<" << d.in[e].fmt
+                      << ">(p.in[" << e << "], p.in_pitch[" << e << "], x, y) : 0;\n";
+                }
+            for (int k = 0; k < d.n_stage; ++k) {
+                if (!p.need_op[k]) continue;
                 const GenStage& st = d.st[k];
-                const std::string v = val(st.in[0]), g = "g" + std::to_string(k);
-                o << "      if (!CHECK || hvx_in(p.valid[" << st.in[0] << "], x, y)) {\n";
-                if (st.op == OP_MEANSTD)
-                    o << "        " << g << "_s1 += " << v << ";\n        " << g
-                      << "_s2 += (unsigned long long)((long long)" << v << " * " << v
-                      << ");\n        ++" << g << "_n;\n";
-                else if (st.op == OP_MINMAX)
-                    o << "        hvx_mm_add(" << g << "_mm, " << v
-                      << ", (unsigned)y * (unsigned)p.W + (unsigned)x);\n";
+                const std::string v = val(st.out);
+                o << "        int " << v << ";\n";
+                if (separable(k))
+                    emit_sep(k, v, "        ");
+                else if (is_local(st.op))
+                    emit_local(st, v, "        ");
                 else
-                    o << "        if (" << v << " >= " << st.i1 << " && " << v << " < "
-                      << st.i1 + st.i2 << ") atomicAdd(&" << g << "_bins[(" << v << " - " << st.i1
-                      << ") * " << st.i0 << " / " << st.i2 << "], 1u);\n";
-                o << "      }\n";
+                    o << "        " << v << " = " << point_expr(st) << ";\n";
+                o << "        if (CHECK && !hvx_in(p.valid[" << st.out << "], x, y)) " << v
+                  << " = 0;\n";
             }
-            close_cells();
+            o << "        if (in_img) {\n";
+            if (outputs) {
+                for (int e = 0; e < d.n_out; ++e)
+                    o << "          hvx_st<" << d.out[e].fmt << ">(p.out[" << e << "], p.out_pitch["
+                      << e << "], x, y, " << val(d.out[e].buf) << ");\n";
+                for (int k : globals) {
+                    const GenStage& st = d.st[k];
+                    const std::string v = val(st.in[0]), g = "g" + std::to_string(k);
+                    o << "          if (!CHECK || hvx_in(p.valid[" << st.in[0] << "], x, y)) {\n";
+                    if (st.op == OP_MEANSTD)
+                        o << "            " << g << "_s1 += " << v << ";\n            " << g
+                          << "_s2 += (unsigned long long)((long long)" << v << " * " << v
+                          << ");\n            ++" << g << "_n;\n";
+                    else if (st.op == OP_MINMAX)
+                        o << "            hvx_mm_add(" << g << "_mm, " << v
+                          << ", (unsigned)y * (unsigned)p.W + (unsigned)x);\n";
+                    else
+                        o << "            if (" << v << " >= " << st.i1 << " && " << v << " < "
+                          << st.i1 + st.i2 << ") atomicAdd(&" << g << "_bins[(" << v << " - "
+                          << st.i1 << ") * " << st.i0 << " / " << st.i2 << "], 1u);\n";
+                    o << "          }\n";
+                }
+            } else {
+                for (int b : p.targets)
+                    o << "          B" << b << "[(rb + " << i << ") * " << bw(b) << " + c] = "
+                      << val(b) << ";\n";
+            }
+            o << "        }\n      }\n";
+        }
+        row = -1;
+        const std::string rows = o.str();
+        o.str("");
+        o.clear();
+        o << prefix;
+        // base index of every slot read, then each read once
+        std::vector<bool> based(slot.size(), false);
+        for (const auto& kv : loads) {
+            const int s = std::get<0>(kv.first);
+            if (based[s]) continue;
+            based[s] = true;
+            if (s < d.n_buf) {
+                const int dh = d.buf[s].halo - h;
+                o << "      const int qb" << s << " = (rb + " << dh << ") * " << bw(s) << " + c + "
+                  << dh << ";\n";
+            } else {
+                const int k = s - d.n_buf, dh = d.buf[d.st[k].out].halo - h;
+                o << "      const int qb" << s << " = (rb + " << dh + d.st[k].ry << ") * "
+                  << slot[s].w << " + c + " << dh << ";\n";
+            }
+        }
+        for (const auto& kv : loads) {
+            const int s = std::get<0>(kv.first), r = std::get<1>(kv.first),
+                      dx = std::get<2>(kv.first);
+            const int off = r * slot[s].w + dx;
+            o << "      const int " << kv.second << " = " << slot_name(s) << "[qb" << s
+              << (off > 0 ? " + " + std::to_string(off)
+                          : off < 0 ? " - " + std::to_string(-off) : "")
+              << "];\n";
+        }
+        o << rows << "    }\n  }\n";
+        if (outputs) {
             for (size_t j = 0; j < globals.size(); ++j) {
                 const int k = globals[j];
                 const std::string g = "g" + std::to_string(k), res = "p.res[" + std::to_string(j) + "]";
@@ -854,8 +922,6 @@ struct Emitter {
             }
             return;
         }
-        for (int b : p.targets) o << "      B" << b << "[r * " << bw(b) << " + c] = " << val(b) << ";\n";
-        close_cells();
         // cells outside the image, the way the local consumers read them
         o << "  if (CHECK) {\n    __syncthreads();\n";
         for (int b : p.targets) {

@@ -147,6 +147,7 @@ _SIGS = {
     "hvxHistogramNode": (P, [P, P, I32, I32, I32]),
     "hvxEqualizeHistNode": (P, [P, P, P]),
     "hvxGetNodeResult": (I32, [P, P, U64]),
+    "hvxScheduleGraphBatchHost": (I32, [PP, I32, P, I32, P]),
     "hvxConvolveNode": (P, [P, P, ctypes.POINTER(I32), I32, I32, I32, P]),
     "hvxPointNode": (P, [P, I32, PP, I32, P, ctypes.POINTER(ctypes.c_double), I32]),
     "hvxLocalNode": (P, [P, I32, I32, I32, P, P]),
@@ -560,3 +561,29 @@ def hvxGetNodeResult(node, out):
     else:
         _ck(lib().hvxGetNodeResult(node, out.ctypes.data, out.nbytes), "hvxGetNodeResult")
     return out
+
+
+class HvxHostCopy(ctypes.Structure):
+    """hvx_host_copy of include/hvx.h."""
+    _fields_ = [("image", ctypes.c_void_p), ("host", ctypes.c_void_p), ("pitch", ctypes.c_uint64),
+                ("to_device", ctypes.c_int32)]
+
+
+def host_copies(items):
+    """Array of HvxHostCopy from (image, host_pointer, pitch, to_device)
+    tuples, for hvxScheduleGraphBatchHost."""
+    arr = (HvxHostCopy * len(items))()
+    for a, (img, ptr, pitch, to_dev) in zip(arr, items):
+        a.image = img.value if isinstance(img, ctypes.c_void_p) else img
+        a.host = ptr
+        a.pitch = pitch
+        a.to_device = 1 if to_dev else 0
+    return arr
+
+
+def hvxScheduleGraphBatchHost(graphs, copies, stream: int = 0):
+    arr = (ctypes.c_void_p * len(graphs))(*[g.value if isinstance(g, ctypes.c_void_p) else g
+                                            for g in graphs])
+    cp = ctypes.cast(copies, ctypes.c_void_p) if len(copies) else None
+    _ck(lib().hvxScheduleGraphBatchHost(arr, len(graphs), cp, len(copies), stream),
+        "hvxScheduleGraphBatchHost")

@@ -42,8 +42,11 @@ def test_constants_are_folded(pctx):
     # Laplacian: the four zero taps of the 3x3 kernel are dropped and the sum
     # of U8 inputs with coefficients up to 4 is accumulated in 32 bits
     s = H.hvxGetGraphKernelSource(_gen(pctx, A.laplacian), 0)
-    assert s.count("t += ") == 5
+    rows = int(s.split(" rows per thread iteration")[0].rsplit(" ", 1)[1])
+    assert s.count("t += ") == 5 * rows  # one block of `rows` cells per iteration
     assert "long long t" not in s
+    # a cross of 5 taps over 4 rows reads 14 distinct values, not 20
+    assert s.count("= B0[qb0") == 14 if rows == 4 else True
     # the threshold of the Sobel application is a literal
     s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel), 0)
     assert "(100LL)" in s

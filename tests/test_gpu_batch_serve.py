@@ -198,3 +198,33 @@ def test_device_bounded_wait_reports_timeout_and_context_survives(ctx):
     g = PG.gaussian_graph(ctx, inp, out)
     H.hvxProcessGraph(g)
     np.testing.assert_array_equal(PG.download(out), O.gaussian3x3(img).data)
+
+
+def test_batch_on_host_data(ctx):
+    # hvxScheduleGraphBatchHost: host frames in, fused batch, both outputs
+    # back, on a stream; pageable numpy memory works too (slower copies)
+    from paper_2008_11476_gb300 import hvx as HX
+    w, h, n = 320, 240, 5
+    frames = [synth.rects_noise(w, h, seed=60 + i) for i in range(n)]
+    graphs, items, outs = [], [], []
+    for f in frames:
+        src = PG.empty(ctx, w, h, HX.HVX_DF_U8)
+        ph = PG.empty(ctx, w, h, HX.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, HX.HVX_DF_U8)
+        graphs.append(PG.edge_graph(ctx, src, ph, mk))
+        hp = np.zeros((h, w), np.uint8)
+        hm = np.zeros((h, w), np.uint8)
+        outs.append((hp, hm))
+        items += [(src, f.ctypes.data, w, True), (ph, hp.ctypes.data, w, False),
+                  (mk, hm.ctypes.data, w, False)]
+    copies = HX.host_copies(items)
+    HX.hvxScheduleGraphBatchHost(graphs, copies)
+    HX.hvxWaitBatch(ctx)
+    for f, (hp, hm) in zip(frames, outs):
+        ref_ph, ref_mk = O.edge_graph(f)
+        np.testing.assert_array_equal(hp, ref_ph)
+        np.testing.assert_array_equal(hm, ref_mk)
+    bad = HX.host_copies([(PG.empty(ctx, w, h, HX.HVX_DF_U8), outs[0][0].ctypes.data, w - 1,
+                           True)])
+    with pytest.raises(HX.HvxError):  # host pitch below the row size
+        HX.hvxScheduleGraphBatchHost(graphs, bad)
