@@ -1052,6 +1052,7 @@ std::unordered_map<std::string, std::unique_ptr<JitKernel>>& cache() {
 }
 
 bool compile(JitKernel& k) {
+    NvtxRange nvtx("hvx codegen compile");
     Nvrtc& n = nvrtc();
     if (!n.ok) {
         k.log = n.why;

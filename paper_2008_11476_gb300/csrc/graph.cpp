@@ -553,6 +553,7 @@ void release_plan(Graph* g) {
 }
 
 hvx_status verify_graph(Graph* g) {
+    NvtxRange nvtx("hvx verify");
     release_plan(g);
     Plan& P = g->plan;
     try {

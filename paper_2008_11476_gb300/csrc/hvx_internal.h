@@ -16,6 +16,8 @@
 #include <vector>
 
 #include "../../include/hvx.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "jit_params.h"
 #include "kernel_params.h"
 
@@ -166,6 +168,16 @@ struct Op {
     int rx = 0, ry = 0;  // window radius (local ops)
     bool alive = false;
     int group = -1;
+};
+
+// NVTX range for profilers (nsys / ncu timelines): verification, code
+// generation, launches, batches and server dispatch are marked; without a
+// profiler attached the calls cost a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // MIRROR / REPEAT read arbitrary pixels of a local operator's input: such an

@@ -651,6 +651,7 @@ hvx_status prepare_launches(Graph* g) {
 
 hvx_status launch_plan(Graph* g, cudaStream_t s) {
     for (Group& G : g->plan.groups) {
+        NvtxRange nvtx(G.jit_on ? "hvx launch generated" : group_kernel_name(G.kernel));
         cudaError_t e = cudaSuccess;
         for (const ResultReset& r : G.resets) {
             e = cudaMemsetAsync(r.p, r.byte, r.n, s);
@@ -867,6 +868,7 @@ hvx_status build_jit_batch_entry(Graph* const* gs, int n, JitKernel* jk, BatchEn
 }
 
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
+    NvtxRange nvtx("hvx batch");
     // one launch when every plan is a single group running the same
     // generated kernel
     JitKernel* jk = nullptr;

@@ -114,6 +114,7 @@ void Server::run() {
             }
             r->ev = event_pool.back();
             event_pool.pop_back();
+            NvtxRange nvtx("hvx serve dispatch");
             hvx_status st = launch_plan(r->g, s);
             if (st == HVX_SUCCESS && cudaEventRecord(r->ev, s) != cudaSuccess) st = HVX_ERROR_DEVICE;
             if (st != HVX_SUCCESS) {
