@@ -279,7 +279,11 @@ hvx_status hvxSetGraphFusion(hvx_graph g, int32_t enable);
  * NVRTC for sm_103a and loaded; kernels are cached by source text for the life
  * of the process, so graphs of the same shape compile once.  Generated
  * kernels give the same results as the interpreter, cell for cell.  mode is
- * HVX_CODEGEN_*; marks the graph unverified. */
+ * HVX_CODEGEN_*; marks the graph unverified.  HVX_CODEGEN_ROWS=1, 2 or 4 in
+ * the environment overrides how many vertically adjacent cells a thread
+ * computes per iteration of a generated pass (a tuning knob; results are
+ * the same); HVX_CODEGEN_VERBOSE=1 prints why a group got no generated
+ * kernel. */
 hvx_status hvxSetGraphCodegen(hvx_graph g, int32_t mode);
 
 /* Source text of the kernel generated for launch `group` of a verified graph

@@ -416,20 +416,39 @@ hvx_status hvxCopyImage(hvx_image img, void* host, uint64_t host_pitch, int32_t 
 }
 
 // Host-side data of one batch call: uploads before the launch, downloads after
-// it, all on the caller's stream (each image one 2-D copy).
+// it, all on the caller's stream.  Consecutive copies whose images follow one
+// another in device memory and whose host buffers follow one another too (same
+// row size and pitches, e.g. frames of one tensor) are merged into one 2-D
+// copy of all their rows.
 static hvx_status host_copies(const hvx_host_copy* copies, int32_t n, bool to_device,
                               cudaStream_t s) {
+    struct Run {
+        char* dev;
+        char* host;
+        uint64_t dpitch, hpitch, row, rows;
+    };
+    std::vector<Run> runs;
     for (int32_t i = 0; i < n; ++i) {
         const hvx_host_copy& c = copies[i];
         if ((c.to_device != 0) != to_device) continue;
-        Image* im = I(c.image);
-        const uint64_t row = (uint64_t)im->w * bytes_per_pixel(im->fmt);
-        cudaError_t e =
-            to_device
-                ? cudaMemcpy2DAsync(im->dev, im->pitch, c.host, c.pitch, row, im->h,
-                                    cudaMemcpyHostToDevice, s)
-                : cudaMemcpy2DAsync(c.host, c.pitch, im->dev, im->pitch, row, im->h,
-                                    cudaMemcpyDeviceToHost, s);
+        const Image* im = I(c.image);
+        Run r{static_cast<char*>(im->dev), static_cast<char*>(c.host), im->pitch, c.pitch,
+              (uint64_t)im->w * bytes_per_pixel(im->fmt), im->h};
+        if (!runs.empty()) {
+            Run& b = runs.back();
+            if (b.dpitch == r.dpitch && b.hpitch == r.hpitch && b.row == r.row &&
+                b.dev + b.rows * b.dpitch == r.dev && b.host + b.rows * b.hpitch == r.host) {
+                b.rows += r.rows;
+                continue;
+            }
+        }
+        runs.push_back(r);
+    }
+    for (const Run& r : runs) {
+        cudaError_t e = to_device ? cudaMemcpy2DAsync(r.dev, r.dpitch, r.host, r.hpitch, r.row,
+                                                      r.rows, cudaMemcpyHostToDevice, s)
+                                  : cudaMemcpy2DAsync(r.host, r.hpitch, r.dev, r.dpitch, r.row,
+                                                      r.rows, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return HVX_SUCCESS;

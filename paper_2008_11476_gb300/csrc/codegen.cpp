@@ -24,6 +24,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -794,7 +795,15 @@ struct Emitter {
     // operators' partial results).  Row-blocked: see `row`.
     void emit_cells(const Pass& p) {
         const int h = p.h, BH = th + 2 * h, BW = tw + 2 * h;
-        const int RB = BH % 4 == 0 ? 4 : BH % 2 == 0 ? 2 : 1;  // rows per block, no tail
+        int RB = BH % 4 == 0 ? 4 : BH % 2 == 0 ? 2 : 1;  // rows per block, no tail
+        // a pass evaluating the corner responses keeps its 64-bit arithmetic
+        // for one cell per iteration (registers)
+        for (int k = 0; k < d.n_stage; ++k)
+            if (p.need_op[k] && (d.st[k].op == OP_TOMASI || d.st[k].op == OP_HARRIS)) RB = 1;
+        if (const char* e = getenv("HVX_CODEGEN_ROWS")) {
+            const int v = atoi(e);
+            if ((v == 1 || v == 2 || v == 4) && BH % v == 0) RB = v;
+        }
         const bool outputs = p.kind == OUT;
         o << "  // pass: ";
         if (outputs)
@@ -978,6 +987,12 @@ struct Emitter {
           << "__device__ __forceinline__ void hvx_tile(const HvxJitParams& p, int* smem, int x0, "
              "int y0) {\n"
           << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
+        // the body is written first: every launch parameter it reads per cell
+        // is then read once into a register (the batched entry point's
+        // parameters live in global memory)
+        const std::string head = o.str();
+        o.str("");
+        o.clear();
         bool hist = false;
         for (int k : globals)
             if (d.st[k].op == OP_HIST) {
@@ -1006,6 +1021,30 @@ struct Emitter {
                 case OUT: emit_cells(p); break;
             }
         }
+        std::string body = o.str();
+        std::string regs = "  const int pW = p.W, pH = p.H;\n";
+        auto swap_all = [&](const std::string& from, const std::string& to) {
+            for (size_t at = body.find(from); at != std::string::npos;
+                 at = body.find(from, at + to.size()))
+                body.replace(at, from.size(), to);
+        };
+        for (int e = 0; e < d.n_in; ++e) {
+            const std::string E = std::to_string(e);
+            regs += "  const void* const in" + E + " = p.in[" + E +
+                    "];\n  const unsigned long long ip" + E + " = p.in_pitch[" + E + "];\n";
+            swap_all("p.in[" + E + "], p.in_pitch[" + E + "]", "in" + E + ", ip" + E);
+        }
+        for (int e = 0; e < d.n_out; ++e) {
+            const std::string E = std::to_string(e);
+            regs += "  void* const out" + E + " = p.out[" + E +
+                    "];\n  const unsigned long long op" + E + " = p.out_pitch[" + E + "];\n";
+            swap_all("p.out[" + E + "], p.out_pitch[" + E + "]", "out" + E + ", op" + E);
+        }
+        swap_all("p.W", "pW");
+        swap_all("p.H", "pH");
+        o.str("");
+        o.clear();
+        o << head << regs << body;
         o << "}\n\n"
           << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
           << ") hvx_generated(const HvxJitParams p) {\n"
