@@ -65,6 +65,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=1,
+                    help="edge workload: streams the end-to-end calls rotate over")
+    ap.add_argument("--e2e-chunks", type=int, default=1,
+                    help="edge workload: hvxScheduleGraphBatchHost calls per step (each "
+                         "call pipelines its frames' copies and kernels internally)")
     ap.add_argument("--apps", default=None,
                     help="apps workload: comma-separated subset (e.g. Gauss,Tomasi)")
     return ap.parse_args()
@@ -339,19 +344,19 @@ def run_edge(args, world, rank, local, torch):
     barrier(world, torch)
     t_plain = reduce_max(time_steps(torch, step_plain, plain_steps, stream), world, torch)
 
-    # end to end through the C ABI on host data: every step, each chunk of
-    # frames is one hvxScheduleGraphBatchHost call (copies of its frames in
-    # from pinned host memory, the fused batch, both outputs back), chunks
-    # rotating over three streams so that one chunk's copies overlap another's
-    # kernel.  The host link (about 210 GB/s in, 193 GB/s out, 341 GB/s both
-    # ways) bounds this number, not the kernel.
+    # end to end through the C ABI on host data: every step is one
+    # hvxScheduleGraphBatchHost call on the 64 frames (copies in from pinned
+    # host memory, the fused batch, both outputs back), which pipelines parts
+    # of the batch over two copy streams and the launch stream so that copies
+    # in both directions overlap the kernels.  The host link (about 210 GB/s
+    # in, 193 GB/s out, 341 GB/s both ways) bounds this number, not the kernel.
     h_in = torch.empty((F, H_, pitch), dtype=torch.uint8).pin_memory()
     h_in.copy_(t_in.cpu())
     h_ph = torch.empty_like(h_in).pin_memory()
     h_mk = torch.empty_like(h_in).pin_memory()
-    chunk = max(1, F // 16)
+    chunk = max(1, F // args.e2e_chunks)
     chunks = [(i, min(F, i + chunk)) for i in range(0, F, chunk)]
-    streams = [torch.cuda.Stream() for _ in range(3)]
+    streams = [torch.cuda.Stream() for _ in range(max(1, args.e2e_streams))]
     sub = [fused[a:b] for a, b in chunks]
     copies = []
     for a, b in chunks:

@@ -261,6 +261,9 @@ hvx_status hvxReleaseContext(hvx_context* pc) {
     c->images.clear();
     destroy_batch_cache(c);
     if (c->d_error) cudaFree(c->d_error);
+    for (cudaEvent_t e : c->io_events) cudaEventDestroy(e);
+    if (c->io_in) cudaStreamDestroy(c->io_in);
+    if (c->io_out) cudaStreamDestroy(c->io_out);
     c->magic = 0;
     delete c;
     *pc = nullptr;
@@ -415,24 +418,26 @@ hvx_status hvxCopyImage(hvx_image img, void* host, uint64_t host_pitch, int32_t 
     return cuda_status(e);
 }
 
-// Host-side data of one batch call: uploads before the launch, downloads after
-// it, all on the caller's stream.  Consecutive copies whose images follow one
-// another in device memory and whose host buffers follow one another too (same
-// row size and pitches, e.g. frames of one tensor) are merged into one 2-D
-// copy of all their rows.
-static hvx_status host_copies(const hvx_host_copy* copies, int32_t n, bool to_device,
+// Host-side copies of one batch call.  Consecutive copies whose images follow
+// one another in device memory and whose host buffers follow one another too
+// (same row size and pitches, e.g. frames of one tensor) are merged into one
+// 2-D copy of all their rows.
+static hvx_status host_copies(std::vector<const hvx_host_copy*> copies, bool to_device,
                               cudaStream_t s) {
+    // in device-address order, so that images adjacent in memory meet
+    std::stable_sort(copies.begin(), copies.end(),
+                     [](const hvx_host_copy* a, const hvx_host_copy* b) {
+                         return I(a->image)->dev < I(b->image)->dev;
+                     });
     struct Run {
         char* dev;
         char* host;
         uint64_t dpitch, hpitch, row, rows;
     };
     std::vector<Run> runs;
-    for (int32_t i = 0; i < n; ++i) {
-        const hvx_host_copy& c = copies[i];
-        if ((c.to_device != 0) != to_device) continue;
-        const Image* im = I(c.image);
-        Run r{static_cast<char*>(im->dev), static_cast<char*>(c.host), im->pitch, c.pitch,
+    for (const hvx_host_copy* c : copies) {
+        const Image* im = I(c->image);
+        Run r{static_cast<char*>(im->dev), static_cast<char*>(c->host), im->pitch, c->pitch,
               (uint64_t)im->w * bytes_per_pixel(im->fmt), im->h};
         if (!runs.empty()) {
             Run& b = runs.back();
@@ -454,6 +459,14 @@ static hvx_status host_copies(const hvx_host_copy* copies, int32_t n, bool to_de
     return HVX_SUCCESS;
 }
 
+// Whether graph g reads (inputs) or writes (outputs) image im from memory.
+static bool graph_touches(const Graph* g, const Image* im, bool inputs) {
+    for (const Group& G : g->plan.groups)
+        for (const Image* x : inputs ? G.inputs : G.outputs)
+            if (x == im) return true;
+    return false;
+}
+
 hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_host_copy* copies,
                                      int32_t n_copies, void* stream) {
     if (!gs || n <= 0 || n_copies < 0 || (n_copies > 0 && !copies))
@@ -465,21 +478,73 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
         if (G(gs[i])->ctx != G(gs[0])->ctx) return HVX_ERROR_INVALID_REFERENCE;
         v.push_back(G(gs[i]));
     }
-    if (v[0]->ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    Context* ctx = v[0]->ctx;
+    if (ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
     for (int32_t i = 0; i < n_copies; ++i) {
         const hvx_host_copy& c = copies[i];
         if (!ok_image(c.image) || !c.host) return HVX_ERROR_INVALID_PARAMETERS;
         const Image* im = I(c.image);
-        if (im->is_virtual || im->is_result || im->ctx != v[0]->ctx || !im->dev)
+        if (im->is_virtual || im->is_result || im->ctx != ctx || !im->dev)
             return HVX_ERROR_INVALID_REFERENCE;
         if (c.pitch < (uint64_t)im->w * bytes_per_pixel(im->fmt)) return HVX_ERROR_INVALID_PARAMETERS;
     }
+    // A pipeline over parts of the batch: part j's uploads (copy stream in),
+    // its launches (the caller's stream), its downloads (copy stream out), so
+    // that part j + 1's uploads and part j - 1's downloads overlap part j's
+    // kernels.  The caller's stream waits for the last download at the end.
+    const int parts = std::min(n, 8);
+    if (!ctx->io_in && (cudaStreamCreateWithFlags(&ctx->io_in, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking) != cudaSuccess))
+        return HVX_ERROR_DEVICE;
+    while ((int)ctx->io_events.size() < 2 * parts + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HVX_ERROR_DEVICE;
+        ctx->io_events.push_back(e);
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    hvx_status st = host_copies(copies, n_copies, true, s);
-    if (st != HVX_SUCCESS) return st;
-    st = process_batch(v[0]->ctx, v.data(), n, s);
-    if (st != HVX_SUCCESS) return st;
-    return host_copies(copies, n_copies, false, s);
+    cudaEvent_t start = ctx->io_events[0];
+    cudaError_t e = cudaEventRecord(start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_in, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_out, start, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    // each copy goes with the first part whose graphs read / write its image
+    std::vector<std::vector<const hvx_host_copy*>> up(parts), down(parts);
+    for (int32_t i = 0; i < n_copies; ++i) {
+        const hvx_host_copy& c = copies[i];
+        const Image* im = I(c.image);
+        int part = c.to_device ? 0 : parts - 1;
+        for (int j = 0; j < parts; ++j) {
+            const int a = (int)((int64_t)n * j / parts), b = (int)((int64_t)n * (j + 1) / parts);
+            bool hit = false;
+            for (int k = a; k < b && !hit; ++k) hit = graph_touches(v[k], im, c.to_device != 0);
+            if (hit) {
+                part = j;
+                break;
+            }
+        }
+        (c.to_device ? up : down)[part].push_back(&c);
+    }
+    for (int j = 0; j < parts; ++j) {
+        const int a = (int)((int64_t)n * j / parts), b = (int)((int64_t)n * (j + 1) / parts);
+        cudaEvent_t uploaded = ctx->io_events[1 + 2 * j], computed = ctx->io_events[2 + 2 * j];
+        hvx_status st = host_copies(up[j], true, ctx->io_in);
+        if (st != HVX_SUCCESS) return st;
+        if ((e = cudaEventRecord(uploaded, ctx->io_in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, uploaded, 0)) != cudaSuccess)
+            return cuda_status(e);
+        st = process_batch(ctx, v.data() + a, b - a, s);
+        if (st != HVX_SUCCESS) return st;
+        if ((e = cudaEventRecord(computed, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->io_out, computed, 0)) != cudaSuccess)
+            return cuda_status(e);
+        st = host_copies(down[j], false, ctx->io_out);
+        if (st != HVX_SUCCESS) return st;
+    }
+    cudaEvent_t done = ctx->io_events[2 * parts];
+    if ((e = cudaEventRecord(done, ctx->io_out)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, done, 0)) != cudaSuccess)
+        return cuda_status(e);
+    return HVX_SUCCESS;
 }
 
 hvx_status hvxGetImageDevicePtr(hvx_image img, void** dev, uint64_t* pitch) {

@@ -213,6 +213,21 @@ struct Emitter {
 
     int bw(int b) const { return tw + 2 * d.buf[b].halo; }
     int bh(int b) const { return th + 2 * d.buf[b].halo; }
+
+    // Staged U8 external inputs are held as bytes, in rows that start on the
+    // 4-byte boundary at or left of the region (image x = x0 - A, A = halo
+    // rounded up to a multiple of 4), so that interior tiles load them with
+    // one 32-bit load per 4 pixels.  Other staged images hold int32 cells.
+    bool byte_slot(int b) const {
+        return b < d.n_buf && staged[b] && ext_in[b] >= 0 && d.buf[b].fmt == HVX_DF_U8;
+    }
+    int align4(int b) const { return (d.buf[b].halo + 3) & ~3; }
+    int slot_w(int b) const { return byte_slot(b) ? tw + 2 * align4(b) : bw(b); }
+    int slot_x(int b) const { return byte_slot(b) ? align4(b) - d.buf[b].halo : 0; }
+    int slot_words(int s) const {
+        const int n = slot[s].w * slot[s].h;
+        return byte_slot(s) ? ((n / 4 + 3) & ~3) : ((n + 3) & ~3);  // 16-byte aligned
+    }
     int row_slot(int k) const { return d.n_buf + k; }
     bool separable(int k) const { return !sep_s[k].empty(); }
 
@@ -389,7 +404,7 @@ struct Emitter {
         slot.assign(d.n_buf + d.n_stage, Slot{});
         for (int b = 0; b < d.n_buf; ++b)
             if (staged[b]) {
-                slot[b].w = bw(b);
+                slot[b].w = slot_w(b);
                 slot[b].h = bh(b);
             }
         for (int k = 0; k < d.n_stage; ++k)
@@ -428,11 +443,11 @@ struct Emitter {
         int words = 0;
         std::vector<int> placed;
         for (int s : ids) {
-            const int n = (slot[s].w * slot[s].h + 3) & ~3;  // 16-byte aligned slots
+            const int n = slot_words(s);
             std::vector<std::pair<int, int>> busy;
             for (int t : placed)
                 if (slot[t].def <= slot[s].last && slot[s].def <= slot[t].last)
-                    busy.push_back({slot[t].off, slot[t].off + ((slot[t].w * slot[t].h + 3) & ~3)});
+                    busy.push_back({slot[t].off, slot[t].off + slot_words(t)});
             std::sort(busy.begin(), busy.end());
             int off = 0;
             for (const auto& iv : busy) {
@@ -510,7 +525,7 @@ struct Emitter {
     // Read of staged buffer b at offset (dx, dy) from the current cell.
     std::string tap(int b, int dx, int dy) const {
         if (row >= 0) return load_var(b, row + dy, dx);
-        const int off = dy * bw(b) + dx;
+        const int off = dy * slot_w(b) + dx;
         std::string s = "B" + std::to_string(b) + "[q" + std::to_string(b);
         if (off > 0) s += " + " + std::to_string(off);
         if (off < 0) s += " - " + std::to_string(-off);
@@ -714,6 +729,36 @@ struct Emitter {
         const std::string ld = "hvx_ld<" + std::to_string(d.in[e].fmt) + ">(p.in[" +
                                std::to_string(e) + "], p.in_pitch[" + std::to_string(e) + "], ";
         o << "  // external input " << e << " -> B" << b << " (halo " << h << ")\n";
+        if (byte_slot(b)) {
+            // interior tiles: the region's rows are inside the image, and the
+            // words [x0 - A, x0 + tw + A) stay inside each row's pitch
+            const int A = align4(b), words = slot_w(b) / 4, rows = bh(b);
+            o << "  if (!CHECK) {\n"
+              << "    const unsigned char* const g0 = (const unsigned char*)p.in[" << e
+              << "] + (unsigned long long)(y0 - " << h << ") * p.in_pitch[" << e << "] + (x0 - " << A
+              << ");\n"
+              << "    #pragma unroll 8\n"
+              << "    for (int i = threadIdx.x; i < " << rows * words << "; i += " << kThreads
+              << ") {\n"
+              << "      const int r = i / " << words << ", k = i - r * " << words << ";\n"
+              << "      ((unsigned*)B" << b << ")[i] = __ldg((const unsigned*)(g0 + "
+                 "(unsigned long long)r * p.in_pitch["
+              << e << "]) + k);\n"
+              << "    }\n  } else {\n";
+            open_cells(bh(b), bw(b), h, h, true);
+            o << "      int v;\n"
+              << "      if (x >= 0 && x < p.W && y >= 0 && y < p.H) v = " << ld << "x, y);\n"
+              << "      else v = "
+              << (d.buf[b].fill == FILL_MIRROR || d.buf[b].fill == FILL_REPEAT
+                      ? ld + fill_coords(b)
+                      : fill_expr(b, ld + fill_coords(b)))
+              << ";\n"
+              << "      B" << b << "[r * " << slot_w(b) << " + c + " << slot_x(b)
+              << "] = (unsigned char)v;\n";
+            close_cells();
+            o << "  }\n";
+            return;
+        }
         open_cells(bh(b), bw(b), h, h, true);
         o << "      int v;\n"
           << "      if (!CHECK || (x >= 0 && x < p.W && y >= 0 && y < p.H)) v = " << ld
@@ -736,8 +781,8 @@ struct Emitter {
         const Slot& R = slot[row_slot(k)];
         o << "  // row sums of op " << k << " -> R" << k << " (" << R.w << " x " << R.h << ")\n";
         open_cells(R.h, R.w, 0, 0, false, false);
-        o << "      const int q = (r + " << hb - hl - st.ry << ") * " << bw(b) << " + c + "
-          << hb - hl << ";\n";
+        o << "      const int q = (r + " << hb - hl - st.ry << ") * " << slot_w(b) << " + c + "
+          << hb - hl + slot_x(b) << ";\n";
         const bool lsum = st.op == OP_LSUM;
         o << "      " << (lsum ? "unsigned" : "int") << " t = 0;\n";
         for (int j = 0; j < (int)sep_s[k].size(); ++j) {
@@ -897,8 +942,8 @@ struct Emitter {
             based[s] = true;
             if (s < d.n_buf) {
                 const int dh = d.buf[s].halo - h;
-                o << "      const int qb" << s << " = (rb + " << dh << ") * " << bw(s) << " + c + "
-                  << dh << ";\n";
+                o << "      const int qb" << s << " = (rb + " << dh << ") * " << slot_w(s)
+                  << " + c + " << dh + slot_x(s) << ";\n";
             } else {
                 const int k = s - d.n_buf, dh = d.buf[d.st[k].out].halo - h;
                 o << "      const int qb" << s << " = (rb + " << dh + d.st[k].ry << ") * "
@@ -1004,7 +1049,9 @@ struct Emitter {
         if (hist) o << "  __syncthreads();\n";
         for (int s = 0; s < (int)slot.size(); ++s)
             if (slot[s].w > 0)
-                o << "  int* const " << slot_name(s) << " = smem + " << slot[s].off << ";  // "
+                o << (byte_slot(s) ? "  unsigned char* const " : "  int* const ") << slot_name(s)
+                  << (byte_slot(s) ? " = (unsigned char*)(smem + " : " = (smem + ") << slot[s].off
+                  << ");  // "
                   << slot[s].w << " x " << slot[s].h << ", passes " << slot[s].def << ".."
                   << slot[s].last << "\n";
         for (const Pass& p : passes) {

@@ -275,6 +275,9 @@ struct Context {
     int* d_error = nullptr;      // device error word (bounded waits that ran out)
     int num_sms = 0;
     BatchCache* batch = nullptr;
+    // hvxScheduleGraphBatchHost: copy streams and events of its pipeline
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    std::vector<cudaEvent_t> io_events;
 };
 
 // ---------------------------------------------------------------------------
