@@ -65,9 +65,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--e2e-streams", type=int, default=1,
+    ap.add_argument("--e2e-streams", type=int, default=2,
                     help="edge workload: streams the end-to-end calls rotate over")
-    ap.add_argument("--e2e-chunks", type=int, default=1,
+    ap.add_argument("--e2e-chunks", type=int, default=2,
                     help="edge workload: hvxScheduleGraphBatchHost calls per step (each "
                          "call pipelines its frames' copies and kernels internally)")
     ap.add_argument("--apps", default=None,
@@ -344,11 +344,11 @@ def run_edge(args, world, rank, local, torch):
     barrier(world, torch)
     t_plain = reduce_max(time_steps(torch, step_plain, plain_steps, stream), world, torch)
 
-    # end to end through the C ABI on host data: every step is one
-    # hvxScheduleGraphBatchHost call on the 64 frames (copies in from pinned
-    # host memory, the fused batch, both outputs back), which pipelines parts
-    # of the batch over two copy streams and the launch stream so that copies
-    # in both directions overlap the kernels.  The host link (about 210 GB/s
+    # end to end through the C ABI on host data: every step is two
+    # hvxScheduleGraphBatchHost calls of 32 frames on two streams (copies in
+    # from pinned host memory, the fused batch, both outputs back); each call
+    # pipelines parts of its batch over two copy streams and the launch
+    # stream so that copies in both directions overlap the kernels.  The host link (about 210 GB/s
     # in, 193 GB/s out, 341 GB/s both ways) bounds this number, not the kernel.
     h_in = torch.empty((F, H_, pitch), dtype=torch.uint8).pin_memory()
     h_in.copy_(t_in.cpu())
