@@ -65,7 +65,6 @@ typedef CUresult (*FnModuleGetFunction)(CUfunction*, CUmodule, const char*);
 typedef CUresult (*FnFuncSetAttribute)(CUfunction, CUfunction_attribute, int);
 typedef CUresult (*FnLaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
                                    unsigned, unsigned, CUstream, void**, void**);
-typedef CUresult (*FnOccupancy)(int*, CUfunction, int, size_t);
 
 struct Nvrtc {
     bool ok = false;
@@ -117,7 +116,6 @@ struct Driver {
     FnModuleGetFunction get = nullptr;
     FnFuncSetAttribute attr = nullptr;
     FnLaunchKernel launch = nullptr;
-    FnOccupancy occupancy = nullptr;
 };
 
 Driver& driver() {
@@ -139,8 +137,7 @@ Driver& driver() {
         d.get = (FnModuleGetFunction)entry("cuModuleGetFunction");
         d.attr = (FnFuncSetAttribute)entry("cuFuncSetAttribute");
         d.launch = (FnLaunchKernel)entry("cuLaunchKernel");
-        d.occupancy = (FnOccupancy)entry("cuOccupancyMaxActiveBlocksPerMultiprocessor");
-        d.ok = d.load && d.get && d.attr && d.launch && d.occupancy;
+        d.ok = d.load && d.get && d.attr && d.launch;
     });
     return d;
 }
@@ -158,7 +155,6 @@ struct JitKernel {
     CUfunction fn = nullptr;
     CUfunction fn_batch = nullptr;  // several images per launch
     int smem_bytes = 0;
-    int blocks_per_sm = 1;          // resident CTAs per SM (persistent grids)
     int tw = 0, th = 0;
 };
 
@@ -997,60 +993,6 @@ struct Emitter {
         o << "  }\n  __syncthreads();\n";
     }
 
-    // Pointers to the shared-memory slots (only the staged inputs' when
-    // inputs_only).
-    void emit_slot_pointers(bool inputs_only) {
-        for (int s = 0; s < (int)slot.size(); ++s) {
-            if (slot[s].w <= 0) continue;
-            if (inputs_only && !(s < d.n_buf && staged[s] && ext_in[s] >= 0)) continue;
-            o << (byte_slot(s) ? "  unsigned char* const " : "  int* const ") << slot_name(s)
-              << (byte_slot(s) ? " = (unsigned char*)(smem + " : " = (smem + ") << slot[s].off
-              << ");  // " << slot[s].w << " x " << slot[s].h << ", passes " << slot[s].def
-              << ".." << slot[s].last << "\n";
-        }
-    }
-
-    // One device function: its body is written first, so that every launch
-    // parameter it reads per cell is then read once into a register (the
-    // batched entry point's parameters live in global memory).
-    template <class Body>
-    void emit_function(const std::string& head, Body body_fn) {
-        const std::string before = o.str();
-        o.str("");
-        o.clear();
-        body_fn();
-        std::string body = o.str();
-        std::string regs = "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n"
-                           "  (void)lane;\n  (void)warp;\n"
-                           "  const int pW = p.W, pH = p.H;\n  (void)pW;\n  (void)pH;\n";
-        auto swap_all = [&](const std::string& from, const std::string& to) {
-            for (size_t at = body.find(from); at != std::string::npos;
-                 at = body.find(from, at + to.size()))
-                body.replace(at, from.size(), to);
-        };
-        for (int e = 0; e < d.n_in; ++e) {
-            const std::string E = std::to_string(e);
-            const std::string from = "p.in[" + E + "], p.in_pitch[" + E + "]";
-            if (body.find(from) == std::string::npos) continue;
-            regs += "  const void* const in" + E + " = p.in[" + E +
-                    "];\n  const unsigned long long ip" + E + " = p.in_pitch[" + E + "];\n";
-            swap_all(from, "in" + E + ", ip" + E);
-        }
-        for (int e = 0; e < d.n_out; ++e) {
-            const std::string E = std::to_string(e);
-            const std::string from = "p.out[" + E + "], p.out_pitch[" + E + "]";
-            if (body.find(from) == std::string::npos) continue;
-            regs += "  void* const out" + E + " = p.out[" + E +
-                    "];\n  const unsigned long long op" + E + " = p.out_pitch[" + E + "];\n";
-            swap_all(from, "out" + E + ", op" + E);
-        }
-        swap_all("p.W", "pW");
-        swap_all("p.H", "pH");
-        o.str("");
-        o.clear();
-        o << before << head << regs << body << "}\n\n";
-    }
-
     bool emit() {
         analyse();
         // MIRROR / REPEAT fills are only possible for external inputs
@@ -1086,153 +1028,101 @@ struct Emitter {
           << "  if (F == " << HVX_DF_U8 << ") row[x] = (unsigned char)v;\n"
           << "  else if (F == " << HVX_DF_S16 << ") ((short*)row)[x] = (short)v;\n"
           << "  else ((int*)row)[x] = v;\n}\n\n"
-          ;
-        // the tile function without its input loads; the loads; the register
-        // prefetch of the next tile's U8 inputs; the persistent entry points
-        emit_function("template <bool CHECK>\n__device__ __forceinline__ void hvx_tile(const "
-                      "HvxJitParams& p, int* smem, int x0, int y0) {\n",
-                      [&] {
-                          bool hist = false;
-                          for (int k : globals)
-                              if (d.st[k].op == OP_HIST) {
-                                  o << "  __shared__ unsigned g" << k << "_bins[" << d.st[k].i0
-                                    << "];\n  for (int i = threadIdx.x; i < " << d.st[k].i0
-                                    << "; i += " << kThreads << ") g" << k << "_bins[i] = 0;\n";
-                                  hist = true;
-                              }
-                          if (hist) o << "  __syncthreads();\n";
-                          emit_slot_pointers(false);
-                          for (const Pass& q : passes) {
-                              if (q.kind == ROW) {
-                                  for (int k : q.targets) emit_row(k);
-                                  o << "  __syncthreads();\n";
-                              } else if (q.kind == CELLS || q.kind == OUT) {
-                                  emit_cells(q);
-                              }
-                          }
-                      });
-        // staged inputs; BYTES false leaves out the U8 inputs (prefetched)
-        emit_function("template <bool CHECK, bool BYTES>\n__device__ __forceinline__ void "
-                      "hvx_load(const HvxJitParams& p, int* smem, int x0, int y0) {\n",
-                      [&] {
-                          emit_slot_pointers(true);
-                          for (int b = 0; b < d.n_buf; ++b) {
-                              if (!staged[b] || ext_in[b] < 0) continue;
-                              if (byte_slot(b)) o << "  if (BYTES) {\n";
-                              emit_load(b);
-                              if (byte_slot(b)) o << "  }\n";
-                          }
-                      });
-        int kt = 0;
-        std::ostringstream fetch, put;
-        for (int b = 0; b < d.n_buf; ++b) {
-            if (!byte_slot(b)) continue;
-            const int e = ext_in[b], h = d.buf[b].halo, A = align4(b), words = slot_w(b) / 4;
-            const int n = bh(b) * words, K = (n + kThreads - 1) / kThreads;
-            fetch << "  {\n    const unsigned char* const g0 = (const unsigned char*)p.in[" << e
-                  << "] + (unsigned long long)(y0 - " << h << ") * p.in_pitch[" << e
-                  << "] + (x0 - " << A << ");\n    #pragma unroll\n    for (int j = 0; j < " << K
-                  << "; ++j) {\n      const int i = threadIdx.x + j * " << kThreads
-                  << ";\n      if (i < " << n << ") {\n        const int r = i / " << words
-                  << ", k = i - r * " << words << ";\n        pf[" << kt
-                  << " + j] = __ldg((const unsigned*)(g0 + (unsigned long long)r * p.in_pitch[" << e
-                  << "]) + k);\n      }\n    }\n  }\n";
-            put << "  #pragma unroll\n  for (int j = 0; j < " << K << "; ++j) {\n"
-                << "    const int i = threadIdx.x + j * " << kThreads << ";\n"
-                << "    if (i < " << n << ") ((unsigned*)(smem + " << slot[b].off << "))[i] = pf["
-                << kt << " + j];\n  }\n";
-            kt += K;
+          << "template <bool CHECK>\n"
+          << "__device__ __forceinline__ void hvx_tile(const HvxJitParams& p, int* smem, int x0, "
+             "int y0) {\n"
+          << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
+        // the body is written first: every launch parameter it reads per cell
+        // is then read once into a register (the batched entry point's
+        // parameters live in global memory)
+        const std::string head = o.str();
+        o.str("");
+        o.clear();
+        bool hist = false;
+        for (int k : globals)
+            if (d.st[k].op == OP_HIST) {
+                o << "  __shared__ unsigned g" << k << "_bins[" << d.st[k].i0 << "];\n"
+                  << "  for (int i = threadIdx.x; i < " << d.st[k].i0 << "; i += " << kThreads
+                  << ") g" << k << "_bins[i] = 0;\n";
+                hist = true;
+            }
+        if (hist) o << "  __syncthreads();\n";
+        for (int s = 0; s < (int)slot.size(); ++s)
+            if (slot[s].w > 0)
+                o << (byte_slot(s) ? "  unsigned char* const " : "  int* const ") << slot_name(s)
+                  << (byte_slot(s) ? " = (unsigned char*)(smem + " : " = (smem + ") << slot[s].off
+                  << ");  // "
+                  << slot[s].w << " x " << slot[s].h << ", passes " << slot[s].def << ".."
+                  << slot[s].last << "\n";
+        for (const Pass& p : passes) {
+            switch (p.kind) {
+                case LOAD:
+                    for (int b : p.targets) emit_load(b);
+                    o << "  __syncthreads();\n";
+                    break;
+                case ROW:
+                    for (int k : p.targets) emit_row(k);
+                    o << "  __syncthreads();\n";
+                    break;
+                case CELLS:
+                case OUT: emit_cells(p); break;
+            }
         }
-        o << "__device__ __forceinline__ void hvx_fetch(const HvxJitParams& p, int x0, int y0, "
-             "unsigned* pf) {\n"
-          << fetch.str() << "}\n\n"
-          << "__device__ __forceinline__ void hvx_put(int* smem, const unsigned* pf) {\n"
-          << put.str() << "}\n\n";
-        const std::string T = std::to_string(tw), TH = std::to_string(th),
-                          KT = std::to_string(std::max(kt, 1));
-        const std::string interior = "(X >= P.ix0 && X <= P.ix1 && Y >= P.iy0 && Y <= P.iy1)";
-        auto inner = [&](const std::string& P, const std::string& X, const std::string& Y) {
-            std::string s = interior;
-            for (auto [from, to] : {std::make_pair(std::string("P."), P + "."),
-                                    std::make_pair(std::string("X "), X + " "),
-                                    std::make_pair(std::string("Y "), Y + " ")})
-                for (size_t at = s.find(from); at != std::string::npos;
-                     at = s.find(from, at + to.size()))
-                    s.replace(at, from.size(), to);
-            return s;
+        std::string body = o.str();
+        std::string regs = "  const int pW = p.W, pH = p.H;\n";
+        auto swap_all = [&](const std::string& from, const std::string& to) {
+            for (size_t at = body.find(from); at != std::string::npos;
+                 at = body.find(from, at + to.size()))
+                body.replace(at, from.size(), to);
         };
-        // Persistent: a CTA walks tiles t, t + grid, ...; while it computes one
-        // tile its threads hold the next interior tile's U8 input words in
-        // registers and store them to shared memory after the tile.
-        o << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+        for (int e = 0; e < d.n_in; ++e) {
+            const std::string E = std::to_string(e);
+            regs += "  const void* const in" + E + " = p.in[" + E +
+                    "];\n  const unsigned long long ip" + E + " = p.in_pitch[" + E + "];\n";
+            swap_all("p.in[" + E + "], p.in_pitch[" + E + "]", "in" + E + ", ip" + E);
+        }
+        for (int e = 0; e < d.n_out; ++e) {
+            const std::string E = std::to_string(e);
+            regs += "  void* const out" + E + " = p.out[" + E +
+                    "];\n  const unsigned long long op" + E + " = p.out_pitch[" + E + "];\n";
+            swap_all("p.out[" + E + "], p.out_pitch[" + E + "]", "out" + E + ", op" + E);
+        }
+        swap_all("p.W", "pW");
+        swap_all("p.H", "pH");
+        o.str("");
+        o.clear();
+        o << head << regs << body;
+        o << "}\n\n"
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
           << ") hvx_generated(const HvxJitParams p) {\n"
           << "  extern __shared__ __align__(16) int smem[];\n"
-          << "  const int gx = (p.W + " << tw - 1 << ") / " << T << ", tiles = gx * ((p.H + "
-          << th - 1 << ") / " << TH << ");\n"
-          << "  int t = blockIdx.x;\n  if (t >= tiles) return;\n"
-          << "  int ty = t / gx, tx = t - ty * gx;\n"
-          << "  if " << inner("p", "tx", "ty") << " hvx_load<false, true>(p, smem, tx * " << T
-          << ", ty * " << TH << ");\n"
-          << "  else hvx_load<true, true>(p, smem, tx * " << T << ", ty * " << TH << ");\n"
-          << "  for (;;) {\n"
-          << "    const int n = t + gridDim.x;\n"
-          << "    const int nty = n / gx, ntx = n - nty * gx;\n"
-          << "    const bool nin = n < tiles && " << inner("p", "ntx", "nty") << ";\n"
-          << "    unsigned pf[" << KT << "];\n"
-          << "    if (nin) hvx_fetch(p, ntx * " << T << ", nty * " << TH << ", pf);\n"
-          << "    __syncthreads();\n"
-          << "    if " << inner("p", "tx", "ty") << " hvx_tile<false>(p, smem, tx * " << T
-          << ", ty * " << TH << ");\n"
-          << "    else hvx_tile<true>(p, smem, tx * " << T << ", ty * " << TH << ");\n"
-          << "    if (n >= tiles) break;\n"
-          << "    __syncthreads();\n"
-          << "    if (nin) {\n      hvx_put(smem, pf);\n      hvx_load<false, false>(p, smem, ntx * "
-          << T << ", nty * " << TH << ");\n"
-          << "    } else {\n      hvx_load<true, true>(p, smem, ntx * " << T << ", nty * " << TH
-          << ");\n    }\n"
-          << "    t = n;\n    tx = ntx;\n    ty = nty;\n  }\n}\n\n"
-          << "// n images in one launch: tile t belongs to the last image i with\n"
-          << "// tile_start[i] <= t\n"
-          << "__device__ __forceinline__ int hvx_image_of(const int* tile_start, int n, int t) {\n"
+          << "  const int tx = blockIdx.x, ty = blockIdx.y;\n"
+          << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
+          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "  else\n"
+          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "}\n\n"
+          << "// n images in one launch: block t is tile t - tile_start[i] of the last\n"
+          << "// image i with tile_start[i] <= t\n"
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+          << ") hvx_generated_batch(const HvxJitParams* __restrict__ ps, const int* __restrict__ "
+             "tile_start, int n) {\n"
+          << "  extern __shared__ __align__(16) int smem[];\n"
+          << "  const int t = blockIdx.x;\n"
           << "  int lo = 0, hi = n - 1;\n"
           << "  while (lo < hi) {\n"
           << "    const int mid = (lo + hi + 1) >> 1;\n"
           << "    if (__ldg(tile_start + mid) <= t) lo = mid; else hi = mid - 1;\n"
-          << "  }\n  return lo;\n}\n\n"
-          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
-          << ") hvx_generated_batch(const HvxJitParams* __restrict__ ps, const int* __restrict__ "
-             "tile_start, int n_img, int total) {\n"
-          << "  extern __shared__ __align__(16) int smem[];\n"
-          << "  int t = blockIdx.x;\n  if (t >= total) return;\n"
-          << "  int im = hvx_image_of(tile_start, n_img, t);\n"
-          << "  int gx = (ps[im].W + " << tw - 1 << ") / " << T << ";\n"
-          << "  int local = t - __ldg(tile_start + im), ty = local / gx, tx = local - ty * gx;\n"
-          << "  if " << inner("ps[im]", "tx", "ty") << " hvx_load<false, true>(ps[im], smem, tx * "
-          << T << ", ty * " << TH << ");\n"
-          << "  else hvx_load<true, true>(ps[im], smem, tx * " << T << ", ty * " << TH << ");\n"
-          << "  for (;;) {\n"
-          << "    const int n = t + gridDim.x;\n"
-          << "    int nim = im, ntx = 0, nty = 0;\n    bool nin = false;\n"
-          << "    unsigned pf[" << KT << "];\n"
-          << "    if (n < total) {\n"
-          << "      nim = hvx_image_of(tile_start, n_img, n);\n"
-          << "      const int ngx = (ps[nim].W + " << tw - 1 << ") / " << T
-          << ", nl = n - __ldg(tile_start + nim);\n"
-          << "      nty = nl / ngx;\n      ntx = nl - nty * ngx;\n"
-          << "      nin = " << inner("ps[nim]", "ntx", "nty") << ";\n"
-          << "      if (nin) hvx_fetch(ps[nim], ntx * " << T << ", nty * " << TH << ", pf);\n"
-          << "    }\n"
-          << "    __syncthreads();\n"
-          << "    if " << inner("ps[im]", "tx", "ty") << " hvx_tile<false>(ps[im], smem, tx * " << T
-          << ", ty * " << TH << ");\n"
-          << "    else hvx_tile<true>(ps[im], smem, tx * " << T << ", ty * " << TH << ");\n"
-          << "    if (n >= total) break;\n"
-          << "    __syncthreads();\n"
-          << "    if (nin) {\n      hvx_put(smem, pf);\n      hvx_load<false, false>(ps[nim], smem, ntx * "
-          << T << ", nty * " << TH << ");\n"
-          << "    } else {\n      hvx_load<true, true>(ps[nim], smem, ntx * " << T << ", nty * "
-          << TH << ");\n    }\n"
-          << "    t = n;\n    im = nim;\n    tx = ntx;\n    ty = nty;\n  }\n}\n";
+          << "  }\n"
+          << "  const HvxJitParams& p = ps[lo];\n"
+          << "  const int local = t - __ldg(tile_start + lo), gx = (p.W + " << tw - 1 << ") / "
+          << tw << ";\n"
+          << "  const int ty = local / gx, tx = local - ty * gx;\n"
+          << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
+          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "  else\n"
+          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "}\n";
         return true;
     }
 };
@@ -1302,9 +1192,6 @@ bool load(JitKernel& k, int device, std::string* why) {
         *why = "cuFuncSetAttribute failed";
         return false;
     }
-    int bps = 0;
-    if (dr.occupancy(&bps, k.fn, kThreads, (size_t)k.smem_bytes) != CUDA_SUCCESS || bps < 1) bps = 1;
-    k.blocks_per_sm = bps;
     k.device = device;
     return true;
 }
@@ -1371,14 +1258,6 @@ bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* 
     const int tw = k->tw, th = k->th;
     j.gx = (unsigned)((d.W + tw - 1) / tw);
     j.gy = (unsigned)((d.H + th - 1) / th);
-    // persistent grid: every resident CTA slot once, at most one per tile
-    int sms = 1;
-    if (load_module && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-        cudaGetLastError();
-        sms = 1;
-    }
-    j.sms = sms;
-    j.grid = (unsigned)std::min<long long>((long long)j.gx * j.gy, (long long)sms * k->blocks_per_sm);
     int ix0 = 0, iy0 = 0, ix1 = (int)j.gx - 1, iy1 = (int)j.gy - 1;
     std::vector<bool> is_in(d.n_buf, false);
     for (int e = 0; e < d.n_in; ++e) is_in[d.in[e].buf] = true;
@@ -1401,17 +1280,15 @@ bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* 
 
 cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s) {
     void* args[] = {const_cast<HvxJitParams*>(&j.p)};
-    const CUresult r = driver().launch(j.k->fn, j.grid, 1, 1, kThreads, 1, 1,
+    const CUresult r = driver().launch(j.k->fn, j.gx, j.gy, 1, kThreads, 1, 1,
                                        (unsigned)j.k->smem_bytes, (CUstream)s, args, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
 cudaError_t jit_launch_batch(const JitKernel* k, const HvxJitParams* params, const int* tile_start,
-                             int n, int total_tiles, int sms, cudaStream_t s) {
-    void* args[] = {&params, &tile_start, &n, &total_tiles};
-    const unsigned grid =
-        (unsigned)std::min<long long>(total_tiles, (long long)std::max(sms, 1) * k->blocks_per_sm);
-    const CUresult r = driver().launch(k->fn_batch, grid, 1, 1, kThreads, 1, 1,
+                             int n, int total_tiles, cudaStream_t s) {
+    void* args[] = {&params, &tile_start, &n};
+    const CUresult r = driver().launch(k->fn_batch, (unsigned)total_tiles, 1, 1, kThreads, 1, 1,
                                        (unsigned)k->smem_bytes, (CUstream)s, args, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }

@@ -191,9 +191,7 @@ struct JitKernel;
 struct JitLaunch {
     JitKernel* k = nullptr;  // cached for the life of the process
     HvxJitParams p;
-    unsigned gx = 0, gy = 0;  // tiles
-    unsigned grid = 0;        // persistent CTAs
-    int sms = 1;
+    unsigned gx = 0, gy = 0;
 };
 
 // A fused group: ops run by one kernel launch.
@@ -304,7 +302,7 @@ cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s);
 // n images' groups that run the same generated kernel, in one launch: params
 // and tile_start (n + 1 prefix sums of tiles per image) in device memory
 cudaError_t jit_launch_batch(const JitKernel* k, const HvxJitParams* params, const int* tile_start,
-                             int n, int total_tiles, int sms, cudaStream_t s);
+                             int n, int total_tiles, cudaStream_t s);
 void jit_tile(const JitKernel* k, int* tw, int* th);
 const std::string& jit_source(const JitLaunch& j);
 

@@ -941,7 +941,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
         return cuda_status(jit_launch_batch(
             hit->jk, reinterpret_cast<const HvxJitParams*>(base),
             reinterpret_cast<const int*>(base + (size_t)hit->n * sizeof(HvxJitParams)), hit->n,
-            hit->total_tiles, ctx->num_sms, s));
+            hit->total_tiles, s));
     }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
 }
