@@ -172,6 +172,23 @@ def recorded_traffic(kernel: str, frames: int):
     return int(rec["dram_read_bytes"] + rec["dram_write_bytes"])
 
 
+# Thread-instructions per output pixel of edge_batch_kernel<MASK_PHASE>
+# (ncu smsp__inst_executed.sum x 32 / pixels of one 64-frame launch; the
+# capture is summarised in profiles/edge_batch_kernel_1080p.md).
+EDGE_INSTR_PER_PX = 49.9
+
+
+def issue_roofline(mpix_s, instr_per_px, clocks):
+    """Instruction-issue roofline of a kernel bound by issue: achieved
+    thread-instructions/s against 152 SMs x 4 schedulers x 32 lanes x clock."""
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = 152 * 4 * 32 * mhz * 1e6 / 1e12
+    ach = mpix_s * 1e6 * instr_per_px / 1e12
+    return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2),
+            "unit": "T thread-instr/s", "frac": round(ach / peak, 4),
+            "instr_per_px": instr_per_px, "sm_mhz": mhz}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -439,7 +456,12 @@ def run_edge(args, world, rank, local, torch):
                      "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
                      "traffic": recorded_traffic("edge_batch_kernel<MASK_PHASE>", F),
                      "peak_source": src, "kernel": "edge_batch_kernel",
-                     "algorithmic_bytes_per_launch": ext_bytes},
+                     "algorithmic_bytes_per_launch": ext_bytes,
+                     # the bound that holds: instruction issue (the kernel's
+                     # instructions per pixel from its ncu capture, times the
+                     # live pixel rate, against 152 SMs x 4 schedulers x 32
+                     # lanes x the sampled SM clock)
+                     "issue": issue_roofline(value / world, EDGE_INSTR_PER_PX, clocks)},
         "e2e": {"value": round(e2e_v, 1), "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(F * H_ * pitch),
                 "d2h_bytes_per_step": int(2 * F * H_ * pitch)},
