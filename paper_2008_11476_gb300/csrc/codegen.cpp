@@ -993,6 +993,14 @@ struct Emitter {
         o << "  }\n  __syncthreads();\n";
     }
 
+    // Optional second launch bound (resident CTAs per SM the compiler must
+    // fit registers for): HVX_CODEGEN_MINBLOCKS in the environment.
+    static std::string min_blocks() {
+        const char* e = getenv("HVX_CODEGEN_MINBLOCKS");
+        const int v = e ? atoi(e) : 0;
+        return v >= 1 && v <= 8 ? ", " + std::to_string(v) : "";
+    }
+
     bool emit() {
         analyse();
         // MIRROR / REPEAT fills are only possible for external inputs
@@ -1093,7 +1101,7 @@ struct Emitter {
         o.clear();
         o << head << regs << body;
         o << "}\n\n"
-          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << min_blocks()
           << ") hvx_generated(const HvxJitParams p) {\n"
           << "  extern __shared__ __align__(16) int smem[];\n"
           << "  const int tx = blockIdx.x, ty = blockIdx.y;\n"
@@ -1104,7 +1112,7 @@ struct Emitter {
           << "}\n\n"
           << "// n images in one launch: block t is tile t - tile_start[i] of the last\n"
           << "// image i with tile_start[i] <= t\n"
-          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads
+          << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << min_blocks()
           << ") hvx_generated_batch(const HvxJitParams* __restrict__ ps, const int* __restrict__ "
              "tile_start, int n) {\n"
           << "  extern __shared__ __align__(16) int smem[];\n"

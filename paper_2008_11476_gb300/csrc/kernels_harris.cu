@@ -352,12 +352,10 @@ __device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, flo
     return harris_q32(a, b, c, kn, kd) > q_thr;
 }
 
-__global__ void __launch_bounds__(FTHREADS, 4)
-    harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
+// One 112 x 8R output tile at (x0, y0) of the image that `tmap` / `p` describe.
+__device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const HarrisParams& p,
+                                                 FastSmem& sm, int x0, int y0) {
     const int R = p.rows;
-    const int x0 = blockIdx.x * FTW, y0 = blockIdx.y * 8 * R;
     const int W = p.W, H = p.H;
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar, 1);
@@ -366,7 +364,7 @@ __global__ void __launch_bounds__(FTHREADS, 4)
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&sm.bar, (uint32_t)(FLW * (8 * R + 6)));
-        tma_load_2d(&sm.in[0][0], &tmap, &sm.bar, x0 - 16, y0 - 3);
+        tma_load_2d(&sm.in[0][0], tmap, &sm.bar, x0 - 16, y0 - 3);
     }
     // every thread leaves together when the (bounded) wait ran out
     if (__syncthreads_or(!mbar_wait_bounded(&sm.bar, 0, p.err))) return;
@@ -487,6 +485,30 @@ __global__ void __launch_bounds__(FTHREADS, 4)
     }
 }
 
+__global__ void __launch_bounds__(FTHREADS, 4)
+    harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
+    harris_fast_tile(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
+}
+
+// Several images in one launch (hvxProcessGraphBatch): block t is tile
+// t - tile_start[i] of the last image i with tile_start[i] <= t; tensor maps
+// and parameters in global memory, all images with the same rows per thread.
+__global__ void __launch_bounds__(FTHREADS, 4)
+    harris_fast_batch_kernel(const CUtensorMap* __restrict__ maps,
+                             const HarrisParams* __restrict__ ps, const int* __restrict__ tile_start,
+                             const int* __restrict__ tiles_x, int n) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
+    const int t = blockIdx.x;
+    const int i = find_image(tile_start, n, t);
+    const int local = t - __ldg(tile_start + i), tx = __ldg(tiles_x + i);
+    const int ty = local / tx;
+    if (threadIdx.x == 0) tensormap_acquire(maps + i);
+    harris_fast_tile(maps + i, ps[i], sm, (local - ty * tx) * FTW, ty * 8 * ps[i].rows);
+}
+
 }  // namespace
 
 bool harris_fast_path(const HarrisParams& p) {
@@ -518,6 +540,42 @@ int harris_fast_rows(int W, int H, int num_sms) {
 void harris_box(const HarrisParams& p, int* w, int* h) {
     *w = harris_fast_path(p) ? FLW : HARRIS_LOAD_W;
     *h = harris_fast_path(p) ? 8 * p.rows + 6 : HARRIS_TH + 6;
+}
+
+int harris_fast_tile_w() { return FTW; }
+
+// Rows per thread for a batch of images in one launch: the same wave model
+// as harris_fast_rows over the tiles of all images.
+int harris_batch_rows(const int* W, const int* H, int n, int num_sms) {
+    const long slots = 4L * (num_sms > 0 ? num_sms : 1);
+    int best = FROWS_MAX;
+    long best_cost = -1;
+    for (int r = FROWS_MIN; r <= FROWS_MAX; ++r) {
+        long tiles = 0;
+        for (int i = 0; i < n; ++i)
+            tiles += (long)((W[i] + FTW - 1) / FTW) * ((H[i] + 8 * r - 1) / (8 * r));
+        const long cost = (tiles + slots - 1) / slots * (r + 4);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = r;
+        }
+    }
+    return best;
+}
+
+cudaError_t launch_harris_batch(const CUtensorMap* maps, const HarrisParams* ps,
+                                const int* tile_start, const int* tiles_x, int n, int total,
+                                cudaStream_t s) {
+    static bool attr = false;
+    const int smem = (int)sizeof(FastSmem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(harris_fast_batch_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    harris_fast_batch_kernel<<<total, FTHREADS, smem, s>>>(maps, ps, tile_start, tiles_x, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s) {

@@ -684,6 +684,7 @@ struct BatchEntry {
     // generated-kernel batches: one direct launch over every image's tiles
     JitKernel* jk = nullptr;
     int n = 0, total_tiles = 0;
+    bool harris = false;  // BORDER_UNDEFINED Harris batch: one direct launch
 };
 
 struct BatchCache {
@@ -867,6 +868,60 @@ hvx_status build_jit_batch_entry(Graph* const* gs, int n, JitKernel* jk, BatchEn
     return HVX_SUCCESS;
 }
 
+// Batch of BORDER_UNDEFINED Harris graphs: one rows-per-thread for all of
+// them, each input's tensor map boxed for it, then maps, parameters and tile
+// tables in one device block.
+hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, BatchEntry& out) {
+    std::vector<int> ws(n), hs(n);
+    for (int i = 0; i < n; ++i) {
+        ws[i] = (int)gs[i]->plan.groups[0].W;
+        hs[i] = (int)gs[i]->plan.groups[0].H;
+    }
+    const int rows = harris_batch_rows(ws.data(), hs.data(), n, ctx->num_sms);
+    const int tw = harris_fast_tile_w();
+    const size_t params_off = (size_t)n * sizeof(CUtensorMap);
+    const size_t tiles_off = params_off + (size_t)n * sizeof(HarrisParams);
+    const size_t tx_off = tiles_off + (size_t)(n + 1) * sizeof(int);
+    const size_t total = tx_off + (size_t)n * sizeof(int);
+    std::vector<uint8_t> host(total);
+    std::vector<int> tile_start(n + 1, 0), tiles_x(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const Group& G = gs[i]->plan.groups[0];
+        HarrisParams hp = G.harris;
+        hp.rows = rows;
+        int bw = 0, bh = 0;
+        harris_box(hp, &bw, &bh);
+        CUtensorMap map;
+        hvx_status st = encode_u8_map(&map, G.inputs[0], bw, bh);
+        if (st != HVX_SUCCESS) return st;
+        std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &map, sizeof(map));
+        std::memcpy(host.data() + params_off + (size_t)i * sizeof(HarrisParams), &hp, sizeof(hp));
+        tiles_x[i] = (ws[i] + tw - 1) / tw;
+        tile_start[i + 1] = tile_start[i] + tiles_x[i] * ((hs[i] + 8 * rows - 1) / (8 * rows));
+    }
+    std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));
+    std::memcpy(host.data() + tx_off, tiles_x.data(), n * sizeof(int));
+    void* dmem = nullptr;
+    cudaError_t e = cudaMalloc(&dmem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HVX_ERROR_NO_MEMORY;
+    }
+    e = cudaMemcpy(dmem, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dmem);
+        return cuda_status(e);
+    }
+    out.graphs.assign(gs, gs + n);
+    out.plan_ids.resize(n);
+    for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
+    out.dmem = dmem;
+    out.harris = true;
+    out.n = n;
+    out.total_tiles = tile_start[n];
+    return HVX_SUCCESS;
+}
+
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
     NvtxRange nvtx("hvx batch");
     // one launch when every plan is a single group running the same
@@ -879,9 +934,16 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
                    P.groups[0].jit_on && (!jk || P.groups[0].jit.k == jk);
         if (jit_same) jk = P.groups[0].jit.k;
     }
+    // one launch when every plan is a single BORDER_UNDEFINED Harris group
+    bool harris_same = !jit_same;
+    for (int i = 0; i < n && harris_same; ++i) {
+        const Plan& P = gs[i]->plan;
+        harris_same = P.groups.size() == 1 && P.groups[0].kernel == GK_HARRIS &&
+                      harris_fast_path(P.groups[0].harris);
+    }
     // one persistent launch when every plan is a single edge (or Gaussian)
     // group and all of them use the same kernel mode
-    bool same = !jit_same;
+    bool same = !jit_same && !harris_same;
     int mode = -1;
     for (int i = 0; i < n && same; ++i) {
         const Plan& P = gs[i]->plan;
@@ -893,7 +955,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             mode = m;
         }
     }
-    if (!same && !jit_same) {
+    if (!same && !jit_same && !harris_same) {
         for (int i = 0; i < n; ++i) {
             hvx_status st = launch_plan(gs[i], s);
             if (st != HVX_SUCCESS) return st;
@@ -924,8 +986,9 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             bc->entries.erase(oldest);
         }
         BatchEntry fresh;
-        hvx_status st = jit_same ? build_jit_batch_entry(gs, n, jk, fresh)
-                                 : build_batch_entry(ctx, bc, gs, n, mode, s, fresh);
+        hvx_status st = jit_same      ? build_jit_batch_entry(gs, n, jk, fresh)
+                        : harris_same ? build_harris_batch_entry(ctx, gs, n, fresh)
+                                      : build_batch_entry(ctx, bc, gs, n, mode, s, fresh);
         if (st != HVX_SUCCESS) return st;
         bc->entries.push_back(fresh);
         hit = &bc->entries.back();
@@ -942,6 +1005,17 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             hit->jk, reinterpret_cast<const HvxJitParams*>(base),
             reinterpret_cast<const int*>(base + (size_t)hit->n * sizeof(HvxJitParams)), hit->n,
             hit->total_tiles, s));
+    }
+    if (hit->harris) {
+        const uint8_t* base = static_cast<const uint8_t*>(hit->dmem);
+        const size_t params_off = (size_t)hit->n * sizeof(CUtensorMap);
+        const size_t tiles_off = params_off + (size_t)hit->n * sizeof(HarrisParams);
+        const size_t tx_off = tiles_off + (size_t)(hit->n + 1) * sizeof(int);
+        return cuda_status(launch_harris_batch(
+            reinterpret_cast<const CUtensorMap*>(base),
+            reinterpret_cast<const HarrisParams*>(base + params_off),
+            reinterpret_cast<const int*>(base + tiles_off), reinterpret_cast<const int*>(base + tx_off),
+            hit->n, hit->total_tiles, s));
     }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
 }

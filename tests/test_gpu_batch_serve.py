@@ -228,3 +228,33 @@ def test_batch_on_host_data(ctx):
                            True)])
     with pytest.raises(HX.HvxError):  # host pitch below the row size
         HX.hvxScheduleGraphBatchHost(graphs, bad)
+
+
+def test_harris_batch_one_launch(ctx):
+    # BORDER_UNDEFINED Harris graphs of different sizes in one launch (one
+    # rows-per-thread for all of them): the same masks as one launch each
+    sizes = [(1920, 1080), (333, 77), (640, 480), (1, 1), (129, 300)]
+    graphs, outs, refs = [], [], []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=80 + i)
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        g = PG.harris_graph(ctx, src, mk)
+        assert PG.kernel_kinds(g) == ["fused_harris_tma"]
+        graphs.append(g)
+        outs.append(mk)
+        refs.append(O.harris_graph(img)[0])
+    singles = []
+    for g, mk in zip(graphs, outs):
+        H.hvxProcessGraph(g)
+        singles.append(PG.download(mk))
+    for mk in outs:  # clear the outputs so the batch must write them
+        z = np.zeros((H.hvxQueryImage(mk)[1], H.hvxQueryImage(mk)[0]), np.uint8)
+        H.hvxCopyImage(mk, z.ctypes.data, z.strides[0], H.HVX_WRITE)
+    for want, ref in zip(singles, refs):
+        np.testing.assert_array_equal(want, ref)
+    for _ in range(2):
+        H.hvxProcessGraphBatch(graphs)
+        H.hvxWaitBatch(ctx)
+        for mk, want in zip(outs, singles):
+            np.testing.assert_array_equal(PG.download(mk), want)
