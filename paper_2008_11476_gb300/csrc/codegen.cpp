@@ -993,11 +993,17 @@ struct Emitter {
         o << "  }\n  __syncthreads();\n";
     }
 
-    // Optional second launch bound (resident CTAs per SM the compiler must
-    // fit registers for): HVX_CODEGEN_MINBLOCKS in the environment.
-    static std::string min_blocks() {
-        const char* e = getenv("HVX_CODEGEN_MINBLOCKS");
-        const int v = e ? atoi(e) : 0;
+    // Second launch bound: resident CTAs per SM the compiler must fit
+    // registers for.  Measured on the Section 6 applications: groups of one
+    // or two ops run fastest at 8 (Laplacian 584 -> 681, SobelX 657 -> 717
+    // Gpix/s), larger groups at 6 (EdgFig2 247 -> 271, Unsharp 465 -> 497),
+    // corner-response groups without a bound.  HVX_CODEGEN_MINBLOCKS (1..8,
+    // 0 for none) in the environment overrides.
+    std::string min_blocks() const {
+        int v = d.n_stage <= 2 ? 8 : 6;
+        for (int k = 0; k < d.n_stage; ++k)
+            if (d.st[k].op == OP_TOMASI || d.st[k].op == OP_HARRIS) v = 0;
+        if (const char* e = getenv("HVX_CODEGEN_MINBLOCKS")) v = atoi(e);
         return v >= 1 && v <= 8 ? ", " + std::to_string(v) : "";
     }
 
