@@ -98,6 +98,7 @@ def _declare(L):
     L.orc_minmaxloc.argtypes = [P, I, I, I, R, ctypes.POINTER(ctypes.c_int64)]
     L.orc_histogram.argtypes = [P, I, I, R, I, I, I, P]
     L.orc_equalize_hist.argtypes = [P, P, I, I, R, R]
+    L.orc_convert_depth.argtypes = [P, I, P, I, I, I, I, I, R, R]
     for name in ("orc_gaussian3x3", "orc_box3x3", "orc_morph3x3", "orc_bitwise",
                  "orc_convolve_u8_u8", "orc_tomasi_response",
                  "orc_sobel3x3", "orc_window_sum_s32",
@@ -105,7 +106,7 @@ def _declare(L):
                  "orc_channel_extract_uyvy", "orc_arith", "orc_mul_s16_s32",
                  "orc_harris_response", "orc_harris_graph", "orc_edge_graph",
                  "orc_multiply", "orc_mean_stddev", "orc_minmaxloc", "orc_histogram",
-                 "orc_equalize_hist"):
+                 "orc_equalize_hist", "orc_convert_depth"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -350,6 +351,18 @@ def equalize_hist(src) -> Img:
     out = np.empty(A.data.shape, np.uint8)
     vo = (ctypes.c_int * 4)()
     _check(lib().orc_equalize_hist(_p(A.data), _p(out), A.w, A.h, _rect(A.rect), vo))
+    return Img(out, tuple(vo))
+
+
+def convert_depth(src, out_dtype, shift=0, saturate=True) -> Img:
+    """ConvertDepth (Copy when the formats agree): U8 -> S16 shifts left,
+    S16 -> U8 shifts right (floor) then wraps or saturates."""
+    A = _as_img(src)
+    out = np.empty(A.data.shape, out_dtype)
+    vo = (ctypes.c_int * 4)()
+    _check(lib().orc_convert_depth(_p(A.data), _FMT_OF[A.data.dtype], _p(out),
+                                   _FMT_OF[np.dtype(out_dtype)], A.w, A.h, shift, int(saturate),
+                                   _rect(A.rect), vo))
     return Img(out, tuple(vo))
 
 

@@ -118,6 +118,7 @@ _IN_FMTS = {
     "add": [("U8", "S16"), ("U8", "S16")], "subtract": [("U8", "S16"), ("U8", "S16")],
     "absdiff": [("U8", "S16"), ("U8", "S16")],
     "multiply": [("U8", "S16"), ("U8", "S16")],
+    "convert_depth": [("U8", "S16")], "copy": [("U8", "S16")],
     "dilate3x3": [("U8",)], "erode3x3": [("U8",)], "median3x3": [("U8",)],
     "and": [("U8",), ("U8",)], "or": [("U8",), ("U8",)], "xor": [("U8",), ("U8",)],
     "not": [("U8",)],
@@ -351,6 +352,9 @@ def run(g: GraphDesc, inputs: dict, dce: bool = True) -> dict:
             r = O.morph3x3(x[0], _MORPH[k], b, c)
         elif k in _BITS:
             r = O.bitwise(x[0], x[1] if k != "not" else None, _BITS[k])
+        elif k in ("convert_depth", "copy"):
+            r = O.convert_depth(x[0], _NPFMT[g.data[op.out].fmt], p.get("shift", 0),
+                                p.get("policy", "saturate") == "saturate")
         elif k == "multiply":
             r = O.multiply(x[0], x[1], p.get("scale", 1.0), _NPFMT[g.data[op.out].fmt],
                            p.get("policy", "saturate") == "saturate",

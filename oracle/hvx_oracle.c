@@ -477,6 +477,32 @@ int orc_multiply(const void* a, int fa, const void* b, int fb, void* out, int fo
     return ORC_OK;
 }
 
+/* ConvertDepth (Table 2 point operator; OpenVX semantics, which the paper
+ * does not print): U8 -> S16 is v << shift (exact); S16 -> U8 is v >> shift
+ * (arithmetic, i.e. floor division by 2^shift), then wrapped to the low 8
+ * bits or saturated to 0..255.  Same format in and out is Copy (shift 0).
+ * 0 <= shift < 8. */
+int orc_convert_depth(const void* in, int fi, void* out, int fo, int w, int h, int shift,
+                      int saturate, const int vin[4], int vout[4]) {
+    if (shift < 0 || shift > 7) return ORC_ERR;
+    memset(out, 0, (size_t)w * h * (fo == ORC_U8 ? 1 : 2));
+    for (int y = vin[1]; y < vin[3]; ++y)
+        for (int x = vin[0]; x < vin[2]; ++x) {
+            size_t i = (size_t)y * w + x;
+            int64_t v = (int64_t)load_as_double(in, fi, i);
+            int64_t r;
+            if (fi == fo)
+                r = v;
+            else if (fo == ORC_S16)
+                r = v * (1 << shift);
+            else
+                r = (int64_t)floor((double)v / (double)(1 << shift));
+            store_int(out, fo, i, sat_or_wrap(r, fo, saturate));
+        }
+    rect_copy(vout, vin);
+    return ORC_OK;
+}
+
 /* Bitwise point operators on U8 (Table 2: And, Or, Xor, Not): op 0 = a & b,
  * 1 = a | b, 2 = a ^ b, 3 = ~a (b unused, may be NULL). */
 int orc_bitwise(const uint8_t* a, const uint8_t* b, uint8_t* out, int w, int h, int op,

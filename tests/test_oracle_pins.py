@@ -727,3 +727,22 @@ def test_equalize_hist_closed_forms_and_brute_force(orc):
         want = ((cv - cmin) * 255 * 2 + (n - cmin)) // (2 * (n - cmin))
         assert (out[a == v] == want).all()
     assert (np.diff(out.ravel()[np.argsort(a.ravel(), kind="stable")].astype(int)) >= 0).all()
+
+
+# --- ConvertDepth / Copy (Table 2 point operators) ---------------------------
+
+def test_convert_depth_exhaustive(orc):
+    u8 = np.arange(256, dtype=np.uint8).reshape(16, 16)
+    s16 = np.arange(-32768, 32768, dtype=np.int64).astype(np.int16).reshape(256, 256)
+    for shift in range(8):
+        up = orc.convert_depth(u8, np.int16, shift).data
+        assert (up.astype(np.int64) == u8.astype(np.int64) * 2 ** shift).all()
+        down_sat = orc.convert_depth(s16, np.uint8, shift, True).data.astype(np.int64)
+        down_wrap = orc.convert_depth(s16, np.uint8, shift, False).data.astype(np.int64)
+        q = np.floor_divide(s16.astype(np.int64), 2 ** shift)   # floor, also for negatives
+        assert (down_sat == np.clip(q, 0, 255)).all()
+        assert (down_wrap == np.mod(q, 256)).all()
+    assert (orc.convert_depth(u8, np.uint8).data == u8).all()          # Copy
+    assert (orc.convert_depth(s16, np.int16).data == s16).all()
+    with pytest.raises(Exception):
+        orc.convert_depth(u8, np.int16, 8)
