@@ -356,6 +356,16 @@ hvx_node hvxAddNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_i
 hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 
+/* Copy (point, Table 2): U8 -> U8 or S16 -> S16, unchanged. */
+hvx_node hvxCopyNode(hvx_graph g, hvx_image in, hvx_image out);
+
+/* ConvertDepth (point, Table 2): U8 -> S16 is v << shift; S16 -> U8 is
+ * v >> shift (arithmetic: floor division by 2^shift), then wrapped to 8 bits
+ * or saturated to 0..255 per policy.  0 <= shift <= 7; NULL
+ * (HVX_ERROR_INVALID_PARAMETERS) otherwise. */
+hvx_node hvxConvertDepthNode(hvx_graph g, hvx_image in, hvx_image out, int32_t policy,
+                             int32_t shift);
+
 /* Multiply (point, Table 2): U8 or S16 inputs -> U8 or S16 output (formats as
  * for Add).  out = a * b * scale, taken exactly for the binary32 scale given
  * (0 <= scale <= 65536), rounded once per rounding (HVX_ROUND_TO_ZERO or

@@ -866,6 +866,23 @@ hvx_node hvxMultiplyNode(hvx_graph g, hvx_image a, hvx_image b, float scale, int
     return add_node(g, N_MULTIPLY, {a, b}, {out}, 1, p);
 }
 
+hvx_node hvxCopyNode(hvx_graph g, hvx_image in, hvx_image out) {
+    return add_node(g, N_COPY, {in}, {out}, 1, NodeParams());
+}
+
+hvx_node hvxConvertDepthNode(hvx_graph g, hvx_image in, hvx_image out, int32_t policy,
+                             int32_t shift) {
+    if (!ok_graph(g)) return nullptr;
+    if ((policy != HVX_POLICY_WRAP && policy != HVX_POLICY_SATURATE) || shift < 0 || shift > 7) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        return nullptr;
+    }
+    NodeParams p;
+    p.policy = policy;
+    p.shift = shift;
+    return add_node(g, N_CONVDEPTH, {in}, {out}, 1, p);
+}
+
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out) {
     return arith_node(g, N_ABSDIFF, a, b, HVX_POLICY_SATURATE, out);
 }

@@ -578,6 +578,12 @@ struct Emitter {
                        lit64(st.k0) + ", " + lit64(st.k1) + "), " + lit64(st.k1) + "))";
             case OP_TOMASI:
                 return "__float_as_int(tomasi_response_f32(" + a + ", " + b + ", " + c + "))";
+            case OP_CONVDEPTH:
+                if (st.i1 == st.i3) return a;
+                if (st.i1 == HVX_DF_S16)
+                    return "(int)((unsigned)" + a + " << " + std::to_string(st.i0) + ")";
+                return st.i2 ? "sat_u8(" + a + " >> " + std::to_string(st.i0) + ")"
+                             : "((" + a + " >> " + std::to_string(st.i0) + ") & 0xFF)";
             case OP_MULTIPLY: {
                 const std::string v = "multiply_scaled(" + a + ", " + b + ", " + lit64(st.k0) +
                                       ", " + std::to_string(st.i3) + ", " +

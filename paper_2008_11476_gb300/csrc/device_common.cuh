@@ -163,6 +163,10 @@ __device__ __forceinline__ int32_t eval_point(const P& st, int32_t a, int32_t b,
         case OP_HARRIS:
             return __float_as_int(ratio_to_float(harris_q(a, b, c, st.k0, st.k1), st.k1));
         case OP_TOMASI: return __float_as_int(tomasi_response_f32(a, b, c));
+        case OP_CONVDEPTH:
+            if (st.i1 == st.i3) return a;                    // Copy
+            if (st.i1 == HVX_DF_S16) return (int32_t)((uint32_t)a << st.i0);  // U8 -> S16
+            return st.i2 ? sat_u8(a >> st.i0) : ((a >> st.i0) & 0xFF);    // S16 -> U8
         case OP_MULTIPLY: {
             const long long v = multiply_scaled(a, b, st.k0, st.i3, st.i2 != 0);
             if (st.i1 == HVX_DF_U8) return st.i0 ? sat64_u8(v) : (int32_t)(v & 0xFF);

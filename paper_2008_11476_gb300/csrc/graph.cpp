@@ -71,6 +71,7 @@ const char* op_name(int kind) {
         case OP_MINMAX: return "minmaxloc";
         case OP_HIST: return "histogram";
         case OP_EQHIST: return "equalize_hist";
+        case OP_CONVDEPTH: return "convert_depth";
     }
     return "?";
 }
@@ -138,6 +139,8 @@ void lower(Graph* g, Plan& P) {
             case N_MINMAX: add(OP_MINMAX, 0, 0); break;
             case N_HIST: add(OP_HIST, 0, 0); break;
             case N_EQHIST: add(OP_EQHIST, 0, 0); break;
+            case N_COPY:
+            case N_CONVDEPTH: add(OP_CONVDEPTH, 0, 0); break;
             case N_SOBEL:
                 if (!n->out[0] && !n->out[1]) fail(HVX_ERROR_INVALID_PARAMETERS);
                 if (n->out[0]) add(OP_SOBEL_X, 0, 1);
@@ -251,6 +254,15 @@ void infer(Op& op) {
         case OP_MINMAX: need(0, {HVX_DF_U8, HVX_DF_S16}); of = HVX_DF_RESULT; break;
         case OP_HIST: need(0, {HVX_DF_U8}); of = HVX_DF_RESULT; break;
         case OP_EQHIST: need(0, {HVX_DF_U8}); of = HVX_DF_U8; break;
+        case OP_CONVDEPTH: {
+            // Copy keeps the format; ConvertDepth goes U8 <-> S16
+            need(0, {HVX_DF_U8, HVX_DF_S16});
+            if (op.node->kind == N_COPY)
+                of = in[0]->fmt;
+            else
+                of = in[0]->fmt == HVX_DF_U8 ? HVX_DF_S16 : HVX_DF_U8;
+            break;
+        }
         default: fail(HVX_ERROR_INVALID_PARAMETERS);
     }
     if (op.kind != OP_CHX)

@@ -122,6 +122,8 @@ enum NodeKind : int {
     N_MINMAX,
     N_HIST,
     N_EQHIST,
+    N_COPY,
+    N_CONVDEPTH,
 };
 
 struct NodeParams {

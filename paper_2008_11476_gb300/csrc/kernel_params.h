@@ -40,6 +40,7 @@ enum OpKind : int {
     OP_HIST,
     // EqualizeHist (histogram + point): its own two launches
     OP_EQHIST,
+    OP_CONVDEPTH,  // ConvertDepth / Copy
 };
 
 #ifdef __CUDACC__

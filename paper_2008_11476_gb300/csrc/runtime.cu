@@ -105,6 +105,12 @@ void fill_point_params(T& st, const Op& op) {
             break;
         }
         case OP_CHX: st.i0 = p.channel; break;
+        case OP_CONVDEPTH:
+            st.i0 = p.shift;
+            st.i1 = op.out->fmt;
+            st.i2 = p.policy == HVX_POLICY_SATURATE;
+            st.i3 = op.in[0]->fmt;
+            break;
         default: break;
     }
 }

@@ -142,6 +142,8 @@ _SIGS = {
     "hvxSubtractNode": (P, [P, P, P, I32, P]),
     "hvxAbsDiffNode": (P, [P, P, P, P]),
     "hvxMultiplyNode": (P, [P, P, P, ctypes.c_float, I32, I32, P]),
+    "hvxCopyNode": (P, [P, P, P]),
+    "hvxConvertDepthNode": (P, [P, P, P, I32, I32]),
     "hvxMeanStdDevNode": (P, [P, P]),
     "hvxMinMaxLocNode": (P, [P, P]),
     "hvxHistogramNode": (P, [P, P, I32, I32, I32]),
@@ -430,6 +432,14 @@ def hvxAddNode(g, a, b, policy, o):
 
 def hvxSubtractNode(g, a, b, policy, o):
     return _node(lib().hvxSubtractNode(g, a, b, policy, o), g, "hvxSubtractNode")
+
+
+def hvxCopyNode(g, i, o):
+    return _node(lib().hvxCopyNode(g, i, o), g, "hvxCopyNode")
+
+
+def hvxConvertDepthNode(g, i, o, policy, shift):
+    return _node(lib().hvxConvertDepthNode(g, i, o, policy, shift), g, "hvxConvertDepthNode")
 
 
 def hvxMultiplyNode(g, a, b, scale, policy, rounding, o):

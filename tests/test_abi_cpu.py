@@ -436,3 +436,25 @@ def test_global_operator_plans(pctx):
     H.hvxHistogramNode(g, s16, 16, 0, 256)
     with pytest.raises(H.HvxError):  # histograms take U8 only
         H.hvxVerifyGraph(g)
+
+
+def test_convert_depth_and_copy_plans(pctx):
+    a = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8)
+    s = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    for bad in ((H.HVX_POLICY_WRAP, 8), (H.HVX_POLICY_WRAP, -1), (5, 1)):
+        with pytest.raises(H.HvxError):
+            H.hvxConvertDepthNode(g, a, H.hvxCreateVirtualImage(g), *bad)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxConvertDepthNode(g, a, s, H.HVX_POLICY_SATURATE, 2)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["plain_point"]
+    g = H.hvxCreateGraph(pctx)
+    H.hvxCopyNode(g, a, s)  # Copy keeps the format: U8 -> S16 is rejected
+    with pytest.raises(H.HvxError):
+        H.hvxVerifyGraph(g)
+    g = H.hvxCreateGraph(pctx)
+    H.hvxConvertDepthNode(g, a, H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8),
+                          H.HVX_POLICY_SATURATE, 0)
+    with pytest.raises(H.HvxError):  # ConvertDepth changes the depth
+        H.hvxVerifyGraph(g)

@@ -30,7 +30,7 @@ def random_graph(seed):
         u8 = [k for k, f in fmt.items() if f == "U8"]
         s16 = [k for k, f in fmt.items() if f == "S16"]
         kinds = ["gaussian3x3", "box3x3", "dilate3x3", "erode3x3", "median3x3", "convolve",
-                 "sobel3x3", "not", "threshold", "and", "add"]
+                 "sobel3x3", "not", "threshold", "and", "add", "depth"]
         if s16:
             kinds += ["magnitude", "threshold16", "add16"]
         if len(sobel_out) >= 2:
@@ -99,6 +99,17 @@ def random_graph(seed):
         elif k == "magnitude":
             nodes.append((k, [pick(s16), pick(s16)], [o], p, ["S16"]))
             fmt[o] = "S16"
+        elif k == "depth":
+            src = pick(u8 + s16)
+            if rng.random() < 0.3:
+                nodes.append(("copy", [src], [o], p, [fmt[src]]))
+                fmt[o] = fmt[src]
+            else:
+                p.update(shift=int(rng.integers(0, 8)),
+                         policy=["saturate", "wrap"][int(rng.integers(2))])
+                f = "S16" if fmt[src] == "U8" else "U8"
+                nodes.append(("convert_depth", [src], [o], p, [f]))
+                fmt[o] = f
         elif k == "phase":
             so = sorted(sobel_out)
             nodes.append((k, [pick(so), pick(so)], [o], p, ["U8"]))
@@ -174,6 +185,10 @@ def build_hvx(ctx, src, nodes, fmt, external, w, h):
                                   else H.HVX_ROUND_TO_ZERO, o)
         elif k == "magnitude":
             n = H.hvxMagnitudeNode(g, a[0], a[1], o)
+        elif k == "copy":
+            n = H.hvxCopyNode(g, a[0], o)
+        elif k == "convert_depth":
+            n = H.hvxConvertDepthNode(g, a[0], o, pol[p["policy"]], p["shift"])
         elif k == "phase":
             n = H.hvxPhaseNode(g, a[0], a[1], o)
         if "border" in p:
@@ -388,3 +403,32 @@ def test_multiply_node(ctx, fmts, scale):
                 H.hvxProcessGraph(g)
                 np.testing.assert_array_equal(PG.download(out), want)
                 H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("codegen", [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE])
+@pytest.mark.parametrize("w,h", [(1, 1), (97, 31), (640, 480)])
+def test_convert_depth_and_copy(ctx, w, h, codegen):
+    import oracle as O
+    rng = np.random.default_rng(w)
+    u8 = rng.integers(0, 256, (h, w)).astype(np.uint8)
+    s16 = rng.integers(-32768, 32768, (h, w)).astype(np.int16)
+    for arr, fin, fout, npout in ((u8, H.HVX_DF_U8, H.HVX_DF_S16, np.int16),
+                                  (s16, H.HVX_DF_S16, H.HVX_DF_U8, np.uint8)):
+        src = PG.upload(ctx, arr, fin)
+        for shift in (0, 3, 7):
+            for pol, sat in ((H.HVX_POLICY_SATURATE, True), (H.HVX_POLICY_WRAP, False)):
+                for fused in (False, True):
+                    out = PG.empty(ctx, w, h, fout)
+                    g = H.hvxCreateGraph(ctx)
+                    if fused:  # behind a Copy and before nothing: one staged-tile group
+                        c = H.hvxCreateVirtualImage(g)
+                        H.hvxCopyNode(g, src, c)
+                        H.hvxConvertDepthNode(g, c, out, pol, shift)
+                    else:
+                        H.hvxConvertDepthNode(g, src, out, pol, shift)
+                    H.hvxSetGraphCodegen(g, codegen)
+                    H.hvxVerifyGraph(g)
+                    H.hvxProcessGraph(g)
+                    np.testing.assert_array_equal(PG.download(out),
+                                                  O.convert_depth(arr, npout, shift, sat).data)
+                    H.hvxReleaseGraph(g)
