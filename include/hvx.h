@@ -356,6 +356,26 @@ hvx_node hvxAddNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_i
 hvx_node hvxSubtractNode(hvx_graph g, hvx_image a, hvx_image b, int32_t policy, hvx_image out);
 hvx_node hvxAbsDiffNode(hvx_graph g, hvx_image a, hvx_image b, hvx_image out);
 
+/* User-defined operators (Section 5.1: user kernels written against the
+ * point / local abstractions run on the accelerator like the library's own
+ * nodes).  The operator is an integer expression in a small C-like language:
+ * integer literals; a, b, c (a point operator's inputs at the pixel) or
+ * in(dx, dy) (a local operator's input at literal offsets within its kw x kh
+ * window, read under the node's border mode); unary - + ~; binary * + -
+ * << >> < > <= >= == != & ^ |; min(x, y), max(x, y), abs(x); parentheses.
+ * C precedence, 64-bit two's-complement arithmetic, comparisons 0 or 1; the
+ * result is saturated to the output image's format (U8, S16 or S32, which
+ * the output must declare).  Inputs are U8, S16 or S32.  Such nodes fuse
+ * with their neighbours like library nodes and run only in generated kernels
+ * (NVRTC): verification fails with HVX_ERROR_NOT_SUPPORTED when code
+ * generation is off or unavailable.  NULL (HVX_ERROR_INVALID_PARAMETERS) for
+ * an expression outside the language, an offset outside the window, n_in
+ * outside 1..3 or kw, kh not odd in 1..9; HVX_CODEGEN_VERBOSE=1 prints why. */
+hvx_node hvxUserPointNode(hvx_graph g, const char* expr, const hvx_image* in, int32_t n_in,
+                          hvx_image out);
+hvx_node hvxUserLocalNode(hvx_graph g, const char* expr, int32_t kw, int32_t kh, hvx_image in,
+                          hvx_image out);
+
 /* Copy (point, Table 2): U8 -> U8 or S16 -> S16, unchanged. */
 hvx_node hvxCopyNode(hvx_graph g, hvx_image in, hvx_image out);
 

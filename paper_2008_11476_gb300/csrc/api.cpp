@@ -2,6 +2,8 @@
 // node constructors (Section 3.1, Listing 1; Section 5.1, Listing 4).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <new>
 
 #include "hvx_internal.h"
@@ -864,6 +866,42 @@ hvx_node hvxMultiplyNode(hvx_graph g, hvx_image a, hvx_image b, float scale, int
     p.scale = scale;
     p.mul_rounding = rounding;
     return add_node(g, N_MULTIPLY, {a, b}, {out}, 1, p);
+}
+
+hvx_node hvxUserPointNode(hvx_graph g, const char* expr, const hvx_image* in, int32_t n_in,
+                          hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    std::string code, why;
+    if (!expr || !in || n_in < 1 || n_in > 3 ||
+        !parse_user_expr(expr, false, n_in, 0, 0, &code, &why)) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        if (getenv("HVX_CODEGEN_VERBOSE") && !why.empty())
+            fprintf(stderr, "hvx: user expression rejected: %s\n", why.c_str());
+        return nullptr;
+    }
+    NodeParams p;
+    p.user_code = code;
+    if (n_in == 1) return add_node(g, N_USER_POINT, {in[0]}, {out}, 1, p);
+    if (n_in == 2) return add_node(g, N_USER_POINT, {in[0], in[1]}, {out}, 1, p);
+    return add_node(g, N_USER_POINT, {in[0], in[1], in[2]}, {out}, 1, p);
+}
+
+hvx_node hvxUserLocalNode(hvx_graph g, const char* expr, int32_t kw, int32_t kh, hvx_image in,
+                          hvx_image out) {
+    if (!ok_graph(g)) return nullptr;
+    std::string code, why;
+    if (!expr || kw < 1 || kh < 1 || kw > 9 || kh > 9 || !(kw & 1) || !(kh & 1) ||
+        !parse_user_expr(expr, true, 1, kw / 2, kh / 2, &code, &why)) {
+        G(g)->last = HVX_ERROR_INVALID_PARAMETERS;
+        if (getenv("HVX_CODEGEN_VERBOSE") && !why.empty())
+            fprintf(stderr, "hvx: user expression rejected: %s\n", why.c_str());
+        return nullptr;
+    }
+    NodeParams p;
+    p.user_code = code;
+    p.kw = kw;
+    p.kh = kh;
+    return add_node(g, N_USER_LOCAL, {in}, {out}, 1, p);
 }
 
 hvx_node hvxCopyNode(hvx_graph g, hvx_image in, hvx_image out) {

@@ -24,6 +24,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -167,6 +168,7 @@ constexpr int kThreads = 256;  // 8 warps: warps take rows, lanes columns
 
 struct Emitter {
     const GenericDesc& d;
+    const std::vector<std::string>& user;  // user-defined operators' code
     int tw = 0, th = 0;
     std::vector<int> producer;  // buffer -> stage index, or -1 (external input)
     std::vector<int> ext_in;    // buffer -> external input index, or -1
@@ -203,12 +205,37 @@ struct Emitter {
     int smem_words = 0;
     std::ostringstream o;
 
-    explicit Emitter(const GenericDesc& desc) : d(desc) {}
+    Emitter(const GenericDesc& desc, const std::vector<std::string>& u) : d(desc), user(u) {}
 
     static bool is_local(int op) {
         return op == OP_GAUSS || op == OP_BOX || op == OP_SOBEL_X || op == OP_SOBEL_Y ||
                op == OP_CONV || op == OP_LSUM || op == OP_DILATE || op == OP_ERODE ||
-               op == OP_MEDIAN;
+               op == OP_MEDIAN || op == OP_USER_LOCAL;
+    }
+
+    // A user operator's code with its placeholders replaced by reads, the
+    // 64-bit result saturated to the output format.
+    std::string user_expr(const GenStage& st, bool local) const {
+        std::string s = user[st.i0];
+        auto swap = [&](const std::string& from, const std::string& to) {
+            for (size_t at = s.find(from); at != std::string::npos; at = s.find(from, at + to.size()))
+                s.replace(at, from.size(), to);
+        };
+        if (local) {
+            for (size_t at = s.find("HVX_TAP("); at != std::string::npos; at = s.find("HVX_TAP(")) {
+                const size_t end = s.find(')', at);
+                int dx = 0, dy = 0;
+                std::sscanf(s.c_str() + at, "HVX_TAP(%d,%d)", &dx, &dy);
+                s.replace(at, end + 1 - at, "((long long)" + tap(st.in[0], dx, dy) + ")");
+            }
+        } else {
+            const char* names[3] = {"HVX_A", "HVX_B", "HVX_C"};
+            for (int i = 0; i < 3; ++i)
+                if (st.in[i] >= 0) swap(names[i], "((long long)" + val(st.in[i]) + ")");
+        }
+        const char* sat = st.i1 == HVX_DF_U8 ? "sat64_u8" : st.i1 == HVX_DF_S16 ? "sat64_s16"
+                                                                             : "sat64_s32";
+        return std::string(sat) + "(" + s + ")";
     }
 
     int bw(int b) const { return tw + 2 * d.buf[b].halo; }
@@ -578,6 +605,7 @@ struct Emitter {
                        lit64(st.k0) + ", " + lit64(st.k1) + "), " + lit64(st.k1) + "))";
             case OP_TOMASI:
                 return "__float_as_int(tomasi_response_f32(" + a + ", " + b + ", " + c + "))";
+            case OP_USER_POINT: return user_expr(st, false);
             case OP_CONVDEPTH:
                 if (st.i1 == st.i3) return a;
                 if (st.i1 == HVX_DF_S16)
@@ -681,6 +709,9 @@ struct Emitter {
                 o << ind << "}\n";
                 return;
             }
+            case OP_USER_LOCAL:
+                o << ind << dst << " = " << user_expr(st, true) << ";\n";
+                return;
             case OP_LSUM: {
                 // int32 wrap-around sum: the low 32 bits of the exact sum
                 o << ind << "{\n" << ind << "  unsigned t = 0;\n";
@@ -1027,6 +1058,11 @@ struct Emitter {
           << "#include \"jit_params.h\"\n\n"
           << "__device__ __forceinline__ bool hvx_in(const int* r, int x, int y) {\n"
           << "  return x >= r[0] && x < r[2] && y >= r[1] && y < r[3];\n}\n"
+          << "__device__ __forceinline__ long long hvx_min(long long x, long long y) { return x < y "
+             "? x : y; }\n"
+          << "__device__ __forceinline__ long long hvx_max(long long x, long long y) { return x > y "
+             "? x : y; }\n"
+          << "__device__ __forceinline__ long long hvx_abs(long long x) { return x < 0 ? -x : x; }\n"
           << "__device__ __forceinline__ int hvx_mirror(int v, int n) {\n"
           << "  const int p = 2 * n;\n  int m = v % p;\n  if (m < 0) m += p;\n"
           << "  return m < n ? m : p - 1 - m;\n}\n"
@@ -1223,9 +1259,9 @@ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 bool jit_available() { return nvrtc().ok; }
 
-bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* out,
-                 std::string* why) {
-    Emitter em(d);
+bool jit_prepare(const GenericDesc& d, const std::vector<std::string>& user_code, bool load_module,
+                 int device, JitLaunch* out, std::string* why) {
+    Emitter em(d, user_code);
     if (!em.emit()) {
         *why = "group shape not handled by the code generator";
         return false;

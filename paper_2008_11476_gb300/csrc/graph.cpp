@@ -72,6 +72,8 @@ const char* op_name(int kind) {
         case OP_HIST: return "histogram";
         case OP_EQHIST: return "equalize_hist";
         case OP_CONVDEPTH: return "convert_depth";
+        case OP_USER_POINT: return "user_point";
+        case OP_USER_LOCAL: return "user_local";
     }
     return "?";
 }
@@ -79,7 +81,7 @@ const char* op_name(int kind) {
 bool op_is_local(int kind) {
     return kind == OP_GAUSS || kind == OP_BOX || kind == OP_SOBEL_X || kind == OP_SOBEL_Y ||
            kind == OP_LSUM || kind == OP_CONV || kind == OP_DILATE || kind == OP_ERODE ||
-           kind == OP_MEDIAN;
+           kind == OP_MEDIAN || kind == OP_USER_LOCAL;
 }
 
 const char* group_kernel_name(int gk) {
@@ -141,6 +143,13 @@ void lower(Graph* g, Plan& P) {
             case N_EQHIST: add(OP_EQHIST, 0, 0); break;
             case N_COPY:
             case N_CONVDEPTH: add(OP_CONVDEPTH, 0, 0); break;
+            case N_USER_POINT: add(OP_USER_POINT, 0, 0); break;
+            case N_USER_LOCAL: {
+                add(OP_USER_LOCAL, 0, 0);
+                P.ops.back().rx = n->p.kw / 2;
+                P.ops.back().ry = n->p.kh / 2;
+                break;
+            }
             case N_SOBEL:
                 if (!n->out[0] && !n->out[1]) fail(HVX_ERROR_INVALID_PARAMETERS);
                 if (n->out[0]) add(OP_SOBEL_X, 0, 1);
@@ -254,6 +263,15 @@ void infer(Op& op) {
         case OP_MINMAX: need(0, {HVX_DF_U8, HVX_DF_S16}); of = HVX_DF_RESULT; break;
         case OP_HIST: need(0, {HVX_DF_U8}); of = HVX_DF_RESULT; break;
         case OP_EQHIST: need(0, {HVX_DF_U8}); of = HVX_DF_U8; break;
+        case OP_USER_POINT:
+        case OP_USER_LOCAL: {
+            // integer inputs; the output image declares U8, S16 or S32
+            for (int i = 0; i < op.n_in; ++i) need(i, {HVX_DF_U8, HVX_DF_S16, HVX_DF_S32});
+            of = op.out->is_virtual ? op.out->user_fmt : op.out->fmt;
+            if (of != HVX_DF_U8 && of != HVX_DF_S16 && of != HVX_DF_S32)
+                fail(HVX_ERROR_INVALID_FORMAT);
+            break;
+        }
         case OP_CONVDEPTH: {
             // Copy keeps the format; ConvertDepth goes U8 <-> S16
             need(0, {HVX_DF_U8, HVX_DF_S16});

@@ -124,6 +124,8 @@ enum NodeKind : int {
     N_EQHIST,
     N_COPY,
     N_CONVDEPTH,
+    N_USER_POINT,
+    N_USER_LOCAL,
 };
 
 struct NodeParams {
@@ -140,6 +142,7 @@ struct NodeParams {
     float scale = 1.0f;        // Multiply
     int mul_rounding = HVX_ROUND_TO_ZERO;
     int hist_bins = 256, hist_offset = 0, hist_range = 256;  // Histogram
+    std::string user_code;     // user-defined operator, rewritten (user_expr.cpp)
 };
 
 struct Node {
@@ -232,6 +235,7 @@ struct Group {
     bool jit_on = false;
     EqHistParams eqh;            // GK_EQHIST
     std::vector<ResultReset> resets;
+    std::vector<std::string> user_code;  // user-defined operators' code (GenStage.i0)
     uint64_t ext_bytes = 0;      // bytes of non-virtual images read + written
     uint64_t mem_bytes = 0;      // bytes of every image read + written
     bool closed = false;         // planning: no further op may join
@@ -295,11 +299,16 @@ hvx_status ensure_context_device_state(Context* ctx);
 void destroy_batch_cache(Context* ctx);
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s);
 
+// user-defined operators (user_expr.cpp): check an expression and rewrite it
+// for the code generator
+bool parse_user_expr(const std::string& src, bool local, int n_in, int rx, int ry,
+                     std::string* code, std::string* why);
+
 // code generation for staged-tile groups (codegen.cpp): generate, compile
 // (cached by source) and, with load_module, load the group's kernel
 bool jit_available();
-bool jit_prepare(const GenericDesc& d, bool load_module, int device, JitLaunch* out,
-                 std::string* why);
+bool jit_prepare(const GenericDesc& d, const std::vector<std::string>& user_code, bool load_module,
+                 int device, JitLaunch* out, std::string* why);
 cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s);
 // n images' groups that run the same generated kernel, in one launch: params
 // and tile_start (n + 1 prefix sums of tiles per image) in device memory

@@ -41,6 +41,9 @@ enum OpKind : int {
     // EqualizeHist (histogram + point): its own two launches
     OP_EQHIST,
     OP_CONVDEPTH,  // ConvertDepth / Copy
+    // user-defined operators (generated kernels only): i0 = expression index
+    OP_USER_POINT,
+    OP_USER_LOCAL,
 };
 
 #ifdef __CUDACC__

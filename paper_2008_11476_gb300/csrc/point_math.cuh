@@ -154,6 +154,9 @@ __device__ __forceinline__ int sat64_s16(long long v) {
     return (int)(v < -32768 ? -32768 : (v > 32767 ? 32767 : v));
 }
 __device__ __forceinline__ int wrap64_s16(long long v) { return (int)(short)(unsigned short)(v & 0xFFFF); }
+__device__ __forceinline__ int sat64_s32(long long v) {
+    return (int)(v < -2147483648ll ? -2147483648ll : (v > 2147483647ll ? 2147483647ll : v));
+}
 
 // ---------------------------------------------------------------------------
 // Shi-Tomasi response: the smaller eigenvalue of the structure matrix

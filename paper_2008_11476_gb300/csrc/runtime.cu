@@ -412,6 +412,7 @@ hvx_status build_eqhist(Plan& P, Group& G) {
 hvx_status build_generic(Plan& P, Group& G) {
     GenericDesc& d = G.gdesc;
     std::memset(&d, 0, sizeof(d));
+    G.user_code.clear();
     d.W = G.W;
     d.H = G.H;
     // halo of every image: sum of the window radii of in-group ops downstream
@@ -497,6 +498,11 @@ hvx_status build_generic(Plan& P, Group& G) {
             st.shift = op.node->p.shift;
             st.i0 = op.out->fmt;  // U8 or S16: the saturation range
             for (int32_t v : c) d.coeff[coeffs++] = v;
+        }
+        if (op.kind == OP_USER_POINT || op.kind == OP_USER_LOCAL) {
+            st.i0 = (int32_t)G.user_code.size();
+            st.i1 = op.out->fmt;
+            G.user_code.push_back(op.node->p.user_code);
         }
         if (op.kind == OP_HIST) {
             // bins, offset, range; shared-memory words of the tile's histogram
@@ -625,7 +631,8 @@ hvx_status prepare_launches(Graph* g) {
                    first.node->p.channel != HVX_CHANNEL_Y) {
             G.kernel = GK_CHX_UV;
             st = build_point(P, G);
-        } else if (G.ops.size() == 1 && !op_is_local(first.kind) && !op_is_global(first.kind)) {
+        } else if (G.ops.size() == 1 && !op_is_local(first.kind) && !op_is_global(first.kind) &&
+                   first.kind != OP_USER_POINT) {
             G.kernel = GK_POINT;
             st = build_point(P, G);
         } else if (match_edge(P, G, em)) {
@@ -638,15 +645,21 @@ hvx_status prepare_launches(Graph* g) {
             G.kernel = GK_GENERIC;
             st = build_generic(P, G);
             G.jit_on = false;
+            // user-defined operators exist only as generated code
+            const bool user = !G.user_code.empty();
+            if (st == HVX_SUCCESS && user && g->codegen == HVX_CODEGEN_OFF)
+                return HVX_ERROR_NOT_SUPPORTED;
             // plan-only contexts compile generated kernels only when asked to
             const bool gen = g->codegen == HVX_CODEGEN_REQUIRE ||
                              (g->codegen == HVX_CODEGEN_AUTO && !ctx->plan_only);
             if (st == HVX_SUCCESS && gen) {
                 std::string why;
-                G.jit_on = jit_prepare(G.gdesc, !ctx->plan_only, ctx->device, &G.jit, &why);
+                G.jit_on = jit_prepare(G.gdesc, G.user_code, !ctx->plan_only, ctx->device, &G.jit,
+                                       &why);
                 if (!G.jit_on && getenv("HVX_CODEGEN_VERBOSE"))
                     fprintf(stderr, "hvx: no generated kernel for a group: %s\n", why.c_str());
-                if (!G.jit_on && g->codegen == HVX_CODEGEN_REQUIRE) return HVX_ERROR_NOT_SUPPORTED;
+                if (!G.jit_on && (g->codegen == HVX_CODEGEN_REQUIRE || user))
+                    return HVX_ERROR_NOT_SUPPORTED;
             }
         }
         if (st != HVX_SUCCESS) return st;

@@ -143,6 +143,8 @@ _SIGS = {
     "hvxAbsDiffNode": (P, [P, P, P, P]),
     "hvxMultiplyNode": (P, [P, P, P, ctypes.c_float, I32, I32, P]),
     "hvxCopyNode": (P, [P, P, P]),
+    "hvxUserPointNode": (P, [P, ctypes.c_char_p, PP, I32, P]),
+    "hvxUserLocalNode": (P, [P, ctypes.c_char_p, I32, I32, P, P]),
     "hvxConvertDepthNode": (P, [P, P, P, I32, I32]),
     "hvxMeanStdDevNode": (P, [P, P]),
     "hvxMinMaxLocNode": (P, [P, P]),
@@ -432,6 +434,17 @@ def hvxAddNode(g, a, b, policy, o):
 
 def hvxSubtractNode(g, a, b, policy, o):
     return _node(lib().hvxSubtractNode(g, a, b, policy, o), g, "hvxSubtractNode")
+
+
+def hvxUserPointNode(g, expr: str, inputs, o):
+    arr = (ctypes.c_void_p * len(inputs))(*[x.value if isinstance(x, ctypes.c_void_p) else x
+                                            for x in inputs])
+    return _node(lib().hvxUserPointNode(g, expr.encode(), arr, len(inputs), o), g,
+                 "hvxUserPointNode")
+
+
+def hvxUserLocalNode(g, expr: str, kw, kh, i, o):
+    return _node(lib().hvxUserLocalNode(g, expr.encode(), kw, kh, i, o), g, "hvxUserLocalNode")
 
 
 def hvxCopyNode(g, i, o):

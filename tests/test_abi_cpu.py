@@ -458,3 +458,31 @@ def test_convert_depth_and_copy_plans(pctx):
                           H.HVX_POLICY_SATURATE, 0)
     with pytest.raises(H.HvxError):  # ConvertDepth changes the depth
         H.hvxVerifyGraph(g)
+
+
+def test_user_defined_operator_checks(pctx):
+    a = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8)
+    o = H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(pctx)
+    for bad in ("a / 2", "a && 1", "!a", "b", "foo(a)", "a +", "asm(1)", "a; b", "in(0, 0)"):
+        with pytest.raises(H.HvxError):
+            H.hvxUserPointNode(g, bad, [a], o)
+    for bad, kw, kh in (("in(2, 0)", 3, 3), ("in(x, 0)", 3, 3), ("a", 3, 3), ("in(0,0)", 4, 3),
+                        ("in(0,0)", 11, 1)):
+        with pytest.raises(H.HvxError):
+            H.hvxUserLocalNode(g, bad, kw, kh, a, o)
+    # only generated kernels run them
+    g = H.hvxCreateGraph(pctx)
+    H.hvxUserPointNode(g, "a * 2 - 1", [a], o)
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_OFF)
+    with pytest.raises(H.HvxError):
+        H.hvxVerifyGraph(g)
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_REQUIRE)
+    H.hvxVerifyGraph(g)  # compiles with NVRTC, no device needed
+    assert "sat64_s16" in H.hvxGetGraphKernelSource(g, 0)
+    # a user operator's output must declare its format
+    g = H.hvxCreateGraph(pctx)
+    H.hvxUserPointNode(g, "a", [a], H.hvxCreateVirtualImage(g))
+    H.hvxCopyNode(g, a, H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8))
+    with pytest.raises(H.HvxError):
+        H.hvxVerifyGraph(g)

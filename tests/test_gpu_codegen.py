@@ -432,3 +432,39 @@ def test_convert_depth_and_copy(ctx, w, h, codegen):
                     np.testing.assert_array_equal(PG.download(out),
                                                   O.convert_depth(arr, npout, shift, sat).data)
                     H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("border", [H.HVX_BORDER_REPLICATE, H.HVX_BORDER_CONSTANT,
+                                    H.HVX_BORDER_UNDEFINED, H.HVX_BORDER_MIRROR,
+                                    H.HVX_BORDER_REPEAT])
+@pytest.mark.parametrize("w,h", [(1, 1), (45, 17), (640, 480)])
+def test_user_defined_operators(ctx, border, w, h):
+    # a user local operator (5x3 window) feeding a library Gaussian's output
+    # and a user point operator on two images, fused into one generated kernel
+    import oracle as O
+    from oracle import user_ops as U
+    ob = {H.HVX_BORDER_REPLICATE: O.BORDER_REPLICATE, H.HVX_BORDER_CONSTANT: O.BORDER_CONSTANT,
+          H.HVX_BORDER_UNDEFINED: O.BORDER_UNDEFINED, H.HVX_BORDER_MIRROR: O.BORDER_MIRROR,
+          H.HVX_BORDER_REPEAT: O.BORDER_REPEAT}[border]
+    loc = "in(-2, 0) - 2 * in(0, 0) + in(2, 0) + max(in(0, -1), in(1, 1)) - abs(in(-1, 1) - 99)"
+    pnt = "((a * 3 - b) >> 1) + (a < b) * 1000 - (a & 255 ^ b)"
+    img = synth.rects_noise(w, h, seed=w + 7)
+    src = PG.upload(ctx, img, H.HVX_DF_U8)
+    out = PG.empty(ctx, w, h, H.HVX_DF_S16)
+    g = H.hvxCreateGraph(ctx)
+    G = H.hvxCreateVirtualImage(g)
+    t = H.hvxCreateVirtualImage(g, 0, 0, H.HVX_DF_S16)
+    H.hvxGaussian3x3Node(g, src, G)
+    H.hvxSetNodeBorder(H.hvxUserLocalNode(g, loc, 5, 3, G, t), border, 17)
+    H.hvxUserPointNode(g, pnt, [t, src], out)
+    H.hvxVerifyGraph(g)
+    if border not in (H.HVX_BORDER_MIRROR, H.HVX_BORDER_REPEAT):
+        assert H.hvxQueryGraph(g, H.HVX_GRAPH_NUM_LAUNCHES) == 1
+    assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) >= 1
+    H.hvxProcessGraph(g)
+    Gr = O.gaussian3x3(img, O.BORDER_REPLICATE)
+    tr = U.user_local(loc, Gr, 5, 3, ob, 17, np.int16)
+    ref = U.user_point(pnt, [tr, O.Img(img)], np.int16)
+    np.testing.assert_array_equal(PG.download(out), ref.data)
+    assert H.hvxGetValidRegion(out) == ref.rect
+    H.hvxReleaseGraph(g)

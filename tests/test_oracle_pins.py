@@ -746,3 +746,52 @@ def test_convert_depth_exhaustive(orc):
     assert (orc.convert_depth(s16, np.int16).data == s16).all()
     with pytest.raises(Exception):
         orc.convert_depth(u8, np.int16, 8)
+
+
+# --- User-defined operators (Section 5.1) -----------------------------------
+
+def test_user_expression_semantics_are_c():
+    from oracle import user_ops as U
+    one = np.ones((1, 1), np.int64)
+
+    def ev(expr, a=0, b=0, dtype=np.int32):
+        return int(U.user_point(expr, [one * a, one * b], dtype).data[0, 0])
+
+    assert ev("1 + 2 * 3") == 7
+    assert ev("a & 2 == 2", a=6) == 0            # C: 6 & (2 == 2); not (6 & 2) == 2
+    assert ev("1 << 2 + 1") == 8
+    assert ev("-a >> 1", a=3) == -2              # arithmetic shift: floor
+    assert ev("~0") == -1
+    assert ev("(a < b) * 10 + (a == b)", a=2, b=5) == 10
+    assert ev("min(a, b) - max(a, b) + abs(0 - 7)", a=9, b=4) == 2
+    assert ev("a * 100", a=3, dtype=np.uint8) == 255     # saturated to U8
+    assert ev("a - 1000", a=3, dtype=np.uint8) == 0
+    assert ev("a * a * a", a=40000, dtype=np.int32) == 2 ** 31 - 1
+
+
+@pytest.mark.parametrize("border,mode", [(O.BORDER_REPLICATE, "nearest"),
+                                         (O.BORDER_MIRROR, "reflect"), (O.BORDER_REPEAT, "wrap"),
+                                         (O.BORDER_CONSTANT, "constant")])
+def test_user_local_matches_scipy(border, mode):
+    from oracle import user_ops as U
+    img = synth.uniform_u8(23, 17, seed=5)
+    a = img.astype(np.int64)
+    r = U.user_local("2 * in(-1, 0) - in(1, 1) + in(0, -2)", img, 3, 5, border, 9, np.int16)
+    k = np.zeros((5, 3), np.int64)
+    k[2, 0] += 2
+    k[3, 2] -= 1
+    k[0, 1] += 1
+    want = ndi.correlate(a, k, mode=mode, cval=9)
+    assert (r.data == want).all() and r.rect == (0, 0, 23, 17)
+    mx = U.user_local("max(max(in(-1, 0), in(1, 0)), in(0, 0))", img, 3, 1, border, 9, np.uint8)
+    assert (mx.data == ndi.maximum_filter(img, size=(1, 3), mode=mode, cval=9)).all()
+
+
+def test_user_local_undefined_shrinks():
+    from oracle import user_ops as U
+    img = synth.uniform_u8(11, 9, seed=6)
+    r = U.user_local("in(-2, -1) + in(2, 1)", img, 5, 3, O.BORDER_UNDEFINED, 0, np.int16)
+    assert r.rect == (2, 1, 9, 8)
+    a = img.astype(np.int64)
+    assert (r.data[1:8, 2:9] == a[0:7, 0:7] + a[2:9, 4:11]).all()
+    assert (r.data[0] == 0).all() and (r.data[:, :2] == 0).all()
