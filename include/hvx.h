@@ -459,6 +459,13 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* graphs, int32_t n,
                                      const hvx_host_copy* copies, int32_t n_copies,
                                      void* stream);
 
+/* hvxServerSubmit on host data: the request's to_device copies run on its
+ * stream right before its launches and the device-to-host copies right after
+ * them, so that completion (hvxServerWait) means the results are in host
+ * memory.  The host buffers must stay valid until then. */
+hvx_status hvxServerSubmitHost(hvx_server server, hvx_graph g, const hvx_host_copy* copies,
+                               int32_t n_copies, uint64_t* ticket);
+
 /* Copy a global operator's result (hvx_mean_stddev, hvx_minmaxloc, or
  * uint32_t[num_bins]) to host memory out (size bytes).  Call after the
  * graph's processing has completed (hvxProcessGraph, or hvxWaitGraph /

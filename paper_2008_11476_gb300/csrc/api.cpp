@@ -420,12 +420,15 @@ hvx_status hvxCopyImage(hvx_image img, void* host, uint64_t host_pitch, int32_t 
     return cuda_status(e);
 }
 
+}  // extern "C"
+
+namespace hvx {
+
 // Host-side copies of one batch call.  Consecutive copies whose images follow
 // one another in device memory and whose host buffers follow one another too
 // (same row size and pitches, e.g. frames of one tensor) are merged into one
 // 2-D copy of all their rows.
-static hvx_status host_copies(std::vector<const hvx_host_copy*> copies, bool to_device,
-                              cudaStream_t s) {
+hvx_status host_copies(std::vector<const hvx_host_copy*> copies, bool to_device, cudaStream_t s) {
     // in device-address order, so that images adjacent in memory meet
     std::stable_sort(copies.begin(), copies.end(),
                      [](const hvx_host_copy* a, const hvx_host_copy* b) {
@@ -461,6 +464,19 @@ static hvx_status host_copies(std::vector<const hvx_host_copy*> copies, bool to_
     return HVX_SUCCESS;
 }
 
+hvx_status check_host_copies(const Context* ctx, const hvx_host_copy* copies, int32_t n) {
+    if (n < 0 || (n > 0 && !copies)) return HVX_ERROR_INVALID_PARAMETERS;
+    for (int32_t i = 0; i < n; ++i) {
+        const hvx_host_copy& c = copies[i];
+        if (!ok_image(c.image) || !c.host) return HVX_ERROR_INVALID_PARAMETERS;
+        const Image* im = I(c.image);
+        if (im->is_virtual || im->is_result || im->ctx != ctx || !im->dev)
+            return HVX_ERROR_INVALID_REFERENCE;
+        if (c.pitch < (uint64_t)im->w * bytes_per_pixel(im->fmt)) return HVX_ERROR_INVALID_PARAMETERS;
+    }
+    return HVX_SUCCESS;
+}
+
 // Whether graph g reads (inputs) or writes (outputs) image im from memory.
 static bool graph_touches(const Graph* g, const Image* im, bool inputs) {
     for (const Group& G : g->plan.groups)
@@ -468,6 +484,10 @@ static bool graph_touches(const Graph* g, const Image* im, bool inputs) {
             if (x == im) return true;
     return false;
 }
+
+}  // namespace hvx
+
+extern "C" {
 
 hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_host_copy* copies,
                                      int32_t n_copies, void* stream) {
@@ -482,14 +502,8 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
     }
     Context* ctx = v[0]->ctx;
     if (ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
-    for (int32_t i = 0; i < n_copies; ++i) {
-        const hvx_host_copy& c = copies[i];
-        if (!ok_image(c.image) || !c.host) return HVX_ERROR_INVALID_PARAMETERS;
-        const Image* im = I(c.image);
-        if (im->is_virtual || im->is_result || im->ctx != ctx || !im->dev)
-            return HVX_ERROR_INVALID_REFERENCE;
-        if (c.pitch < (uint64_t)im->w * bytes_per_pixel(im->fmt)) return HVX_ERROR_INVALID_PARAMETERS;
-    }
+    hvx_status vs = check_host_copies(ctx, copies, n_copies);
+    if (vs != HVX_SUCCESS) return vs;
     // A pipeline over parts of the batch: part j's uploads (copy stream in),
     // its launches (the caller's stream), its downloads (copy stream out), so
     // that part j + 1's uploads and part j - 1's downloads overlap part j's

@@ -317,6 +317,11 @@ cudaError_t jit_launch_batch(const JitKernel* k, const HvxJitParams* params, con
 void jit_tile(const JitKernel* k, int* tw, int* th);
 const std::string& jit_source(const JitLaunch& j);
 
+// host data of a call (api.cpp): checks, and the 2-D copies in one direction
+// on a stream (adjacent images merged)
+hvx_status check_host_copies(const Context* ctx, const hvx_host_copy* copies, int32_t n);
+hvx_status host_copies(std::vector<const hvx_host_copy*> copies, bool to_device, cudaStream_t s);
+
 // server (server.cpp)
 void server_destroy(Server* s);
 

@@ -35,6 +35,7 @@ struct Request {
     hvx_status result = HVX_SUCCESS;
     bool done = false;
     cudaEvent_t ev = nullptr;
+    std::vector<hvx_host_copy> copies;  // host data: copied in before, out after
 };
 
 struct Server {
@@ -115,7 +116,11 @@ void Server::run() {
             r->ev = event_pool.back();
             event_pool.pop_back();
             NvtxRange nvtx("hvx serve dispatch");
-            hvx_status st = launch_plan(r->g, s);
+            std::vector<const hvx_host_copy*> up, down;
+            for (const hvx_host_copy& c : r->copies) (c.to_device ? up : down).push_back(&c);
+            hvx_status st = host_copies(up, true, s);
+            if (st == HVX_SUCCESS) st = launch_plan(r->g, s);
+            if (st == HVX_SUCCESS) st = host_copies(down, false, s);
             if (st == HVX_SUCCESS && cudaEventRecord(r->ev, s) != cudaSuccess) st = HVX_ERROR_DEVICE;
             if (st != HVX_SUCCESS) {
                 cudaGetLastError();
@@ -201,6 +206,11 @@ hvx_status hvxCreateServer(hvx_context ctx, uint64_t budget, int32_t max_infligh
 }
 
 hvx_status hvxServerSubmit(hvx_server hs, hvx_graph hg, uint64_t* ticket) {
+    return hvxServerSubmitHost(hs, hg, nullptr, 0, ticket);
+}
+
+hvx_status hvxServerSubmitHost(hvx_server hs, hvx_graph hg, const hvx_host_copy* copies,
+                               int32_t n_copies, uint64_t* ticket) {
     if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
     Graph* g = reinterpret_cast<Graph*>(hg);
     if (!g || g->magic != kMagicGraph) return HVX_ERROR_INVALID_REFERENCE;
@@ -227,8 +237,11 @@ hvx_status hvxServerSubmit(hvx_server hs, hvx_graph hg, uint64_t* ticket) {
             }
     }
     if (s->budget && bytes > s->budget) return HVX_ERROR_OVER_BUDGET;
+    hvx_status cs = check_host_copies(s->ctx, copies, n_copies);
+    if (cs != HVX_SUCCESS) return cs;
     Request* r = new (std::nothrow) Request();
     if (!r) return HVX_ERROR_NO_MEMORY;
+    if (n_copies > 0) r->copies.assign(copies, copies + n_copies);
     r->g = g;
     r->bytes = bytes;
     r->mpix = mpix;

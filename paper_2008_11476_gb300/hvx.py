@@ -152,6 +152,7 @@ _SIGS = {
     "hvxEqualizeHistNode": (P, [P, P, P]),
     "hvxGetNodeResult": (I32, [P, P, U64]),
     "hvxScheduleGraphBatchHost": (I32, [PP, I32, P, I32, P]),
+    "hvxServerSubmitHost": (I32, [P, P, P, I32, ctypes.POINTER(ctypes.c_uint64)]),
     "hvxConvolveNode": (P, [P, P, ctypes.POINTER(I32), I32, I32, I32, P]),
     "hvxPointNode": (P, [P, I32, PP, I32, P, ctypes.POINTER(ctypes.c_double), I32]),
     "hvxLocalNode": (P, [P, I32, I32, I32, P, P]),
@@ -610,3 +611,13 @@ def hvxScheduleGraphBatchHost(graphs, copies, stream: int = 0):
     cp = ctypes.cast(copies, ctypes.c_void_p) if len(copies) else None
     _ck(lib().hvxScheduleGraphBatchHost(arr, len(graphs), cp, len(copies), stream),
         "hvxScheduleGraphBatchHost")
+
+
+def hvxServerSubmitHost(server, g, copies):
+    """Submit a request whose host data (an array from host_copies) is copied
+    in before and out after its launches; returns the ticket."""
+    t = ctypes.c_uint64()
+    cp = ctypes.cast(copies, ctypes.c_void_p) if len(copies) else None
+    _ck(lib().hvxServerSubmitHost(server, g, cp, len(copies), ctypes.byref(t)),
+        "hvxServerSubmitHost")
+    return t.value

@@ -258,3 +258,35 @@ def test_harris_batch_one_launch(ctx):
         H.hvxWaitBatch(ctx)
         for mk, want in zip(outs, singles):
             np.testing.assert_array_equal(PG.download(mk), want)
+
+
+def test_server_requests_on_host_data(ctx):
+    # hvxServerSubmitHost: each request copies its frame in, runs, copies both
+    # outputs out; a completed request's results are in host memory
+    w, h = 320, 200
+    srv = H.hvxCreateServer(ctx, 1 << 30, 4, 2)
+    graphs, bufs = [], []
+    for i in range(3):
+        src = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        ph = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        graphs.append((PG.edge_graph(ctx, src, ph, mk), src, ph, mk))
+    tickets = []
+    for k in range(9):
+        g, src, ph, mk = graphs[k % 3]
+        f = synth.rects_noise(w, h, seed=200 + k)
+        hp = np.zeros((h, w), np.uint8)
+        hm = np.zeros((h, w), np.uint8)
+        copies = H.host_copies([(src, f.ctypes.data, w, True), (ph, hp.ctypes.data, w, False),
+                                (mk, hm.ctypes.data, w, False)])
+        bufs.append((f, hp, hm, copies))
+        tickets.append(H.hvxServerSubmitHost(srv, g, copies))
+        if k % 3 == 2:  # a graph runs one request at a time: wait before reusing it
+            for t in tickets[-3:]:
+                st, _ = H.hvxServerWait(srv, t)
+                assert st == H.HVX_SUCCESS
+    for f, hp, hm, _ in bufs:
+        rp, rm = O.edge_graph(f)
+        np.testing.assert_array_equal(hp, rp)
+        np.testing.assert_array_equal(hm, rm)
+    H.hvxReleaseServer(srv)
