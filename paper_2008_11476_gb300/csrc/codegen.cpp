@@ -241,12 +241,13 @@ struct Emitter {
     int bw(int b) const { return tw + 2 * d.buf[b].halo; }
     int bh(int b) const { return th + 2 * d.buf[b].halo; }
 
-    // Staged U8 external inputs are held as bytes, in rows that start on the
-    // 4-byte boundary at or left of the region (image x = x0 - A, A = halo
-    // rounded up to a multiple of 4), so that interior tiles load them with
-    // one 32-bit load per 4 pixels.  Other staged images hold int32 cells.
+    // Staged U8 images are held as bytes (a U8 image's values are 0..255),
+    // in rows that start on the 4-byte boundary at or left of the region
+    // (image x = x0 - A, A = halo rounded up to a multiple of 4), so that
+    // interior tiles load external ones with one 32-bit load per 4 pixels.
+    // Other staged images hold int32 cells.
     bool byte_slot(int b) const {
-        return b < d.n_buf && staged[b] && ext_in[b] >= 0 && d.buf[b].fmt == HVX_DF_U8;
+        return b < d.n_buf && staged[b] && d.buf[b].fmt == HVX_DF_U8;
     }
     int align4(int b) const { return (d.buf[b].halo + 3) & ~3; }
     int slot_w(int b) const { return byte_slot(b) ? tw + 2 * align4(b) : bw(b); }
@@ -961,8 +962,9 @@ struct Emitter {
                 }
             } else {
                 for (int b : p.targets)
-                    o << "          B" << b << "[(rb + " << i << ") * " << bw(b) << " + c] = "
-                      << val(b) << ";\n";
+                    o << "          B" << b << "[(rb + " << i << ") * " << slot_w(b) << " + c + "
+                      << slot_x(b) << "] = " << (byte_slot(b) ? "(unsigned char)" : "") << val(b)
+                      << ";\n";
             }
             o << "        }\n      }\n";
         }
@@ -1019,10 +1021,12 @@ struct Emitter {
             o << "    {\n";
             open_cells(bh(b), bw(b), h, h, false);
             o << "      if (x >= 0 && x < p.W && y >= 0 && y < p.H) continue;\n"
-              << "      B" << b << "[r * " << bw(b) << " + c] = "
+              << "      B" << b << "[r * " << slot_w(b) << " + c + " << slot_x(b) << "] = "
+              << (byte_slot(b) ? "(unsigned char)" : "")
               << fill_expr(b, "B" + std::to_string(b) + "[(min(max(y, 0), p.H - 1) - y0 + " +
-                                  std::to_string(h) + ") * " + std::to_string(bw(b)) +
-                                  " + min(max(x, 0), p.W - 1) - x0 + " + std::to_string(h) + "]")
+                                  std::to_string(h) + ") * " + std::to_string(slot_w(b)) +
+                                  " + min(max(x, 0), p.W - 1) - x0 + " +
+                                  std::to_string(h + slot_x(b)) + "]")
               << ";\n";
             close_cells();
             o << "    }\n";
