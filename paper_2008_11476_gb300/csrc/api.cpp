@@ -504,6 +504,7 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
     if (ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
     hvx_status vs = check_host_copies(ctx, copies, n_copies);
     if (vs != HVX_SUCCESS) return vs;
+    std::lock_guard<std::mutex> lock(ctx->io_mu);
     // A pipeline over parts of the batch: part j's uploads (copy stream in),
     // its launches (the caller's stream), its downloads (copy stream out), so
     // that part j + 1's uploads and part j - 1's downloads overlap part j's

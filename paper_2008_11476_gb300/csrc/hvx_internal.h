@@ -284,6 +284,9 @@ struct Context {
     // hvxScheduleGraphBatchHost: copy streams and events of its pipeline
     cudaStream_t io_in = nullptr, io_out = nullptr;
     std::vector<cudaEvent_t> io_events;
+    // calls from several host threads: the batch cache and the host-data
+    // pipeline are each used by one call at a time
+    std::mutex batch_mu, io_mu;
 };
 
 // ---------------------------------------------------------------------------

@@ -943,6 +943,7 @@ hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, Batch
 
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
     NvtxRange nvtx("hvx batch");
+    std::lock_guard<std::mutex> lock(ctx->batch_mu);
     // one launch when every plan is a single group running the same
     // generated kernel
     JitKernel* jk = nullptr;

@@ -290,3 +290,42 @@ def test_server_requests_on_host_data(ctx):
         np.testing.assert_array_equal(hp, rp)
         np.testing.assert_array_equal(hm, rm)
     H.hvxReleaseServer(srv)
+
+
+def test_batches_from_two_host_threads(ctx):
+    # two threads issue batch calls on one context (shared batch cache) on
+    # their own streams; every output stays exact
+    import threading
+    import torch
+    w, h = 256, 144
+    sets = []
+    for k in range(2):
+        graphs, refs, outs = [], [], []
+        for i in range(4):
+            img = synth.rects_noise(w, h, seed=300 + 10 * k + i)
+            src = PG.upload(ctx, img, H.HVX_DF_U8)
+            ph, mk = PG.empty(ctx, w, h, H.HVX_DF_U8), PG.empty(ctx, w, h, H.HVX_DF_U8)
+            graphs.append(PG.edge_graph(ctx, src, ph, mk))
+            refs.append(O.edge_graph(img))
+            outs.append((ph, mk))
+        sets.append((graphs, refs, outs))
+    errors = []
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            graphs, refs, outs = sets[k]
+            for _ in range(20):
+                H.hvxProcessGraphBatch(graphs, st.cuda_stream)
+            H.hvxWaitBatch(ctx, st.cuda_stream)
+            for (rp, rm), (ph, mk) in zip(refs, outs):
+                assert np.array_equal(PG.download(ph), rp) and np.array_equal(PG.download(mk), rm)
+        except Exception as e:  # reported to the main thread
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
