@@ -72,6 +72,9 @@ def parse():
                          "call pipelines its frames' copies and kernels internally)")
     ap.add_argument("--apps", default=None,
                     help="apps workload: comma-separated subset (e.g. Gauss,Tomasi)")
+    ap.add_argument("--codegen", default="auto", choices=["auto", "only"],
+                    help="apps workload: 'only' runs generated kernels in place of the "
+                         "hand-written corner kernel (HVX_CODEGEN_ONLY), to compare them")
     return ap.parse_args()
 
 
@@ -687,7 +690,8 @@ def run_harris(args, world, rank, local, torch):
             "config": {"workload": "Sobel3x3->products->5x5 sums->response(k=1/25)->"
                                    "Threshold(1e6), 4096x2160 U8, BORDER_UNDEFINED, 16 frames "
                                    "per step (one launch each)",
-                       "l2": "16 distinct frames per step, larger than L2"},
+                       "l2": "16 distinct frames per step, larger than L2",
+                       "codegen": args.codegen},
             "unfused": {"value": round(mp * 3 / tp, 1), "unit": "Mpix/s", "launches_per_frame": 9},
             "roofline": {"bound": "hbm", "achieved": round(ext / per_launch_s / 1e9, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
@@ -762,7 +766,8 @@ def run_morph(args, world, rank, local, torch):
             "config": {"workload": "Dilate3x3 -> Erode3x3 -> AbsDiff(input) -> Threshold(20), "
                                    "AND Median3x3(input); 1920x1080 U8, BORDER_REPLICATE, 16 "
                                    "frames per step (one launch each)",
-                       "l2": "16 distinct frames per step, larger than L2"},
+                       "l2": "16 distinct frames per step, larger than L2",
+                       "codegen": args.codegen},
             "unfused": {"value": round(mp * 3 / tp, 1), "unit": "Mpix/s", "launches_per_frame": 6},
             "roofline": {"bound": "hbm", "achieved": round(ext / per_launch_s / 1e9, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
@@ -798,6 +803,9 @@ def run_apps(args, world, rank, local, torch):
         fused, plain = [], []
         for a in ins:
             g, outs = build(ctx, a, W, H_, True)
+            if args.codegen == "only":
+                H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+                H.hvxVerifyGraph(g)
             fused.append(g)
             g2, _ = build(ctx, a, W, H_, False)
             plain.append(g2)
@@ -821,11 +829,13 @@ def run_apps(args, world, rank, local, torch):
         px = W * H_ * F * steps * world
         fv, bv, pv = px / tf / 1e6, px / tb / 1e6, px / tp / 1e6
         gen = H.hvxQueryGraph(fused[0], H.HVX_GRAPH_GENERATED_KERNELS)
+        kind = "generated" if gen else PG.kernel_kinds(fused[0])[0]
         res[name] = {"batched_mpix_s": round(bv, 1), "fused_mpix_s": round(fv, 1),
                      "unfused_mpix_s": round(pv, 1), "speedup_batched_vs_unfused": round(bv / pv, 2),
                      "speedup_fused_vs_unfused": round(fv / pv, 2),
-                     "kernel": "generated" if gen else PG.kernel_kinds(fused[0])[0],
-                     "batch_launches": 1 if gen else F,
+                     "kernel": kind,
+                     # generated and corner kernels cover all frames in one launch
+                     "batch_launches": 1 if kind in ("generated", "fused_harris_tma") else F,
                      "unfused_launches_per_frame": H.hvxQueryGraph(plain[0],
                                                                    H.HVX_GRAPH_NUM_LAUNCHES),
                      "external_bytes_per_px": ext // (W * H_),
@@ -851,7 +861,8 @@ def run_apps(args, world, rank, local, torch):
                                    "Harris, Tomasi (Section 6) on 16 1920x1080 U8 frames per "
                                    "step: one hvxProcessGraphBatch call (one launch where the "
                                    "frames share a generated kernel), or one call per frame",
-                       "l2": "16 distinct frames per step, larger than L2"},
+                       "l2": "16 distinct frames per step, larger than L2",
+                       "codegen": args.codegen},
             "apps": res, "peak_source": src,
             "gpu_launches": steps * sum(v["batch_launches"] for v in res.values())}), flush=True)
 

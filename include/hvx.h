@@ -24,8 +24,13 @@
  *    `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
  *    default stream).
  *  - A context, and every graph and image it owns, is used by one host thread
- *    at a time.  hvxServerSubmit / hvxServerWait / hvxServerStats are
- *    thread-safe.
+ *    at a time, with two exceptions: hvxServerSubmit / hvxServerWait /
+ *    hvxServerStats are thread-safe, and several threads may issue
+ *    hvxProcessGraphBatch / hvxScheduleGraphBatchHost on one context (on
+ *    disjoint graphs; the calls take turns on the context's batch cache and
+ *    copy pipeline).  Calls that verify, launch or batch make the context's
+ *    device current in the calling thread (cudaSetDevice), which may be a
+ *    thread that has made no CUDA call yet.
  *  - Any change to a verified graph (new node, border or rounding change)
  *    marks it unverified; hvxProcessGraph then returns HVX_ERROR_NOT_VERIFIED
  *    until hvxVerifyGraph succeeds again.
@@ -132,6 +137,10 @@ typedef int32_t hvx_status;
 #define HVX_CODEGEN_REQUIRE 2 /* generate every staged-tile group's kernel, also in a
                                  plan-only context (compile only); verification fails
                                  with HVX_ERROR_NOT_SUPPORTED where that is impossible   */
+#define HVX_CODEGEN_ONLY 3    /* as REQUIRE, and the fused groups that hand-written
+                                 kernels cover (edge, Gaussian3x3, Harris / Shi-Tomasi
+                                 corners) become staged-tile groups with generated
+                                 kernels too (to compare the two; same results)         */
 
 /* hvxQueryNode attributes */
 #define HVX_NODE_LIVE_OUTPUTS 1 /* uint32 bitmask: output i computed if bit i set */

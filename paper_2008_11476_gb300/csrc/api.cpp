@@ -674,8 +674,7 @@ hvx_status hvxSetGraphFusion(hvx_graph hg, int32_t enable) {
 
 hvx_status hvxSetGraphCodegen(hvx_graph hg, int32_t mode) {
     if (!ok_graph(hg)) return HVX_ERROR_INVALID_REFERENCE;
-    if (mode != HVX_CODEGEN_OFF && mode != HVX_CODEGEN_AUTO && mode != HVX_CODEGEN_REQUIRE)
-        return HVX_ERROR_INVALID_PARAMETERS;
+    if (mode < HVX_CODEGEN_OFF || mode > HVX_CODEGEN_ONLY) return HVX_ERROR_INVALID_PARAMETERS;
     Graph* g = G(hg);
     g->codegen = mode;
     release_plan(g);

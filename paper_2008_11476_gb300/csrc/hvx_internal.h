@@ -289,6 +289,15 @@ struct Context {
     std::mutex batch_mu, io_mu;
 };
 
+// Driver-API work (tensor-map encoding, loading and launching generated
+// kernels) runs in the calling thread's current context: runtime calls bind the
+// device's primary context to a thread lazily, driver calls do not.  Entry
+// points that do such work first make the context's device current in the
+// calling thread, which may be a fresh one.
+inline void bind_device(const Context* ctx) {
+    if (!ctx->plan_only) cudaSetDevice(ctx->device);
+}
+
 // ---------------------------------------------------------------------------
 // verification (graph.cpp)
 hvx_status verify_graph(Graph* g);

@@ -183,15 +183,15 @@ struct alignas(16) EdgeParams {
     int32_t thr_type, tv, fv;
     int32_t thr_lo, thr_hi;
     int32_t s_thr;     // mask = gx^2 + gy^2 > s_thr (clamped to int32)
-    int32_t pad;
+    int32_t rows;      // single-image kernel: output rows per thread (2 .. EDGE_ROWS)
     int32_t gvalid[4];  // valid rectangle of the Gaussian image
     int32_t valid[4];   // valid rectangle of the outputs
     int* err;
 };
 
 // ---------------------------------------------------------------------------
-// Fused Harris group: Sobel3x3 -> gx^2, gy^2, gx*gy -> 5x5 window sums ->
-// response -> binary threshold.
+// Fused corner group: Sobel3x3 -> gx^2, gy^2, gx*gy -> 5x5 window sums ->
+// Harris or Shi-Tomasi response -> binary threshold.
 constexpr int HARRIS_TW = 64;
 constexpr int HARRIS_TH = 32;
 constexpr int HARRIS_THREADS = 256;
@@ -210,6 +210,8 @@ struct HarrisParams {
     int32_t wr;                // window radius (2 for 5x5)
     int32_t tv, fv;
     int32_t rows;              // BORDER_UNDEFINED kernel: output rows per thread
+    int32_t tomasi;            // 1: Shi-Tomasi response instead of Harris's
+    float thr_f;               // Shi-Tomasi: mask = (binary32 response > thr_f)
     int64_t kn, kd;
     int64_t q_thr;     // mask = kd * R > q_thr, exact integer form of R_f32 > T
     int32_t pvalid[4]; // valid rectangle of gx, gy and the products

@@ -169,18 +169,20 @@ __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint
     }
 }
 
-__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
-    return x0 >= 2 && y0 >= 2 && x0 + TW + 2 <= (int)p.W && y0 + TH + 2 <= (int)p.H;
+__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0,
+                                                 int th = TH) {
+    return x0 >= 2 && y0 >= 2 && x0 + TW + 2 <= (int)p.W && y0 + th + 2 <= (int)p.H;
 }
 
 // ---- input box border ------------------------------------------------------------
 
-__device__ void fix_input_border(Box& in, const EdgeParams& p, int x0, int y0) {
+// lh: box rows the TMA filled (LH, or 8 rows + 4 in the single-image kernel)
+__device__ void fix_input_border(Box& in, const EdgeParams& p, int x0, int y0, int lh = LH) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
     const bool cst = p.border_g == HVX_BORDER_CONSTANT;
     const uint8_t cv = (uint8_t)p.cval_g;
-    for_each_outside(LH, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
+    for_each_outside(lh, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
         const int x = x0 - 16 + c, y = y0 - 2 + r;
         in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
     });
@@ -471,14 +473,15 @@ __device__ __forceinline__ void edge_row(const RowCtx& cx, const GPolicy& gp, co
     point_row<MODE>(cx, p, gx, gy, y);
 }
 
-// One tile after its box has landed (and, on edge tiles, been border-fixed).
+// One tile after its box has landed (and, on edge tiles, been border-fixed):
+// 128 x 8 rows output pixels, `rows` per thread.
 template <int MODE>
 __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, int x0, int y0,
                                           bool interior, const PhaseEntry* plut,
-                                          uint32_t (*gslow)[5]) {
+                                          uint32_t (*gslow)[5], int rows = ROWS) {
     const int q = threadIdx.x & 15, gi = threadIdx.x >> 4;
     const int W = p.W, H = p.H;
-    const int x = x0 + 8 * q, yb = y0 + ROWS * gi;
+    const int x = x0 + 8 * q, yb = y0 + rows * gi;
     if (x >= W || yb >= H) return;
     RowCtx cx;
     cx.plut = plut;
@@ -505,7 +508,7 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     gp.L = min(10, W - x + 1);
     gp.cv = (uint32_t)(p.cval_s & 0xFF);
     const int c = 16 + 8 * q;
-    const uint8_t* row = &in[ROWS * gi][0];  // input row yb - 2
+    const uint8_t* row = &in[rows * gi][0];  // input row yb - 2
     // prologue: G rows yb - 1 and yb
     uint32_t P0[6], P1[6], P2[6], G0[5], G1[5], G2[5];
     load_pairs(row, c, P1);           // yb - 2
@@ -516,7 +519,7 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
     // rows: P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y); the
     // windows rotate with period 3, so three rows per trip keep them in place
-    const int n = min(ROWS, H - yb);
+    const int n = min(rows, H - yb);
     const uint8_t* r = row + 4 * LW;  // input row yb + 2
 #pragma unroll 1
     for (int i = 0; i < n; i += 3) {
@@ -534,31 +537,36 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
 // ---- kernels -------------------------------------------------------------------------
 
 __device__ __forceinline__ void issue_box(Box& in, uint64_t* bar, const CUtensorMap* map, int x0,
-                                          int y0) {
-    mbar_arrive_expect_tx(bar, BOX_BYTES);
+                                          int y0, uint32_t bytes = BOX_BYTES) {
+    mbar_arrive_expect_tx(bar, bytes);
     tma_load_2d(&in[0][0], map, bar, x0 - 16, y0 - 2);
 }
 
 template <int MODE>
+// One image: one CTA per 128 x 8R tile, R = p.rows output rows per thread
+// (chosen per image size so that a single image still spreads over every SM;
+// the tensor map's box is 160 x (8R + 4) bytes).
 __global__ void __launch_bounds__(EDGE_THREADS)
     edge_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
     __shared__ EdgeSmem<1> sm;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int rows = p.rows, th = 8 * rows;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * th;
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
     build_phase_lut(sm.plut);
     __syncthreads();
-    if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
+    if (threadIdx.x == 0)
+        issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0, (uint32_t)(LW * (th + 4)));
     // every thread leaves together when the (bounded) wait ran out
     if (__syncthreads_or(!mbar_wait_bounded(&sm.bar[0], 0, p.err))) return;
-    const bool interior = tile_is_interior(p, x0, y0);
+    const bool interior = tile_is_interior(p, x0, y0, th);
     if (!interior) {
-        fix_input_border(sm.in[0].b, p, x0, y0);
+        fix_input_border(sm.in[0].b, p, x0, y0, th + 4);
         __syncthreads();
     }
-    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior, sm.plut, sm.gslow);
+    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior, sm.plut, sm.gslow, rows);
 }
 
 // Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
@@ -647,7 +655,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
 
 template <int MODE>
 cudaError_t launch_mode(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
-    dim3 grid((p.W + TW - 1) / TW, (p.H + TH - 1) / TH);
+    const int th = 8 * p.rows;
+    dim3 grid((p.W + TW - 1) / TW, (p.H + th - 1) / th);
     edge_kernel<MODE><<<grid, EDGE_THREADS, 0, s>>>(map, p);
     return cudaGetLastError();
 }
@@ -666,6 +675,28 @@ int edge_mode(const EdgeParams& p) {
     if (p.mask && p.phase) return M_MASK_PHASE;
     if (p.mask) return M_MASK;
     return M_PHASE;
+}
+
+// Rows per thread of the single-image kernel: R in 2 .. EDGE_ROWS minimising
+// the busiest SM's time, modelled as (CTAs on it) x (R + 2 Gaussian rows it
+// walks) / min(CTAs on it, 4) (up to 4 resident CTAs hide each other's
+// latency); ties go to the larger R.  A 1920 x 1080 image gets R = 4 (510
+// tiles), where the batch kernel's R = 15 would give 135 tiles for 152 SMs.
+int edge_single_rows(int W, int H, int num_sms) {
+    const int tx = (W + TW - 1) / TW;
+    const int S = num_sms > 0 ? num_sms : 152;
+    int best = ROWS;
+    double best_cost = 0;
+    for (int R = ROWS; R >= 2; --R) {
+        const long long n = (long long)tx * ((H + 8 * R - 1) / (8 * R));
+        const long long c = (n + S - 1) / S;
+        const double cost = (double)c * (R + 2) / (double)(c < 4 ? c : 4);
+        if (R == ROWS || cost < best_cost) {
+            best = R;
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 void edge_tile_dims(int mode, int* tw, int* th) {

@@ -23,6 +23,13 @@
 //      as q > q_thr, where the host computed q_thr so that this equals the
 //      comparison of the correctly rounded binary32 response with T.  When R
 //      is exported it is rounded once from q / kd.
+//
+// The Tomasi application of Section 6 is the same group with the Shi-Tomasi
+// response (the smaller eigenvalue of [Sxx Sxy; Sxy Syy]) in place of R; both
+// kernels below then evaluate tomasi_response_f32 on the window sums, the
+// binary32 function the point operator computes, and threshold its value.
+#include <atomic>
+
 #include "device_common.cuh"
 #include "launchers.h"
 
@@ -197,9 +204,18 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         bool ok = full || in_rect(p.valid, xs + j, y);
-        long long q = harris_q(S[0][j], S[1][j], S[2][j], p.kn, p.kd);
-        mk[j] = ok ? (q > p.q_thr ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
-        if (p.resp) rv[j] = ok ? ratio_to_float(q, p.kd) : 0.0f;
+        bool hit;
+        float r;
+        if (p.tomasi) {
+            r = tomasi_response_f32(S[0][j], S[1][j], S[2][j]);
+            hit = r > p.thr_f;
+        } else {
+            long long q = harris_q(S[0][j], S[1][j], S[2][j], p.kn, p.kd);
+            hit = q > p.q_thr;
+            r = p.resp ? ratio_to_float(q, p.kd) : 0.0f;
+        }
+        mk[j] = ok ? (hit ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
+        if (p.resp) rv[j] = ok ? r : 0.0f;
     }
     if (p.mask) {
         uint8_t* dst = p.mask + (size_t)y * p.mask_pitch;
@@ -328,6 +344,41 @@ __device__ __forceinline__ long long harris_q32(int a, int b, int c, int kn, int
     return det * kd - (long long)((unsigned long long)tr * tr) * kn;
 }
 
+// Hardware approximations (PTX rsqrt.approx / rcp.approx, relative error at
+// most 2^-22.9 and 2^-23).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// tomasi_response_f32(a, b, c) > T for the window sums of one window of
+// squares and cross products (a, b >= 0 and a b >= c^2, so det, tr and s are
+// >= 0), decided from an estimate r' that replaces the IEEE square root and
+// division by the approximations above, unless r' is within 2^-19 r' of T.
+// Both r' and the binary32 response r are within 6e-7 (relative) of the
+// exact eigenvalue -- about ten roundings of 2^-24 and the two approximations
+// -- so a gap above 2^-19 r' (1.9e-6 r') puts r on the same side of T as r'.
+// disc = 0 makes r' NaN (0 * inf), which fails both tests and takes r.
+// tests/test_tomasi_decision.py replays the bound.
+__device__ __forceinline__ bool tomasi_above(int a, int b, int c, float T) {
+    const long long cc = (long long)c * c;
+    const long long det = (long long)a * b - cc;
+    const int d = a - b;
+    const float disc = (float)((long long)d * d + 4 * cc);
+    const float den = (float)(a + b) + disc * rsqrt_approx(disc);
+    const float r = 2.0f * (float)det * rcp_approx(den);
+    const float g = r * 0x1p-19f;
+    if (r - T > g) return true;
+    if (T - r > g) return false;
+    return tomasi_response_f32(a, b, c) > T;
+}
+
 // q > q_thr, decided in binary32 when the computed q is farther from the
 // threshold than its error bound, else exactly in 64-bit integers.  With
 // u = 2^-24 and M = kd (a b + c^2) + kn (a + b)^2, the binary32 evaluation
@@ -353,6 +404,7 @@ __device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, flo
 }
 
 // One 112 x 8R output tile at (x0, y0) of the image that `tmap` / `p` describe.
+template <bool TOMASI>
 __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const HarrisParams& p,
                                                  FastSmem& sm, int x0, int y0) {
     const int R = p.rows;
@@ -448,7 +500,15 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                 }
                 const bool ok = full || in_rect(p.valid, xs + j, y);
                 bool hit;
-                if (rrow) {  // the response is exported: exact q for both
+                if (TOMASI) {  // binary32 response, as the point operator computes it
+                    if (rrow) {
+                        const float t = tomasi_response_f32(h[0], h[1], h[2]);
+                        hit = t > p.thr_f;
+                        rv[j] = ok ? t : 0.0f;
+                    } else {
+                        hit = tomasi_above(h[0], h[1], h[2], p.thr_f);
+                    }
+                } else if (rrow) {  // the response is exported: exact q for both
                     const long long qv = harris_q32(h[0], h[1], h[2], kn, kd);
                     hit = qv > p.q_thr;
                     rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
@@ -485,16 +545,19 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
     }
 }
 
+template <bool TOMASI>
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
-    harris_fast_tile(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
+    harris_fast_tile<TOMASI>(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
 }
 
 // Several images in one launch (hvxProcessGraphBatch): block t is tile
 // t - tile_start[i] of the last image i with tile_start[i] <= t; tensor maps
-// and parameters in global memory, all images with the same rows per thread.
+// and parameters in global memory, all images with the same rows per thread
+// and the same response (Harris or Shi-Tomasi: TOMASI).
+template <bool TOMASI>
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_batch_kernel(const CUtensorMap* __restrict__ maps,
                              const HarrisParams* __restrict__ ps, const int* __restrict__ tile_start,
@@ -506,7 +569,7 @@ __global__ void __launch_bounds__(FTHREADS, 4)
     const int local = t - __ldg(tile_start + i), tx = __ldg(tiles_x + i);
     const int ty = local / tx;
     if (threadIdx.x == 0) tensormap_acquire(maps + i);
-    harris_fast_tile(maps + i, ps[i], sm, (local - ty * tx) * FTW, ty * 8 * ps[i].rows);
+    harris_fast_tile<TOMASI>(maps + i, ps[i], sm, (local - ty * tx) * FTW, ty * 8 * ps[i].rows);
 }
 
 }  // namespace
@@ -563,33 +626,50 @@ int harris_batch_rows(const int* W, const int* H, int n, int num_sms) {
     return best;
 }
 
+namespace {
+template <class K>
+cudaError_t set_fast_smem(K kernel, std::atomic<bool>& done) {
+    if (done.load(std::memory_order_acquire)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FastSmem));
+    if (e == cudaSuccess) done.store(true, std::memory_order_release);
+    return e;
+}
+}  // namespace
+
 cudaError_t launch_harris_batch(const CUtensorMap* maps, const HarrisParams* ps,
                                 const int* tile_start, const int* tiles_x, int n, int total,
-                                cudaStream_t s) {
-    static bool attr = false;
+                                bool tomasi, cudaStream_t s) {
+    static std::atomic<bool> attr[2] = {false, false};
     const int smem = (int)sizeof(FastSmem);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(harris_fast_batch_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (tomasi) {
+        cudaError_t e = set_fast_smem(harris_fast_batch_kernel<true>, attr[1]);
         if (e != cudaSuccess) return e;
-        attr = true;
+        harris_fast_batch_kernel<true><<<total, FTHREADS, smem, s>>>(maps, ps, tile_start,
+                                                                     tiles_x, n);
+    } else {
+        cudaError_t e = set_fast_smem(harris_fast_batch_kernel<false>, attr[0]);
+        if (e != cudaSuccess) return e;
+        harris_fast_batch_kernel<false><<<total, FTHREADS, smem, s>>>(maps, ps, tile_start,
+                                                                      tiles_x, n);
     }
-    harris_fast_batch_kernel<<<total, FTHREADS, smem, s>>>(maps, ps, tile_start, tiles_x, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s) {
     if (harris_fast_path(p)) {
-        static bool fast_attr = false;
+        static std::atomic<bool> fast_attr[2] = {false, false};
         const int smem = (int)sizeof(FastSmem);
-        if (!fast_attr) {
-            cudaError_t e = cudaFuncSetAttribute(harris_fast_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            fast_attr = true;
-        }
         dim3 grid((p.W + FTW - 1) / FTW, (p.H + 8 * p.rows - 1) / (8 * p.rows));
-        harris_fast_kernel<<<grid, FTHREADS, smem, s>>>(map, p);
+        if (p.tomasi) {
+            cudaError_t e = set_fast_smem(harris_fast_kernel<true>, fast_attr[1]);
+            if (e != cudaSuccess) return e;
+            harris_fast_kernel<true><<<grid, FTHREADS, smem, s>>>(map, p);
+        } else {
+            cudaError_t e = set_fast_smem(harris_fast_kernel<false>, fast_attr[0]);
+            if (e != cudaSuccess) return e;
+            harris_fast_kernel<false><<<grid, FTHREADS, smem, s>>>(map, p);
+        }
         return cudaGetLastError();
     }
     static bool attr_set = false;

@@ -25,6 +25,8 @@ struct EdgeBatchDesc {
 constexpr int EDGE_MODE_GAUSS = 0;
 int edge_mode(const EdgeParams& p);
 void edge_tile_dims(int mode, int* tw, int* th);
+// output rows per thread of the single-image edge kernel for a W x H image
+int edge_single_rows(int W, int H, int num_sms);
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
 cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s);
 int edge_batch_blocks_per_sm(int mode);
@@ -43,7 +45,7 @@ cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStr
 // equal; tensor maps boxed for them); total = tile_start[n]
 cudaError_t launch_harris_batch(const CUtensorMap* maps, const HarrisParams* ps,
                                 const int* tile_start, const int* tiles_x, int n, int total,
-                                cudaStream_t s);
+                                bool tomasi, cudaStream_t s);
 int harris_fast_tile_w();
 int harris_batch_rows(const int* W, const int* H, int n, int num_sms);
 cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);

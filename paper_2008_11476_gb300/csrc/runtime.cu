@@ -211,7 +211,10 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
             e.thr_general = 1;
         }
     }
-    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, EDGE_LOAD_H);
+    // one image per launch: R rows per thread, a 160 x (8R + 4) box (the
+    // batch kernel encodes its own 160 x EDGE_LOAD_H maps)
+    e.rows = edge_single_rows((int)G.W, (int)G.H, ctx->num_sms);
+    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));
 }
 
 hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
@@ -233,6 +236,7 @@ hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
 struct HarrisMatch {
     int sx = -1, sy = -1, pxx = -1, pyy = -1, pxy = -1, sxx = -1, syy = -1, sxy = -1, resp = -1,
         thr = -1;
+    bool tomasi = false;  // Shi-Tomasi response in place of Harris's
 };
 
 bool match_harris(const Plan& P, const Group& G, HarrisMatch& m) {
@@ -251,8 +255,10 @@ bool match_harris(const Plan& P, const Group& G, HarrisMatch& m) {
             case OP_MUL: muls.push_back(i); break;
             case OP_LSUM: sums.push_back(i); break;
             case OP_HARRIS:
+            case OP_TOMASI:
                 if (m.resp >= 0) return false;
                 m.resp = i;
+                m.tomasi = o.kind == OP_TOMASI;
                 break;
             case OP_THRESH:
                 if (m.thr >= 0) return false;
@@ -342,8 +348,9 @@ hvx_status build_harris(Plan& P, Group& G, const HarrisMatch& m, Context* ctx) {
     h.cval_b = s0.node->cval;
     h.wr = 2;
     h.rows = harris_fast_rows((int)G.W, (int)G.H, ctx->num_sms > 0 ? ctx->num_sms : 152);
-    h.kn = r.node->p.kn;
-    h.kd = r.node->p.kd;
+    h.tomasi = m.tomasi ? 1 : 0;
+    h.kn = m.tomasi ? 0 : r.node->p.kn;
+    h.kd = m.tomasi ? 1 : r.node->p.kd;
     set_rect(h.pvalid, P.ops[m.pxy].out->valid);
     set_rect(h.valid, r.out->valid);
     h.err = ctx->d_error;
@@ -358,7 +365,8 @@ hvx_status build_harris(Plan& P, Group& G, const HarrisMatch& m, Context* ctx) {
         h.mask_pitch = t.out->pitch;
         h.tv = t.node->p.true_value;
         h.fv = t.node->p.false_value;
-        h.q_thr = harris_q_threshold((float)t.node->p.thr_value, h.kd);
+        h.thr_f = (float)t.node->p.thr_value;
+        if (!m.tomasi) h.q_thr = harris_q_threshold(h.thr_f, h.kd);
     }
     int bw = 0, bh = 0;
     harris_box(h, &bw, &bh);
@@ -595,10 +603,14 @@ hvx_status alloc_results(Plan& P, Context* ctx) {
 hvx_status prepare_launches(Graph* g) {
     Plan& P = g->plan;
     Context* ctx = g->ctx;
+    bind_device(ctx);
     if (!ctx->plan_only) {
         hvx_status st = alloc_results(P, ctx);
         if (st != HVX_SUCCESS) return st;
     }
+    // HVX_CODEGEN_ONLY: generated kernels in place of the hand-written ones
+    const bool hand = g->codegen != HVX_CODEGEN_ONLY;
+    const bool must_gen = g->codegen == HVX_CODEGEN_REQUIRE || g->codegen == HVX_CODEGEN_ONLY;
     for (Group& G : P.groups) {
         G.ext_bytes = G.mem_bytes = 0;
         for (Image* im : G.inputs) {
@@ -624,7 +636,8 @@ hvx_status prepare_launches(Graph* g) {
         if (G.ops.size() == 1 && first.kind == OP_EQHIST) {
             G.kernel = GK_EQHIST;
             st = build_eqhist(P, G);
-        } else if (G.ops.size() == 1 && first.kind == OP_GAUSS && !border_wraps(first.node->border)) {
+        } else if (hand && G.ops.size() == 1 && first.kind == OP_GAUSS &&
+                   !border_wraps(first.node->border)) {
             G.kernel = GK_GAUSS;
             st = build_gauss(P, G, ctx);
         } else if (G.ops.size() == 1 && first.kind == OP_CHX &&
@@ -635,10 +648,10 @@ hvx_status prepare_launches(Graph* g) {
                    first.kind != OP_USER_POINT) {
             G.kernel = GK_POINT;
             st = build_point(P, G);
-        } else if (match_edge(P, G, em)) {
+        } else if (hand && match_edge(P, G, em)) {
             G.kernel = GK_EDGE;
             st = build_edge(P, G, em, ctx);
-        } else if (match_harris(P, G, hm)) {
+        } else if (hand && match_harris(P, G, hm)) {
             G.kernel = GK_HARRIS;
             st = build_harris(P, G, hm, ctx);
         } else {
@@ -650,15 +663,14 @@ hvx_status prepare_launches(Graph* g) {
             if (st == HVX_SUCCESS && user && g->codegen == HVX_CODEGEN_OFF)
                 return HVX_ERROR_NOT_SUPPORTED;
             // plan-only contexts compile generated kernels only when asked to
-            const bool gen = g->codegen == HVX_CODEGEN_REQUIRE ||
-                             (g->codegen == HVX_CODEGEN_AUTO && !ctx->plan_only);
+            const bool gen = must_gen || (g->codegen == HVX_CODEGEN_AUTO && !ctx->plan_only);
             if (st == HVX_SUCCESS && gen) {
                 std::string why;
                 G.jit_on = jit_prepare(G.gdesc, G.user_code, !ctx->plan_only, ctx->device, &G.jit,
                                        &why);
                 if (!G.jit_on && getenv("HVX_CODEGEN_VERBOSE"))
                     fprintf(stderr, "hvx: no generated kernel for a group: %s\n", why.c_str());
-                if (!G.jit_on && (g->codegen == HVX_CODEGEN_REQUIRE || user))
+                if (!G.jit_on && (must_gen || user))
                     return HVX_ERROR_NOT_SUPPORTED;
             }
         }
@@ -669,6 +681,7 @@ hvx_status prepare_launches(Graph* g) {
 }
 
 hvx_status launch_plan(Graph* g, cudaStream_t s) {
+    bind_device(g->ctx);
     for (Group& G : g->plan.groups) {
         NvtxRange nvtx(G.jit_on ? "hvx launch generated" : group_kernel_name(G.kernel));
         cudaError_t e = cudaSuccess;
@@ -703,7 +716,8 @@ struct BatchEntry {
     // generated-kernel batches: one direct launch over every image's tiles
     JitKernel* jk = nullptr;
     int n = 0, total_tiles = 0;
-    bool harris = false;  // BORDER_UNDEFINED Harris batch: one direct launch
+    bool harris = false;  // BORDER_UNDEFINED corner batch: one direct launch
+    bool tomasi = false;  // ... of the Shi-Tomasi kernel
 };
 
 struct BatchCache {
@@ -786,7 +800,15 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     edge_tile_dims(mode, &tw, &th);
     for (int i = 0; i < n; ++i) {
         const Group& G = gs[i]->plan.groups[0];
-        std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap, sizeof(CUtensorMap));
+        if (mode == EDGE_MODE_GAUSS) {
+            std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap,
+                        sizeof(CUtensorMap));
+        } else {  // the batch kernel's box: EDGE_TH rows and the halo
+            CUtensorMap map;
+            hvx_status st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, EDGE_LOAD_H);
+            if (st != HVX_SUCCESS) return st;
+            std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &map, sizeof(map));
+        }
         std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &G.edge,
                     sizeof(EdgeParams));
         tiles_x[i] = (int)((G.W + tw - 1) / tw);
@@ -936,6 +958,7 @@ hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, Batch
     for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
     out.dmem = dmem;
     out.harris = true;
+    out.tomasi = gs[0]->plan.groups[0].harris.tomasi != 0;
     out.n = n;
     out.total_tiles = tile_start[n];
     return HVX_SUCCESS;
@@ -944,6 +967,7 @@ hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, Batch
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {
     NvtxRange nvtx("hvx batch");
     std::lock_guard<std::mutex> lock(ctx->batch_mu);
+    bind_device(ctx);
     // one launch when every plan is a single group running the same
     // generated kernel
     JitKernel* jk = nullptr;
@@ -954,12 +978,14 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
                    P.groups[0].jit_on && (!jk || P.groups[0].jit.k == jk);
         if (jit_same) jk = P.groups[0].jit.k;
     }
-    // one launch when every plan is a single BORDER_UNDEFINED Harris group
+    // one launch when every plan is a single BORDER_UNDEFINED corner group
+    // with the same response (Harris or Shi-Tomasi)
     bool harris_same = !jit_same;
     for (int i = 0; i < n && harris_same; ++i) {
         const Plan& P = gs[i]->plan;
         harris_same = P.groups.size() == 1 && P.groups[0].kernel == GK_HARRIS &&
-                      harris_fast_path(P.groups[0].harris);
+                      harris_fast_path(P.groups[0].harris) &&
+                      P.groups[0].harris.tomasi == gs[0]->plan.groups[0].harris.tomasi;
     }
     // one persistent launch when every plan is a single edge (or Gaussian)
     // group and all of them use the same kernel mode
@@ -1035,7 +1061,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             reinterpret_cast<const CUtensorMap*>(base),
             reinterpret_cast<const HarrisParams*>(base + params_off),
             reinterpret_cast<const int*>(base + tiles_off), reinterpret_cast<const int*>(base + tx_off),
-            hit->n, hit->total_tiles, s));
+            hit->n, hit->total_tiles, hit->tomasi, s));
     }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
 }

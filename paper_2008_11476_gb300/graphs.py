@@ -84,7 +84,10 @@ def edge_graph(ctx, inp, phase=None, mask=None, border=H.HVX_BORDER_REPLICATE, c
 
 
 def harris_graph(ctx, inp, mask=None, resp_out=None, border=H.HVX_BORDER_UNDEFINED, cval=0,
-                 kn=1, kd=25, thr=1e6, fusion=True, verify=True):
+                 kn=1, kd=25, thr=1e6, fusion=True, verify=True, tomasi=False):
+    """Corner graph: Sobel3x3 -> products -> 5x5 window sums -> Harris
+    response (kn / kd), or the Shi-Tomasi response when tomasi is set ->
+    binary threshold."""
     g = H.hvxCreateGraph(ctx)
     gx = H.hvxCreateVirtualImage(g)
     gy = H.hvxCreateVirtualImage(g)
@@ -102,7 +105,10 @@ def harris_graph(ctx, inp, mask=None, resp_out=None, border=H.HVX_BORDER_UNDEFIN
         H.hvxSetNodeBorder(ln, border, cval)
         sums.append(s)
     r = resp_out if resp_out is not None else H.hvxCreateVirtualImage(g)
-    H.hvxPointNode(g, H.HVX_POINT_HARRIS_RESPONSE, sums, r, (kn, kd))
+    if tomasi:
+        H.hvxPointNode(g, H.HVX_POINT_TOMASI_RESPONSE, sums, r)
+    else:
+        H.hvxPointNode(g, H.HVX_POINT_HARRIS_RESPONSE, sums, r, (kn, kd))
     if mask is not None:
         H.hvxThresholdNode(g, r, H.HVX_THRESHOLD_BINARY, thr, 0, 255, 0, mask)
     H.hvxSetGraphFusion(g, fusion)

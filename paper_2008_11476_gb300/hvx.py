@@ -48,7 +48,7 @@ HVX_GRAPH_EXTERNAL_BYTES = 6
 HVX_GRAPH_FUSION = 7
 HVX_GRAPH_KERNEL_KINDS = 8
 HVX_GRAPH_GENERATED_KERNELS = 9
-HVX_CODEGEN_OFF, HVX_CODEGEN_AUTO, HVX_CODEGEN_REQUIRE = 0, 1, 2
+HVX_CODEGEN_OFF, HVX_CODEGEN_AUTO, HVX_CODEGEN_REQUIRE, HVX_CODEGEN_ONLY = 0, 1, 2, 3
 HVX_NODE_LIVE_OUTPUTS = 1
 HVX_NODE_GROUP = 2
 

@@ -338,11 +338,16 @@ def test_section6_applications_plan(pctx):
     from paper_2008_11476_gb300 import apps as A
     unfused = {"Gauss": 1, "Laplacian": 1, "FChain": 3, "SobelX": 1, "EdgFig2": 4, "Sobel": 3,
                "Unsharp": 4, "Harris": 9, "Tomasi": 9}
-    special = {"Harris": "fused_harris_tma"}
+    special = {"Harris": "fused_harris_tma", "Tomasi": "fused_harris_tma"}
     for name, build in A.APPS:
         src = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
         g, _ = build(pctx, src, 1920, 1080, True)
         assert PG.kernel_kinds(g) == [special.get(name, "staged_tile")], name
+        # with HVX_CODEGEN_ONLY every application is one generated staged-tile kernel
+        H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["staged_tile"], name
+        assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 1, name
         g2, _ = build(pctx, src, 1920, 1080, False)
         assert H.hvxQueryGraph(g2, H.HVX_GRAPH_NUM_LAUNCHES) == unfused[name], name
         if name == "EdgFig2":

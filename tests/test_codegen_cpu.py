@@ -28,11 +28,14 @@ def _gen(ctx, build, w=1920, h=1080, fusion=True, mode=H.HVX_CODEGEN_REQUIRE):
     return g
 
 
+@pytest.mark.parametrize("mode", [H.HVX_CODEGEN_REQUIRE, H.HVX_CODEGEN_ONLY])
 @pytest.mark.parametrize("name", [a for a, _ in A.APPS])
-def test_applications_compile(pctx, name):
-    g = _gen(pctx, dict(A.APPS)[name])
+def test_applications_compile(pctx, name, mode):
+    g = _gen(pctx, dict(A.APPS)[name], mode=mode)
     kinds = PG.kernel_kinds(g)
     assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == kinds.count("staged_tile")
+    if mode == H.HVX_CODEGEN_ONLY:
+        assert kinds == ["staged_tile"]
     for i, k in enumerate(kinds):
         s = H.hvxGetGraphKernelSource(g, i)
         assert (s is not None) == (k == "staged_tile")
@@ -58,9 +61,29 @@ def test_products_share_one_pass(pctx):
     # Tomasi: the three products are staged by one pass that evaluates the
     # Sobel derivatives once; the sums, response and threshold are evaluated
     # inline in the output pass
-    s = H.hvxGetGraphKernelSource(_gen(pctx, A.tomasi), 0)
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.tomasi, mode=H.HVX_CODEGEN_ONLY), 0)
     assert s.count("// pass:") == 2
     assert "tomasi_response_f32" in s
+
+
+def test_codegen_only_replaces_hand_written_kernels(pctx):
+    # the edge graph, Gaussian3x3 alone and the Harris group have hand-written
+    # kernels; HVX_CODEGEN_ONLY generates theirs instead
+    src = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+    ph, mk, go = (H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8) for _ in range(3))
+    ge = PG.edge_graph(pctx, src, ph, mk, verify=False)
+    gg = H.hvxCreateGraph(pctx)
+    H.hvxGaussian3x3Node(gg, src, go)
+    gh, _ = A.harris(pctx, src, 640, 480, True)
+    for g in (ge, gg, gh):
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g)[0] != "staged_tile"
+        H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["staged_tile"]
+        assert "hvx_generated" in H.hvxGetGraphKernelSource(g, 0)
+    with pytest.raises(H.HvxError):
+        H.hvxSetGraphCodegen(gg, 4)
 
 
 def test_same_shape_same_source(pctx):
@@ -82,7 +105,7 @@ def test_modes(pctx):
 
 def test_unfused_nodes_compile(pctx):
     # one generated kernel per staged-tile node when fusion is off
-    g = _gen(pctx, A.tomasi, fusion=False)
+    g = _gen(pctx, A.tomasi, fusion=False, mode=H.HVX_CODEGEN_ONLY)
     kinds = PG.kernel_kinds(g)
     assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == kinds.count("staged_tile") > 0
 

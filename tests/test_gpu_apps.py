@@ -109,7 +109,8 @@ def ctx():
     H.hvxReleaseContext(c)
 
 
-@pytest.mark.parametrize("codegen", [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE])
+@pytest.mark.parametrize("codegen", [H.HVX_CODEGEN_OFF, H.HVX_CODEGEN_REQUIRE,
+                                     H.HVX_CODEGEN_ONLY])
 @pytest.mark.parametrize("name", [a for a, _ in A.APPS])
 @pytest.mark.parametrize("w,h", [(640, 480), (385, 361)])
 def test_app_matches_oracle(ctx, name, w, h, codegen):

@@ -230,20 +230,24 @@ def test_batch_on_host_data(ctx):
         HX.hvxScheduleGraphBatchHost(graphs, bad)
 
 
-def test_harris_batch_one_launch(ctx):
-    # BORDER_UNDEFINED Harris graphs of different sizes in one launch (one
-    # rows-per-thread for all of them): the same masks as one launch each
-    sizes = [(1920, 1080), (333, 77), (640, 480), (1, 1), (129, 300)]
+@pytest.mark.parametrize("mix", ["harris", "tomasi", "both"])
+def test_harris_batch_one_launch(ctx, mix):
+    # BORDER_UNDEFINED corner graphs of different sizes in one launch (one
+    # rows-per-thread for all of them): the same masks as one launch each.
+    # Harris and Shi-Tomasi graphs run different kernels: a batch of both
+    # falls back to one launch per graph, with the same results
+    sizes = [(1920, 1080), (333, 77), (640, 480), (1, 1), (129, 300), (500, 260)]
     graphs, outs, refs = [], [], []
     for i, (w, h) in enumerate(sizes):
         img = synth.rects_noise(w, h, seed=80 + i)
         src = PG.upload(ctx, img, H.HVX_DF_U8)
         mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
-        g = PG.harris_graph(ctx, src, mk)
+        tomasi = mix == "tomasi" or (mix == "both" and i % 2 == 1)
+        g = PG.harris_graph(ctx, src, mk, thr=4.0e4 if tomasi else 1e6, tomasi=tomasi)
         assert PG.kernel_kinds(g) == ["fused_harris_tma"]
         graphs.append(g)
         outs.append(mk)
-        refs.append(O.harris_graph(img)[0])
+        refs.append(None if tomasi else O.harris_graph(img)[0])
     singles = []
     for g, mk in zip(graphs, outs):
         H.hvxProcessGraph(g)
@@ -252,7 +256,10 @@ def test_harris_batch_one_launch(ctx):
         z = np.zeros((H.hvxQueryImage(mk)[1], H.hvxQueryImage(mk)[0]), np.uint8)
         H.hvxCopyImage(mk, z.ctypes.data, z.strides[0], H.HVX_WRITE)
     for want, ref in zip(singles, refs):
-        np.testing.assert_array_equal(want, ref)
+        if ref is not None:
+            np.testing.assert_array_equal(want, ref)
+    if mix != "harris":
+        assert singles[-1].any() and not singles[-1].all()
     for _ in range(2):
         H.hvxProcessGraphBatch(graphs)
         H.hvxWaitBatch(ctx)
@@ -329,3 +336,42 @@ def test_batches_from_two_host_threads(ctx):
     for t in ts:
         t.join()
     assert not errors, errors
+
+
+def test_calls_from_a_fresh_host_thread(ctx):
+    # a thread that has made no CUDA call yet: the batch call encodes its
+    # tensor maps and the generated kernel launches through the driver API,
+    # both in that thread
+    import threading
+    w, h = 300, 170
+    img = synth.rects_noise(w, h, seed=404)
+    src = PG.upload(ctx, img, H.HVX_DF_U8)
+    mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+    gh = PG.harris_graph(ctx, src, mk, thr=4.0e4, tomasi=True)
+    out = PG.empty(ctx, w, h, H.HVX_DF_U8)
+    gg = H.hvxCreateGraph(ctx)
+    m = H.hvxCreateVirtualImage(gg)
+    H.hvxSetNodeBorder(H.hvxMedian3x3Node(gg, src, m), H.HVX_BORDER_REPLICATE, 0)
+    H.hvxAbsDiffNode(gg, m, src, out)
+    H.hvxVerifyGraph(gg)
+    assert H.hvxQueryGraph(gg, H.HVX_GRAPH_GENERATED_KERNELS) == 1
+    errors = []
+
+    def work():
+        try:
+            for _ in range(3):
+                H.hvxProcessGraphBatch([gh])
+                H.hvxWaitBatch(ctx)
+                H.hvxProcessGraph(gg)
+        except Exception as e:  # reported to the main thread
+            errors.append(e)
+
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    assert not errors, errors
+    med = O.morph3x3(img, O.MORPH_MEDIAN, O.BORDER_REPLICATE)
+    want = O.arith(med, img, np.uint8, O.ARITH_ABSDIFF)
+    np.testing.assert_array_equal(PG.download(out), want.data)
+    got = PG.download(mk)
+    assert got.any() and not got.all()

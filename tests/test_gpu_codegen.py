@@ -263,10 +263,11 @@ def test_generated_source_query(ctx):
     H.hvxReleaseGraph(g)
 
 
-@pytest.mark.parametrize("name", ["FChain", "Tomasi", "Unsharp", "EdgFig2"])
+@pytest.mark.parametrize("name", ["FChain", "Tomasi", "Harris", "Unsharp", "EdgFig2"])
 def test_batched_generated_kernel(ctx, name):
     # graphs of the same shape on images of different sizes share one
-    # generated kernel: hvxProcessGraphBatch runs them in one launch
+    # generated kernel: hvxProcessGraphBatch runs them in one launch (the
+    # corner groups get theirs under HVX_CODEGEN_ONLY)
     from paper_2008_11476_gb300 import apps as A
     build = dict(A.APPS)[name]
     sizes = [(300, 250), (1, 1), (640, 480), (97, 45), (129, 33)]
@@ -275,6 +276,8 @@ def test_batched_generated_kernel(ctx, name):
         img = synth.rects_noise(w, h, seed=70 + i)
         src = PG.upload(ctx, img, H.HVX_DF_U8)
         g, res = build(ctx, src, w, h, True)
+        H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+        H.hvxVerifyGraph(g)
         assert H.hvxQueryGraph(g, H.HVX_GRAPH_GENERATED_KERNELS) == 1
         graphs.append(g)
         outs.append(res)

@@ -314,6 +314,77 @@ def check_resp(got, ref):
     np.testing.assert_array_equal(got, ref)  # single rounding of the exact value
 
 
+TOMASI_THR = 4.0e4
+
+
+def tomasi_oracle(img, border, cval=0):
+    og = OG.GraphDesc()
+    h, w = img.shape
+    og.image("in", w, h, "U8")
+    og.image("r", w, h, "F32")
+    for v in ("gx", "gy", "xx", "yy", "xy", "sxx", "syy", "sxy"):
+        og.virtual(v)
+    bn = {O.BORDER_UNDEFINED: "undefined", O.BORDER_REPLICATE: "replicate",
+          O.BORDER_CONSTANT: "constant"}[border]
+    og.node("sobel3x3", ["in"], ["gx", "gy"], border=bn, cval=cval)
+    og.node("mul", ["gx", "gx"], ["xx"])
+    og.node("mul", ["gy", "gy"], ["yy"])
+    og.node("mul", ["gx", "gy"], ["xy"])
+    for a, b in (("xx", "sxx"), ("yy", "syy"), ("xy", "sxy")):
+        og.node("window_sum", [a], [b], kw=5, kh=5, border=bn, cval=cval)
+    og.node("tomasi_response", ["sxx", "syy", "sxy"], ["r"])
+    return OG.run(og, {"in": img})["r"].data
+
+
+def run_tomasi(ctx, img, border, fusion=True, codegen=H.HVX_CODEGEN_AUTO, cval=0):
+    h, w = img.shape
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+    rs = PG.empty(ctx, w, h, H.HVX_DF_F32)
+    g = PG.harris_graph(ctx, inp, mk, rs, border=border, fusion=fusion, thr=TOMASI_THR,
+                        cval=cval, tomasi=True, verify=False)
+    H.hvxSetGraphCodegen(g, codegen)
+    H.hvxVerifyGraph(g)
+    kinds = PG.kernel_kinds(g)
+    H.hvxProcessGraph(g)
+    out = PG.download(mk), PG.download(rs)
+    H.hvxReleaseGraph(g)
+    return out, kinds
+
+
+@pytest.mark.parametrize("w,h", [(1, 1), (7, 7), (97, 45), (300, 200), (385, 361)])
+@pytest.mark.parametrize("border", BORDERS)
+def test_tomasi_on_the_corner_kernel(ctx, w, h, border):
+    # the Shi-Tomasi group runs on the hand-written corner kernels; its
+    # binary32 response is the point operator's, bit for bit, so the fused,
+    # generated and unfused forms agree exactly, and the oracle's singly
+    # rounded eigenvalue within a few units in the last place
+    img = synth.rects_noise(w, h, seed=5)
+    ref = tomasi_oracle(img, B_ORC[border], cval=5).astype(np.float64)
+    (mk, r), kinds = run_tomasi(ctx, img, border, cval=5)
+    assert kinds == ["fused_harris_tma"]
+    assert (np.abs(r - ref) <= 2e-6 * np.abs(ref)).all()
+    near = np.abs(ref - TOMASI_THR) <= 1e-5 * TOMASI_THR
+    np.testing.assert_array_equal((mk == 255)[~near], (ref > TOMASI_THR)[~near])
+    # without the exported response the UNDEFINED kernel decides from a cheaper
+    # estimate where that is safe: the same mask
+    h_, w_ = img.shape
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    mk1 = PG.empty(ctx, w_, h_, H.HVX_DF_U8)
+    g1 = PG.harris_graph(ctx, inp, mk1, None, border=border, thr=TOMASI_THR, cval=5, tomasi=True)
+    assert PG.kernel_kinds(g1) == ["fused_harris_tma"]
+    H.hvxProcessGraph(g1)
+    np.testing.assert_array_equal(PG.download(mk1), mk)
+    H.hvxReleaseGraph(g1)
+    (mk2, r2), kinds2 = run_tomasi(ctx, img, border, codegen=H.HVX_CODEGEN_ONLY, cval=5)
+    assert kinds2 == ["staged_tile"]
+    (mk3, r3), kinds3 = run_tomasi(ctx, img, border, fusion=False, cval=5)
+    assert len(kinds3) == 9
+    for m, x in ((mk2, r2), (mk3, r3)):
+        np.testing.assert_array_equal(m, mk)
+        np.testing.assert_array_equal(x.view(np.uint32), r.view(np.uint32))
+
+
 @pytest.mark.parametrize("w,h", [(1, 1), (7, 7), (64, 32), (97, 45), (300, 200), (385, 361)])
 @pytest.mark.parametrize("border", BORDERS)
 def test_harris_fused_and_plain(ctx, w, h, border):
