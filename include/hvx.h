@@ -291,8 +291,10 @@ hvx_status hvxSetGraphFusion(hvx_graph g, int32_t enable);
  * HVX_CODEGEN_*; marks the graph unverified.  HVX_CODEGEN_ROWS=1, 2 or 4 in
  * the environment overrides how many vertically adjacent cells a thread
  * computes per iteration of a generated pass (a tuning knob; results are
- * the same); HVX_CODEGEN_VERBOSE=1 prints why a group got no generated
- * kernel. */
+ * the same); HVX_CODEGEN_COLS=4 turns on 4-column blocks (vector loads
+ * and stores) in the output pass of 128-wide tiles (slower on the
+ * applications measured; kept for experiments);
+ * HVX_CODEGEN_VERBOSE=1 prints why a group got no generated kernel. */
 hvx_status hvxSetGraphCodegen(hvx_graph g, int32_t mode);
 
 /* Source text of the kernel generated for launch `group` of a verified graph

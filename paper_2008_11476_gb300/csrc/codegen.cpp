@@ -527,8 +527,9 @@ struct Emitter {
     // shared-memory value they read is loaded once into a named variable
     // (a window of k rows serves k cells).  While a row of the block is being
     // emitted, `row` is its index; reads register their (slot, row, column)
-    // in `loads`.
-    int row = -1;
+    // in `loads`.  The output pass of an unhaloed tile is also column-blocked
+    // (`col`: the cell's column in a block of 4 adjacent ones).
+    int row = -1, col = 0;
     mutable std::map<std::tuple<int, int, int>, std::string> loads;
     std::vector<bool> cell_read;  // staged buffers read at the cell itself this pass
 
@@ -546,13 +547,14 @@ struct Emitter {
     // Expression of the value of buffer b at the current cell.
     std::string val(int b) const {
         if (row < 0) return "v" + std::to_string(b);
-        if (cell_read[b]) return load_var(b, row, 0);
-        return "v" + std::to_string(b) + "_" + std::to_string(row);
+        if (cell_read[b]) return load_var(b, row, col);
+        return "v" + std::to_string(b) + "_" + std::to_string(row) +
+               (col ? "_" + std::to_string(col) : "");
     }
 
     // Read of staged buffer b at offset (dx, dy) from the current cell.
     std::string tap(int b, int dx, int dy) const {
-        if (row >= 0) return load_var(b, row + dy, dx);
+        if (row >= 0) return load_var(b, row + dy, dx + col);
         const int off = dy * slot_w(b) + dx;
         std::string s = "B" + std::to_string(b) + "[q" + std::to_string(b);
         if (off > 0) s += " + " + std::to_string(off);
@@ -818,6 +820,10 @@ struct Emitter {
         const int b = st.in[0], hb = d.buf[b].halo, hl = d.buf[st.out].halo;
         const Slot& R = slot[row_slot(k)];
         o << "  // row sums of op " << k << " -> R" << k << " (" << R.w << " x " << R.h << ")\n";
+        if (R.w % 128 == 0) {
+            emit_row4(k);
+            return;
+        }
         open_cells(R.h, R.w, 0, 0, false, false);
         o << "      const int q = (r + " << hb - hl - st.ry << ") * " << slot_w(b) << " + c + "
           << hb - hl + slot_x(b) << ";\n";
@@ -840,6 +846,60 @@ struct Emitter {
         close_cells();
     }
 
+    // Row sums of 4 adjacent cells per thread (rows of a multiple of 128
+    // cells): the 4 + 2 rx input values of the block are read once -- from a
+    // byte slot as the aligned 32-bit words that hold them, the bytes taken by
+    // shifts -- and the 4 sums go out in one 16-byte store.  Values and their
+    // order of summation are the scalar form's.
+    void emit_row4(int k) {
+        const GenStage& st = d.st[k];
+        const int b = st.in[0], hb = d.buf[b].halo, hl = d.buf[st.out].halo;
+        const Slot& R = slot[row_slot(k)];
+        const int rx = st.rx, n = 4 + 2 * rx;
+        const int dr = hb - hl - st.ry;          // slot row of block row r
+        const int lo = hb - hl + slot_x(b) - rx;  // slot column of value 0 minus c
+        const bool lsum = st.op == OP_LSUM;
+        o << "  #pragma unroll 1\n"
+          << "  for (int r = warp; r < " << R.h << "; r += " << kThreads / 32 << ") {\n"
+          << "    #pragma unroll\n"
+          << "    for (int c = 4 * lane; c < " << R.w << "; c += 128) {\n";
+        std::vector<std::string> u(n);
+        if (byte_slot(b)) {
+            const int m = lo & 3, nw = (m + n + 3) / 4;
+            o << "      const unsigned* const wp = (const unsigned*)B" << b << " + (r + " << dr
+              << ") * " << slot_w(b) / 4 << " + (c >> 2) + " << (lo - m) / 4 << ";\n";
+            for (int w = 0; w < nw; ++w) o << "      const unsigned w" << w << " = wp[" << w << "];\n";
+            for (int i = 0; i < n; ++i) {
+                const int pw = (m + i) / 4, pb = (m + i) % 4;
+                u[i] = "u" + std::to_string(i);
+                o << "      const int " << u[i] << " = (int)((w" << pw << " >> " << 8 * pb
+                  << ") & 0xFFu);\n";
+            }
+        } else {
+            o << "      const int q = (r + " << dr << ") * " << slot_w(b) << " + c + " << lo << ";\n";
+            for (int i = 0; i < n; ++i) {
+                u[i] = "u" + std::to_string(i);
+                o << "      const int " << u[i] << " = B" << b << "[q + " << i << "];\n";
+            }
+        }
+        for (int j = 0; j < 4; ++j) {
+            o << "      " << (lsum ? "unsigned" : "int") << " t" << j << " = 0;\n";
+            for (int jj = 0; jj < (int)sep_s[k].size(); ++jj) {
+                const int c = sep_s[k][jj];
+                if (c == 0) continue;
+                const std::string& rd = u[j + jj];
+                if (lsum)
+                    o << "      t" << j << " += (unsigned)" << rd << ";\n";
+                else
+                    o << "      t" << j << " += " << (c == 1 ? "" : std::to_string(c) + " * ") << rd
+                      << ";\n";
+            }
+        }
+        o << "      *(int4*)&R" << k << "[r * " << R.w << " + c] = make_int4((int)t0, (int)t1, "
+          << "(int)t2, (int)t3);\n"
+          << "    }\n  }\n";
+    }
+
     // Column sum of separable stage k at the current cell of a pass of halo h.
     void emit_sep(int k, const std::string& dst, const std::string& ind) {
         const GenStage& st = d.st[k];
@@ -851,7 +911,7 @@ struct Emitter {
             if (c == 0) continue;
             const int off = (i - st.ry) * R.w;
             const std::string rd =
-                row >= 0 ? load_var(row_slot(k), row + i - st.ry, 0)
+                row >= 0 ? load_var(row_slot(k), row + i - st.ry, col)
                          : "R" + std::to_string(k) + "[qR" + std::to_string(k) +
                                (off > 0 ? " + " + std::to_string(off)
                                         : off < 0 ? " - " + std::to_string(-off) : "") +
@@ -873,6 +933,32 @@ struct Emitter {
         o << ind << "}\n";
     }
 
+    // Interior tiles of a column-blocked output pass: the 4 values of row i of
+    // the block go out in one 4-, 8- or 16-byte store per output (columns
+    // xc .. xc + 3 of an image whose rows start 16-byte aligned).
+    void emit_vector_stores(int i, int h) {
+        for (int e = 0; e < d.n_out; ++e) {
+            const int f = d.out[e].fmt;
+            const std::string v = "so" + std::to_string(e) + "_" + std::to_string(i) + "_";
+            o << "      if (!CHECK && va" << e << ") {\n"
+              << "        unsigned char* const rp = (unsigned char*)p.out[" << e
+              << "] + (unsigned long long)(y0 + rb + " << i - h << ") * p.out_pitch[" << e
+              << "];\n";
+            if (f == HVX_DF_U8)
+                o << "        *(unsigned*)(rp + xc) = ((unsigned)" << v << "0 & 0xFFu) | (((unsigned)"
+                  << v << "1 & 0xFFu) << 8) | (((unsigned)" << v << "2 & 0xFFu) << 16) | ((unsigned)"
+                  << v << "3 << 24);\n";
+            else if (f == HVX_DF_S16)
+                o << "        *(uint2*)(rp + 2 * xc) = make_uint2(((unsigned)" << v
+                  << "0 & 0xFFFFu) | ((unsigned)" << v << "1 << 16), ((unsigned)" << v
+                  << "2 & 0xFFFFu) | ((unsigned)" << v << "3 << 16));\n";
+            else
+                o << "        *(int4*)(rp + 4 * xc) = make_int4(" << v << "0, " << v << "1, " << v
+                  << "2, " << v << "3);\n";
+            o << "      }\n";
+        }
+    }
+
     // One pass over the cells of halo p.h producing the pass's staged
     // buffers or, for the last pass, the external outputs (and the global
     // operators' partial results).  Row-blocked: see `row`.
@@ -888,12 +974,32 @@ struct Emitter {
             if ((v == 1 || v == 2 || v == 4) && BH % v == 0) RB = v;
         }
         const bool outputs = p.kind == OUT;
+        // HVX_CODEGEN_COLS=4: the output pass of an unhaloed tile in blocks
+        // of 4 adjacent columns (vector loads of the values they read, one
+        // vector store per row of a block on interior tiles) and at most 2
+        // rows.  Off by default: on the Section 6 applications it measured 3
+        // to 14 % slower than 4 rows x 1 column (more live registers under
+        // the 32-register bound of 8 resident CTAs per SM).
+        const char* env_cols = getenv("HVX_CODEGEN_COLS");
+        const bool cols_on = env_cols && atoi(env_cols) == 4;
+        const int CB = outputs && h == 0 && BW % 128 == 0 && RB > 1 && cols_on ? 4 : 1;
+        if (CB > 1 && RB > 2) RB = 2;
         o << "  // pass: ";
         if (outputs)
             o << "external outputs";
         else
             for (int b : p.targets) o << "B" << b << " ";
-        o << "(halo " << h << ", " << RB << " rows per thread iteration)\n";
+        o << "(halo " << h << ", " << RB << " rows";
+        if (CB > 1) o << " x " << CB << " columns";
+        o << " per thread iteration)\n";
+        std::vector<bool> vec_ok(d.n_out, false);
+        if (CB > 1)
+            for (int e = 0; e < d.n_out; ++e) {
+                // vector stores need the row starts 16-byte aligned
+                o << "  const bool va" << e << " = ((reinterpret_cast<unsigned long long>(p.out["
+                  << e << "]) | p.out_pitch[" << e << "]) & 15) == 0;\n";
+                vec_ok[e] = true;
+            }
         if (outputs)
             for (int k : globals) {
                 if (d.st[k].op == OP_MEANSTD)
@@ -906,8 +1012,8 @@ struct Emitter {
           << "  for (int rb = warp * " << RB << "; rb < " << BH << "; rb += " << kThreads / 32 * RB
           << ") {\n"
           << "    #pragma unroll\n"
-          << "    for (int c = lane; c < " << BW << "; c += 32) {\n"
-          << "      const int x = x0 + c - " << h << ";\n";
+          << "    for (int c = lane * " << CB << "; c < " << BW << "; c += " << 32 * CB << ") {\n"
+          << "      const int xc = x0 + c - " << h << ";\n";
         // the rows of the block, into a buffer: their reads decide the loads
         const std::string prefix = o.str();
         o.str("");
@@ -915,8 +1021,17 @@ struct Emitter {
         loads.clear();
         cell_read = p.read_cell;
         for (int i = 0; i < RB; ++i) {
+          if (CB > 1)
+              for (int e = 0; e < d.n_out; ++e) {
+                  o << "      int";
+                  for (int j = 0; j < CB; ++j)
+                      o << (j ? "," : "") << " so" << e << "_" << i << "_" << j << " = 0";
+                  o << ";\n";
+              }
+          for (int j = 0; j < CB; ++j) {
             row = i;
-            o << "      {\n        const int y = y0 + rb + " << i - h << ";\n"
+            col = j;
+            o << "      {\n        const int x = xc + " << j << ", y = y0 + rb + " << i - h << ";\n"
               << "        const bool in_img = !CHECK || (x >= 0 && x < p.W && y >= 0 && y < p.H);\n";
             for (int b = 0; b < d.n_buf; ++b)
                 if (p.need_ld[b]) {
@@ -940,9 +1055,17 @@ struct Emitter {
             }
             o << "        if (in_img) {\n";
             if (outputs) {
-                for (int e = 0; e < d.n_out; ++e)
-                    o << "          hvx_st<" << d.out[e].fmt << ">(p.out[" << e << "], p.out_pitch["
-                      << e << "], x, y, " << val(d.out[e].buf) << ");\n";
+                for (int e = 0; e < d.n_out; ++e) {
+                    const std::string st = "hvx_st<" + std::to_string(d.out[e].fmt) + ">(p.out[" +
+                                           std::to_string(e) + "], p.out_pitch[" +
+                                           std::to_string(e) + "], x, y, " + val(d.out[e].buf) +
+                                           ");\n";
+                    if (CB > 1)
+                        o << "          so" << e << "_" << i << "_" << j << " = "
+                          << val(d.out[e].buf) << ";\n          if (CHECK || !va" << e << ") " << st;
+                    else
+                        o << "          " << st;
+                }
                 for (int k : globals) {
                     const GenStage& st = d.st[k];
                     const std::string v = val(st.in[0]), g = "g" + std::to_string(k);
@@ -967,8 +1090,11 @@ struct Emitter {
                       << ";\n";
             }
             o << "        }\n      }\n";
+          }
+          if (CB > 1) emit_vector_stores(i, h);
         }
         row = -1;
+        col = 0;
         const std::string rows = o.str();
         o.str("");
         o.clear();
@@ -989,14 +1115,56 @@ struct Emitter {
                   << slot[s].w << " + c + " << dh << ";\n";
             }
         }
-        for (const auto& kv : loads) {
-            const int s = std::get<0>(kv.first), r = std::get<1>(kv.first),
-                      dx = std::get<2>(kv.first);
-            const int off = r * slot[s].w + dx;
-            o << "      const int " << kv.second << " = " << slot_name(s) << "[qb" << s
-              << (off > 0 ? " + " + std::to_string(off)
-                          : off < 0 ? " - " + std::to_string(-off) : "")
-              << "];\n";
+        auto plus = [](int v) {
+            return v > 0 ? " + " + std::to_string(v) : v < 0 ? " - " + std::to_string(-v) : "";
+        };
+        // reads of one slot row, grouped; in column blocks they are covered by
+        // aligned chunks of 4 values (one 16-byte load from an int32 slot, one
+        // 32-bit word from a byte slot) when the row stride keeps rows aligned
+        std::map<std::pair<int, int>, std::vector<std::pair<int, std::string>>> groups;
+        for (const auto& kv : loads)
+            groups[{std::get<0>(kv.first), std::get<1>(kv.first)}].push_back(
+                {std::get<2>(kv.first), kv.second});
+        for (const auto& g : groups) {
+            const int s = g.first.first, r = g.first.second, w = slot[s].w, base = r * w;
+            if (CB == 1 || w % 4 != 0) {
+                for (const auto& dn : g.second)
+                    o << "      const int " << dn.second << " = " << slot_name(s) << "[qb" << s
+                      << plus(base + dn.first) << "];\n";
+                continue;
+            }
+            // qb's constant part (rb and c are multiples of 4 here, and so is w)
+            int c0;
+            if (s < d.n_buf) {
+                const int dh = d.buf[s].halo - h;
+                c0 = dh * w + dh + slot_x(s);
+            } else {
+                const int k = s - d.n_buf, dh = d.buf[d.st[k].out].halo - h;
+                c0 = (dh + d.st[k].ry) * w + dh;
+            }
+            int lo = g.second.front().first;
+            for (const auto& dn : g.second) lo = std::min(lo, dn.first);
+            const int a = ((c0 + lo) & ~3) - c0;  // first chunk, from qb + base
+            std::map<int, std::string> chunk;
+            for (const auto& dn : g.second) {
+                const int k = (dn.first - a) >> 2, comp = (dn.first - a) & 3;
+                std::string& L = chunk[k];
+                if (L.empty()) {
+                    L = "L" + std::to_string(s) + "_" + enc(r) + "_" + std::to_string(k);
+                    if (byte_slot(s))
+                        o << "      const unsigned " << L << " = ((const unsigned*)" << slot_name(s)
+                          << ")[(qb" << s << plus(base + a + 4 * k) << ") >> 2];\n";
+                    else
+                        o << "      const int4 " << L << " = *(const int4*)&" << slot_name(s)
+                          << "[qb" << s << plus(base + a + 4 * k) << "];\n";
+                }
+                if (byte_slot(s))
+                    o << "      const int " << dn.second << " = (int)((" << L << " >> " << 8 * comp
+                      << ") & 0xFFu);\n";
+                else
+                    o << "      const int " << dn.second << " = " << L << "." << "xyzw"[comp]
+                      << ";\n";
+            }
         }
         o << rows << "    }\n  }\n";
         if (outputs) {

@@ -47,14 +47,32 @@ def test_constants_are_folded(pctx):
     # Laplacian: the four zero taps of the 3x3 kernel are dropped and the sum
     # of U8 inputs with coefficients up to 4 is accumulated in 32 bits
     s = H.hvxGetGraphKernelSource(_gen(pctx, A.laplacian), 0)
-    rows = int(s.split(" rows per thread iteration")[0].rsplit(" ", 1)[1])
-    assert s.count("t += ") == 5 * rows  # one block of `rows` cells per iteration
+    m = re.search(r"(\d+) rows(?: x (\d+) columns)? per thread iteration", s)
+    rows, cols = int(m.group(1)), int(m.group(2) or 1)
+    # one block of rows x cols cells per iteration
+    assert s.count("t += ") == 5 * rows * cols
     assert "long long t" not in s
-    # a cross of 5 taps over 4 rows reads 14 distinct values, not 20
-    assert s.count("= B0[qb0") == 14 if rows == 4 else True
+    if rows == 4:
+        # a cross of 5 taps over 4 rows reads 14 distinct values, not 20
+        assert s.count("= B0[qb0") == 14
     # the threshold of the Sobel application is a literal
     s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel), 0)
     assert "(100LL)" in s
+
+
+def test_column_blocks(pctx, monkeypatch):
+    # HVX_CODEGEN_COLS=4: the output pass in blocks of 2 rows x 4 columns
+    monkeypatch.setenv("HVX_CODEGEN_COLS", "4")
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.laplacian, 1000, 600), 0)
+    m = re.search(r"(\d+) rows(?: x (\d+) columns)? per thread iteration", s)
+    rows, cols = int(m.group(1)), int(m.group(2) or 1)
+    assert (rows, cols) == (2, 4)
+    assert s.count("t += ") == 5 * rows * cols
+    # a cross of 5 taps over 2 rows x 4 columns reads 20 distinct values,
+    # not 40, from at most 3 aligned words of each of the 4 input rows
+    assert len(set(re.findall(r"const int (t0_\w+) = ", s))) == 20
+    assert s.count("const unsigned L0_") <= 12
+    assert "if (!CHECK && va0)" in s
 
 
 def test_products_share_one_pass(pctx):

@@ -471,3 +471,25 @@ def test_user_defined_operators(ctx, border, w, h):
     np.testing.assert_array_equal(PG.download(out), ref.data)
     assert H.hvxGetValidRegion(out) == ref.rect
     H.hvxReleaseGraph(g)
+
+
+@pytest.mark.parametrize("name", ["Laplacian", "Sobel", "Unsharp", "Gauss"])
+@pytest.mark.parametrize("w,h", [(1920, 1080), (385, 361)])
+def test_column_blocks_match_the_interpreter(ctx, name, w, h, monkeypatch):
+    # HVX_CODEGEN_COLS=4 (output pass in 2 x 4 cell blocks, vector loads,
+    # vector stores on interior tiles) gives the interpreter's results
+    from paper_2008_11476_gb300 import apps as A
+    monkeypatch.setenv("HVX_CODEGEN_COLS", "4")
+    build = dict(A.APPS)[name]
+    img = synth.rects_noise(w, h, seed=w + h)
+    g, res = build(ctx, PG.upload(ctx, img, H.HVX_DF_U8), w, h, True)
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_REQUIRE)
+    H.hvxVerifyGraph(g)
+    assert "columns per thread iteration" in H.hvxGetGraphKernelSource(g, 0)
+    H.hvxProcessGraph(g)
+    g2, res2 = build(ctx, PG.upload(ctx, img, H.HVX_DF_U8), w, h, True)
+    H.hvxSetGraphCodegen(g2, H.HVX_CODEGEN_OFF)
+    H.hvxVerifyGraph(g2)
+    H.hvxProcessGraph(g2)
+    for (_, a, _), (_, b, _) in zip(res, res2):
+        np.testing.assert_array_equal(PG.download(a), PG.download(b))
