@@ -530,6 +530,7 @@ struct Emitter {
     // in `loads`.  The output pass of an unhaloed tile is also column-blocked
     // (`col`: the cell's column in a block of 4 adjacent ones).
     int row = -1, col = 0;
+    const std::vector<bool>* need_now = nullptr;  // stages evaluated inline in the current pass
     mutable std::map<std::tuple<int, int, int>, std::string> loads;
     std::vector<bool> cell_read;  // staged buffers read at the cell itself this pass
 
@@ -571,7 +572,24 @@ struct Emitter {
             case OP_PHASE: return "(int)phase_u8(" + a + ", " + b + ")";
             case OP_THRESH: {
                 std::string t;
-                if (st.i3) {
+                const int pm = producer[st.in[0]];
+                if (!st.i3 && st.i0 == HVX_THRESHOLD_BINARY && pm >= 0 && d.st[pm].op == OP_MAG &&
+                    need_now && (*need_now)[pm]) {
+                    // Magnitude -> binary threshold: round(sqrt(s)) > T is s > T^2 + T
+                    // for 0 <= T < 32767 (s = gx^2 + gy^2 an integer, the rounding
+                    // half up, ties impossible); always for T < 0 and never for
+                    // T >= 32767 (the magnitude saturates at 32767)
+                    const long long T = st.k0;
+                    if (T < 0) {
+                        t = "true";
+                    } else if (T >= 32767) {
+                        t = "false";
+                    } else {
+                        const std::string gx = val(d.st[pm].in[0]), gy = val(d.st[pm].in[1]);
+                        t = "((unsigned)(" + gx + " * " + gx + ") + (unsigned)(" + gy + " * " + gy +
+                            ") > " + std::to_string(T * T + T) + "u)";
+                    }
+                } else if (st.i3) {
                     const std::string f = "__int_as_float(" + a + ")";
                     t = st.i0 == HVX_THRESHOLD_BINARY
                             ? "(" + f + " > " + flit(st.f0) + ")"
@@ -1020,6 +1038,7 @@ struct Emitter {
         o.clear();
         loads.clear();
         cell_read = p.read_cell;
+        need_now = &p.need_op;
         for (int i = 0; i < RB; ++i) {
           if (CB > 1)
               for (int e = 0; e < d.n_out; ++e) {
@@ -1095,6 +1114,7 @@ struct Emitter {
         }
         row = -1;
         col = 0;
+        need_now = nullptr;
         const std::string rows = o.str();
         o.str("");
         o.clear();

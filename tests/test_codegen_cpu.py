@@ -55,9 +55,10 @@ def test_constants_are_folded(pctx):
     if rows == 4:
         # a cross of 5 taps over 4 rows reads 14 distinct values, not 20
         assert s.count("= B0[qb0") == 14
-    # the threshold of the Sobel application is a literal
+    # the Sobel application's Magnitude -> Threshold(100) is the integer
+    # compare gx^2 + gy^2 > 100^2 + 100, with the bound a literal
     s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel), 0)
-    assert "(100LL)" in s
+    assert "> 10100u)" in s
 
 
 def test_column_blocks(pctx, monkeypatch):

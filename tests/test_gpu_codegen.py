@@ -493,3 +493,38 @@ def test_column_blocks_match_the_interpreter(ctx, name, w, h, monkeypatch):
     H.hvxProcessGraph(g2)
     for (_, a, _), (_, b, _) in zip(res, res2):
         np.testing.assert_array_equal(PG.download(a), PG.download(b))
+
+
+@pytest.mark.parametrize("thr", [-5, 0, 1, 100, 1441, 32766, 32767, 40000])
+def test_magnitude_threshold_compare(ctx, thr):
+    # the generated kernel decides Magnitude -> Threshold as the integer
+    # compare gx^2 + gy^2 > T^2 + T; the interpreter computes the rounded,
+    # saturated magnitude first; both must give the oracle's mask.  S16
+    # gradients from a 5x5 convolution reach magnitudes past 32767
+    import oracle as O
+    w, h = 333, 201
+    img = synth.rects_noise(w, h, seed=thr & 0xFFFF)
+    big = np.full((5, 5), 60, np.int32)
+    big[:, :2] = -60
+    outs = []
+    for mode in (H.HVX_CODEGEN_REQUIRE, H.HVX_CODEGEN_OFF):
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        mk = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        g = H.hvxCreateGraph(ctx)
+        gx, gy, m = (H.hvxCreateVirtualImage(g) for _ in range(3))
+        a = H.hvxCreateVirtualImage(g, 0, 0, H.HVX_DF_S16)
+        H.hvxSetNodeBorder(H.hvxConvolveNode(g, src, big.ravel(), 5, 5, 0, a),
+                           H.HVX_BORDER_REPLICATE, 0)
+        H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, src, gx, gy), H.HVX_BORDER_REPLICATE, 0)
+        H.hvxMagnitudeNode(g, a, gy, m)
+        H.hvxThresholdNode(g, m, H.HVX_THRESHOLD_BINARY, thr, 0, 255, 0, mk)
+        H.hvxSetGraphCodegen(g, mode)
+        H.hvxVerifyGraph(g)
+        H.hvxProcessGraph(g)
+        outs.append(PG.download(mk))
+        H.hvxReleaseGraph(g)
+    ga = O.convolve(img, big, 0, O.BORDER_REPLICATE)
+    _, gyo = O.sobel3x3(img, O.BORDER_REPLICATE)
+    want = O.threshold(O.magnitude(ga, gyo), thr).data
+    np.testing.assert_array_equal(outs[0], want)
+    np.testing.assert_array_equal(outs[1], want)
