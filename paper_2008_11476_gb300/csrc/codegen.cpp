@@ -838,11 +838,18 @@ struct Emitter {
         const int b = st.in[0], hb = d.buf[b].halo, hl = d.buf[st.out].halo;
         const Slot& R = slot[row_slot(k)];
         o << "  // row sums of op " << k << " -> R" << k << " (" << R.w << " x " << R.h << ")\n";
-        if (R.w % 128 == 0) {
-            emit_row4(k);
-            return;
+        // columns [0, W4) four at a time, the rest one cell per thread
+        const int W4 = R.w & ~127;
+        if (W4 > 0) emit_row4(k, W4);
+        if (W4 == R.w) return;
+        if (W4 > 0) {
+            const int rest = R.w - W4;
+            o << "  for (int i = threadIdx.x; i < " << R.h * rest << "; i += " << kThreads
+              << ") {\n    {\n      const int r = i / " << rest << ", c = " << W4 << " + i % "
+              << rest << ";\n";
+        } else {
+            open_cells(R.h, R.w, 0, 0, false, false);
         }
-        open_cells(R.h, R.w, 0, 0, false, false);
         o << "      const int q = (r + " << hb - hl - st.ry << ") * " << slot_w(b) << " + c + "
           << hb - hl + slot_x(b) << ";\n";
         const bool lsum = st.op == OP_LSUM;
@@ -864,12 +871,13 @@ struct Emitter {
         close_cells();
     }
 
-    // Row sums of 4 adjacent cells per thread (rows of a multiple of 128
-    // cells): the 4 + 2 rx input values of the block are read once -- from a
-    // byte slot as the aligned 32-bit words that hold them, the bytes taken by
-    // shifts -- and the 4 sums go out in one 16-byte store.  Values and their
-    // order of summation are the scalar form's.
-    void emit_row4(int k) {
+    // Row sums of 4 adjacent cells per thread over columns [0, W) (W a
+    // multiple of 128): the 4 + 2 rx input values of the block are read once
+    // -- from a byte slot as the aligned 32-bit words that hold them, the
+    // bytes taken by shifts -- and the 4 sums go out in one 16-byte store (two
+    // 8-byte stores when the row length is not a multiple of 4).  Values and
+    // their order of summation are the scalar form's.
+    void emit_row4(int k, int W) {
         const GenStage& st = d.st[k];
         const int b = st.in[0], hb = d.buf[b].halo, hl = d.buf[st.out].halo;
         const Slot& R = slot[row_slot(k)];
@@ -880,7 +888,7 @@ struct Emitter {
         o << "  #pragma unroll 1\n"
           << "  for (int r = warp; r < " << R.h << "; r += " << kThreads / 32 << ") {\n"
           << "    #pragma unroll\n"
-          << "    for (int c = 4 * lane; c < " << R.w << "; c += 128) {\n";
+          << "    for (int c = 4 * lane; c < " << W << "; c += 128) {\n";
         std::vector<std::string> u(n);
         if (byte_slot(b)) {
             const int m = lo & 3, nw = (m + n + 3) / 4;
@@ -913,9 +921,17 @@ struct Emitter {
                       << ";\n";
             }
         }
-        o << "      *(int4*)&R" << k << "[r * " << R.w << " + c] = make_int4((int)t0, (int)t1, "
-          << "(int)t2, (int)t3);\n"
-          << "    }\n  }\n";
+        if (R.w % 4 == 0)
+            o << "      *(int4*)&R" << k << "[r * " << R.w << " + c] = make_int4((int)t0, (int)t1, "
+              << "(int)t2, (int)t3);\n";
+        else if (R.w % 2 == 0)
+            o << "      *(int2*)&R" << k << "[r * " << R.w << " + c] = make_int2((int)t0, (int)t1);\n"
+              << "      *(int2*)&R" << k << "[r * " << R.w << " + c + 2] = make_int2((int)t2, "
+              << "(int)t3);\n";
+        else
+            for (int j = 0; j < 4; ++j)
+                o << "      R" << k << "[r * " << R.w << " + c + " << j << "] = (int)t" << j << ";\n";
+        o << "    }\n  }\n";
     }
 
     // Column sum of separable stage k at the current cell of a pass of halo h.
