@@ -677,26 +677,15 @@ int edge_mode(const EdgeParams& p) {
     return M_PHASE;
 }
 
-// Rows per thread of the single-image kernel: R in 2 .. EDGE_ROWS minimising
-// the busiest SM's time, modelled as (CTAs on it) x (R + 2 Gaussian rows it
-// walks) / min(CTAs on it, 4) (up to 4 resident CTAs hide each other's
-// latency); ties go to the larger R.  A 1920 x 1080 image gets R = 4 (510
-// tiles), where the batch kernel's R = 15 would give 135 tiles for 152 SMs.
+// Rows per thread of the single-image kernel: R = 5 (2 Gaussian halo rows per
+// 5 output rows; 405 CTAs on 1920 x 1080, 1620 on 3840 x 2160), or R = 2 when
+// an image has fewer 128 x 40 tiles than SMs (the most CTAs for a small
+// image).  Measured per launch, back to back, on 640x480 / 1920x1080 /
+// 3840x2160: R = 2 8.2 / 12.8 / 26.6 us, R = 5 12.3 / 12.3 / 24.6 us, R = 15
+// 20.6 / 20.5 / 26.7 us (timer steps of 2.05 us).
 int edge_single_rows(int W, int H, int num_sms) {
-    const int tx = (W + TW - 1) / TW;
-    const int S = num_sms > 0 ? num_sms : 152;
-    int best = ROWS;
-    double best_cost = 0;
-    for (int R = ROWS; R >= 2; --R) {
-        const long long n = (long long)tx * ((H + 8 * R - 1) / (8 * R));
-        const long long c = (n + S - 1) / S;
-        const double cost = (double)c * (R + 2) / (double)(c < 4 ? c : 4);
-        if (R == ROWS || cost < best_cost) {
-            best = R;
-            best_cost = cost;
-        }
-    }
-    return best;
+    const long long tiles5 = (long long)((W + TW - 1) / TW) * ((H + 39) / 40);
+    return tiles5 >= (num_sms > 0 ? num_sms : 152) ? 5 : 2;
 }
 
 void edge_tile_dims(int mode, int* tw, int* th) {

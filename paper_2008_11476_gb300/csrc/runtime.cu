@@ -214,6 +214,10 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
     // one image per launch: R rows per thread, a 160 x (8R + 4) box (the
     // batch kernel encodes its own 160 x EDGE_LOAD_H maps)
     e.rows = edge_single_rows((int)G.W, (int)G.H, ctx->num_sms);
+    if (const char* env = getenv("HVX_EDGE_ROWS")) {  // tuning knob: 2 .. EDGE_ROWS
+        const int r = atoi(env);
+        if (r >= 2 && r <= EDGE_ROWS) e.rows = r;
+    }
     return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));
 }
 
