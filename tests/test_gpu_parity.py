@@ -409,6 +409,26 @@ def test_harris_full_size_4096x2160(ctx):
     check_resp(r, ref_r)
 
 
+def test_tomasi_full_size_4096x2160(ctx):
+    # the Shi-Tomasi group at full size on the corner kernel, with the
+    # response exported and (second run) without it, where the threshold is
+    # decided from the estimate: both masks equal, and equal to the oracle's
+    # eigenvalue test away from the threshold
+    img = synth.rects_noise(4096, 2160, seed=9)
+    ref = tomasi_oracle(img, O.BORDER_UNDEFINED).astype(np.float64)
+    (mk, r), kinds = run_tomasi(ctx, img, H.HVX_BORDER_UNDEFINED)
+    assert kinds == ["fused_harris_tma"]
+    assert (np.abs(r - ref) <= 2e-6 * np.abs(ref)).all()
+    near = np.abs(ref - TOMASI_THR) <= 1e-5 * TOMASI_THR
+    np.testing.assert_array_equal((mk == 255)[~near], (ref > TOMASI_THR)[~near])
+    inp = PG.upload(ctx, img, H.HVX_DF_U8)
+    mk1 = PG.empty(ctx, 4096, 2160, H.HVX_DF_U8)
+    g = PG.harris_graph(ctx, inp, mk1, None, thr=TOMASI_THR, tomasi=True)
+    H.hvxProcessGraph(g)
+    np.testing.assert_array_equal(PG.download(mk1), mk)
+    H.hvxReleaseGraph(g)
+
+
 @pytest.mark.parametrize("w,h", [(1000, 700), (129, 241)])
 def test_harris_mask_only_undefined(ctx, w, h):
     # the BORDER_UNDEFINED kernel without the response export (the benchmark's
