@@ -10,10 +10,15 @@ launch (hvxProcessGraphBatch, replayed from a captured CUDA graph).  The batch
 
 The line reports: fused Mpix/s (value); the unfused one-launch-per-node form
 on the same frames; the HBM roofline of the fused kernel on external bytes; an
-end-to-end number with host<->device copies in the timed region; a short
-serving run (Poisson arrivals of a Gaussian / edge / Harris mix) with p50 / p99
-latency against one-request-at-a-time unfused serving; the CPU oracle timed on
-the host (cpu_baseline); SM clocks sampled during the timed region.
+end-to-end number with host<->device copies in the timed region; the other
+workloads under "configs" (Gaussian3x3 on one 640x480 image per launch, the
+Harris graph on 4096x2160, 256 images of uneven sizes in one launch, batched
+Gaussian3x3 on 1080p frames), each with its own timing, roofline and clocks;
+serving (Poisson arrivals of a Gaussian / edge / Harris mix) with p50 / p99
+latency against one-request-at-a-time unfused serving, at 2000 req/s and at
+saturation; the CPU oracle timed on the host (cpu_baseline), whose outputs on
+the sampled frames are also compared with the GPU's (parity); SM clocks
+sampled during each timed region.
 
 --impl reference times the CPU oracle on the same metric (the reference arm).
 --workload gauss | harris | batch | serve measure the other workloads:
@@ -29,8 +34,10 @@ the host (cpu_baseline); SM clocks sampled during the timed region.
   apps    the nine applications of the paper's evaluation (Gauss .. Tomasi)
           on 1920x1080 frames, fused vs unfused
 
-Multi-GPU (torchrun, one rank per GPU): replicas only -- every rank runs the
-same per-GPU batch on its own frames; value = all frames / max rank time.
+Multi-GPU (one rank per GPU, launched by torch.distributed.run; a bare
+`--gpus N` with N > 1 re-launches itself that way): replicas only -- every
+rank runs the same per-GPU batch on its own frames; value = all frames / max
+rank time.
 """
 from __future__ import annotations
 
@@ -65,6 +72,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="edge workload: skip the other workloads' sub-results")
     ap.add_argument("--e2e-streams", type=int, default=2,
                     help="edge workload: streams the end-to-end calls rotate over")
     ap.add_argument("--e2e-chunks", type=int, default=2,
@@ -161,10 +170,14 @@ def kernel_source_hash(files=EDGE_SOURCES) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(kernel: str, frames: int):
-    """DRAM bytes per launch from the committed ncu record, or None when the
-    kernel's sources changed since the counters were taken or the launch
-    size differs."""
+EDGE_KERNEL = "edge_batch_kernel<MASK_PHASE>"
+
+
+def recorded_counters(kernel: str, frames: int):
+    """The committed ncu record of `kernel` (profiles/dram_traffic.json):
+    DRAM bytes and thread-instructions per pixel of one launch of `frames`
+    frames, or None when the kernel's sources changed since the counters were
+    taken or the launch size differs."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f).get(kernel)
@@ -172,18 +185,28 @@ def recorded_traffic(kernel: str, frames: int):
         return None
     if not rec or rec.get("source_sha256") != kernel_source_hash() or rec.get("frames") != frames:
         return None
-    return int(rec["dram_read_bytes"] + rec["dram_write_bytes"])
+    return rec
 
 
-# Thread-instructions per output pixel of edge_batch_kernel<MASK_PHASE>
-# (ncu smsp__inst_executed.sum x 32 / pixels of one 64-frame launch; the
-# capture is summarised in profiles/edge_batch_kernel_1080p.md).
-EDGE_INSTR_PER_PX = 49.9
+def recorded_traffic(kernel: str, frames: int):
+    rec = recorded_counters(kernel, frames)
+    return None if rec is None else int(rec["dram_read_bytes"] + rec["dram_write_bytes"])
+
+
+def recorded_instr_per_px(kernel: str, frames: int):
+    """Thread-instructions per output pixel (ncu smsp__inst_executed.sum x 32
+    / pixels of the launch), from the same hash-checked record."""
+    rec = recorded_counters(kernel, frames)
+    if rec is None or not rec.get("warp_instructions") or not rec.get("pixels"):
+        return None
+    return round(32.0 * rec["warp_instructions"] / rec["pixels"], 1)
 
 
 def issue_roofline(mpix_s, instr_per_px, clocks):
     """Instruction-issue roofline of a kernel bound by issue: achieved
     thread-instructions/s against 152 SMs x 4 schedulers x 32 lanes x clock."""
+    if instr_per_px is None:
+        return None
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = 152 * 4 * 32 * mhz * 1e6 / 1e12
     ach = mpix_s * 1e6 * instr_per_px / 1e12
@@ -245,6 +268,42 @@ def timed_with_clocks(torch, fn, steps, stream, local):
     clk.mark_end()
     clk.stop()
     return t, clk.summary()
+
+
+def replica_time(world, torch, step, steps, timer):
+    """Time `steps` calls of `step` with `timer` (returns (seconds, clocks)),
+    bracketed by barriers; the replicas' time is the slowest rank's.
+    Returns (max seconds over ranks, this rank's seconds, clocks)."""
+    barrier(world, torch)
+    t, clocks = timer(step, steps)
+    barrier(world, torch)
+    return reduce_max(t, world, torch), t, clocks
+
+
+def replica_mpix_s(px_per_rank_step: float, world: int, steps: int, t_max: float) -> float:
+    """Whole-job rate: the pixels every rank processed over the slowest time."""
+    return px_per_rank_step * world * steps / t_max / 1e6
+
+
+def rank_seeds(rank: int, n: int, base: int) -> list[int]:
+    """Seeds of a rank's own frames (replicas process different frames)."""
+    return [base + 1000 * rank + i for i in range(n)]
+
+
+def hbm_roofline(ext_bytes: float, seconds_per_launch: float, kernel: str, traffic=None):
+    peaks, src = measured_peaks()
+    ach = ext_bytes / seconds_per_launch / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": src,
+            "kernel": kernel, "algorithmic_bytes_per_launch": int(ext_bytes)}
+
+
+def parity_of(pairs, rule="bit-exact"):
+    """pairs: (gpu array, oracle array) of the sampled frames' outputs."""
+    bad = int(sum(int(np.count_nonzero(a != b)) for a, b in pairs))
+    n = int(sum(a.size for a, _ in pairs))
+    return {"rule": rule, "outputs_compared": n, "mismatches": bad, "ok": bad == 0}
 
 
 def edge_config(args, world):
@@ -331,7 +390,7 @@ def run_edge(args, world, rank, local, torch):
     sh = stream.cuda_stream
     ctx = H.hvxCreateContext()
     F = args.frames
-    distinct = [synth.rects_noise(W, H_, seed=2 + 1000 * rank + i) for i in range(min(F, 8))]
+    distinct = [synth.rects_noise(W, H_, seed=s) for s in rank_seeds(rank, min(F, 8), 2)]
     pitch = W  # 1920: a multiple of 16
     t_in, ins = wrap_frames(ctx, torch, H, [distinct[i % len(distinct)] for i in range(F)], W,
                             H_, pitch)
@@ -353,16 +412,14 @@ def run_edge(args, world, rank, local, torch):
     step_fused()  # builds, autotunes and captures the batch launch
     for _ in range(args.warmup):
         step_fused()
-    barrier(world, torch)
-    t_fused, clocks = timed_with_clocks(torch, step_fused, args.steps, stream, local)
-    barrier(world, torch)
-    t_fused = reduce_max(t_fused, world, torch)
+    t_fused, _, clocks = replica_time(world, torch, step_fused, args.steps,
+                                      _timer(torch, stream, local))
+    gpu0 = (t_ph[0].cpu().numpy(), t_mk[0].cpu().numpy())
 
     plain_steps = max(2, min(args.steps, 40) // 4)
     for _ in range(2):
         step_plain()
-    barrier(world, torch)
-    t_plain = reduce_max(time_steps(torch, step_plain, plain_steps, stream), world, torch)
+    t_plain, _, _ = replica_time(world, torch, step_plain, plain_steps, _plain_timer(torch, stream))
 
     # end to end through the C ABI on host data: every step is two
     # hvxScheduleGraphBatchHost calls of 32 frames on two streams (copies in
@@ -418,8 +475,21 @@ def run_edge(args, world, rank, local, torch):
     serving = None
     if not args.no_serve and rank == 0:
         secs = args.serve_seconds if args.serve_seconds is not None else 1.5
-        serving = serve_compare(ctx, H, PG, synth, secs, instances=3)
+        serving = serve_compare(ctx, H, PG, synth, secs, instances=3, sat_rate=200000.0,
+                                sat_seconds=0.05)
     H.hvxReleaseContext(ctx)
+    del t_in, t_ph, t_mk, h_in, h_ph, h_mk
+    torch.cuda.empty_cache()
+    configs = None
+    if not args.no_configs:
+        cpu = not args.no_cpu_baseline
+        configs = {}
+        for name, fn in (("config1_gauss_640x480", measure_gauss640),
+                         ("config3_harris_4096x2160", measure_harris),
+                         ("config4_batch256_uneven", measure_batch256),
+                         ("gauss_batch_1080p", measure_gauss_batch)):
+            configs[name] = fn(world, rank, local, torch, cpu)
+            torch.cuda.empty_cache()
     if rank != 0:
         return
     mpix_step = F * W * H_ / 1e6 * world
@@ -430,8 +500,10 @@ def run_edge(args, world, rank, local, torch):
     ext_bytes = 3 * W * H_ * F  # input + phase + mask, per launch (per GPU)
     kernel_s = t_fused / args.steps
     achieved = ext_bytes / kernel_s / 1e9
-    cpu = cpu_all = None
+    cpu = cpu_all = parity = None
     if not args.no_cpu_baseline:
+        import oracle as O
+        parity = parity_of(list(zip(gpu0, O.edge_graph(distinct[0]))))
         n = 48
         v_cpu, dt = cpu_oracle_edge(n)
         cpu = {"value": round(v_cpu, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
@@ -457,19 +529,22 @@ def run_edge(args, world, rank, local, torch):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
-                     "traffic": recorded_traffic("edge_batch_kernel<MASK_PHASE>", F),
+                     "traffic": recorded_traffic(EDGE_KERNEL, F),
                      "peak_source": src, "kernel": "edge_batch_kernel",
                      "algorithmic_bytes_per_launch": ext_bytes,
                      # the bound that holds: instruction issue (the kernel's
-                     # instructions per pixel from its ncu capture, times the
-                     # live pixel rate, against 152 SMs x 4 schedulers x 32
-                     # lanes x the sampled SM clock)
-                     "issue": issue_roofline(value / world, EDGE_INSTR_PER_PX, clocks)},
+                     # instructions per pixel from its hash-checked ncu
+                     # record, times the live pixel rate, against 152 SMs x 4
+                     # schedulers x 32 lanes x the sampled SM clock)
+                     "issue": issue_roofline(value / world,
+                                             recorded_instr_per_px(EDGE_KERNEL, F), clocks)},
         "e2e": {"value": round(e2e_v, 1), "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(F * H_ * pitch),
                 "d2h_bytes_per_step": int(2 * F * H_ * pitch)},
+        "configs": configs,
         "serving": serving,
         "gpu_launches": args.steps,
+        "parity": parity,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
@@ -504,6 +579,12 @@ def build_serve_pool(ctx, H, PG, synth, fused: bool, instances: int):
 
 
 def serve_run(H, synth, pool, srv, seconds: float, rate: float, seed: int):
+    """Poisson arrivals at `rate` for `seconds`: at each wake-up of the
+    submitting loop, every request whose arrival time has passed is submitted
+    in one hvxServerSubmitMany call (so offered rates above what one call per
+    request allows are still offered on time).  Latency runs from submission
+    to completion; Mpix/s is the completed work over the time from the first
+    submission to the last completion."""
     n = max(1, int(rate * seconds))
     arrivals = synth.poisson_arrivals(rate, n, seed)
     kinds = synth.choice(seed, 13, n, [0.5, 0.3, 0.2])
@@ -514,21 +595,27 @@ def serve_run(H, synth, pool, srv, seconds: float, rate: float, seed: int):
         for g in lst:
             H.hvxServerWait(srv, H.hvxServerSubmit(srv, g))
     H.hvxServerResetStats(srv)
-    tickets = []
-    t0 = time.perf_counter()
+    order = []
     for i in range(n):
-        target = t0 + arrivals[i]
-        while True:
-            now = time.perf_counter()
-            if now >= target:
-                break
-            if target - now > 0.002:
-                time.sleep(target - now - 0.001)
         key = (int(kinds[i]), int(sizes[i]))
         j = rr.get(key, 0)
         rr[key] = j + 1
         lst = pool[key]
-        tickets.append(H.hvxServerSubmit(srv, lst[j % len(lst)]))
+        order.append(lst[j % len(lst)])
+    tickets = []
+    i = 0
+    t0 = time.perf_counter()
+    while i < n:
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            if arrivals[i] - now > 0.002:
+                time.sleep(arrivals[i] - now - 0.001)
+            continue
+        k = i
+        while k < n and arrivals[k] <= now:
+            k += 1
+        tickets += H.hvxServerSubmitMany(srv, order[i:k])
+        i = k
     fails = 0
     for t in tickets:
         st, _ = H.hvxServerWait(srv, t)
@@ -538,77 +625,133 @@ def serve_run(H, synth, pool, srv, seconds: float, rate: float, seed: int):
     return {"requests": n, "failed": fails, "p50_ms": round(st["p50_ms"], 4),
             "p99_ms": round(st["p99_ms"], 4), "mean_ms": round(st["mean_ms"], 4),
             "max_ms": round(st["max_ms"], 3),
+            "queue_wait_p99_ms": round(st["wait_p99_ms"], 4),
+            "queue_wait_max_ms": round(st["wait_max_ms"], 3),
             "mpix_per_s": round(st["mpix_completed"] / elapsed, 1),
             "max_in_flight": int(st["max_in_flight"]),
-            "offered_req_per_s": rate, "seconds": round(elapsed, 3)}
+            "offered_req_per_s": rate, "achieved_req_per_s": round(n / elapsed, 1),
+            "seconds": round(elapsed, 3)}
 
 
-def serve_compare(ctx, H, PG, synth, seconds, instances=4, rate=2000.0):
+SERVE_WORKLOAD = ("Poisson arrivals, 50/30/20 Gaussian3x3/edge/Harris graphs, sizes "
+                  "640x480/1920x1080/3840x2160/7680x4320 uniform, 40 GB budget, uniform-byte "
+                  "inputs")
+
+
+def serve_compare(ctx, H, PG, synth, seconds, instances=4, rate=2000.0, sat_rate=None,
+                  sat_seconds=0.05):
+    """Fused continuous serving (16 slots, 8 streams) against one request at a
+    time on unfused graphs, at `rate`, and when sat_rate is given, both at
+    an offered rate above either's capacity (saturation)."""
     budget = 40 << 30
     fused_pool = build_serve_pool(ctx, H, PG, synth, True, instances)
-    srv = H.hvxCreateServer(ctx, budget, 16, 8)
-    fused = serve_run(H, synth, fused_pool, srv, seconds, rate, seed=5)
-    H.hvxReleaseServer(srv)
     plain_pool = build_serve_pool(ctx, H, PG, synth, False, instances)
-    srv = H.hvxCreateServer(ctx, budget, 1, 1)
-    plain = serve_run(H, synth, plain_pool, srv, seconds, rate, seed=5)
-    H.hvxReleaseServer(srv)
+    out = {"workload": SERVE_WORKLOAD, "budget_bytes": budget, "slots": 16, "streams": 8}
+    runs = [("fused_continuous", fused_pool, 16, 8), ("unfused_one_at_a_time", plain_pool, 1, 1)]
+    for name, pool, slots, nst in runs:
+        srv = H.hvxCreateServer(ctx, budget, slots, nst)
+        out[name] = serve_run(H, synth, pool, srv, seconds, rate, seed=5)
+        H.hvxReleaseServer(srv)
+    if sat_rate:
+        sat = {"offered_req_per_s": sat_rate,
+               "note": "offered load above both forms' capacity: Mpix/s is what each "
+                       "form sustains; latency includes the queueing"}
+        for name, pool, slots, nst in runs:
+            srv = H.hvxCreateServer(ctx, budget, slots, nst)
+            sat[name] = serve_run(H, synth, pool, srv, sat_seconds, sat_rate, seed=8)
+            H.hvxReleaseServer(srv)
+        sat["fused_over_unfused_mpix"] = round(sat["fused_continuous"]["mpix_per_s"] /
+                                               sat["unfused_one_at_a_time"]["mpix_per_s"], 2)
+        out["saturation"] = sat
+    out["p99_unfused_over_fused"] = round(out["unfused_one_at_a_time"]["p99_ms"] /
+                                          max(out["fused_continuous"]["p99_ms"], 1e-9), 2)
     for pool in (fused_pool, plain_pool):
         for lst in pool.values():
             for g in lst:
                 H.hvxReleaseGraph(g)
-    return {"workload": "Poisson 2000 req/s, 50/30/20 Gaussian3x3/edge/Harris, sizes "
-                        "640x480..7680x4320 uniform, 40 GB budget, uniform-byte inputs",
-            "fused_continuous": fused, "unfused_one_at_a_time": plain,
-            "budget_bytes": budget, "slots": 16, "streams": 8}
+    return out
 
 
-# ---------------------------------------------------------------------------
-def run_gauss(args, world, rank, local, torch):
+def _timer(torch, stream, local):
+    return lambda f, n: timed_with_clocks(torch, f, n, stream, local)
+
+
+def _plain_timer(torch, stream):
+    return lambda f, n: (time_steps(torch, f, n, stream), None)
+
+
+def _oracle_timed(fn, min_s=0.0):
+    """Run the oracle call fn() once (or until min_s seconds passed); returns
+    (last result, runs, seconds)."""
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        out = fn()
+        runs += 1
+        if time.perf_counter() - t0 >= min_s:
+            break
+    return out, runs, time.perf_counter() - t0
+
+
+def measure_gauss640(world, rank, local, torch, cpu, steps=2000, warmup=50):
+    """Config 1: Gaussian3x3 on one 640x480 U8 image per launch.  400 images
+    (246 MB of inputs and outputs, larger than L2) are cycled, so every launch
+    reads an image that left L2 since its previous use."""
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
     from paper_2008_11476_gb300 import synth
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     ctx = H.hvxCreateContext()
-    w, h = 640, 480
-    img = synth.uniform_u8(w, h, seed=1)
-    inp = PG.upload(ctx, img, H.HVX_DF_U8)
-    out = PG.empty(ctx, w, h, H.HVX_DF_U8)
-    g = PG.gaussian_graph(ctx, inp, out)
+    w, h, n_img = 640, 480, 400
+    seed = rank_seeds(rank, 1, 1)[0]
+    img = synth.uniform_u8(w, h, seed=seed)
+    t_in, ins = wrap_frames(ctx, torch, H, [img] * n_img, w, h, w)
+    t_out, outs = empty_frames(ctx, torch, H, n_img, w, h, w)
+    graphs = [PG.gaussian_graph(ctx, a, o) for a, o in zip(ins, outs)]
+    assert PG.kernel_kinds(graphs[0]) == ["gaussian3x3_tma"]
+    it = [0]
 
     def step():
-        H.hvxScheduleGraph(g, sh)
+        H.hvxScheduleGraph(graphs[it[0] % n_img], sh)
+        it[0] += 1
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    barrier(world, torch)
-    t, clocks = timed_with_clocks(torch, step, args.steps, stream, local)
-    t = reduce_max(t, world, torch)
+    t, _, clocks = replica_time(world, torch, step, steps, _timer(torch, stream, local))
+    H.hvxWaitBatch(ctx, sh)
+    gpu = t_out[0].cpu().numpy()
     H.hvxReleaseContext(ctx)
-    if rank == 0:
-        mp = w * h / 1e6 * args.steps * world
-        print(json.dumps({"metric": "Gaussian3x3 640x480 Mpix/s (one image per launch)",
-                          "value": round(mp / t, 1), "unit": "Mpix/s", "n_gpus": world,
-                          "steps": args.steps, "warmup": args.warmup,
-                          "us_per_image": round(t / args.steps * 1e6, 3),
-                          "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-                          "config": {"workload": "Gaussian3x3 640x480 U8 BORDER_REPLICATE",
-                                     "l2": "resident in L2 (launch-latency bound)"},
-                          "gpu_launches": args.steps, "clocks": clocks}), flush=True)
+    per = t / steps
+    r = {"workload": "Gaussian3x3 on one 640x480 U8 image per launch (uniform bytes 0-255, "
+                     "seed 1), BORDER_REPLICATE, OpenVX truncating /16; launches back to back "
+                     "on one stream over 400 image buffers",
+         "value": round(replica_mpix_s(w * h, world, steps, t), 1), "unit": "Mpix/s",
+         "us_per_launch": round(per * 1e6, 3), "steps": steps,
+         "roofline": hbm_roofline(2 * w * h, per, "gauss_kernel"),
+         "bound_note": "launch latency: 0.6 MB per launch would take 0.1 us at the HBM peak",
+         "l2": "400 distinct image buffers cycled (246 MB, larger than L2)",
+         "gpu_launches": steps, "clocks": clocks}
+    if cpu and rank == 0:
+        import oracle as O
+        ref, runs, dt = _oracle_timed(lambda: O.gaussian3x3(img).data, 0.3)
+        r["cpu_baseline"] = {"value": round(runs * w * h / 1e6 / dt, 3), "unit": "Mpix/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"{runs} runs of the 640x480 image, single thread"}
+        r["parity"] = parity_of([(gpu, ref)])
+    return r
 
 
-def run_gauss_batch(args, world, rank, local, torch):
-    """Gaussian3x3 alone on --frames 1920x1080 frames per step, one batched
-    launch: the HBM roofline of the Gaussian kernel (2 B/px)."""
+def measure_gauss_batch(world, rank, local, torch, cpu, F=64, steps=40, warmup=5):
+    """Gaussian3x3 alone on F 1920x1080 frames per step, one batched launch:
+    the HBM roofline of the Gaussian kernel (2 B/px)."""
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
     from paper_2008_11476_gb300 import synth
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     ctx = H.hvxCreateContext()
-    F = args.frames
-    distinct = [synth.uniform_u8(W, H_, seed=1 + i) for i in range(min(F, 8))]
+    distinct = [synth.uniform_u8(W, H_, seed=s) for s in rank_seeds(rank, min(F, 8), 1)]
     t_in, ins = wrap_frames(ctx, torch, H, [distinct[i % len(distinct)] for i in range(F)], W, H_, W)
     t_o, outs = empty_frames(ctx, torch, H, F, W, H_, W)
     graphs = [PG.gaussian_graph(ctx, a, o) for a, o in zip(ins, outs)]
@@ -618,33 +761,33 @@ def run_gauss_batch(args, world, rank, local, torch):
         H.hvxProcessGraphBatch(graphs, sh)
 
     step()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    barrier(world, torch)
-    t, clocks = timed_with_clocks(torch, step, args.steps, stream, local)
-    t = reduce_max(t, world, torch)
+    t, _, clocks = replica_time(world, torch, step, steps, _timer(torch, stream, local))
     H.hvxWaitBatch(ctx, sh)
+    gpu = t_o[0].cpu().numpy()
     H.hvxReleaseContext(ctx)
-    if rank == 0:
-        peaks, src = measured_peaks()
-        ext = 2 * W * H_ * F
-        ach = ext / (t / args.steps) / 1e9
-        print(json.dumps({
-            "metric": "Gaussian3x3 Mpix/s (batched 1920x1080 frames)",
-            "value": round(W * H_ * F / 1e6 * args.steps / t * world, 1), "unit": "Mpix/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
-            "dtype": "u8", "data": "synthetic (uniform bytes)",
-            "config": {"workload": f"Gaussian3x3 1920x1080 U8 BORDER_REPLICATE, {F} frames per "
-                                   "step in one persistent launch", "l2": "larger than L2"},
-            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs"),
-                         "unit": "GB/s", "frac": round(ach / peaks.get("hbm_gbs", 6800), 4),
-                         "peak_source": src, "kernel": "gauss_batch_kernel",
-                         "algorithmic_bytes_per_launch": ext},
-            "gpu_launches": args.steps, "clocks": clocks}), flush=True)
+    per = t / steps
+    r = {"workload": f"Gaussian3x3 on {F} 1920x1080 U8 frames per step (uniform bytes) in one "
+                     "persistent launch, BORDER_REPLICATE",
+         "value": round(replica_mpix_s(W * H_ * F, world, steps, t), 1), "unit": "Mpix/s",
+         "ms_per_step": round(per * 1e3, 4), "steps": steps,
+         "roofline": hbm_roofline(2 * W * H_ * F, per, "gauss_batch_kernel"),
+         "l2": "inputs + outputs per step (265 MB) larger than L2",
+         "gpu_launches": steps, "clocks": clocks}
+    if cpu and rank == 0:
+        import oracle as O
+        ref, runs, dt = _oracle_timed(lambda: O.gaussian3x3(distinct[0]).data)
+        r["cpu_baseline"] = {"value": round(runs * W * H_ / 1e6 / dt, 3), "unit": "Mpix/s",
+                             "cores": 1, "kind": "oracle", "sample": "1 frame, single thread"}
+        r["parity"] = parity_of([(gpu, ref)])
+    return r
 
 
-def run_harris(args, world, rank, local, torch):
+def measure_harris(world, rank, local, torch, cpu, steps=5, warmup=3, codegen="auto"):
+    """Config 3: the Harris graph on 16 4096x2160 frames per step, fused, one
+    launch per frame and one batched launch for all 16; the unfused
+    one-launch-per-node form (9 launches per frame) on the same frames."""
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
     from paper_2008_11476_gb300 import synth
@@ -652,53 +795,189 @@ def run_harris(args, world, rank, local, torch):
     sh = stream.cuda_stream
     ctx = H.hvxCreateContext()
     w, h, F = 4096, 2160, 16
-    distinct = [synth.rects_noise(w, h, seed=3 + i) for i in range(4)]
+    distinct = [synth.rects_noise(w, h, seed=s) for s in rank_seeds(rank, 4, 3)]
     t_in, ins = wrap_frames(ctx, torch, H, [distinct[i % 4] for i in range(F)], w, h, w)
     t_mk, mks = empty_frames(ctx, torch, H, F, w, h, w)
     fused = [PG.harris_graph(ctx, a, m) for a, m in zip(ins, mks)]
+    if codegen == "only":
+        for g in fused:
+            H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+            H.hvxVerifyGraph(g)
     plain = [PG.harris_graph(ctx, a, m, fusion=False) for a, m in zip(ins, mks)]
-    assert PG.kernel_kinds(fused[0]) == ["fused_harris_tma"]
+    if codegen != "only":
+        assert PG.kernel_kinds(fused[0]) == ["fused_harris_tma"]
 
     def step_fused():
         for gr in fused:
             H.hvxScheduleGraph(gr, sh)
 
+    def step_batch():
+        H.hvxProcessGraphBatch(fused, sh)
+
     def step_plain():
         for gr in plain:
             H.hvxScheduleGraph(gr, sh)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step_fused()
-    barrier(world, torch)
-    steps = max(3, args.steps // 10)
-    t, clocks = timed_with_clocks(torch, step_fused, steps, stream, local)
-    t = reduce_max(t, world, torch)
-    step_plain()
-    tp = reduce_max(time_steps(torch, step_plain, 3, stream), world, torch)
+        step_batch()
+    t, _, clocks = replica_time(world, torch, step_fused, steps, _timer(torch, stream, local))
+    tb, _, clocks_b = replica_time(world, torch, step_batch, steps, _timer(torch, stream, local))
+    step_fused()  # frame outputs from the per-frame kernel for the parity check
     H.hvxWaitGraph(fused[-1])
+    gpu = t_mk[0].cpu().numpy()
+    step_plain()
+    tp, _, _ = replica_time(world, torch, step_plain, 2, _plain_timer(torch, stream))
+    H.hvxWaitGraph(plain[-1])
+    n_plain = H.hvxQueryGraph(plain[0], H.HVX_GRAPH_NUM_LAUNCHES)
     H.hvxReleaseContext(ctx)
+    px = w * h * F
+    r = {"workload": "Harris graph Sobel3x3 -> gx^2, gy^2, gx*gy -> 5x5 window sums -> "
+                     "response det - (1/25) trace^2 -> Threshold(1e6) -> U8 mask; 4096x2160 U8 "
+                     "(seeded rectangles + sigma 10 noise), BORDER_UNDEFINED, 16 frames per "
+                     "step, one fused launch per frame",
+         "value": round(replica_mpix_s(px, world, steps, t), 1), "unit": "Mpix/s",
+         "ms_per_step": round(t / steps * 1e3, 4), "steps": steps,
+         "roofline": hbm_roofline(2 * w * h, t / steps / F, "harris_fast_kernel"),
+         "batched": {"value": round(replica_mpix_s(px, world, steps, tb), 1), "unit": "Mpix/s",
+                     "ms_per_step": round(tb / steps * 1e3, 4),
+                     "roofline": hbm_roofline(2 * px, tb / steps, "harris_fast_batch_kernel"),
+                     "gpu_launches": steps, "clocks": clocks_b},
+         "unfused": {"value": round(replica_mpix_s(px, world, 2, tp), 1), "unit": "Mpix/s",
+                     "launches_per_frame": n_plain},
+         "l2": "16 frame buffers per step (283 MB), larger than L2",
+         "codegen": codegen, "gpu_launches": steps * F, "clocks": clocks}
+    r["fused_over_unfused"] = round(r["value"] / r["unfused"]["value"], 2)
+    if cpu and rank == 0:
+        import oracle as O
+        (ref, _), runs, dt = _oracle_timed(lambda: O.harris_graph(distinct[0]))
+        r["cpu_baseline"] = {"value": round(runs * w * h / 1e6 / dt, 3), "unit": "Mpix/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": "1 frame of 4096x2160, single thread"}
+        r["parity"] = parity_of([(gpu, ref)])
+    return r
+
+
+def measure_batch256(world, rank, local, torch, cpu, steps=10, warmup=3):
+    """Config 4: 256 U8 images of seeded uneven sizes through the edge graph in
+    one persistent fused launch (replayed from a captured CUDA graph, grid
+    chosen by the autotuner); against one fused launch per image and 256
+    unfused runs of 5 launches each."""
+    from paper_2008_11476_gb300 import graphs as PG
+    from paper_2008_11476_gb300 import hvx as H
+    from paper_2008_11476_gb300 import synth
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = H.hvxCreateContext()
+    sizes = synth.batch_sizes(256, seed=4)
+    bases = [synth.rects_noise(3840, 2160, seed=s) for s in rank_seeds(rank, 4, 40)]
+    offs = synth.randint(4, 20, 512, 0, 1 << 20)
+    graphs, plain, keep, crops, outs = [], [], [], [], []
+    for i, (w, h) in enumerate(sizes):
+        b = bases[i % 4]
+        ox = int(offs[2 * i]) % (3840 - w + 1)
+        oy = int(offs[2 * i + 1]) % (2160 - h + 1)
+        crop = np.ascontiguousarray(b[oy:oy + h, ox:ox + w])
+        pitch = (w + 15) // 16 * 16
+        t_in, (a,) = wrap_frames(ctx, torch, H, [crop], w, h, pitch)
+        t_o, (p, m) = empty_frames(ctx, torch, H, 2, w, h, pitch)
+        keep += [t_in, t_o]
+        crops.append(crop)
+        outs.append(t_o)
+        graphs.append(PG.edge_graph(ctx, a, p, m))
+        plain.append(PG.edge_graph(ctx, a, p, m, fusion=False))
+    mpix = sum(w * h for w, h in sizes) / 1e6
+
+    def step_fused():
+        H.hvxProcessGraphBatch(graphs, sh)
+
+    def step_per_image():
+        for g in graphs:
+            H.hvxScheduleGraph(g, sh)
+
+    def step_plain():
+        for g in plain:
+            H.hvxScheduleGraph(g, sh)
+
+    t_build = time.perf_counter()
+    step_fused()  # build + autotune + capture
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    for _ in range(warmup):
+        step_fused()
+    t, _, clocks = replica_time(world, torch, step_fused, steps, _timer(torch, stream, local))
+    H.hvxWaitBatch(ctx, sh)
+    # sampled images for the parity check: the first and the smallest
+    pick = sorted({0, int(np.argmin([w * h for w, h in sizes]))})
+    gpu = {i: (outs[i][0][:, :sizes[i][0]].cpu().numpy(), outs[i][1][:, :sizes[i][0]].cpu().numpy())
+           for i in pick}
+    step_per_image()
+    ti, _, _ = replica_time(world, torch, step_per_image, 3, _plain_timer(torch, stream))
+    step_plain()
+    tp, _, _ = replica_time(world, torch, step_plain, 3, _plain_timer(torch, stream))
+    H.hvxWaitBatch(ctx, sh)
+    H.hvxReleaseContext(ctx)
+    value = replica_mpix_s(mpix * 1e6, world, steps, t)
+    unf = replica_mpix_s(mpix * 1e6, world, 3, tp)
+    r = {"workload": "256 U8 images, w~U{320..3840}, h~U{240..2160} (seed 4; crops of seeded "
+                     f"rectangles + noise frames), {mpix:.1f} Mpix per step, edge graph "
+                     "BORDER_REPLICATE, one persistent fused launch replayed from a CUDA graph",
+         "value": round(value, 1), "unit": "Mpix/s", "ms_per_step": round(t / steps * 1e3, 4),
+         "steps": steps,
+         "roofline": hbm_roofline(3 * mpix * 1e6, t / steps, "edge_batch_kernel"),
+         "per_image_fused_launches": {"value": round(replica_mpix_s(mpix * 1e6, world, 3, ti), 1),
+                                      "unit": "Mpix/s", "launches_per_step": 256},
+         "unfused_256_runs": {"value": round(unf, 1), "unit": "Mpix/s",
+                              "launches_per_step": 256 * 5},
+         "batched_over_unfused": round(value / unf, 2),
+         "first_call_s": round(t_build, 3),
+         "l2": "larger than L2 (1.9 GB of external bytes per step)",
+         "gpu_launches": steps, "clocks": clocks}
+    if cpu and rank == 0:
+        import oracle as O
+        pairs, t_cpu, px_cpu = [], 0.0, 0
+        for i in pick:
+            (rp, rm), _, dt = _oracle_timed(lambda i=i: O.edge_graph(crops[i]))
+            t_cpu += dt
+            px_cpu += sizes[i][0] * sizes[i][1]
+            pairs += [(gpu[i][0], rp), (gpu[i][1], rm)]
+        r["cpu_baseline"] = {"value": round(px_cpu / 1e6 / t_cpu, 3), "unit": "Mpix/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"images {pick} of the batch, single thread"}
+        r["parity"] = parity_of(pairs)
+    return r
+
+
+def _print_sub(rank, world, metric, r, **extra):
     if rank == 0:
-        peaks, src = measured_peaks()
-        mp = w * h * F / 1e6
-        per_launch_s = t / steps / F
-        ext = 2 * w * h
-        print(json.dumps({
-            "metric": "Harris graph 4096x2160 Mpix/s (fused)", "value": round(mp * steps / t, 1),
-            "unit": "Mpix/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
-            "ms_per_step": round(t / steps * 1e3, 4), "higher_is_better": True, "dtype": "u8/s32",
-            "data": "synthetic (seeded rectangles + sigma 10 noise)",
-            "config": {"workload": "Sobel3x3->products->5x5 sums->response(k=1/25)->"
-                                   "Threshold(1e6), 4096x2160 U8, BORDER_UNDEFINED, 16 frames "
-                                   "per step (one launch each)",
-                       "l2": "16 distinct frames per step, larger than L2",
-                       "codegen": args.codegen},
-            "unfused": {"value": round(mp * 3 / tp, 1), "unit": "Mpix/s", "launches_per_frame": 9},
-            "roofline": {"bound": "hbm", "achieved": round(ext / per_launch_s / 1e9, 1),
-                         "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                         "frac": round(ext / per_launch_s / 1e9 / peaks.get("hbm_gbs", 6800), 4),
-                         "peak_source": src, "kernel": "harris_fast_kernel",
-                         "algorithmic_bytes_per_launch": ext},
-            "gpu_launches": steps * F, "clocks": clocks}), flush=True)
+        line = {"metric": metric, "n_gpus": world, "higher_is_better": True,
+                "data": "synthetic", **extra, **r}
+        print(json.dumps(line), flush=True)
+
+
+def run_gauss(args, world, rank, local, torch):
+    r = measure_gauss640(world, rank, local, torch, not args.no_cpu_baseline,
+                         steps=max(args.steps, 400), warmup=max(args.warmup, 3))
+    _print_sub(rank, world, "Gaussian3x3 640x480 Mpix/s (one image per launch)", r, dtype="u8")
+
+
+def run_gauss_batch(args, world, rank, local, torch):
+    r = measure_gauss_batch(world, rank, local, torch, not args.no_cpu_baseline, F=args.frames,
+                            steps=args.steps, warmup=args.warmup)
+    _print_sub(rank, world, "Gaussian3x3 Mpix/s (batched 1920x1080 frames)", r, dtype="u8")
+
+
+def run_harris(args, world, rank, local, torch):
+    r = measure_harris(world, rank, local, torch, not args.no_cpu_baseline,
+                       steps=max(3, args.steps // 10), warmup=args.warmup, codegen=args.codegen)
+    _print_sub(rank, world, "Harris graph 4096x2160 Mpix/s (fused)", r, dtype="u8/s32")
+
+
+def run_batch(args, world, rank, local, torch):
+    r = measure_batch256(world, rank, local, torch, not args.no_cpu_baseline,
+                         steps=max(5, args.steps // 10), warmup=args.warmup)
+    _print_sub(rank, world, "batched edge graph Mpix/s (256 uneven images, one launch)", r,
+               dtype="u8")
 
 
 def morph_graph(ctx, H, src, out, fusion=True):
@@ -867,98 +1146,21 @@ def run_apps(args, world, rank, local, torch):
             "gpu_launches": steps * sum(v["batch_launches"] for v in res.values())}), flush=True)
 
 
-def run_batch(args, world, rank, local, torch):
-    from paper_2008_11476_gb300 import graphs as PG
-    from paper_2008_11476_gb300 import hvx as H
-    from paper_2008_11476_gb300 import synth
-    stream = torch.cuda.current_stream()
-    sh = stream.cuda_stream
-    ctx = H.hvxCreateContext()
-    sizes = synth.batch_sizes(256, seed=4)
-    bases = [synth.rects_noise(3840, 2160, seed=40 + i) for i in range(4)]
-    offs = synth.randint(4, 20, 512, 0, 1 << 20)
-    graphs, plain, keep = [], [], []
-    for i, (w, h) in enumerate(sizes):
-        b = bases[i % 4]
-        ox = int(offs[2 * i]) % (3840 - w + 1)
-        oy = int(offs[2 * i + 1]) % (2160 - h + 1)
-        crop = np.ascontiguousarray(b[oy:oy + h, ox:ox + w])
-        pitch = (w + 15) // 16 * 16
-        t_in, (a,) = wrap_frames(ctx, torch, H, [crop], w, h, pitch)
-        t_o, (p, m) = empty_frames(ctx, torch, H, 2, w, h, pitch)
-        keep += [t_in, t_o]
-        graphs.append(PG.edge_graph(ctx, a, p, m))
-        plain.append(PG.edge_graph(ctx, a, p, m, fusion=False))
-    mpix = sum(w * h for w, h in sizes) / 1e6
-
-    def step_fused():
-        H.hvxProcessGraphBatch(graphs, sh)
-
-    def step_per_image():
-        for g in graphs:
-            H.hvxScheduleGraph(g, sh)
-
-    def step_plain():
-        for g in plain:
-            H.hvxScheduleGraph(g, sh)
-
-    t_build = time.perf_counter()
-    step_fused()  # build + autotune + capture
-    torch.cuda.synchronize()
-    t_build = time.perf_counter() - t_build
-    for _ in range(args.warmup):
-        step_fused()
-    barrier(world, torch)
-    steps = max(5, args.steps // 10)
-    t, clocks = timed_with_clocks(torch, step_fused, steps, stream, local)
-    t = reduce_max(t, world, torch)
-    step_per_image()
-    ti = reduce_max(time_steps(torch, step_per_image, 3, stream), world, torch)
-    step_plain()
-    tp = reduce_max(time_steps(torch, step_plain, 3, stream), world, torch)
-    H.hvxWaitBatch(ctx, sh)
-    H.hvxReleaseContext(ctx)
-    if rank == 0:
-        peaks, src = measured_peaks()
-        ext = 3 * mpix * 1e6
-        ach = ext / (t / steps) / 1e9
-        print(json.dumps({
-            "metric": "batched edge graph Mpix/s (256 uneven images, one launch)",
-            "value": round(mpix * steps / t, 1), "unit": "Mpix/s", "n_gpus": world,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": round(t / steps * 1e3, 4),
-            "higher_is_better": True, "dtype": "u8",
-            "data": "synthetic (crops of seeded rectangles + noise frames)",
-            "config": {"workload": "256 U8 images, w~U{320..3840}, h~U{240..2160} (seed 4), "
-                                   f"{mpix:.1f} Mpix per step, edge graph BORDER_REPLICATE",
-                       "l2": "larger than L2"},
-            "per_image_fused_launches": {"value": round(mpix * 3 / ti, 1), "unit": "Mpix/s"},
-            "unfused_256_runs": {"value": round(mpix * 3 / tp, 1), "unit": "Mpix/s",
-                                 "launches_per_step": 256 * 5},
-            "batched_over_unfused": round((mpix * steps / t) / (mpix * 3 / tp), 2),
-            "first_call_s": round(t_build, 3),
-            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs"),
-                         "unit": "GB/s", "frac": round(ach / peaks.get("hbm_gbs", 6800), 4),
-                         "peak_source": src, "kernel": "edge_batch_kernel"},
-            "gpu_launches": steps, "clocks": clocks}), flush=True)
-
-
 def run_serve(args, world, rank, local, torch):
     from paper_2008_11476_gb300 import graphs as PG
     from paper_2008_11476_gb300 import hvx as H
     from paper_2008_11476_gb300 import synth
     ctx = H.hvxCreateContext()
     secs = args.serve_seconds if args.serve_seconds is not None else 5.0
-    res = serve_compare(ctx, H, PG, synth, secs, instances=4)
-    # offered-rate sweep of the fused server up to saturation (the host loop
-    # that submits requests is the limit at the top), and a 256 MB budget run
-    # where admission waits for memory
+    res = serve_compare(ctx, H, PG, synth, secs, instances=4, sat_rate=200000.0,
+                        sat_seconds=0.05)
+    # offered-rate sweep of the fused server up to saturation, and a 256 MB
+    # budget run where admission waits for memory
     pool = build_serve_pool(ctx, H, PG, synth, True, 4)
     sweep = []
-    for rate in (2000.0, 5000.0, 10000.0, 20000.0, 40000.0):
+    for rate in (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0):
         srv = H.hvxCreateServer(ctx, 40 << 30, 16, 8)
-        r = serve_run(H, synth, pool, srv, 1.0, rate, seed=6)
-        r["achieved_req_per_s"] = round(r["requests"] / r["seconds"], 1)
-        sweep.append(r)
+        sweep.append(serve_run(H, synth, pool, srv, 0.5, rate, seed=6))
         H.hvxReleaseServer(srv)
     srv = H.hvxCreateServer(ctx, 256 << 20, 16, 8)
     small = serve_run(H, synth, pool, srv, 1.0, 2000.0, seed=7)
@@ -968,22 +1170,39 @@ def run_serve(args, world, rank, local, torch):
             H.hvxReleaseGraph(g)
     H.hvxReleaseContext(ctx)
     if rank == 0:
-        f, p = res["fused_continuous"], res["unfused_one_at_a_time"]
+        f = res["fused_continuous"]
         print(json.dumps({"metric": "serving p50/p99 ms and Mpix/s", "value": f["p99_ms"],
                           "unit": "ms (p99)", "higher_is_better": False, "n_gpus": world,
                           "dtype": "u8", "data": "synthetic", "serving": res,
-                          "p99_speedup_vs_unfused": round(p["p99_ms"] / max(f["p99_ms"], 1e-9), 2),
                           "rate_sweep_fused": sweep, "budget_256MB_fused": small}),
               flush=True)
+
+
+def relaunch_replicas(n: int) -> int:
+    """`--gpus N` (N > 1) run without a launcher: start N ranks of this same
+    command with torch.distributed.run (one process per GPU, loopback
+    rendezvous) and return their exit status."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr=127.0.0.1", f"--master-port={port}",
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 def main():
     args = parse()
     world, rank, local = dist_setup()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_replicas(args.gpus))
     if args.impl == "reference":
         reference_arm(args, world, rank)
         return
     import torch
+    if world > torch.cuda.device_count():
+        sys.exit(f"bench.py: {world} ranks but {torch.cuda.device_count()} visible GPUs")
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist

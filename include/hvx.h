@@ -544,6 +544,8 @@ typedef struct {
     double mean_ms;
     double max_ms;
     double mpix_completed;    /* output megapixels of completed requests     */
+    double wait_p99_ms;       /* submit -> admission (queueing) percentile   */
+    double wait_max_ms;
 } hvx_server_stats;
 
 /* Create a server on ctx.  mem_budget_bytes bounds the device bytes held by
@@ -556,9 +558,21 @@ hvx_status hvxCreateServer(hvx_context ctx, uint64_t mem_budget_bytes, int32_t m
 /* Submit verified graph g.  The request waits in FIFO order until a slot and
  * budget are free, then runs on the next stream.  A graph may have only one
  * request in flight at a time; a later request on it waits for the earlier
- * one.  *ticket identifies the request.  Fails with HVX_ERROR_OVER_BUDGET if
- * g alone exceeds the budget. */
+ * one, and requests on other graphs queued behind it are admitted meanwhile
+ * (a request that does not fit the budget holds back all behind it).
+ * *ticket identifies the request.  Fails with HVX_ERROR_OVER_BUDGET if g
+ * alone exceeds the budget. */
 hvx_status hvxServerSubmit(hvx_server s, hvx_graph g, uint64_t* ticket);
+
+/* Submit n verified graphs that arrive together: all n requests enter the
+ * queue at once, in array order, under one lock, so the dispatcher sees them
+ * together and admits as many as slots and budget allow in one pass (their
+ * work then overlaps on the server's streams).  tickets[i] identifies the
+ * request on graphs[i].  All-or-nothing: on any error (an invalid or
+ * unverified graph, one larger than the budget) nothing is queued and
+ * tickets is untouched.  n = 0 does nothing. */
+hvx_status hvxServerSubmitMany(hvx_server s, const hvx_graph* graphs, int32_t n,
+                               uint64_t* tickets);
 
 /* Wait up to timeout_ms (negative = forever) for a request.  On success
  * *result holds the request's own status and *latency_ms its latency; each

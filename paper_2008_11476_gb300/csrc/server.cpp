@@ -31,6 +31,7 @@ struct Request {
     uint64_t bytes = 0;
     double mpix = 0;
     double t_submit = 0;
+    double t_admit = 0;
     double latency_ms = 0;
     hvx_status result = HVX_SUCCESS;
     bool done = false;
@@ -60,6 +61,7 @@ struct Server {
     // statistics
     uint64_t submitted = 0, completed = 0, failed = 0, max_in_flight = 0, peak_reserved = 0;
     std::vector<double> latencies;
+    std::vector<double> waits;  // submission -> admission of completed requests
     double mpix_completed = 0;
 
     void run();
@@ -88,6 +90,7 @@ void Server::run() {
             if (r->result == HVX_SUCCESS) {
                 ++completed;
                 latencies.push_back(r->latency_ms);
+                waits.push_back(r->t_admit - r->t_submit);
                 mpix_completed += r->mpix;
             } else {
                 ++failed;
@@ -96,14 +99,22 @@ void Server::run() {
             inflight.pop_back();
             cv_done.notify_all();
         }
-        // admit in FIFO order while a slot and the budget allow
-        while (!queue.empty()) {
-            Request* r = queue.front();
+        // admit in FIFO order while a slot and the budget allow.  A request
+        // whose graph still has one in flight is passed over (it keeps its
+        // place; requests on other graphs behind it go ahead); one that does
+        // not fit the budget stops admission, so a large request is not
+        // overtaken indefinitely by smaller ones.
+        for (size_t qi = 0; qi < queue.size();) {
+            Request* r = queue[qi];
             if ((int)inflight.size() >= max_inflight) break;
+            if (r->g->busy.load()) {
+                ++qi;
+                continue;
+            }
             if (budget && reserved + r->bytes > budget) break;
-            if (r->g->busy.load()) break;
-            queue.pop_front();
+            queue.erase(queue.begin() + (std::ptrdiff_t)qi);
             r->g->busy.store(1);
+            r->t_admit = now_ms();
             reserved += r->bytes;
             peak_reserved = std::max(peak_reserved, reserved);
             cudaStream_t s = streams[next_stream];
@@ -209,13 +220,13 @@ hvx_status hvxServerSubmit(hvx_server hs, hvx_graph hg, uint64_t* ticket) {
     return hvxServerSubmitHost(hs, hg, nullptr, 0, ticket);
 }
 
-hvx_status hvxServerSubmitHost(hvx_server hs, hvx_graph hg, const hvx_host_copy* copies,
-                               int32_t n_copies, uint64_t* ticket) {
-    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+namespace {
+
+// Validate one request and build it (not yet queued).
+hvx_status make_request(Server* s, hvx_graph hg, const hvx_host_copy* copies, int32_t n_copies,
+                        Request** out) {
     Graph* g = reinterpret_cast<Graph*>(hg);
     if (!g || g->magic != kMagicGraph) return HVX_ERROR_INVALID_REFERENCE;
-    if (!ticket) return HVX_ERROR_INVALID_PARAMETERS;
-    Server* s = S(hs);
     if (g->ctx != s->ctx) return HVX_ERROR_INVALID_REFERENCE;
     if (!g->verified) return HVX_ERROR_NOT_VERIFIED;
     // device bytes the request holds while in flight: its images and the
@@ -245,20 +256,71 @@ hvx_status hvxServerSubmitHost(hvx_server hs, hvx_graph hg, const hvx_host_copy*
     r->g = g;
     r->bytes = bytes;
     r->mpix = mpix;
+    *out = r;
+    return HVX_SUCCESS;
+}
+
+// Queue built requests under one lock (they arrive together).
+hvx_status enqueue(Server* s, Request* const* rs, int n, uint64_t* tickets) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stop) {
-            delete r;
-            return HVX_ERROR_INVALID_REFERENCE;
+        if (s->stop) return HVX_ERROR_INVALID_REFERENCE;
+        const double t = now_ms();
+        for (int i = 0; i < n; ++i) {
+            Request* r = rs[i];
+            r->ticket = s->next_ticket++;
+            r->t_submit = t;
+            s->queue.push_back(r);
+            s->by_ticket[r->ticket] = r;
+            ++s->submitted;
+            tickets[i] = r->ticket;
         }
-        r->ticket = s->next_ticket++;
-        r->t_submit = now_ms();
-        s->queue.push_back(r);
-        s->by_ticket[r->ticket] = r;
-        ++s->submitted;
     }
     s->cv_work.notify_all();
-    *ticket = r->ticket;
+    return HVX_SUCCESS;
+}
+
+}  // namespace
+
+hvx_status hvxServerSubmitHost(hvx_server hs, hvx_graph hg, const hvx_host_copy* copies,
+                               int32_t n_copies, uint64_t* ticket) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!ticket) return HVX_ERROR_INVALID_PARAMETERS;
+    Server* s = S(hs);
+    Request* r = nullptr;
+    hvx_status st = make_request(s, hg, copies, n_copies, &r);
+    if (st != HVX_SUCCESS) return st;
+    uint64_t t = 0;
+    st = enqueue(s, &r, 1, &t);
+    if (st != HVX_SUCCESS) {
+        delete r;
+        return st;
+    }
+    *ticket = t;
+    return HVX_SUCCESS;
+}
+
+hvx_status hvxServerSubmitMany(hvx_server hs, const hvx_graph* graphs, int32_t n,
+                               uint64_t* tickets) {
+    if (!ok_server(hs)) return HVX_ERROR_INVALID_REFERENCE;
+    if (!graphs || !tickets || n < 0) return HVX_ERROR_INVALID_PARAMETERS;
+    if (n == 0) return HVX_SUCCESS;
+    Server* s = S(hs);
+    std::vector<Request*> rs;
+    rs.reserve((size_t)n);
+    hvx_status st = HVX_SUCCESS;
+    for (int i = 0; i < n && st == HVX_SUCCESS; ++i) {
+        Request* r = nullptr;
+        st = make_request(s, graphs[i], nullptr, 0, &r);
+        if (st == HVX_SUCCESS) rs.push_back(r);
+    }
+    std::vector<uint64_t> t((size_t)n);
+    if (st == HVX_SUCCESS) st = enqueue(s, rs.data(), n, t.data());
+    if (st != HVX_SUCCESS) {
+        for (Request* r : rs) delete r;
+        return st;
+    }
+    std::copy(t.begin(), t.end(), tickets);
     return HVX_SUCCESS;
 }
 
@@ -313,6 +375,13 @@ hvx_status hvxServerStats(hvx_server hs, hvx_server_stats* out) {
         st.mean_ms = sum / v.size();
         st.max_ms = v.back();
     }
+    if (!s->waits.empty()) {
+        std::vector<double> v = s->waits;
+        std::sort(v.begin(), v.end());
+        const size_t k = (size_t)std::ceil(0.99 * v.size()) - 1;
+        st.wait_p99_ms = v[std::min(k, v.size() - 1)];
+        st.wait_max_ms = v.back();
+    }
     *out = st;
     return HVX_SUCCESS;
 }
@@ -322,6 +391,7 @@ hvx_status hvxServerResetStats(hvx_server hs) {
     Server* s = S(hs);
     std::lock_guard<std::mutex> lk(s->mu);
     s->latencies.clear();
+    s->waits.clear();
     s->mpix_completed = 0;
     s->max_in_flight = s->inflight.size();
     s->peak_reserved = s->reserved;

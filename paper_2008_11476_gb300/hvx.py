@@ -71,7 +71,7 @@ class hvx_server_stats(ctypes.Structure):
                                                "in_flight", "max_in_flight", "bytes_reserved",
                                                "peak_bytes_reserved")] + \
                [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
-                                              "mpix_completed")]
+                                              "mpix_completed", "wait_p99_ms", "wait_max_ms")]
 
 
 HVX_NOALLOC_MAX_FRAMES = 256
@@ -161,6 +161,7 @@ _SIGS = {
     "hvxQueryNode": (I32, [P, I32, P, U64]),
     "hvxCreateServer": (I32, [P, U64, I32, I32, PP]),
     "hvxServerSubmit": (I32, [P, P, ctypes.POINTER(U64)]),
+    "hvxServerSubmitMany": (I32, [P, P, I32, ctypes.POINTER(U64)]),
     "hvxServerWait": (I32, [P, U64, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
     "hvxServerStats": (I32, [P, ctypes.POINTER(hvx_server_stats)]),
     "hvxServerResetStats": (I32, [P]),
@@ -509,6 +510,16 @@ def hvxServerSubmit(srv, g) -> int:
     t = U64()
     _ck(lib().hvxServerSubmit(srv, g, ctypes.byref(t)), "hvxServerSubmit")
     return t.value
+
+
+def hvxServerSubmitMany(srv, graphs) -> list[int]:
+    """Submit requests that arrive together (one queue insertion)."""
+    n = len(graphs)
+    arr = (ctypes.c_void_p * max(1, n))(*[g.value if isinstance(g, ctypes.c_void_p) else g
+                                          for g in graphs])
+    t = (U64 * max(1, n))()
+    _ck(lib().hvxServerSubmitMany(srv, arr, n, t), "hvxServerSubmitMany")
+    return [t[i] for i in range(n)]
 
 
 def hvxServerWait(srv, ticket: int, timeout_ms: int = -1):
