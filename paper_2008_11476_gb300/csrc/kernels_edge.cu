@@ -16,12 +16,18 @@
 //     in five words of pairs (x - 1 + 2j, x + 2j)) is computed once from three
 //     input rows and enters three Sobel rows.
 // Gaussian and Sobel sums run in 16-bit lanes (two pixels per 32-bit add,
-// biased so that no lane goes negative); gx and gy are unpacked to binary32
-// by exponent splicing and the point operators run in binary32, where every
-// value is an exact integer.  Magnitude followed by a binary threshold T is
-// evaluated as gx^2 + gy^2 > T^2 + T, which equals round(sqrt(gx^2 + gy^2)) > T.
-// The mask and phase bytes of a strip row leave in one 8-byte store each (a
-// half-warp writes 128 contiguous bytes).
+// biased so that no lane goes negative).  A Gaussian lane holds 16 G, the
+// weighted sum with its low four bits cleared (one mask instead of a shift
+// and a mask), and the Sobel sums run on those lanes; gx and gy are unpacked
+// to binary32 by exponent splicing and one packed fma that also takes out the
+// factor 16, and the point operators run in binary32, where every value is an
+// exact integer.  Magnitude followed by a binary threshold T is evaluated as
+// gx^2 + gy^2 > T^2 + T, which equals round(sqrt(gx^2 + gy^2)) > T, two
+// pixels per packed fma; the mask bytes come from the sign bits of those
+// values by sign-replicating byte permutes.  The mask and phase bytes of a
+// strip row leave in one 8-byte store each (a half-warp writes 128
+// contiguous bytes).  Interior tiles run a copy of the row loop with no
+// border, validity or bounds tests.
 //
 // Borders.  The TMA load fills the box cells outside the image with 0; edge
 // tiles then apply the Gaussian's border mode to them.  G rows and columns
@@ -88,14 +94,6 @@ struct EdgeSmem {
     int ts[BATCH_SMEM_IMAGES + 1], tx[BATCH_SMEM_IMAGES];
 };
 
-// Lane values of a 16-bit-lane word as binary32, minus a bias, exactly.
-__device__ __forceinline__ float lane_lo_f(uint32_t w, float bias) {
-    return __int_as_float(__byte_perm(w, 0x4B00u, 0x5410)) - (8388608.0f + bias);
-}
-__device__ __forceinline__ float lane_hi_f(uint32_t w, float bias) {
-    return __int_as_float(__byte_perm(w, 0x4B00u, 0x5432)) - (8388608.0f + bias);
-}
-
 __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
     return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
 }
@@ -104,13 +102,6 @@ __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2,
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// All-ones when a > b, else 0 (one instruction).
-__device__ __forceinline__ uint32_t set_gt(float a, float b) {
-    uint32_t r;
-    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
     return r;
 }
 
@@ -143,21 +134,50 @@ __device__ __forceinline__ float fma_rm(float a, float b, float c) {
 // mn - mx tan((n - 1/2) pi / 128) > 0.  n comes out of a round-down fma as
 // the low mantissa bits of a number in [1.5 * 2^23, 2^24); the table entry of
 // (octant, n) holds tan((n - 1/2) pi / 128) and the final phase byte for both
-// outcomes, and the sign of the test picks the byte.  The entry index is
-// formed with multiply-adds of sign bits.  gx = gy = 0 gives t = 0, n = 1 and
-// a negative test (mx is raised to 1 there), so phase 0.
-__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const PhaseEntry* lut) {
+// outcomes (byte 0: n, byte 1: n - 1), and the sign of the test picks the
+// byte.  The entry index is formed with multiply-adds of sign bits.
+// gx = gy = 0 gives t = 0, n = 1 and a negative test (mx is raised to 1
+// there), so phase 0.
+struct PhaseCand {
+    uint32_t q;  // phase byte for n (byte 0) and for n - 1 (byte 1)
+    float h;     // the exact test: negative selects byte 1
+};
+
+// The octant's sign bits as 0 / 1 floats come from saturating operations on
+// exact integers (sat(-gx) = [gx < 0], sat(|gy| - |gx|) = [|gy| > |gx|]),
+// and the table index is added to the guess with exact fmas (the guess has
+// unit spacing in [1.5 * 2^23, 2^24)), so the index costs floating-point
+// operations only.
+__device__ __forceinline__ PhaseCand phase_cand(float gx, float gy, const PhaseEntry* lut) {
     const float ax = fabsf(gx), ay = fabsf(gy);
-    const float mx = fmaxf(fmaxf(ax, ay), 1.0f), mn = fminf(ax, ay);
+    float mx;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(mx) : "f"(ax), "f"(ay), "f"(1.0f));
+    const float mn = fminf(ax, ay);
     const float t = mn * rcp_approx(mx);
-    const float y = fma_rm(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 12582913.0f);  // 1.5*2^23 + 1
-    int idx = __float_as_int(y) - 0x4B400000;                // n = 1 .. 33
-    idx = (int)(__float_as_uint(gx) >> 31) * 136 + idx;     // + 4 * 34 [gx < 0]
-    idx = (int)(__float_as_uint(gy) >> 31) * 68 + idx;      // + 2 * 34 [gy < 0]
-    idx = (int)set_gt(ay, ax) * -34 + idx;                  // + 34 [|gy| > |gx|]
-    const PhaseEntry e = lut[idx];
-    const float h = fmaf(-mx, e.tan, mn);  // < 0: the octant angle rounds to n - 1
-    return __byte_perm(e.q, 0u, __float_as_uint(h) >> 31);
+    float y = fma_rm(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 12582913.0f);  // 1.5*2^23 + 1
+    y = fmaf(__saturatef(-gx), 136.0f, y);     // + 4 * 34 [gx < 0]
+    y = fmaf(__saturatef(-gy), 68.0f, y);      // + 2 * 34 [gy < 0]
+    y = fmaf(__saturatef(ay - ax), 34.0f, y);  // + 34 [|gy| > |gx|]
+    const PhaseEntry e = lut[__float_as_int(y) - 0x4B400000];  // n = 1 .. 33 + 34 x octant
+    return {e.q, fmaf(-mx, e.tan, mn)};
+}
+
+// The phase bytes of two pixels in bytes 0 and 1 of a word: one byte permute
+// whose selector takes byte 0 or 1 of the first candidate word and byte 4 or
+// 5 (bytes 0, 1 of the second) by the signs of the two tests.  A test is
+// never smaller than 2^-40 in magnitude, so sat(-2^40 h) = [h < 0]; the
+// selector is formed in the low bits of 2^23 + 0x40 + [ha < 0] + 16 [hb < 0]
+// (the byte permute reads only the low 16 bits of its selector).
+__device__ __forceinline__ uint32_t phase_pair(const PhaseCand& a, const PhaseCand& b) {
+    const float na = __saturatef(a.h * -1099511627776.0f);
+    const float nb = __saturatef(b.h * -1099511627776.0f);
+    const float sel = fmaf(nb, 16.0f, na + 8388672.0f);  // 2^23 + 0x40
+    return __byte_perm(a.q, b.q, __float_as_uint(sel));
+}
+
+__device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const PhaseEntry* lut) {
+    const PhaseCand c = phase_cand(gx, gy, lut);
+    return __byte_perm(c.q, 0u, __float_as_uint(c.h) >> 31);
 }
 
 __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
@@ -176,16 +196,50 @@ __device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, in
 
 // ---- input box border ------------------------------------------------------------
 
-// lh: box rows the TMA filled (LH, or 8 rows + 4 in the single-image kernel)
+// Both borders REPLICATE: every tile runs the plain row loop (see
+// fix_input_border).
+__device__ __forceinline__ bool rep2_borders(const EdgeParams& p) {
+    return p.border_g == HVX_BORDER_REPLICATE && p.border_s == HVX_BORDER_REPLICATE;
+}
+
+// Box cells outside the image that a G value inside the image, or the plain
+// G of the row / column just outside it, reads: the two rows above and below
+// the image and the two columns left and right of it.  They take the
+// Gaussian's border mode (CONSTANT: the constant; REPLICATE: the nearest
+// pixel).  When the Sobel replicates too (rep2), the second cell repeats the
+// pixel one further in (-2 -> 1, W + 1 -> W - 2): the plain Gaussian of row
+// (column) -1 then equals the Gaussian of row (column) 0, which is exactly
+// the value Sobel REPLICATE reads there, and the same at the far edges, so
+// no G row or lane needs a fix.  Cells further out are never read for a
+// stored output.  lh: box rows the TMA filled (LH, or 8R + 4 in the
+// single-image kernel).  Reads only cells inside the image, writes only
+// cells outside it, so threads never race.
 __device__ void fix_input_border(Box& in, const EdgeParams& p, int x0, int y0, int lh = LH) {
-    const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
+    const int W = p.W, H = p.H, bx = x0 - 16, by = y0 - 2;
     const bool cst = p.border_g == HVX_BORDER_CONSTANT;
+    const bool rep2 = rep2_borders(p);
     const uint8_t cv = (uint8_t)p.cval_g;
-    for_each_outside(lh, LW, x0 - 16, y0 - 2, W, H, [&](int r, int c) {
-        const int x = x0 - 16 + c, y = y0 - 2 + r;
-        in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 2)][clampi(x, 0, W - 1) - (x0 - 16)];
-    });
+    auto src = [&](int v, int n) {  // source coordinate of v in [-2, n + 1]
+        if (v >= 0 && v < n) return v;
+        if (v < 0) return (rep2 && v == -2) ? min(1, n - 1) : 0;
+        return (rep2 && v == n + 1) ? max(n - 2, 0) : n - 1;
+    };
+    auto put = [&](int r, int c) {
+        in[r][c] = cst ? cv : in[src(by + r, H) - by][src(bx + c, W) - bx];
+    };
+    // rows -2, -1, H, H + 1 that the box holds, every column
+    for (int k = threadIdx.x; k < 4 * LW; k += blockDim.x) {
+        const int j = k / LW, c = k - j * LW;
+        const int r = (j < 2 ? j - 2 : H + j - 2) - by;
+        if (r >= 0 && r < lh) put(r, c);
+    }
+    // columns -2, -1, W, W + 1 of the box rows inside the image
+    for (int k = threadIdx.x; k < 4 * lh; k += blockDim.x) {
+        const int r = k >> 2, j = k & 3;
+        const int c = (j < 2 ? j - 2 : W + j - 2) - bx;
+        if (by + r >= 0 && by + r < H && c >= 0 && c < LW) put(r, c);
+    }
 }
 
 // ---- Gaussian rows ---------------------------------------------------------------
@@ -204,9 +258,10 @@ __device__ __forceinline__ void load_pairs(const uint8_t* row, int c, uint32_t P
     P[5] = lo_pair(wr);
 }
 
-// G at x - 1 .. x + 8 of one row from the pair words of the input rows above
-// (a), at (b) and below (c): word j holds (x - 1 + 2j, x + 2j) in 16-bit lanes.
-// Lane sums stay below 16 * 255 + 8 < 2^12, so lanes never carry.
+// 16 G at x - 1 .. x + 8 of one row from the pair words of the input rows
+// above (a), at (b) and below (c): word j holds (x - 1 + 2j, x + 2j) in
+// 16-bit lanes.  Lane sums stay below 16 * 255 + 8 < 2^12, so lanes never
+// carry; clearing the low four bits of a lane leaves 16 floor(sum / 16).
 __device__ __forceinline__ void g_row(const uint32_t* a, const uint32_t* b, const uint32_t* c,
                                       uint32_t rnd, uint32_t* G) {
     uint32_t V[6];
@@ -214,10 +269,10 @@ __device__ __forceinline__ void g_row(const uint32_t* a, const uint32_t* b, cons
     for (int k = 0; k < 6; ++k) V[k] = a[k] + 2u * b[k] + c[k];
 #pragma unroll
     for (int j = 0; j < 5; ++j)
-        G[j] = ((V[j] + V[j + 1] + rnd + 2u * shift_pair(V[j], V[j + 1])) >> 4) & 0x00FF00FFu;
+        G[j] = (V[j] + V[j + 1] + rnd + 2u * shift_pair(V[j], V[j + 1])) & 0xFFF0FFF0u;
 }
 
-// G row yq (x - 1 .. x + 8) as the Sobel reads it, for a strip whose window
+// G row yq (x - 1 .. x + 8, as 16 G) as the Sobel reads it, for a strip whose window
 // leaves the Gaussian's valid region: outside the image the Sobel's border
 // mode (REPLICATE: the Gaussian output at the clamped position; CONSTANT: the
 // constant; UNDEFINED: 0, read by no valid output), inside the image but
@@ -227,7 +282,7 @@ __device__ __forceinline__ void g_row(const uint32_t* a, const uint32_t* b, cons
 __device__ __noinline__ void g_row_edge(const Box& in, const EdgeParams& p, int x, int x0, int y0,
                                         int yq, uint32_t rnd, uint32_t* G) {
     const int W = p.W, H = p.H;
-    const uint32_t cv = (uint32_t)(p.cval_s & 0xFF);
+    const uint32_t cv = 16u * (uint32_t)(p.cval_s & 0xFF);
     int yy = yq;
     if (yy < 0 || yy >= H) {
         if (p.border_s != HVX_BORDER_REPLICATE) {
@@ -259,7 +314,7 @@ __device__ __noinline__ void g_row_edge(const Box& in, const EdgeParams& p, int 
         const uint32_t s = (r0[c - 1] + 2u * r0[c] + r0[c + 1]) +
                            2u * (r1[c - 1] + 2u * r1[c] + r1[c + 1]) +
                            (r2[c - 1] + 2u * r2[c] + r2[c + 1]) + (rnd & 0xFFFFu);
-        g[l] = s >> 4;
+        g[l] = s & ~15u;
     }
     for (int j = 0; j < 5; ++j) G[j] = g[2 * j] | (g[2 * j + 1] << 16);
 }
@@ -277,7 +332,7 @@ struct GPolicy {
     bool rep;          // Sobel border REPLICATE (else CONSTANT)
     bool left;         // x == 0: lane 0 (x - 1) is outside the image
     int L;             // lanes 0 .. L - 1 are inside the image
-    uint32_t cv;       // Sobel border constant
+    uint32_t cv;       // Sobel border constant, times 16
 };
 
 __device__ __forceinline__ void patch_cols(const GPolicy& gp, uint32_t* G) {
@@ -319,34 +374,32 @@ __device__ __forceinline__ void g_row_any(const GPolicy& gp, const Box& in, cons
 
 // ---- Sobel + point operators of one output row --------------------------------------
 
-// gx, gy at x .. x + 7 from the G rows above (a), at (b) and below (c).
-// Lanes: vs <= 1020, dy = c - a + 255 in [0, 510]; gx + 1024 and gy + 1020
-// are in [4, 2044].
+// gx, gy at x .. x + 7 from the 16 G rows above (a), at (b) and below (c),
+// as pairs (x + 2j, x + 2j + 1).  Lanes: vs <= 16320, dy = c - a + 4080 in
+// [0, 8160]; 16 gx + 16384 and 16 gy + 16320 are in [0, 32704].  A lane
+// spliced under the exponent of 2^23 is 2^23 + lane; one packed fma scales by
+// 1/16 and takes out both offsets, exactly.
 __device__ __forceinline__ void sobel8(const uint32_t* a, const uint32_t* b, const uint32_t* c,
-                                       float* gx, float* gy) {
+                                       float2* gx, float2* gy) {
     uint32_t vs[5], dy[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         vs[j] = a[j] + 2u * b[j] + c[j];
-        dy[j] = c[j] + 0x00FF00FFu - a[j];
+        dy[j] = c[j] + 0x0FF00FF0u - a[j];
     }
-    // both lanes of a word unpacked by one packed binary32 subtraction
-    const float2 bx = make_float2(-(8388608.0f + 1024.0f), -(8388608.0f + 1024.0f));
-    const float2 by = make_float2(-(8388608.0f + 1020.0f), -(8388608.0f + 1020.0f));
+    const float2 s16 = make_float2(0.0625f, 0.0625f);
+    const float2 bx = make_float2(-(8388608.0f + 16384.0f) / 16, -(8388608.0f + 16384.0f) / 16);
+    const float2 by = make_float2(-(8388608.0f + 16320.0f) / 16, -(8388608.0f + 16320.0f) / 16);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const uint32_t gxp = vs[j + 1] + 0x04000400u - vs[j];
+        const uint32_t gxp = vs[j + 1] + 0x40004000u - vs[j];
         const uint32_t gyp = dy[j] + dy[j + 1] + 2u * shift_pair(dy[j], dy[j + 1]);
-        const float2 fx = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gxp, 0x4B00u, 0x5410)),
-                                                 __int_as_float(__byte_perm(gxp, 0x4B00u, 0x5432))),
-                                     bx);
-        const float2 fy = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gyp, 0x4B00u, 0x5410)),
-                                                 __int_as_float(__byte_perm(gyp, 0x4B00u, 0x5432))),
-                                     by);
-        gx[2 * j] = fx.x;
-        gx[2 * j + 1] = fx.y;
-        gy[2 * j] = fy.x;
-        gy[2 * j + 1] = fy.y;
+        gx[j] = __ffma2_rn(make_float2(__int_as_float(__byte_perm(gxp, 0x4B00u, 0x5410)),
+                                       __int_as_float(__byte_perm(gxp, 0x4B00u, 0x5432))),
+                           s16, bx);
+        gy[j] = __ffma2_rn(make_float2(__int_as_float(__byte_perm(gyp, 0x4B00u, 0x5410)),
+                                       __int_as_float(__byte_perm(gyp, 0x4B00u, 0x5432))),
+                           s16, by);
     }
 }
 
@@ -357,10 +410,11 @@ struct RowCtx {
     uint8_t* mask;
     uint8_t* phase;
     size_t mask_pitch, phase_pitch;
-    float s_thr;
-    uint32_t tvx, fvx;  // mask bytes: (c & tvx) ^ fvx from all-ones / zero compares
+    float nthr;         // -(min(s_thr, 2^22) + 1/2): gx^2 + gy^2 + nthr > 0 <=> mask true
+    uint32_t fx, tvx;   // mask bytes: (c & fx) ^ tvx from all-ones (false) / zero (true)
     int W, x;
     bool full;          // every output of the strip is inside its valid region
+    bool fast;          // whole 8-byte stores: a fast tile and the strip inside the image
 };
 
 __device__ __forceinline__ void store8_words(uint8_t* row, int x, int W, uint32_t lo, uint32_t hi) {
@@ -372,76 +426,111 @@ __device__ __forceinline__ void store8_words(uint8_t* row, int x, int W, uint32_
     }
 }
 
+// gx^2 + gy^2 + nthr for a pixel pair: every term is an integer or a half
+// below 2^23, so the packed fmas are exact and the value is never 0; it is
+// negative exactly when the mask is false.
+__device__ __forceinline__ float2 mask_value2(float2 gx, float2 gy, float nthr) {
+    return __ffma2_rn(gx, gx, __ffma2_rn(gy, gy, make_float2(nthr, nthr)));
+}
+
+// Bytes 0 and 1: the sign bits of a and b replicated over a byte (prmt with
+// the sign flag of selector nibbles 0xB and 0xF; __byte_perm ignores that flag).
+__device__ __forceinline__ uint32_t sign_bytes2(float a, float b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xFB;" : "=r"(r) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
+    return r;
+}
+
+// Mask bytes of four pixels from the sign bits of their values: 0xFF where
+// the mask is false, then true / false values applied.
+__device__ __forceinline__ uint32_t mask4(const RowCtx& cx, float2 a, float2 b) {
+    return (__byte_perm(sign_bytes2(a.x, a.y), sign_bytes2(b.x, b.y), 0x5410) & cx.fx) ^ cx.tvx;
+}
+
+__device__ __forceinline__ void point_row_general(const RowCtx& cx, const EdgeParams& p,
+                                                  const float2* gx2, const float2* gy2, int y);
+
 template <int MODE>
-__device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p, const float* gx,
-                                          const float* gy, int y) {
+__device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p, const float2* gx2,
+                                          const float2* gy2, int y) {
     constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK;
     constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
+    const int x = cx.x;
+    if constexpr (MODE != M_GENERAL) {
+        uint32_t mw[2] = {0u, 0u}, pw[2] = {0u, 0u};
+        if (kMask) {
+            float2 mv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mv[j] = mask_value2(gx2[j], gy2[j], cx.nthr);
+            mw[0] = mask4(cx, mv[0], mv[1]);
+            mw[1] = mask4(cx, mv[2], mv[3]);
+        }
+        if (kPhase) {
+            uint32_t pp[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                pp[j] = phase_pair(phase_cand(gx2[j].x, gy2[j].x, cx.plut),
+                                   phase_cand(gx2[j].y, gy2[j].y, cx.plut));
+            pw[0] = __byte_perm(pp[0], pp[1], 0x5410);
+            pw[1] = __byte_perm(pp[2], pp[3], 0x5410);
+        }
+        if (cx.fast) {
+            if (kMask)
+                *reinterpret_cast<uint2*>(cx.mask + (size_t)y * cx.mask_pitch + x) =
+                    make_uint2(mw[0], mw[1]);
+            if (kPhase)
+                *reinterpret_cast<uint2*>(cx.phase + (size_t)y * cx.phase_pitch + x) =
+                    make_uint2(pw[0], pw[1]);
+            return;
+        }
+        if (!cx.full) {  // zero outside the valid region, byte by byte
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (!in_rect(p.valid, x + i, y)) {
+                    const uint32_t keep = ~(0xFFu << (8 * (i & 3)));
+                    mw[i >> 2] &= keep;
+                    pw[i >> 2] &= keep;
+                }
+        }
+        if (kMask) store8_words(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W, mw[0], mw[1]);
+        if (kPhase) store8_words(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W, pw[0], pw[1]);
+    } else {
+        point_row_general(cx, p, gx2, gy2, y);
+    }
+}
+
+// Any outputs: magnitude export, range threshold, mask and / or phase.
+__device__ __forceinline__ void point_row_general(const RowCtx& cx, const EdgeParams& p,
+                                                  const float2* gx2, const float2* gy2, int y) {
+    const int x = cx.x;
     uint32_t mk[8], ph[8];
     int mg[8];
-    if (kMask) {
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-            if (kPhase) {
-                mk[i] = set_gt(fmaf(gx[i], gx[i], gy[i] * gy[i]), cx.s_thr);
-                mk[i + 1] = set_gt(fmaf(gx[i + 1], gx[i + 1], gy[i + 1] * gy[i + 1]), cx.s_thr);
-            } else {  // mask alone: gx^2 + gy^2 of two pixels per packed operation
-                const float2 X = make_float2(gx[i], gx[i + 1]), Y = make_float2(gy[i], gy[i + 1]);
-                const float2 s2 = __ffma2_rn(X, X, __fmul2_rn(Y, Y));
-                mk[i] = set_gt(s2.x, cx.s_thr);
-                mk[i + 1] = set_gt(s2.y, cx.s_thr);
-            }
-        }
-    }
-    if (kPhase) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
-    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        if (!kMask) mk[i] = 0u;
-        if (!kPhase) ph[i] = 0u;
-        mg[i] = 0;
-        if (MODE == M_GENERAL) {
-            const int ix = (int)gx[i], iy = (int)gy[i];
-            mg[i] = magnitude_s16(ix, iy);
-            if (cx.mask) {
-                bool t;
-                if (!p.thr_general)
-                    t = ix * ix + iy * iy > p.s_thr;
-                else
-                    t = p.thr_type == HVX_THRESHOLD_BINARY ? mg[i] > p.thr_lo
-                                                           : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
-                mk[i] = t ? 0xFFFFFFFFu : 0u;
-            }
-            if (cx.phase) ph[i] = phase_from_float(gx[i], gy[i], cx.plut);
+        const float gx = (i & 1) ? gx2[i >> 1].y : gx2[i >> 1].x;
+        const float gy = (i & 1) ? gy2[i >> 1].y : gy2[i >> 1].x;
+        const int ix = (int)gx, iy = (int)gy;
+        mg[i] = magnitude_s16(ix, iy);
+        mk[i] = 0u;
+        if (cx.mask) {
+            bool t;
+            if (!p.thr_general)
+                t = ix * ix + iy * iy > p.s_thr;
+            else
+                t = p.thr_type == HVX_THRESHOLD_BINARY ? mg[i] > p.thr_lo
+                                                       : !(mg[i] > p.thr_hi || mg[i] < p.thr_lo);
+            mk[i] = (uint32_t)(t ? p.tv : p.fv) & 0xFFu;
+        }
+        ph[i] = cx.phase ? phase_from_float(gx, gy, cx.plut) : 0u;
+        if (!cx.full && !in_rect(p.valid, x + i, y)) {
+            mk[i] = 0u;
+            ph[i] = 0u;
+            mg[i] = 0;
         }
     }
-    const bool want_mask = kMask || (MODE == M_GENERAL && cx.mask);
-    const bool want_phase = kPhase || (MODE == M_GENERAL && cx.phase);
-    const int x = cx.x;
-    if (cx.full) {
-        if (want_mask)
-            store8_words(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W,
-                         (pack4(mk[0], mk[1], mk[2], mk[3]) & cx.tvx) ^ cx.fvx,
-                         (pack4(mk[4], mk[5], mk[6], mk[7]) & cx.tvx) ^ cx.fvx);
-        if (want_phase)
-            store8_words(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W,
-                         pack4(ph[0], ph[1], ph[2], ph[3]), pack4(ph[4], ph[5], ph[6], ph[7]));
-    } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            mk[i] = (mk[i] & cx.tvx) ^ cx.fvx;
-            if (!in_rect(p.valid, x + i, y)) {
-                mk[i] = 0u;
-                ph[i] = 0u;
-                mg[i] = 0;
-            }
-        }
-        if (want_mask) store8_u8(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W, mk);
-        if (want_phase) store8_u8(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W, ph);
-    }
-    if (MODE == M_GENERAL && p.mag) {
+    if (cx.mask) store8_u8(cx.mask + (size_t)y * cx.mask_pitch, x, cx.W, mk);
+    if (cx.phase) store8_u8(cx.phase + (size_t)y * cx.phase_pitch, x, cx.W, ph);
+    if (p.mag) {
         int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
                                                   (size_t)y * p.mag_pitch);
         if (x + 8 <= cx.W) {
@@ -460,24 +549,34 @@ __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p,
 
 // One output row y of the strip: load input row y + 2 into Pn, form G row y + 1
 // into Gc from (Pa, Pb, Pn), then Sobel over (Ga, Gb, Gc) and the point ops.
-template <int MODE>
+// FAST: the plain G row (no border fix-ups) and whole stores where the strip
+// lies inside the image.
+template <int MODE, bool FAST>
 __device__ __forceinline__ void edge_row(const RowCtx& cx, const GPolicy& gp, const EdgeParams& p,
                                          const Box& in, const uint8_t* in_row, int c, int x0,
                                          int y0, uint32_t rnd, const uint32_t* Pa,
                                          const uint32_t* Pb, uint32_t* Pn, const uint32_t* Ga,
                                          const uint32_t* Gb, uint32_t* Gc, int y) {
     load_pairs(in_row, c, Pn);
-    g_row_any(gp, in, p, cx.x, x0, y0, y + 1, rnd, cx.gslow, Pa, Pb, Pn, Gc);
-    float gx[8], gy[8];
+    if (FAST)
+        g_row(Pa, Pb, Pn, rnd, Gc);
+    else
+        g_row_any(gp, in, p, cx.x, x0, y0, y + 1, rnd, cx.gslow, Pa, Pb, Pn, Gc);
+    float2 gx[4], gy[4];
     sobel8(Ga, Gb, Gc, gx, gy);
     point_row<MODE>(cx, p, gx, gy, y);
 }
 
 // One tile after its box has landed (and, on edge tiles, been border-fixed):
-// 128 x 8 rows output pixels, `rows` per thread.
+// 128 x 8 rows output pixels, `rows` per thread.  `fast`: every G row of the
+// tile is the plain Gaussian of the box and every output is valid -- interior
+// tiles, and every tile when both borders replicate (fix_input_border).  Those
+// run the row loop unrolled three times (the sliding windows rotate by
+// renaming); the others run the general loop, one row per trip with the
+// windows moved, which keeps the code small.
 template <int MODE>
 __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, int x0, int y0,
-                                          bool interior, const PhaseEntry* plut,
+                                          bool fast, const PhaseEntry* plut,
                                           uint32_t (*gslow)[5], int rows = ROWS) {
     const int q = threadIdx.x & 15, gi = threadIdx.x >> 4;
     const int W = p.W, H = p.H;
@@ -490,14 +589,42 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     cx.phase = p.phase;
     cx.mask_pitch = p.mask_pitch;
     cx.phase_pitch = p.phase_pitch;
-    cx.s_thr = (float)p.s_thr;
-    cx.tvx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
-    cx.fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
+    cx.nthr = -((float)min(p.s_thr, 1 << 22) + 0.5f);
+    cx.fx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
+    cx.tvx = ((uint32_t)p.tv & 0xFFu) * 0x01010101u;
     cx.W = W;
     cx.x = x;
-    cx.full = interior || rect_full(p.valid, W, H);
+    cx.full = fast || rect_full(p.valid, W, H);
+    cx.fast = fast && x + 8 <= W;  // whole 8-byte stores
     const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
+    const int c = 16 + 8 * q;
+    const uint8_t* row = &in[rows * gi][0];  // input row yb - 2
+    const int n = min(rows, H - yb);
+    uint32_t P0[6], P1[6], P2[6], G0[5], G1[5], G2[5];
+    load_pairs(row, c, P1);           // yb - 2
+    load_pairs(row + 2 * LW, c, P0);  // yb
     GPolicy gp;
+    if (fast) {
+        load_pairs(row + LW, c, P2);      // yb - 1
+        g_row(P1, P2, P0, rnd, G0);       // G(yb - 1)
+        load_pairs(row + 3 * LW, c, P1);  // yb + 1
+        g_row(P2, P0, P1, rnd, G1);       // G(yb)
+        // rows: P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y); the
+        // windows rotate with period 3, so three rows per trip keep them in place
+        const uint8_t* r = row + 4 * LW;  // input row yb + 2
+#pragma unroll 1
+        for (int i = 0; i < n; i += 3) {
+            edge_row<MODE, true>(cx, gp, p, in, r, c, x0, y0, rnd, P0, P1, P2, G0, G1, G2, yb + i);
+            if (i + 1 >= n) break;
+            edge_row<MODE, true>(cx, gp, p, in, r + LW, c, x0, y0, rnd, P1, P2, P0, G1, G2, G0,
+                                 yb + i + 1);
+            if (i + 2 >= n) break;
+            edge_row<MODE, true>(cx, gp, p, in, r + 2 * LW, c, x0, y0, rnd, P2, P0, P1, G2, G0,
+                                 G1, yb + i + 2);
+            r += 3 * LW;
+        }
+        return;
+    }
     gp.gv1 = p.gvalid[1];
     gp.gv3 = p.gvalid[3];
     gp.sobel_undef = p.border_s == HVX_BORDER_UNDEFINED;
@@ -506,31 +633,28 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     gp.rep = p.border_s == HVX_BORDER_REPLICATE;
     gp.left = x == 0;
     gp.L = min(10, W - x + 1);
-    gp.cv = (uint32_t)(p.cval_s & 0xFF);
-    const int c = 16 + 8 * q;
-    const uint8_t* row = &in[rows * gi][0];  // input row yb - 2
-    // prologue: G rows yb - 1 and yb
-    uint32_t P0[6], P1[6], P2[6], G0[5], G1[5], G2[5];
-    load_pairs(row, c, P1);           // yb - 2
-    load_pairs(row + LW, c, P2);      // yb - 1
-    load_pairs(row + 2 * LW, c, P0);  // yb
+    gp.cv = 16u * (uint32_t)(p.cval_s & 0xFF);
+    load_pairs(row + LW, c, P2);  // yb - 1
     g_row_any(gp, in, p, x, x0, y0, yb - 1, rnd, cx.gslow, P1, P2, P0, G0);
     load_pairs(row + 3 * LW, c, P1);  // yb + 1
     g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
-    // rows: P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y); the
-    // windows rotate with period 3, so three rows per trip keep them in place
-    const int n = min(rows, H - yb);
-    const uint8_t* r = row + 4 * LW;  // input row yb + 2
+    // P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y): one row per
+    // trip, then the windows move up by one
+    const uint8_t* r = row + 4 * LW;
 #pragma unroll 1
-    for (int i = 0; i < n; i += 3) {
-        edge_row<MODE>(cx, gp, p, in, r, c, x0, y0, rnd, P0, P1, P2, G0, G1, G2, yb + i);
-        if (i + 1 >= n) break;
-        edge_row<MODE>(cx, gp, p, in, r + LW, c, x0, y0, rnd, P1, P2, P0, G1, G2, G0,
-                       yb + i + 1);
-        if (i + 2 >= n) break;
-        edge_row<MODE>(cx, gp, p, in, r + 2 * LW, c, x0, y0, rnd, P2, P0, P1, G2, G0, G1,
-                       yb + i + 2);
-        r += 3 * LW;
+    for (int i = 0; i < n; ++i) {
+        edge_row<MODE, false>(cx, gp, p, in, r, c, x0, y0, rnd, P0, P1, P2, G0, G1, G2, yb + i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            P0[k] = P1[k];
+            P1[k] = P2[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            G0[k] = G1[k];
+            G1[k] = G2[k];
+        }
+        r += LW;
     }
 }
 
@@ -566,7 +690,7 @@ __global__ void __launch_bounds__(EDGE_THREADS)
         fix_input_border(sm.in[0].b, p, x0, y0, th + 4);
         __syncthreads();
     }
-    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior, sm.plut, sm.gslow, rows);
+    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, rows);
 }
 
 // Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
@@ -644,7 +768,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
             fix_input_border(sm.in[s].b, p, x0, y0);
             __syncthreads();
         }
-        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior, sm.plut, sm.gslow);
+        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow);
         __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
         if (threadIdx.x == 0) {
             const int tn = t + STAGES * (int)gridDim.x;
