@@ -306,12 +306,21 @@ def parity_of(pairs, rule="bit-exact"):
     return {"rule": rule, "outputs_compared": n, "mismatches": bad, "ok": bad == 0}
 
 
+def library_env():
+    """HVX_* tuning variables set for this run (they change kernel choices, so
+    a line measured with any of them says so)."""
+    return {k: v for k, v in sorted(os.environ.items()) if k.startswith("HVX_")}
+
+
 def edge_config(args, world):
-    return {"workload": f"edge graph Gaussian3x3->Sobel3x3->Magnitude->Threshold(100)+Phase, "
-                        f"1920x1080 U8, {args.frames} frames per step, BORDER_REPLICATE",
-            "global_batch": args.frames * max(1, world), "frames_per_gpu": args.frames,
-            "width": W, "height": H_, "parallelism": f"replicas x{world}",
-            "l2": "inputs+outputs per step larger than L2 (no flush)"}
+    cfg = {"workload": f"edge graph Gaussian3x3->Sobel3x3->Magnitude->Threshold(100)+Phase, "
+                       f"1920x1080 U8, {args.frames} frames per step, BORDER_REPLICATE",
+           "global_batch": args.frames * max(1, world), "frames_per_gpu": args.frames,
+           "width": W, "height": H_, "parallelism": f"replicas x{world}",
+           "l2": "inputs+outputs per step larger than L2 (no flush)"}
+    if library_env():
+        cfg["env"] = library_env()
+    return cfg
 
 
 # ---------------------------------------------------------------------------

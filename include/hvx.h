@@ -192,6 +192,19 @@ hvx_status hvxReleaseContext(hvx_context* ctx);
  * when that happened (the expected result); the context remains usable. */
 hvx_status hvxSelfTestBoundedWait(hvx_context ctx);
 
+/* Self-test of the fused edge kernel's point arithmetic (Table 2 Phase and
+ * Magnitude -> binary Threshold; the kernel's own device functions and Phase
+ * table, not a copy): for every integer gradient pair (gx, gy) in
+ * [-gmax, gmax]^2, element i = (gy + gmax) * (2 gmax + 1) + (gx + gmax) of
+ * phase_out receives the Phase byte round(atan2(gy, gx) * 128 / pi) mod 256
+ * and mask_out 255 when gx^2 + gy^2 > s_thr, else 0.  Both are HOST buffers
+ * of (2 gmax + 1)^2 bytes, written on success.  0 <= gmax <= 4096 (Sobel3x3
+ * on U8 input reaches 1020), else HVX_ERROR_INVALID_PARAMETERS; allocates
+ * 2 (2 gmax + 1)^2 bytes of device memory for the call (HVX_ERROR_NO_MEMORY)
+ * and synchronises the device. */
+hvx_status hvxSelfTestEdgePoint(hvx_context ctx, int32_t gmax, int32_t s_thr, uint8_t* phase_out,
+                                uint8_t* mask_out);
+
 /* Cap the device bytes the context may allocate for images and plans
  * (0 = unlimited).  Allocations beyond it fail with HVX_ERROR_OVER_BUDGET. */
 hvx_status hvxSetContextMemoryBudget(hvx_context ctx, uint64_t bytes);
@@ -629,11 +642,14 @@ typedef struct {
  * The launch tables and the device error word live in a fixed array of the
  * library; its address is looked up (cudaGetSymbolAddress) on the first call
  * made on each device, with that device current, so make that first call
- * before any stream capture.  Every call rewrites the array (clearing the
- * error word), so calls whose GPU work overlaps -- from different host
- * threads or on different streams without ordering -- race on it; calls are
- * serialised on the host side only.  The call waits for its work on `stream`
- * and returns HVX_ERROR_TIMEOUT if a kernel's bounded wait ran out.
+ * before any stream capture.  Every call shares the array and rewrites it
+ * (clearing the error word), so calls whose GPU work overlapped would race on
+ * it; this implementation keeps them apart by holding one process-wide lock
+ * from its first write of the array until its work on `stream` has finished
+ * (it copies the tables in, launches, reads the error word back and waits
+ * for `stream`), so calls from several host threads run one after another.
+ * Work the caller puts on `stream` before the call runs before it.  Returns
+ * HVX_ERROR_TIMEOUT if a kernel's bounded wait ran out.
  * Returns HVX_ERROR_OVER_BUDGET if n > HVX_NOALLOC_MAX_FRAMES and
  * HVX_ERROR_INVALID_PARAMETERS for a NULL, misaligned or inconsistent frame. */
 hvx_status hvxEdgeBatchNoAlloc(const hvx_edge_frame* frames, int32_t n, int32_t border,

@@ -791,6 +791,37 @@ cudaError_t launch_batch_mode(const EdgeBatchDesc& d, int grid, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// Point operators of the fused edge kernel over every integer gradient pair
+// (gx, gy) in [-gmax, gmax]^2, element i = (gy + gmax) (2 gmax + 1) + gx + gmax:
+// the Phase byte through phase_cand / phase_pair (two elements per call, as
+// the kernel pairs neighbouring pixels) and the mask byte (255 / 0) through
+// mask_value2 / sign_bytes2 for gx^2 + gy^2 > s_thr.  Same device code and
+// shared-memory table as edge_batch_kernel; a self-test, not a hot path.
+__global__ void __launch_bounds__(256) edge_point_selftest_kernel(int gmax, int s_thr,
+                                                                  uint8_t* phase, uint8_t* mask) {
+    __shared__ PhaseEntry lut[8 * 34];
+    build_phase_lut(lut);
+    __syncthreads();
+    const int N = 2 * gmax + 1;
+    const long long n = (long long)N * N;
+    const float nthr = -((float)min(s_thr, 1 << 22) + 0.5f);
+    for (long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i < n;
+         i += 2ll * gridDim.x * blockDim.x) {
+        const long long j = i + 1 < n ? i + 1 : i;  // an odd count pairs the last with itself
+        const float gxa = (float)(int)(i % N - gmax), gya = (float)(int)(i / N - gmax);
+        const float gxb = (float)(int)(j % N - gmax), gyb = (float)(int)(j / N - gmax);
+        const uint32_t pp = phase_pair(phase_cand(gxa, gya, lut), phase_cand(gxb, gyb, lut));
+        const float2 mv = mask_value2(make_float2(gxa, gxb), make_float2(gya, gyb), nthr);
+        const uint32_t mb = ~sign_bytes2(mv.x, mv.y);  // 0xFF where the mask is true
+        phase[i] = (uint8_t)pp;
+        mask[i] = (uint8_t)mb;
+        if (j != i) {
+            phase[j] = (uint8_t)(pp >> 8);
+            mask[j] = (uint8_t)(mb >> 8);
+        }
+    }
+}
+
 }  // namespace
 
 int edge_mode(const EdgeParams& p) {
@@ -835,6 +866,12 @@ cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaSt
         case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, s);
         default: return launch_batch_mode<M_GENERAL>(d, grid, s);
     }
+}
+
+cudaError_t launch_edge_point_selftest(int gmax, int s_thr, uint8_t* phase, uint8_t* mask,
+                                       cudaStream_t s) {
+    edge_point_selftest_kernel<<<1216, 256, 0, s>>>(gmax, s_thr, phase, mask);
+    return cudaGetLastError();
 }
 
 int edge_batch_blocks_per_sm(int mode) {

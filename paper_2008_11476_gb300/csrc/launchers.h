@@ -30,6 +30,10 @@ int edge_single_rows(int W, int H, int num_sms);
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
 cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s);
 int edge_batch_blocks_per_sm(int mode);
+// the fused edge kernel's Phase and mask arithmetic over every gradient pair
+// in [-gmax, gmax]^2 ((2 gmax + 1)^2 bytes each, device memory)
+cudaError_t launch_edge_point_selftest(int gmax, int s_thr, uint8_t* phase, uint8_t* mask,
+                                       cudaStream_t s);
 
 cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
 cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);

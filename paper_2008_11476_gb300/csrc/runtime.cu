@@ -216,6 +216,15 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
     e.rows = edge_single_rows((int)G.W, (int)G.H, ctx->num_sms);
     if (const char* env = getenv("HVX_EDGE_ROWS")) {  // tuning knob: 2 .. EDGE_ROWS
         const int r = atoi(env);
+        static bool said = false;
+        if (!said) {
+            said = true;
+            if (r >= 2 && r <= EDGE_ROWS)
+                fprintf(stderr, "hvx: HVX_EDGE_ROWS=%d replaces the rows per thread of every "
+                                "single-image edge kernel\n", r);
+            else
+                fprintf(stderr, "hvx: HVX_EDGE_ROWS=%s ignored (not in 2..%d)\n", env, EDGE_ROWS);
+        }
         if (r >= 2 && r <= EDGE_ROWS) e.rows = r;
     }
     return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));

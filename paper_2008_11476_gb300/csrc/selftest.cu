@@ -5,6 +5,7 @@
 // HVX_ERROR_TIMEOUT.  No fault, trap or unbounded spin is involved.
 #include "device_common.cuh"
 #include "hvx_internal.h"
+#include "launchers.h"
 
 namespace hvx {
 namespace {
@@ -35,4 +36,24 @@ extern "C" hvx_status hvxSelfTestBoundedWait(hvx_context hc) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_status(e);
     return check_device_error(ctx);
+}
+
+extern "C" hvx_status hvxSelfTestEdgePoint(hvx_context hc, int32_t gmax, int32_t s_thr,
+                                           uint8_t* phase_out, uint8_t* mask_out) {
+    Context* ctx = reinterpret_cast<Context*>(hc);
+    if (!ctx || ctx->magic != kMagicContext) return HVX_ERROR_INVALID_REFERENCE;
+    if (ctx->plan_only) return HVX_ERROR_NOT_SUPPORTED;
+    if (gmax < 0 || gmax > 4096 || !phase_out || !mask_out) return HVX_ERROR_INVALID_PARAMETERS;
+    bind_device(ctx);
+    const size_t n = (size_t)(2 * gmax + 1) * (size_t)(2 * gmax + 1);
+    uint8_t* d = nullptr;
+    if (cudaMalloc(&d, 2 * n) != cudaSuccess) {
+        cudaGetLastError();
+        return HVX_ERROR_NO_MEMORY;
+    }
+    cudaError_t e = launch_edge_point_selftest(gmax, s_thr, d, d + n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(phase_out, d, n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mask_out, d + n, n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? HVX_SUCCESS : cuda_status(e);
 }

@@ -101,6 +101,7 @@ _SIGS = {
     "hvxReleaseContext": (I32, [PP]),
     "hvxSetContextMemoryBudget": (I32, [P, U64]),
     "hvxSelfTestBoundedWait": (I32, [P]),
+    "hvxSelfTestEdgePoint": (I32, [P, I32, I32, P, P]),
     "hvxGetContextMemoryUsage": (I32, [P, ctypes.POINTER(U64)]),
     "hvxCreateImage": (I32, [P, U32, U32, I32, PP]),
     "hvxCreateImageFromHandle": (I32, [P, U32, U32, I32, P, U64, PP]),
@@ -229,6 +230,18 @@ def hvxReleaseContext(ctx):
 def hvxSelfTestBoundedWait(ctx) -> int:
     """Status of the bounded-wait self-test (HVX_ERROR_TIMEOUT is the expected one)."""
     return lib().hvxSelfTestBoundedWait(ctx)
+
+
+def hvxSelfTestEdgePoint(ctx, gmax: int, s_thr: int):
+    """The fused edge kernel's Phase and mask bytes over every (gx, gy) in
+    [-gmax, gmax]^2, as two (2 gmax + 1) x (2 gmax + 1) arrays indexed [gy, gx]."""
+    import numpy as np
+    n = 2 * gmax + 1
+    ph = np.empty((n, n), np.uint8)
+    mk = np.empty((n, n), np.uint8)
+    _ck(lib().hvxSelfTestEdgePoint(ctx, gmax, s_thr, ph.ctypes.data, mk.ctypes.data),
+        "hvxSelfTestEdgePoint")
+    return ph, mk
 
 
 def hvxSetContextMemoryBudget(ctx, nbytes: int):

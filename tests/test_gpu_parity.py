@@ -184,6 +184,20 @@ def test_magnitude_phase_exhaustive(ctx):
     assert int((got != ref).sum()) == 0
 
 
+@pytest.mark.parametrize("thr", [0, 1, 100, 1000, 1442, 1443])
+def test_edge_kernel_point_ops_exhaustive(ctx, thr):
+    """The fused edge kernel's own Phase (octant guess, exact binary32 test,
+    paired byte select) and Magnitude -> Threshold (packed fma, sign bytes)
+    over every gradient pair (gx, gy) in [-1020, 1020]^2, bit-exact with the
+    oracle's Phase and Threshold(Magnitude) definitions."""
+    ph, mk = H.hvxSelfTestEdgePoint(ctx, 1020, thr * thr + thr)
+    v = np.arange(-1020, 1021, dtype=np.int16)
+    gx, gy = [np.ascontiguousarray(a) for a in np.meshgrid(v, v)]  # [gy, gx]
+    np.testing.assert_array_equal(mk, O.threshold(O.magnitude(gx, gy), thr).data)
+    if thr == 100:
+        np.testing.assert_array_equal(ph, O.phase(gx, gy).data)
+
+
 def test_threshold_all_s16_and_range(ctx):
     v = np.arange(-32768, 32768, dtype=np.int32).astype(np.int16).reshape(256, 256)
     a = PG.upload(ctx, v, H.HVX_DF_S16)
@@ -366,6 +380,9 @@ def test_tomasi_on_the_corner_kernel(ctx, w, h, border):
     assert (np.abs(r - ref) <= 2e-6 * np.abs(ref)).all()
     near = np.abs(ref - TOMASI_THR) <= 1e-5 * TOMASI_THR
     np.testing.assert_array_equal((mk == 255)[~near], (ref > TOMASI_THR)[~near])
+    # the mask is the kernel's own binary32 response compared with the
+    # threshold, everywhere (near the threshold too)
+    np.testing.assert_array_equal(mk == 255, r > np.float32(TOMASI_THR))
     # without the exported response the UNDEFINED kernel decides from a cheaper
     # estimate where that is safe: the same mask
     h_, w_ = img.shape
@@ -421,6 +438,7 @@ def test_tomasi_full_size_4096x2160(ctx):
     assert (np.abs(r - ref) <= 2e-6 * np.abs(ref)).all()
     near = np.abs(ref - TOMASI_THR) <= 1e-5 * TOMASI_THR
     np.testing.assert_array_equal((mk == 255)[~near], (ref > TOMASI_THR)[~near])
+    np.testing.assert_array_equal(mk == 255, r > np.float32(TOMASI_THR))
     inp = PG.upload(ctx, img, H.HVX_DF_U8)
     mk1 = PG.empty(ctx, 4096, 2160, H.HVX_DF_U8)
     g = PG.harris_graph(ctx, inp, mk1, None, thr=TOMASI_THR, tomasi=True)
