@@ -205,6 +205,19 @@ hvx_status hvxSelfTestBoundedWait(hvx_context ctx);
 hvx_status hvxSelfTestEdgePoint(hvx_context ctx, int32_t gmax, int32_t s_thr, uint8_t* phase_out,
                                 uint8_t* mask_out);
 
+/* Host-side fault injection for failure-path tests (process-wide, off by
+ * default; no device fault is ever made).  kind HVX_FAULT_DEVICE_ALLOC makes
+ * the n-th device allocation the library attempts from now on (images,
+ * materialised intermediates, result blocks; n >= 1) fail as if cudaMalloc
+ * had, so that call returns HVX_ERROR_NO_MEMORY; HVX_FAULT_LAUNCH makes the
+ * n-th graph launch from now on (hvxProcessGraph, hvxScheduleGraph, a server
+ * dispatch) fail with HVX_ERROR_DEVICE before anything is enqueued.  Each armed fault fires once.  HVX_FAULT_NONE (n ignored) disarms
+ * both.  Returns HVX_ERROR_INVALID_PARAMETERS for another kind or n < 1. */
+#define HVX_FAULT_NONE 0
+#define HVX_FAULT_DEVICE_ALLOC 1
+#define HVX_FAULT_LAUNCH 2
+hvx_status hvxTestInjectFault(int32_t kind, int64_t n);
+
 /* Cap the device bytes the context may allocate for images and plans
  * (0 = unlimited).  Allocations beyond it fail with HVX_ERROR_OVER_BUDGET. */
 hvx_status hvxSetContextMemoryBudget(hvx_context ctx, uint64_t bytes);
@@ -331,6 +344,17 @@ hvx_status hvxQueryGraph(hvx_graph g, int32_t attribute, void* out, uint64_t siz
  * after another.  Image sizes may differ.  Wait with hvxWaitBatch. */
 hvx_status hvxProcessGraphBatch(const hvx_graph* graphs, int32_t n, void* stream);
 hvx_status hvxWaitBatch(hvx_context ctx, void* stream);
+
+/* The launch that hvxProcessGraphBatch tuned for exactly this sequence of
+ * graphs (its first call times candidate tile heights per image-size class
+ * and persistent grids, and caches the fastest): for each
+ * graph, rows_out[i] = R, the rows per thread of the persistent edge kernel's
+ * tiles for that image (its tiles are 128 x 8R pixels; 0 where the batch runs
+ * another kernel, which keeps its own tile), and *grid_out = the persistent
+ * grid (CTAs; 0 for a direct launch).  rows_out holds n entries.
+ * HVX_ERROR_INVALID_PARAMETERS when no batch of these graphs has run since
+ * they were last verified. */
+hvx_status hvxQueryBatch(const hvx_graph* graphs, int32_t n, int32_t* rows_out, int32_t* grid_out);
 
 /* ------------------------------------------------------------------------ */
 /* Nodes.  Standard CV functions (Table 2).  Each returns NULL on failure.    */

@@ -1,6 +1,7 @@
 // C ABI of the image-graph library: handle checks, object ownership and the
 // node constructors (Section 3.1, Listing 1; Section 5.1, Listing 4).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -16,6 +17,21 @@ hvx_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return HVX_SUCCESS;
     if (e == cudaErrorMemoryAllocation) return HVX_ERROR_NO_MEMORY;
     return HVX_ERROR_DEVICE;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection: a countdown per kind; the call that brings it
+// from 1 to 0 fails.  0 = disarmed.
+namespace {
+std::atomic<int64_t> g_fault_count[3];
+}
+
+bool fault_fires(int kind) {
+    std::atomic<int64_t>& c = g_fault_count[kind];
+    int64_t v = c.load();
+    while (v > 0)
+        if (c.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -47,6 +63,7 @@ hvx_status DevicePool::alloc(uint64_t bytes, void** out) {
         cache_.erase(c);
     }
     void* p = nullptr;
+    if (fault_fires(HVX_FAULT_DEVICE_ALLOC)) return HVX_ERROR_NO_MEMORY;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -755,6 +772,23 @@ hvx_status hvxProcessGraphBatch(const hvx_graph* gs, int32_t n, void* stream) {
     return process_batch(v[0]->ctx, v.data(), n, reinterpret_cast<cudaStream_t>(stream));
 }
 
+hvx_status hvxQueryBatch(const hvx_graph* gs, int32_t n, int32_t* rows_out, int32_t* grid_out) {
+    if (!gs || n <= 0 || !rows_out || !grid_out) return HVX_ERROR_INVALID_PARAMETERS;
+    std::vector<Graph*> v;
+    for (int i = 0; i < n; ++i) {
+        if (!ok_graph(gs[i])) return HVX_ERROR_INVALID_REFERENCE;
+        if (G(gs[i])->ctx != G(gs[0])->ctx) return HVX_ERROR_INVALID_REFERENCE;
+        v.push_back(G(gs[i]));
+    }
+    std::vector<int> rows(n);
+    int grid = 0;
+    hvx_status st = query_batch(v[0]->ctx, v.data(), n, rows.data(), &grid);
+    if (st != HVX_SUCCESS) return st;
+    for (int i = 0; i < n; ++i) rows_out[i] = rows[i];
+    *grid_out = grid;
+    return HVX_SUCCESS;
+}
+
 hvx_status hvxWaitBatch(hvx_context ctx, void* stream) {
     if (!ok_ctx(ctx)) return HVX_ERROR_INVALID_REFERENCE;
     if (C(ctx)->plan_only) return HVX_ERROR_NOT_SUPPORTED;
@@ -1145,3 +1179,14 @@ hvx_status hvxGetNodeResult(hvx_node hn, void* out, uint64_t size) {
 }
 
 }  // extern "C"
+
+extern "C" hvx_status hvxTestInjectFault(int32_t kind, int64_t n) {
+    if (kind == HVX_FAULT_NONE) {
+        for (auto& c : g_fault_count) c.store(0);
+        return HVX_SUCCESS;
+    }
+    if ((kind != HVX_FAULT_DEVICE_ALLOC && kind != HVX_FAULT_LAUNCH) || n < 1)
+        return HVX_ERROR_INVALID_PARAMETERS;
+    g_fault_count[kind].store(n);
+    return HVX_SUCCESS;
+}

@@ -42,6 +42,10 @@ Rect rect_intersect(const Rect& a, const Rect& b);
 // handed out again; the budget counts bytes held by live blocks plus cached
 // ones, and cached blocks are returned to the driver before an allocation is
 // refused.
+// Host-side fault injection (hvxTestInjectFault): true when the armed fault of
+// this kind fires on this call.
+bool fault_fires(int kind);
+
 class DevicePool {
   public:
     explicit DevicePool(uint64_t budget = 0) : budget_(budget) {}
@@ -310,6 +314,11 @@ hvx_status check_device_error(Context* ctx);
 hvx_status ensure_context_device_state(Context* ctx);
 void destroy_batch_cache(Context* ctx);
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s);
+// The tuned launch of a cached batch of exactly these graphs: rows per thread
+// of each image's tiles (0 where the kernel has its own tile) and the
+// persistent grid (0 for a direct launch).  HVX_ERROR_INVALID_PARAMETERS when
+// no such batch has run.
+hvx_status query_batch(Context* ctx, Graph* const* gs, int n, int* rows, int* grid);
 
 // user-defined operators (user_expr.cpp): check an expression and rewrite it
 // for the code generator

@@ -87,7 +87,7 @@ struct EdgeSmem {
     // than the box ring (tile k uses slot k mod (NS + 1), so the slot that
     // tile k + NS fills belongs to tile k - 1, which is finished)
     EdgeParams prm[NS + 1];
-    int tx0[NS + 1], ty0[NS + 1];
+    int tx0[NS + 1], ty0[NS + 1], trows[NS + 1];
     PhaseEntry plut[8 * 34];            // Phase table (build_phase_lut)
     uint32_t gslow[EDGE_THREADS][5];    // per-thread result of the slow G path
     // batch of at most BATCH_SMEM_IMAGES images: its tile tables
@@ -693,29 +693,34 @@ __global__ void __launch_bounds__(EDGE_THREADS)
     edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, rows);
 }
 
-// Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
-// its image's parameter block into slot ps and the TMA load of its box into
-// stage s, both completing on the stage's barrier (so the issuing thread never
-// waits on global memory).  `tab`: the tile tables are in shared memory.
+// Thread 0: the origin and rows per thread of batch tile t into slot ps, then
+// one bulk copy of its image's parameter block into slot ps and the TMA load
+// of its box into stage s, both completing on the stage's barrier (so the
+// issuing thread never waits on global memory).  `tab`: the tile tables are in
+// shared memory.  An image's tiles are 128 x 8R with R = its tile-table entry
+// >> 16 (the autotuner's choice; 0 means ROWS), its box 160 x (8R + 4).
 __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, bool tab,
                                            int s, int ps, int t) {
-    int img, t0, tiles_x;
+    int img, t0, txr;
     if (tab) {
         img = find_image_smem(sm.ts, d.n_img, t);
         t0 = sm.ts[img];
-        tiles_x = sm.tx[img];
+        txr = sm.tx[img];
     } else {
         img = find_image(d.tile_start, d.n_img, t);
         t0 = __ldg(d.tile_start + img);
-        tiles_x = __ldg(d.tiles_x + img);
+        txr = __ldg(d.tiles_x + img);
     }
+    const int tiles_x = txr & 0xFFFF, rows = (txr >> 16) ? (txr >> 16) : ROWS;
     const int local = t - t0, ty = local / tiles_x;
-    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * TH;
+    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * 8 * rows;
     sm.tx0[ps] = x0;
     sm.ty0[ps] = y0;
+    sm.trows[ps] = rows;
     tensormap_acquire(&d.maps[img]);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&sm.bar[s], BOX_BYTES + (uint32_t)sizeof(EdgeParams));
+    mbar_arrive_expect_tx(&sm.bar[s],
+                          (uint32_t)(LW * (8 * rows + 4)) + (uint32_t)sizeof(EdgeParams));
     bulk_copy_g2s(&sm.prm[ps], &d.params[img], (uint32_t)sizeof(EdgeParams), &sm.bar[s]);
     tma_load_2d(&sm.in[s].b[0][0], &d.maps[img], &sm.bar[s], x0 - 16, y0 - 2);
 }
@@ -762,13 +767,14 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
             return;
         }
         const EdgeParams& p = sm.prm[ps];
-        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
-        const bool interior = tile_is_interior(p, x0, y0);
+        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps], rows = sm.trows[ps];
+        const bool interior = tile_is_interior(p, x0, y0, 8 * rows);
         if (!interior) {
-            fix_input_border(sm.in[s].b, p, x0, y0);
+            fix_input_border(sm.in[s].b, p, x0, y0, 8 * rows + 4);
             __syncthreads();
         }
-        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow);
+        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow,
+                        rows);
         __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
         if (threadIdx.x == 0) {
             const int tn = t + STAGES * (int)gridDim.x;

@@ -13,7 +13,8 @@ struct EdgeBatchDesc {
     const CUtensorMap* maps;     // one per image, 64-byte aligned, in device memory
     const EdgeParams* params;    // one per image, in device memory
     const int* tile_start;       // n_img + 1 prefix sums of per-image tile counts
-    const int* tiles_x;          // n_img tile columns per image (the kernel's tile width)
+    const int* tiles_x;          // n_img tile columns per image (the kernel's tile width);
+                                 // edge modes: | rows per thread << 16 (0: the default)
     int n_img;
     int total_tiles;
     int* err;

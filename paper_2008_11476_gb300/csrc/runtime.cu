@@ -694,6 +694,7 @@ hvx_status prepare_launches(Graph* g) {
 }
 
 hvx_status launch_plan(Graph* g, cudaStream_t s) {
+    if (fault_fires(HVX_FAULT_LAUNCH)) return HVX_ERROR_DEVICE;  // injected, nothing enqueued
     bind_device(g->ctx);
     for (Group& G : g->plan.groups) {
         NvtxRange nvtx(G.jit_on ? "hvx launch generated" : group_kernel_name(G.kernel));
@@ -731,6 +732,7 @@ struct BatchEntry {
     int n = 0, total_tiles = 0;
     bool harris = false;  // BORDER_UNDEFINED corner batch: one direct launch
     bool tomasi = false;  // ... of the Shi-Tomasi kernel
+    std::vector<int> rows;  // edge batch: rows per thread of each image's tiles
 };
 
 struct BatchCache {
@@ -800,8 +802,12 @@ int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode
     return best;
 }
 
-hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
-                             cudaStream_t user_stream, BatchEntry& out) {
+// Device tables of one edge / Gaussian batch: per image its tensor map, its
+// parameter block and its tile counts, for the rows per thread `rows` gives
+// (edge modes: tiles of 128 x 8R and boxes of 160 x (8R + 4); the Gaussian
+// kernel keeps its own tile).  One device block; *d describes it.
+hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode,
+                            const std::vector<int>& rows, void** dmem_out, EdgeBatchDesc* d) {
     const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
     const size_t params_off = maps_bytes;
     const size_t tiles_off = params_off + (size_t)n * sizeof(EdgeParams);
@@ -813,20 +819,26 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     edge_tile_dims(mode, &tw, &th);
     for (int i = 0; i < n; ++i) {
         const Group& G = gs[i]->plan.groups[0];
+        EdgeParams ep = G.edge;
+        int r = EDGE_ROWS;
         if (mode == EDGE_MODE_GAUSS) {
             std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap,
                         sizeof(CUtensorMap));
-        } else {  // the batch kernel's box: EDGE_TH rows and the halo
+        } else {  // the batch kernel's box: 8R rows and the halo
+            r = rows[i];
+            th = 8 * r;
+            ep.rows = r;
             CUtensorMap map;
-            hvx_status st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, EDGE_LOAD_H);
+            hvx_status st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, (uint32_t)(th + 4));
             if (st != HVX_SUCCESS) return st;
             std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &map, sizeof(map));
         }
-        std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &G.edge,
-                    sizeof(EdgeParams));
-        tiles_x[i] = (int)((G.W + tw - 1) / tw);
-        int tiles = tiles_x[i] * (int)((G.H + th - 1) / th);
-        tile_start[i + 1] = tile_start[i] + tiles;
+        std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &ep, sizeof(ep));
+        const int tx = (int)((G.W + tw - 1) / tw);
+        tiles_x[i] = mode == EDGE_MODE_GAUSS ? tx : (tx | (r << 16));
+        const long long t = (long long)tile_start[i] + (long long)tx * ((G.H + th - 1) / th);
+        if (t > (1ll << 30)) return HVX_ERROR_NOT_SUPPORTED;
+        tile_start[i + 1] = (int)t;
     }
     std::memcpy(host.data() + tiles_off, tile_start.data(), (n + 1) * sizeof(int));
     std::memcpy(host.data() + tx_off, tiles_x.data(), n * sizeof(int));
@@ -841,21 +853,117 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
         cudaFree(dmem);
         return cuda_status(e);
     }
-    EdgeBatchDesc d;
-    d.maps = static_cast<const CUtensorMap*>(dmem);
-    d.params = reinterpret_cast<const EdgeParams*>(static_cast<uint8_t*>(dmem) + params_off);
-    d.tile_start = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tiles_off);
-    d.tiles_x = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tx_off);
-    d.n_img = n;
-    d.total_tiles = tile_start[n];
-    d.err = ctx->d_error;
-    if (!bc->capture) {
-        e = cudaStreamCreateWithFlags(&bc->capture, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            cudaFree(dmem);
-            return cuda_status(e);
+    d->maps = static_cast<const CUtensorMap*>(dmem);
+    d->params = reinterpret_cast<const EdgeParams*>(static_cast<uint8_t*>(dmem) + params_off);
+    d->tile_start = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tiles_off);
+    d->tiles_x = reinterpret_cast<const int*>(static_cast<uint8_t*>(dmem) + tx_off);
+    d->n_img = n;
+    d->total_tiles = tile_start[n];
+    d->err = ctx->d_error;
+    *dmem_out = dmem;
+    return HVX_SUCCESS;
+}
+
+// Size classes of the tile-shape tuner, by image height: under 480 rows,
+// under 1080 rows, and the rest.
+int shape_class(uint32_t H) { return H < 480 ? 0 : H < 1080 ? 1 : 2; }
+
+// Milliseconds of one launch of the batch `d` (one warm-up, the mean of two)
+// on the internal stream, or a huge value when it could not be timed.
+float time_edge_batch(BatchCache* bc, const EdgeBatchDesc& d, int mode, int grid) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = 1e30f;
+    if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+        launch_edge_batch(d, mode, grid, bc->capture);
+        cudaEventRecord(a, bc->capture);
+        launch_edge_batch(d, mode, grid, bc->capture);
+        launch_edge_batch(d, mode, grid, bc->capture);
+        cudaEventRecord(b, bc->capture);
+        float t = 0;
+        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess)
+            ms = t / 2;
+    }
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return ms;
+}
+
+// Tile shape per size class (edge modes): starting from 128 x 120 tiles
+// (R = 15 rows per thread) for every image, each class present in the batch
+// tries R = 10 and R = 5 (tiles of 128 x 80 and 128 x 40) with the others
+// fixed, keeping a shape that is at least 2 % faster (shorter tiles waste
+// fewer rows on ragged image heights and spread small images over more SMs;
+// taller ones recompute fewer halo rows).  The trials run on the internal
+// stream after the caller's stream has drained, at the occupancy-limit grid;
+// the batch's work is idempotent, so they are harmless.  HVX_AUTOTUNE=0 or
+// =grid in the environment keeps 128 x 120 for every image; HVX_BATCH_ROWS=R
+// (5, 10 or 15) gives every image 128 x 8R tiles without trials.
+std::vector<int> autotune_shapes(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
+                                 cudaStream_t s) {
+    std::vector<int> rows(n, EDGE_ROWS);
+    if (mode == EDGE_MODE_GAUSS) return rows;
+    if (const char* fixed = std::getenv("HVX_BATCH_ROWS")) {  // test / tuning knob: 5, 10, 15
+        const int r = std::atoi(fixed);
+        static bool said = false;
+        if (!said) {
+            said = true;
+            std::fprintf(stderr, "hvx: HVX_BATCH_ROWS=%s %s\n", fixed,
+                         (r == 5 || r == 10 || r == 15)
+                             ? "fixes the rows per thread of every batched edge tile"
+                             : "ignored (not 5, 10 or 15)");
+        }
+        if (r == 5 || r == 10 || r == 15) return std::vector<int>(n, r);
+    }
+    const char* env = std::getenv("HVX_AUTOTUNE");
+    if (env && (env[0] == '0' || std::strcmp(env, "grid") == 0)) return rows;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return rows;
+    }
+    bool present[3] = {false, false, false};
+    for (int i = 0; i < n; ++i) present[shape_class(gs[i]->plan.groups[0].H)] = true;
+    const int grid_max = ctx->num_sms * std::max(1, edge_batch_blocks_per_sm(mode));
+    auto trial = [&](const std::vector<int>& r) {
+        void* dm = nullptr;
+        EdgeBatchDesc d;
+        if (make_edge_tables(ctx, gs, n, mode, r, &dm, &d) != HVX_SUCCESS) return 1e30f;
+        const float ms = time_edge_batch(bc, d, mode, std::min(d.total_tiles, grid_max));
+        cudaFree(dm);
+        return ms;
+    };
+    float best = trial(rows);
+    for (int k = 0; k < 3; ++k) {
+        if (!present[k]) continue;
+        for (int r : {10, 5}) {
+            std::vector<int> cand = rows;
+            for (int i = 0; i < n; ++i)
+                if (shape_class(gs[i]->plan.groups[0].H) == k) cand[i] = r;
+            const float ms = trial(cand);
+            if (std::getenv("HVX_AUTOTUNE_VERBOSE"))
+                std::fprintf(stderr, "hvx autotune: class %d rows %d: %.4f ms (best %.4f)\n", k, r,
+                             ms, best);
+            if (ms < 0.98f * best) {
+                best = ms;
+                rows = cand;
+            }
         }
     }
+    return rows;
+}
+
+hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
+                             cudaStream_t user_stream, BatchEntry& out) {
+    cudaError_t e;
+    if (!bc->capture) {
+        e = cudaStreamCreateWithFlags(&bc->capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const std::vector<int> rows = autotune_shapes(ctx, bc, gs, n, mode, user_stream);
+    void* dmem = nullptr;
+    EdgeBatchDesc d;
+    hvx_status tst = make_edge_tables(ctx, gs, n, mode, rows, &dmem, &d);
+    if (tst != HVX_SUCCESS) return tst;
     const int grid = autotune_grid(ctx, bc, d, mode, user_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bc->capture, cudaStreamCaptureModeThreadLocal);
@@ -878,6 +986,7 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     out.dmem = dmem;
     out.exec = exec;
     out.grid = grid;
+    out.rows = rows;
     return HVX_SUCCESS;
 }
 
@@ -975,6 +1084,22 @@ hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, Batch
     out.n = n;
     out.total_tiles = tile_start[n];
     return HVX_SUCCESS;
+}
+
+hvx_status query_batch(Context* ctx, Graph* const* gs, int n, int* rows, int* grid) {
+    std::lock_guard<std::mutex> lock(ctx->batch_mu);
+    if (!ctx->batch) return HVX_ERROR_INVALID_PARAMETERS;
+    for (const BatchEntry& e : ctx->batch->entries) {
+        if ((int)e.graphs.size() != n) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i)
+            same = e.graphs[i] == gs[i] && e.plan_ids[i] == gs[i]->plan_id;
+        if (!same) continue;
+        for (int i = 0; i < n; ++i) rows[i] = (int)e.rows.size() == n ? e.rows[i] : 0;
+        *grid = e.grid;
+        return HVX_SUCCESS;
+    }
+    return HVX_ERROR_INVALID_PARAMETERS;
 }
 
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) {

@@ -102,6 +102,7 @@ _SIGS = {
     "hvxSetContextMemoryBudget": (I32, [P, U64]),
     "hvxSelfTestBoundedWait": (I32, [P]),
     "hvxSelfTestEdgePoint": (I32, [P, I32, I32, P, P]),
+    "hvxTestInjectFault": (I32, [I32, ctypes.c_int64]),
     "hvxGetContextMemoryUsage": (I32, [P, ctypes.POINTER(U64)]),
     "hvxCreateImage": (I32, [P, U32, U32, I32, PP]),
     "hvxCreateImageFromHandle": (I32, [P, U32, U32, I32, P, U64, PP]),
@@ -163,6 +164,7 @@ _SIGS = {
     "hvxCreateServer": (I32, [P, U64, I32, I32, PP]),
     "hvxServerSubmit": (I32, [P, P, ctypes.POINTER(U64)]),
     "hvxServerSubmitMany": (I32, [P, P, I32, ctypes.POINTER(U64)]),
+    "hvxQueryBatch": (I32, [P, I32, P, ctypes.POINTER(I32)]),
     "hvxServerWait": (I32, [P, U64, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
     "hvxServerStats": (I32, [P, ctypes.POINTER(hvx_server_stats)]),
     "hvxServerResetStats": (I32, [P]),
@@ -242,6 +244,16 @@ def hvxSelfTestEdgePoint(ctx, gmax: int, s_thr: int):
     _ck(lib().hvxSelfTestEdgePoint(ctx, gmax, s_thr, ph.ctypes.data, mk.ctypes.data),
         "hvxSelfTestEdgePoint")
     return ph, mk
+
+
+HVX_FAULT_NONE, HVX_FAULT_DEVICE_ALLOC, HVX_FAULT_LAUNCH = 0, 1, 2
+
+
+def hvxTestInjectFault(kind: int, n: int = 1):
+    """Arm a host-side fault: the n-th device allocation (HVX_FAULT_DEVICE_ALLOC)
+    or graph launch (HVX_FAULT_LAUNCH) from now on fails once; HVX_FAULT_NONE
+    disarms both."""
+    _ck(lib().hvxTestInjectFault(kind, n), "hvxTestInjectFault")
 
 
 def hvxSetContextMemoryBudget(ctx, nbytes: int):
@@ -378,6 +390,17 @@ def hvxProcessGraphBatch(graphs, stream: int = 0):
     arr = (ctypes.c_void_p * len(graphs))(*[g.value if isinstance(g, ctypes.c_void_p) else g
                                             for g in graphs])
     _ck(lib().hvxProcessGraphBatch(arr, len(graphs), stream), "hvxProcessGraphBatch")
+
+
+def hvxQueryBatch(graphs):
+    """(rows per thread of each image's tiles, persistent grid) of the cached
+    batch launch of exactly these graphs."""
+    n = len(graphs)
+    arr = (ctypes.c_void_p * n)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
+    rows = (I32 * n)()
+    grid = I32()
+    _ck(lib().hvxQueryBatch(arr, n, rows, ctypes.byref(grid)), "hvxQueryBatch")
+    return [rows[i] for i in range(n)], grid.value
 
 
 def hvxWaitBatch(ctx, stream: int = 0):

@@ -491,3 +491,14 @@ def test_user_defined_operator_checks(pctx):
     H.hvxCopyNode(g, a, H.hvxCreateImage(pctx, 64, 48, H.HVX_DF_U8))
     with pytest.raises(H.HvxError):
         H.hvxVerifyGraph(g)
+
+
+def test_fault_injection_arguments():
+    """hvxTestInjectFault accepts the two fault kinds with n >= 1 and
+    HVX_FAULT_NONE; anything else is refused (no GPU needed)."""
+    from paper_2008_11476_gb300 import hvx as H
+    L = H.lib()
+    assert L.hvxTestInjectFault(H.HVX_FAULT_DEVICE_ALLOC, 0) == H.HVX_ERROR_INVALID_PARAMETERS
+    assert L.hvxTestInjectFault(7, 1) == H.HVX_ERROR_INVALID_PARAMETERS
+    assert L.hvxTestInjectFault(H.HVX_FAULT_LAUNCH, 5) == H.HVX_SUCCESS
+    assert L.hvxTestInjectFault(H.HVX_FAULT_NONE, 0) == H.HVX_SUCCESS

@@ -44,6 +44,58 @@ def test_batch_uneven_sizes_matches_oracle(ctx):
             np.testing.assert_array_equal(PG.download(ph), rp)
 
 
+@pytest.mark.parametrize("rows", [5, 10, 15])
+@pytest.mark.parametrize("border", [H.HVX_BORDER_REPLICATE, H.HVX_BORDER_CONSTANT,
+                                    H.HVX_BORDER_UNDEFINED])
+def test_batch_every_tile_height(monkeypatch, rows, border):
+    """The persistent edge kernel with 128 x 8R tiles for each R the tuner can
+    choose, on uneven sizes (ragged tiles in both directions) and every
+    border: exact against the oracle."""
+    monkeypatch.setenv("HVX_BATCH_ROWS", str(rows))
+    c = H.hvxCreateContext()
+    try:
+        sizes = synth.batch_sizes(6, seed=40 + rows, wlo=1, whi=600, hlo=1, hhi=300)
+        sizes += [(1, 1), (640, 481), (130, 41)]
+        items = []
+        for i, (w, h) in enumerate(sizes):
+            img = synth.rects_noise(w, h, seed=500 + i)
+            inp = PG.upload(c, img, H.HVX_DF_U8)
+            ph, mk = PG.empty(c, w, h, H.HVX_DF_U8), PG.empty(c, w, h, H.HVX_DF_U8)
+            items.append((img, PG.edge_graph(c, inp, ph, mk, border=border, cval=9), ph, mk))
+        graphs = [it[1] for it in items]
+        H.hvxProcessGraphBatch(graphs)
+        H.hvxWaitBatch(c)
+        got_rows, grid = H.hvxQueryBatch(graphs)
+        assert got_rows == [rows] * len(items) and grid > 0
+        B = {H.HVX_BORDER_REPLICATE: O.BORDER_REPLICATE, H.HVX_BORDER_CONSTANT: O.BORDER_CONSTANT,
+             H.HVX_BORDER_UNDEFINED: O.BORDER_UNDEFINED}[border]
+        for img, g, ph, mk in items:
+            rp, rm = O.edge_graph(img, B, 9)
+            np.testing.assert_array_equal(PG.download(mk), rm)
+            np.testing.assert_array_equal(PG.download(ph), rp)
+    finally:
+        H.hvxReleaseContext(c)
+
+
+def test_batch_shape_tuner_choice_is_exact(ctx):
+    """The tuner's own choice (per size class, by timed trials) on a batch with
+    all three classes: one R of 5 / 10 / 15 per class, exact results."""
+    sizes = [(700, 300), (500, 200), (900, 700), (640, 1000), (1920, 1080), (1500, 1300)]
+    items = _edge_set(ctx, sizes, 90)
+    graphs = [it[1] for it in items]
+    H.hvxProcessGraphBatch(graphs)
+    H.hvxWaitBatch(ctx)
+    rows, grid = H.hvxQueryBatch(graphs)
+    cls = [0 if h < 480 else 1 if h < 1080 else 2 for _, h in sizes]
+    for k in set(cls):
+        assert len({r for r, c in zip(rows, cls) if c == k}) == 1
+    assert set(rows) <= {5, 10, 15} and grid > 0
+    for img, g, ph, mk in items:
+        rp, rm = O.edge_graph(img)
+        np.testing.assert_array_equal(PG.download(mk), rm)
+        np.testing.assert_array_equal(PG.download(ph), rp)
+
+
 def test_batch_gaussian_only(ctx):
     sizes = [(33, 7), (640, 480), (129, 300)]
     outs = []
