@@ -965,8 +965,10 @@ def measure_batch256(world, rank, local, torch, cpu, steps=10, warmup=3):
          "batched_over_unfused": round(value / unf, 2),
          "first_call_s": round(t_build, 3),
          "autotuned": {"tile_by_size_class": by_class, "grid": tuned_grid,
-                       "note": "first call times 128x120 / 128x80 / 128x40 tiles per image-"
-                               "height class, then 1..4 CTAs per SM, and keeps the fastest"},
+                       "note": "first call times each image-height class in its own launch "
+                               "with 128x120 / 128x80 / 128x40 tiles, then the per-class "
+                               "launches against one launch of every image at 128x120 (split "
+                               "kept only if 2% faster), then 1..4 CTAs per SM"},
          "fixed_shape_128x120": {"value": round(replica_mpix_s(mpix * 1e6, world, steps,
                                                                t_fixed), 1),
                                  "unit": "Mpix/s", "ms_per_step": round(t_fixed / steps * 1e3, 4),

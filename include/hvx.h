@@ -351,7 +351,9 @@ hvx_status hvxWaitBatch(hvx_context ctx, void* stream);
  * graph, rows_out[i] = R, the rows per thread of the persistent edge kernel's
  * tiles for that image (its tiles are 128 x 8R pixels; 0 where the batch runs
  * another kernel, which keeps its own tile), and *grid_out = the persistent
- * grid (CTAs; 0 for a direct launch).  rows_out holds n entries.
+ * grid of its first launch (CTAs; 0 for a direct launch; a batch whose
+ * size classes got different tile heights runs one launch per class, all
+ * replayed from one captured CUDA graph).  rows_out holds n entries.
  * HVX_ERROR_INVALID_PARAMETERS when no batch of these graphs has run since
  * they were last verified. */
 hvx_status hvxQueryBatch(const hvx_graph* graphs, int32_t n, int32_t* rows_out, int32_t* grid_out);

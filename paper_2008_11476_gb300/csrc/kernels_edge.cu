@@ -87,7 +87,7 @@ struct EdgeSmem {
     // than the box ring (tile k uses slot k mod (NS + 1), so the slot that
     // tile k + NS fills belongs to tile k - 1, which is finished)
     EdgeParams prm[NS + 1];
-    int tx0[NS + 1], ty0[NS + 1], trows[NS + 1];
+    int tx0[NS + 1], ty0[NS + 1];
     PhaseEntry plut[8 * 34];            // Phase table (build_phase_lut)
     uint32_t gslow[EDGE_THREADS][5];    // per-thread result of the slow G path
     // batch of at most BATCH_SMEM_IMAGES images: its tile tables
@@ -693,34 +693,31 @@ __global__ void __launch_bounds__(EDGE_THREADS)
     edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, rows);
 }
 
-// Thread 0: the origin and rows per thread of batch tile t into slot ps, then
-// one bulk copy of its image's parameter block into slot ps and the TMA load
-// of its box into stage s, both completing on the stage's barrier (so the
-// issuing thread never waits on global memory).  `tab`: the tile tables are in
-// shared memory.  An image's tiles are 128 x 8R with R = its tile-table entry
-// >> 16 (the autotuner's choice; 0 means ROWS), its box 160 x (8R + 4).
+// Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
+// its image's parameter block into slot ps and the TMA load of its box into
+// stage s, both completing on the stage's barrier (so the issuing thread never
+// waits on global memory).  `tab`: the tile tables are in shared memory.
+// Tiles are 128 x 8R, boxes 160 x (8R + 4).
+template <int R>
 __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatchDesc& d, bool tab,
                                            int s, int ps, int t) {
-    int img, t0, txr;
+    int img, t0, tiles_x;
     if (tab) {
         img = find_image_smem(sm.ts, d.n_img, t);
         t0 = sm.ts[img];
-        txr = sm.tx[img];
+        tiles_x = sm.tx[img];
     } else {
         img = find_image(d.tile_start, d.n_img, t);
         t0 = __ldg(d.tile_start + img);
-        txr = __ldg(d.tiles_x + img);
+        tiles_x = __ldg(d.tiles_x + img);
     }
-    const int tiles_x = txr & 0xFFFF, rows = (txr >> 16) ? (txr >> 16) : ROWS;
     const int local = t - t0, ty = local / tiles_x;
-    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * 8 * rows;
+    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * 8 * R;
     sm.tx0[ps] = x0;
     sm.ty0[ps] = y0;
-    sm.trows[ps] = rows;
     tensormap_acquire(&d.maps[img]);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&sm.bar[s],
-                          (uint32_t)(LW * (8 * rows + 4)) + (uint32_t)sizeof(EdgeParams));
+    mbar_arrive_expect_tx(&sm.bar[s], (uint32_t)(LW * (8 * R + 4)) + (uint32_t)sizeof(EdgeParams));
     bulk_copy_g2s(&sm.prm[ps], &d.params[img], (uint32_t)sizeof(EdgeParams), &sm.bar[s]);
     tma_load_2d(&sm.in[s].b[0][0], &d.maps[img], &sm.bar[s], x0 - 16, y0 - 2);
 }
@@ -729,9 +726,13 @@ __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatch
 // CTA lives in box stage k mod STAGES, so the next box loads while one is
 // computed.  Each tile's parameters come from shared memory.  A wait that
 // runs out (bounded, about a second) records the error and ends the CTA,
-// after thread 0 has waited (bounded) for the copies still in flight.
-template <int MODE>
+// after thread 0 has waited (bounded) for the copies still in flight.  R:
+// output rows per thread (tiles of 128 x 8R; a compile-time constant, so the
+// row loop's bounds and box offsets fold; the autotuner picks one per image
+// size class and launches each class with its own R).
+template <int MODE, int R>
 __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatchDesc d) {
+    static_assert(R >= 3 && R <= ROWS, "box ring holds at most 8 ROWS + 4 rows");
     __shared__ EdgeSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
@@ -750,7 +751,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
     if (threadIdx.x == 0)
         for (int s = 0; s < STAGES; ++s) {
             const int t = first + s * (int)gridDim.x;
-            if (t < d.total_tiles) issue_tile(sm, d, tab, s, s, t);
+            if (t < d.total_tiles) issue_tile<R>(sm, d, tab, s, s, t);
         }
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
@@ -767,18 +768,17 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
             return;
         }
         const EdgeParams& p = sm.prm[ps];
-        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps], rows = sm.trows[ps];
-        const bool interior = tile_is_interior(p, x0, y0, 8 * rows);
+        const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
+        const bool interior = tile_is_interior(p, x0, y0, 8 * R);
         if (!interior) {
-            fix_input_border(sm.in[s].b, p, x0, y0, 8 * rows + 4);
+            fix_input_border(sm.in[s].b, p, x0, y0, 8 * R + 4);
             __syncthreads();
         }
-        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow,
-                        rows);
+        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, R);
         __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
         if (threadIdx.x == 0) {
             const int tn = t + STAGES * (int)gridDim.x;
-            if (tn < d.total_tiles) issue_tile(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
+            if (tn < d.total_tiles) issue_tile<R>(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
         }
     }
 }
@@ -792,8 +792,12 @@ cudaError_t launch_mode(const CUtensorMap& map, const EdgeParams& p, cudaStream_
 }
 
 template <int MODE>
-cudaError_t launch_batch_mode(const EdgeBatchDesc& d, int grid, cudaStream_t s) {
-    edge_batch_kernel<MODE><<<grid, EDGE_THREADS, 0, s>>>(d);
+cudaError_t launch_batch_mode(const EdgeBatchDesc& d, int grid, int rows, cudaStream_t s) {
+    switch (rows) {
+        case 5: edge_batch_kernel<MODE, 5><<<grid, EDGE_THREADS, 0, s>>>(d); break;
+        case 10: edge_batch_kernel<MODE, 10><<<grid, EDGE_THREADS, 0, s>>>(d); break;
+        default: edge_batch_kernel<MODE, ROWS><<<grid, EDGE_THREADS, 0, s>>>(d); break;
+    }
     return cudaGetLastError();
 }
 
@@ -864,13 +868,14 @@ cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_
     }
 }
 
-cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s) {
+cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s,
+                              int rows) {
     switch (mode) {
         case M_GAUSS: return launch_gauss_batch(d, grid, s);
-        case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, s);
-        case M_MASK: return launch_batch_mode<M_MASK>(d, grid, s);
-        case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, s);
-        default: return launch_batch_mode<M_GENERAL>(d, grid, s);
+        case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, rows, s);
+        case M_MASK: return launch_batch_mode<M_MASK>(d, grid, rows, s);
+        case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, rows, s);
+        default: return launch_batch_mode<M_GENERAL>(d, grid, rows, s);
     }
 }
 
@@ -883,7 +888,7 @@ cudaError_t launch_edge_point_selftest(int gmax, int s_thr, uint8_t* phase, uint
 int edge_batch_blocks_per_sm(int mode) {
     if (mode == M_GAUSS) return gauss_batch_blocks_per_sm();
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel<M_MASK_PHASE>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel<M_MASK_PHASE, ROWS>,
                                                   EDGE_THREADS, 0);
     return n;
 }

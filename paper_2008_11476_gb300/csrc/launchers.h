@@ -13,8 +13,7 @@ struct EdgeBatchDesc {
     const CUtensorMap* maps;     // one per image, 64-byte aligned, in device memory
     const EdgeParams* params;    // one per image, in device memory
     const int* tile_start;       // n_img + 1 prefix sums of per-image tile counts
-    const int* tiles_x;          // n_img tile columns per image (the kernel's tile width);
-                                 // edge modes: | rows per thread << 16 (0: the default)
+    const int* tiles_x;          // n_img tile columns per image (the kernel's tile width)
     int n_img;
     int total_tiles;
     int* err;
@@ -29,7 +28,10 @@ void edge_tile_dims(int mode, int* tw, int* th);
 // output rows per thread of the single-image edge kernel for a W x H image
 int edge_single_rows(int W, int H, int num_sms);
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
-cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s);
+// rows: output rows per thread of the edge kernel's 128 x 8R tiles, R = 5,
+// 10 or EDGE_ROWS (15, the default); the Gaussian kernel keeps its own tile
+cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaStream_t s,
+                              int rows = EDGE_ROWS);
 int edge_batch_blocks_per_sm(int mode);
 // the fused edge kernel's Phase and mask arithmetic over every gradient pair
 // in [-gmax, gmax]^2 ((2 gmax + 1)^2 bytes each, device memory)

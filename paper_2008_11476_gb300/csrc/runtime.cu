@@ -733,6 +733,7 @@ struct BatchEntry {
     bool harris = false;  // BORDER_UNDEFINED corner batch: one direct launch
     bool tomasi = false;  // ... of the Shi-Tomasi kernel
     std::vector<int> rows;  // edge batch: rows per thread of each image's tiles
+    std::vector<void*> more_dmem;  // edge batch split by size class: the other tables
 };
 
 struct BatchCache {
@@ -747,6 +748,7 @@ void destroy_batch_cache(Context* ctx) {
     for (BatchEntry& e : bc->entries) {
         if (e.exec) cudaGraphExecDestroy(e.exec);
         if (e.dmem) cudaFree(e.dmem);
+        for (void* p : e.more_dmem) cudaFree(p);
     }
     if (bc->capture) cudaStreamDestroy(bc->capture);
     delete bc;
@@ -762,7 +764,8 @@ namespace {
 // rewritten with the same value), so the trial runs are harmless.
 // HVX_AUTOTUNE=0 in the environment skips the trials and takes the
 // occupancy limit.
-int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode, cudaStream_t s) {
+int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode, cudaStream_t s,
+                  int rows = EDGE_ROWS) {
     const int per_sm_max = std::max(1, edge_batch_blocks_per_sm(mode));
     int best = std::min(d.total_tiles, ctx->num_sms * per_sm_max);
     const char* env = std::getenv("HVX_AUTOTUNE");
@@ -780,10 +783,10 @@ int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode
     float best_ms = 1e30f;
     for (int per = 1; per <= per_sm_max; ++per) {
         int grid = std::min(d.total_tiles, ctx->num_sms * per);
-        launch_edge_batch(d, mode, grid, bc->capture);  // warm-up
+        launch_edge_batch(d, mode, grid, bc->capture, rows);  // warm-up
         cudaEventRecord(a, bc->capture);
-        launch_edge_batch(d, mode, grid, bc->capture);
-        launch_edge_batch(d, mode, grid, bc->capture);
+        launch_edge_batch(d, mode, grid, bc->capture, rows);
+        launch_edge_batch(d, mode, grid, bc->capture, rows);
         cudaEventRecord(b, bc->capture);
         float ms = 0;
         if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess &&
@@ -802,12 +805,12 @@ int autotune_grid(Context* ctx, BatchCache* bc, const EdgeBatchDesc& d, int mode
     return best;
 }
 
-// Device tables of one edge / Gaussian batch: per image its tensor map, its
-// parameter block and its tile counts, for the rows per thread `rows` gives
-// (edge modes: tiles of 128 x 8R and boxes of 160 x (8R + 4); the Gaussian
-// kernel keeps its own tile).  One device block; *d describes it.
-hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode,
-                            const std::vector<int>& rows, void** dmem_out, EdgeBatchDesc* d) {
+// Device tables of one edge / Gaussian launch: per image its tensor map, its
+// parameter block and its tile counts, for `rows` rows per thread (edge
+// modes: tiles of 128 x 8R and boxes of 160 x (8R + 4); the Gaussian kernel
+// keeps its own tile).  One device block; *d describes it.
+hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode, int rows,
+                            void** dmem_out, EdgeBatchDesc* d) {
     const size_t maps_bytes = (size_t)n * sizeof(CUtensorMap);
     const size_t params_off = maps_bytes;
     const size_t tiles_off = params_off + (size_t)n * sizeof(EdgeParams);
@@ -817,26 +820,23 @@ hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode,
     std::vector<int> tile_start(n + 1, 0), tiles_x(n, 0);
     int tw = 0, th = 0;
     edge_tile_dims(mode, &tw, &th);
+    if (mode != EDGE_MODE_GAUSS) th = 8 * rows;
     for (int i = 0; i < n; ++i) {
         const Group& G = gs[i]->plan.groups[0];
         EdgeParams ep = G.edge;
-        int r = EDGE_ROWS;
         if (mode == EDGE_MODE_GAUSS) {
             std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap,
                         sizeof(CUtensorMap));
         } else {  // the batch kernel's box: 8R rows and the halo
-            r = rows[i];
-            th = 8 * r;
-            ep.rows = r;
+            ep.rows = rows;
             CUtensorMap map;
             hvx_status st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, (uint32_t)(th + 4));
             if (st != HVX_SUCCESS) return st;
             std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &map, sizeof(map));
         }
         std::memcpy(host.data() + params_off + (size_t)i * sizeof(EdgeParams), &ep, sizeof(ep));
-        const int tx = (int)((G.W + tw - 1) / tw);
-        tiles_x[i] = mode == EDGE_MODE_GAUSS ? tx : (tx | (r << 16));
-        const long long t = (long long)tile_start[i] + (long long)tx * ((G.H + th - 1) / th);
+        tiles_x[i] = (int)((G.W + tw - 1) / tw);
+        const long long t = (long long)tile_start[i] + (long long)tiles_x[i] * ((G.H + th - 1) / th);
         if (t > (1ll << 30)) return HVX_ERROR_NOT_SUPPORTED;
         tile_start[i + 1] = (int)t;
     }
@@ -868,16 +868,22 @@ hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode,
 // under 1080 rows, and the rest.
 int shape_class(uint32_t H) { return H < 480 ? 0 : H < 1080 ? 1 : 2; }
 
-// Milliseconds of one launch of the batch `d` (one warm-up, the mean of two)
-// on the internal stream, or a huge value when it could not be timed.
-float time_edge_batch(BatchCache* bc, const EdgeBatchDesc& d, int mode, int grid) {
+// Milliseconds of a sequence of launches (one warm-up, the mean of two) on
+// the internal stream, or a huge value when it could not be timed.
+struct EdgeLaunch {
+    EdgeBatchDesc d;
+    int rows = EDGE_ROWS;
+    int grid = 0;
+};
+
+float time_launches(BatchCache* bc, const std::vector<EdgeLaunch>& ls, int mode) {
     cudaEvent_t a = nullptr, b = nullptr;
     float ms = 1e30f;
     if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
-        launch_edge_batch(d, mode, grid, bc->capture);
+        for (const EdgeLaunch& l : ls) launch_edge_batch(l.d, mode, l.grid, bc->capture, l.rows);
         cudaEventRecord(a, bc->capture);
-        launch_edge_batch(d, mode, grid, bc->capture);
-        launch_edge_batch(d, mode, grid, bc->capture);
+        for (int rep = 0; rep < 2; ++rep)
+            for (const EdgeLaunch& l : ls) launch_edge_batch(l.d, mode, l.grid, bc->capture, l.rows);
         cudaEventRecord(b, bc->capture);
         float t = 0;
         if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess)
@@ -889,69 +895,18 @@ float time_edge_batch(BatchCache* bc, const EdgeBatchDesc& d, int mode, int grid
     return ms;
 }
 
-// Tile shape per size class (edge modes): starting from 128 x 120 tiles
-// (R = 15 rows per thread) for every image, each class present in the batch
-// tries R = 10 and R = 5 (tiles of 128 x 80 and 128 x 40) with the others
-// fixed, keeping a shape that is at least 2 % faster (shorter tiles waste
-// fewer rows on ragged image heights and spread small images over more SMs;
-// taller ones recompute fewer halo rows).  The trials run on the internal
-// stream after the caller's stream has drained, at the occupancy-limit grid;
-// the batch's work is idempotent, so they are harmless.  HVX_AUTOTUNE=0 or
-// =grid in the environment keeps 128 x 120 for every image; HVX_BATCH_ROWS=R
-// (5, 10 or 15) gives every image 128 x 8R tiles without trials.
-std::vector<int> autotune_shapes(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
-                                 cudaStream_t s) {
-    std::vector<int> rows(n, EDGE_ROWS);
-    if (mode == EDGE_MODE_GAUSS) return rows;
-    if (const char* fixed = std::getenv("HVX_BATCH_ROWS")) {  // test / tuning knob: 5, 10, 15
-        const int r = std::atoi(fixed);
-        static bool said = false;
-        if (!said) {
-            said = true;
-            std::fprintf(stderr, "hvx: HVX_BATCH_ROWS=%s %s\n", fixed,
-                         (r == 5 || r == 10 || r == 15)
-                             ? "fixes the rows per thread of every batched edge tile"
-                             : "ignored (not 5, 10 or 15)");
-        }
-        if (r == 5 || r == 10 || r == 15) return std::vector<int>(n, r);
-    }
-    const char* env = std::getenv("HVX_AUTOTUNE");
-    if (env && (env[0] == '0' || std::strcmp(env, "grid") == 0)) return rows;
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return rows;
-    }
-    bool present[3] = {false, false, false};
-    for (int i = 0; i < n; ++i) present[shape_class(gs[i]->plan.groups[0].H)] = true;
-    const int grid_max = ctx->num_sms * std::max(1, edge_batch_blocks_per_sm(mode));
-    auto trial = [&](const std::vector<int>& r) {
-        void* dm = nullptr;
-        EdgeBatchDesc d;
-        if (make_edge_tables(ctx, gs, n, mode, r, &dm, &d) != HVX_SUCCESS) return 1e30f;
-        const float ms = time_edge_batch(bc, d, mode, std::min(d.total_tiles, grid_max));
-        cudaFree(dm);
-        return ms;
-    };
-    float best = trial(rows);
-    for (int k = 0; k < 3; ++k) {
-        if (!present[k]) continue;
-        for (int r : {10, 5}) {
-            std::vector<int> cand = rows;
-            for (int i = 0; i < n; ++i)
-                if (shape_class(gs[i]->plan.groups[0].H) == k) cand[i] = r;
-            const float ms = trial(cand);
-            if (std::getenv("HVX_AUTOTUNE_VERBOSE"))
-                std::fprintf(stderr, "hvx autotune: class %d rows %d: %.4f ms (best %.4f)\n", k, r,
-                             ms, best);
-            if (ms < 0.98f * best) {
-                best = ms;
-                rows = cand;
-            }
-        }
-    }
-    return rows;
-}
-
+// One edge batch signature, tuned: either every image in one persistent
+// launch with 128 x 120 tiles (R = 15 rows per thread), or one launch per
+// image size class, each class with its own tile height.  The tuner times,
+// for each class present, its own launch with R = 15, 10 and 5 (128 x 120 /
+// 80 / 40 tiles: shorter tiles waste fewer rows on ragged heights and spread
+// small images over more SMs, taller ones recompute fewer halo rows), then
+// the whole split sequence against the single launch, keeping the split only
+// when it is at least 2 % faster; then the persistent grid of each launch
+// (autotune_grid).  The trials run on the internal stream after the caller's
+// stream has drained; the batch's work is idempotent, so they are harmless.
+// HVX_AUTOTUNE=0 or =grid keeps the single launch; HVX_BATCH_ROWS=R (5, 10,
+// 15) gives every image 128 x 8R tiles in a single launch, without trials.
 hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int n, int mode,
                              cudaStream_t user_stream, BatchEntry& out) {
     cudaError_t e;
@@ -959,16 +914,109 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
         e = cudaStreamCreateWithFlags(&bc->capture, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    const std::vector<int> rows = autotune_shapes(ctx, bc, gs, n, mode, user_stream);
-    void* dmem = nullptr;
-    EdgeBatchDesc d;
-    hvx_status tst = make_edge_tables(ctx, gs, n, mode, rows, &dmem, &d);
-    if (tst != HVX_SUCCESS) return tst;
-    const int grid = autotune_grid(ctx, bc, d, mode, user_stream);
+    const int grid_max = ctx->num_sms * std::max(1, edge_batch_blocks_per_sm(mode));
+    std::vector<void*> blocks;
+    auto release = [&] {
+        for (void* p : blocks) cudaFree(p);
+        blocks.clear();
+    };
+    // launches for a partition of the batch: parts[k] = image indices, rows[k]
+    auto build = [&](const std::vector<std::vector<int>>& parts, const std::vector<int>& rows,
+                     std::vector<EdgeLaunch>& ls) -> hvx_status {
+        ls.clear();
+        for (size_t k = 0; k < parts.size(); ++k) {
+            std::vector<Graph*> sub;
+            for (int i : parts[k]) sub.push_back(gs[i]);
+            EdgeLaunch l;
+            l.rows = rows[k];
+            void* dm = nullptr;
+            hvx_status st = make_edge_tables(ctx, sub.data(), (int)sub.size(), mode, l.rows, &dm,
+                                             &l.d);
+            if (st != HVX_SUCCESS) return st;
+            blocks.push_back(dm);
+            l.grid = std::min(l.d.total_tiles, grid_max);
+            ls.push_back(l);
+        }
+        return HVX_SUCCESS;
+    };
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    std::vector<std::vector<int>> parts = {all};
+    std::vector<int> rows = {EDGE_ROWS};
+    const char* env = std::getenv("HVX_AUTOTUNE");
+    const char* fixed = std::getenv("HVX_BATCH_ROWS");
+    const int fr = fixed ? std::atoi(fixed) : 0;
+    if (fixed) {  // test / tuning knob
+        static bool said = false;
+        if (!said) {
+            said = true;
+            std::fprintf(stderr, "hvx: HVX_BATCH_ROWS=%s %s\n", fixed,
+                         (fr == 5 || fr == 10 || fr == 15)
+                             ? "fixes the rows per thread of every batched edge tile"
+                             : "ignored (not 5, 10 or 15)");
+        }
+    }
+    const bool verbose = std::getenv("HVX_AUTOTUNE_VERBOSE") != nullptr;
+    if (mode != EDGE_MODE_GAUSS && (fr == 5 || fr == 10 || fr == 15)) {
+        rows[0] = fr;
+    } else if (mode != EDGE_MODE_GAUSS &&
+               !(env && (env[0] == '0' || std::strcmp(env, "grid") == 0))) {
+        std::vector<std::vector<int>> cls(3);
+        for (int i = 0; i < n; ++i) cls[shape_class(gs[i]->plan.groups[0].H)].push_back(i);
+        std::vector<std::vector<int>> split;
+        for (auto& c : cls)
+            if (!c.empty()) split.push_back(c);
+        if (cudaStreamSynchronize(user_stream) == cudaSuccess) {
+            std::vector<EdgeLaunch> ls;
+            float t_single = 1e30f;
+            if (build(parts, rows, ls) == HVX_SUCCESS) t_single = time_launches(bc, ls, mode);
+            release();
+            std::vector<int> split_rows;
+            for (auto& part : split) {
+                int best_r = EDGE_ROWS;
+                float best = 1e30f;
+                for (int r : {EDGE_ROWS, 10, 5}) {
+                    float ms = 1e30f;
+                    if (build({part}, {r}, ls) == HVX_SUCCESS) ms = time_launches(bc, ls, mode);
+                    release();
+                    if (verbose)
+                        std::fprintf(stderr, "hvx autotune: class of %zu images, rows %d: %.4f ms\n",
+                                     part.size(), r, ms);
+                    if (ms < best) {
+                        best = ms;
+                        best_r = r;
+                    }
+                }
+                split_rows.push_back(best_r);
+            }
+            float t_split = 1e30f;
+            if (build(split, split_rows, ls) == HVX_SUCCESS) t_split = time_launches(bc, ls, mode);
+            release();
+            if (verbose)
+                std::fprintf(stderr, "hvx autotune: one launch %.4f ms, per-class launches %.4f ms\n",
+                             t_single, t_split);
+            if (t_split < 0.98f * t_single) {
+                parts = split;
+                rows = split_rows;
+            }
+        }
+        cudaGetLastError();
+    }
+    std::vector<EdgeLaunch> ls;
+    hvx_status st = build(parts, rows, ls);
+    if (st != HVX_SUCCESS) {
+        release();
+        return st;
+    }
+    for (EdgeLaunch& l : ls) l.grid = autotune_grid(ctx, bc, l.d, mode, user_stream, l.rows);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bc->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_edge_batch(d, mode, grid, bc->capture);
+        cudaError_t le = cudaSuccess;
+        for (const EdgeLaunch& l : ls) {
+            cudaError_t x = launch_edge_batch(l.d, mode, l.grid, bc->capture, l.rows);
+            if (le == cudaSuccess) le = x;
+        }
         e = cudaStreamEndCapture(bc->capture, &graph);
         if (le != cudaSuccess) e = le;
     }
@@ -977,16 +1025,20 @@ hvx_status build_batch_entry(Context* ctx, BatchCache* bc, Graph* const* gs, int
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(dmem);
+        release();
         return cuda_status(e);
     }
     out.graphs.assign(gs, gs + n);
     out.plan_ids.resize(n);
     for (int i = 0; i < n; ++i) out.plan_ids[i] = gs[i]->plan_id;
-    out.dmem = dmem;
+    out.dmem = blocks[0];
+    out.more_dmem.assign(blocks.begin() + 1, blocks.end());
     out.exec = exec;
-    out.grid = grid;
-    out.rows = rows;
+    out.grid = ls[0].grid;
+    out.rows.assign(n, mode == EDGE_MODE_GAUSS ? 0 : EDGE_ROWS);
+    if (mode != EDGE_MODE_GAUSS)
+        for (size_t k = 0; k < parts.size(); ++k)
+            for (int i : parts[k]) out.rows[i] = rows[k];
     return HVX_SUCCESS;
 }
 
@@ -1167,6 +1219,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             cudaStreamSynchronize(s);
             if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
             if (oldest->dmem) cudaFree(oldest->dmem);
+            for (void* p : oldest->more_dmem) cudaFree(p);
             bc->entries.erase(oldest);
         }
         BatchEntry fresh;
