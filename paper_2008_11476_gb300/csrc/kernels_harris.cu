@@ -388,8 +388,10 @@ __device__ __forceinline__ bool tomasi_above(int a, int b, int c, float T) {
 // a 4-fold margin (tests/test_harris_decision.py replays the procedure).
 // Inputs: 0 <= a, b < 2^25, |c| < 2^25.  qtf = q_thr in binary32, qtb =
 // 2^-21 |qtf|.
-__device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, float kdf, float qtf,
-                                             float qtb, int kn, int kd, long long q_thr) {
+// The binary32 estimate d of q - q_thr and the bound it must exceed in
+// magnitude to decide the sign (below); pairs with the exact fallback.
+__device__ __forceinline__ void harris_estimate(int a, int b, int c, float knf, float kdf,
+                                                float qtf, float qtb, float* d, float* bound) {
     const float A = __int2float_rn(a), B = __int2float_rn(b), C = __int2float_rn(c);
     const float P = __fmul_rn(A, B);
     const float D = fmaf(-C, C, P);
@@ -397,8 +399,14 @@ __device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, flo
     const float V = __fmul_rn(knf, __fmul_rn(S, S));
     const float Q = fmaf(kdf, D, -V);
     const float M = fmaf(kdf, fmaf(C, C, P), V);
-    const float bound = fmaf(0x1p-19f, M, qtb);
-    const float d = __fsub_rn(Q, qtf);
+    *bound = fmaf(0x1p-19f, M, qtb);
+    *d = __fsub_rn(Q, qtf);
+}
+
+__device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, float kdf, float qtf,
+                                             float qtb, int kn, int kd, long long q_thr) {
+    float d, bound;
+    harris_estimate(a, b, c, knf, kdf, qtf, qtb, &d, &bound);
     if (fabsf(d) > bound) return d > 0.0f;
     return harris_q32(a, b, c, kn, kd) > q_thr;
 }
@@ -482,7 +490,58 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
             R[k][0] = __shfl_down_sync(0xffffffffu, S[k][0], 1);
             R[k][1] = __shfl_down_sync(0xffffffffu, S[k][1], 1);
         }
-        if (producer && y < H) {
+        if (!TOMASI && !rrow && producer && y < H) {
+            // the mask alone (the benchmark's form): every pixel's estimate
+            // first, the exact test only in the rare row where one is too close
+            int ha[8], hb[8], hc[8];
+            int h0 = L[0][0] + L[0][1] + S[0][0] + S[0][1] + S[0][2];
+            int h1 = L[1][0] + L[1][1] + S[1][0] + S[1][1] + S[1][2];
+            int h2 = L[2][0] + L[2][1] + S[2][0] + S[2][1] + S[2][2];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j > 0) {
+                    h0 += (j + 2 < 8 ? S[0][j + 2] : R[0][j - 6]) - (j - 3 >= 0 ? S[0][j - 3] : L[0][j - 1]);
+                    h1 += (j + 2 < 8 ? S[1][j + 2] : R[1][j - 6]) - (j - 3 >= 0 ? S[1][j - 3] : L[1][j - 1]);
+                    h2 += (j + 2 < 8 ? S[2][j + 2] : R[2][j - 6]) - (j - 3 >= 0 ? S[2][j - 3] : L[2][j - 1]);
+                }
+                ha[j] = h0;
+                hb[j] = h1;
+                hc[j] = h2;
+            }
+            float dv[8];
+            bool sure = true;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float bound;
+                harris_estimate(ha[j], hb[j], hc[j], knf, kdf, qtf, qtb, &dv[j], &bound);
+                sure = sure && fabsf(dv[j]) > bound;
+                dv[j] = fabsf(dv[j]) > bound ? dv[j] : 0.0f;  // 0: decide exactly
+            }
+            uint32_t hit = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) hit |= (dv[j] > 0.0f ? 1u : 0u) << j;
+            if (!sure) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (dv[j] == 0.0f && harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr)
+                        hit |= 1u << j;
+            }
+            uint32_t mk[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool ok = full || in_rect(p.valid, xs + j, y);
+                mk[j] = ok ? (((hit >> j) & 1u) ? (uint32_t)p.tv : (uint32_t)p.fv) & 0xFFu : 0u;
+            }
+            if (mrow) {
+                if (xs + 8 <= W) {
+                    *reinterpret_cast<uint2*>(mrow + xs) =
+                        make_uint2(mk[0] | (mk[1] << 8) | (mk[2] << 16) | (mk[3] << 24),
+                                   mk[4] | (mk[5] << 8) | (mk[6] << 16) | (mk[7] << 24));
+                } else {
+                    for (int j = 0; j < 8 && xs + j < W; ++j) mrow[xs + j] = (uint8_t)mk[j];
+                }
+            }
+        } else if (producer && y < H) {
             uint32_t mk[8];
             float rv[8];
             int h[3];
