@@ -526,19 +526,29 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                     if (dv[j] == 0.0f && harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr)
                         hit |= 1u << j;
             }
-            uint32_t mk[8];
+            // decision bits -> bytes: x * 0x00204081 puts bit k of a 4-bit x
+            // at bit 8k (copies at offsets 0, 7, 14, 21 never overlap), times
+            // 255 gives 0xFF where the mask is true, then true / false values
+            const uint32_t fx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
+            const uint32_t fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
+            uint32_t w0 = ((((hit & 15u) * 0x00204081u) & 0x01010101u) * 255u & fx) ^ fvx;
+            uint32_t w1 = ((((hit >> 4) * 0x00204081u) & 0x01010101u) * 255u & fx) ^ fvx;
+            if (!full) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bool ok = full || in_rect(p.valid, xs + j, y);
-                mk[j] = ok ? (((hit >> j) & 1u) ? (uint32_t)p.tv : (uint32_t)p.fv) & 0xFFu : 0u;
+                for (int j = 0; j < 8; ++j)
+                    if (!in_rect(p.valid, xs + j, y)) {
+                        if (j < 4)
+                            w0 &= ~(0xFFu << (8 * j));
+                        else
+                            w1 &= ~(0xFFu << (8 * (j - 4)));
+                    }
             }
             if (mrow) {
                 if (xs + 8 <= W) {
-                    *reinterpret_cast<uint2*>(mrow + xs) =
-                        make_uint2(mk[0] | (mk[1] << 8) | (mk[2] << 16) | (mk[3] << 24),
-                                   mk[4] | (mk[5] << 8) | (mk[6] << 16) | (mk[7] << 24));
+                    *reinterpret_cast<uint2*>(mrow + xs) = make_uint2(w0, w1);
                 } else {
-                    for (int j = 0; j < 8 && xs + j < W; ++j) mrow[xs + j] = (uint8_t)mk[j];
+                    for (int j = 0; j < 8 && xs + j < W; ++j)
+                        mrow[xs + j] = (uint8_t)((j < 4 ? w0 : w1) >> (8 * (j & 3)));
                 }
             }
         } else if (producer && y < H) {
