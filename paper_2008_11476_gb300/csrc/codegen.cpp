@@ -24,6 +24,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -205,7 +206,12 @@ struct Emitter {
     int smem_words = 0;
     std::ostringstream o;
 
-    Emitter(const GenericDesc& desc, const std::vector<std::string>& u) : d(desc), user(u) {}
+    Emitter(const GenericDesc& desc, const std::vector<std::string>& u) : d(desc), user(u) {
+        const char* env = std::getenv("HVX_CODEGEN_TMA");
+        tma = !(env && env[0] == '0');
+    }
+    bool tma = true;                 // stage U8 inputs of interior tiles by TMA
+    std::vector<int> load_bar;       // per pass: word offset of its mbarrier, or -1
 
     static bool is_local(int op) {
         return op == OP_GAUSS || op == OP_BOX || op == OP_SOBEL_X || op == OP_SOBEL_Y ||
@@ -249,9 +255,23 @@ struct Emitter {
     bool byte_slot(int b) const {
         return b < d.n_buf && staged[b] && d.buf[b].fmt == HVX_DF_U8;
     }
-    int align4(int b) const { return (d.buf[b].halo + 3) & ~3; }
-    int slot_w(int b) const { return byte_slot(b) ? tw + 2 * align4(b) : bw(b); }
-    int slot_x(int b) const { return byte_slot(b) ? align4(b) - d.buf[b].halo : 0; }
+    // A staged U8 external input of an interior tile arrives as one TMA box:
+    // its slot rows start at image x = x0 - A with A the halo rounded up to 16
+    // (the box's x must be a multiple of 16 bytes), and the slot's row pitch
+    // is the box width.  Used for halos of 2 or more: on the Section 6
+    // applications it measured 2-4 % faster there (Gauss 5x5, FChain,
+    // EdgFig2) and 3-6 % slower on halo-1 groups (Sobel, SobelX, Unsharp),
+    // whose per-thread loads are fewer.
+    bool tma_slot(int b) const {
+        return tma && byte_slot(b) && ext_in[b] >= 0 && d.in[ext_in[b]].fmt == HVX_DF_U8 &&
+               d.buf[b].halo >= 2;
+    }
+    int align_x(int b) const {
+        const int h = d.buf[b].halo;
+        return tma_slot(b) ? (h + 15) & ~15 : (h + 3) & ~3;
+    }
+    int slot_w(int b) const { return byte_slot(b) ? tw + 2 * align_x(b) : bw(b); }
+    int slot_x(int b) const { return byte_slot(b) ? align_x(b) - d.buf[b].halo : 0; }
     int slot_words(int s) const {
         const int n = slot[s].w * slot[s].h;
         return byte_slot(s) ? ((n / 4 + 3) & ~3) : ((n + 3) & ~3);  // 16-byte aligned
@@ -780,6 +800,37 @@ struct Emitter {
         return s < d.n_buf ? "B" + std::to_string(s) : "R" + std::to_string(s - d.n_buf);
     }
 
+    // Interior tiles: the staged U8 external inputs of a load pass as TMA
+    // boxes on one mbarrier (thread 0 initialises and issues; every thread
+    // waits, boundedly).  GMAP: the tensor maps are in global memory (the
+    // batched entry point) and are acquired before use.
+    void emit_tma_load(const std::vector<int>& T, int bar_words) {
+        int bytes = 0;
+        for (int b : T) bytes += slot_w(b) * bh(b);
+        o << "  if (!CHECK) {  // TMA boxes of the staged U8 inputs\n"
+          << "    unsigned long long* const bar = (unsigned long long*)(smem + " << bar_words
+          << ");\n"
+          << "    if (threadIdx.x == 0) hvx_mbar_init(bar);\n"
+          << "    __syncthreads();\n"
+          << "    if (threadIdx.x == 0) {\n"
+          << "      hvx_expect_tx(bar, " << bytes << "u);\n";
+        for (int b : T) {
+            const int e = ext_in[b];
+            o << "      if (GMAP) hvx_tmap_acquire(&p.tmap[" << e << "]);\n"
+              << "      hvx_tma_2d(B" << b << ", &p.tmap[" << e << "], bar, x0 - " << align_x(b)
+              << ", y0 - " << d.buf[b].halo << ");\n";
+        }
+        o << "    }\n    hvx_mbar_wait(bar, p.err);\n  }\n";
+    }
+
+    // Box of the TMA-staged input e: (e, width, height); none without TMA.
+    std::vector<std::array<int, 3>> tma_boxes() const {
+        std::vector<std::array<int, 3>> v;
+        for (int b = 0; b < d.n_buf; ++b)
+            if (tma_slot(b)) v.push_back({ext_in[b], slot_w(b), bh(b)});
+        return v;
+    }
+
     // All loads of a staged external input are independent: both loops are
     // unrolled so that they are all in flight at once.
     void emit_load(int b) {
@@ -787,10 +838,26 @@ struct Emitter {
         const std::string ld = "hvx_ld<" + std::to_string(d.in[e].fmt) + ">(p.in[" +
                                std::to_string(e) + "], p.in_pitch[" + std::to_string(e) + "], ";
         o << "  // external input " << e << " -> B" << b << " (halo " << h << ")\n";
+        if (tma_slot(b)) {  // interior tiles: the TMA box (emit_tma_load)
+            o << "  if (CHECK) {\n";
+            open_cells(bh(b), bw(b), h, h, true);
+            o << "      int v;\n"
+              << "      if (x >= 0 && x < p.W && y >= 0 && y < p.H) v = " << ld << "x, y);\n"
+              << "      else v = "
+              << (d.buf[b].fill == FILL_MIRROR || d.buf[b].fill == FILL_REPEAT
+                      ? ld + fill_coords(b)
+                      : fill_expr(b, ld + fill_coords(b)))
+              << ";\n"
+              << "      B" << b << "[r * " << slot_w(b) << " + c + " << slot_x(b)
+              << "] = (unsigned char)v;\n";
+            close_cells();
+            o << "  }\n";
+            return;
+        }
         if (byte_slot(b)) {
             // interior tiles: the region's rows are inside the image, and the
             // words [x0 - A, x0 + tw + A) stay inside each row's pitch
-            const int A = align4(b), words = slot_w(b) / 4, rows = bh(b);
+            const int A = align_x(b), words = slot_w(b) / 4, rows = bh(b);
             o << "  if (!CHECK) {\n"
               << "    const unsigned char* const g0 = (const unsigned char*)p.in[" << e
               << "] + (unsigned long long)(y0 - " << h << ") * p.in_pitch[" << e << "] + (x0 - " << A
@@ -1259,6 +1326,17 @@ struct Emitter {
             if ((d.buf[b].fill == FILL_MIRROR || d.buf[b].fill == FILL_REPEAT) && ext_in[b] < 0)
                 return false;
         if (!plan() || !choose_tile()) return false;
+        // one mbarrier (2 words, kept 16-byte aligned) per load pass with TMA boxes
+        load_bar.assign(passes.size(), -1);
+        for (size_t i = 0; i < passes.size(); ++i) {
+            if (passes[i].kind != LOAD) continue;
+            for (int b : passes[i].targets)
+                if (tma_slot(b)) load_bar[i] = 0;
+            if (load_bar[i] == 0) {
+                load_bar[i] = smem_words;
+                smem_words += 4;
+            }
+        }
         o << "// generated kernel: " << d.n_stage << " ops, " << d.n_buf << " images, tile " << tw
           << " x " << th << ", " << passes.size() << " passes, " << smem_words * 4
           << " bytes of shared memory\n"
@@ -1292,7 +1370,43 @@ struct Emitter {
           << "  if (F == " << HVX_DF_U8 << ") row[x] = (unsigned char)v;\n"
           << "  else if (F == " << HVX_DF_S16 << ") ((short*)row)[x] = (short)v;\n"
           << "  else ((int*)row)[x] = v;\n}\n\n"
-          << "template <bool CHECK>\n"
+          << "__device__ __forceinline__ unsigned hvx_smem(const void* q) {\n"
+          << "  return (unsigned)__cvta_generic_to_shared(q);\n}\n"
+          << "__device__ __forceinline__ void hvx_mbar_init(unsigned long long* bar) {\n"
+          << "  asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: \"r\"(hvx_smem(bar)) "
+             ": \"memory\");\n"
+          << "  asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n}\n"
+          << "__device__ __forceinline__ void hvx_expect_tx(unsigned long long* bar, unsigned n) {\n"
+          << "  asm volatile(\"mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\" :: "
+             "\"r\"(hvx_smem(bar)), \"r\"(n) : \"memory\");\n}\n"
+          << "__device__ __forceinline__ void hvx_tmap_acquire(const void* m) {\n"
+          << "  asm volatile(\"fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\" :: "
+             "\"l\"(m) : \"memory\");\n}\n"
+          << "// 2-D tiled TMA load; x * 1 byte is a multiple of 16 (the emitter's slots)\n"
+          << "__device__ __forceinline__ void hvx_tma_2d(void* dst, const void* map, "
+             "unsigned long long* bar, int x, int y) {\n"
+          << "  asm volatile(\"cp.async.bulk.tensor.2d.shared::cluster.global.tile."
+             "mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\" :: \"r\"(hvx_smem(dst)), "
+             "\"l\"((unsigned long long)map), \"r\"(hvx_smem(bar)), \"r\"(x), \"r\"(y) : "
+             "\"memory\");\n}\n"
+          << "__device__ __forceinline__ bool hvx_mbar_try(unsigned long long* bar) {\n"
+          << "  unsigned ok;\n"
+          << "  asm volatile(\"{\\n\\t.reg .pred q;\\n\\tmbarrier.try_wait.parity.shared::cta.b64 "
+             "q, [%1], 0;\\n\\tselp.u32 %0, 1, 0, q;\\n\\t}\" : \"=r\"(ok) : "
+             "\"r\"(hvx_smem(bar)) : \"memory\");\n"
+          << "  return ok != 0;\n}\n"
+          << "// phase 0 of bar, for at most ~2^31 cycles: on time-out record the error\n"
+          << "// and wait once more with the same bound (a late copy must not land\n"
+          << "// after the tile moved on)\n"
+          << "__device__ __forceinline__ void hvx_mbar_wait(unsigned long long* bar, int* err) {\n"
+          << "  const long long c0 = clock64();\n"
+          << "  while (!hvx_mbar_try(bar)) {\n"
+          << "    if (clock64() - c0 > (1ll << 31)) {\n"
+          << "      if (err) atomicCAS(err, 0, 1);\n"
+          << "      const long long c1 = clock64();\n"
+          << "      while (!hvx_mbar_try(bar) && clock64() - c1 < (1ll << 31)) {}\n"
+          << "      return;\n    }\n  }\n}\n\n"
+          << "template <bool CHECK, bool GMAP>\n"
           << "__device__ __forceinline__ void hvx_tile(const HvxJitParams& p, int* smem, int x0, "
              "int y0) {\n"
           << "  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
@@ -1318,12 +1432,18 @@ struct Emitter {
                   << ");  // "
                   << slot[s].w << " x " << slot[s].h << ", passes " << slot[s].def << ".."
                   << slot[s].last << "\n";
-        for (const Pass& p : passes) {
+        for (size_t pi = 0; pi < passes.size(); ++pi) {
+            const Pass& p = passes[pi];
             switch (p.kind) {
-                case LOAD:
+                case LOAD: {
+                    std::vector<int> T;
+                    for (int b : p.targets)
+                        if (tma_slot(b)) T.push_back(b);
+                    if (!T.empty()) emit_tma_load(T, load_bar[pi]);
                     for (int b : p.targets) emit_load(b);
                     o << "  __syncthreads();\n";
                     break;
+                }
                 case ROW:
                     for (int k : p.targets) emit_row(k);
                     o << "  __syncthreads();\n";
@@ -1358,13 +1478,13 @@ struct Emitter {
         o << head << regs << body;
         o << "}\n\n"
           << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << min_blocks()
-          << ") hvx_generated(const HvxJitParams p) {\n"
+          << ") hvx_generated(const __grid_constant__ HvxJitParams p) {\n"
           << "  extern __shared__ __align__(16) int smem[];\n"
           << "  const int tx = blockIdx.x, ty = blockIdx.y;\n"
           << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
-          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "    hvx_tile<false, false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "  else\n"
-          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "    hvx_tile<true, false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "}\n\n"
           << "// n images in one launch: block t is tile t - tile_start[i] of the last\n"
           << "// image i with tile_start[i] <= t\n"
@@ -1383,9 +1503,9 @@ struct Emitter {
           << tw << ";\n"
           << "  const int ty = local / gx, tx = local - ty * gx;\n"
           << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
-          << "    hvx_tile<false>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "    hvx_tile<false, true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "  else\n"
-          << "    hvx_tile<true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
+          << "    hvx_tile<true, true>(p, smem, tx * " << tw << ", ty * " << th << ");\n"
           << "}\n";
         return true;
     }
@@ -1539,6 +1659,18 @@ bool jit_prepare(const GenericDesc& d, const std::vector<std::string>& user_code
     p.ix1 = ix1;
     p.iy0 = iy0;
     p.iy1 = iy1;
+    // tensor maps of the TMA-staged inputs (box = the input's slot)
+    static_assert(sizeof(HvxTensorMap) == sizeof(CUtensorMap), "tensor map blob");
+    if (load_module)
+        for (const auto& bx : em.tma_boxes()) {
+            const GenExt& in = d.in[bx[0]];
+            if (encode_u8_map_raw(reinterpret_cast<CUtensorMap*>(&p.tmap[bx[0]]), in.ptr, in.pitch,
+                                  (uint32_t)d.W, (uint32_t)d.H, (uint32_t)bx[1],
+                                  (uint32_t)bx[2]) != HVX_SUCCESS) {
+                *why = "tensor map of a staged input";
+                return false;
+            }
+        }
     return true;
 }
 

@@ -314,6 +314,10 @@ hvx_status check_device_error(Context* ctx);
 hvx_status ensure_context_device_state(Context* ctx);
 void destroy_batch_cache(Context* ctx);
 hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s);
+// 2-D U8 tensor map of (w x h) bytes at ptr (16-byte aligned, pitch a multiple
+// of 16) with a (box_w x box_h) box; cells outside the image read as 0.
+hvx_status encode_u8_map_raw(CUtensorMap* map, const void* ptr, uint64_t pitch, uint32_t w,
+                             uint32_t h, uint32_t box_w, uint32_t box_h);
 // The tuned launch of a cached batch of exactly these graphs: rows per thread
 // of each image's tiles (0 where the kernel has its own tile) and the
 // persistent grid (0 for a direct launch).  HVX_ERROR_INVALID_PARAMETERS when

@@ -9,6 +9,11 @@
 #define HVX_JIT_MAX_EXT 6
 #define HVX_JIT_MAX_RES 4
 
+/* A CUDA tensor map (CUtensorMap: 128 bytes, 64-byte aligned) as plain data. */
+typedef struct __attribute__((aligned(64))) {
+    unsigned long long opaque[16];
+} HvxTensorMap;
+
 struct HvxJitParams {
     int W, H;                       // size of every image of the group
     int ix0, ix1, iy0, iy1;         // interior tiles (inclusive; none when ix0 > ix1):
@@ -20,4 +25,6 @@ struct HvxJitParams {
     void* out[HVX_JIT_MAX_EXT];     // external outputs
     unsigned long long out_pitch[HVX_JIT_MAX_EXT];
     void* res[HVX_JIT_MAX_RES];     // result blocks of the group's global operators
+    int* err;                       // device error word (a bounded wait that ran out)
+    HvxTensorMap tmap[HVX_JIT_MAX_EXT];  // U8 inputs staged by TMA: box = the staged slot
 };

@@ -36,6 +36,9 @@ hvx_status get_encoder() {
     return g_encode ? HVX_SUCCESS : HVX_ERROR_DEVICE;
 }
 
+hvx_status encode_u8_map_at(CUtensorMap* map, const void* ptr, uint64_t pitch, uint32_t w,
+                            uint32_t h, uint32_t box_w, uint32_t box_h);
+
 // 2-D U8 tensor map of an image with a (box_w x box_h) box; out-of-image
 // elements of a box read as 0.
 hvx_status encode_u8_map(CUtensorMap* map, const Image* im, uint32_t box_w, uint32_t box_h) {
@@ -43,14 +46,20 @@ hvx_status encode_u8_map(CUtensorMap* map, const Image* im, uint32_t box_w, uint
         std::memset(map, 0, sizeof(*map));
         return HVX_SUCCESS;
     }
+    return encode_u8_map_at(map, im->dev, im->pitch, im->w, im->h, box_w, box_h);
+}
+
+hvx_status encode_u8_map_at(CUtensorMap* map, const void* ptr, uint64_t pitch, uint32_t w,
+                            uint32_t h, uint32_t box_w, uint32_t box_h) {
     hvx_status st = get_encoder();
     if (st != HVX_SUCCESS) return st;
-    if (((uintptr_t)im->dev & 15) || (im->pitch & 15)) return HVX_ERROR_INVALID_PARAMETERS;
-    cuuint64_t dims[2] = {im->w, im->h};
-    cuuint64_t strides[1] = {im->pitch};
+    if (((uintptr_t)ptr & 15) || (pitch & 15)) return HVX_ERROR_INVALID_PARAMETERS;
+    void* const dev = const_cast<void*>(ptr);
+    cuuint64_t dims[2] = {w, h};
+    cuuint64_t strides[1] = {pitch};
     cuuint32_t box[2] = {box_w, box_h};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, im->dev, dims, strides, box, estr,
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, dev, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HVX_SUCCESS : HVX_ERROR_DEVICE;
@@ -681,6 +690,7 @@ hvx_status prepare_launches(Graph* g) {
                 std::string why;
                 G.jit_on = jit_prepare(G.gdesc, G.user_code, !ctx->plan_only, ctx->device, &G.jit,
                                        &why);
+                G.jit.p.err = ctx->d_error;
                 if (!G.jit_on && getenv("HVX_CODEGEN_VERBOSE"))
                     fprintf(stderr, "hvx: no generated kernel for a group: %s\n", why.c_str());
                 if (!G.jit_on && (must_gen || user))
@@ -1255,6 +1265,11 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             hit->n, hit->total_tiles, hit->tomasi, s));
     }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
+}
+
+hvx_status encode_u8_map_raw(CUtensorMap* map, const void* ptr, uint64_t pitch, uint32_t w,
+                             uint32_t h, uint32_t box_w, uint32_t box_h) {
+    return encode_u8_map_at(map, ptr, pitch, w, h, box_w, box_h);
 }
 
 }  // namespace hvx

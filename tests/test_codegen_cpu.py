@@ -40,7 +40,19 @@ def test_applications_compile(pctx, name, mode):
         s = H.hvxGetGraphKernelSource(g, i)
         assert (s is not None) == (k == "staged_tile")
         if s:
-            assert "hvx_generated" in s and "hvx_tile<false>" in s
+            assert "hvx_generated" in s and "hvx_tile<false, false>" in s
+
+
+def test_u8_inputs_staged_by_tma(pctx, monkeypatch):
+    # interior tiles take a staged U8 input as one TMA box on an mbarrier; its
+    # slot's rows start 16 bytes left of the tile (halo 2 of the 5x5 Gauss);
+    # HVX_CODEGEN_TMA=0 keeps per-thread loads
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss), 0)
+    assert s.count("hvx_tma_2d(B") == 1 and "hvx_mbar_wait(bar, p.err)" in s
+    assert "x0 - 16, y0 - 2" in s
+    monkeypatch.setenv("HVX_CODEGEN_TMA", "0")
+    s0 = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss), 0)
+    assert "hvx_tma_2d(B" not in s0 and "__ldg((const unsigned*)" in s0
 
 
 def test_constants_are_folded(pctx):
