@@ -53,17 +53,18 @@ struct GaussSmem {
     int ts[BATCH_SMEM_IMAGES + 1], tx[BATCH_SMEM_IMAGES];
 };
 
-__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0) {
-    return x0 >= 1 && y0 >= 1 && x0 + TW + 1 <= (int)p.W && y0 + TH + 1 <= (int)p.H;
+__device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0, int th) {
+    return x0 >= 1 && y0 >= 1 && x0 + TW + 1 <= (int)p.W && y0 + th + 1 <= (int)p.H;
 }
 
-// Box cells outside the image under REPLICATE / CONSTANT (edge tiles only).
-__device__ void fix_box_border(Box& in, const EdgeParams& p, int x0, int y0) {
+// Box cells outside the image under REPLICATE / CONSTANT (edge tiles only);
+// lh: the box rows the TMA filled.
+__device__ void fix_box_border(Box& in, const EdgeParams& p, int x0, int y0, int lh) {
     const int W = p.W, H = p.H;
     if (p.border_g == HVX_BORDER_UNDEFINED) return;
     const bool cst = p.border_g == HVX_BORDER_CONSTANT;
     const uint8_t cv = (uint8_t)p.cval_g;
-    for_each_outside(LH, LW, x0 - 16, y0 - 1, W, H, [&](int r, int c) {
+    for_each_outside(lh, LW, x0 - 16, y0 - 1, W, H, [&](int r, int c) {
         const int x = x0 - 16 + c, y = y0 - 1 + r;
         in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 16)];
     });
@@ -110,31 +111,33 @@ __device__ __noinline__ void store_edge(uint8_t* dst, int x, int y, const EdgePa
     }
 }
 
-// One tile after its box has landed (and, on edge tiles, been border-fixed).
+// One 128 x 8R tile after its box has landed (and, on edge tiles, been
+// border-fixed); R output rows per thread.
+template <int R>
 __device__ __forceinline__ void gauss_tile(const Box& in, const EdgeParams& p, int x0, int y0,
                                            bool interior) {
     const int q = threadIdx.x & 15, g = threadIdx.x >> 4;
     const int W = p.W, H = p.H;
-    const int x = x0 + 8 * q, yb = y0 + ROWS * g;
+    const int x = x0 + 8 * q, yb = y0 + R * g;
     if (x >= W || yb >= H) return;
     const uint32_t rnd = p.rounding == HVX_ROUND_TO_NEAREST ? 0x00080008u : 0u;
     const size_t pitch = p.gout_pitch;
     uint8_t* dst = p.gout + (size_t)yb * pitch;
-    const uint8_t* row = &in[ROWS * g][0];  // input row yb - 1
+    const uint8_t* row = &in[R * g][0];  // input row yb - 1
     const int c = 16 + 8 * q;
     uint32_t P[3][6];
     load_pairs(row, c, P[0]);
     load_pairs(row + LW, c, P[1]);
-    const bool fast = (interior || rect_full(p.gvalid, W, H)) && x + 8 <= W && yb + ROWS <= H;
+    const bool fast = (interior || rect_full(p.gvalid, W, H)) && x + 8 <= W && yb + R <= H;
     if (fast) {
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i) {
+        for (int i = 0; i < R; ++i) {
             load_pairs(row + (i + 2) * LW, c, P[(i + 2) % 3]);
             *reinterpret_cast<uint2*>(dst + x) = gauss8(P[i % 3], P[(i + 1) % 3], P[(i + 2) % 3], rnd);
             dst += pitch;
         }
     } else {
-        const int n = min(ROWS, H - yb);
+        const int n = min(R, H - yb);
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             uint32_t* a = P[0];
@@ -152,30 +155,31 @@ __device__ __forceinline__ void gauss_tile(const Box& in, const EdgeParams& p, i
     }
 }
 
-__device__ __forceinline__ void issue_box(Box& in, uint64_t* bar, const CUtensorMap* map, int x0,
-                                          int y0) {
-    mbar_arrive_expect_tx(bar, BOX_BYTES);
-    tma_load_2d(&in[0][0], map, bar, x0 - 16, y0 - 1);
-}
-
+// One image: one CTA per 128 x 8R tile (R rows per thread, chosen per image
+// size by gauss_single_rows; the tensor map's box is 160 x (8R + 2)).
+template <int R>
 __global__ void __launch_bounds__(GAUSS_THREADS)
     gauss_kernel(const __grid_constant__ CUtensorMap tmap, const EdgeParams p) {
+    static_assert(R >= 1 && R <= ROWS, "the box holds at most 8 ROWS + 2 rows");
     __shared__ GaussSmem<1> sm;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * 8 * R;
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0);
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&sm.bar[0], (uint32_t)(LW * (8 * R + 2)));
+        tma_load_2d(&sm.in[0].b[0][0], &tmap, &sm.bar[0], x0 - 16, y0 - 1);
+    }
     // every thread leaves together when the (bounded) wait ran out
     if (__syncthreads_or(!mbar_wait_bounded(&sm.bar[0], 0, p.err))) return;
-    const bool interior = tile_is_interior(p, x0, y0);
+    const bool interior = tile_is_interior(p, x0, y0, 8 * R);
     if (!interior) {
-        fix_box_border(sm.in[0].b, p, x0, y0);
+        fix_box_border(sm.in[0].b, p, x0, y0, 8 * R + 2);
         __syncthreads();
     }
-    gauss_tile(sm.in[0].b, p, x0, y0, interior);
+    gauss_tile<R>(sm.in[0].b, p, x0, y0, interior);
 }
 
 // Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
@@ -245,12 +249,12 @@ __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBa
         }
         const EdgeParams& p = sm.prm[ps];
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
-        const bool interior = tile_is_interior(p, x0, y0);
+        const bool interior = tile_is_interior(p, x0, y0, TH);
         if (!interior) {
-            fix_box_border(sm.in[s].b, p, x0, y0);
+            fix_box_border(sm.in[s].b, p, x0, y0, LH);
             __syncthreads();
         }
-        gauss_tile(sm.in[s].b, p, x0, y0, interior);
+        gauss_tile<ROWS>(sm.in[s].b, p, x0, y0, interior);
         __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
         if (threadIdx.x == 0) {
             const int tn = t + STAGES * (int)gridDim.x;
@@ -262,9 +266,23 @@ __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBa
 }  // namespace
 
 cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
-    dim3 grid((p.W + TW - 1) / TW, (p.H + TH - 1) / TH);
-    gauss_kernel<<<grid, GAUSS_THREADS, 0, s>>>(map, p);
+    const int R = p.rows == 2 || p.rows == 5 ? p.rows : ROWS;
+    dim3 grid((p.W + TW - 1) / TW, (p.H + 8 * R - 1) / (8 * R));
+    switch (R) {
+        case 2: gauss_kernel<2><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
+        case 5: gauss_kernel<5><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
+        default: gauss_kernel<ROWS><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
+    }
     return cudaGetLastError();
+}
+
+// Rows per thread of the single-image Gaussian kernel (tiles of 128 x 8R):
+// as for the edge kernel, R = 5, or R = 2 when the image has fewer 128 x 40
+// tiles than SMs (a small image then still spreads over the GPU), so that a
+// launch's latency is a few rows of work per thread.
+int gauss_single_rows(int W, int H, int num_sms) {
+    const long long tiles5 = (long long)((W + TW - 1) / TW) * ((H + 39) / 40);
+    return tiles5 >= (num_sms > 0 ? num_sms : 152) ? 5 : 2;
 }
 
 cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s) {

@@ -38,7 +38,10 @@ int edge_batch_blocks_per_sm(int mode);
 cudaError_t launch_edge_point_selftest(int gmax, int s_thr, uint8_t* phase, uint8_t* mask,
                                        cudaStream_t s);
 
+// one image; p.rows (2, 5 or GAUSS_ROWS) rows per thread, the map boxed
+// 160 x (8 p.rows + 2)
 cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
+int gauss_single_rows(int W, int H, int num_sms);
 cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
 int gauss_batch_blocks_per_sm();
 

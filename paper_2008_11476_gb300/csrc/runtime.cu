@@ -250,7 +250,10 @@ hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
     e.gout = static_cast<uint8_t*>(g.out->dev);
     e.gout_pitch = g.out->pitch;
     set_rect(e.gvalid, g.out->valid);
-    return encode_u8_map(&G.tmap, g.in[0], GAUSS_LOAD_W, GAUSS_LOAD_H);
+    // one image per launch: R rows per thread, a 160 x (8R + 2) box (the
+    // batch kernel encodes its own 160 x GAUSS_LOAD_H maps)
+    e.rows = gauss_single_rows((int)G.W, (int)G.H, ctx->num_sms);
+    return encode_u8_map(&G.tmap, g.in[0], GAUSS_LOAD_W, (uint32_t)(8 * e.rows + 2));
 }
 
 // ---- Harris group -------------------------------------------------------------
@@ -834,13 +837,15 @@ hvx_status make_edge_tables(Context* ctx, Graph* const* gs, int n, int mode, int
     for (int i = 0; i < n; ++i) {
         const Group& G = gs[i]->plan.groups[0];
         EdgeParams ep = G.edge;
-        if (mode == EDGE_MODE_GAUSS) {
-            std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &G.tmap,
-                        sizeof(CUtensorMap));
-        } else {  // the batch kernel's box: 8R rows and the halo
-            ep.rows = rows;
+        {  // the batch kernel's box (the single-image map may be shorter)
             CUtensorMap map;
-            hvx_status st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, (uint32_t)(th + 4));
+            hvx_status st;
+            if (mode == EDGE_MODE_GAUSS) {
+                st = encode_u8_map(&map, G.inputs[0], GAUSS_LOAD_W, GAUSS_LOAD_H);
+            } else {  // 8R rows and the halo
+                ep.rows = rows;
+                st = encode_u8_map(&map, G.inputs[0], EDGE_LOAD_W, (uint32_t)(th + 4));
+            }
             if (st != HVX_SUCCESS) return st;
             std::memcpy(host.data() + (size_t)i * sizeof(CUtensorMap), &map, sizeof(map));
         }

@@ -34,8 +34,9 @@ def circ_diff(a, b):
 
 # --- Gaussian3x3 (the plain one-node graph) --------------------------------------
 
-# the Gaussian kernel's tiles are 128 x 120: add sizes with several ragged tile rows
-@pytest.mark.parametrize("w,h", SIZES + [(300, 250), (385, 361)])
+# the single-image Gaussian kernel's tiles are 128 x 8R, R = 2 (fewer 128 x 40
+# tiles than SMs) or 5: add sizes with several ragged tile rows of each
+@pytest.mark.parametrize("w,h", SIZES + [(300, 250), (385, 361), (1921, 1083), (2500, 803)])
 @pytest.mark.parametrize("border", BORDERS)
 def test_gaussian(ctx, w, h, border):
     img = synth.uniform_u8(w, h, seed=1 + w + h)
