@@ -121,12 +121,6 @@ __device__ void build_phase_lut(PhaseEntry* lut) {
     }
 }
 
-__device__ __forceinline__ float fma_rm(float a, float b, float c) {
-    float r;
-    asm("fma.rm.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 // Phase from exact integer gradients held in binary32 (gen_phase_poly.py
 // derives and checks every step over all integer gradient pairs): with
 // mn, mx = min, max of |gx|, |gy| and t = mn / mx, the rounded octant angle
@@ -135,49 +129,64 @@ __device__ __forceinline__ float fma_rm(float a, float b, float c) {
 // the low mantissa bits of a number in [1.5 * 2^23, 2^24); the table entry of
 // (octant, n) holds tan((n - 1/2) pi / 128) and the final phase byte for both
 // outcomes (byte 0: n, byte 1: n - 1), and the sign of the test picks the
-// byte.  The entry index is formed with multiply-adds of sign bits.
-// gx = gy = 0 gives t = 0, n = 1 and a negative test (mx is raised to 1
-// there), so phase 0.
-struct PhaseCand {
-    uint32_t q;  // phase byte for n (byte 0) and for n - 1 (byte 1)
-    float h;     // the exact test: negative selects byte 1
-};
+// byte.  The octant's sign bits as 0 / 1 floats come from saturating
+// operations on exact integers (sat(-gx) = [gx < 0], sat(|gy| - |gx|) =
+// [|gy| > |gx|]), and the table index is added to the guess with exact fmas
+// (the guess has unit spacing in [1.5 * 2^23, 2^24)), so the index costs
+// floating-point operations only.  gx = gy = 0 gives t = 0, n = 1 and a
+// negative test (mx is raised to 1 there), so phase 0.
 
-// The octant's sign bits as 0 / 1 floats come from saturating operations on
-// exact integers (sat(-gx) = [gx < 0], sat(|gy| - |gx|) = [|gy| > |gx|]),
-// and the table index is added to the guess with exact fmas (the guess has
-// unit spacing in [1.5 * 2^23, 2^24)), so the index costs floating-point
-// operations only.
-__device__ __forceinline__ PhaseCand phase_cand(float gx, float gy, const PhaseEntry* lut) {
-    const float ax = fabsf(gx), ay = fabsf(gy);
-    float mx;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(mx) : "f"(ax), "f"(ay), "f"(1.0f));
-    const float mn = fminf(ax, ay);
-    const float t = mn * rcp_approx(mx);
-    float y = fma_rm(t, fmaf(t, kPhaseGuessB, kPhaseGuessA), 12582913.0f);  // 1.5*2^23 + 1
-    y = fmaf(__saturatef(-gx), 136.0f, y);     // + 4 * 34 [gx < 0]
-    y = fmaf(__saturatef(-gy), 68.0f, y);      // + 2 * 34 [gy < 0]
-    y = fmaf(__saturatef(ay - ax), 34.0f, y);  // + 34 [|gy| > |gx|]
-    const PhaseEntry e = lut[__float_as_int(y) - 0x4B400000];  // n = 1 .. 33 + 34 x octant
-    return {e.q, fmaf(-mx, e.tan, mn)};
+// max(|a|, |b|, 1): one three-input max.
+__device__ __forceinline__ float max_abs_1(float a, float b) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(fabsf(a)), "f"(fabsf(b)), "f"(1.0f));
+    return r;
 }
 
-// The phase bytes of two pixels in bytes 0 and 1 of a word: one byte permute
-// whose selector takes byte 0 or 1 of the first candidate word and byte 4 or
-// 5 (bytes 0, 1 of the second) by the signs of the two tests.  A test is
-// never smaller than 2^-40 in magnitude, so sat(-2^40 h) = [h < 0]; the
-// selector is formed in the low bits of 2^23 + 0x40 + [ha < 0] + 16 [hb < 0]
-// (the byte permute reads only the low 16 bits of its selector).
-__device__ __forceinline__ uint32_t phase_pair(const PhaseCand& a, const PhaseCand& b) {
-    const float na = __saturatef(a.h * -1099511627776.0f);
-    const float nb = __saturatef(b.h * -1099511627776.0f);
+// The Phase bytes of a pixel pair (lanes x, y of gx and gy) in bytes 0 and 1:
+// the steps above for both pixels, with the guess and the octant index
+// formed by packed f32x2 instructions (every lane rounds as a scalar step
+// would), then one byte permute whose selector takes byte 0 or 1 of the
+// first entry word and byte 4 or 5 (bytes 0, 1 of the second) by the signs
+// of the two tests.  The pair works with
+// -mn (a max of negated magnitudes), so that no packed operand needs a
+// negation: t' = -t, the inner term -(A + B t) = B t' - A, and the guess
+// t' (B t' - A) = t (A + B t); the tests are h' = mx tan - mn = -h
+// (round-to-nearest is symmetric, so |h'| = |h| >= 2^-40 and
+// sat(2^40 h') = [h < 0]).  The selector is formed in the low bits of
+// 2^23 + 0x40 + [ha < 0] + 16 [hb < 0] (the byte permute reads only the low
+// 16 bits of its selector).  The tests and the selector stay scalar: a
+// packed test needs the two entries' tangents moved into a register pair,
+// and a selector from one packed round-up fma puts two dependent adds after
+// it; both measured slower.
+__device__ __forceinline__ uint32_t phase_pair2(float2 gx, float2 gy, const PhaseEntry* lut) {
+    const float2 mx = make_float2(max_abs_1(gx.x, gy.x), max_abs_1(gx.y, gy.y));
+    const float2 nmn = make_float2(fmaxf(-fabsf(gx.x), -fabsf(gy.x)),
+                                   fmaxf(-fabsf(gx.y), -fabsf(gy.y)));
+    const float2 t = __fmul2_rn(nmn, make_float2(rcp_approx(mx.x), rcp_approx(mx.y)));
+    const float2 in = __ffma2_rn(t, make_float2(kPhaseGuessB, kPhaseGuessB),
+                                 make_float2(-kPhaseGuessA, -kPhaseGuessA));
+    float2 y = __ffma2_rd(t, in, make_float2(12582913.0f, 12582913.0f));  // 1.5*2^23 + 1
+    y = __ffma2_rn(make_float2(__saturatef(-gx.x), __saturatef(-gx.y)),
+                   make_float2(136.0f, 136.0f), y);  // + 4 * 34 [gx < 0]
+    y = __ffma2_rn(make_float2(__saturatef(-gy.x), __saturatef(-gy.y)),
+                   make_float2(68.0f, 68.0f), y);    // + 2 * 34 [gy < 0]
+    y = __ffma2_rn(make_float2(__saturatef(fabsf(gy.x) - fabsf(gx.x)),
+                               __saturatef(fabsf(gy.y) - fabsf(gx.y))),
+                   make_float2(34.0f, 34.0f), y);    // + 34 [|gy| > |gx|]
+    const PhaseEntry ea = lut[__float_as_int(y.x) - 0x4B400000];
+    const PhaseEntry eb = lut[__float_as_int(y.y) - 0x4B400000];
+    const float na = __saturatef(fmaf(mx.x, ea.tan, nmn.x) * 1099511627776.0f);
+    const float nb = __saturatef(fmaf(mx.y, eb.tan, nmn.y) * 1099511627776.0f);
     const float sel = fmaf(nb, 16.0f, na + 8388672.0f);  // 2^23 + 0x40
-    return __byte_perm(a.q, b.q, __float_as_uint(sel));
+    return __byte_perm(ea.q, eb.q, __float_as_uint(sel));
 }
 
+// One pixel's Phase byte (the general output path): the pair routine with
+// the pixel in both lanes, so that every Phase byte of the edge kernel comes
+// from phase_pair2.
 __device__ __forceinline__ uint32_t phase_from_float(float gx, float gy, const PhaseEntry* lut) {
-    const PhaseCand c = phase_cand(gx, gy, lut);
-    return __byte_perm(c.q, 0u, __float_as_uint(c.h) >> 31);
+    return phase_pair2(make_float2(gx, gx), make_float2(gy, gy), lut) & 0xFFu;
 }
 
 __device__ __forceinline__ void store8_u8(uint8_t* row, int x, int W, const uint32_t* b) {
@@ -469,8 +478,7 @@ __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p,
             uint32_t pp[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                pp[j] = phase_pair(phase_cand(gx2[j].x, gy2[j].x, cx.plut),
-                                   phase_cand(gx2[j].y, gy2[j].y, cx.plut));
+                pp[j] = phase_pair2(gx2[j], gy2[j], cx.plut);
             pw[0] = __byte_perm(pp[0], pp[1], 0x5410);
             pw[1] = __byte_perm(pp[2], pp[3], 0x5410);
         }
@@ -803,8 +811,8 @@ cudaError_t launch_batch_mode(const EdgeBatchDesc& d, int grid, int rows, cudaSt
 
 // Point operators of the fused edge kernel over every integer gradient pair
 // (gx, gy) in [-gmax, gmax]^2, element i = (gy + gmax) (2 gmax + 1) + gx + gmax:
-// the Phase byte through phase_cand / phase_pair (two elements per call, as
-// the kernel pairs neighbouring pixels) and the mask byte (255 / 0) through
+// the Phase byte through phase_pair2 (two elements per call, as the kernel
+// pairs neighbouring pixels) and the mask byte (255 / 0) through
 // mask_value2 / sign_bytes2 for gx^2 + gy^2 > s_thr.  Same device code and
 // shared-memory table as edge_batch_kernel; a self-test, not a hot path.
 __global__ void __launch_bounds__(256) edge_point_selftest_kernel(int gmax, int s_thr,
@@ -820,7 +828,7 @@ __global__ void __launch_bounds__(256) edge_point_selftest_kernel(int gmax, int 
         const long long j = i + 1 < n ? i + 1 : i;  // an odd count pairs the last with itself
         const float gxa = (float)(int)(i % N - gmax), gya = (float)(int)(i / N - gmax);
         const float gxb = (float)(int)(j % N - gmax), gyb = (float)(int)(j / N - gmax);
-        const uint32_t pp = phase_pair(phase_cand(gxa, gya, lut), phase_cand(gxb, gyb, lut));
+        const uint32_t pp = phase_pair2(make_float2(gxa, gxb), make_float2(gya, gyb), lut);
         const float2 mv = mask_value2(make_float2(gxa, gxb), make_float2(gya, gyb), nthr);
         const uint32_t mb = ~sign_bytes2(mv.x, mv.y);  // 0xFF where the mask is true
         phase[i] = (uint8_t)pp;
