@@ -251,18 +251,25 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
 // 15 only provide the vertical sums of the halo columns to their neighbours.
 // R (8 .. 24) is chosen per image size at plan time so that the busiest SM
 // walks the fewest rows (harris_fast_rows); 4 CTAs share an SM.
-// Each thread walks down its rows:
+// Each thread walks down its rows (three per loop trip, so the input windows
+// rotate by renaming):
 //   * each step forms one new gradient row (gx, gy at its 8 columns) in
-//     biased 16-bit lanes from a sliding 3-row window of input pixel pairs,
-//     keeps it in a 5-row ring in shared memory (the thread's own slots), and
-//     forms the three exact int32 products;
-//   * 24 running vertical 5-sums (8 columns x 3 products) gain the new row
-//     and, after the outputs of the row, lose the row that leaves the window
-//     (its products recomputed from the ring);
-//   * the vertical sums of columns xs - 2, xs - 1 and xs + 8, xs + 9 come from
-//     the neighbouring lanes by shuffles; horizontal 5-sums slide along the
-//     strip, then the exact 64-bit response q = kd * R and the threshold
-//     q > q_thr, as in the general kernel.
+//     biased 16-bit lanes from a sliding 3-row window of input pixel pairs
+//     and keeps it in a 5-row ring in shared memory (the thread's own slots);
+//   * 24 running vertical 5-sums (8 columns x 3 products, held as pairs of
+//     columns in packed binary32, where every value is an exact integer
+//     below 2^23) gain the new row's products by packed fmas and, after the
+//     outputs of the row, lose the row that leaves the window (its lanes
+//     re-read from the ring);
+//   * the vertical sums become integers through their bit patterns (v plus
+//     2^23 or 1.5 * 2^23), those of columns xs - 2, xs - 1 and xs + 8, xs + 9
+//     come from the neighbouring lanes by shuffles, and exact int32
+//     horizontal 5-sums slide along the strip;
+//   * the mask alone (the benchmark's form) is decided for two pixels per
+//     packed binary32 operation between two bounds of q - q_thr, with the
+//     exact 64-bit test only for the pixels the bounds leave open; the
+//     exported response and the Shi-Tomasi test take the exact sums, as in
+//     the general kernel.
 // Every thread runs all R rows (rows below the image read box rows the TMA
 // filled with 0 and are not stored), so the shuffles always see full warps.
 constexpr int FTW = 112, FTHREADS = 128;
@@ -278,7 +285,9 @@ struct FastSmem {
     alignas(128) uint8_t in[FLH_MAX][FLW];  // image (x0 - 16 + c, y0 - 3 + r)
     alignas(16) uint4 ring[FTHREADS][RSTRIDE];
     alignas(8) uint64_t bar;
+    HarrisParams prm;  // batch: this tile's image parameters
 };
+static_assert(sizeof(HarrisParams) % 4 == 0, "parameters copied as words");
 
 // Pixel pairs (xs - 2, xs - 1), (xs, xs + 1) .. (xs + 8, xs + 9) of one box
 // row, for the strip starting at box column c (= xs - x0 + 16).
@@ -319,20 +328,81 @@ __device__ __forceinline__ void grad_row(const uint32_t* a, const uint32_t* b, c
     }
 }
 
-// S[k][c] += SIGN * (product k of the gradient row G at column c).
-template <int SIGN>
-__device__ __forceinline__ void accumulate(const uint32_t* G, int (*S)[8]) {
+// Vertical 5-sums of the three products at the strip's 8 columns, as pairs of
+// columns (2j, 2j + 1) in packed binary32.  Every product is an integer with
+// |gx^2|, |gy^2| <= 1020^2 and |gx gy| <= 765^2 (for the 3x3 Sobel of bytes,
+// gx = 2 e1 + u + v and gy = 2 e2 + u - v with e1, e2, u, v differences of
+// bytes, so |gx gy| <= 765^2 - v^2), and a sum of at most five rows stays
+// below 2^23 in magnitude, so every packed fma below is exact.
+struct VSums {
+    float2 xx[4], yy[4], xy[4];
+};
+
+// s * gx (or s * gy) of a gradient word's two lanes (lane + 1024 each): a
+// lane spliced under the exponent of 2^23 is the float 2^23 + lane, and one
+// packed fma takes out the offset.
+__device__ __forceinline__ float2 lanes_f32(uint32_t w, float s) {
+    return __ffma2_rn(make_float2(__int_as_float(__byte_perm(w, 0x4B00u, 0x5410)),
+                                  __int_as_float(__byte_perm(w, 0x4B00u, 0x5432))),
+                      make_float2(s, s), make_float2(-s * 8389632.0f, -s * 8389632.0f));
+}
+
+// V += the products of gradient row G (G[j]: gx lanes, G[4 + j]: gy lanes).
+__device__ __forceinline__ void add_products(const uint32_t* G, VSums& V) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+        const float2 gx = lanes_f32(G[j], 1.0f), gy = lanes_f32(G[4 + j], 1.0f);
+        V.xx[j] = __ffma2_rn(gx, gx, V.xx[j]);
+        V.yy[j] = __ffma2_rn(gy, gy, V.yy[j]);
+        V.xy[j] = __ffma2_rn(gx, gy, V.xy[j]);
+    }
+}
+
+// V -= the products of gradient row G (packed operands take no negation, so
+// -gx and -gy come from their own fmas).
+__device__ __forceinline__ void sub_products(const uint32_t* G, VSums& V) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int gx = (int)((G[j] >> (16 * h)) & 0xFFFFu) - 1024;
-            const int gy = (int)((G[4 + j] >> (16 * h)) & 0xFFFFu) - 1024;
-            const int c = 2 * j + h;
-            S[0][c] += SIGN * (gx * gx);
-            S[1][c] += SIGN * (gy * gy);
-            S[2][c] += SIGN * (gx * gy);
-        }
+    for (int j = 0; j < 4; ++j) {
+        const float2 gx = lanes_f32(G[j], 1.0f), ngx = lanes_f32(G[j], -1.0f);
+        const float2 gy = lanes_f32(G[4 + j], 1.0f), ngy = lanes_f32(G[4 + j], -1.0f);
+        V.xx[j] = __ffma2_rn(ngx, gx, V.xx[j]);
+        V.yy[j] = __ffma2_rn(ngy, gy, V.yy[j]);
+        V.xy[j] = __ffma2_rn(ngx, gy, V.xy[j]);
+    }
+}
+
+// The vertical sums as integers: v + 2^23 (squares, v in [0, 2^23)) and
+// v + 1.5 * 2^23 (cross products, |v| < 2^22) lie in [2^23, 2^24), where the
+// float's bit pattern is that of 2^23 plus an integer, so the pattern is
+// v + 0x4B000000 (0x4B400000) exactly; b[k][c] for product k, column c.
+constexpr uint32_t kSqBits = 0x4B000000u, kXyBits = 0x4B400000u;
+__device__ __forceinline__ void vsum_bits(const VSums& V, uint32_t (*b)[8]) {
+    const float2 sq = make_float2(0x1p23f, 0x1p23f), xy = make_float2(0x1.8p23f, 0x1.8p23f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 a = __fadd2_rn(V.xx[j], sq), c = __fadd2_rn(V.yy[j], sq);
+        const float2 e = __fadd2_rn(V.xy[j], xy);
+        b[0][2 * j] = __float_as_uint(a.x);
+        b[0][2 * j + 1] = __float_as_uint(a.y);
+        b[1][2 * j] = __float_as_uint(c.x);
+        b[1][2 * j + 1] = __float_as_uint(c.y);
+        b[2][2 * j] = __float_as_uint(e.x);
+        b[2][2 * j + 1] = __float_as_uint(e.y);
+    }
+}
+
+// Horizontal 5-sums h[j] of the strip's columns j - 2 .. j + 2 from the bit
+// patterns s (own columns), l (columns -2, -1) and r (columns 8, 9), all
+// offset by the same m: five patterns carry 5 m (mod 2^32), taken out once;
+// the sliding steps add one pattern and drop one, so the offsets cancel.
+__device__ __forceinline__ void hsums(const uint32_t* s, const uint32_t* l, const uint32_t* r,
+                                      uint32_t m, int* h) {
+    uint32_t v = l[0] + l[1] + s[0] + s[1] + s[2] - 5u * m;
+    h[0] = (int)v;
+#pragma unroll
+    for (int j = 1; j < 8; ++j) {
+        v += (j + 2 < 8 ? s[j + 2] : r[j - 6]) - (j - 3 >= 0 ? s[j - 3] : l[j - 1]);
+        h[j] = (int)v;
     }
 }
 
@@ -379,36 +449,61 @@ __device__ __forceinline__ bool tomasi_above(int a, int b, int c, float T) {
     return tomasi_response_f32(a, b, c) > T;
 }
 
-// q > q_thr, decided in binary32 when the computed q is farther from the
-// threshold than its error bound, else exactly in 64-bit integers.  With
-// u = 2^-24 and M = kd (a b + c^2) + kn (a + b)^2, the binary32 evaluation
-// below (rounded conversions, products, one rounding per fused multiply-add)
-// is within 8u M of q, the threshold's conversion within u |q_thr|, and the
-// bound 2^-19 M' + 2^-21 |q_thr'| (primes: as computed) exceeds their sum with
-// a 4-fold margin (tests/test_harris_decision.py replays the procedure).
-// Inputs: 0 <= a, b < 2^25, |c| < 2^25.  qtf = q_thr in binary32, qtb =
-// 2^-21 |qtf|.
-// The binary32 estimate d of q - q_thr and the bound it must exceed in
-// magnitude to decide the sign (below); pairs with the exact fallback.
-__device__ __forceinline__ void harris_estimate(int a, int b, int c, float knf, float kdf,
-                                                float qtf, float qtb, float* d, float* bound) {
-    const float A = __int2float_rn(a), B = __int2float_rn(b), C = __int2float_rn(c);
-    const float P = __fmul_rn(A, B);
-    const float D = fmaf(-C, C, P);
-    const float S = __fadd_rn(A, B);
-    const float V = __fmul_rn(knf, __fmul_rn(S, S));
-    const float Q = fmaf(kdf, D, -V);
-    const float M = fmaf(kdf, fmaf(C, C, P), V);
-    *bound = fmaf(0x1p-19f, M, qtb);
-    *d = __fsub_rn(Q, qtf);
+// The mask-only decision of q > q_thr for two pixels at once (packed
+// binary32).  With A, B, C the window sums converted (rounded), the values
+//   lo = kd (A B - C^2) + (S^2 n1 + n2),  hi = kd (A B - C^2) + (S^2 m1 + m2),
+// S = A + B, n1 = -(kn + Kb), n2 = -(q_thr + Qb), m1 = -(kn - Kb), m2 =
+// -(q_thr - Qb), Kb = 2^-19 (kd + 2 kn), Qb = 2^-21 |q_thr| (every step
+// rounded once), bracket q - q_thr: lo > 0 implies q > q_thr, hi < 0 implies
+// q < q_thr, and otherwise the exact test decides.  With u = 2^-24 the
+// computed kd (A B - C^2) - kn S^2 - q_thr is within u ((2 kd + 7 kn) (a + b)^2
+// + 3 |q_thr|) of q - q_thr (up to O(u^2)), using c^2 <= a b <= (a + b)^2 / 4
+// (Cauchy-Schwarz on window sums of gx^2, gy^2, gx gy), and Kb S^2 + Qb
+// exceeds that with a margin above 2.5 (tests/test_harris_decision.py replays
+// the procedure).  lo <= hi always (rounding is monotonic), so at most one
+// decides.
+struct HarrisDecide2 {
+    float2 kd, n1, n2, m1, m2;
+};
+
+__device__ __forceinline__ HarrisDecide2 harris_decide_consts(int kn, int kd, long long q_thr) {
+    const float kb = (float)(kd + 2 * kn) * 0x1p-19f;
+    const float qt = (float)q_thr, qb = fabsf(qt) * 0x1p-21f;
+    HarrisDecide2 k;
+    k.kd = make_float2((float)kd, (float)kd);
+    const float n1 = -((float)kn + kb), n2 = -(qt + qb);
+    const float m1 = -((float)kn - kb), m2 = -(qt - qb);
+    k.n1 = make_float2(n1, n1);
+    k.n2 = make_float2(n2, n2);
+    k.m1 = make_float2(m1, m1);
+    k.m2 = make_float2(m2, m2);
+    return k;
 }
 
-__device__ __forceinline__ bool harris_above(int a, int b, int c, float knf, float kdf, float qtf,
-                                             float qtb, int kn, int kd, long long q_thr) {
-    float d, bound;
-    harris_estimate(a, b, c, knf, kdf, qtf, qtb, &d, &bound);
-    if (fabsf(d) > bound) return d > 0.0f;
-    return harris_q32(a, b, c, kn, kd) > q_thr;
+__device__ __forceinline__ void harris_bracket2(float2 A, float2 B, float2 C, const HarrisDecide2& k,
+                                                float2* lo, float2* hi) {
+    const float2 P = __fmul2_rn(A, B);
+    const float2 CC = __fmul2_rn(C, C);
+    const float2 D = __ffma2_rn(CC, make_float2(-1.0f, -1.0f), P);
+    const float2 S = __fadd2_rn(A, B);
+    const float2 S2 = __fmul2_rn(S, S);
+    *lo = __ffma2_rn(k.kd, D, __ffma2_rn(S2, k.n1, k.n2));
+    *hi = __ffma2_rn(k.kd, D, __ffma2_rn(S2, k.m1, k.m2));
+}
+
+// Bytes 0 and 1: the sign bits of a and b replicated over a byte (prmt with
+// the sign flag of selector nibbles 0xB and 0xF; __byte_perm ignores that flag).
+__device__ __forceinline__ uint32_t sign_bytes2(float a, float b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xFB;" : "=r"(r) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
+    return r;
+}
+
+// max(a, b, c): one three-input max.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // One 112 x 8R output tile at (x0, y0) of the image that `tmap` / `p` describe.
@@ -438,13 +533,14 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
     const bool full = xs >= p.valid[0] && xs + 8 <= p.valid[2] && yb >= p.valid[1] &&
                       yb + R <= p.valid[3];
     const int kn = (int)p.kn, kd = (int)p.kd;
-    const float knf = (float)kn, kdf = (float)kd;
-    const float qtf = (float)p.q_thr, qtb = fabsf(qtf) * 0x1p-21f;
-    int S[3][8];
+    const HarrisDecide2 dk = harris_decide_consts(kn, kd, p.q_thr);
+    VSums V;
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) S[k][j] = 0;
+    for (int j = 0; j < 4; ++j) {
+        V.xx[j] = make_float2(0.0f, 0.0f);
+        V.yy[j] = make_float2(0.0f, 0.0f);
+        V.xy[j] = make_float2(0.0f, 0.0f);
+    }
     // prologue: gradient rows yb - 2 .. yb + 1 (input rows yb - 3 .. yb + 2)
     uint32_t A[6], B[6], C[6], G[8];
     load_pairs6(row, c, A);
@@ -455,7 +551,7 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
         grad_row(A, B, C, G);
         ring[2 * r + 0] = make_uint4(G[0], G[1], G[2], G[3]);
         ring[2 * r + 1] = make_uint4(G[4], G[5], G[6], G[7]);
-        accumulate<1>(G, S);
+        add_products(G, V);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             A[k] = B[k];
@@ -466,142 +562,130 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
     float* rrow = p.resp ? reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(p.resp) +
                                                     (size_t)yb * p.resp_pitch)
                          : nullptr;
-#pragma unroll 1
-    for (int i = 0; i < R; ++i) {
+    const uint32_t fx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
+    const uint32_t tvx = ((uint32_t)p.tv & 0xFFu) * 0x01010101u;
+    // one output row y = yb + i; Pa, Pb: input rows y + 1, y + 2, Pn receives y + 3
+    auto step = [&](const uint32_t* Pa, const uint32_t* Pb, uint32_t* Pn, int i) {
         const int y = yb + i;
         // new gradient row y + 2 (input rows y + 1 .. y + 3) into ring slot (i + 4) mod 5
-        load_pairs6(row + (i + 6) * FLW, c, C);
-        grad_row(A, B, C, G);
+        load_pairs6(row + (i + 6) * FLW, c, Pn);
+        grad_row(Pa, Pb, Pn, G);
         const int sn = (i + 4) % RING, so = i % RING;
         ring[2 * sn + 0] = make_uint4(G[0], G[1], G[2], G[3]);
         ring[2 * sn + 1] = make_uint4(G[4], G[5], G[6], G[7]);
-        accumulate<1>(G, S);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            A[k] = B[k];
-            B[k] = C[k];
-        }
-        // vertical sums of the halo columns from the neighbouring strips
-        int L[3][2], R[3][2];
+        add_products(G, V);
+        // vertical sums as integer bit patterns; those of the halo columns
+        // from the neighbouring strips
+        uint32_t Sb[3][8], L[3][2], Rr[3][2];
+        vsum_bits(V, Sb);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            L[k][0] = __shfl_up_sync(0xffffffffu, S[k][6], 1);
-            L[k][1] = __shfl_up_sync(0xffffffffu, S[k][7], 1);
-            R[k][0] = __shfl_down_sync(0xffffffffu, S[k][0], 1);
-            R[k][1] = __shfl_down_sync(0xffffffffu, S[k][1], 1);
+            L[k][0] = __shfl_up_sync(0xffffffffu, Sb[k][6], 1);
+            L[k][1] = __shfl_up_sync(0xffffffffu, Sb[k][7], 1);
+            Rr[k][0] = __shfl_down_sync(0xffffffffu, Sb[k][0], 1);
+            Rr[k][1] = __shfl_down_sync(0xffffffffu, Sb[k][1], 1);
         }
-        if (!TOMASI && !rrow && producer && y < H) {
-            // the mask alone (the benchmark's form): every pixel's estimate
-            // first, the exact test only in the rare row where one is too close
+        if (producer && y < H) {
             int ha[8], hb[8], hc[8];
-            int h0 = L[0][0] + L[0][1] + S[0][0] + S[0][1] + S[0][2];
-            int h1 = L[1][0] + L[1][1] + S[1][0] + S[1][1] + S[1][2];
-            int h2 = L[2][0] + L[2][1] + S[2][0] + S[2][1] + S[2][2];
+            hsums(Sb[0], L[0], Rr[0], kSqBits, ha);
+            hsums(Sb[1], L[1], Rr[1], kSqBits, hb);
+            hsums(Sb[2], L[2], Rr[2], kXyBits, hc);
+            if (!TOMASI && !rrow) {
+                // the mask alone (the benchmark's form): the bracket of every
+                // pixel pair first, the exact test only in the rare row where
+                // a pixel is left undecided
+                float2 lo[4], hi[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j > 0) {
-                    h0 += (j + 2 < 8 ? S[0][j + 2] : R[0][j - 6]) - (j - 3 >= 0 ? S[0][j - 3] : L[0][j - 1]);
-                    h1 += (j + 2 < 8 ? S[1][j + 2] : R[1][j - 6]) - (j - 3 >= 0 ? S[1][j - 3] : L[1][j - 1]);
-                    h2 += (j + 2 < 8 ? S[2][j + 2] : R[2][j - 6]) - (j - 3 >= 0 ? S[2][j - 3] : L[2][j - 1]);
+                for (int j = 0; j < 4; ++j)
+                    harris_bracket2(make_float2((float)ha[2 * j], (float)ha[2 * j + 1]),
+                                    make_float2((float)hb[2 * j], (float)hb[2 * j + 1]),
+                                    make_float2((float)hc[2 * j], (float)hc[2 * j + 1]), dk,
+                                    &lo[j], &hi[j]);
+                // undecided: lo <= 0 <= hi, i.e. min(-lo, hi) >= 0
+                float un[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    un[2 * j] = fminf(-lo[j].x, hi[j].x);
+                    un[2 * j + 1] = fminf(-lo[j].y, hi[j].y);
                 }
-                ha[j] = h0;
-                hb[j] = h1;
-                hc[j] = h2;
-            }
-            float dv[8];
-            bool sure = true;
+                const float worst = fmaxf(fmax3(un[0], un[1], un[2]),
+                                          fmax3(fmax3(un[3], un[4], un[5]), un[6], un[7]));
+                // mask bytes from the sign bits of lo: 0xFF (false) where lo
+                // is negative, then the true / false values
+                uint32_t w0 = (__byte_perm(sign_bytes2(lo[0].x, lo[0].y),
+                                           sign_bytes2(lo[1].x, lo[1].y), 0x5410) & fx) ^ tvx;
+                uint32_t w1 = (__byte_perm(sign_bytes2(lo[2].x, lo[2].y),
+                                           sign_bytes2(lo[3].x, lo[3].y), 0x5410) & fx) ^ tvx;
+                if (worst >= 0.0f) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float bound;
-                harris_estimate(ha[j], hb[j], hc[j], knf, kdf, qtf, qtb, &dv[j], &bound);
-                sure = sure && fabsf(dv[j]) > bound;
-                dv[j] = fabsf(dv[j]) > bound ? dv[j] : 0.0f;  // 0: decide exactly
-            }
-            uint32_t hit = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) hit |= (dv[j] > 0.0f ? 1u : 0u) << j;
-            if (!sure) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (dv[j] == 0.0f && harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr)
-                        hit |= 1u << j;
-            }
-            // decision bits -> bytes: x * 0x00204081 puts bit k of a 4-bit x
-            // at bit 8k (copies at offsets 0, 7, 14, 21 never overlap), times
-            // 255 gives 0xFF where the mask is true, then true / false values
-            const uint32_t fx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
-            const uint32_t fvx = ((uint32_t)p.fv & 0xFFu) * 0x01010101u;
-            uint32_t w0 = ((((hit & 15u) * 0x00204081u) & 0x01010101u) * 255u & fx) ^ fvx;
-            uint32_t w1 = ((((hit >> 4) * 0x00204081u) & 0x01010101u) * 255u & fx) ^ fvx;
-            if (!full) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (!in_rect(p.valid, xs + j, y)) {
-                        if (j < 4)
-                            w0 &= ~(0xFFu << (8 * j));
-                        else
-                            w1 &= ~(0xFFu << (8 * (j - 4)));
-                    }
-            }
-            if (mrow) {
-                if (xs + 8 <= W) {
-                    *reinterpret_cast<uint2*>(mrow + xs) = make_uint2(w0, w1);
-                } else {
-                    for (int j = 0; j < 8 && xs + j < W; ++j)
-                        mrow[xs + j] = (uint8_t)((j < 4 ? w0 : w1) >> (8 * (j & 3)));
+                    for (int j = 0; j < 8; ++j)
+                        if (un[j] >= 0.0f) {
+                            const bool t = harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr;
+                            const uint32_t v = (uint32_t)(t ? p.tv : p.fv) & 0xFFu;
+                            const int sh = 8 * (j & 3);
+                            if (j < 4)
+                                w0 = (w0 & ~(0xFFu << sh)) | (v << sh);
+                            else
+                                w1 = (w1 & ~(0xFFu << sh)) | (v << sh);
+                        }
                 }
-            }
-        } else if (producer && y < H) {
-            uint32_t mk[8];
-            float rv[8];
-            int h[3];
+                if (!full) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) h[k] = L[k][0] + L[k][1] + S[k][0] + S[k][1] + S[k][2];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j > 0) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int add = j + 2 < 8 ? S[k][j + 2] : R[k][j - 6];
-                        const int sub = j - 3 >= 0 ? S[k][j - 3] : L[k][j - 1];
-                        h[k] += add - sub;
-                    }
+                    for (int j = 0; j < 8; ++j)
+                        if (!in_rect(p.valid, xs + j, y)) {
+                            if (j < 4)
+                                w0 &= ~(0xFFu << (8 * j));
+                            else
+                                w1 &= ~(0xFFu << (8 * (j - 4)));
+                        }
                 }
-                const bool ok = full || in_rect(p.valid, xs + j, y);
-                bool hit;
-                if (TOMASI) {  // binary32 response, as the point operator computes it
-                    if (rrow) {
-                        const float t = tomasi_response_f32(h[0], h[1], h[2]);
-                        hit = t > p.thr_f;
-                        rv[j] = ok ? t : 0.0f;
+                if (mrow) {
+                    if (xs + 8 <= W) {
+                        *reinterpret_cast<uint2*>(mrow + xs) = make_uint2(w0, w1);
                     } else {
-                        hit = tomasi_above(h[0], h[1], h[2], p.thr_f);
+                        for (int j = 0; j < 8 && xs + j < W; ++j)
+                            mrow[xs + j] = (uint8_t)((j < 4 ? w0 : w1) >> (8 * (j & 3)));
                     }
-                } else if (rrow) {  // the response is exported: exact q for both
-                    const long long qv = harris_q32(h[0], h[1], h[2], kn, kd);
-                    hit = qv > p.q_thr;
-                    rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
-                } else {
-                    hit = harris_above(h[0], h[1], h[2], knf, kdf, qtf, qtb, kn, kd, p.q_thr);
                 }
-                mk[j] = ok ? (hit ? (uint32_t)p.tv : (uint32_t)p.fv) : 0u;
-            }
-            if (mrow) {
-                if (xs + 8 <= W) {
-                    *reinterpret_cast<uint2*>(mrow + xs) =
-                        make_uint2(mk[0] | (mk[1] << 8) | (mk[2] << 16) | (mk[3] << 24),
-                                   mk[4] | (mk[5] << 8) | (mk[6] << 16) | (mk[7] << 24));
-                } else {
-                    for (int j = 0; j < 8 && xs + j < W; ++j) mrow[xs + j] = (uint8_t)mk[j];
+            } else {
+                uint32_t mk[8];
+                float rv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool ok = full || in_rect(p.valid, xs + j, y);
+                    bool hit;
+                    if (TOMASI) {  // binary32 response, as the point operator computes it
+                        if (rrow) {
+                            const float t = tomasi_response_f32(ha[j], hb[j], hc[j]);
+                            hit = t > p.thr_f;
+                            rv[j] = ok ? t : 0.0f;
+                        } else {
+                            hit = tomasi_above(ha[j], hb[j], hc[j], p.thr_f);
+                        }
+                    } else {  // the response is exported: exact q for both
+                        const long long qv = harris_q32(ha[j], hb[j], hc[j], kn, kd);
+                        hit = qv > p.q_thr;
+                        rv[j] = ok ? ratio_to_float(qv, p.kd) : 0.0f;
+                    }
+                    mk[j] = ok ? (hit ? (uint32_t)p.tv : (uint32_t)p.fv) & 0xFFu : 0u;
                 }
-            }
-            if (rrow) {
-                if (xs + 8 <= W) {
-                    float4* d4 = reinterpret_cast<float4*>(rrow + xs);
-                    d4[0] = make_float4(rv[0], rv[1], rv[2], rv[3]);
-                    d4[1] = make_float4(rv[4], rv[5], rv[6], rv[7]);
-                } else {
-                    for (int j = 0; j < 8 && xs + j < W; ++j) rrow[xs + j] = rv[j];
+                if (mrow) {
+                    if (xs + 8 <= W) {
+                        *reinterpret_cast<uint2*>(mrow + xs) =
+                            make_uint2(mk[0] | (mk[1] << 8) | (mk[2] << 16) | (mk[3] << 24),
+                                       mk[4] | (mk[5] << 8) | (mk[6] << 16) | (mk[7] << 24));
+                    } else {
+                        for (int j = 0; j < 8 && xs + j < W; ++j) mrow[xs + j] = (uint8_t)mk[j];
+                    }
+                }
+                if (rrow) {
+                    if (xs + 8 <= W) {
+                        float4* d4 = reinterpret_cast<float4*>(rrow + xs);
+                        d4[0] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+                        d4[1] = make_float4(rv[4], rv[5], rv[6], rv[7]);
+                    } else {
+                        for (int j = 0; j < 8 && xs + j < W; ++j) rrow[xs + j] = rv[j];
+                    }
                 }
             }
         }
@@ -610,7 +694,16 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
         // gradient row y - 2 leaves the window
         const uint4 o0 = ring[2 * so + 0], o1 = ring[2 * so + 1];
         const uint32_t O[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
-        accumulate<-1>(O, S);
+        sub_products(O, V);
+    };
+    // three rows per trip: the input windows rotate by renaming
+#pragma unroll 1
+    for (int i = 0; i < R; i += 3) {
+        step(A, B, C, i);
+        if (i + 1 >= R) break;
+        step(B, C, A, i + 1);
+        if (i + 2 >= R) break;
+        step(C, A, B, i + 2);
     }
 }
 
@@ -638,7 +731,14 @@ __global__ void __launch_bounds__(FTHREADS, 4)
     const int local = t - __ldg(tile_start + i), tx = __ldg(tiles_x + i);
     const int ty = local / tx;
     if (threadIdx.x == 0) tensormap_acquire(maps + i);
-    harris_fast_tile<TOMASI>(maps + i, ps[i], sm, (local - ty * tx) * FTW, ty * 8 * ps[i].rows);
+    // the image's parameters into shared memory: the row loop reads them
+    // there instead of from global memory
+    constexpr int PW = (int)(sizeof(HarrisParams) / 4);
+    if (threadIdx.x < PW)
+        reinterpret_cast<uint32_t*>(&sm.prm)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint32_t*>(ps + i) + threadIdx.x);
+    __syncthreads();
+    harris_fast_tile<TOMASI>(maps + i, sm.prm, sm, (local - ty * tx) * FTW, ty * 8 * sm.prm.rows);
 }
 
 }  // namespace

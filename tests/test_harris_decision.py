@@ -1,7 +1,8 @@
 """The BORDER_UNDEFINED Harris kernel decides q > q_thr (q = kd (a b - c^2) -
 kn (a + b)^2, the exact integer form of R > T) in binary32 when the computed
 value is farther from the threshold than an error bound, and exactly in 64-bit
-integers otherwise.  This file replays that binary32 procedure operation by
+integers otherwise, two pixels per packed (f32x2) operation.  This file
+replays that binary32 procedure operation by
 operation (numpy float32 arithmetic is IEEE round-to-nearest; each fused
 multiply-add is rounded once from its exact value) and checks that every
 decision it takes agrees with exact integer arithmetic, on random window sums
@@ -34,23 +35,27 @@ def fma32(x, y, z) -> np.float32:
     return round32(Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z)))
 
 
-def decide32(a, b, c, kn, kd, q_thr):
-    """The kernel's binary32 decision: True / False, or None (exact path)."""
-    A, B, C = F32(a), F32(b), F32(c)
-    knf, kdf = F32(kn), F32(kd)
-    qtf = F32(float(q_thr))
-    qtb = F32(abs(qtf) * F32(2.0 ** -21))
+def decide32(a, b, c, kn, kd, q_thr, kb_scale=1.0):
+    """The kernel's packed binary32 decision for one pixel (each lane of a
+    packed operation rounds as a scalar one would): True / False, or None
+    (left to the exact test).  kb_scale shrinks the bound (planted mistake)."""
+    kb = F32(F32(kd + 2 * kn) * F32(2.0 ** -19) * F32(kb_scale))
+    qt = round32(Fraction(q_thr))
+    qb = F32(abs(qt) * F32(2.0 ** -21) * F32(kb_scale))
+    n1, n2 = -(F32(kn) + kb), -(qt + qb)
+    m1, m2 = -(F32(kn) - kb), -(qt - qb)
+    A, B, C = round32(Fraction(a)), round32(Fraction(b)), round32(Fraction(c))
     P = A * B
-    D = fma32(-C, C, P)
+    CC = C * C
+    D = fma32(CC, F32(-1), P)
     S = A + B
-    V = knf * (S * S)
-    Q = fma32(kdf, D, -V)
-    M = fma32(kdf, fma32(C, C, P), V)
-    bound = fma32(F32(2.0 ** -19), M, qtb)
-    d = Q - qtf
-    if abs(d) > bound:
-        return bool(d > 0)
-    return None
+    S2 = S * S
+    lo = fma32(F32(kd), D, fma32(S2, n1, n2))
+    hi = fma32(F32(kd), D, fma32(S2, m1, m2))
+    assert lo <= hi
+    if min(-lo, hi) >= 0:
+        return None
+    return bool(lo > 0)
 
 
 def exact_q(a, b, c, kn, kd):
@@ -83,24 +88,18 @@ def test_decision_matches_exact_arithmetic():
 
 
 def test_planted_tighter_bound_fails():
-    # with a bound 2^10 times smaller the procedure must err somewhere: the
+    # with the bound 2^10 times smaller the procedure must err somewhere: the
     # check above has teeth
     rng = np.random.default_rng(3)
     wrong = 0
-    for _ in range(4000):
+    for _ in range(1500):
         a = int(rng.integers(2 ** 23, 2 ** 25))
         b = int(rng.integers(2 ** 23, 2 ** 25))
         lim = int(np.sqrt(a * b))
         c = int(rng.integers(-lim, lim + 1))
         q = exact_q(a, b, c, 1, 25)
         for q_thr in (q - 10 ** 6, q + 10 ** 6):
-            A, B, C = F32(a), F32(b), F32(c)
-            P = A * B
-            D = fma32(-C, C, P)
-            S = A + B
-            V = F32(1) * (S * S)
-            Q = fma32(F32(25), D, -V)
-            d = Q - F32(float(q_thr))
-            if d != 0 and bool(d > 0) != (q > q_thr):
+            got = decide32(a, b, c, 1, 25, q_thr, kb_scale=2.0 ** -10)
+            if got is not None and got != (q > q_thr):
                 wrong += 1
     assert wrong > 0
