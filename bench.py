@@ -171,6 +171,10 @@ def kernel_source_hash(files=EDGE_SOURCES) -> str:
 
 
 EDGE_KERNEL = "edge_batch_kernel<MASK_PHASE>"
+HARRIS_SOURCES = ["kernels_harris.cu", "device_common.cuh", "kernel_params.h", "launchers.h",
+                  "point_math.cuh"]
+HARRIS_KERNEL = "harris_fast_batch_kernel<HARRIS>"
+KERNEL_SOURCES = {EDGE_KERNEL: EDGE_SOURCES, HARRIS_KERNEL: HARRIS_SOURCES}
 
 
 def recorded_counters(kernel: str, frames: int):
@@ -183,7 +187,8 @@ def recorded_counters(kernel: str, frames: int):
             rec = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_sha256") != kernel_source_hash() or rec.get("frames") != frames:
+    if not rec or rec.get("frames") != frames or \
+            rec.get("source_sha256") != kernel_source_hash(KERNEL_SOURCES[kernel]):
         return None
     return rec
 
@@ -848,7 +853,11 @@ def measure_harris(world, rank, local, torch, cpu, steps=5, warmup=3, codegen="a
                      "step in one fused launch (hvxProcessGraphBatch)",
          "value": round(replica_mpix_s(px, world, steps, tb), 1), "unit": "Mpix/s",
          "ms_per_step": round(tb / steps * 1e3, 4), "steps": steps,
-         "roofline": hbm_roofline(2 * px, tb / steps, "harris_fast_batch_kernel"),
+         "roofline": dict(hbm_roofline(2 * px, tb / steps, "harris_fast_batch_kernel",
+                                       traffic=recorded_traffic(HARRIS_KERNEL, F)),
+                          issue=issue_roofline(px * steps / tb / 1e6,
+                                               recorded_instr_per_px(HARRIS_KERNEL, F),
+                                               clocks_b)),
          "one_launch_per_frame": {"value": round(replica_mpix_s(px, world, steps, t), 1),
                                   "unit": "Mpix/s", "ms_per_step": round(t / steps * 1e3, 4),
                                   "roofline": hbm_roofline(2 * w * h, t / steps / F,
