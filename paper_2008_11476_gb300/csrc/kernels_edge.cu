@@ -167,13 +167,13 @@ __device__ __forceinline__ uint32_t phase_pair2(float2 gx, float2 gy, const Phas
     const float2 in = __ffma2_rn(t, make_float2(kPhaseGuessB, kPhaseGuessB),
                                  make_float2(-kPhaseGuessA, -kPhaseGuessA));
     float2 y = __ffma2_rd(t, in, make_float2(12582913.0f, 12582913.0f));  // 1.5*2^23 + 1
-    y = __ffma2_rn(make_float2(__saturatef(-gx.x), __saturatef(-gx.y)),
-                   make_float2(136.0f, 136.0f), y);  // + 4 * 34 [gx < 0]
-    y = __ffma2_rn(make_float2(__saturatef(-gy.x), __saturatef(-gy.y)),
-                   make_float2(68.0f, 68.0f), y);    // + 2 * 34 [gy < 0]
-    y = __ffma2_rn(make_float2(__saturatef(fabsf(gy.x) - fabsf(gx.x)),
-                               __saturatef(fabsf(gy.y) - fabsf(gx.y))),
-                   make_float2(34.0f, 34.0f), y);    // + 34 [|gy| > |gx|]
+    // octant o = 4 [gx < 0] + 2 [gy < 0] + [|gy| > |gx|], then + 34 o
+    const float2 two = make_float2(2.0f, 2.0f);
+    float2 o = __ffma2_rn(make_float2(__saturatef(-gx.x), __saturatef(-gx.y)), two,
+                          make_float2(__saturatef(-gy.x), __saturatef(-gy.y)));
+    o = __ffma2_rn(o, two, make_float2(__saturatef(fabsf(gy.x) - fabsf(gx.x)),
+                                       __saturatef(fabsf(gy.y) - fabsf(gx.y))));
+    y = __ffma2_rn(o, make_float2(34.0f, 34.0f), y);
     const PhaseEntry ea = lut[__float_as_int(y.x) - 0x4B400000];
     const PhaseEntry eb = lut[__float_as_int(y.y) - 0x4B400000];
     const float na = __saturatef(fmaf(mx.x, ea.tan, nmn.x) * 1099511627776.0f);
@@ -384,31 +384,30 @@ __device__ __forceinline__ void g_row_any(const GPolicy& gp, const Box& in, cons
 // ---- Sobel + point operators of one output row --------------------------------------
 
 // gx, gy at x .. x + 7 from the 16 G rows above (a), at (b) and below (c),
-// as pairs (x + 2j, x + 2j + 1).  Lanes: vs <= 16320, dy = c - a + 4080 in
-// [0, 8160]; 16 gx + 16384 and 16 gy + 16320 are in [0, 32704].  A lane
-// spliced under the exponent of 2^23 is 2^23 + lane; one packed fma scales by
-// 1/16 and takes out both offsets, exactly.
+// as pairs (x + 2j, x + 2j + 1).  Lanes: vs <= 16320, dy = c - a + 4096 in
+// [16, 8176]; 16 gx + 16384 and 16 gy + 16384 are in [64, 32704].  A lane
+// spliced under the exponent of 2^19 is 2^19 + lane / 16 (the mantissa's
+// unit there is 1/16), and one packed add takes out the common offset,
+// exactly.
 __device__ __forceinline__ void sobel8(const uint32_t* a, const uint32_t* b, const uint32_t* c,
                                        float2* gx, float2* gy) {
     uint32_t vs[5], dy[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         vs[j] = a[j] + 2u * b[j] + c[j];
-        dy[j] = c[j] + 0x0FF00FF0u - a[j];
+        dy[j] = c[j] + 0x10001000u - a[j];
     }
-    const float2 s16 = make_float2(0.0625f, 0.0625f);
-    const float2 bx = make_float2(-(8388608.0f + 16384.0f) / 16, -(8388608.0f + 16384.0f) / 16);
-    const float2 by = make_float2(-(8388608.0f + 16320.0f) / 16, -(8388608.0f + 16320.0f) / 16);
+    const float2 off = make_float2(-(524288.0f + 1024.0f), -(524288.0f + 1024.0f));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t gxp = vs[j + 1] + 0x40004000u - vs[j];
         const uint32_t gyp = dy[j] + dy[j + 1] + 2u * shift_pair(dy[j], dy[j + 1]);
-        gx[j] = __ffma2_rn(make_float2(__int_as_float(__byte_perm(gxp, 0x4B00u, 0x5410)),
-                                       __int_as_float(__byte_perm(gxp, 0x4B00u, 0x5432))),
-                           s16, bx);
-        gy[j] = __ffma2_rn(make_float2(__int_as_float(__byte_perm(gyp, 0x4B00u, 0x5410)),
-                                       __int_as_float(__byte_perm(gyp, 0x4B00u, 0x5432))),
-                           s16, by);
+        gx[j] = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gxp, 0x4900u, 0x5410)),
+                                       __int_as_float(__byte_perm(gxp, 0x4900u, 0x5432))),
+                           off);
+        gy[j] = __fadd2_rn(make_float2(__int_as_float(__byte_perm(gyp, 0x4900u, 0x5410)),
+                                       __int_as_float(__byte_perm(gyp, 0x4900u, 0x5432))),
+                           off);
     }
 }
 
