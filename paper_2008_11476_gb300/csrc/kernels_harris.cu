@@ -266,9 +266,9 @@ __global__ void __launch_bounds__(HARRIS_THREADS, 3)
 //     come from the neighbouring lanes by shuffles, and exact int32
 //     horizontal 5-sums slide along the strip;
 //   * the mask alone (the benchmark's form) is decided for two pixels per
-//     packed binary32 operation between two bounds of q - q_thr, with the
-//     exact 64-bit test only for the pixels the bounds leave open; the
-//     exported response and the Shi-Tomasi test take the exact sums, as in
+//     packed binary32 operation between two bounds of q - q_thr (Shi-Tomasi:
+//     of r - T), with the exact test only for the pixels the bounds leave
+//     open; an exported response is computed exactly from the sums, as in
 //     the general kernel.
 // Every thread runs all R rows (rows below the image read box rows the TMA
 // filled with 0 and are not stored), so the shuffles always see full warps.
@@ -427,26 +427,48 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// tomasi_response_f32(a, b, c) > T for the window sums of one window of
-// squares and cross products (a, b >= 0 and a b >= c^2, so det, tr and s are
-// >= 0), decided from an estimate r' that replaces the IEEE square root and
-// division by the approximations above, unless r' is within 2^-19 r' of T.
-// Both r' and the binary32 response r are within 6e-7 (relative) of the
-// exact eigenvalue -- about ten roundings of 2^-24 and the two approximations
-// -- so a gap above 2^-19 r' (1.9e-6 r') puts r on the same side of T as r'.
-// disc = 0 makes r' NaN (0 * inf), which fails both tests and takes r.
-// tests/test_tomasi_decision.py replays the bound.
-__device__ __forceinline__ bool tomasi_above(int a, int b, int c, float T) {
-    const long long cc = (long long)c * c;
-    const long long det = (long long)a * b - cc;
-    const int d = a - b;
-    const float disc = (float)((long long)d * d + 4 * cc);
-    const float den = (float)(a + b) + disc * rsqrt_approx(disc);
-    const float r = 2.0f * (float)det * rcp_approx(den);
-    const float g = r * 0x1p-19f;
-    if (r - T > g) return true;
-    if (T - r > g) return false;
-    return tomasi_response_f32(a, b, c) > T;
+// The mask-only decision of r > T for the binary32 Shi-Tomasi response
+// r = tomasi_response_f32(a, b, c) of two pixels at once (packed binary32).
+// With A, B, C, E the window sums a, b, c and a - b converted (rounded),
+//   h = D rcp(den) - T / 2,  D = A B - C^2,  den = S + disc rsqrt(disc),
+//   S = A + B,  disc = (2C)^2 + (E^2 + 2^-100)
+// (every step rounded once; rsqrt / rcp are the hardware approximations with
+// relative errors of at most 2^-22.9 and 2^-23), lo = h - K S and hi = h + K S
+// with K = 2^-20 bracket r / 2 - T / 2: lo > 0 implies r > T, hi < 0 implies
+// r < T, otherwise the exact response decides.  With u = 2^-24: D is within
+// 2u (a + b)^2 of det = a b - c^2 (c^2 <= a b <= (a + b)^2 / 4), disc and den
+// (sums of non-negative terms) within a few u relatively, so D rcp(den) is
+// within 3.8u (a + b) of det / (a + b + sqrt(disc)) = lambda / 2, and r within
+// 5u lambda <= 2.5u (a + b) of lambda: K S = 16u (a + b) exceeds the sum 2.4
+// times.  The 2^-100 keeps disc and den positive when the window is all zero
+// (then D = 0 and h = -T / 2 exactly).  tests/test_tomasi_decision.py replays
+// the procedure with the extreme approximation errors.
+struct TomasiDecide2 {
+    float2 nth, nk, k;
+};
+
+__device__ __forceinline__ TomasiDecide2 tomasi_decide_consts(float T) {
+    TomasiDecide2 k;
+    k.nth = make_float2(-0.5f * T, -0.5f * T);
+    k.nk = make_float2(-0x1p-20f, -0x1p-20f);
+    k.k = make_float2(0x1p-20f, 0x1p-20f);
+    return k;
+}
+
+__device__ __forceinline__ void tomasi_bracket2(int a0, int a1, int b0, int b1, int c0, int c1,
+                                                const TomasiDecide2& k, float2* lo, float2* hi) {
+    const float2 A = make_float2((float)a0, (float)a1), B = make_float2((float)b0, (float)b1);
+    const float2 C = make_float2((float)c0, (float)c1);
+    const float2 E = make_float2((float)(a0 - b0), (float)(a1 - b1));
+    const float2 D = __ffma2_rn(__fmul2_rn(C, C), make_float2(-1.0f, -1.0f), __fmul2_rn(A, B));
+    const float2 S = __fadd2_rn(A, B);
+    const float2 C2 = __fadd2_rn(C, C);
+    const float2 disc =
+        __ffma2_rn(C2, C2, __ffma2_rn(E, E, make_float2(0x1p-100f, 0x1p-100f)));
+    const float2 den = __ffma2_rn(disc, make_float2(rsqrt_approx(disc.x), rsqrt_approx(disc.y)), S);
+    const float2 h = __ffma2_rn(D, make_float2(rcp_approx(den.x), rcp_approx(den.y)), k.nth);
+    *lo = __ffma2_rn(S, k.nk, h);
+    *hi = __ffma2_rn(S, k.k, h);
 }
 
 // The mask-only decision of q > q_thr for two pixels at once (packed
@@ -534,6 +556,7 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                       yb + R <= p.valid[3];
     const int kn = (int)p.kn, kd = (int)p.kd;
     const HarrisDecide2 dk = harris_decide_consts(kn, kd, p.q_thr);
+    const TomasiDecide2 tk = tomasi_decide_consts(p.thr_f);
     VSums V;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -590,17 +613,22 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
             hsums(Sb[0], L[0], Rr[0], kSqBits, ha);
             hsums(Sb[1], L[1], Rr[1], kSqBits, hb);
             hsums(Sb[2], L[2], Rr[2], kXyBits, hc);
-            if (!TOMASI && !rrow) {
+            if (!rrow) {
                 // the mask alone (the benchmark's form): the bracket of every
                 // pixel pair first, the exact test only in the rare row where
                 // a pixel is left undecided
                 float2 lo[4], hi[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    harris_bracket2(make_float2((float)ha[2 * j], (float)ha[2 * j + 1]),
-                                    make_float2((float)hb[2 * j], (float)hb[2 * j + 1]),
-                                    make_float2((float)hc[2 * j], (float)hc[2 * j + 1]), dk,
-                                    &lo[j], &hi[j]);
+                for (int j = 0; j < 4; ++j) {
+                    if (TOMASI)
+                        tomasi_bracket2(ha[2 * j], ha[2 * j + 1], hb[2 * j], hb[2 * j + 1],
+                                        hc[2 * j], hc[2 * j + 1], tk, &lo[j], &hi[j]);
+                    else
+                        harris_bracket2(make_float2((float)ha[2 * j], (float)ha[2 * j + 1]),
+                                        make_float2((float)hb[2 * j], (float)hb[2 * j + 1]),
+                                        make_float2((float)hc[2 * j], (float)hc[2 * j + 1]), dk,
+                                        &lo[j], &hi[j]);
+                }
                 // undecided: lo <= 0 <= hi, i.e. min(-lo, hi) >= 0
                 float un[8];
 #pragma unroll
@@ -620,7 +648,9 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                         if (un[j] >= 0.0f) {
-                            const bool t = harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr;
+                            const bool t =
+                                TOMASI ? tomasi_response_f32(ha[j], hb[j], hc[j]) > p.thr_f
+                                       : harris_q32(ha[j], hb[j], hc[j], kn, kd) > p.q_thr;
                             const uint32_t v = (uint32_t)(t ? p.tv : p.fv) & 0xFFu;
                             const int sh = 8 * (j & 3);
                             if (j < 4)
@@ -655,13 +685,9 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                     const bool ok = full || in_rect(p.valid, xs + j, y);
                     bool hit;
                     if (TOMASI) {  // binary32 response, as the point operator computes it
-                        if (rrow) {
-                            const float t = tomasi_response_f32(ha[j], hb[j], hc[j]);
-                            hit = t > p.thr_f;
-                            rv[j] = ok ? t : 0.0f;
-                        } else {
-                            hit = tomasi_above(ha[j], hb[j], hc[j], p.thr_f);
-                        }
+                        const float t = tomasi_response_f32(ha[j], hb[j], hc[j]);
+                        hit = t > p.thr_f;
+                        rv[j] = ok ? t : 0.0f;
                     } else {  // the response is exported: exact q for both
                         const long long qv = harris_q32(ha[j], hb[j], hc[j], kn, kd);
                         hit = qv > p.q_thr;

@@ -1,20 +1,54 @@
 """The BORDER_UNDEFINED corner kernel decides r > T for the binary32 Shi-Tomasi
-response r = tomasi_response_f32(a, b, c) (2 det / (tr + sqrt(disc)), IEEE
-square root and division) from a cheaper estimate r' when r' is farther than
-2^-19 r' from T.  r' replaces the square root by disc * rsqrt(disc) and the
-division by a multiplication with rcp(den), two hardware approximations with
-relative errors of at most 2^-22.9 and 2^-23 (PTX rsqrt.approx / rcp.approx).
+response r = tomasi_response_f32(a, b, c) (2 det / (tr + sqrt(disc)), exact
+integer det and disc, IEEE square root and division) two pixels per packed
+binary32 operation: with A, B, C, E the sums a, b, c and a - b rounded to
+binary32,
+    h = D rcp(den) - T / 2,  D = A B - C^2,  den = S + disc rsqrt(disc),
+    S = A + B,  disc = (2C)^2 + (E^2 + 2^-100),
+lo = h - 2^-20 S and hi = h + 2^-20 S; lo > 0 decides r > T, hi < 0 decides
+r < T, and the exact response decides the rest.  rsqrt and rcp are hardware
+approximations with relative errors of at most 2^-22.9 and 2^-23 (PTX
+rsqrt.approx / rcp.approx).
 
-This file replays both computations with numpy float32 (IEEE, round to
-nearest), the approximations modelled as the exact reciprocal (square root)
-times 1 + e for each extreme e, and checks that |r - r'| stays well inside
-the decision margin 2^-19 r' on window sums of squares and cross products of
-random, edge-like, corner-like and degenerate 5x5 gradient windows."""
+This file replays the procedure operation by operation (each multiply, add and
+fused multiply-add rounded once to binary32 from its exact value), the
+approximations modelled as the exact reciprocal (square root) times 1 + e for
+each extreme e, and checks every decision it takes against r > T on window
+sums of random, edge-like, corner-like, flat and degenerate 5x5 gradient
+windows, with thresholds at r and right next to it."""
+from fractions import Fraction
+
 import numpy as np
 
 F32 = np.float32
 E_RSQ = 2.0 ** -22.9
 E_RCP = 2.0 ** -23
+K = 2.0 ** -20
+
+
+def round32(x: Fraction) -> np.float32:
+    """x rounded once to binary32 (nearest, ties to even)."""
+    f = F32(float(x))
+    lo, hi = f, f
+    for _ in range(2):
+        lo = np.nextafter(lo, F32(-np.inf))
+        hi = np.nextafter(hi, F32(np.inf))
+    best, bd = None, None
+    v = lo
+    while v <= hi:
+        d = abs(Fraction(float(v)) - x)
+        if bd is None or d < bd or (d == bd and (int(v.view(np.uint32)) & 1) == 0):
+            best, bd = v, d
+        v = np.nextafter(v, F32(np.inf))
+    return best
+
+
+def fma32(x, y, z) -> np.float32:
+    return round32(Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z)))
+
+
+def mul32(x, y) -> np.float32:
+    return fma32(x, y, 0.0)
 
 
 def response(a, b, c):
@@ -29,19 +63,28 @@ def response(a, b, c):
     return F32(F32(2) * F32(det) / den)
 
 
-def estimates(a, b, c):
-    """r' for each combination of extreme approximation errors."""
-    det = a * b - c * c
-    disc = F32((a - b) * (a - b) + 4 * c * c)
-    out = []
-    for e1 in (-E_RSQ, E_RSQ):
-        for e2 in (-E_RCP, E_RCP):
-            rs = F32(1.0 / np.sqrt(float(disc)) * (1 + e1)) if disc > 0 else F32(np.inf)
-            with np.errstate(invalid="ignore"):
-                den = F32(F32(a + b) + F32(disc * rs))
-                rc = F32(1.0 / float(den) * (1 + e2)) if den > 0 else F32(np.inf)
-                out.append(F32(F32(F32(2) * F32(det)) * rc))
-    return out
+def bracket(a, b, c, T, e_rsq, e_rcp, k=K):
+    """(lo, hi) of the kernel's packed procedure for one pixel, with the
+    hardware approximations off by the relative errors e_rsq and e_rcp."""
+    A, B, C = round32(Fraction(a)), round32(Fraction(b)), round32(Fraction(c))
+    E = round32(Fraction(a - b))
+    D = fma32(mul32(C, C), -1.0, mul32(A, B))
+    S = round32(Fraction(float(A)) + Fraction(float(B)))
+    C2 = round32(2 * Fraction(float(C)))
+    disc = fma32(C2, C2, fma32(E, E, 2.0 ** -100))
+    rs = F32(1.0 / np.sqrt(float(disc)) * (1 + e_rsq))
+    den = fma32(disc, rs, S)
+    rc = F32(1.0 / float(den) * (1 + e_rcp))
+    h = fma32(D, rc, F32(-0.5 * F32(T)))
+    return fma32(S, -F32(k), h), fma32(S, F32(k), h)
+
+
+def decide(a, b, c, T, e_rsq, e_rcp, k=K):
+    lo, hi = bracket(a, b, c, T, e_rsq, e_rcp, k)
+    assert lo <= hi
+    if min(-lo, hi) >= 0:
+        return None
+    return bool(lo > 0)
 
 
 def windows(rng, n):
@@ -63,50 +106,76 @@ def windows(rng, n):
         yield (int(np.sum(gx * gx)), int(np.sum(gy * gy)), int(np.sum(gx * gy)))
 
 
-def test_estimate_within_margin():
-    rng = np.random.default_rng(7)
-    worst = 0.0
-    for a, b, c in windows(rng, 20000):
-        assert a * b >= c * c and a < 2 ** 25 and b < 2 ** 25
-        r = response(a, b, c)
-        for rp in estimates(a, b, c):
-            if np.isnan(rp):  # disc = 0: the kernel takes r itself
-                continue
-            assert rp >= 0
-            gap = abs(float(r) - float(rp))
-            if rp > 0:
-                worst = max(worst, gap / float(rp))
-            else:
-                assert r == 0
-    # the decision margin is 2^-19 r'; the replayed error (about 2^-21 at
-    # worst) stays below half of it
-    assert worst < 2.0 ** -20, worst
+
+
+ERRS = [(e1, e2) for e1 in (-E_RSQ, E_RSQ) for e2 in (-E_RCP, E_RCP)]
 
 
 def test_decisions_next_to_the_threshold():
-    # thresholds at r and its binary32 neighbours: whenever the estimate
-    # decides (gap above 2^-19 r'), it agrees with r > T
+    # thresholds at r, its binary32 neighbours, a few relative steps away and
+    # beyond the undecided band: whenever the bracket decides, it agrees with
+    # r > T; thresholds beyond the band are decided
     rng = np.random.default_rng(11)
-    for a, b, c in windows(rng, 3000):
+    undecided = far_undecided = 0
+    for a, b, c in windows(rng, 600):
+        assert a * b >= c * c and a < 2 ** 25 and b < 2 ** 25
         r = response(a, b, c)
-        for T in (r, np.nextafter(r, F32(np.inf)), np.nextafter(r, F32(-np.inf)),
-                  F32(float(r) * (1 + 2.0 ** -18)), F32(float(r) * (1 - 2.0 ** -18))):
-            for rp in estimates(a, b, c):
-                if np.isnan(rp):
+        near = (r, np.nextafter(r, F32(np.inf)), np.nextafter(r, F32(-np.inf)),
+                F32(float(r) * (1 + 2.0 ** -18)), F32(float(r) * (1 - 2.0 ** -18)))
+        # the undecided band is |r - T| <= 2 K (a + b) (plus rounding)
+        band = 2 * K * (a + b)
+        far = (F32(float(r) * 1.001 + 2 * band + 1), F32(float(r) * 0.999 - 2 * band - 1))
+        for T in near + far:
+            for e1, e2 in ERRS:
+                got = decide(a, b, c, T, e1, e2)
+                if got is None:
+                    undecided += 1
+                    far_undecided += T in far
                     continue
-                g = F32(rp * F32(2.0 ** -19))
-                if F32(rp - T) > g:
-                    assert r > T
-                elif F32(T - rp) > g:
-                    assert not r > T
+                assert got == bool(r > T), (a, b, c, float(T), e1, e2)
+    assert far_undecided == 0
+    assert undecided > 0  # the thresholds at r itself are left to the exact test
+
+
+def test_bracket_margin_holds_on_random_windows():
+    # the replayed h stays within half of the margin K S of r / 2 - T / 2
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for a, b, c in windows(rng, 1500):
+        r = float(response(a, b, c))
+        for e1, e2 in ERRS:
+            lo, hi = bracket(a, b, c, 0.0, e1, e2)
+            h = (float(lo) + float(hi)) / 2
+            if a + b > 0:
+                worst = max(worst, abs(h - r / 2) / (K * (a + b)))
+    assert worst < 0.5, worst
+
+
+def test_planted_smaller_margin_fails():
+    # with the margin 2^8 times smaller the bracket must err somewhere near the
+    # threshold: the checks above have teeth
+    rng = np.random.default_rng(5)
+    wrong = 0
+    for a, b, c in windows(rng, 400):
+        r = response(a, b, c)
+        for T in (np.nextafter(r, F32(np.inf)), np.nextafter(r, F32(-np.inf))):
+            for e1, e2 in ERRS:
+                got = decide(a, b, c, T, e1, e2, k=K * 2.0 ** -8)
+                if got is not None and got != bool(r > T):
+                    wrong += 1
+    assert wrong > 0
 
 
 def test_degenerate_windows():
-    # all-zero window: disc = 0, the estimate is NaN and the kernel takes r = 0;
-    # collinear gradients: det = 0 and both r and r' are exactly 0
+    # all-zero window: disc and den stay positive, D = 0, h = -T / 2 exactly;
+    # collinear gradients: det = 0 and r = 0
     assert response(0, 0, 0) == 0
-    assert all(np.isnan(x) for x in estimates(0, 0, 0))
+    for e1, e2 in ERRS:
+        assert decide(0, 0, 0, 5.0, e1, e2) is False
+        assert decide(0, 0, 0, -5.0, e1, e2) is True
+        assert decide(0, 0, 0, 0.0, e1, e2) is None
     a, b, c = 25 * 9, 25 * 4, 25 * 6  # gx = 3, gy = 2 everywhere
-    assert a * b == c * c
-    assert response(a, b, c) == 0
-    assert all(x == 0 for x in estimates(a, b, c))
+    assert a * b == c * c and response(a, b, c) == 0
+    for e1, e2 in ERRS:
+        assert decide(a, b, c, 1.0, e1, e2) is False
+        assert decide(a, b, c, -1.0, e1, e2) is True
