@@ -608,11 +608,15 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
             Rr[k][0] = __shfl_down_sync(0xffffffffu, Sb[k][0], 1);
             Rr[k][1] = __shfl_down_sync(0xffffffffu, Sb[k][1], 1);
         }
-        if (producer && y < H) {
-            int ha[8], hb[8], hc[8];
-            hsums(Sb[0], L[0], Rr[0], kSqBits, ha);
-            hsums(Sb[1], L[1], Rr[1], kSqBits, hb);
-            hsums(Sb[2], L[2], Rr[2], kXyBits, hc);
+        // every lane forms the sums and (mask alone) the decisions, so the
+        // common path has no divergent branch; only producers of rows inside
+        // the image store
+        const bool out = producer && y < H;
+        int ha[8], hb[8], hc[8];
+        hsums(Sb[0], L[0], Rr[0], kSqBits, ha);
+        hsums(Sb[1], L[1], Rr[1], kSqBits, hb);
+        hsums(Sb[2], L[2], Rr[2], kXyBits, hc);
+        {
             if (!rrow) {
                 // the mask alone (the benchmark's form): the bracket of every
                 // pixel pair first, the exact test only in the rare row where
@@ -659,17 +663,17 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                                 w1 = (w1 & ~(0xFFu << sh)) | (v << sh);
                         }
                 }
-                if (!full) {
+                if (out && mrow) {
+                    if (!full) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (!in_rect(p.valid, xs + j, y)) {
-                            if (j < 4)
-                                w0 &= ~(0xFFu << (8 * j));
-                            else
-                                w1 &= ~(0xFFu << (8 * (j - 4)));
-                        }
-                }
-                if (mrow) {
+                        for (int j = 0; j < 8; ++j)
+                            if (!in_rect(p.valid, xs + j, y)) {
+                                if (j < 4)
+                                    w0 &= ~(0xFFu << (8 * j));
+                                else
+                                    w1 &= ~(0xFFu << (8 * (j - 4)));
+                            }
+                    }
                     if (xs + 8 <= W) {
                         *reinterpret_cast<uint2*>(mrow + xs) = make_uint2(w0, w1);
                     } else {
@@ -677,7 +681,7 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
                             mrow[xs + j] = (uint8_t)((j < 4 ? w0 : w1) >> (8 * (j & 3)));
                     }
                 }
-            } else {
+            } else if (out) {
                 uint32_t mk[8];
                 float rv[8];
 #pragma unroll
