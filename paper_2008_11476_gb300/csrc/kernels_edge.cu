@@ -92,6 +92,10 @@ struct EdgeSmem {
     uint32_t gslow[EDGE_THREADS][5];    // per-thread result of the slow G path
     // batch of at most BATCH_SMEM_IMAGES images: its tile tables
     int ts[BATCH_SMEM_IMAGES + 1], tx[BATCH_SMEM_IMAGES];
+    // batch: warps that finished with each box stage (the last of a tile
+    // issues the stage's next load) and the last tile index loaded into it
+    unsigned released[NS];
+    int last_k[NS];
 };
 
 __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
@@ -249,6 +253,45 @@ __device__ void fix_input_border(Box& in, const EdgeParams& p, int x0, int y0, i
         const int c = (j < 2 ? j - 2 : W + j - 2) - bx;
         if (by + r >= 0 && by + r < H && c >= 0 && c < LW) put(r, c);
     }
+}
+
+// The cells of fix_input_border in box rows r0 .. r1 - 1 (every column the
+// strips read, 12 .. 147), for the batch kernel, whose warps run ahead of
+// each other without a block barrier: each warp fixes the rows its two row
+// groups read, its lanes striding over the cells, then syncs.  Windows of
+// neighbouring warps overlap in their halo rows; both write the same values,
+// each taken from a cell inside the image (which no thread writes).
+__device__ void fix_input_border_warp(Box& in, const EdgeParams& p, int x0, int y0, int r0,
+                                      int r1) {
+    if (p.border_g == HVX_BORDER_UNDEFINED) return;
+    const int W = p.W, H = p.H, bx = x0 - 16, by = y0 - 2;
+    const bool cst = p.border_g == HVX_BORDER_CONSTANT;
+    const bool rep2 = rep2_borders(p);
+    const uint8_t cv = (uint8_t)p.cval_g;
+    const int lane = threadIdx.x & 31;
+    auto src = [&](int v, int n) {  // source coordinate of v in [-2, n + 1]
+        if (v >= 0 && v < n) return v;
+        if (v < 0) return (rep2 && v == -2) ? min(1, n - 1) : 0;
+        return (rep2 && v == n + 1) ? max(n - 2, 0) : n - 1;
+    };
+    auto put = [&](int r, int cc) {
+        in[r][cc] = cst ? cv : in[src(by + r, H) - by][src(bx + cc, W) - bx];
+    };
+    constexpr int C0 = 12, NC = 136;  // columns 12 .. 147
+    // rows -2, -1, H, H + 1 among r0 .. r1 - 1: every column
+    for (int j = 0; j < 4; ++j) {
+        const int r = (j < 2 ? j - 2 : H + j - 2) - by;
+        if (r >= r0 && r < r1)
+            for (int cc = C0 + lane; cc < C0 + NC; cc += 32) put(r, cc);
+    }
+    // columns -2, -1, W, W + 1: the rows inside the image
+    const int ra = max(r0, -by), rb = min(r1, H - by);
+    for (int j = 0; j < 4; ++j) {
+        const int cc = (j < 2 ? j - 2 : W + j - 2) - bx;
+        if (cc >= C0 && cc < C0 + NC)
+            for (int r = ra + lane; r < rb; r += 32) put(r, cc);
+    }
+    __syncwarp();
 }
 
 // ---- Gaussian rows ---------------------------------------------------------------
@@ -731,20 +774,31 @@ __device__ __forceinline__ void issue_tile(EdgeSmem<STAGES>& sm, const EdgeBatch
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
 // CTA lives in box stage k mod STAGES, so the next box loads while one is
-// computed.  Each tile's parameters come from shared memory.  A wait that
-// runs out (bounded, about a second) records the error and ends the CTA,
-// after thread 0 has waited (bounded) for the copies still in flight.  R:
-// output rows per thread (tiles of 128 x 8R; a compile-time constant, so the
-// row loop's bounds and box offsets fold; the autotuner picks one per image
-// size class and launches each class with its own R).
+// computed.  Each tile's parameters come from shared memory.  The warps run
+// ahead of each other without a block barrier in the tile loop: each waits
+// for its tile's box on the stage's mbarrier, fixes the border cells its own
+// rows read (edge tiles), computes, and then counts itself out of the
+// stage; the last warp out of tile k issues tile k + STAGES into the stage
+// (every warp is then done with tile k and with the parameter slot of tile
+// k - 1 that the load reuses).  A wait that runs out (bounded, about a
+// second) records the error and ends the warp's loop; after the loop thread
+// 0 waits (bounded) for any load still in flight.  R: output rows per thread
+// (tiles of 128 x 8R; a compile-time constant, so the row loop's bounds and
+// box offsets fold; the autotuner picks one per image size class and
+// launches each class with its own R).
 template <int MODE, int R>
 __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatchDesc d) {
     static_assert(R >= 3 && R <= ROWS, "box ring holds at most 8 ROWS + 4 rows");
+    constexpr unsigned NWARPS = EDGE_THREADS / 32;
     __shared__ EdgeSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            sm.released[s] = 0u;
+            sm.last_k[s] = -1;
+        }
         fence_barrier_init();
     }
     const bool tab = d.n_img <= BATCH_SMEM_IMAGES;
@@ -758,36 +812,48 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
     if (threadIdx.x == 0)
         for (int s = 0; s < STAGES; ++s) {
             const int t = first + s * (int)gridDim.x;
-            if (t < d.total_tiles) issue_tile<R>(sm, d, tab, s, s, t);
+            if (t < d.total_tiles) {
+                sm.last_k[s] = s;
+                issue_tile<R>(sm, d, tab, s, s, t);
+            }
         }
+    const int r0 = 2 * R * (threadIdx.x >> 5);  // first box row of this warp's two row groups
+    bool failed = false;
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
         const int s = k % STAGES;
         const int ps = k % (STAGES + 1);
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
-        const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0)  // tiles k + 1 .. k + STAGES - 1 may still be loading
-                for (int j = 1; j < STAGES; ++j)
-                    if (t + j * (int)gridDim.x < d.total_tiles)
-                        mbar_wait_bounded(&sm.bar[(k + j) % STAGES],
-                                          (uint32_t)((k + j) / STAGES) & 1u, nullptr);
-            return;
+        if (!mbar_wait_bounded(&sm.bar[s], parity, d.err)) {
+            failed = true;
+            break;
         }
         const EdgeParams& p = sm.prm[ps];
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const bool interior = tile_is_interior(p, x0, y0, 8 * R);
-        if (!interior) {
-            fix_input_border(sm.in[s].b, p, x0, y0, 8 * R + 4);
-            __syncthreads();
-        }
+        if (!interior) fix_input_border_warp(sm.in[s].b, p, x0, y0, r0, r0 + 2 * R + 4);
         edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, R);
-        __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
-        if (threadIdx.x == 0) {
-            const int tn = t + STAGES * (int)gridDim.x;
-            if (tn < d.total_tiles) issue_tile<R>(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
+        // this warp is done with box s: count it out (release: its reads of
+        // the box happen before the count), the last one loads the next tile
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            __threadfence_block();
+            const unsigned prev = atomicAdd(&sm.released[s], 1u);
+            if (prev % NWARPS == NWARPS - 1) {
+                __threadfence_block();
+                const int tn = t + STAGES * (int)gridDim.x;
+                if (tn < d.total_tiles) {
+                    sm.last_k[s] = k + STAGES;
+                    issue_tile<R>(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
+                }
+            }
         }
     }
+    // a wait that ran out: no load may still be writing shared memory when the CTA ends
+    if (__syncthreads_or(failed) && threadIdx.x == 0)
+        for (int s = 0; s < STAGES; ++s)
+            if (sm.last_k[s] >= 0)
+                mbar_wait_bounded(&sm.bar[s], (uint32_t)(sm.last_k[s] / STAGES) & 1u, nullptr);
 }
 
 template <int MODE>
