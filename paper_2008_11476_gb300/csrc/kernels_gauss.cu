@@ -51,6 +51,10 @@ struct GaussSmem {
     int tx0[NS + 1], ty0[NS + 1];
     // batch of at most BATCH_SMEM_IMAGES images: its tile tables
     int ts[BATCH_SMEM_IMAGES + 1], tx[BATCH_SMEM_IMAGES];
+    // batch: warps that finished with each box stage (the last of a tile
+    // issues the stage's next load) and the last tile index loaded into it
+    unsigned released[NS];
+    int last_k[NS];
 };
 
 __device__ __forceinline__ bool tile_is_interior(const EdgeParams& p, int x0, int y0, int th) {
@@ -68,6 +72,39 @@ __device__ void fix_box_border(Box& in, const EdgeParams& p, int x0, int y0, int
         const int x = x0 - 16 + c, y = y0 - 1 + r;
         in[r][c] = cst ? cv : in[clampi(y, 0, H - 1) - (y0 - 1)][clampi(x, 0, W - 1) - (x0 - 16)];
     });
+}
+
+// fix_box_border restricted to box rows r0 .. r1 - 1 and the columns the
+// strips read (12 .. 147), for the batch kernel, whose warps run ahead of
+// each other without a block barrier: each warp fixes the rows its two row
+// groups read, lanes striding over the cells, then syncs.  Neighbouring
+// warps share halo rows; both write the same values, each taken from a cell
+// inside the image (which no thread writes).
+__device__ void fix_box_border_warp(Box& in, const EdgeParams& p, int x0, int y0, int r0,
+                                    int r1) {
+    if (p.border_g == HVX_BORDER_UNDEFINED) return;
+    const int W = p.W, H = p.H, bx = x0 - 16, by = y0 - 1;
+    const bool cst = p.border_g == HVX_BORDER_CONSTANT;
+    const uint8_t cv = (uint8_t)p.cval_g;
+    const int lane = threadIdx.x & 31;
+    auto put = [&](int r, int c) {
+        in[r][c] = cst ? cv : in[clampi(by + r, 0, H - 1) - by][clampi(bx + c, 0, W - 1) - bx];
+    };
+    constexpr int C0 = 12, C1 = 148;
+    const int ra = max(r0, -by), rb = min(r1, H - by);  // rows inside the image
+    // rows outside the image: every column
+    for (int r = r0; r < r1; ++r)
+        if (r < ra || r >= rb)
+            for (int c = C0 + lane; c < C1; c += 32) put(r, c);
+    // rows inside: the columns left and right of the image
+    const int la = C0, lb = min(C1, -bx), rca = max(C0, W - bx), rcb = C1;
+    const int nl = max(lb - la, 0), nr = max(rcb - rca, 0), n = nl + nr;
+    if (n > 0)
+        for (int i = lane; i < (rb - ra) * n; i += 32) {
+            const int r = ra + i / n, j = i - (i / n) * n;
+            put(r, j < nl ? la + j : rca + j - nl);
+        }
+    __syncwarp();
 }
 
 // Pixel pairs (x - 2, x - 1), (x, x + 1) .. (x + 8, x + 9) of one box row as
@@ -210,15 +247,24 @@ __device__ __forceinline__ void issue_tile(GaussSmem<STAGES>& sm, const EdgeBatc
 }
 
 // Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...; tile k of the
-// CTA lives in box stage k mod STAGES.  A wait that runs out (bounded, about a
-// second) records the error and ends the CTA, after thread 0 has waited
-// (bounded) for the copies still in flight.
+// CTA lives in box stage k mod STAGES.  No block barrier in the tile loop:
+// each warp waits for its tile's box on the stage's mbarrier, fixes the
+// border cells of its own rows (edge tiles), computes, and counts itself out
+// of the stage; the last warp out of tile k issues tile k + STAGES into it.
+// A wait that runs out (bounded, about a second) records the error and ends
+// the warp's loop; after the loop thread 0 waits (bounded) for any load still
+// in flight.
 __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBatchDesc d) {
+    constexpr unsigned NWARPS = GAUSS_THREADS / 32;
     __shared__ GaussSmem<STAGES> sm;
     const int first = blockIdx.x;
     if (first >= d.total_tiles) return;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            sm.released[s] = 0u;
+            sm.last_k[s] = -1;
+        }
         fence_barrier_init();
     }
     const bool tab = d.n_img <= BATCH_SMEM_IMAGES;
@@ -231,36 +277,47 @@ __global__ void __launch_bounds__(GAUSS_THREADS) gauss_batch_kernel(const EdgeBa
     if (threadIdx.x == 0)
         for (int s = 0; s < STAGES; ++s) {
             const int t = first + s * (int)gridDim.x;
-            if (t < d.total_tiles) issue_tile(sm, d, tab, s, s, t);
+            if (t < d.total_tiles) {
+                sm.last_k[s] = s;
+                issue_tile(sm, d, tab, s, s, t);
+            }
         }
+    const int r0 = 2 * ROWS * (threadIdx.x >> 5);  // first box row of this warp's row groups
+    bool failed = false;
     int k = 0;
     for (int t = first; t < d.total_tiles; t += gridDim.x, ++k) {
         const int s = k % STAGES;
         const int ps = k % (STAGES + 1);
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
-        const bool ok = mbar_wait_bounded(&sm.bar[s], parity, d.err);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0)  // tiles k + 1 .. k + STAGES - 1 may still be loading
-                for (int j = 1; j < STAGES; ++j)
-                    if (t + j * (int)gridDim.x < d.total_tiles)
-                        mbar_wait_bounded(&sm.bar[(k + j) % STAGES],
-                                          (uint32_t)((k + j) / STAGES) & 1u, nullptr);
-            return;
+        if (!mbar_wait_bounded(&sm.bar[s], parity, d.err)) {
+            failed = true;
+            break;
         }
         const EdgeParams& p = sm.prm[ps];
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const bool interior = tile_is_interior(p, x0, y0, TH);
-        if (!interior) {
-            fix_box_border(sm.in[s].b, p, x0, y0, LH);
-            __syncthreads();
-        }
+        if (!interior) fix_box_border_warp(sm.in[s].b, p, x0, y0, r0, r0 + 2 * ROWS + 2);
         gauss_tile<ROWS>(sm.in[s].b, p, x0, y0, interior);
-        __syncthreads();  // box s and parameter slot (k + STAGES) mod (STAGES + 1) are free
-        if (threadIdx.x == 0) {
-            const int tn = t + STAGES * (int)gridDim.x;
-            if (tn < d.total_tiles) issue_tile(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
+        // this warp is done with box s: count it out, the last one loads the next tile
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            __threadfence_block();
+            const unsigned prev = atomicAdd(&sm.released[s], 1u);
+            if (prev % NWARPS == NWARPS - 1) {
+                __threadfence_block();
+                const int tn = t + STAGES * (int)gridDim.x;
+                if (tn < d.total_tiles) {
+                    sm.last_k[s] = k + STAGES;
+                    issue_tile(sm, d, tab, s, (k + STAGES) % (STAGES + 1), tn);
+                }
+            }
         }
     }
+    // a wait that ran out: no load may still be writing shared memory when the CTA ends
+    if (__syncthreads_or(failed) && threadIdx.x == 0)
+        for (int s = 0; s < STAGES; ++s)
+            if (sm.last_k[s] >= 0)
+                mbar_wait_bounded(&sm.bar[s], (uint32_t)(sm.last_k[s] / STAGES) & 1u, nullptr);
 }
 
 }  // namespace
