@@ -67,6 +67,7 @@ typedef CUresult (*FnModuleGetFunction)(CUfunction*, CUmodule, const char*);
 typedef CUresult (*FnFuncSetAttribute)(CUfunction, CUfunction_attribute, int);
 typedef CUresult (*FnLaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
                                    unsigned, unsigned, CUstream, void**, void**);
+typedef CUresult (*FnLaunchKernelEx)(const CUlaunchConfig*, CUfunction, void**, void**);
 
 struct Nvrtc {
     bool ok = false;
@@ -118,6 +119,7 @@ struct Driver {
     FnModuleGetFunction get = nullptr;
     FnFuncSetAttribute attr = nullptr;
     FnLaunchKernel launch = nullptr;
+    FnLaunchKernelEx launch_ex = nullptr;  // optional: programmatic dependent launches
 };
 
 Driver& driver() {
@@ -139,6 +141,7 @@ Driver& driver() {
         d.get = (FnModuleGetFunction)entry("cuModuleGetFunction");
         d.attr = (FnFuncSetAttribute)entry("cuFuncSetAttribute");
         d.launch = (FnLaunchKernel)entry("cuLaunchKernel");
+        d.launch_ex = (FnLaunchKernelEx)entry("cuLaunchKernelEx");
         d.ok = d.load && d.get && d.attr && d.launch;
     });
     return d;
@@ -1479,6 +1482,10 @@ struct Emitter {
         o << "}\n\n"
           << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << min_blocks()
           << ") hvx_generated(const __grid_constant__ HvxJitParams p) {\n"
+          << "  // a programmatic dependent launch: no global-memory access before the\n"
+          << "  // previous grid on the stream has completed\n"
+          << "  asm volatile(\"griddepcontrol.launch_dependents;\");\n"
+          << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
           << "  extern __shared__ __align__(16) int smem[];\n"
           << "  const int tx = blockIdx.x, ty = blockIdx.y;\n"
           << "  if (tx >= p.ix0 && tx <= p.ix1 && ty >= p.iy0 && ty <= p.iy1)\n"
@@ -1676,8 +1683,30 @@ bool jit_prepare(const GenericDesc& d, const std::vector<std::string>& user_code
 
 cudaError_t jit_launch(const JitLaunch& j, cudaStream_t s) {
     void* args[] = {const_cast<HvxJitParams*>(&j.p)};
-    const CUresult r = driver().launch(j.k->fn, j.gx, j.gy, 1, kThreads, 1, 1,
-                                       (unsigned)j.k->smem_bytes, (CUstream)s, args, nullptr);
+    const Driver& dr = driver();
+    CUresult r;
+    if (dr.launch_ex) {
+        // programmatic stream serialisation: the launch may begin while the
+        // previous kernel on the stream finishes (the kernel waits for it)
+        CUlaunchAttribute attr = {};
+        attr.id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+        attr.value.programmaticStreamSerializationAllowed = 1;
+        CUlaunchConfig cfg = {};
+        cfg.gridDimX = j.gx;
+        cfg.gridDimY = j.gy;
+        cfg.gridDimZ = 1;
+        cfg.blockDimX = kThreads;
+        cfg.blockDimY = 1;
+        cfg.blockDimZ = 1;
+        cfg.sharedMemBytes = (unsigned)j.k->smem_bytes;
+        cfg.hStream = (CUstream)s;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        r = dr.launch_ex(&cfg, j.k->fn, args, nullptr);
+    } else {
+        r = dr.launch(j.k->fn, j.gx, j.gy, 1, kThreads, 1, 1, (unsigned)j.k->smem_bytes,
+                      (CUstream)s, args, nullptr);
+    }
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 

@@ -14,6 +14,36 @@ namespace hvx {
 namespace dev {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Single-image kernels are launched with
+// programmatic stream serialisation (launch_pdl): a launch may begin while
+// the previous kernel on its stream is still running, so such a kernel lets
+// the next launch begin (pdl_launch_dependents) and waits for the previous
+// grid to complete and its memory to be visible (pdl_wait) before its first
+// global-memory access.  In a launch without the attribute both are no-ops.
+
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // TMA and mbarrier
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

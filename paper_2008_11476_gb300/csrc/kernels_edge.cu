@@ -725,11 +725,15 @@ __global__ void __launch_bounds__(EDGE_THREADS)
     __shared__ EdgeSmem<1> sm;
     const int rows = p.rows, th = 8 * rows;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * th;
+    // a programmatic dependent launch (launch_pdl): the table is built while
+    // the previous grid on the stream finishes, global memory only after it
+    pdl_launch_dependents();
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
     build_phase_lut(sm.plut);
+    pdl_wait();
     __syncthreads();
     if (threadIdx.x == 0)
         issue_box(sm.in[0].b, &sm.bar[0], &tmap, x0, y0, (uint32_t)(LW * (th + 4)));
@@ -860,8 +864,7 @@ template <int MODE>
 cudaError_t launch_mode(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
     const int th = 8 * p.rows;
     dim3 grid((p.W + TW - 1) / TW, (p.H + th - 1) / th);
-    edge_kernel<MODE><<<grid, EDGE_THREADS, 0, s>>>(map, p);
-    return cudaGetLastError();
+    return launch_pdl(edge_kernel<MODE>, grid, dim3(EDGE_THREADS), 0, s, map, p);
 }
 
 template <int MODE>

@@ -200,10 +200,14 @@ __global__ void __launch_bounds__(GAUSS_THREADS)
     static_assert(R >= 1 && R <= ROWS, "the box holds at most 8 ROWS + 2 rows");
     __shared__ GaussSmem<1> sm;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * 8 * R;
+    // a programmatic dependent launch (launch_pdl): no global-memory access
+    // before the previous grid on the stream has completed
+    pdl_launch_dependents();
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         fence_barrier_init();
     }
+    pdl_wait();
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&sm.bar[0], (uint32_t)(LW * (8 * R + 2)));
@@ -326,11 +330,10 @@ cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream
     const int R = p.rows == 2 || p.rows == 5 ? p.rows : ROWS;
     dim3 grid((p.W + TW - 1) / TW, (p.H + 8 * R - 1) / (8 * R));
     switch (R) {
-        case 2: gauss_kernel<2><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
-        case 5: gauss_kernel<5><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
-        default: gauss_kernel<ROWS><<<grid, GAUSS_THREADS, 0, s>>>(map, p); break;
+        case 2: return launch_pdl(gauss_kernel<2>, grid, dim3(GAUSS_THREADS), 0, s, map, p);
+        case 5: return launch_pdl(gauss_kernel<5>, grid, dim3(GAUSS_THREADS), 0, s, map, p);
+        default: return launch_pdl(gauss_kernel<ROWS>, grid, dim3(GAUSS_THREADS), 0, s, map, p);
     }
-    return cudaGetLastError();
 }
 
 // Rows per thread of the single-image Gaussian kernel (tiles of 128 x 8R):

@@ -249,6 +249,8 @@ __device__ __forceinline__ int32_t buf_at(const GenericDesc& d, const int32_t* s
 }
 
 __global__ void __launch_bounds__(GEN_THREADS) generic_kernel(const GenericDesc d) {
+    pdl_launch_dependents();  // launched by launch_pdl
+    pdl_wait();
     extern __shared__ int32_t s[];
     const int x0 = blockIdx.x * GEN_TW, y0 = blockIdx.y * GEN_TH;
     const int W = d.W, H = d.H;
@@ -329,8 +331,7 @@ cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s) {
         attr_bytes = smem;
     }
     dim3 grid((d.W + GEN_TW - 1) / GEN_TW, (d.H + GEN_TH - 1) / GEN_TH);
-    generic_kernel<<<grid, GEN_THREADS, smem, s>>>(d);
-    return cudaGetLastError();
+    return launch_pdl(generic_kernel, grid, dim3(GEN_THREADS), (size_t)smem, s, d);
 }
 
 }  // namespace hvx

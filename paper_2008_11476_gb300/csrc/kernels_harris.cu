@@ -71,6 +71,8 @@ __device__ __forceinline__ int4 sub4(int4 a, int4 b) {
 
 __global__ void __launch_bounds__(HARRIS_THREADS, 3)
     harris_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
+    pdl_launch_dependents();  // launched by launch_pdl
+    pdl_wait();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     HarrisSmem& sm = *reinterpret_cast<HarrisSmem*>(smem_raw);
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
@@ -740,6 +742,8 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
 template <bool TOMASI>
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
+    pdl_launch_dependents();  // launched by launch_pdl
+    pdl_wait();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
     harris_fast_tile<TOMASI>(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
@@ -863,13 +867,12 @@ cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStr
         if (p.tomasi) {
             cudaError_t e = set_fast_smem(harris_fast_kernel<true>, fast_attr[1]);
             if (e != cudaSuccess) return e;
-            harris_fast_kernel<true><<<grid, FTHREADS, smem, s>>>(map, p);
+            return launch_pdl(harris_fast_kernel<true>, grid, dim3(FTHREADS), smem, s, map, p);
         } else {
             cudaError_t e = set_fast_smem(harris_fast_kernel<false>, fast_attr[0]);
             if (e != cudaSuccess) return e;
-            harris_fast_kernel<false><<<grid, FTHREADS, smem, s>>>(map, p);
+            return launch_pdl(harris_fast_kernel<false>, grid, dim3(FTHREADS), smem, s, map, p);
         }
-        return cudaGetLastError();
     }
     static bool attr_set = false;
     const int smem = (int)sizeof(HarrisSmem);
@@ -880,8 +883,7 @@ cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStr
         attr_set = true;
     }
     dim3 grid((p.W + TW - 1) / TW, (p.H + TH - 1) / TH);
-    harris_kernel<<<grid, HARRIS_THREADS, smem, s>>>(map, p);
-    return cudaGetLastError();
+    return launch_pdl(harris_kernel, grid, dim3(HARRIS_THREADS), smem, s, map, p);
 }
 
 }  // namespace hvx

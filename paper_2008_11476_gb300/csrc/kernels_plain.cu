@@ -95,6 +95,8 @@ __device__ __forceinline__ void store4(const PlainImg& im, int x, int y, int W, 
 }
 
 __global__ void __launch_bounds__(PT_THREADS) point_kernel(const PlainParams p) {
+    pdl_launch_dependents();  // launched by launch_pdl
+    pdl_wait();
     const int x = (blockIdx.x * PT_THREADS + threadIdx.x) * 4;
     const int y = blockIdx.y;
     const int W = p.W;
@@ -115,6 +117,8 @@ __global__ void __launch_bounds__(PT_THREADS) point_kernel(const PlainParams p) 
 // U (i0 = 1) or V (i0 = 2) plane of a UYVY image: output pixel x is byte
 // 4x (U) or 4x + 2 (V) of the input row.
 __global__ void __launch_bounds__(PT_THREADS) chx_uv_kernel(const PlainParams p) {
+    pdl_launch_dependents();  // launched by launch_pdl
+    pdl_wait();
     const int x = blockIdx.x * PT_THREADS + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= (int)p.W) return;
@@ -129,12 +133,10 @@ __global__ void __launch_bounds__(PT_THREADS) chx_uv_kernel(const PlainParams p)
 cudaError_t launch_plain(const PlainParams& p, cudaStream_t s) {
     if (p.op == OP_CHX && p.i0 != HVX_CHANNEL_Y) {
         dim3 grid((p.W + PT_THREADS - 1) / PT_THREADS, p.H);
-        chx_uv_kernel<<<grid, PT_THREADS, 0, s>>>(p);
-    } else {
-        dim3 grid((p.W + 4 * PT_THREADS - 1) / (4 * PT_THREADS), p.H);
-        point_kernel<<<grid, PT_THREADS, 0, s>>>(p);
+        return launch_pdl(chx_uv_kernel, grid, dim3(PT_THREADS), 0, s, p);
     }
-    return cudaGetLastError();
+    dim3 grid((p.W + 4 * PT_THREADS - 1) / (4 * PT_THREADS), p.H);
+    return launch_pdl(point_kernel, grid, dim3(PT_THREADS), 0, s, p);
 }
 
 }  // namespace hvx
