@@ -525,12 +525,16 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
     // A pipeline over parts of the batch: part j's uploads (copy stream in),
     // its launches (the caller's stream), its downloads (copy stream out), so
     // that part j + 1's uploads and part j - 1's downloads overlap part j's
-    // kernels.  The caller's stream waits for the last download at the end.
+    // kernels.  Uploads are paced: part j's begin once part j - 2's downloads
+    // have begun, so that they spread over the downloads instead of taking
+    // the shared host link while the downloads (the larger direction for
+    // graphs with more output than input bytes) wait.  The caller's stream
+    // waits for the last download at the end.
     const int parts = std::min(n, 8);
     if (!ctx->io_in && (cudaStreamCreateWithFlags(&ctx->io_in, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking) != cudaSuccess))
         return HVX_ERROR_DEVICE;
-    while ((int)ctx->io_events.size() < 2 * parts + 1) {
+    while ((int)ctx->io_events.size() < 3 * parts + 2) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HVX_ERROR_DEVICE;
         ctx->io_events.push_back(e);
@@ -560,7 +564,11 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
     }
     for (int j = 0; j < parts; ++j) {
         const int a = (int)((int64_t)n * j / parts), b = (int)((int64_t)n * (j + 1) / parts);
-        cudaEvent_t uploaded = ctx->io_events[1 + 2 * j], computed = ctx->io_events[2 + 2 * j];
+        cudaEvent_t uploaded = ctx->io_events[1 + 3 * j], computed = ctx->io_events[2 + 3 * j];
+        cudaEvent_t downloading = ctx->io_events[3 + 3 * j];
+        if (j >= 2 && (e = cudaStreamWaitEvent(ctx->io_in, ctx->io_events[3 + 3 * (j - 2)], 0)) !=
+                          cudaSuccess)
+            return cuda_status(e);
         hvx_status st = host_copies(up[j], true, ctx->io_in);
         if (st != HVX_SUCCESS) return st;
         if ((e = cudaEventRecord(uploaded, ctx->io_in)) != cudaSuccess ||
@@ -569,12 +577,13 @@ hvx_status hvxScheduleGraphBatchHost(const hvx_graph* gs, int32_t n, const hvx_h
         st = process_batch(ctx, v.data() + a, b - a, s);
         if (st != HVX_SUCCESS) return st;
         if ((e = cudaEventRecord(computed, s)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ctx->io_out, computed, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(ctx->io_out, computed, 0)) != cudaSuccess ||
+            (e = cudaEventRecord(downloading, ctx->io_out)) != cudaSuccess)
             return cuda_status(e);
         st = host_copies(down[j], false, ctx->io_out);
         if (st != HVX_SUCCESS) return st;
     }
-    cudaEvent_t done = ctx->io_events[2 * parts];
+    cudaEvent_t done = ctx->io_events[3 * parts + 1];
     if ((e = cudaEventRecord(done, ctx->io_out)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s, done, 0)) != cudaSuccess)
         return cuda_status(e);
