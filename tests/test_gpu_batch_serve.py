@@ -111,6 +111,32 @@ def test_batch_gaussian_only(ctx):
         np.testing.assert_array_equal(PG.download(o), O.gaussian3x3(img).data)
 
 
+@pytest.mark.parametrize("border", [H.HVX_BORDER_REPLICATE, H.HVX_BORDER_CONSTANT,
+                                    H.HVX_BORDER_UNDEFINED])
+def test_batch_gaussian_every_border(ctx, border):
+    # the persistent Gaussian kernel, whose warps fix the border cells of
+    # their own rows without a block barrier: edge tiles on all four sides,
+    # ragged tiles, images smaller than a tile, every border mode, exact
+    sizes = [(1, 1), (7, 3), (128, 120), (129, 121), (300, 250), (1000, 241)]
+    B = {H.HVX_BORDER_REPLICATE: O.BORDER_REPLICATE, H.HVX_BORDER_CONSTANT: O.BORDER_CONSTANT,
+         H.HVX_BORDER_UNDEFINED: O.BORDER_UNDEFINED}[border]
+    outs, graphs = [], []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=80 + i)
+        o = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        graphs.append(PG.gaussian_graph(ctx, PG.upload(ctx, img, H.HVX_DF_U8), o, border=border,
+                                        cval=201))
+        outs.append((img, o))
+    assert PG.kernel_kinds(graphs[0]) == ["gaussian3x3_tma"]
+    H.hvxProcessGraphBatch(graphs)
+    H.hvxWaitBatch(ctx)
+    for img, o in outs:
+        ref = O.gaussian3x3(img, B, 201)
+        got = PG.download(o)
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(got[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+
+
 def test_batch_mixed_kinds_falls_back_to_sequential(ctx):
     img = synth.rects_noise(100, 60, 70)
     inp = PG.upload(ctx, img, H.HVX_DF_U8)
