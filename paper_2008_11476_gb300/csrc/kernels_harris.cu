@@ -531,7 +531,9 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 }
 
 // One 112 x 8R output tile at (x0, y0) of the image that `tmap` / `p` describe.
-template <bool TOMASI>
+// RESP: the launch may export the response (p.resp); without it the row loop
+// holds only the mask path, which keeps the loop body small.
+template <bool TOMASI, bool RESP>
 __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const HarrisParams& p,
                                                  FastSmem& sm, int x0, int y0) {
     const int R = p.rows;
@@ -584,7 +586,7 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
         }
     }
     uint8_t* mrow = p.mask ? p.mask + (size_t)yb * p.mask_pitch : nullptr;
-    float* rrow = p.resp ? reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(p.resp) +
+    float* rrow = RESP && p.resp ? reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(p.resp) +
                                                     (size_t)yb * p.resp_pitch)
                          : nullptr;
     const uint32_t fx = ((uint32_t)(p.tv ^ p.fv) & 0xFFu) * 0x01010101u;
@@ -619,7 +621,7 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
         hsums(Sb[1], L[1], Rr[1], kSqBits, hb);
         hsums(Sb[2], L[2], Rr[2], kXyBits, hc);
         {
-            if (!rrow) {
+            if (!RESP || !rrow) {
                 // the mask alone (the benchmark's form): the bracket of every
                 // pixel pair first, the exact test only in the rare row where
                 // a pixel is left undecided
@@ -739,21 +741,22 @@ __device__ __forceinline__ void harris_fast_tile(const CUtensorMap* tmap, const 
     }
 }
 
-template <bool TOMASI>
+template <bool TOMASI, bool RESP>
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_kernel(const __grid_constant__ CUtensorMap tmap, const HarrisParams p) {
     pdl_launch_dependents();  // launched by launch_pdl
     pdl_wait();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     FastSmem& sm = *reinterpret_cast<FastSmem*>(smem_raw);
-    harris_fast_tile<TOMASI>(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
+    harris_fast_tile<TOMASI, RESP>(&tmap, p, sm, blockIdx.x * FTW, blockIdx.y * 8 * p.rows);
 }
 
 // Several images in one launch (hvxProcessGraphBatch): block t is tile
 // t - tile_start[i] of the last image i with tile_start[i] <= t; tensor maps
 // and parameters in global memory, all images with the same rows per thread
-// and the same response (Harris or Shi-Tomasi: TOMASI).
-template <bool TOMASI>
+// and the same response (Harris or Shi-Tomasi: TOMASI); RESP: some image
+// exports its response.
+template <bool TOMASI, bool RESP>
 __global__ void __launch_bounds__(FTHREADS, 4)
     harris_fast_batch_kernel(const CUtensorMap* __restrict__ maps,
                              const HarrisParams* __restrict__ ps, const int* __restrict__ tile_start,
@@ -772,7 +775,8 @@ __global__ void __launch_bounds__(FTHREADS, 4)
         reinterpret_cast<uint32_t*>(&sm.prm)[threadIdx.x] =
             __ldg(reinterpret_cast<const uint32_t*>(ps + i) + threadIdx.x);
     __syncthreads();
-    harris_fast_tile<TOMASI>(maps + i, sm.prm, sm, (local - ty * tx) * FTW, ty * 8 * sm.prm.rows);
+    harris_fast_tile<TOMASI, RESP>(maps + i, sm.prm, sm, (local - ty * tx) * FTW,
+                                   ty * 8 * sm.prm.rows);
 }
 
 }  // namespace
@@ -840,39 +844,45 @@ cudaError_t set_fast_smem(K kernel, std::atomic<bool>& done) {
 }
 }  // namespace
 
+template <bool TOMASI, bool RESP>
+cudaError_t launch_harris_batch_t(const CUtensorMap* maps, const HarrisParams* ps,
+                                  const int* tile_start, const int* tiles_x, int n, int total,
+                                  cudaStream_t s) {
+    static std::atomic<bool> attr{false};
+    cudaError_t e = set_fast_smem(harris_fast_batch_kernel<TOMASI, RESP>, attr);
+    if (e != cudaSuccess) return e;
+    harris_fast_batch_kernel<TOMASI, RESP><<<total, FTHREADS, (int)sizeof(FastSmem), s>>>(
+        maps, ps, tile_start, tiles_x, n);
+    return cudaGetLastError();
+}
+
+template <bool TOMASI, bool RESP>
+cudaError_t launch_harris_fast_t(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s) {
+    static std::atomic<bool> attr{false};
+    cudaError_t e = set_fast_smem(harris_fast_kernel<TOMASI, RESP>, attr);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.W + FTW - 1) / FTW, (p.H + 8 * p.rows - 1) / (8 * p.rows));
+    return launch_pdl(harris_fast_kernel<TOMASI, RESP>, grid, dim3(FTHREADS), sizeof(FastSmem), s,
+                      map, p);
+}
+
 cudaError_t launch_harris_batch(const CUtensorMap* maps, const HarrisParams* ps,
                                 const int* tile_start, const int* tiles_x, int n, int total,
-                                bool tomasi, cudaStream_t s) {
-    static std::atomic<bool> attr[2] = {false, false};
-    const int smem = (int)sizeof(FastSmem);
-    if (tomasi) {
-        cudaError_t e = set_fast_smem(harris_fast_batch_kernel<true>, attr[1]);
-        if (e != cudaSuccess) return e;
-        harris_fast_batch_kernel<true><<<total, FTHREADS, smem, s>>>(maps, ps, tile_start,
-                                                                     tiles_x, n);
-    } else {
-        cudaError_t e = set_fast_smem(harris_fast_batch_kernel<false>, attr[0]);
-        if (e != cudaSuccess) return e;
-        harris_fast_batch_kernel<false><<<total, FTHREADS, smem, s>>>(maps, ps, tile_start,
-                                                                      tiles_x, n);
-    }
-    return cudaGetLastError();
+                                bool tomasi, bool resp, cudaStream_t s) {
+    if (tomasi)
+        return resp ? launch_harris_batch_t<true, true>(maps, ps, tile_start, tiles_x, n, total, s)
+                    : launch_harris_batch_t<true, false>(maps, ps, tile_start, tiles_x, n, total, s);
+    return resp ? launch_harris_batch_t<false, true>(maps, ps, tile_start, tiles_x, n, total, s)
+                : launch_harris_batch_t<false, false>(maps, ps, tile_start, tiles_x, n, total, s);
 }
 
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s) {
     if (harris_fast_path(p)) {
-        static std::atomic<bool> fast_attr[2] = {false, false};
-        const int smem = (int)sizeof(FastSmem);
-        dim3 grid((p.W + FTW - 1) / FTW, (p.H + 8 * p.rows - 1) / (8 * p.rows));
-        if (p.tomasi) {
-            cudaError_t e = set_fast_smem(harris_fast_kernel<true>, fast_attr[1]);
-            if (e != cudaSuccess) return e;
-            return launch_pdl(harris_fast_kernel<true>, grid, dim3(FTHREADS), smem, s, map, p);
-        } else {
-            cudaError_t e = set_fast_smem(harris_fast_kernel<false>, fast_attr[0]);
-            if (e != cudaSuccess) return e;
-            return launch_pdl(harris_fast_kernel<false>, grid, dim3(FTHREADS), smem, s, map, p);
-        }
+        if (p.tomasi)
+            return p.resp ? launch_harris_fast_t<true, true>(map, p, s)
+                          : launch_harris_fast_t<true, false>(map, p, s);
+        return p.resp ? launch_harris_fast_t<false, true>(map, p, s)
+                      : launch_harris_fast_t<false, false>(map, p, s);
     }
     static bool attr_set = false;
     const int smem = (int)sizeof(HarrisSmem);

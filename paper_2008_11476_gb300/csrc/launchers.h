@@ -52,10 +52,11 @@ int harris_fast_rows(int W, int H, int num_sms);
 void harris_box(const HarrisParams& p, int* w, int* h);
 cudaError_t launch_harris(const CUtensorMap& map, const HarrisParams& p, cudaStream_t s);
 // BORDER_UNDEFINED Harris over n images in one launch (every image's rows
-// equal; tensor maps boxed for them); total = tile_start[n]
+// equal; tensor maps boxed for them); total = tile_start[n]; resp: some
+// image exports its response
 cudaError_t launch_harris_batch(const CUtensorMap* maps, const HarrisParams* ps,
                                 const int* tile_start, const int* tiles_x, int n, int total,
-                                bool tomasi, cudaStream_t s);
+                                bool tomasi, bool resp, cudaStream_t s);
 int harris_fast_tile_w();
 int harris_batch_rows(const int* W, const int* H, int n, int num_sms);
 cudaError_t launch_generic(const GenericDesc& d, cudaStream_t s);

@@ -745,6 +745,7 @@ struct BatchEntry {
     int n = 0, total_tiles = 0;
     bool harris = false;  // BORDER_UNDEFINED corner batch: one direct launch
     bool tomasi = false;  // ... of the Shi-Tomasi kernel
+    bool resp = false;    // ... where some image exports its response
     std::vector<int> rows;  // edge batch: rows per thread of each image's tiles
     std::vector<void*> more_dmem;  // edge batch split by size class: the other tables
 };
@@ -1148,6 +1149,8 @@ hvx_status build_harris_batch_entry(Context* ctx, Graph* const* gs, int n, Batch
     out.dmem = dmem;
     out.harris = true;
     out.tomasi = gs[0]->plan.groups[0].harris.tomasi != 0;
+    out.resp = false;
+    for (int i = 0; i < n; ++i) out.resp = out.resp || gs[i]->plan.groups[0].harris.resp != nullptr;
     out.n = n;
     out.total_tiles = tile_start[n];
     return HVX_SUCCESS;
@@ -1267,7 +1270,7 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
             reinterpret_cast<const CUtensorMap*>(base),
             reinterpret_cast<const HarrisParams*>(base + params_off),
             reinterpret_cast<const int*>(base + tiles_off), reinterpret_cast<const int*>(base + tx_off),
-            hit->n, hit->total_tiles, hit->tomasi, s));
+            hit->n, hit->total_tiles, hit->tomasi, hit->resp, s));
     }
     return cuda_status(cudaGraphLaunch(hit->exec, s));
 }
