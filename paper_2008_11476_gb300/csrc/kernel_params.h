@@ -184,6 +184,7 @@ struct alignas(16) EdgeParams {
     int32_t thr_lo, thr_hi;
     int32_t s_thr;     // mask = gx^2 + gy^2 > s_thr (clamped to int32)
     int32_t rows;      // single-image kernel: output rows per thread (2 .. EDGE_ROWS)
+    int32_t mag_yy;    // 1: Magnitude(gy, gy) (the Sobel's gx dead): mask = 2 gy^2 > s_thr
     int32_t gvalid[4];  // valid rectangle of the Gaussian image
     int32_t valid[4];   // valid rectangle of the outputs
     int* err;

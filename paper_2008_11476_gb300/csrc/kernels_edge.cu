@@ -64,6 +64,7 @@ constexpr int M_MASK_PHASE = 1;  // binary threshold mask + phase
 constexpr int M_MASK = 2;        // binary threshold mask only
 constexpr int M_PHASE = 3;       // phase only
 constexpr int M_GENERAL = 4;     // any outputs (magnitude export, range threshold)
+constexpr int M_MASK_YY = 5;     // binary threshold mask of Magnitude(gy, gy) (gx dead)
 
 using Box = uint8_t[LH][LW];  // image (x0 - 16 + c, y0 - 2 + r)
 
@@ -504,7 +505,7 @@ __device__ __forceinline__ void point_row_general(const RowCtx& cx, const EdgePa
 template <int MODE>
 __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p, const float2* gx2,
                                           const float2* gy2, int y) {
-    constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK;
+    constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK || MODE == M_MASK_YY;
     constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
     const int x = cx.x;
     if constexpr (MODE != M_GENERAL) {
@@ -512,7 +513,8 @@ __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p,
         if (kMask) {
             float2 mv[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mv[j] = mask_value2(gx2[j], gy2[j], cx.nthr);
+            for (int j = 0; j < 4; ++j)
+                mv[j] = mask_value2(MODE == M_MASK_YY ? gy2[j] : gx2[j], gy2[j], cx.nthr);
             mw[0] = mask4(cx, mv[0], mv[1]);
             mw[1] = mask4(cx, mv[2], mv[3]);
         }
@@ -912,6 +914,7 @@ __global__ void __launch_bounds__(256) edge_point_selftest_kernel(int gmax, int 
 
 int edge_mode(const EdgeParams& p) {
     if (p.gout) return M_GAUSS;
+    if (p.mag_yy) return M_MASK_YY;  // the planner admits only the binary mask there
     if (p.mag || p.thr_general) return M_GENERAL;
     if (p.mask && p.phase) return M_MASK_PHASE;
     if (p.mask) return M_MASK;
@@ -940,6 +943,7 @@ cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_
         case M_MASK_PHASE: return launch_mode<M_MASK_PHASE>(map, p, s);
         case M_MASK: return launch_mode<M_MASK>(map, p, s);
         case M_PHASE: return launch_mode<M_PHASE>(map, p, s);
+        case M_MASK_YY: return launch_mode<M_MASK_YY>(map, p, s);
         default: return launch_mode<M_GENERAL>(map, p, s);
     }
 }
@@ -951,6 +955,7 @@ cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaSt
         case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, rows, s);
         case M_MASK: return launch_batch_mode<M_MASK>(d, grid, rows, s);
         case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, rows, s);
+        case M_MASK_YY: return launch_batch_mode<M_MASK_YY>(d, grid, rows, s);
         default: return launch_batch_mode<M_GENERAL>(d, grid, rows, s);
     }
 }

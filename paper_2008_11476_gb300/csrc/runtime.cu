@@ -145,12 +145,24 @@ bool match_edge(const Plan& P, const Group& G, EdgeMatch& m) {
         if (*slot >= 0) return false;
         *slot = i;
     }
-    if (m.gauss < 0 || m.sx < 0 || m.sy < 0) return false;
-    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx], &sy = P.ops[m.sy];
+    if (m.gauss < 0 || m.sy < 0) return false;
+    const Op &g = P.ops[m.gauss], &sy = P.ops[m.sy];
+    if (m.sx < 0) {
+        // the Sobel's gx is dead (Algorithm 1 removed it): only Magnitude(gy, gy)
+        // -> binary Threshold, the graph of Listing 1, maps onto the kernel
+        if (m.mag < 0 || m.thr < 0 || m.ph >= 0) return false;
+        const Op& mg = P.ops[m.mag];
+        if (mg.in[0] != sy.out || mg.in[1] != sy.out) return false;
+        if (P.ops[m.thr].node->p.thr_type != HVX_THRESHOLD_BINARY) return false;
+        if (G.outputs.size() != 1 || G.outputs[0] != P.ops[m.thr].out) return false;
+    }
+    const Op& sx = P.ops[m.sx >= 0 ? m.sx : m.sy];
     if (border_wraps(g.node->border) || border_wraps(sx.node->border)) return false;
     if (G.inputs.size() != 1 || G.inputs[0] != g.in[0] || g.in[0]->fmt != HVX_DF_U8) return false;
     if (sx.in[0] != g.out || sy.in[0] != g.out || sx.node != sy.node) return false;
-    if (m.mag >= 0 && (P.ops[m.mag].in[0] != sx.out || P.ops[m.mag].in[1] != sy.out)) return false;
+    if (m.sx >= 0 && m.mag >= 0 &&
+        (P.ops[m.mag].in[0] != sx.out || P.ops[m.mag].in[1] != sy.out))
+        return false;
     if (m.ph >= 0 && (P.ops[m.ph].in[0] != sx.out || P.ops[m.ph].in[1] != sy.out)) return false;
     if (m.thr >= 0 && (m.mag < 0 || P.ops[m.thr].in[0] != P.ops[m.mag].out)) return false;
     if (G.outputs.empty()) return false;
@@ -175,9 +187,10 @@ void base_edge_params(EdgeParams& e, const Group& G, const Image* in, Context* c
 }
 
 hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
-    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx];
+    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx >= 0 ? m.sx : m.sy];
     EdgeParams& e = G.edge;
     base_edge_params(e, G, g.in[0], ctx);
+    e.mag_yy = m.sx < 0 ? 1 : 0;
     e.border_g = g.node->border;
     e.cval_g = g.node->cval & 0xFF;
     e.border_s = sx.node->border;
@@ -207,7 +220,8 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
         e.thr_lo = (int32_t)std::max<int64_t>(-40000, std::min<int64_t>(40000, (int64_t)tp.thr_value));
         e.thr_hi = (int32_t)std::max<int64_t>(-40000, std::min<int64_t>(40000, (int64_t)tp.thr_upper));
         if (tp.thr_type == HVX_THRESHOLD_BINARY) {
-            // round(sqrt(s)) > T  <=>  s > T^2 + T  (T >= 0), always true for T < 0
+            // round(sqrt(s)) > T  <=>  s > T^2 + T  (T >= 0), always true for T < 0;
+            // s = gx^2 + gy^2, or 2 gy^2 for Magnitude(gy, gy)
             int64_t T = (int64_t)tp.thr_value;
             e.thr_general = 0;
             if (T < 0)

@@ -338,7 +338,10 @@ def test_section6_applications_plan(pctx):
     from paper_2008_11476_gb300 import apps as A
     unfused = {"Gauss": 1, "Laplacian": 1, "FChain": 3, "SobelX": 1, "EdgFig2": 4, "Sobel": 3,
                "Unsharp": 4, "Harris": 9, "Tomasi": 9}
-    special = {"Harris": "fused_harris_tma", "Tomasi": "fused_harris_tma"}
+    # EdgFig2 (Listing 1, gx dead) maps onto the fused edge kernel's
+    # Magnitude(gy, gy) mask mode
+    special = {"Harris": "fused_harris_tma", "Tomasi": "fused_harris_tma",
+               "EdgFig2": "fused_edge_tma"}
     for name, build in A.APPS:
         src = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
         g, _ = build(pctx, src, 1920, 1080, True)

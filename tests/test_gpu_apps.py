@@ -142,3 +142,63 @@ def test_app_matches_oracle(ctx, name, w, h, codegen):
                 np.testing.assert_array_equal(got, want)
             assert H.hvxGetValidRegion(im) == ref[rname].rect
         H.hvxReleaseGraph(g)
+
+
+def _listing1_graph(ctx, src, w, h, border, cval):
+    # Listing 1 / Fig. 2: Gaussian3x3 -> Sobel3x3 -> Magnitude(gy, gy) ->
+    # Threshold(100); gx has no consumer (Algorithm 1 removes it)
+    out = PG.empty(ctx, w, h, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(ctx)
+    blur, gx, gy, m = (H.hvxCreateVirtualImage(g) for _ in range(4))
+    H.hvxSetNodeBorder(H.hvxGaussian3x3Node(g, src, blur), border, cval)
+    H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, blur, gx, gy), border, cval)
+    H.hvxMagnitudeNode(g, gy, gy, m)
+    H.hvxThresholdNode(g, m, H.HVX_THRESHOLD_BINARY, 100, 0, 255, 0, out)
+    H.hvxVerifyGraph(g)
+    return g, out
+
+
+def _listing1_oracle(img, border, cval):
+    h, w = img.shape
+    g = OG.GraphDesc()
+    g.image("in", w, h, "U8")
+    for v in ("G", "gx", "gy", "m"):
+        g.virtual(v)
+    g.image("out", w, h, "U8")
+    b = dict(border=border, cval=cval)
+    g.node("gaussian3x3", ["in"], ["G"], **b)
+    g.node("sobel3x3", ["G"], ["gx", "gy"], **b)
+    g.node("magnitude", ["gy", "gy"], ["m"])
+    g.node("threshold", ["m"], ["out"], value=100)
+    return OG.run(g, {"in": img})["out"]
+
+
+@pytest.mark.parametrize("border", ["replicate", "constant", "undefined"])
+def test_listing1_graph_on_the_fused_edge_kernel(ctx, border):
+    # with gx dead, Magnitude(gy, gy) -> binary Threshold runs on the fused
+    # edge kernel (its mask mode with 2 gy^2 > T^2 + T), one image per launch
+    # and batched, every border, exact against the oracle
+    hb = {"replicate": H.HVX_BORDER_REPLICATE, "constant": H.HVX_BORDER_CONSTANT,
+          "undefined": H.HVX_BORDER_UNDEFINED}[border]
+    sizes = [(1, 1), (97, 45), (300, 200), (129, 121), (1920, 1080)]
+    items = []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=90 + i)
+        g, out = _listing1_graph(ctx, PG.upload(ctx, img, H.HVX_DF_U8), w, h, hb, 7)
+        assert PG.kernel_kinds(g) == ["fused_edge_tma"]
+        items.append((img, g, out, _listing1_oracle(img, border, 7)))
+    for img, g, out, ref in items:
+        H.hvxProcessGraph(g)
+        x0, y0, x1, y1 = ref.rect
+        got = PG.download(out)
+        np.testing.assert_array_equal(got[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+        assert H.hvxGetValidRegion(out) == ref.rect
+    for _, _, out, _ in items:  # clear the outputs, then the batched form
+        w, h, _ = H.hvxQueryImage(out)
+        z = np.zeros((h, w), np.uint8)
+        H.hvxCopyImage(out, z.ctypes.data, w, H.HVX_WRITE)
+    H.hvxProcessGraphBatch([it[1] for it in items])
+    H.hvxWaitBatch(ctx)
+    for img, g, out, ref in items:
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
