@@ -89,6 +89,7 @@ const char* group_kernel_name(int gk) {
         case GK_GENERIC: return "staged_tile";
         case GK_GAUSS: return "gaussian3x3_tma";
         case GK_EDGE: return "fused_edge_tma";
+        case GK_BINOM5: return "binomial5x5_tma";
         case GK_HARRIS: return "fused_harris_tma";
         case GK_POINT: return "plain_point";
         case GK_CHX_UV: return "plain_channel_uv";

@@ -208,6 +208,7 @@ enum GroupKernel : int {
     GK_GENERIC = 0,  // staged tile interpreter (any point/local ops)
     GK_GAUSS,        // Gaussian3x3, TMA tile loads
     GK_EDGE,         // Gaussian -> Sobel -> Magnitude/Threshold + Phase
+    GK_BINOM5,       // 5x5 binomial Convolve, TMA tile loads
     GK_HARRIS,       // Sobel -> products -> window sums -> response -> threshold
     GK_POINT,        // plain point op
     GK_CHX_UV,       // ChannelExtract U/V (half width)

@@ -65,6 +65,8 @@ constexpr int M_MASK = 2;        // binary threshold mask only
 constexpr int M_PHASE = 3;       // phase only
 constexpr int M_GENERAL = 4;     // any outputs (magnitude export, range threshold)
 constexpr int M_MASK_YY = 5;     // binary threshold mask of Magnitude(gy, gy) (gx dead)
+constexpr int M_SOBEL_MASK = 6;  // no Gaussian: the mask of Sobel -> Magnitude -> Threshold
+constexpr int M_BINOM5 = EDGE_MODE_BINOM5;  // 5x5 binomial Convolve alone (kernels_gauss5.cu)
 
 using Box = uint8_t[LH][LW];  // image (x0 - 16 + c, y0 - 2 + r)
 
@@ -216,6 +218,15 @@ __device__ __forceinline__ bool rep2_borders(const EdgeParams& p) {
     return p.border_g == HVX_BORDER_REPLICATE && p.border_s == HVX_BORDER_REPLICATE;
 }
 
+// Whether every G row of a tile is the plain one of its (border-filled) box,
+// so that the tile runs the unrolled loop: interior tiles; every tile when
+// both borders replicate (fix_input_border); and every tile without a
+// Gaussian node whose Sobel border is REPLICATE or CONSTANT (the box then
+// holds exactly the values the Sobel reads).
+__device__ __forceinline__ bool plain_g_rows(const EdgeParams& p, bool interior) {
+    return interior || rep2_borders(p) || (p.g_op == 1 && p.border_s != HVX_BORDER_UNDEFINED);
+}
+
 // Box cells outside the image that a G value inside the image, or the plain
 // G of the row / column just outside it, reads: the two rows above and below
 // the image and the two columns left and right of it.  They take the
@@ -323,6 +334,16 @@ __device__ __forceinline__ void g_row(const uint32_t* a, const uint32_t* b, cons
 #pragma unroll
     for (int j = 0; j < 5; ++j)
         G[j] = (V[j] + V[j + 1] + rnd + 2u * shift_pair(V[j], V[j + 1])) & 0xFFF0FFF0u;
+}
+
+// The input row b itself in place of a Gaussian row (no Gaussian node): the
+// pixels x - 1 .. x + 8 as pairs (x - 1 + 2j, x + 2j), times 16 like the
+// Gaussian lanes (at most 4080, so lanes never carry).  When the box cells
+// outside the image hold the Sobel's border values, these rows are exactly
+// what the Sobel reads, on every tile.
+__device__ __forceinline__ void input_row16(const uint32_t* b, uint32_t* G) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) G[j] = shift_pair(b[j], b[j + 1]) << 4;
 }
 
 // G row yq (x - 1 .. x + 8, as 16 G) as the Sobel reads it, for a strip whose window
@@ -505,7 +526,8 @@ __device__ __forceinline__ void point_row_general(const RowCtx& cx, const EdgePa
 template <int MODE>
 __device__ __forceinline__ void point_row(const RowCtx& cx, const EdgeParams& p, const float2* gx2,
                                           const float2* gy2, int y) {
-    constexpr bool kMask = MODE == M_MASK_PHASE || MODE == M_MASK || MODE == M_MASK_YY;
+    constexpr bool kMask =
+        MODE == M_MASK_PHASE || MODE == M_MASK || MODE == M_MASK_YY || MODE == M_SOBEL_MASK;
     constexpr bool kPhase = MODE == M_MASK_PHASE || MODE == M_PHASE;
     const int x = cx.x;
     if constexpr (MODE != M_GENERAL) {
@@ -610,7 +632,9 @@ __device__ __forceinline__ void edge_row(const RowCtx& cx, const GPolicy& gp, co
                                          const uint32_t* Pb, uint32_t* Pn, const uint32_t* Ga,
                                          const uint32_t* Gb, uint32_t* Gc, int y) {
     load_pairs(in_row, c, Pn);
-    if (FAST)
+    if constexpr (MODE == M_SOBEL_MASK)
+        input_row16(Pb, Gc);
+    else if (FAST)
         g_row(Pa, Pb, Pn, rnd, Gc);
     else
         g_row_any(gp, in, p, cx.x, x0, y0, y + 1, rnd, cx.gslow, Pa, Pb, Pn, Gc);
@@ -658,9 +682,15 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     GPolicy gp;
     if (fast) {
         load_pairs(row + LW, c, P2);      // yb - 1
-        g_row(P1, P2, P0, rnd, G0);       // G(yb - 1)
+        if constexpr (MODE == M_SOBEL_MASK)
+            input_row16(P2, G0);          // input row yb - 1 in place of G(yb - 1)
+        else
+            g_row(P1, P2, P0, rnd, G0);   // G(yb - 1)
         load_pairs(row + 3 * LW, c, P1);  // yb + 1
-        g_row(P2, P0, P1, rnd, G1);       // G(yb)
+        if constexpr (MODE == M_SOBEL_MASK)
+            input_row16(P0, G1);          // input row yb in place of G(yb)
+        else
+            g_row(P2, P0, P1, rnd, G1);   // G(yb)
         // rows: P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y); the
         // windows rotate with period 3, so three rows per trip keep them in place
         const uint8_t* r = row + 4 * LW;  // input row yb + 2
@@ -687,9 +717,15 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     gp.L = min(10, W - x + 1);
     gp.cv = 16u * (uint32_t)(p.cval_s & 0xFF);
     load_pairs(row + LW, c, P2);  // yb - 1
-    g_row_any(gp, in, p, x, x0, y0, yb - 1, rnd, cx.gslow, P1, P2, P0, G0);
+    if constexpr (MODE == M_SOBEL_MASK)
+        input_row16(P2, G0);
+    else
+        g_row_any(gp, in, p, x, x0, y0, yb - 1, rnd, cx.gslow, P1, P2, P0, G0);
     load_pairs(row + 3 * LW, c, P1);  // yb + 1
-    g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
+    if constexpr (MODE == M_SOBEL_MASK)
+        input_row16(P0, G1);
+    else
+        g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
     // P0 = input y, P1 = input y + 1, G0 = G(y - 1), G1 = G(y): one row per
     // trip, then the windows move up by one
     const uint8_t* r = row + 4 * LW;
@@ -746,7 +782,7 @@ __global__ void __launch_bounds__(EDGE_THREADS)
         fix_input_border(sm.in[0].b, p, x0, y0, th + 4);
         __syncthreads();
     }
-    edge_tile<MODE>(sm.in[0].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, rows);
+    edge_tile<MODE>(sm.in[0].b, p, x0, y0, plain_g_rows(p, interior), sm.plut, sm.gslow, rows);
 }
 
 // Thread 0: the origin of batch tile t into slot ps, then one bulk copy of
@@ -838,7 +874,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge_batch_kernel(const EdgeBatc
         const int x0 = sm.tx0[ps], y0 = sm.ty0[ps];
         const bool interior = tile_is_interior(p, x0, y0, 8 * R);
         if (!interior) fix_input_border_warp(sm.in[s].b, p, x0, y0, r0, r0 + 2 * R + 4);
-        edge_tile<MODE>(sm.in[s].b, p, x0, y0, interior || rep2_borders(p), sm.plut, sm.gslow, R);
+        edge_tile<MODE>(sm.in[s].b, p, x0, y0, plain_g_rows(p, interior), sm.plut, sm.gslow, R);
         // this warp is done with box s: count it out (release: its reads of
         // the box happen before the count), the last one loads the next tile
         __syncwarp();
@@ -913,8 +949,10 @@ __global__ void __launch_bounds__(256) edge_point_selftest_kernel(int gmax, int 
 }  // namespace
 
 int edge_mode(const EdgeParams& p) {
+    if (p.g_op == 2) return M_BINOM5;
     if (p.gout) return M_GAUSS;
     if (p.mag_yy) return M_MASK_YY;  // the planner admits only the binary mask there
+    if (p.g_op == 1) return M_SOBEL_MASK;  // likewise
     if (p.mag || p.thr_general) return M_GENERAL;
     if (p.mask && p.phase) return M_MASK_PHASE;
     if (p.mask) return M_MASK;
@@ -940,10 +978,12 @@ void edge_tile_dims(int mode, int* tw, int* th) {
 cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s) {
     switch (edge_mode(p)) {
         case M_GAUSS: return launch_gauss(map, p, s);
+        case M_BINOM5: return launch_binom5(map, p, s);
         case M_MASK_PHASE: return launch_mode<M_MASK_PHASE>(map, p, s);
         case M_MASK: return launch_mode<M_MASK>(map, p, s);
         case M_PHASE: return launch_mode<M_PHASE>(map, p, s);
         case M_MASK_YY: return launch_mode<M_MASK_YY>(map, p, s);
+        case M_SOBEL_MASK: return launch_mode<M_SOBEL_MASK>(map, p, s);
         default: return launch_mode<M_GENERAL>(map, p, s);
     }
 }
@@ -952,10 +992,12 @@ cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaSt
                               int rows) {
     switch (mode) {
         case M_GAUSS: return launch_gauss_batch(d, grid, s);
+        case M_BINOM5: return launch_binom5_batch(d, grid, rows, s);
         case M_MASK_PHASE: return launch_batch_mode<M_MASK_PHASE>(d, grid, rows, s);
         case M_MASK: return launch_batch_mode<M_MASK>(d, grid, rows, s);
         case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, rows, s);
         case M_MASK_YY: return launch_batch_mode<M_MASK_YY>(d, grid, rows, s);
+        case M_SOBEL_MASK: return launch_batch_mode<M_SOBEL_MASK>(d, grid, rows, s);
         default: return launch_batch_mode<M_GENERAL>(d, grid, rows, s);
     }
 }
@@ -968,6 +1010,7 @@ cudaError_t launch_edge_point_selftest(int gmax, int s_thr, uint8_t* phase, uint
 
 int edge_batch_blocks_per_sm(int mode) {
     if (mode == M_GAUSS) return gauss_batch_blocks_per_sm();
+    if (mode == M_BINOM5) return binom5_batch_blocks_per_sm();
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, edge_batch_kernel<M_MASK_PHASE, ROWS>,
                                                   EDGE_THREADS, 0);

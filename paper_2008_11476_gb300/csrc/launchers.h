@@ -21,8 +21,11 @@ struct EdgeBatchDesc {
 
 // Output mode of an edge / Gaussian group (which kernel instantiation runs it);
 // every image of one batch launch must have the same mode.  EDGE_MODE_GAUSS
-// (the Gaussian3x3 group alone) runs the Gaussian kernel, with its own tile.
+// (the Gaussian3x3 group alone) runs the Gaussian kernel, with its own tile;
+// EDGE_MODE_BINOM5 (a 5x5 binomial Convolve alone) the binomial kernel, with
+// the edge kernel's tiles and boxes.
 constexpr int EDGE_MODE_GAUSS = 0;
+constexpr int EDGE_MODE_BINOM5 = 7;
 int edge_mode(const EdgeParams& p);
 void edge_tile_dims(int mode, int* tw, int* th);
 // output rows per thread of the single-image edge kernel for a W x H image
@@ -44,6 +47,12 @@ cudaError_t launch_gauss(const CUtensorMap& map, const EdgeParams& p, cudaStream
 int gauss_single_rows(int W, int H, int num_sms);
 cudaError_t launch_gauss_batch(const EdgeBatchDesc& d, int grid, cudaStream_t s);
 int gauss_batch_blocks_per_sm();
+
+// 5x5 binomial Convolve: one image (p.rows 2 or 5, the map boxed 160 x
+// (8 p.rows + 4)), or a batch with 128 x 8 rows tiles (rows 5, 10, 15)
+cudaError_t launch_binom5(const CUtensorMap& map, const EdgeParams& p, cudaStream_t s);
+cudaError_t launch_binom5_batch(const EdgeBatchDesc& d, int grid, int rows, cudaStream_t s);
+int binom5_batch_blocks_per_sm();
 
 // Harris: the UNDEFINED-border fast kernel or the general one; the tensor map
 // of the group's input must use the box harris_box() gives.

@@ -145,7 +145,20 @@ bool match_edge(const Plan& P, const Group& G, EdgeMatch& m) {
         if (*slot >= 0) return false;
         *slot = i;
     }
-    if (m.gauss < 0 || m.sy < 0) return false;
+    if (m.sy < 0) return false;
+    if (m.gauss < 0) {
+        // no Gaussian: Sobel3x3 -> Magnitude(gx, gy) -> binary Threshold on
+        // the group's U8 input (the Sobel application) runs on the kernel with
+        // the input itself in place of the Gaussian image
+        if (m.sx < 0 || m.mag < 0 || m.thr < 0 || m.ph >= 0) return false;
+        const Op &sx = P.ops[m.sx], &sy = P.ops[m.sy], &mg = P.ops[m.mag], &t = P.ops[m.thr];
+        if (sx.node != sy.node || border_wraps(sx.node->border)) return false;
+        if (G.inputs.size() != 1 || G.inputs[0] != sx.in[0] || sx.in[0]->fmt != HVX_DF_U8)
+            return false;
+        if (mg.in[0] != sx.out || mg.in[1] != sy.out || t.in[0] != mg.out) return false;
+        if (t.node->p.thr_type != HVX_THRESHOLD_BINARY) return false;
+        return G.outputs.size() == 1 && G.outputs[0] == t.out;
+    }
     const Op &g = P.ops[m.gauss], &sy = P.ops[m.sy];
     if (m.sx < 0) {
         // the Sobel's gx is dead (Algorithm 1 removed it): only Magnitude(gy, gy)
@@ -187,16 +200,29 @@ void base_edge_params(EdgeParams& e, const Group& G, const Image* in, Context* c
 }
 
 hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
-    const Op &g = P.ops[m.gauss], &sx = P.ops[m.sx >= 0 ? m.sx : m.sy];
+    const Op& sx = P.ops[m.sx >= 0 ? m.sx : m.sy];
+    Image* const input = m.gauss >= 0 ? P.ops[m.gauss].in[0] : sx.in[0];
     EdgeParams& e = G.edge;
-    base_edge_params(e, G, g.in[0], ctx);
+    base_edge_params(e, G, input, ctx);
     e.mag_yy = m.sx < 0 ? 1 : 0;
-    e.border_g = g.node->border;
-    e.cval_g = g.node->cval & 0xFF;
     e.border_s = sx.node->border;
     e.cval_s = sx.node->cval & 0xFF;
-    e.rounding = g.node->rounding;
-    set_rect(e.gvalid, g.out->valid);
+    if (m.gauss >= 0) {
+        const Op& g = P.ops[m.gauss];
+        e.border_g = g.node->border;
+        e.cval_g = g.node->cval & 0xFF;
+        e.rounding = g.node->rounding;
+        set_rect(e.gvalid, g.out->valid);
+    } else {
+        // the input stands in for the Gaussian image: its cells outside the
+        // image take the Sobel's border, and all of it is valid
+        e.g_op = 1;
+        e.border_g = e.border_s;
+        e.cval_g = e.cval_s;
+        e.gvalid[0] = e.gvalid[1] = 0;
+        e.gvalid[2] = (int32_t)G.W;
+        e.gvalid[3] = (int32_t)G.H;
+    }
     set_rect(e.valid, rect_intersect(sx.out->valid, P.ops[m.sy].out->valid));
     auto is_out = [&](const Image* im) {
         return std::find(G.outputs.begin(), G.outputs.end(), im) != G.outputs.end();
@@ -250,7 +276,41 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
         }
         if (r >= 2 && r <= EDGE_ROWS) e.rows = r;
     }
-    return encode_u8_map(&G.tmap, g.in[0], EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));
+    return encode_u8_map(&G.tmap, input, EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));
+}
+
+// A Convolve node that is the 5x5 binomial filter [1 4 6 4 1]^T [1 4 6 4 1]
+// divided by 256 (shift 8), U8 to U8, with a border the kernel's box fill
+// implements (every sum is non-negative and at most 255 * 256, so the floor
+// division is a shift and no output saturates).
+bool is_binomial5(const Op& op) {
+    if (op.kind != OP_CONV || border_wraps(op.node->border)) return false;
+    const NodeParams& p = op.node->p;
+    if (p.kw != 5 || p.kh != 5 || p.shift != 8 || p.coeffs.size() != 25) return false;
+    if (op.in[0]->fmt != HVX_DF_U8 || op.out->fmt != HVX_DF_U8) return false;
+    static const int32_t b[5] = {1, 4, 6, 4, 1};
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c)
+            if (p.coeffs[r * 5 + c] != b[r] * b[c]) return false;
+    return true;
+}
+
+hvx_status build_binom5(Plan& P, Group& G, Context* ctx) {
+    const Op& op = P.ops[G.ops[0]];
+    EdgeParams& e = G.edge;
+    base_edge_params(e, G, op.in[0], ctx);
+    e.g_op = 2;
+    e.border_g = op.node->border;
+    e.cval_g = op.node->cval & 0xFF;
+    e.border_s = HVX_BORDER_UNDEFINED;
+    e.gout = static_cast<uint8_t*>(op.out->dev);
+    e.gout_pitch = op.out->pitch;
+    set_rect(e.gvalid, op.out->valid);
+    set_rect(e.valid, op.out->valid);
+    // one image per launch: R rows per thread, a 160 x (8R + 4) box (the batch
+    // kernel encodes its own 160 x (8R + 4) maps for the R it runs)
+    e.rows = edge_single_rows((int)G.W, (int)G.H, ctx->num_sms);
+    return encode_u8_map(&G.tmap, op.in[0], EDGE_LOAD_W, (uint32_t)(8 * e.rows + 4));
 }
 
 hvx_status build_gauss(Plan& P, Group& G, Context* ctx) {
@@ -679,6 +739,9 @@ hvx_status prepare_launches(Graph* g) {
                    !border_wraps(first.node->border)) {
             G.kernel = GK_GAUSS;
             st = build_gauss(P, G, ctx);
+        } else if (hand && G.ops.size() == 1 && is_binomial5(first)) {
+            G.kernel = GK_BINOM5;
+            st = build_binom5(P, G, ctx);
         } else if (G.ops.size() == 1 && first.kind == OP_CHX &&
                    first.node->p.channel != HVX_CHANNEL_Y) {
             G.kernel = GK_CHX_UV;
@@ -733,6 +796,7 @@ hvx_status launch_plan(Graph* g, cudaStream_t s) {
         switch (G.kernel) {
             case GK_EQHIST: e = launch_eqhist(G.eqh, s); break;
             case GK_GAUSS:
+            case GK_BINOM5:
             case GK_EDGE: e = launch_edge(G.tmap, G.edge, s); break;
             case GK_HARRIS: e = launch_harris(G.tmap, G.harris, s); break;
             case GK_POINT:
@@ -1216,7 +1280,8 @@ hvx_status process_batch(Context* ctx, Graph* const* gs, int n, cudaStream_t s) 
     for (int i = 0; i < n && same; ++i) {
         const Plan& P = gs[i]->plan;
         same = P.groups.size() == 1 &&
-               (P.groups[0].kernel == GK_EDGE || P.groups[0].kernel == GK_GAUSS);
+               (P.groups[0].kernel == GK_EDGE || P.groups[0].kernel == GK_GAUSS ||
+                P.groups[0].kernel == GK_BINOM5);
         if (same) {
             int m = edge_mode(P.groups[0].edge);
             same = mode < 0 || m == mode;

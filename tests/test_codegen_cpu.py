@@ -46,12 +46,14 @@ def test_applications_compile(pctx, name, mode):
 def test_u8_inputs_staged_by_tma(pctx, monkeypatch):
     # interior tiles take a staged U8 input as one TMA box on an mbarrier; its
     # slot's rows start 16 bytes left of the tile (halo 2 of the 5x5 Gauss);
-    # HVX_CODEGEN_TMA=0 keeps per-thread loads
-    s = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss), 0)
+    # HVX_CODEGEN_TMA=0 keeps per-thread loads (the group has a hand-written
+    # kernel, so the generated one is asked for)
+    only = H.HVX_CODEGEN_ONLY
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss, mode=only), 0)
     assert s.count("hvx_tma_2d(B") == 1 and "hvx_mbar_wait(bar, p.err)" in s
     assert "x0 - 16, y0 - 2" in s
     monkeypatch.setenv("HVX_CODEGEN_TMA", "0")
-    s0 = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss), 0)
+    s0 = H.hvxGetGraphKernelSource(_gen(pctx, A.gauss, mode=only), 0)
     assert "hvx_tma_2d(B" not in s0 and "__ldg((const unsigned*)" in s0
 
 
@@ -68,8 +70,9 @@ def test_constants_are_folded(pctx):
         # a cross of 5 taps over 4 rows reads 14 distinct values, not 20
         assert s.count("= B0[qb0") == 14
     # the Sobel application's Magnitude -> Threshold(100) is the integer
-    # compare gx^2 + gy^2 > 100^2 + 100, with the bound a literal
-    s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel), 0)
+    # compare gx^2 + gy^2 > 100^2 + 100, with the bound a literal (the group
+    # has a hand-written kernel, so the generated one is asked for)
+    s = H.hvxGetGraphKernelSource(_gen(pctx, A.sobel, mode=H.HVX_CODEGEN_ONLY), 0)
     assert "> 10100u)" in s
 
 

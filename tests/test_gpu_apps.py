@@ -202,3 +202,108 @@ def test_listing1_graph_on_the_fused_edge_kernel(ctx, border):
     for img, g, out, ref in items:
         x0, y0, x1, y1 = ref.rect
         np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+
+
+def _sobel_graph(ctx, src, w, h, border, cval, thr):
+    out = PG.empty(ctx, w, h, H.HVX_DF_U8)
+    g = H.hvxCreateGraph(ctx)
+    gx, gy, m = (H.hvxCreateVirtualImage(g) for _ in range(3))
+    H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, src, gx, gy), border, cval)
+    H.hvxMagnitudeNode(g, gx, gy, m)
+    H.hvxThresholdNode(g, m, H.HVX_THRESHOLD_BINARY, thr, 0, 255, 0, out)
+    H.hvxVerifyGraph(g)
+    return g, out
+
+
+def _sobel_oracle(img, border, cval, thr):
+    h, w = img.shape
+    g = OG.GraphDesc()
+    g.image("in", w, h, "U8")
+    for v in ("gx", "gy", "m"):
+        g.virtual(v)
+    g.image("out", w, h, "U8")
+    g.node("sobel3x3", ["in"], ["gx", "gy"], border=border, cval=cval)
+    g.node("magnitude", ["gx", "gy"], ["m"])
+    g.node("threshold", ["m"], ["out"], value=thr)
+    return OG.run(g, {"in": img})["out"]
+
+
+@pytest.mark.parametrize("border", ["replicate", "constant", "undefined"])
+def test_sobel_graph_on_the_fused_edge_kernel(ctx, border):
+    # Sobel3x3 -> Magnitude -> binary Threshold with no Gaussian node runs on
+    # the fused edge kernel with the input rows in place of Gaussian rows: every
+    # border, ragged sizes, thresholds at both ends, single and batched launches
+    hb = {"replicate": H.HVX_BORDER_REPLICATE, "constant": H.HVX_BORDER_CONSTANT,
+          "undefined": H.HVX_BORDER_UNDEFINED}[border]
+    sizes = [(1, 1), (97, 45), (300, 200), (129, 121), (1920, 1080)]
+    for thr in (100, 0, 1441):
+        items = []
+        for i, (w, h) in enumerate(sizes):
+            img = synth.rects_noise(w, h, seed=110 + i)
+            g, out = _sobel_graph(ctx, PG.upload(ctx, img, H.HVX_DF_U8), w, h, hb, 250, thr)
+            assert PG.kernel_kinds(g) == ["fused_edge_tma"]
+            items.append((g, out, _sobel_oracle(img, border, 250, thr)))
+        for g, out, ref in items:
+            H.hvxProcessGraph(g)
+            x0, y0, x1, y1 = ref.rect
+            np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1],
+                                          ref.data[y0:y1, x0:x1])
+            assert H.hvxGetValidRegion(out) == ref.rect
+        for _, out, _ in items:
+            w, h, _ = H.hvxQueryImage(out)
+            z = np.zeros((h, w), np.uint8)
+            H.hvxCopyImage(out, z.ctypes.data, w, H.HVX_WRITE)
+        H.hvxProcessGraphBatch([it[0] for it in items])
+        H.hvxWaitBatch(ctx)
+        for _, out, ref in items:
+            x0, y0, x1, y1 = ref.rect
+            np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1],
+                                          ref.data[y0:y1, x0:x1])
+
+
+B5_COEFFS = np.outer([1, 4, 6, 4, 1], [1, 4, 6, 4, 1]).astype(np.int32)
+
+
+@pytest.mark.parametrize("border", [H.HVX_BORDER_REPLICATE, H.HVX_BORDER_CONSTANT,
+                                    H.HVX_BORDER_UNDEFINED])
+def test_binomial5x5_kernel(ctx, border):
+    # the 5x5 binomial Convolve (shift 8, U8 -> U8) on its hand-written
+    # kernel: every border, ragged tiles, images smaller than a tile, extreme
+    # bytes (sums up to 255 * 256), single and batched launches, exact
+    ob = {H.HVX_BORDER_REPLICATE: O.BORDER_REPLICATE, H.HVX_BORDER_CONSTANT: O.BORDER_CONSTANT,
+          H.HVX_BORDER_UNDEFINED: O.BORDER_UNDEFINED}[border]
+    sizes = [(1, 1), (3, 2), (97, 45), (300, 200), (129, 121), (1920, 1080)]
+    items = []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=130 + i)
+        if i == 3:
+            img[::2] = 255  # saturated rows: the largest sums
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        out = PG.empty(ctx, w, h, H.HVX_DF_U8)
+        g = H.hvxCreateGraph(ctx)
+        H.hvxSetNodeBorder(H.hvxConvolveNode(g, src, B5_COEFFS.ravel(), 5, 5, 8, out), border, 251)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["binomial5x5_tma"]
+        items.append((g, out, O.convolve(img, B5_COEFFS, 8, ob, 251, out_dtype=np.uint8)))
+    for g, out, ref in items:
+        H.hvxProcessGraph(g)
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+        assert H.hvxGetValidRegion(out) == ref.rect
+    for _, out, _ in items:
+        w, h, _ = H.hvxQueryImage(out)
+        z = np.zeros((h, w), np.uint8)
+        H.hvxCopyImage(out, z.ctypes.data, w, H.HVX_WRITE)
+    H.hvxProcessGraphBatch([it[0] for it in items])
+    H.hvxWaitBatch(ctx)
+    for _, out, ref in items:
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(PG.download(out)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+    # other coefficients stay on the generated kernels
+    g = H.hvxCreateGraph(ctx)
+    c2 = B5_COEFFS.copy()
+    c2[2, 2] += 1
+    H.hvxConvolveNode(g, PG.upload(ctx, synth.rects_noise(40, 30, seed=1), H.HVX_DF_U8),
+                      c2.ravel(), 5, 5, 8, PG.empty(ctx, 40, 30, H.HVX_DF_U8))
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) != ["binomial5x5_tma"]
