@@ -187,7 +187,8 @@ struct alignas(16) EdgeParams {
     int32_t mag_yy;    // 1: Magnitude(gy, gy) (the Sobel's gx dead): mask = 2 gy^2 > s_thr
     int32_t g_op;      // the local op of the group's first stage: 0 Gaussian3x3 (before the
                        // Sobel, or alone into gout); 1 none, the Sobel reads the input
-                       // (mask only); 2 a 5x5 binomial Convolve alone (into gout)
+                       // (the mask only, or gx alone into mag as S16); 2 a 5x5 binomial
+                       // Convolve alone (into gout)
     int32_t gvalid[4];  // valid rectangle of the Gaussian image
     int32_t valid[4];   // valid rectangle of the outputs
     int* err;

@@ -67,6 +67,7 @@ constexpr int M_GENERAL = 4;     // any outputs (magnitude export, range thresho
 constexpr int M_MASK_YY = 5;     // binary threshold mask of Magnitude(gy, gy) (gx dead)
 constexpr int M_SOBEL_MASK = 6;  // no Gaussian: the mask of Sobel -> Magnitude -> Threshold
 constexpr int M_BINOM5 = EDGE_MODE_BINOM5;  // 5x5 binomial Convolve alone (kernels_gauss5.cu)
+constexpr int M_SOBEL_GX = 8;    // no Gaussian: the Sobel's gx alone, stored as S16
 
 using Box = uint8_t[LH][LW];  // image (x0 - 16 + c, y0 - 2 + r)
 
@@ -621,6 +622,43 @@ __device__ __forceinline__ void point_row_general(const RowCtx& cx, const EdgePa
 
 // ---- one tile ------------------------------------------------------------------------
 
+// gx of a pixel pair as two's-complement S16 lanes from its (16 gx + 16384)
+// lanes: (lane >> 4) - 1024 in each lane, without a borrow between lanes
+// (the top bit of each lane is set before the subtraction and flipped after).
+__device__ __forceinline__ uint32_t gx_s16_pair(uint32_t gxp) {
+    return ((((gxp >> 4) & 0x0FFF0FFFu) | 0x80008000u) - 0x04000400u) ^ 0x80008000u;
+}
+
+// Store of a gx strip row that is cut by the right image edge or crosses the
+// valid region.
+__device__ __noinline__ void store_gx_edge(int16_t* row, int x, int y, const EdgeParams& p,
+                                           const uint32_t* w, bool full) {
+    for (int j = 0; j < 8 && x + j < (int)p.W; ++j) {
+        int16_t v = (int16_t)(w[j >> 1] >> (16 * (j & 1)));
+        if (!full && !in_rect(p.valid, x + j, y)) v = 0;
+        row[x + j] = v;
+    }
+}
+
+// The Sobel's gx at x .. x + 7 of row y from the rows above (a), at (b) and
+// below (c), stored as S16 (one 16-byte store on whole strips).
+__device__ __forceinline__ void sobel_gx_row(const RowCtx& cx, const EdgeParams& p,
+                                             const uint32_t* a, const uint32_t* b,
+                                             const uint32_t* c, int y) {
+    uint32_t vs[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) vs[j] = a[j] + 2u * b[j] + c[j];
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = gx_s16_pair(vs[j + 1] + 0x40004000u - vs[j]);
+    int16_t* row = reinterpret_cast<int16_t*>(reinterpret_cast<uint8_t*>(p.mag) +
+                                              (size_t)y * p.mag_pitch);
+    if (cx.fast)
+        *reinterpret_cast<uint4*>(row + cx.x) = make_uint4(w[0], w[1], w[2], w[3]);
+    else
+        store_gx_edge(row, cx.x, y, p, w, cx.full);
+}
+
 // One output row y of the strip: load input row y + 2 into Pn, form G row y + 1
 // into Gc from (Pa, Pb, Pn), then Sobel over (Ga, Gb, Gc) and the point ops.
 // FAST: the plain G row (no border fix-ups) and whole stores where the strip
@@ -632,15 +670,19 @@ __device__ __forceinline__ void edge_row(const RowCtx& cx, const GPolicy& gp, co
                                          const uint32_t* Pb, uint32_t* Pn, const uint32_t* Ga,
                                          const uint32_t* Gb, uint32_t* Gc, int y) {
     load_pairs(in_row, c, Pn);
-    if constexpr (MODE == M_SOBEL_MASK)
+    if constexpr (MODE == M_SOBEL_MASK || MODE == M_SOBEL_GX)
         input_row16(Pb, Gc);
     else if (FAST)
         g_row(Pa, Pb, Pn, rnd, Gc);
     else
         g_row_any(gp, in, p, cx.x, x0, y0, y + 1, rnd, cx.gslow, Pa, Pb, Pn, Gc);
-    float2 gx[4], gy[4];
-    sobel8(Ga, Gb, Gc, gx, gy);
-    point_row<MODE>(cx, p, gx, gy, y);
+    if constexpr (MODE == M_SOBEL_GX) {
+        sobel_gx_row(cx, p, Ga, Gb, Gc, y);
+    } else {
+        float2 gx[4], gy[4];
+        sobel8(Ga, Gb, Gc, gx, gy);
+        point_row<MODE>(cx, p, gx, gy, y);
+    }
 }
 
 // One tile after its box has landed (and, on edge tiles, been border-fixed):
@@ -682,12 +724,12 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     GPolicy gp;
     if (fast) {
         load_pairs(row + LW, c, P2);      // yb - 1
-        if constexpr (MODE == M_SOBEL_MASK)
+        if constexpr (MODE == M_SOBEL_MASK || MODE == M_SOBEL_GX)
             input_row16(P2, G0);          // input row yb - 1 in place of G(yb - 1)
         else
             g_row(P1, P2, P0, rnd, G0);   // G(yb - 1)
         load_pairs(row + 3 * LW, c, P1);  // yb + 1
-        if constexpr (MODE == M_SOBEL_MASK)
+        if constexpr (MODE == M_SOBEL_MASK || MODE == M_SOBEL_GX)
             input_row16(P0, G1);          // input row yb in place of G(yb)
         else
             g_row(P2, P0, P1, rnd, G1);   // G(yb)
@@ -717,12 +759,12 @@ __device__ __forceinline__ void edge_tile(const Box& in, const EdgeParams& p, in
     gp.L = min(10, W - x + 1);
     gp.cv = 16u * (uint32_t)(p.cval_s & 0xFF);
     load_pairs(row + LW, c, P2);  // yb - 1
-    if constexpr (MODE == M_SOBEL_MASK)
+    if constexpr (MODE == M_SOBEL_MASK || MODE == M_SOBEL_GX)
         input_row16(P2, G0);
     else
         g_row_any(gp, in, p, x, x0, y0, yb - 1, rnd, cx.gslow, P1, P2, P0, G0);
     load_pairs(row + 3 * LW, c, P1);  // yb + 1
-    if constexpr (MODE == M_SOBEL_MASK)
+    if constexpr (MODE == M_SOBEL_MASK || MODE == M_SOBEL_GX)
         input_row16(P0, G1);
     else
         g_row_any(gp, in, p, x, x0, y0, yb, rnd, cx.gslow, P2, P0, P1, G1);
@@ -952,7 +994,7 @@ int edge_mode(const EdgeParams& p) {
     if (p.g_op == 2) return M_BINOM5;
     if (p.gout) return M_GAUSS;
     if (p.mag_yy) return M_MASK_YY;  // the planner admits only the binary mask there
-    if (p.g_op == 1) return M_SOBEL_MASK;  // likewise
+    if (p.g_op == 1) return p.mask ? M_SOBEL_MASK : M_SOBEL_GX;  // likewise
     if (p.mag || p.thr_general) return M_GENERAL;
     if (p.mask && p.phase) return M_MASK_PHASE;
     if (p.mask) return M_MASK;
@@ -984,6 +1026,7 @@ cudaError_t launch_edge(const CUtensorMap& map, const EdgeParams& p, cudaStream_
         case M_PHASE: return launch_mode<M_PHASE>(map, p, s);
         case M_MASK_YY: return launch_mode<M_MASK_YY>(map, p, s);
         case M_SOBEL_MASK: return launch_mode<M_SOBEL_MASK>(map, p, s);
+        case M_SOBEL_GX: return launch_mode<M_SOBEL_GX>(map, p, s);
         default: return launch_mode<M_GENERAL>(map, p, s);
     }
 }
@@ -998,6 +1041,7 @@ cudaError_t launch_edge_batch(const EdgeBatchDesc& d, int mode, int grid, cudaSt
         case M_PHASE: return launch_batch_mode<M_PHASE>(d, grid, rows, s);
         case M_MASK_YY: return launch_batch_mode<M_MASK_YY>(d, grid, rows, s);
         case M_SOBEL_MASK: return launch_batch_mode<M_SOBEL_MASK>(d, grid, rows, s);
+        case M_SOBEL_GX: return launch_batch_mode<M_SOBEL_GX>(d, grid, rows, s);
         default: return launch_batch_mode<M_GENERAL>(d, grid, rows, s);
     }
 }

@@ -145,6 +145,16 @@ bool match_edge(const Plan& P, const Group& G, EdgeMatch& m) {
         if (*slot >= 0) return false;
         *slot = i;
     }
+    if (m.gauss < 0 && m.sy < 0) {
+        // Sobel3x3 with only gx alive, exported as S16 (the SobelX application):
+        // the kernel's input-row mode, storing gx
+        if (m.sx < 0 || m.mag >= 0 || m.thr >= 0 || m.ph >= 0) return false;
+        const Op& sx = P.ops[m.sx];
+        if (border_wraps(sx.node->border)) return false;
+        if (G.inputs.size() != 1 || G.inputs[0] != sx.in[0] || sx.in[0]->fmt != HVX_DF_U8)
+            return false;
+        return G.outputs.size() == 1 && G.outputs[0] == sx.out && sx.out->fmt == HVX_DF_S16;
+    }
     if (m.sy < 0) return false;
     if (m.gauss < 0) {
         // no Gaussian: Sobel3x3 -> Magnitude(gx, gy) -> binary Threshold on
@@ -201,6 +211,7 @@ void base_edge_params(EdgeParams& e, const Group& G, const Image* in, Context* c
 
 hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
     const Op& sx = P.ops[m.sx >= 0 ? m.sx : m.sy];
+    const Op& sy = P.ops[m.sy >= 0 ? m.sy : m.sx];
     Image* const input = m.gauss >= 0 ? P.ops[m.gauss].in[0] : sx.in[0];
     EdgeParams& e = G.edge;
     base_edge_params(e, G, input, ctx);
@@ -223,7 +234,11 @@ hvx_status build_edge(Plan& P, Group& G, const EdgeMatch& m, Context* ctx) {
         e.gvalid[2] = (int32_t)G.W;
         e.gvalid[3] = (int32_t)G.H;
     }
-    set_rect(e.valid, rect_intersect(sx.out->valid, P.ops[m.sy].out->valid));
+    set_rect(e.valid, rect_intersect(sx.out->valid, sy.out->valid));
+    if (m.sy < 0) {  // gx alone, exported as S16 (it uses the magnitude's slot)
+        e.mag = static_cast<int16_t*>(sx.out->dev);
+        e.mag_pitch = sx.out->pitch;
+    }
     auto is_out = [&](const Image* im) {
         return std::find(G.outputs.begin(), G.outputs.end(), im) != G.outputs.end();
     };

@@ -339,11 +339,12 @@ def test_section6_applications_plan(pctx):
     unfused = {"Gauss": 1, "Laplacian": 1, "FChain": 3, "SobelX": 1, "EdgFig2": 4, "Sobel": 3,
                "Unsharp": 4, "Harris": 9, "Tomasi": 9}
     # EdgFig2 (Listing 1, gx dead) maps onto the fused edge kernel's
-    # Magnitude(gy, gy) mask mode, Sobel (no Gaussian) onto its input-row mode,
+    # Magnitude(gy, gy) mask mode, Sobel and SobelX (no Gaussian) onto its
+    # input-row modes,
     # and Gauss (the 5x5 binomial Convolve) onto the binomial kernel
     special = {"Harris": "fused_harris_tma", "Tomasi": "fused_harris_tma",
                "EdgFig2": "fused_edge_tma", "Sobel": "fused_edge_tma",
-               "Gauss": "binomial5x5_tma"}
+               "SobelX": "fused_edge_tma", "Gauss": "binomial5x5_tma"}
     for name, build in A.APPS:
         src = H.hvxCreateImage(pctx, 1920, 1080, H.HVX_DF_U8)
         g, _ = build(pctx, src, 1920, 1080, True)

@@ -307,3 +307,42 @@ def test_binomial5x5_kernel(ctx, border):
                       c2.ravel(), 5, 5, 8, PG.empty(ctx, 40, 30, H.HVX_DF_U8))
     H.hvxVerifyGraph(g)
     assert PG.kernel_kinds(g) != ["binomial5x5_tma"]
+
+
+@pytest.mark.parametrize("border", ["replicate", "constant", "undefined"])
+def test_sobel_x_on_the_fused_edge_kernel(ctx, border):
+    # Sobel3x3 with only gx exported (S16) runs on the fused edge kernel's
+    # input-row mode, gx converted to S16 lanes in registers: every border,
+    # ragged sizes, extreme gradients, single and batched launches, exact
+    hb = {"replicate": H.HVX_BORDER_REPLICATE, "constant": H.HVX_BORDER_CONSTANT,
+          "undefined": H.HVX_BORDER_UNDEFINED}[border]
+    ob = {"replicate": O.BORDER_REPLICATE, "constant": O.BORDER_CONSTANT,
+          "undefined": O.BORDER_UNDEFINED}[border]
+    sizes = [(1, 1), (3, 2), (97, 45), (300, 200), (129, 121), (1920, 1080)]
+    items = []
+    for i, (w, h) in enumerate(sizes):
+        img = synth.rects_noise(w, h, seed=150 + i)
+        if i == 3:
+            img[:, ::2] = 0      # vertical stripes: gx at the extremes +-1020
+            img[:, 1::2] = 255
+        src = PG.upload(ctx, img, H.HVX_DF_U8)
+        gx = PG.empty(ctx, w, h, H.HVX_DF_S16)
+        g = H.hvxCreateGraph(ctx)
+        H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, src, gx, None), hb, 77)
+        H.hvxVerifyGraph(g)
+        assert PG.kernel_kinds(g) == ["fused_edge_tma"]
+        items.append((g, gx, O.sobel3x3(img, ob, 77)[0]))
+    for g, gx, ref in items:
+        H.hvxProcessGraph(g)
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(PG.download(gx)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
+        assert H.hvxGetValidRegion(gx) == ref.rect
+    for _, gx, _ in items:
+        w, h, _ = H.hvxQueryImage(gx)
+        z = np.zeros((h, w), np.int16)
+        H.hvxCopyImage(gx, z.ctypes.data, 2 * w, H.HVX_WRITE)
+    H.hvxProcessGraphBatch([it[0] for it in items])
+    H.hvxWaitBatch(ctx)
+    for _, gx, ref in items:
+        x0, y0, x1, y1 = ref.rect
+        np.testing.assert_array_equal(PG.download(gx)[y0:y1, x0:x1], ref.data[y0:y1, x0:x1])
