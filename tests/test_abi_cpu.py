@@ -508,3 +508,67 @@ def test_fault_injection_arguments():
     assert L.hvxTestInjectFault(7, 1) == H.HVX_ERROR_INVALID_PARAMETERS
     assert L.hvxTestInjectFault(H.HVX_FAULT_LAUNCH, 5) == H.HVX_SUCCESS
     assert L.hvxTestInjectFault(H.HVX_FAULT_NONE, 0) == H.HVX_SUCCESS
+
+
+def test_hand_written_kernel_matches(pctx):
+    # which single groups the planner maps onto the hand-written edge-family
+    # kernels, and which near misses it leaves to generated / interpreted code
+    import numpy as np
+    src = H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+
+    def kinds(build):
+        g = H.hvxCreateGraph(pctx)
+        build(g)
+        H.hvxVerifyGraph(g)
+        return PG.kernel_kinds(g)
+
+    def u8():
+        return H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_U8)
+
+    def s16():
+        return H.hvxCreateImage(pctx, 640, 480, H.HVX_DF_S16)
+
+    def sobel_mag_thr(g, a_sel, b_sel, thr_type=H.HVX_THRESHOLD_BINARY, gauss=True):
+        base = src
+        if gauss:
+            base = H.hvxCreateVirtualImage(g)
+            H.hvxGaussian3x3Node(g, src, base)
+        gx, gy, m = (H.hvxCreateVirtualImage(g) for _ in range(3))
+        H.hvxSobel3x3Node(g, base, gx, gy)
+        H.hvxMagnitudeNode(g, {"x": gx, "y": gy}[a_sel], {"x": gx, "y": gy}[b_sel], m)
+        H.hvxThresholdNode(g, m, thr_type, 100, 120, 255, 0, u8())
+
+    # Listing 1 (gx dead, Magnitude(gy, gy)) and the plain edge graph
+    assert kinds(lambda g: sobel_mag_thr(g, "y", "y")) == ["fused_edge_tma"]
+    assert kinds(lambda g: sobel_mag_thr(g, "x", "y")) == ["fused_edge_tma"]
+    # Magnitude(gx, gx) with gy dead, or a range threshold on Magnitude(gy, gy): not mapped
+    assert kinds(lambda g: sobel_mag_thr(g, "x", "x")) != ["fused_edge_tma"]
+    assert kinds(lambda g: sobel_mag_thr(g, "y", "y", H.HVX_THRESHOLD_RANGE)) != ["fused_edge_tma"]
+    # no Gaussian: Sobel -> Magnitude -> binary Threshold, and gx alone as S16
+    assert kinds(lambda g: sobel_mag_thr(g, "x", "y", gauss=False)) == ["fused_edge_tma"]
+    assert kinds(lambda g: H.hvxSobel3x3Node(g, src, s16(), None)) == ["fused_edge_tma"]
+    # gy alone, both derivatives exported, or a MIRROR border: not mapped
+    assert kinds(lambda g: H.hvxSobel3x3Node(g, src, None, s16())) != ["fused_edge_tma"]
+    assert kinds(lambda g: H.hvxSobel3x3Node(g, src, s16(), s16())) != ["fused_edge_tma"]
+
+    def mirrored(g):
+        H.hvxSetNodeBorder(H.hvxSobel3x3Node(g, src, s16(), None), H.HVX_BORDER_MIRROR, 0)
+    assert kinds(mirrored) != ["fused_edge_tma"]
+    # the 5x5 binomial Convolve (shift 8, U8 -> U8) and near misses
+    b5 = np.outer([1, 4, 6, 4, 1], [1, 4, 6, 4, 1]).astype(np.int32)
+    assert kinds(lambda g: H.hvxConvolveNode(g, src, b5.ravel(), 5, 5, 8, u8())) == \
+        ["binomial5x5_tma"]
+    assert kinds(lambda g: H.hvxConvolveNode(g, src, b5.ravel(), 5, 5, 7, u8())) != \
+        ["binomial5x5_tma"]
+    assert kinds(lambda g: H.hvxConvolveNode(g, src, b5.ravel(), 5, 5, 8, s16())) != \
+        ["binomial5x5_tma"]
+    odd = b5.copy()
+    odd[0, 0] = 2
+    assert kinds(lambda g: H.hvxConvolveNode(g, src, odd.ravel(), 5, 5, 8, u8())) != \
+        ["binomial5x5_tma"]
+    # HVX_CODEGEN_ONLY generates code for every one of them instead
+    g = H.hvxCreateGraph(pctx)
+    H.hvxConvolveNode(g, src, b5.ravel(), 5, 5, 8, u8())
+    H.hvxSetGraphCodegen(g, H.HVX_CODEGEN_ONLY)
+    H.hvxVerifyGraph(g)
+    assert PG.kernel_kinds(g) == ["staged_tile"]
